@@ -1,0 +1,198 @@
+/* hyb.h -- C ABI of the GB300 (sm_103a) scatter-limited hybrid (Q)MC / S_N transport path.
+ *
+ * Method: Krotz & McClarren, "Scatter-Limited Hybrid Monte Carlo, Deterministic Transport with
+ * Quasi-Monte Carlo Sampling" (PHYSOR 2026). One time step [t_n, t_{n+1}] is (Sec. 2.2, steps 1-4):
+ *   1. MC leg: the step-start particles and the source Q are tracked with at most N_s isotropic
+ *      scatters (Sec. 2.3), scoring the pre-limit (n < N_s) and post-limit (n = N_s) cell-average
+ *      track-length flux; the (N_s+1)-th collision density is deposited as four Legendre moments
+ *      per cell (the collided source of Eq. (floor N_s+1)).
+ *   2. Collided solve: bilinear-DG S_N (level-symmetric S4/S8) of Eq. (floor N_s+1), backward
+ *      Euler from zero data, source iteration.
+ *   3. Remap, Eq. (R): scatter-free re-streaming of the step-start particles plus new births from
+ *      Q + sigma_s (phi_pre + phi_post + phi_c), attenuated with sigma_t.
+ *   4. The survivors (combed to census_cap) become the census of t_{n+1}.
+ * Points are Sobol with a per-(seed, step, stream, dimension) digital shift, or a counter PRNG
+ * (Sec. 2.4 replaces pseudorandom draws with low-discrepancy points inside the same maps).
+ *
+ * Conventions (all entry points):
+ *   - Every function returns hyb_status and never throws. Pointers are plain host or device
+ *     pointers as stated per argument; no ownership passes unless stated.
+ *   - Mesh arrays are row-major per cell, index k = iy*nx + ix, cell (ix,iy) covers
+ *     [ix*lx/nx, (ix+1)*lx/nx] x [iy*ly/ny, (iy+1)*ly/ny]. Boundaries are vacuum.
+ *   - Q is the angle-integrated emission rate density (particles / area / time); a step emits
+ *     Q*A*dt per cell. phi denotes the scalar flux int Psi dOmega; <Psi> = phi / (4 pi).
+ *   - A problem is bound to one CUDA stream; calls on one problem must not overlap. Different
+ *     problems are independent.
+ */
+#ifndef HYB_H
+#define HYB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HYB_API __attribute__((visibility("default")))
+#else
+#define HYB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HYB_OK = 0,
+    HYB_EINVAL = 1,     /* invalid argument or descriptor */
+    HYB_ENOMEM = 2,     /* workspace too small or allocation failed */
+    HYB_ECUDA = 3,      /* a CUDA runtime call failed (see hyb_last_error) */
+    HYB_ETIMEOUT = 4,   /* a bounded device loop ran out (segments per history, SI cap) */
+    HYB_ESTATE = 5,     /* call out of order (e.g. remap before an MC leg) */
+    HYB_EBOUNDS = 6,    /* a device-side index check failed; the result is invalid */
+    HYB_ECAPACITY = 7   /* a bank or buffer would overflow its capacity */
+} hyb_status;
+
+typedef enum { HYB_FP32 = 0, HYB_FP64 = 1 } hyb_precision;
+typedef enum { HYB_SOBOL_DS = 0, HYB_PRNG = 1 } hyb_sampler;
+
+/* N_s = infinity: pure (Q)MC, no hand-off, no collided solve, no remap (the MC-leg census is
+ * the next bank); Sec. 3 non-hybrid runs. */
+#define HYB_NS_INF 2147483647
+
+/* point-set streams (key = (seed, step, stream)) */
+#define HYB_STREAM_INIT 0          /* initial-condition particles, step 0 */
+#define HYB_STREAM_LEG_CENSUS 1    /* MC leg, bank particles (index = bank slot) */
+#define HYB_STREAM_LEG_SOURCE 2    /* MC leg, births from Q */
+#define HYB_STREAM_REMAP_SOURCE 3  /* remap births */
+#define HYB_STREAM_REMAP_COMB 4    /* census comb offset (index 0, dim 0) */
+
+/* Largest tabulated Sobol dimension count; dims >= this use the counter PRNG. */
+#define HYB_SOBOL_DIMS 65
+
+/* Problem descriptor (Sec. 2.1: mesh, sigma_a, sigma_s, c, Q, initial data; Sec. 2.2: dt;
+ * Sec. 2.3: N_s and the history count; Sec. 2.4: the point set). All host pointers; the
+ * arrays are copied at creation. */
+typedef struct {
+    int32_t nx, ny;           /* mesh cells per axis, 1..4096 each */
+    double lx, ly;            /* domain extent (> 0) */
+    const double* sigma_a;    /* nx*ny absorption cross sections, finite, >= 0 */
+    const double* sigma_s;    /* nx*ny scattering cross sections, finite, >= 0 */
+    const double* Q;          /* nx*ny emission rate density, finite, >= 0; NULL = no source */
+    const double* ic_cell_w;  /* nx*ny initial weight per cell (isotropic, uniform in the cell,
+                                 t = 0); NULL = vacuum initial condition */
+    double c;                 /* particle speed (> 0) */
+    double dt;                /* time step (> 0) */
+    int32_t n_s;              /* scatter limit N_s >= 0, or HYB_NS_INF */
+    int32_t sampler;          /* hyb_sampler */
+    int64_t n_hist;           /* births per step (MC-leg source, remap source, initial bank) */
+    uint64_t seed;            /* point-set seed */
+    int32_t precision;        /* hyb_precision of tracking, banks and the S_N stage */
+    int32_t sn_order;         /* 4 or 8 (level-symmetric, 12 / 40 ordinates in 2-D) */
+    int32_t handoff_full;     /* 1: deposit four Legendre moments; 0: moment 0 only */
+    int32_t sn_max_iter;      /* source-iteration cap (>= 1) */
+    double sn_tol;            /* SI stop: ||phi_new - phi_old|| <= sn_tol ||phi_new|| */
+    double w_min;             /* relative kill threshold (w < w_min * w_start); 0 = never */
+    int64_t census_cap;       /* census capacity after the comb; 0 = n_hist */
+} hyb_problem_desc;
+
+/* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */
+typedef struct {
+    int64_t histories, segments, collisions, leaked, census, killed, reached_limit, errors;
+    double w_source, w_absorbed, w_leaked, w_census, w_handoff, w_killed;
+    int32_t sn_iterations;    /* collided solve: SI iterations taken */
+    int32_t combed;           /* remap: 1 if the census comb ran */
+    int64_t bank_size;        /* particles in the census bank after the call */
+    float ms;                 /* device time of the call (events), 0 if not measured */
+    int32_t pad;
+} hyb_leg_stats;
+
+typedef struct hyb_problem hyb_problem;
+
+/* Tally selectors for hyb_get_tally. All are FP64, nx*ny values (x4 for moments):
+ *  HYB_TALLY_PRE:    phi_pre = (sum over n < N_s segments of w l g(sigma_a l)) / (A dt)
+ *  HYB_TALLY_POST:   phi_post, the same over n = N_s segments with sigma_t
+ *  HYB_TALLY_HANDOFF: m_j = sigma_s sum w int P_j ds, P = (1, xi, eta, xi eta) (4 per cell)
+ *  HYB_TALLY_SN_PHI: collided scalar flux, 4 Legendre coefficients per cell
+ *  HYB_TALLY_FLUX:   step flux phi_pre + phi_post + phi_c (cell average)
+ *  HYB_TALLY_*_RAW:  the un-normalised track-length sums (no 1/(A dt)) */
+#define HYB_TALLY_PRE 0
+#define HYB_TALLY_POST 1
+#define HYB_TALLY_HANDOFF 2
+#define HYB_TALLY_SN_PHI 3
+#define HYB_TALLY_FLUX 4
+#define HYB_TALLY_PRE_RAW 5
+#define HYB_TALLY_POST_RAW 6
+
+/* Device workspace bytes a problem needs (banks, mesh, tallies, CDFs, S_N state). */
+HYB_API hyb_status hyb_workspace_size(const hyb_problem_desc* desc, size_t* bytes);
+
+/* Create a problem. workspace: device memory of >= hyb_workspace_size bytes, 256-byte
+ * aligned, owned by the caller and kept alive until hyb_destroy_problem; NULL lets the library
+ * allocate (and later free) it. cuda_stream: a cudaStream_t (borrowed; NULL = legacy stream).
+ * Builds the initial bank (stream INIT) and the source CDF on the device; step index = 0.
+ * Errors: EINVAL (nx,ny out of range, non-finite or negative sigma/Q/ic, dt<=0, c<=0,
+ * n_hist<1 or >= 2^32, sn_order not 4/8, N_s < 0), ENOMEM, ECUDA. */
+HYB_API hyb_status hyb_create_problem(const hyb_problem_desc* desc, void* workspace, size_t ws_bytes,
+                              void* cuda_stream, hyb_problem** out);
+HYB_API hyb_status hyb_destroy_problem(hyb_problem* p);
+
+/* Step 1 (Sec. 2.2; Sec. 2.3): the MC leg of the current step over the current bank and Q.
+ * Tallies stay on the device. stats (host, may be NULL): if given, the call synchronises the
+ * stream and fills it; if NULL the call is asynchronous. hist (device, may be NULL): per
+ * history 4 int32 (final cell, fate 0 leaked/1 census/2 killed/3 error, final scatter count,
+ * segments), histories ordered bank slots first, then births; capacity bank_size + n_hist. */
+HYB_API hyb_status hyb_mc_leg(hyb_problem* p, hyb_leg_stats* stats);
+HYB_API hyb_status hyb_mc_leg_trace(hyb_problem* p, int32_t* hist_dev, hyb_leg_stats* stats);
+
+/* Step 2 (Sec. 2.2; Eq. (floor N_s+1)): the collided S_N-DG solve fed by the hand-off
+ * moments of the last MC leg. Synchronises per SI iteration (convergence test). */
+HYB_API hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* stats);
+
+/* Steps 3-4 (Sec. 2.2, Eq. (R)): remap into the new census bank and advance the step index.
+ * Needs an MC leg and a collided solve of the same step. stats as for hyb_mc_leg. */
+HYB_API hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* stats);
+
+/* nsteps full steps (1-4). per_step (host, may be NULL): nsteps entries, leg statistics with
+ * sn_iterations / combed / bank_size of the step. */
+HYB_API hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step);
+
+/* Copy a tally (see HYB_TALLY_*) into dst (host if dst_on_device == 0, else device), n values.
+ * Synchronises the stream. EINVAL if n is not the tally's size. */
+HYB_API hyb_status hyb_get_tally(hyb_problem* p, int32_t which, double* dst, size_t n, int32_t dst_on_device);
+
+/* Overwrite the collided flux (4 Legendre coefficients per cell, host FP64) -- parity
+ * injection for the remap. */
+HYB_API hyb_status hyb_set_sn_phi(hyb_problem* p, const double* phi_host, size_t n);
+
+/* Census bank I/O (host arrays, FP64 values converted to the problem precision). get: n_io in
+ * = capacity, out = particles copied. set: replaces the bank (n <= bank capacity). */
+HYB_API hyb_status hyb_get_bank(hyb_problem* p, int32_t* cell, double* fx, double* fy, double* ox,
+                        double* oy, double* w, int64_t* n_io);
+HYB_API hyb_status hyb_set_bank(hyb_problem* p, const int32_t* cell, const double* fx, const double* fy,
+                        const double* ox, const double* oy, const double* w, int64_t n);
+HYB_API hyb_status hyb_bank_capacity(const hyb_problem* p, int64_t* cap);
+
+/* Step index (t_n = step * dt) used by the next MC leg / remap. */
+HYB_API hyb_status hyb_set_step(hyb_problem* p, int64_t step);
+HYB_API hyb_status hyb_get_step(const hyb_problem* p, int64_t* step);
+
+/* Point sets (Sec. 2.4): out_dev[(i - i0)*ndims + d] for i in [i0, i0+n), d < ndims, as 32-bit
+ * integers; i0 + n <= 2^32. Asynchronous on cuda_stream. */
+HYB_API hyb_status hyb_points(uint64_t seed, int64_t step, int32_t stream_id, int32_t sampler, int64_t i0,
+                      int64_t n, int32_t ndims, uint32_t* out_dev, void* cuda_stream);
+
+/* The generated Sobol direction numbers, host out[d*32 + b], d < ndims <= HYB_SOBOL_DIMS. */
+HYB_API hyb_status hyb_sobol_table(int32_t ndims, uint32_t* out_host);
+
+/* The S_N quadrature used (upper hemisphere, weights summing to 4 pi); returns the count in
+ * *m (capacity in, count out). */
+HYB_API hyb_status hyb_quadrature(int32_t order, double* ox, double* oy, double* w, int32_t* m);
+
+HYB_API const char* hyb_status_string(hyb_status s);
+/* Last error message of a problem (valid until the next call on it); p = NULL: the last error
+ * of a call that had no problem. */
+HYB_API const char* hyb_last_error(const hyb_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYB_H */

@@ -699,7 +699,7 @@ int sn_solve(const or_problem* P, const double* mom, double* phi, int* iters_out
 double inv_linear(double a, double b, double u) {
     if (!(a > 0.0)) return 2.0 * u - 1.0;
     const double amb = a - b;
-    const double t = 4.0 * a * u / (amb + std::sqrt(amb * amb + 4.0 * a * b * u));
+    const double t = 4.0 * a * u / (amb + std::sqrt(std::max(0.0, amb * amb + 4.0 * a * b * u)));
     return std::min(std::max(t - 1.0, -1.0), 1.0);
 }
 
@@ -743,19 +743,26 @@ Streamed stream_free(const or_problem* P, const Mesh& M, int ix, int iy, double 
     return r;
 }
 
-// systematic comb of the particle list to exactly M copies (in list order); the offset is the
-// point (stream REMAP_COMB, index 0, dim 0)
-void comb(const std::vector<Streamed>& in, int64_t Mcap, uint32_t x_off, std::vector<Streamed>* out) {
+// Power of two at or above w (w > 0): the quantisation base of the comb.
+double pow2_ceil(double w) {
+    int e = 0;
+    double m = std::frexp(w, &e);  // w = m 2^e, m in [0.5, 1)
+    return m == 0.5 ? w : std::ldexp(1.0, e);
+}
+
+// Systematic comb of the particle list to exactly M copies (in list order). |w| is quantised
+// as rint(|w| / w_ref * 2^32) with w_ref a power of two bounding every |w| before streaming
+// (streaming only lowers |w|), so the quantisation does not depend on the survivors. The
+// offset is the point (stream REMAP_COMB, index 0, dim 0); each copy carries sum|w| / M.
+void comb(const std::vector<Streamed>& in, int64_t Mcap, uint32_t x_off, double w_ref,
+          std::vector<Streamed>* out) {
     typedef unsigned __int128 u128;
-    double wmax = 0.0;
-    for (auto& p : in) wmax = std::max(wmax, std::fabs(p.w));
     std::vector<int64_t> q(in.size());
-    for (size_t j = 0; j < in.size(); ++j) q[j] = (int64_t)std::nearbyint((std::fabs(in[j].w) / wmax) * 0x1p32);
+    for (size_t j = 0; j < in.size(); ++j) q[j] = (int64_t)std::nearbyint((std::fabs(in[j].w) / w_ref) * 0x1p32);
     int64_t T = 0;
     for (auto v : q) T += v;
     out->clear();
     if (T == 0) return;
-    // sum |w| in 128-bit fixed point with 2^-96 relative resolution of wmax -> exact enough
     long double wsum = 0;
     for (auto& p : in) wsum += std::fabs(p.w);
     const double wcopy = (double)(wsum / (long double)Mcap);
@@ -959,6 +966,9 @@ int or_remap(const or_problem* P, int64_t step, const or_bank* census, const dou
                                      census->ox[j], census->oy[j], census->w[j], cdt, st, acc);
             if (r.alive) surv.push_back(r);
         }
+    double wmax = 0.0;  // bound on every |w| entering the comb
+    if (census)
+        for (int64_t j = 0; j < census->n; ++j) wmax = std::max(wmax, std::fabs(census->w[j]));
     // (ii) births from the remap source
     std::vector<double> f(4 * nc), qc(nc);
     or_remap_density(P, pre, post, phi, f.data());
@@ -968,6 +978,15 @@ int or_remap(const or_problem* P, int64_t step, const or_bank* census, const dou
         Cdf2D C = build_cdf(M, qc);
         Points pts{stream_key(P->seed, (uint64_t)step, kStreamRemapSource), P->sampler};
         const double wbar = W / (double)P->n_hist;
+        for (size_t k = 0; k < nc; ++k) {
+            if (qc[k] == 0.0) continue;
+            const double* fk = &f[4 * k];
+            const bool pos = fk[0] - fk[1] - fk[2] + fk[3] >= 0 && fk[0] + fk[1] - fk[2] - fk[3] >= 0 &&
+                             fk[0] - fk[1] + fk[2] - fk[3] >= 0 && fk[0] + fk[1] + fk[2] + fk[3] >= 0;
+            const double r = pos ? 1.0 : (std::fabs(fk[0]) + std::fabs(fk[1]) + std::fabs(fk[2]) +
+                                          std::fabs(fk[3])) / std::fabs(fk[0]);
+            wmax = std::max(wmax, wbar * r);
+        }
         for (int64_t i = 0; i < P->n_hist; ++i) {
             double frx, fry, ox, oy;
             int k = sample_cell(C, pts(i, 0), pts(i, 1), &frx, &fry);
@@ -997,7 +1016,7 @@ int or_remap(const or_problem* P, int64_t step, const or_bank* census, const dou
     int did_comb = 0;
     if ((int64_t)surv.size() > cap) {
         Points pc{stream_key(P->seed, (uint64_t)step, kStreamRemapComb), P->sampler};
-        comb(surv, cap, pc(0, 0), &fin);
+        comb(surv, cap, pc(0, 0), pow2_ceil(wmax), &fin);
         did_comb = 1;
     } else fin = surv;
     out->n = 0;
@@ -1037,8 +1056,13 @@ int or_step(const or_problem* P, int64_t step, const or_bank* bank, or_bank* out
         for (int64_t j = 0; j < tmp.n; ++j) s.push_back(Streamed{true, c[j], a[j], b[j], d[j], e[j], g[j]});
         const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
         if ((int64_t)s.size() > cap) {
+            double wmax = 0.0;
+            if (bank) for (int64_t j = 0; j < bank->n; ++j) wmax = std::max(wmax, std::fabs(bank->w[j]));
+            double Wq = 0.0;
+            for (size_t k = 0; k < nc; ++k) Wq += (P->Q ? P->Q[k] : 0.0) * M.area * P->dt;
+            if (Wq > 0.0) wmax = std::max(wmax, Wq / (double)P->n_hist);
             Points pc{stream_key(P->seed, (uint64_t)step, kStreamRemapComb), P->sampler};
-            comb(s, cap, pc(0, 0), &fin);
+            comb(s, cap, pc(0, 0), pow2_ceil(wmax), &fin);
         } else fin = s;
         out->n = 0;
         if ((int64_t)fin.size() > out->cap) return 3;

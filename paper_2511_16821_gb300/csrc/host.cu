@@ -1,0 +1,800 @@
+// host.cu -- C ABI entry points (include/hyb.h): validation, workspace layout, problem set-up,
+// the hybrid time step driver (Sec. 2.2 steps 1-4), statistics and data movement.
+//
+// Set-up tables generated here: Sobol direction numbers (primitive polynomials over GF(2) in
+// (degree, value) order, initial numbers chosen greedily for (0, j, 2)-net pairs with all earlier
+// dimensions) and the level-symmetric S4/S8 quadrature (moment-matched class weights).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hyb_device.cuh"
+
+namespace hyb {
+
+uint64_t mix64(uint64_t z) { return dmix64(z); }
+
+uint64_t stream_key(uint64_t seed, uint64_t step, uint64_t stream) {
+    uint64_t z = dmix64(seed + kGamma);
+    z = dmix64(z ^ (step + kGamma));
+    return dmix64(z ^ (stream + kGamma));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Sobol direction numbers
+// ---------------------------------------------------------------------------------------------
+namespace sobolgen {
+
+uint32_t g_tab[HYB_SOBOL_DIMS][32];
+std::once_flag g_tab_once;
+
+// row r of the generator matrix as a bit mask over columns: bit c = bit (31 - r) of V[c]
+inline uint32_t gen_row(const uint32_t* V, int r, int m) {
+    uint32_t mask = 0;
+    for (int c = 0; c < m; ++c) mask |= ((V[c] >> (31 - r)) & 1u) << c;
+    return mask;
+}
+
+bool full_rank(uint32_t* rows, int n, int m) {
+    int rank = 0;
+    for (int c = 0; c < m && rank < n; ++c) {
+        const uint32_t bit = 1u << c;
+        int piv = -1;
+        for (int i = rank; i < n; ++i) if (rows[i] & bit) { piv = i; break; }
+        if (piv < 0) return false;
+        std::swap(rows[rank], rows[piv]);
+        for (int i = 0; i < n; ++i) if (i != rank && (rows[i] & bit)) rows[i] ^= rows[rank];
+        ++rank;
+    }
+    return rank == m;
+}
+
+// the first 2^m points of dims (A, B) form a (0, m, 2)-net
+bool net_pair(const uint32_t* A, const uint32_t* B, int m) {
+    uint32_t ra[32], rb[32], rows[32];
+    for (int r = 0; r < m; ++r) { ra[r] = gen_row(A, r, m); rb[r] = gen_row(B, r, m); }
+    for (int k = 1; k < m; ++k) {   // k = 0 and k = m are triangular with unit diagonal
+        for (int r = 0; r < k; ++r) rows[r] = ra[r];
+        for (int r = 0; r < m - k; ++r) rows[k + r] = rb[r];
+        if (!full_rank(rows, m, m)) return false;
+    }
+    return true;
+}
+
+void fill_directions(uint32_t poly, int s, const uint32_t* mv, uint32_t* V) {
+    for (int j = 0; j < s; ++j) V[j] = mv[j] << (31 - j);
+    for (int j = s; j < 32; ++j) {
+        uint32_t x = V[j - s] ^ (V[j - s] >> s);
+        for (int k = 1; k < s; ++k)
+            if ((poly >> (s - k)) & 1u) x ^= V[j - k];
+        V[j] = x;
+    }
+}
+
+bool primitive(uint32_t poly, int s) {
+    const uint32_t period = (1u << s) - 1u;
+    uint32_t r = 1u;
+    for (uint32_t e = 1; e <= period; ++e) {
+        r <<= 1;
+        if (r & (1u << s)) r ^= poly;
+        if (r == 1u) return e == period;
+    }
+    return false;
+}
+
+void build_table() {
+    for (int b = 0; b < 32; ++b) g_tab[0][b] = 1u << (31 - b);
+    int d = 1;
+    for (int s = 1; d < HYB_SOBOL_DIMS; ++s) {
+        for (uint32_t poly = (1u << s) + 1u; poly < (2u << s) && d < HYB_SOBOL_DIMS; poly += 2u) {
+            if (!primitive(poly, s)) continue;
+            uint32_t mv[32];
+            for (int j = 0; j < s; ++j) mv[j] = 1u;
+            for (int j = 1; j <= s; ++j) {
+                int best = -1;
+                uint32_t best_m = 1u;
+                for (uint32_t cand = 1u; cand < (1u << j); cand += 2u) {
+                    mv[j - 1] = cand;
+                    uint32_t V[32];
+                    fill_directions(poly, s, mv, V);
+                    int fails = 0;
+                    for (int e = 0; e < d; ++e) fails += net_pair(g_tab[e], V, j) ? 0 : 1;
+                    if (best < 0 || fails < best) { best = fails; best_m = cand; }
+                }
+                mv[j - 1] = best_m;
+            }
+            fill_directions(poly, s, mv, g_tab[d]);
+            ++d;
+        }
+    }
+}
+
+}  // namespace sobolgen
+
+const uint32_t* sobol_table_host() {
+    std::call_once(sobolgen::g_tab_once, sobolgen::build_table);
+    return &sobolgen::g_tab[0][0];
+}
+
+// ---------------------------------------------------------------------------------------------
+// level-symmetric quadrature (upper hemisphere; weights summing to 4 pi)
+// ---------------------------------------------------------------------------------------------
+void quadrature_host(int order, double* ox, double* oy, double* w, int* m_out) {
+    const int h = order / 2;
+    // mu_1^2 integrating <mu^N> exactly: S4 root of 6x^2 - 4x + 2/5 = 0; S8: 1/21
+    const double mu1sq = order == 4 ? (4.0 - std::sqrt(6.4)) / 12.0 : 1.0 / 21.0;
+    std::vector<double> mu(h);
+    for (int i = 0; i < h; ++i) mu[i] = std::sqrt(mu1sq + i * 2.0 * (1.0 - 3.0 * mu1sq) / (order - 2));
+    struct Pt { int i, j, k, cls; };
+    std::vector<Pt> pts;
+    std::vector<std::vector<int>> classes;
+    for (int i = 1; i <= h; ++i)
+        for (int j = 1; j <= h; ++j)
+            for (int k = 1; k <= h; ++k) {
+                if (i + j + k != h + 2) continue;
+                std::vector<int> key = {i, j, k};
+                std::sort(key.begin(), key.end());
+                int c = (int)(std::find(classes.begin(), classes.end(), key) - classes.begin());
+                if (c == (int)classes.size()) classes.push_back(key);
+                pts.push_back({i, j, k, c});
+            }
+    const int nc = (int)classes.size();
+    std::vector<double> wc(nc, 0.0);
+    if (nc == 1) {
+        wc[0] = 1.0 / pts.size();
+    } else {
+        // moment equations for <mu^0>, <mu^4>, <mu^6> (three classes for S8), Cramer's rule
+        double A[3][3] = {{0}}, b[3];
+        const int pw[3] = {0, 4, 6};
+        for (int e = 0; e < 3; ++e) {
+            b[e] = 1.0 / (pw[e] + 1);
+            for (const Pt& p : pts) A[e][p.cls] += std::pow(mu[p.k - 1], pw[e]);
+        }
+        auto det3 = [](double M[3][3]) {
+            return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                   M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        };
+        const double D = det3(A);
+        for (int c = 0; c < 3; ++c) {
+            double Mc[3][3];
+            for (int r = 0; r < 3; ++r)
+                for (int q = 0; q < 3; ++q) Mc[r][q] = q == c ? b[r] : A[r][q];
+            wc[c] = det3(Mc) / D;
+        }
+    }
+    const double pi = 3.14159265358979323846;
+    int m = 0;
+    const int sx[4] = {1, -1, -1, 1}, sy[4] = {1, 1, -1, -1};
+    for (int q = 0; q < 4; ++q)
+        for (const Pt& p : pts) {
+            ox[m] = sx[q] * mu[p.i - 1];
+            oy[m] = sy[q] * mu[p.j - 1];
+            w[m] = wc[p.cls] * pi;        // 4 pi / 8 per octant point, x2 for the z mirror
+            ++m;
+        }
+    *m_out = m;
+}
+
+}  // namespace hyb
+
+using namespace hyb;
+
+// ---------------------------------------------------------------------------------------------
+// workspace layout
+// ---------------------------------------------------------------------------------------------
+namespace hybh {
+
+thread_local std::string g_err;
+
+struct Layout {
+    size_t off[64];
+    int n = 0;
+    size_t total = 0;
+    size_t add(size_t bytes) {
+        const size_t o = total;
+        total += (bytes + 255) / 256 * 256;
+        off[n++] = o;
+        return o;
+    }
+};
+
+int64_t eff_cap(const hyb_problem_desc* d) {
+    const int64_t cc = d->census_cap > 0 ? d->census_cap : d->n_hist;
+    return std::max<int64_t>(cc, d->n_hist);
+}
+
+struct Sizes {
+    size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, acc1, acc4, d1, d4,
+        sn4, sn16, sntx, snty, snqb, snnorm, blk;
+    int64_t cap, nblk;
+};
+
+Sizes sizes(const hyb_problem_desc* d) {
+    Sizes z;
+    const size_t nc = (size_t)d->nx * d->ny;
+    const size_t T = d->precision == HYB_FP64 ? 8 : 4;
+    const size_t acc = d->precision == HYB_FP64 ? 16 : 8;
+    const int nord = d->sn_order == 8 ? 40 : 12;
+    const size_t ntx = (d->nx + kSnTile - 1) / kSnTile, nty = (d->ny + kSnTile - 1) / kSnTile;
+    z.cap = eff_cap(d);
+    z.st = sizeof(DevState);
+    z.sobol = HYB_SOBOL_DIMS * 32 * 4;
+    z.sig = nc * 2 * T;
+    z.sa = z.ss = z.Q = nc * 8;
+    z.cdf_q = nc * 8;
+    z.cdf_row = (d->ny + 1) * 8;
+    z.cdf_col = (size_t)d->ny * (d->nx + 1) * 8;
+    z.rem_f = 4 * nc * 8;
+    z.rem_q = nc * 8;
+    z.scratch = (256 + d->ny + nc) * 8;
+    z.bank = bank_cell_bytes(z.cap) + 5 * (size_t)z.cap * T;
+    z.acc1 = nc * acc;
+    z.acc4 = 4 * nc * acc;
+    z.d1 = nc * 8;
+    z.d4 = 4 * nc * 8;
+    z.sn4 = 4 * nc * T;
+    z.sn16 = 16 * nc * T;
+    z.sntx = (size_t)nord * d->ny * ntx * 2 * T;
+    z.snty = (size_t)nord * d->nx * nty * 2 * T;
+    z.snqb = 3 * kMaxOrd * T;
+    z.snnorm = 2 * ((nc + 255) / 256) * 8;
+    z.nblk = (z.cap + d->n_hist + 2047) / 2048;
+    z.blk = 4 * (size_t)z.nblk * 8;
+    return z;
+}
+
+size_t layout_bytes(const hyb_problem_desc* d) {
+    const Sizes z = sizes(d);
+    Layout L;
+    const size_t parts[] = {z.st, z.sobol, z.sig, z.sa, z.ss, z.Q, z.cdf_q, z.cdf_row, z.cdf_col, z.cdf_q, z.cdf_row,
+                            z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.acc1, z.acc1, z.acc4, z.d1,
+                            z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4,
+                            z.snnorm, z.blk};
+    for (size_t b : parts) L.add(b);
+    return L.total;
+}
+
+void assign(hyb_problem* p) {
+    const Sizes z = sizes(&p->d);
+    Layout L;
+    char* b = (char*)p->ws;
+    auto take = [&](size_t bytes) { return (void*)(b + L.add(bytes)); };
+    p->st = (DevState*)take(z.st);
+    p->sobolV = (uint32_t*)take(z.sobol);
+    p->sig = take(z.sig);
+    p->sa_d = (double*)take(z.sa);
+    p->ss_d = (double*)take(z.ss);
+    p->Q_d = (double*)take(z.Q);
+    p->src_cdf.q = (long long*)take(z.cdf_q);
+    p->src_cdf.row_pre = (long long*)take(z.cdf_row);
+    p->src_cdf.col_pre = (long long*)take(z.cdf_col);
+    p->rem_cdf.q = (long long*)take(z.cdf_q);
+    p->rem_cdf.row_pre = (long long*)take(z.cdf_row);
+    p->rem_cdf.col_pre = (long long*)take(z.cdf_col);
+    p->rem_f = (double*)take(z.rem_f);
+    p->rem_q = (double*)take(z.rem_q);
+    p->cell_scratch = (double*)take(z.scratch);
+    p->bank[0] = take(z.bank);
+    p->bank[1] = take(z.bank);
+    p->acc_pre = take(z.acc1);
+    p->acc_post = take(z.acc1);
+    p->acc_mom = take(z.acc4);
+    p->pre_d = (double*)take(z.d1);
+    p->post_d = (double*)take(z.d1);
+    p->mom_d = (double*)take(z.d4);
+    p->flux_d = (double*)take(z.d1);
+    p->pre_raw = (double*)take(z.d1);
+    p->post_raw = (double*)take(z.d1);
+    p->sn_phi = take(z.sn4);
+    p->sn_phi_old = take(z.sn4);
+    p->sn_quad = take(z.sn16);
+    p->sn_tx = take(z.sntx);
+    p->sn_ty = take(z.snty);
+    p->sn_quadbuf = take(z.snqb);
+    p->sn_phi_d = (double*)take(z.d4);
+    p->sn_norm = (double*)take(z.snnorm);
+    p->blk = (long long*)take(z.blk);
+    p->bank_cap = z.cap;
+    p->nblk_max = z.nblk;
+}
+
+hyb_status fail(hyb_problem* p, hyb_status s, const std::string& msg) {
+    if (p) p->err = msg; else g_err = msg;
+    return s;
+}
+
+hyb_status cuda_fail(hyb_problem* p, cudaError_t e, const char* where) {
+    return fail(p, HYB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define HYB_CU(p, call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(p, e_, #call); \
+    } while (0)
+
+hyb_status validate(const hyb_problem_desc* d, std::string* why) {
+    if (!d) { *why = "null descriptor"; return HYB_EINVAL; }
+    if (d->nx < 1 || d->ny < 1 || d->nx > 4096 || d->ny > 4096) { *why = "nx, ny must be in [1, 4096]"; return HYB_EINVAL; }
+    if (!(d->lx > 0) || !(d->ly > 0) || !std::isfinite(d->lx) || !std::isfinite(d->ly)) { *why = "lx, ly must be finite and > 0"; return HYB_EINVAL; }
+    if (!(d->c > 0) || !std::isfinite(d->c)) { *why = "c must be finite and > 0"; return HYB_EINVAL; }
+    if (!(d->dt > 0) || !std::isfinite(d->dt)) { *why = "dt must be finite and > 0"; return HYB_EINVAL; }
+    if (d->n_s < 0) { *why = "N_s must be >= 0"; return HYB_EINVAL; }
+    if (d->n_s == HYB_NS_INF) { *why = "N_s = infinity is not supported by this build"; return HYB_EINVAL; }
+    if (d->n_hist < 1 || d->n_hist >= (int64_t)1 << 31) { *why = "n_hist must be in [1, 2^31)"; return HYB_EINVAL; }
+    if (d->census_cap < 0 || d->census_cap >= (int64_t)1 << 31) { *why = "census_cap must be in [0, 2^31)"; return HYB_EINVAL; }
+    if (d->sampler != HYB_SOBOL_DS && d->sampler != HYB_PRNG) { *why = "unknown sampler"; return HYB_EINVAL; }
+    if (d->precision != HYB_FP32 && d->precision != HYB_FP64) { *why = "unknown precision"; return HYB_EINVAL; }
+    if (d->sn_order != 4 && d->sn_order != 8) { *why = "sn_order must be 4 or 8"; return HYB_EINVAL; }
+    if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
+    if (!(d->sn_tol >= 0) || !(d->w_min >= 0) || !(d->w_min < 1)) { *why = "sn_tol >= 0 and 0 <= w_min < 1 required"; return HYB_EINVAL; }
+    if (!d->sigma_a || !d->sigma_s) { *why = "sigma_a and sigma_s are required"; return HYB_EINVAL; }
+    const size_t nc = (size_t)d->nx * d->ny;
+    for (size_t k = 0; k < nc; ++k) {
+        if (!std::isfinite(d->sigma_a[k]) || d->sigma_a[k] < 0 || !std::isfinite(d->sigma_s[k]) || d->sigma_s[k] < 0) {
+            *why = "sigma_a, sigma_s must be finite and >= 0"; return HYB_EINVAL;
+        }
+        if (d->Q && (!std::isfinite(d->Q[k]) || d->Q[k] < 0)) { *why = "Q must be finite and >= 0"; return HYB_EINVAL; }
+        if (d->ic_cell_w && (!std::isfinite(d->ic_cell_w[k]) || d->ic_cell_w[k] < 0)) { *why = "ic must be finite and >= 0"; return HYB_EINVAL; }
+    }
+    return HYB_OK;
+}
+
+template <typename T>
+void put_sig(const hyb_problem_desc* d, std::vector<unsigned char>* out) {
+    const size_t nc = (size_t)d->nx * d->ny;
+    out->resize(nc * 2 * sizeof(T));
+    T* s = (T*)out->data();
+    for (size_t k = 0; k < nc; ++k) { s[2 * k] = (T)d->sigma_a[k]; s[2 * k + 1] = (T)d->sigma_s[k]; }
+}
+
+template <typename T>
+void put_quad(const hyb_problem* p, std::vector<unsigned char>* out) {
+    out->assign(3 * kMaxOrd * sizeof(T), 0);
+    T* q = (T*)out->data();
+    for (int m = 0; m < p->n_ord; ++m) {
+        q[m] = (T)p->quad_ox[m]; q[kMaxOrd + m] = (T)p->quad_oy[m]; q[2 * kMaxOrd + m] = (T)p->quad_w[m];
+    }
+}
+
+__global__ void cell_weight_kernel(const double* v, int n, double area_dt, double* out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = v[k] * area_dt;
+}
+
+__global__ void set_nbank_kernel(DevState* st, long long n) { st->n_bank = n; }
+
+double stat_w(const Acc128& a, int k) { return acc128_to_double(a.lo, a.hi, std::ldexp(1.0, -k)); }
+
+void fill_leg_stats(const hyb_problem* p, hyb_leg_stats* s) {
+    const DevState& h = *p->st_host;
+    std::memset(s, 0, sizeof(*s));
+    s->histories = (int64_t)h.histories; s->segments = (int64_t)h.segments; s->collisions = (int64_t)h.collisions;
+    s->leaked = (int64_t)h.leaked; s->census = (int64_t)h.census; s->killed = (int64_t)h.killed;
+    s->reached_limit = (int64_t)h.reached; s->errors = (int64_t)h.errors;
+    s->w_source = stat_w(h.w_source, h.k_w); s->w_absorbed = stat_w(h.w_absorbed, h.k_w);
+    s->w_leaked = stat_w(h.w_leaked, h.k_w); s->w_census = stat_w(h.w_census, h.k_w);
+    s->w_handoff = stat_w(h.w_handoff, h.k_w); s->w_killed = stat_w(h.w_killed, h.k_w);
+    s->bank_size = h.n_bank;
+}
+
+void fill_remap_stats(const hyb_problem* p, hyb_leg_stats* s) {
+    const DevState& h = *p->st_host;
+    std::memset(s, 0, sizeof(*s));
+    s->histories = (int64_t)h.r_histories; s->segments = (int64_t)h.r_segments; s->leaked = (int64_t)h.r_leaked;
+    s->killed = (int64_t)h.r_killed; s->errors = (int64_t)h.r_errors; s->census = h.out_count;
+    s->w_source = stat_w(h.r_w_source, h.k_rw); s->w_absorbed = stat_w(h.r_w_absorbed, h.k_rw);
+    s->w_leaked = stat_w(h.r_w_leaked, h.k_rw); s->w_killed = stat_w(h.r_w_killed, h.k_rw);
+    s->w_census = h.bank_wsum;
+    s->combed = h.comb_on;
+    s->bank_size = h.n_bank;
+}
+
+hyb_status pull_state(hyb_problem* p) {
+    HYB_CU(p, cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
+    HYB_CU(p, cudaStreamSynchronize(p->stream));
+    if (p->st_host->status & kStBounds) return fail(p, HYB_EBOUNDS, "device index check failed (bank cell out of range)");
+    if (p->st_host->status & kStSegments) return fail(p, HYB_ETIMEOUT, "a history exceeded the segment bound");
+    return HYB_OK;
+}
+
+template <typename T>
+static hyb_status get_bank_t(hyb_problem* p, int32_t* cell, double* fx, double* fy, double* ox, double* oy, double* w,
+                             int64_t* n_io) {
+    HYB_CU(p, cudaMemcpyAsync(&p->st_host->n_bank, &p->st->n_bank, sizeof(long long), cudaMemcpyDeviceToHost, p->stream));
+    HYB_CU(p, cudaStreamSynchronize(p->stream));
+    const int64_t n = p->st_host->n_bank;
+    if (*n_io < n) { *n_io = n; return fail(p, HYB_ECAPACITY, "host arrays too small for the bank"); }
+    BankView<T> b = bank_view<T>(p, p->cur);
+    std::vector<T> tmp((size_t)n);
+    HYB_CU(p, cudaMemcpy(cell, b.cell, (size_t)n * 4, cudaMemcpyDeviceToHost));
+    T* src[5] = {b.fx, b.fy, b.ox, b.oy, b.w};
+    double* dst[5] = {fx, fy, ox, oy, w};
+    for (int q = 0; q < 5; ++q) {
+        if (n) HYB_CU(p, cudaMemcpy(tmp.data(), src[q], (size_t)n * sizeof(T), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i) dst[q][i] = (double)tmp[(size_t)i];
+    }
+    *n_io = n;
+    return HYB_OK;
+}
+
+template <typename T>
+static hyb_status set_bank_t(hyb_problem* p, const int32_t* cell, const double* fx, const double* fy, const double* ox,
+                             const double* oy, const double* w, int64_t n) {
+    HYB_CU(p, cudaStreamSynchronize(p->stream));
+    BankView<T> b = bank_view<T>(p, p->cur);
+    std::vector<T> tmp((size_t)n);
+    if (n) HYB_CU(p, cudaMemcpy(b.cell, cell, (size_t)n * 4, cudaMemcpyHostToDevice));
+    T* dst[5] = {b.fx, b.fy, b.ox, b.oy, b.w};
+    const double* src[5] = {fx, fy, ox, oy, w};
+    for (int q = 0; q < 5; ++q) {
+        for (int64_t i = 0; i < n; ++i) tmp[(size_t)i] = (T)src[q][i];
+        if (n) HYB_CU(p, cudaMemcpy(dst[q], tmp.data(), (size_t)n * sizeof(T), cudaMemcpyHostToDevice));
+    }
+    set_nbank_kernel<<<1, 1, 0, p->stream>>>(p->st, n);
+    HYB_CU(p, cudaGetLastError());
+    HYB_CU(p, launch_bank_stats(p));
+    HYB_CU(p, cudaStreamSynchronize(p->stream));
+    return HYB_OK;
+}
+
+}  // namespace hybh
+
+using namespace hybh;
+
+extern "C" {
+
+const char* hyb_status_string(hyb_status s) {
+    switch (s) {
+        case HYB_OK: return "ok";
+        case HYB_EINVAL: return "invalid argument";
+        case HYB_ENOMEM: return "out of memory / workspace too small";
+        case HYB_ECUDA: return "CUDA error";
+        case HYB_ETIMEOUT: return "bounded device loop exhausted";
+        case HYB_ESTATE: return "call out of order";
+        case HYB_EBOUNDS: return "device bounds check failed";
+        case HYB_ECAPACITY: return "capacity exceeded";
+    }
+    return "unknown status";
+}
+
+const char* hyb_last_error(const hyb_problem* p) { return p ? p->err.c_str() : g_err.c_str(); }
+
+hyb_status hyb_workspace_size(const hyb_problem_desc* d, size_t* bytes) {
+    std::string why;
+    hyb_status s = validate(d, &why);
+    if (s != HYB_OK) return fail(nullptr, s, why);
+    if (!bytes) return fail(nullptr, HYB_EINVAL, "bytes is NULL");
+    *bytes = layout_bytes(d);
+    return HYB_OK;
+}
+
+hyb_status hyb_sobol_table(int32_t ndims, uint32_t* out) {
+    if (ndims < 1 || ndims > HYB_SOBOL_DIMS || !out) return fail(nullptr, HYB_EINVAL, "ndims out of range");
+    std::memcpy(out, sobol_table_host(), (size_t)ndims * 32 * sizeof(uint32_t));
+    return HYB_OK;
+}
+
+hyb_status hyb_quadrature(int32_t order, double* ox, double* oy, double* w, int32_t* m) {
+    if ((order != 4 && order != 8) || !m) return fail(nullptr, HYB_EINVAL, "order must be 4 or 8");
+    const int need = order == 4 ? 12 : 40;
+    if (*m < need) return fail(nullptr, HYB_EINVAL, "capacity too small");
+    int mm = 0;
+    quadrature_host(order, ox, oy, w, &mm);
+    *m = mm;
+    return HYB_OK;
+}
+
+hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t ws_bytes, void* cuda_stream,
+                              hyb_problem** out) {
+    std::string why;
+    hyb_status s = validate(d, &why);
+    if (s != HYB_OK) return fail(nullptr, s, why);
+    if (!out) return fail(nullptr, HYB_EINVAL, "out is NULL");
+    *out = nullptr;
+    const size_t need = layout_bytes(d);
+    if (workspace && ws_bytes < need) return fail(nullptr, HYB_ENOMEM, "workspace smaller than hyb_workspace_size");
+    if (workspace && ((uintptr_t)workspace & 255u)) return fail(nullptr, HYB_EINVAL, "workspace must be 256-byte aligned");
+    hyb_problem* p = new (std::nothrow) hyb_problem();
+    if (!p) return fail(nullptr, HYB_ENOMEM, "host allocation failed");
+    p->d = *d;
+    p->d.sigma_a = p->d.sigma_s = p->d.Q = p->d.ic_cell_w = nullptr;
+    p->nx = d->nx; p->ny = d->ny; p->ncells = d->nx * d->ny;
+    p->dx = d->lx / d->nx; p->dy = d->ly / d->ny; p->area = p->dx * p->dy;
+    p->prec = d->precision;
+    p->stream = (cudaStream_t)cuda_stream;
+    p->step = 0;
+    p->cur = 0;
+    p->ndims = 5 + 3 * d->n_s;
+    p->leg_done = p->sn_done = false;
+    p->ev0 = p->ev1 = nullptr;
+    p->st_host = nullptr;
+    if (workspace) { p->ws = workspace; p->ws_bytes = ws_bytes; p->owns_ws = false; }
+    else {
+        cudaError_t e = cudaMalloc(&p->ws, need);
+        if (e != cudaSuccess) { delete p; return fail(nullptr, HYB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e)); }
+        p->ws_bytes = need; p->owns_ws = true;
+    }
+    assign(p);
+    auto bail = [&](hyb_status st) {
+        g_err = p->err;
+        hyb_destroy_problem(p);
+        return st;
+    };
+    if (cudaMallocHost((void**)&p->st_host, sizeof(DevState)) != cudaSuccess) return bail(fail(p, HYB_ENOMEM, "pinned alloc"));
+    if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess)
+        return bail(fail(p, HYB_ECUDA, "event create"));
+    const size_t nc = (size_t)p->ncells;
+    p->sig_s_max = 0;
+    for (size_t k = 0; k < nc; ++k) p->sig_s_max = std::max(p->sig_s_max, d->sigma_s[k]);
+    // device copies of the problem data
+    std::vector<unsigned char> sig;
+    if (p->prec == HYB_FP64) put_sig<double>(d, &sig); else put_sig<float>(d, &sig);
+    std::vector<double> zeros(nc, 0.0);
+    cudaStream_t st = p->stream;
+    auto chk = [&](cudaError_t e, const char* w) { return e == cudaSuccess ? HYB_OK : cuda_fail(p, e, w); };
+    if (chk(cudaMemsetAsync(p->st, 0, sizeof(DevState), st), "memset state") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(cudaMemcpyAsync(p->sobolV, sobol_table_host(), HYB_SOBOL_DIMS * 32 * 4, cudaMemcpyHostToDevice, st), "copy sobol") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(cudaMemcpyAsync(p->sig, sig.data(), sig.size(), cudaMemcpyHostToDevice, st), "copy sigma") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(cudaMemcpyAsync(p->sa_d, d->sigma_a, nc * 8, cudaMemcpyHostToDevice, st), "copy sa") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(cudaMemcpyAsync(p->ss_d, d->sigma_s, nc * 8, cudaMemcpyHostToDevice, st), "copy ss") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(cudaMemcpyAsync(p->Q_d, d->Q ? d->Q : zeros.data(), nc * 8, cudaMemcpyHostToDevice, st), "copy Q") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(cudaMemsetAsync(p->sn_phi_d, 0, 4 * nc * 8, st), "memset phi") != HYB_OK) return bail(HYB_ECUDA);
+    // quadrature
+    p->n_ord = 0;
+    quadrature_host(d->sn_order, p->quad_ox, p->quad_oy, p->quad_w, &p->n_ord);
+    std::vector<unsigned char> qb;
+    if (p->prec == HYB_FP64) put_quad<double>(p, &qb); else put_quad<float>(p, &qb);
+    if (chk(cudaMemcpyAsync(p->sn_quadbuf, qb.data(), qb.size(), cudaMemcpyHostToDevice, st), "copy quad") != HYB_OK) return bail(HYB_ECUDA);
+    // static source CDF: cell weights Q A dt
+    double* cw = p->cell_scratch + 256 + p->ny;
+    double* scal = (double*)p->rem_f;   // two scalars of scratch before the first remap
+    double host_sc[2] = {0, 0};
+    p->has_src = false;
+    p->w_src = 0;
+    if (d->Q) {
+        if (chk(cudaMemcpyAsync(cw, d->Q, nc * 8, cudaMemcpyHostToDevice, st), "copy Q weights") != HYB_OK) return bail(HYB_ECUDA);
+        cell_weight_kernel<<<(p->ncells + 255) / 256, 256, 0, st>>>(cw, p->ncells, p->area * d->dt, cw);
+        if (chk(launch_cdf_build(p, cw, p->src_cdf, scal, scal + 1), "source cdf") != HYB_OK) return bail(HYB_ECUDA);
+        if (chk(cudaMemcpyAsync(host_sc, scal, 16, cudaMemcpyDeviceToHost, st), "read W") != HYB_OK) return bail(HYB_ECUDA);
+        if (chk(cudaStreamSynchronize(st), "sync") != HYB_OK) return bail(HYB_ECUDA);
+        p->w_src = host_sc[0];
+        p->has_src = host_sc[0] > 0;
+    }
+    // initial bank from the initial weight per cell (stream INIT)
+    long long nb = 0;
+    if (d->ic_cell_w) {
+        double Wic = 0;
+        for (size_t k = 0; k < nc; ++k) Wic += d->ic_cell_w[k];
+        if (Wic > 0) {
+            if (chk(cudaMemcpyAsync(cw, d->ic_cell_w, nc * 8, cudaMemcpyHostToDevice, st), "copy ic") != HYB_OK) return bail(HYB_ECUDA);
+            if (chk(launch_cdf_build(p, cw, p->rem_cdf, scal, scal + 1), "ic cdf") != HYB_OK) return bail(HYB_ECUDA);
+            if (chk(cudaMemcpyAsync(host_sc, scal, 16, cudaMemcpyDeviceToHost, st), "read Wic") != HYB_OK) return bail(HYB_ECUDA);
+            if (chk(cudaStreamSynchronize(st), "sync") != HYB_OK) return bail(HYB_ECUDA);
+            if (chk(launch_init_bank(p, p->rem_cdf, host_sc[0] / (double)d->n_hist), "init bank") != HYB_OK) return bail(HYB_ECUDA);
+            nb = d->n_hist;
+        }
+    }
+    set_nbank_kernel<<<1, 1, 0, st>>>(p->st, nb);
+    if (chk(launch_bank_stats(p), "bank stats") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(cudaStreamSynchronize(st), "sync") != HYB_OK) return bail(HYB_ECUDA);
+    *out = p;
+    return HYB_OK;
+}
+
+hyb_status hyb_destroy_problem(hyb_problem* p) {
+    if (!p) return HYB_OK;
+    if (p->stream) cudaStreamSynchronize(p->stream); else cudaDeviceSynchronize();
+    if (p->owns_ws && p->ws) cudaFree(p->ws);
+    if (p->st_host) cudaFreeHost(p->st_host);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    delete p;
+    return HYB_OK;
+}
+
+static hyb_status leg_impl(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) {
+    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    const size_t nc = (size_t)p->ncells;
+    const size_t acc = p->prec == HYB_FP64 ? 16 : 8;
+    HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
+    HYB_CU(p, cudaMemsetAsync(p->acc_pre, 0, nc * acc, p->stream));
+    HYB_CU(p, cudaMemsetAsync(p->acc_post, 0, nc * acc, p->stream));
+    HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, 4 * nc * acc, p->stream));
+    HYB_CU(p, cudaMemsetAsync(p->st, 0, offsetof(DevState, r_histories), p->stream));
+    HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+    HYB_CU(p, launch_mc_leg(p, hist));
+    HYB_CU(p, launch_leg_normalise(p));
+    HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
+    p->leg_done = true;
+    p->sn_done = false;
+    if (out) {
+        hyb_status s = pull_state(p);
+        fill_leg_stats(p, out);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+        out->ms = ms;
+        if (s != HYB_OK) return s;
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_mc_leg(hyb_problem* p, hyb_leg_stats* out) { return leg_impl(p, nullptr, out); }
+hyb_status hyb_mc_leg_trace(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) { return leg_impl(p, hist, out); }
+
+hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
+    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    if (!p->leg_done) return fail(p, HYB_ESTATE, "collided solve needs an MC leg of this step");
+    HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
+    const double tol = p->prec == HYB_FP64 ? p->d.sn_tol : std::max(p->d.sn_tol, 2e-6);
+    int it = 0;
+    for (it = 1; it <= p->d.sn_max_iter; ++it) {
+        HYB_CU(p, sn_iteration(p, it == 1));
+        HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_norm_num, &p->st->sn_norm_num, 2 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, p->stream));
+        HYB_CU(p, cudaStreamSynchronize(p->stream));
+        const double num = p->st_host->sn_norm_num, den = p->st_host->sn_norm_den;
+        if (den == 0.0 || std::sqrt(num) <= tol * std::sqrt(den)) break;
+    }
+    if (it > p->d.sn_max_iter) it = p->d.sn_max_iter;
+    HYB_CU(p, sn_finish(p));
+    HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
+    p->last_sn_iters = it;
+    p->sn_done = true;
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        HYB_CU(p, cudaEventSynchronize(p->ev1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+        out->ms = ms;
+        out->sn_iterations = it;
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* out) {
+    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    if (!p->leg_done || !p->sn_done) return fail(p, HYB_ESTATE, "remap needs an MC leg and a collided solve of this step");
+    HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
+    HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+    HYB_CU(p, launch_remap(p));
+    HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
+    p->cur = 1 - p->cur;
+    p->step += 1;
+    p->leg_done = p->sn_done = false;
+    if (out) {
+        hyb_status s = pull_state(p);
+        fill_remap_stats(p, out);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+        out->ms = ms;
+        if (s != HYB_OK) return s;
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
+    if (!p || nsteps < 0) return fail(p, HYB_EINVAL, "bad arguments");
+    for (int32_t i = 0; i < nsteps; ++i) {
+        hyb_leg_stats ls, ss, rs;
+        hyb_status s = hyb_mc_leg(p, per_step ? &ls : nullptr);
+        if (s != HYB_OK) return s;
+        s = hyb_collided_solve(p, per_step ? &ss : nullptr);
+        if (s != HYB_OK) return s;
+        s = hyb_remap(p, per_step ? &rs : nullptr);
+        if (s != HYB_OK) return s;
+        if (per_step) {
+            per_step[i] = ls;
+            per_step[i].sn_iterations = ss.sn_iterations;
+            per_step[i].combed = rs.combed;
+            per_step[i].bank_size = rs.bank_size;
+            per_step[i].ms = ls.ms + ss.ms + rs.ms;
+        }
+    }
+    if (!per_step) {
+        HYB_CU(p, cudaStreamSynchronize(p->stream));
+    }
+    return HYB_OK;
+}
+
+hyb_status hyb_get_tally(hyb_problem* p, int32_t which, double* dst, size_t n, int32_t on_dev) {
+    if (!p || !dst) return fail(p, HYB_EINVAL, "null argument");
+    const size_t nc = (size_t)p->ncells;
+    const double* src = nullptr;
+    size_t need = nc;
+    switch (which) {
+        case HYB_TALLY_PRE: src = p->pre_d; break;
+        case HYB_TALLY_POST: src = p->post_d; break;
+        case HYB_TALLY_HANDOFF: src = p->mom_d; need = 4 * nc; break;
+        case HYB_TALLY_SN_PHI: src = p->sn_phi_d; need = 4 * nc; break;
+        case HYB_TALLY_FLUX: src = p->flux_d; break;
+        case HYB_TALLY_PRE_RAW: src = p->pre_raw; break;
+        case HYB_TALLY_POST_RAW: src = p->post_raw; break;
+        default: return fail(p, HYB_EINVAL, "unknown tally");
+    }
+    if (n != need) return fail(p, HYB_EINVAL, "n does not match the tally size");
+    HYB_CU(p, cudaMemcpyAsync(dst, src, need * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
+    HYB_CU(p, cudaStreamSynchronize(p->stream));
+    return HYB_OK;
+}
+
+hyb_status hyb_set_sn_phi(hyb_problem* p, const double* phi, size_t n) {
+    if (!p || !phi || n != 4 * (size_t)p->ncells) return fail(p, HYB_EINVAL, "bad arguments");
+    HYB_CU(p, cudaMemcpyAsync(p->sn_phi_d, phi, n * 8, cudaMemcpyHostToDevice, p->stream));
+    HYB_CU(p, launch_flux(p));
+    HYB_CU(p, cudaStreamSynchronize(p->stream));
+    p->sn_done = true;
+    return HYB_OK;
+}
+
+hyb_status hyb_get_bank(hyb_problem* p, int32_t* cell, double* fx, double* fy, double* ox, double* oy, double* w,
+                        int64_t* n_io) {
+    if (!p || !n_io || !cell || !fx || !fy || !ox || !oy || !w) return fail(p, HYB_EINVAL, "null argument");
+    return p->prec == HYB_FP64 ? get_bank_t<double>(p, cell, fx, fy, ox, oy, w, n_io)
+                               : get_bank_t<float>(p, cell, fx, fy, ox, oy, w, n_io);
+}
+
+hyb_status hyb_set_bank(hyb_problem* p, const int32_t* cell, const double* fx, const double* fy, const double* ox,
+                        const double* oy, const double* w, int64_t n) {
+    if (!p || n < 0 || (n > 0 && (!cell || !fx || !fy || !ox || !oy || !w))) return fail(p, HYB_EINVAL, "bad arguments");
+    if (n > p->bank_cap) return fail(p, HYB_ECAPACITY, "bank larger than its capacity");
+    for (int64_t i = 0; i < n; ++i) {
+        if (cell[i] < 0 || cell[i] >= p->ncells) return fail(p, HYB_EINVAL, "bank cell index out of range");
+        if (!(fx[i] >= 0 && fx[i] <= p->dx && fy[i] >= 0 && fy[i] <= p->dy))
+            return fail(p, HYB_EINVAL, "bank in-cell offset out of [0, dx] x [0, dy]");
+        if (!std::isfinite(ox[i]) || !std::isfinite(oy[i]) || ox[i] * ox[i] + oy[i] * oy[i] > 1.0 + 1e-12 || !std::isfinite(w[i]))
+            return fail(p, HYB_EINVAL, "bank direction or weight invalid");
+    }
+    return p->prec == HYB_FP64 ? set_bank_t<double>(p, cell, fx, fy, ox, oy, w, n)
+                               : set_bank_t<float>(p, cell, fx, fy, ox, oy, w, n);
+}
+
+hyb_status hyb_bank_capacity(const hyb_problem* p, int64_t* cap) {
+    if (!p || !cap) return HYB_EINVAL;
+    *cap = p->bank_cap;
+    return HYB_OK;
+}
+
+hyb_status hyb_set_step(hyb_problem* p, int64_t step) {
+    if (!p || step < 0) return fail(p, HYB_EINVAL, "bad arguments");
+    p->step = step;
+    p->leg_done = p->sn_done = false;
+    return HYB_OK;
+}
+
+hyb_status hyb_get_step(const hyb_problem* p, int64_t* step) {
+    if (!p || !step) return HYB_EINVAL;
+    *step = p->step;
+    return HYB_OK;
+}
+
+hyb_status hyb_points(uint64_t seed, int64_t step, int32_t stream_id, int32_t sampler, int64_t i0, int64_t n,
+                      int32_t ndims, uint32_t* out_dev, void* cuda_stream) {
+    if (i0 < 0 || n < 0 || i0 + n > ((int64_t)1 << 32) || ndims < 1 || ndims > 1024 || !out_dev ||
+        (sampler != HYB_SOBOL_DS && sampler != HYB_PRNG))
+        return fail(nullptr, HYB_EINVAL, "bad point-set arguments");
+    if (n == 0) return HYB_OK;
+    static uint32_t* dev_tab[64] = {nullptr};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return fail(nullptr, HYB_EINVAL, "device index");
+    if (!dev_tab[dev]) {
+        cudaError_t e = cudaMalloc(&dev_tab[dev], HYB_SOBOL_DIMS * 32 * 4);
+        if (e != cudaSuccess) return fail(nullptr, HYB_ENOMEM, "table alloc");
+        e = cudaMemcpy(dev_tab[dev], sobol_table_host(), HYB_SOBOL_DIMS * 32 * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(nullptr, HYB_ECUDA, cudaGetErrorString(e));
+    }
+    const uint64_t key = stream_key(seed, (uint64_t)step, (uint64_t)stream_id);
+    cudaError_t e = launch_points(key, sampler, dev_tab[dev], i0, n, ndims, out_dev, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return fail(nullptr, HYB_ECUDA, cudaGetErrorString(e));
+    return HYB_OK;
+}
+
+}  // extern "C"

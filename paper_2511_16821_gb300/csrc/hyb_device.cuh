@@ -1,0 +1,256 @@
+// hyb_device.cuh -- device helpers shared by the sm_103a kernels: counter hashing and point
+// sets (Sec. 2.4), isotropic directions, segment integrals, fixed-point tally accumulation and
+// the integer 2-D CDF pick used for births (Sec. 2.3) and the remap (Sec. 2.2, Eq. (R)).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hyb_internal.h"
+
+namespace hyb {
+
+// SoA bank layout inside a bank buffer: cell (int32, padded to 256 B), then fx, fy, ox, oy, w
+inline size_t bank_cell_bytes(int64_t cap) { return (size_t)(((cap * 4 + 255) / 256) * 256); }
+
+template <typename T>
+inline BankView<T> bank_view(hyb_problem* p, int which) {
+    BankView<T> b;
+    const int64_t cap = p->bank_cap;
+    char* bk = (char*)p->bank[which];
+    b.cell = (int32_t*)bk;
+    T* f = (T*)(bk + bank_cell_bytes(cap));
+    b.fx = f; b.fy = f + cap; b.ox = f + 2 * cap; b.oy = f + 3 * cap; b.w = f + 4 * cap;
+    return b;
+}
+
+// ---------------------------------------------------------------------------------------------
+// splitmix64 output function (Steele, Lea & Flood 2014) and the point-set keys
+// ---------------------------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t dmix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint32_t dshift(uint64_t key, uint64_t d) {
+    return (uint32_t)(dmix64(key ^ (d + kGamma)) >> 32);
+}
+
+// A point set in shared memory: Sobol direction numbers (ntab dims x 32) and per-dimension
+// digital shifts; dimensions beyond the table (or sampler == PRNG) use the counter hash.
+struct Points {
+    const uint32_t* V;
+    const uint32_t* shift;
+    uint64_t key;
+    int sampler;
+    int ntab;
+    __device__ __forceinline__ uint32_t operator()(uint32_t i, int d) const {
+        if (sampler == HYB_SOBOL_DS && d < ntab) {
+            const uint32_t* v = V + d * 32;
+            uint32_t x = 0, m = i;
+            while (m) {
+                x ^= v[__ffs(m) - 1];
+                m &= m - 1;
+            }
+            return x ^ shift[d];
+        }
+        const uint64_t h = dmix64(key ^ ((uint64_t)i + kGamma));
+        return (uint32_t)(dmix64(h ^ ((uint64_t)d + kGamma)) >> 32);
+    }
+};
+
+// ---------------------------------------------------------------------------------------------
+// precision traits: FP32 path (int64 fixed point), FP64 path (128-bit fixed point)
+// ---------------------------------------------------------------------------------------------
+template <typename T> struct Prec;
+
+template <> struct Prec<float> {
+    using acc_t = unsigned long long;
+    static constexpr int kbits = 61;
+    // u in (0,1): (2 (x >> 9) + 1) 2^-24, exact in FP32
+    static __device__ __forceinline__ float unit(uint32_t x) { return (float)(2u * (x >> 9) + 1u) * 0x1p-24f; }
+    static __device__ __forceinline__ float neglog(float u) { return -logf(u); }
+    static __device__ __forceinline__ float ex(float x) { return expf(x); }
+    static __device__ __forceinline__ float exm1(float x) { return expm1f(x); }
+    static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    // exact-order a*b + c (FP32 path: contraction allowed)
+    static __device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
+    static __device__ __forceinline__ float msub(float c, float a, float b) { return fmaf(-a, b, c); }
+    static __device__ __forceinline__ void add(acc_t* p, float c, float scale) {
+        const long long v = __float2ll_rn(c * scale);
+        if (v) atomicAdd(p, (unsigned long long)v);
+    }
+    static __device__ __forceinline__ double to_double(const acc_t* p, double inv_scale) {
+        return (double)(long long)(*p) * inv_scale;
+    }
+    static constexpr int kSeries = 11;
+};
+
+__device__ __forceinline__ void to_i128(double v, unsigned long long* lo, unsigned long long* hi) {
+    const bool neg = v < 0.0;
+    const double a = fabs(v);
+    const double h = floor(a * 0x1p-64);
+    unsigned long long H = (unsigned long long)h;
+    unsigned long long L = __double2ull_rn(a - h * 0x1p64);
+    if (neg) {
+        L = ~L + 1ull;
+        H = ~H + (L == 0ull ? 1ull : 0ull);
+    }
+    *lo = L;
+    *hi = H;
+}
+
+__device__ __forceinline__ void atomic_add128(Acc128* p, unsigned long long lo, unsigned long long hi) {
+    if (lo) {
+        const unsigned long long old = atomicAdd(&p->lo, lo);
+        if (old + lo < old) hi += 1ull;
+    }
+    if (hi) atomicAdd(&p->hi, hi);
+}
+
+__host__ __device__ __forceinline__ double acc128_to_double(unsigned long long lo, unsigned long long hi,
+                                                            double inv_scale) {
+    const bool neg = (hi >> 63) != 0ull;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0ull ? 1ull : 0ull);
+    }
+    const double v = ((double)hi * 0x1p64 + (double)lo) * inv_scale;
+    return neg ? -v : v;
+}
+
+template <> struct Prec<double> {
+    using acc_t = Acc128;
+    static constexpr int kbits = 125;
+    static __device__ __forceinline__ double unit(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
+    static __device__ __forceinline__ double neglog(double u) { return -log(u); }
+    static __device__ __forceinline__ double ex(double x) { return exp(x); }
+    static __device__ __forceinline__ double exm1(double x) { return expm1(x); }
+    static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    // separately rounded product and sum: FP64 geometry follows IEEE order exactly
+    static __device__ __forceinline__ double madd(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
+    static __device__ __forceinline__ double msub(double c, double a, double b) { return __dsub_rn(c, __dmul_rn(a, b)); }
+    static __device__ __forceinline__ void add(acc_t* p, double c, double scale) {
+        unsigned long long lo, hi;
+        to_i128(c * scale, &lo, &hi);
+        atomic_add128(p, lo, hi);
+    }
+    static __device__ __forceinline__ double to_double(const acc_t* p, double inv_scale) {
+        return acc128_to_double(p->lo, p->hi, inv_scale);
+    }
+    static constexpr int kSeries = 19;
+};
+
+// scale 2^(kbits - ceil(log2 B)) so that sums bounded by B fit the accumulator; 0 if B == 0
+__host__ __device__ __forceinline__ int scale_exponent(double B, int kbits) {
+    if (!(B > 0.0)) return 0;
+    int e = 0;
+    const double m = frexp(B, &e);
+    const int cl = (m == 0.5) ? e - 1 : e;
+    int k = kbits - cl;
+    if (k > 1000) k = 1000;
+    return k;
+}
+
+// ---------------------------------------------------------------------------------------------
+// g_n(x) = int_0^1 t^n e^{-x t} dt, n = 0,1,2: series below x = 1, closed form above
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void gfun(T x, T* g0, T* g1, T* g2) {
+    if (x < T(1)) {
+        T s0 = 0, s1 = 0, s2 = 0, term = 1;
+#pragma unroll
+        for (int k = 0; k < Prec<T>::kSeries; ++k) {
+            s0 += term / T(k + 1);
+            s1 += term / T(k + 2);
+            s2 += term / T(k + 3);
+            term *= -x / T(k + 1);
+        }
+        *g0 = s0; *g1 = s1; *g2 = s2;
+    } else {
+        const T e = Prec<T>::ex(-x);
+        *g0 = -Prec<T>::exm1(-x) / x;
+        *g1 = (*g0 - e) / x;
+        *g2 = (T(2) * *g1 - e) / x;
+    }
+}
+
+// isotropic direction: mu = 2u - 1, phi = 2 pi u'; returns the in-plane components
+template <typename T>
+__device__ __forceinline__ void iso_dir(T u_mu, T u_phi, T* ox, T* oy) {
+    const T st = T(2) * Prec<T>::sqrt_(u_mu * (T(1) - u_mu));
+    T s, c;
+    Prec<T>::sincos2pi(u_phi, &s, &c);
+    *ox = st * c;
+    *oy = st * s;
+}
+
+// ---------------------------------------------------------------------------------------------
+// integer CDF pick: bin j of pre[0..n] with pre[j] 2^33 <= (2x+1) total < pre[j+1] 2^33;
+// a, b: the remainder split as rem = a 2^33 + b; W: the bin weight
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ int pick_bin(const long long* __restrict__ pre, int n, uint32_t x,
+                                        unsigned long long* a, unsigned long long* b,
+                                        unsigned long long* W) {
+    const unsigned long long total = (unsigned long long)pre[n];
+    const unsigned long long m = 2ull * (unsigned long long)x + 1ull;
+    const unsigned long long Plo = m * total, Phi = __umul64hi(m, total);
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const unsigned long long v = (unsigned long long)pre[mid];
+        const unsigned long long vhi = v >> 31, vlo = v << 33;
+        if (vhi < Phi || (vhi == Phi && vlo <= Plo)) lo = mid; else hi = mid - 1;
+    }
+    const unsigned long long v = (unsigned long long)pre[lo];
+    const unsigned long long vhi = v >> 31, vlo = v << 33;
+    const unsigned long long rlo = Plo - vlo;
+    const unsigned long long rhi = Phi - vhi - (Plo < vlo ? 1ull : 0ull);
+    *a = (rhi << 31) | (rlo >> 33);
+    *b = rlo & ((1ull << 33) - 1ull);
+    *W = (unsigned long long)(pre[lo + 1] - pre[lo]);
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T bin_frac(unsigned long long a, unsigned long long b, unsigned long long W) {
+    return (T)(((double)a + (double)b * 0x1p-33) / (double)W);
+}
+
+template <>
+__device__ __forceinline__ float bin_frac<float>(unsigned long long a, unsigned long long b, unsigned long long W) {
+    return ((float)a + (float)b * 0x1p-33f) / (float)W;
+}
+
+// cell and in-cell fractions from the 2-D CDF: row from x1, column within the row from x0
+template <typename T>
+__device__ __forceinline__ int sample_cell(const Cdf2DView& C, int nx, int ny, uint32_t x0, uint32_t x1,
+                                           T* frx, T* fry) {
+    unsigned long long a, b, W;
+    const int iy = pick_bin(C.row_pre, ny, x1, &a, &b, &W);
+    *fry = bin_frac<T>(a, b, W);
+    const int ix = pick_bin(C.col_pre + (size_t)iy * (nx + 1), nx, x0, &a, &b, &W);
+    *frx = bin_frac<T>(a, b, W);
+    return iy * nx + ix;
+}
+
+template <typename T>
+__device__ __forceinline__ T clamp_(T v, T lo, T hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// deterministic block reduction of a double (fixed tree order for a fixed block size)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace hyb

@@ -1,0 +1,131 @@
+// hyb_internal.h -- internal structures of the sm_103a hybrid (Q)MC / S_N library (not ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hyb.h"
+
+namespace hyb {
+
+constexpr int kTile = 256;               // threads per block of the streaming kernels
+constexpr int64_t kMaxSegments = 1 << 20;
+constexpr int kFateLeaked = 0, kFateCensus = 1, kFateKilled = 2, kFateError = 3;
+constexpr int kSnTile = 32;              // S_N-DG sweep tile (cells per side)
+constexpr int kMaxOrd = 40;              // S8 upper hemisphere
+constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
+
+// status bits written by kernels (device status word)
+constexpr int kStBounds = 1, kStSegments = 2, kStCapacity = 4;
+
+// 128-bit two's-complement fixed-point accumulator cell (lo word carries into hi)
+struct Acc128 { unsigned long long lo, hi; };
+
+// Device-resident per-leg counters and scalars (one block of memory per problem).
+struct DevState {
+    // counters of the last MC leg
+    unsigned long long histories, segments, collisions, leaked, census, killed, reached, errors;
+    Acc128 w_source, w_absorbed, w_leaked, w_census, w_handoff, w_killed;
+    // counters of the last remap
+    unsigned long long r_histories, r_segments, r_leaked, r_killed, r_errors, r_alive;
+    Acc128 r_w_source, r_w_absorbed, r_w_leaked, r_w_killed, r_w_census;
+    // bank descriptors
+    long long n_bank;          // particles in the current bank
+    double bank_wmax;          // max |w| of the current bank
+    double bank_wsum;          // sum |w| of the current bank
+    // remap / comb scalars
+    double remap_W;            // sum |q_cell|
+    double remap_qmax;         // max |q_cell|
+    double remap_rmax;         // max weight factor bound over source cells
+    double w_ref;              // power-of-two quantisation base of the comb
+    long long comb_T;          // total quantised |w|
+    long long comb_o;          // tooth offset
+    long long comb_total_alive;
+    int comb_on;
+    int status;                // kSt* bits
+    double wcopy;              // comb copy weight
+    double sn_norm_num, sn_norm_den;
+    int k_track, k_mom, k_w;   // fixed-point scale exponents of the last MC leg
+    int k_rw;                  // scale exponent of the remap weight sums
+    Acc128 bank_wsum_acc;      // scratch of the bank-statistics kernels
+    long long out_count;       // particles written by the last remap
+    int pad[2];
+};
+
+template <typename T>
+struct BankView { int32_t* cell; T *fx, *fy, *ox, *oy, *w; };
+
+struct Cdf2DView { long long* q; long long* row_pre; long long* col_pre; };
+
+}  // namespace hyb
+
+// Problem object behind the opaque hyb_problem handle.
+struct hyb_problem {
+    hyb_problem_desc d;       // copy of the descriptor (array pointers cleared)
+    int nx, ny, ncells;
+    double dx, dy, area;
+    int prec;                 // HYB_FP32 / HYB_FP64
+    int64_t bank_cap;
+    int64_t step;
+    cudaStream_t stream;
+    void* ws;                 // device workspace base
+    size_t ws_bytes;
+    bool owns_ws;
+    int ndims;                // point dimensions used: 5 + 3 N_s (capped)
+    double w_src;             // total source weight per step (sum Q A dt)
+    bool has_src;
+    int n_ord;                // S_N ordinates
+    double quad_ox[hyb::kMaxOrd], quad_oy[hyb::kMaxOrd], quad_w[hyb::kMaxOrd];
+    bool leg_done, sn_done;
+    int last_sn_iters;
+    std::string err;
+    // device pointers (into ws)
+    uint32_t* sobolV;         // HYB_SOBOL_DIMS x 32
+    void* sig;                // ncells x 2 (T): sigma_a, sigma_s
+    double *sa_d, *ss_d, *Q_d;  // FP64 copies for the remap density
+    hyb::Cdf2DView src_cdf, rem_cdf;
+    double* rem_f;            // 4 x ncells remap density coefficients
+    double* rem_q;            // ncells signed remap cell weights q = f0 A dt
+    double* cell_scratch;     // per-row partials for the CDF build
+    void* bank[2];            // two SoA banks (T)
+    int cur;                  // current bank index
+    void* acc_pre; void* acc_post; void* acc_mom;   // fixed-point tallies
+    double *pre_d, *post_d, *mom_d, *flux_d;        // normalised tallies (FP64)
+    double *pre_raw, *post_raw;                     // raw track-length sums (FP64)
+    double sig_s_max;         // max sigma_s (bound of the hand-off moments)
+    void* sn_phi; void* sn_phi_old; void* sn_quad; void* sn_tx; void* sn_ty;  // S_N state (T)
+    void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, precision T
+    double* sn_phi_d;         // collided flux, FP64 copy (4 x ncells)
+    double* sn_norm;          // per-block norm partials
+    long long* blk;           // remap block partials (4 x nblk)
+    int64_t nblk_max;
+    hyb::DevState* st;        // device counters
+    hyb::DevState* st_host;   // pinned host mirror
+    cudaEvent_t ev0, ev1;
+};
+
+namespace hyb {
+
+// launchers (defined in the .cu files)
+cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev);
+cudaError_t launch_leg_normalise(hyb_problem* p);
+cudaError_t launch_remap(hyb_problem* p);
+cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView cdf, double* W_out_dev,
+                             double* qmax_out_dev);
+cudaError_t launch_flux(hyb_problem* p);
+cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0);
+cudaError_t launch_bank_stats(hyb_problem* p);
+cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,
+                          uint32_t* out, cudaStream_t s);
+cudaError_t sn_iteration(hyb_problem* p, int first);
+cudaError_t sn_finish(hyb_problem* p);
+
+// host helpers (host.cu)
+uint64_t mix64(uint64_t z);
+uint64_t stream_key(uint64_t seed, uint64_t step, uint64_t stream);
+const uint32_t* sobol_table_host();
+void quadrature_host(int order, double* ox, double* oy, double* w, int* m);
+
+}  // namespace hyb

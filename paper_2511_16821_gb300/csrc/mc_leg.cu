@@ -1,0 +1,434 @@
+// mc_leg.cu -- the scatter-limited (Q)MC leg (Sec. 2.2 step 1; Sec. 2.3) on sm_103a.
+//
+// One thread per history, grid-stride over [bank slots | source births]. Per history: pick-up
+// from the SoA census bank or birth from the integer source CDF (implicit capture, isotropic
+// direction, uniform time in the step), then the segment loop: distance to the x face, the y face,
+// the next candidate collision (pre-limit only) and census; the shortest wins (collision over
+// face over census). Pre-limit segments (n < N_s) tally w l g(sigma_a l) into <Psi>_pre and
+// attenuate with sigma_a; post-limit segments (n = N_s) tally into <Psi>_post, attenuate with
+// sigma_t and deposit the (N_s+1)-th collision density sigma_s int w P_j ds into four Legendre
+// moments per cell. Tallies are fixed-point integer atomics (order-free, deterministic).
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "hyb_device.cuh"
+
+namespace hyb {
+
+template <typename T>
+struct LegArgs {
+    int nx, ny;
+    T dx, dy, cdt;
+    const T* sig;               // (sigma_a, sigma_s) per cell
+    int n_s, sampler, handoff_full, ntab;
+    T w_min;
+    const uint32_t* V;
+    uint64_t key_c, key_s;
+    BankView<T> bank;
+    Cdf2DView cdf;
+    long long n_src;
+    T w0;
+    typename Prec<T>::acc_t *pre, *post, *mom;
+    DevState* st;
+    int32_t* hist;
+    double sig_s_max, w_src_total, cdt_d;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) mc_leg_kernel(LegArgs<T> a) {
+    using P = Prec<T>;
+    extern __shared__ uint32_t sm[];
+    uint32_t* sV = sm;
+    uint32_t* sShC = sm + a.ntab * 32;
+    uint32_t* sShS = sShC + a.ntab;
+    for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
+    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) {
+        sShC[d] = dshift(a.key_c, (uint64_t)d);
+        sShS[d] = dshift(a.key_s, (uint64_t)d);
+    }
+    __syncthreads();
+
+    const long long nb = a.st->n_bank;
+    const long long N = nb + a.n_src;
+    const double Wstep = a.st->bank_wsum + a.w_src_total;
+    const int kt = scale_exponent(Wstep * a.cdt_d, P::kbits);
+    const int km = scale_exponent(Wstep * a.cdt_d * a.sig_s_max, P::kbits);
+    const T sc_t = (T)ldexp(1.0, kt), sc_m = (T)ldexp(1.0, km);
+
+    unsigned long long c_hist = 0, c_seg = 0, c_col = 0, c_leak = 0, c_cen = 0, c_kill = 0, c_reach = 0, c_err = 0;
+    double w_src = 0, w_abs = 0, w_leak = 0, w_cen = 0, w_hand = 0, w_kill = 0;
+    int status = 0;
+    const T DX = a.dx, DY = a.dy;
+    const T INF = (T)INFINITY;
+    const int Ns = a.n_s;
+    const int nx = a.nx, ny = a.ny;
+
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+         j += (long long)gridDim.x * blockDim.x) {
+        int ix, iy;
+        T fx, fy, ox, oy, w, srem;
+        uint32_t idx;
+        Points pts;
+        pts.V = sV;
+        pts.sampler = a.sampler;
+        pts.ntab = a.ntab;
+        if (j < nb) {
+            idx = (uint32_t)j;
+            pts.key = a.key_c;
+            pts.shift = sShC;
+            const int k = a.bank.cell[j];
+            if (k < 0 || k >= nx * ny) { status |= kStBounds; continue; }
+            ix = k % nx; iy = k / nx;
+            fx = a.bank.fx[j]; fy = a.bank.fy[j];
+            ox = a.bank.ox[j]; oy = a.bank.oy[j];
+            w = a.bank.w[j];
+            srem = a.cdt;
+        } else {
+            idx = (uint32_t)(j - nb);
+            pts.key = a.key_s;
+            pts.shift = sShS;
+            T frx, fry;
+            const int k = sample_cell<T>(a.cdf, nx, ny, pts(idx, 0), pts(idx, 1), &frx, &fry);
+            ix = k % nx; iy = k / nx;
+            fx = frx * DX; fy = fry * DY;
+            const T tf = P::unit(pts(idx, 2));
+            iso_dir<T>(P::unit(pts(idx, 3)), P::unit(pts(idx, 4)), &ox, &oy);
+            w = a.w0;
+            srem = a.cdt * (T(1) - tf);
+        }
+        ++c_hist;
+        const T w_start = w;
+        w_src += (double)w;
+        int n = 0;
+        if (Ns == 0) ++c_reach;
+        T tau = 0;
+        if (Ns > 0) tau = P::neglog(P::unit(pts(idx, 5)));
+        int seg = 0, fate = kFateError;
+        while (seg < (int)kMaxSegments) {
+            ++seg;
+            const int k = iy * nx + ix;
+            const T sa = a.sig[2 * k], ss = a.sig[2 * k + 1], st = sa + ss;
+            const T dxf = ox > T(0) ? (DX - fx) / ox : (ox < T(0) ? fx / (-ox) : INF);
+            const T dyf = oy > T(0) ? (DY - fy) / oy : (oy < T(0) ? fy / (-oy) : INF);
+            const T dcol = (n < Ns && ss > T(0)) ? tau / ss : INF;
+            T l;
+            int ev;
+            bool xc = false, yc = false;
+            if (dcol <= dxf && dcol <= dyf && dcol <= srem) { l = dcol; ev = 0; }
+            else if (dxf <= srem || dyf <= srem) {
+                l = dxf < dyf ? dxf : dyf; ev = 1; xc = (dxf == l); yc = (dyf == l);
+            } else { l = srem; ev = 2; }
+
+            if (n < Ns) {
+                const T att = -P::exm1(-sa * l);
+                P::add(&a.pre[k], sa > T(0) ? w * att / sa : w * l, sc_t);
+                w_abs += (double)(w * att);
+                w = w * P::ex(-sa * l);
+                tau = P::msub(tau, ss, l);
+            } else {
+                const T att = -P::exm1(-st * l);
+                P::add(&a.post[k], st > T(0) ? w * att / st : w * l, sc_t);
+                if (ss > T(0)) {
+                    T g0, g1, g2;
+                    gfun<T>(st * l, &g0, &g1, &g2);
+                    const T I0 = l * g0, I1 = l * l * g1, I2 = l * l * l * g2;
+                    const T sw = ss * w;
+                    P::add(&a.mom[4 * k + 0], sw * I0, sc_m);
+                    if (a.handoff_full) {
+                        const T xi0 = T(2) * fx / DX - T(1), eta0 = T(2) * fy / DY - T(1);
+                        const T axi = T(2) * ox / DX, aeta = T(2) * oy / DY;
+                        P::add(&a.mom[4 * k + 1], sw * (xi0 * I0 + axi * I1), sc_m);
+                        P::add(&a.mom[4 * k + 2], sw * (eta0 * I0 + aeta * I1), sc_m);
+                        P::add(&a.mom[4 * k + 3],
+                               sw * (xi0 * eta0 * I0 + (xi0 * aeta + eta0 * axi) * I1 + axi * aeta * I2), sc_m);
+                    }
+                }
+                if (st > T(0)) {
+                    w_hand += (double)(w * att * (ss / st));
+                    w_abs += (double)(w * att * (sa / st));
+                }
+                w = w * P::ex(-st * l);
+            }
+            fx = P::madd(ox, l, fx);
+            fy = P::madd(oy, l, fy);
+            srem = srem - l;
+
+            if (ev == 2) {
+                fate = kFateCensus; ++c_cen; w_cen += (double)w;
+                break;
+            }
+            if (ev == 1) {
+                if (xc) { ix += ox > T(0) ? 1 : -1; fx = ox > T(0) ? T(0) : DX; }
+                else fx = clamp_(fx, T(0), DX);
+                if (yc) { iy += oy > T(0) ? 1 : -1; fy = oy > T(0) ? T(0) : DY; }
+                else fy = clamp_(fy, T(0), DY);
+                if (ix < 0 || ix >= nx || iy < 0 || iy >= ny) {
+                    fate = kFateLeaked; ++c_leak; w_leak += (double)w;
+                    ix = ix < 0 ? 0 : (ix >= nx ? nx - 1 : ix);
+                    iy = iy < 0 ? 0 : (iy >= ny ? ny - 1 : iy);
+                    break;
+                }
+            } else {
+                fx = clamp_(fx, T(0), DX);
+                fy = clamp_(fy, T(0), DY);
+                ++n; ++c_col;
+                const int base = 5 + 3 * (n - 1);
+                iso_dir<T>(P::unit(pts(idx, base + 1)), P::unit(pts(idx, base + 2)), &ox, &oy);
+                if (n < Ns) tau = P::neglog(P::unit(pts(idx, 5 + 3 * n)));
+                else { tau = T(0); ++c_reach; }
+            }
+            if (a.w_min > T(0) && w < a.w_min * w_start) {
+                fate = kFateKilled; ++c_kill; w_kill += (double)w;
+                break;
+            }
+        }
+        c_seg += (unsigned long long)seg;
+        if (fate == kFateError) { ++c_err; status |= kStSegments; }
+        if (a.hist) {
+            int4 r = make_int4(iy * nx + ix, fate, n, seg);
+            reinterpret_cast<int4*>(a.hist)[j] = r;
+        }
+    }
+
+    // block reduction of the statistics (fixed order for a fixed launch shape)
+    __shared__ double s_w[kTile / 32][6];
+    __shared__ unsigned long long s_c[kTile / 32][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long cs[8] = {c_hist, c_seg, c_col, c_leak, c_cen, c_kill, c_reach, c_err};
+    double ws[6] = {w_src, w_abs, w_leak, w_cen, w_hand, w_kill};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cs[q] = warp_sum_u64(cs[q]);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) ws[q] = warp_sum(ws[q]);
+    if (lane == 0) {
+        for (int q = 0; q < 8; ++q) s_c[wid][q] = cs[q];
+        for (int q = 0; q < 6; ++q) s_w[wid][q] = ws[q];
+    }
+    if (status) atomicOr(&a.st->status, status);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long* cdst[8] = {&a.st->histories, &a.st->segments, &a.st->collisions, &a.st->leaked,
+                                       &a.st->census, &a.st->killed, &a.st->reached, &a.st->errors};
+        Acc128* wdst[6] = {&a.st->w_source, &a.st->w_absorbed, &a.st->w_leaked, &a.st->w_census,
+                           &a.st->w_handoff, &a.st->w_killed};
+        const int kw = scale_exponent(Wstep, 125);
+        const double scw = ldexp(1.0, kw);
+        for (int q = 0; q < 8; ++q) {
+            unsigned long long v = 0;
+            for (int ww = 0; ww < kTile / 32; ++ww) v += s_c[ww][q];
+            if (v) atomicAdd(cdst[q], v);
+        }
+        for (int q = 0; q < 6; ++q) {
+            double v = 0;
+            for (int ww = 0; ww < kTile / 32; ++ww) v += s_w[ww][q];
+            unsigned long long lo, hi;
+            to_i128(v * scw, &lo, &hi);
+            atomic_add128(wdst[q], lo, hi);
+        }
+        if (blockIdx.x == 0) {
+            a.st->k_track = kt;
+            a.st->k_mom = km;
+            a.st->k_w = kw;
+        }
+    }
+}
+
+// fixed point -> FP64: raw track-length sums, step-average fluxes and hand-off moments
+template <typename T>
+__global__ void leg_normalise_kernel(const typename Prec<T>::acc_t* pre, const typename Prec<T>::acc_t* post,
+                                     const typename Prec<T>::acc_t* mom, const DevState* st, int ncells,
+                                     double inv_adt, double* pre_raw, double* post_raw, double* pre_d,
+                                     double* post_d, double* mom_d) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncells) return;
+    const double it = ldexp(1.0, -st->k_track), im = ldexp(1.0, -st->k_mom);
+    const double a = Prec<T>::to_double(&pre[k], it), b = Prec<T>::to_double(&post[k], it);
+    pre_raw[k] = a;
+    post_raw[k] = b;
+    pre_d[k] = a * inv_adt;
+    post_d[k] = b * inv_adt;
+    for (int j = 0; j < 4; ++j) mom_d[4 * k + j] = Prec<T>::to_double(&mom[4 * k + j], im);
+}
+
+// initial bank: n particles from the initial-weight CDF (stream INIT, step 0), isotropic, t = 0
+template <typename T>
+__global__ void init_bank_kernel(BankView<T> b, Cdf2DView cdf, int nx, int ny, T dx, T dy, long long n, T w0,
+                                 const uint32_t* V, int ntab, int sampler, uint64_t key) {
+    __shared__ uint32_t sV[5 * 32];
+    __shared__ uint32_t sSh[5];
+    const int nt = ntab < 5 ? ntab : 5;
+    for (int i = threadIdx.x; i < nt * 32; i += blockDim.x) sV[i] = V[i];
+    if (threadIdx.x < nt) sSh[threadIdx.x] = dshift(key, threadIdx.x);
+    __syncthreads();
+    Points pts{sV, sSh, key, sampler, nt};
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        T frx, fry, ox, oy;
+        const int k = sample_cell<T>(cdf, nx, ny, pts((uint32_t)i, 0), pts((uint32_t)i, 1), &frx, &fry);
+        iso_dir<T>(Prec<T>::unit(pts((uint32_t)i, 3)), Prec<T>::unit(pts((uint32_t)i, 4)), &ox, &oy);
+        b.cell[i] = k;
+        b.fx[i] = frx * dx;
+        b.fy[i] = fry * dy;
+        b.ox[i] = ox;
+        b.oy[i] = oy;
+        b.w[i] = w0;
+    }
+}
+
+// bank statistics: max |w| (exact, bitwise atomic max) and sum |w| (block order)
+template <typename T>
+__global__ void bank_wmax_kernel(const T* w, DevState* st) {
+    const long long n = st->n_bank;
+    double m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)w[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax((unsigned long long*)&st->bank_wmax, (unsigned long long)__double_as_longlong(m));
+}
+
+template <typename T>
+__global__ void bank_wsum_kernel(const T* w, DevState* st) {
+    const long long n = st->n_bank;
+    const int kw = scale_exponent((double)n * st->bank_wmax, 125);
+    const double sc = ldexp(1.0, kw);
+    double s = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += fabs((double)w[i]);
+    s = warp_sum(s);
+    __shared__ double sw[32];
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sw[q];
+        unsigned long long lo, hi;
+        to_i128(t * sc, &lo, &hi);
+        atomic_add128(&st->bank_wsum_acc, lo, hi);
+    }
+}
+
+__global__ void bank_wsum_final_kernel(DevState* st) {
+    const int kw = scale_exponent((double)st->n_bank * st->bank_wmax, 125);
+    st->bank_wsum = acc128_to_double(st->bank_wsum_acc.lo, st->bank_wsum_acc.hi, ldexp(1.0, -kw));
+}
+
+__global__ void points_kernel(uint64_t key, int sampler, const uint32_t* V, long long i0, long long n, int ndims,
+                              uint32_t* out) {
+    extern __shared__ uint32_t sm[];
+    const int ntab = ndims < HYB_SOBOL_DIMS ? ndims : HYB_SOBOL_DIMS;
+    uint32_t* sV = sm;
+    uint32_t* sSh = sm + ntab * 32;
+    for (int i = threadIdx.x; i < ntab * 32; i += blockDim.x) sV[i] = V[i];
+    for (int d = threadIdx.x; d < ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
+    __syncthreads();
+    Points pts{sV, sSh, key, sampler, ntab};
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(i0 + t);
+        for (int d = 0; d < ndims; ++d) out[t * ndims + d] = pts(i, d);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------------
+static int leg_grid(long long work) {
+    long long g = (work + kTile - 1) / kTile;
+    const long long cap = 152LL * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename T>
+static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
+    LegArgs<T> a;
+    a.nx = p->nx; a.ny = p->ny;
+    a.dx = (T)p->dx; a.dy = (T)p->dy;
+    a.cdt = (T)(p->d.c * p->d.dt);
+    a.cdt_d = p->d.c * p->d.dt;
+    a.sig = (const T*)p->sig;
+    a.n_s = p->d.n_s; a.sampler = p->d.sampler; a.handoff_full = p->d.handoff_full;
+    a.ntab = p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS;
+    a.w_min = (T)p->d.w_min;
+    a.V = p->sobolV;
+    a.key_c = stream_key(p->d.seed, (uint64_t)p->step, HYB_STREAM_LEG_CENSUS);
+    a.key_s = stream_key(p->d.seed, (uint64_t)p->step, HYB_STREAM_LEG_SOURCE);
+    a.bank = bank_view<T>(p, p->cur);
+    a.cdf = p->src_cdf;
+    a.n_src = p->has_src ? p->d.n_hist : 0;
+    a.w0 = (T)(p->has_src ? p->w_src / (double)p->d.n_hist : 0.0);
+    a.pre = (typename Prec<T>::acc_t*)p->acc_pre;
+    a.post = (typename Prec<T>::acc_t*)p->acc_post;
+    a.mom = (typename Prec<T>::acc_t*)p->acc_mom;
+    a.st = p->st;
+    a.hist = hist;
+    a.sig_s_max = p->sig_s_max;
+    a.w_src_total = p->has_src ? p->w_src : 0.0;
+    const size_t smem = (size_t)(a.ntab * 32 + 2 * a.ntab) * sizeof(uint32_t);
+    const long long work = p->bank_cap + a.n_src;
+    mc_leg_kernel<T><<<leg_grid(work), kTile, smem, p->stream>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev) {
+    return p->prec == HYB_FP64 ? mc_leg_t<double>(p, hist_dev) : mc_leg_t<float>(p, hist_dev);
+}
+
+cudaError_t launch_leg_normalise(hyb_problem* p) {
+    const double inv_adt = 1.0 / (p->area * p->d.dt);
+    const int g = (p->ncells + 255) / 256;
+    if (p->prec == HYB_FP64)
+        leg_normalise_kernel<double><<<g, 256, 0, p->stream>>>((const Acc128*)p->acc_pre, (const Acc128*)p->acc_post,
+                                                               (const Acc128*)p->acc_mom, p->st, p->ncells, inv_adt,
+                                                               p->pre_raw, p->post_raw, p->pre_d, p->post_d, p->mom_d);
+    else
+        leg_normalise_kernel<float><<<g, 256, 0, p->stream>>>(
+            (const unsigned long long*)p->acc_pre, (const unsigned long long*)p->acc_post,
+            (const unsigned long long*)p->acc_mom, p->st, p->ncells, inv_adt, p->pre_raw, p->post_raw, p->pre_d,
+            p->post_d, p->mom_d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0) {
+    const uint64_t key = stream_key(p->d.seed, 0, HYB_STREAM_INIT);
+    const int ntab = p->d.sampler == HYB_SOBOL_DS ? 5 : 0;
+    const long long n = p->d.n_hist;
+    const int g = leg_grid(n);
+    if (p->prec == HYB_FP64)
+        init_bank_kernel<double><<<g, kTile, 0, p->stream>>>(bank_view<double>(p, p->cur), cdf, p->nx, p->ny, p->dx,
+                                                             p->dy, n, w0, p->sobolV, ntab, p->d.sampler, key);
+    else
+        init_bank_kernel<float><<<g, kTile, 0, p->stream>>>(bank_view<float>(p, p->cur), cdf, p->nx, p->ny,
+                                                            (float)p->dx, (float)p->dy, n, (float)w0, p->sobolV, ntab,
+                                                            p->d.sampler, key);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bank_stats(hyb_problem* p) {
+    cudaError_t e = cudaMemsetAsync(&p->st->bank_wmax, 0, sizeof(double), p->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&p->st->bank_wsum_acc, 0, sizeof(Acc128), p->stream);
+    if (e != cudaSuccess) return e;
+    const int g = leg_grid(p->bank_cap);
+    if (p->prec == HYB_FP64) {
+        BankView<double> b = bank_view<double>(p, p->cur);
+        bank_wmax_kernel<double><<<g, kTile, 0, p->stream>>>(b.w, p->st);
+        bank_wsum_kernel<double><<<g, kTile, 0, p->stream>>>(b.w, p->st);
+    } else {
+        BankView<float> b = bank_view<float>(p, p->cur);
+        bank_wmax_kernel<float><<<g, kTile, 0, p->stream>>>(b.w, p->st);
+        bank_wsum_kernel<float><<<g, kTile, 0, p->stream>>>(b.w, p->st);
+    }
+    bank_wsum_final_kernel<<<1, 1, 0, p->stream>>>(p->st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,
+                          uint32_t* out, cudaStream_t s) {
+    const int ntab = ndims < HYB_SOBOL_DIMS ? ndims : HYB_SOBOL_DIMS;
+    const size_t smem = (size_t)(ntab * 32 + ntab) * sizeof(uint32_t);
+    points_kernel<<<leg_grid(n), kTile, smem, s>>>(key, sampler, V, i0, n, ndims, out);
+    return cudaGetLastError();
+}
+
+}  // namespace hyb

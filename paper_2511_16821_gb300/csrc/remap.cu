@@ -1,0 +1,595 @@
+// remap.cu -- scatter-free census remap (Sec. 2.2 steps 3-4, Eq. (R)) and the integer 2-D CDF.
+//
+// CDF build (shared by the static source and the remap source): per cell |q| -> max and sum
+// (deterministic block order) -> q_int = rint(|q| / max |q| 2^40) -> per-row exclusive scans
+// (column conditional) -> row-total scan (row marginal). Exact integer arithmetic, so cells are
+// picked identically on the FP32 and FP64 paths.
+//
+// Remap: slot j in [bank slots | births] is re-streamed straight with sigma_t attenuation from its
+// step-start state (bank particles are copied, births come from the remap source density
+// Q + sigma_s (phi_pre + phi_post + phi_c), bilinear within a cell). Three launches:
+//   pass A  re-stream, count survivors, sum quantised |w| and |w| per block (no bank writes)
+//   scan    one block: block offsets, totals, comb decision and tooth offset
+//   pass B  re-stream again (same arithmetic), block scan, write survivors (or their comb
+//           copies) into the other bank in slot order.
+// Recomputing the straight-line stream is cheaper than staging the state through HBM.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "hyb_device.cuh"
+
+namespace hyb {
+
+constexpr int kRounds = 8;                       // slot rounds per block (2048 slots per block)
+constexpr int kSlotsPerBlock = kTile * kRounds;
+
+// ---------------------------------------------------------------------------------------------
+// CDF build
+// ---------------------------------------------------------------------------------------------
+__global__ void cdf_reduce_kernel(const double* __restrict__ w, int ncells, double* part_sum, double* qmax) {
+    double s = 0, m = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncells; k += gridDim.x * blockDim.x) {
+        const double a = fabs(w[k]);
+        s += a;
+        m = fmax(m, a);
+    }
+    s = warp_sum(s);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    __shared__ double ss[32];
+    if ((threadIdx.x & 31) == 0) {
+        ss[threadIdx.x >> 5] = s;
+        if (m > 0) atomicMax((unsigned long long*)qmax, (unsigned long long)__double_as_longlong(m));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += ss[q];
+        part_sum[blockIdx.x] = t;
+    }
+}
+
+__global__ void cdf_total_kernel(const double* part_sum, int nparts, double* W) {
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int i = 0; i < nparts; ++i) t += part_sum[i];
+        *W = t;
+    }
+}
+
+// one block per row: q_int and the exclusive column scan of the row
+__global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax, int nx, Cdf2DView C,
+                                long long* row_tot) {
+    const int iy = blockIdx.x;
+    const double qm = *qmax;
+    const int per = (nx + blockDim.x - 1) / blockDim.x;
+    const int c0 = threadIdx.x * per;
+    long long local = 0;
+    for (int c = c0; c < c0 + per && c < nx; ++c) {
+        const size_t k = (size_t)iy * nx + c;
+        const long long q = qm > 0 ? __double2ll_rn((fabs(w[k]) / qm) * 0x1p40) : 0;
+        C.q[k] = q;
+        local += q;
+    }
+    // block exclusive scan of the per-thread totals
+    __shared__ long long sw[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long inc = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += v;
+    }
+    if (lane == 31) sw[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = blockDim.x >> 5;
+        long long v = lane < nw ? sw[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
+        }
+        if (lane < nw) sw[lane] = v;
+    }
+    __syncthreads();
+    long long run = (wid > 0 ? sw[wid - 1] : 0) + inc - local;
+    long long* pre = C.col_pre + (size_t)iy * (nx + 1);
+    for (int c = c0; c < c0 + per && c < nx; ++c) {
+        pre[c] = run;
+        run += C.q[(size_t)iy * nx + c];
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+        const long long tot = sw[(blockDim.x >> 5) - 1];
+        pre[nx] = tot;
+        row_tot[iy] = tot;
+    }
+}
+
+__global__ void cdf_rowpre_kernel(const long long* row_tot, int ny, long long* row_pre) {
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        row_pre[0] = 0;
+        for (int i = 0; i < ny; ++i) {
+            acc += row_tot[i];
+            row_pre[i + 1] = acc;
+        }
+    }
+}
+
+cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w, Cdf2DView cdf, double* W_out, double* qmax_out) {
+    const int nparts = 256;
+    cudaError_t e = cudaMemsetAsync(qmax_out, 0, sizeof(double), p->stream);
+    if (e != cudaSuccess) return e;
+    double* part = p->cell_scratch;                     // nparts doubles
+    long long* row_tot = (long long*)(p->cell_scratch + nparts);  // ny
+    cdf_reduce_kernel<<<nparts, 256, 0, p->stream>>>(cell_w, p->ncells, part, qmax_out);
+    cdf_total_kernel<<<1, 32, 0, p->stream>>>(part, nparts, W_out);
+    cdf_rows_kernel<<<p->ny, 256, 0, p->stream>>>(cell_w, qmax_out, p->nx, cdf, row_tot);
+    cdf_rowpre_kernel<<<1, 32, 0, p->stream>>>(row_tot, p->ny, cdf.row_pre);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------------
+// remap density: f = (Q + sigma_s (phi_pre + phi_post) + sigma_s phi_c0, sigma_s phi_c1..3)
+// ---------------------------------------------------------------------------------------------
+__global__ void remap_density_kernel(int ncells, double adt, const double* __restrict__ Q, const double* __restrict__ ss,
+                                     const double* __restrict__ pre, const double* __restrict__ post,
+                                     const double* __restrict__ phi, double* f, double* q, DevState* st) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double r = 0;
+    if (k < ncells) {
+        const double s = ss[k];
+        const double f0 = Q[k] + s * (pre[k] + post[k]) + s * phi[4 * k];
+        const double f1 = s * phi[4 * k + 1], f2 = s * phi[4 * k + 2], f3 = s * phi[4 * k + 3];
+        f[4 * k] = f0; f[4 * k + 1] = f1; f[4 * k + 2] = f2; f[4 * k + 3] = f3;
+        const double qc = f0 * adt;
+        q[k] = qc;
+        if (qc != 0.0) {
+            const bool pos = f0 - f1 - f2 + f3 >= 0 && f0 + f1 - f2 - f3 >= 0 && f0 - f1 + f2 - f3 >= 0 &&
+                             f0 + f1 + f2 + f3 >= 0;
+            r = pos ? 1.0 : (fabs(f0) + fabs(f1) + fabs(f2) + fabs(f3)) / fabs(f0);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0 && r > 0)
+        atomicMax((unsigned long long*)&st->remap_rmax, (unsigned long long)__double_as_longlong(r));
+}
+
+__host__ __device__ inline double pow2_ceil(double w) {
+    int e = 0;
+    const double m = frexp(w, &e);
+    return m == 0.5 ? w : ldexp(1.0, e);
+}
+
+// comb base w_ref and birth weight; runs after the CDF build
+__global__ void remap_prep_kernel(DevState* st, long long n_hist) {
+    const double W = st->remap_W;
+    const double wbar = W > 0 ? W / (double)n_hist : 0.0;
+    double wmax = fmax(st->bank_wmax, wbar * st->remap_rmax);
+    st->w_ref = wmax > 0 ? pow2_ceil(wmax) : 1.0;
+}
+
+// ---------------------------------------------------------------------------------------------
+// remap streaming
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+struct RemapArgs {
+    int nx, ny;
+    T dx, dy, cdt, w_min;
+    const T* sig;
+    BankView<T> in, out;
+    Cdf2DView cdf;
+    const double* f;
+    long long n_hist, cap;
+    const uint32_t* V;
+    int ntab, sampler;
+    uint64_t key;
+    uint32_t x_off;
+    DevState* st;
+    long long* blk;            // per block: alive count, sum q, sum|w| lo, sum|w| hi
+};
+
+template <typename T>
+struct Particle { int cell; T fx, fy, ox, oy, w; bool alive; };
+
+// inverse CDF on [-1,1] of the density proportional to a + b s (a > 0, |b| <= a)
+template <typename T>
+__device__ __forceinline__ T inv_linear(T a, T b, T u) {
+    if (!(a > T(0))) return T(2) * u - T(1);
+    const T amb = a - b;
+    const T disc = amb * amb + T(4) * a * b * u;
+    const T t = T(4) * a * u / (amb + Prec<T>::sqrt_(disc > T(0) ? disc : T(0)));
+    return clamp_(t - T(1), T(-1), T(1));
+}
+
+// start state of slot j and its straight-line stream to t_{n+1} with sigma_t attenuation
+template <typename T>
+__device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long long j, long long nb, double wbar,
+                                  double* w_start, double* w_abs, double* w_leak, double* w_kill, int* leaked,
+                                  int* killed, int* segs, int* err) {
+    using P = Prec<T>;
+    int ix, iy;
+    T fx, fy, ox, oy, w, srem;
+    if (j < nb) {
+        const int k = a.in.cell[j];
+        ix = k % a.nx; iy = k / a.nx;
+        fx = a.in.fx[j]; fy = a.in.fy[j]; ox = a.in.ox[j]; oy = a.in.oy[j]; w = a.in.w[j];
+        srem = a.cdt;
+    } else {
+        const uint32_t i = (uint32_t)(j - nb);
+        T frx, fry;
+        const int k = sample_cell<T>(a.cdf, a.nx, a.ny, pts(i, 0), pts(i, 1), &frx, &fry);
+        ix = k % a.nx; iy = k / a.nx;
+        const double* fk = a.f + 4 * (size_t)k;
+        const T f0 = (T)fk[0], f1 = (T)fk[1], f2 = (T)fk[2], f3 = (T)fk[3];
+        const bool pos = fk[0] - fk[1] - fk[2] + fk[3] >= 0 && fk[0] + fk[1] - fk[2] - fk[3] >= 0 &&
+                         fk[0] - fk[1] + fk[2] - fk[3] >= 0 && fk[0] + fk[1] + fk[2] + fk[3] >= 0;
+        T xi, eta;
+        if (pos) {
+            xi = inv_linear<T>(f0, f1, frx);
+            eta = inv_linear<T>(f0 + f1 * xi, f2 + f3 * xi, fry);
+            w = (T)wbar;
+        } else {
+            xi = T(2) * frx - T(1);
+            eta = T(2) * fry - T(1);
+            w = (T)wbar * (f0 + f1 * xi + f2 * eta + f3 * xi * eta) / (f0 < T(0) ? -f0 : f0);
+        }
+        fx = T(0.5) * (xi + T(1)) * a.dx;
+        fy = T(0.5) * (eta + T(1)) * a.dy;
+        const T tf = P::unit(pts(i, 2));
+        iso_dir<T>(P::unit(pts(i, 3)), P::unit(pts(i, 4)), &ox, &oy);
+        srem = a.cdt * (T(1) - tf);
+    }
+    *w_start = (double)w;
+    const T w0 = w;
+    const T INF = (T)INFINITY;
+    Particle<T> r;
+    r.alive = false;
+    r.cell = iy * a.nx + ix;
+    int s = 0;
+    while (s < (int)kMaxSegments) {
+        ++s;
+        const int k = iy * a.nx + ix;
+        const T st = a.sig[2 * k] + a.sig[2 * k + 1];
+        const T dxf = ox > T(0) ? (a.dx - fx) / ox : (ox < T(0) ? fx / (-ox) : INF);
+        const T dyf = oy > T(0) ? (a.dy - fy) / oy : (oy < T(0) ? fy / (-oy) : INF);
+        T l;
+        bool face = false, xc = false, yc = false;
+        if (dxf <= srem || dyf <= srem) { l = dxf < dyf ? dxf : dyf; face = true; xc = dxf == l; yc = dyf == l; }
+        else l = srem;
+        *w_abs += (double)(w * (-P::exm1(-st * l)));
+        w = w * P::ex(-st * l);
+        fx = P::madd(ox, l, fx);
+        fy = P::madd(oy, l, fy);
+        srem = srem - l;
+        if (!face) {
+            r.cell = k;
+            r.fx = clamp_(fx, T(0), a.dx); r.fy = clamp_(fy, T(0), a.dy);
+            r.ox = ox; r.oy = oy; r.w = w; r.alive = true;
+            *segs += s;
+            return r;
+        }
+        if (xc) { ix += ox > T(0) ? 1 : -1; fx = ox > T(0) ? T(0) : a.dx; } else fx = clamp_(fx, T(0), a.dx);
+        if (yc) { iy += oy > T(0) ? 1 : -1; fy = oy > T(0) ? T(0) : a.dy; } else fy = clamp_(fy, T(0), a.dy);
+        if (ix < 0 || ix >= a.nx || iy < 0 || iy >= a.ny) { *w_leak += (double)w; ++*leaked; *segs += s; return r; }
+        const T aw = w < T(0) ? -w : w, aw0 = w0 < T(0) ? -w0 : w0;
+        if (a.w_min > T(0) && aw < a.w_min * aw0) { *w_kill += (double)w; ++*killed; *segs += s; return r; }
+    }
+    ++*err;
+    *segs += s;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ long long quant_w(T w, double w_ref) {
+    return __double2ll_rn((fabs((double)w) / w_ref) * 0x1p32);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* sV = sm;
+    uint32_t* sSh = sm + a.ntab * 32;
+    for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
+    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(a.key, (uint64_t)d);
+    __syncthreads();
+    Points pts{sV, sSh, a.key, a.sampler, a.ntab};
+    const long long nb = a.st->n_bank;
+    const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
+    const long long N = nb + nbirth;
+    const double wbar = nbirth ? a.st->remap_W / (double)a.n_hist : 0.0;
+    const double w_ref = a.st->w_ref;
+    const int krw = scale_exponent((double)(N > 0 ? N : 1) * w_ref, 125);
+    const double scw = ldexp(1.0, krw);
+    long long cnt = 0, qs = 0;
+    double ws = 0, w_src = 0, w_abs = 0, w_leak = 0, w_kill = 0;
+    int leaked = 0, killed = 0, segs = 0, err = 0;
+    const long long base = (long long)blockIdx.x * kSlotsPerBlock;
+    for (int r = 0; r < kRounds; ++r) {
+        const long long j = base + r * kTile + threadIdx.x;
+        if (j >= N) break;
+        double wst;
+        const Particle<T> pr = remap_slot<T>(a, pts, j, nb, wbar, &wst, &w_abs, &w_leak, &w_kill, &leaked, &killed,
+                                             &segs, &err);
+        w_src += wst;
+        if (pr.alive) {
+            ++cnt;
+            qs += quant_w<T>(pr.w, w_ref);
+            ws += fabs((double)pr.w);
+        }
+    }
+    // block sums in fixed order
+    __shared__ long long s_l[kTile / 32][2];
+    __shared__ double s_d[kTile / 32][5];
+    __shared__ int s_i[kTile / 32][4];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        qs += __shfl_down_sync(0xffffffffu, qs, o);
+        leaked += __shfl_down_sync(0xffffffffu, leaked, o);
+        killed += __shfl_down_sync(0xffffffffu, killed, o);
+        segs += __shfl_down_sync(0xffffffffu, segs, o);
+        err += __shfl_down_sync(0xffffffffu, err, o);
+    }
+    ws = warp_sum(ws); w_src = warp_sum(w_src); w_abs = warp_sum(w_abs); w_leak = warp_sum(w_leak);
+    w_kill = warp_sum(w_kill);
+    if (lane == 0) {
+        s_l[wid][0] = cnt; s_l[wid][1] = qs;
+        s_d[wid][0] = ws; s_d[wid][1] = w_src; s_d[wid][2] = w_abs; s_d[wid][3] = w_leak; s_d[wid][4] = w_kill;
+        s_i[wid][0] = leaked; s_i[wid][1] = killed; s_i[wid][2] = segs; s_i[wid][3] = err;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long c = 0, q = 0;
+        double d[5] = {0, 0, 0, 0, 0};
+        long long iv[4] = {0, 0, 0, 0};
+        for (int ww = 0; ww < kTile / 32; ++ww) {
+            c += s_l[ww][0]; q += s_l[ww][1];
+            for (int t = 0; t < 5; ++t) d[t] += s_d[ww][t];
+            for (int t = 0; t < 4; ++t) iv[t] += s_i[ww][t];
+        }
+        unsigned long long lo, hi;
+        to_i128(d[0] * scw, &lo, &hi);
+        long long* b = a.blk + 4 * (size_t)blockIdx.x;
+        b[0] = c; b[1] = q; b[2] = (long long)lo; b[3] = (long long)hi;
+        const int kw = scale_exponent((double)(N > 0 ? N : 1) * fmax(w_ref, 1e-300) * 4.0, 125);
+        const double sc = ldexp(1.0, kw);
+        Acc128* wd[4] = {&a.st->r_w_source, &a.st->r_w_absorbed, &a.st->r_w_leaked, &a.st->r_w_killed};
+        for (int t = 0; t < 4; ++t) {
+            to_i128(d[t + 1] * sc, &lo, &hi);
+            atomic_add128(wd[t], lo, hi);
+        }
+        if (iv[0]) atomicAdd(&a.st->r_leaked, (unsigned long long)iv[0]);
+        if (iv[1]) atomicAdd(&a.st->r_killed, (unsigned long long)iv[1]);
+        if (iv[2]) atomicAdd(&a.st->r_segments, (unsigned long long)iv[2]);
+        if (iv[3]) { atomicAdd(&a.st->r_errors, (unsigned long long)iv[3]); atomicOr(&a.st->status, kStSegments); }
+        if (blockIdx.x == 0) { a.st->k_rw = kw; a.st->r_histories = (unsigned long long)N; }
+    }
+}
+
+// one block: exclusive scan of block counts and quantised sums; totals, comb decision
+__global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long long cap, uint32_t x_off,
+                                  long long n_hist) {
+    __shared__ long long sc[1024], sq[1024];
+    __shared__ unsigned long long slo[1024], shi[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int per = (nblk + nt - 1) / nt;
+    const int b0 = t * per;
+    long long c = 0, q = 0;
+    unsigned long long lo = 0, hi = 0;
+    for (int b = b0; b < b0 + per && b < nblk; ++b) {
+        c += blk[4 * b]; q += blk[4 * b + 1];
+        const unsigned long long l = (unsigned long long)blk[4 * b + 2], h = (unsigned long long)blk[4 * b + 3];
+        const unsigned long long nl = lo + l;
+        hi += h + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+    sc[t] = c; sq[t] = q; slo[t] = lo; shi[t] = hi;
+    __syncthreads();
+    if (t == 0) {
+        long long ac = 0, aq = 0;
+        unsigned long long al = 0, ah = 0;
+        for (int u = 0; u < nt; ++u) {
+            const long long cc = sc[u], qq = sq[u];
+            sc[u] = ac; sq[u] = aq;
+            ac += cc; aq += qq;
+            const unsigned long long nl = al + slo[u];
+            ah += shi[u] + (nl < al ? 1ull : 0ull);
+            al = nl;
+        }
+        const long long nb = st->n_bank;
+        const long long nbirth = st->remap_W > 0 ? n_hist : 0;
+        const long long N = nb + nbirth;
+        const int krw = scale_exponent((double)(N > 0 ? N : 1) * st->w_ref, 125);
+        const double wsum = acc128_to_double(al, ah, ldexp(1.0, -krw));
+        st->comb_total_alive = ac;
+        st->comb_T = aq;
+        const int comb = ac > cap ? 1 : 0;
+        st->comb_on = comb;
+        const unsigned long long ua = (unsigned long long)aq, ux = (unsigned long long)x_off;
+        st->comb_o = (long long)((__umul64hi(ux, ua) << 32) | ((ux * ua) >> 32));
+        st->wcopy = comb ? wsum / (double)cap : 0.0;
+        // a comb needs a positive quantised total; otherwise every survivor is below the
+        // quantum 2^-33 w_ref and the census is empty
+        st->out_count = comb ? (aq > 0 ? cap : 0) : ac;
+        st->r_alive = (unsigned long long)ac;
+        st->bank_wsum = wsum;
+        st->bank_wmax = comb ? st->wcopy : 0.0;   // non-comb: max gathered in pass B
+    }
+    __syncthreads();
+    long long rc = sc[t], rq = sq[t];
+    for (int b = b0; b < b0 + per && b < nblk; ++b) {
+        const long long cc = blk[4 * b], qq = blk[4 * b + 1];
+        blk[4 * b] = rc; blk[4 * b + 1] = rq;
+        rc += cc; rq += qq;
+    }
+}
+
+// ceil(num / T) for num = hi 2^64 + lo >= 0 with quotient < 2^40, T > 0 (T < 2^63)
+__device__ __forceinline__ long long ceil_div(unsigned long long hi, unsigned long long lo, unsigned long long T) {
+    const double est = ((double)hi * 0x1p64 + (double)lo) / (double)T;
+    long long q = (long long)est;
+    if (q < 0) q = 0;
+    for (int it = 0; it < 16; ++it) {
+        // prod = q T
+        const unsigned long long plo = (unsigned long long)q * T, phi = __umul64hi((unsigned long long)q, T);
+        const bool gt = phi > hi || (phi == hi && plo > lo);
+        if (gt) { --q; continue; }
+        // rem = num - prod >= 0; if rem >= T then q++
+        const unsigned long long rlo = lo - plo;
+        const unsigned long long rhi = hi - phi - (lo < plo ? 1ull : 0ull);
+        if (rhi > 0 || rlo >= T) { ++q; continue; }
+        return (rhi == 0 && rlo == 0) ? q : q + 1;
+    }
+    return q;
+}
+
+// first tooth index at or after cumulative weight S: ceil((S M - o) / T), 0 if S M <= o
+__device__ __forceinline__ long long first_tooth(long long S, long long M, long long o, long long T) {
+    unsigned long long lo = (unsigned long long)S * (unsigned long long)M;
+    unsigned long long hi = __umul64hi((unsigned long long)S, (unsigned long long)M);
+    const unsigned long long uo = (unsigned long long)o;
+    if (hi == 0 && lo <= uo) return 0;
+    const unsigned long long nlo = lo - uo;
+    hi -= (lo < uo ? 1ull : 0ull);
+    return ceil_div(hi, nlo, (unsigned long long)T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* sV = sm;
+    uint32_t* sSh = sm + a.ntab * 32;
+    for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
+    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(a.key, (uint64_t)d);
+    __shared__ long long s_c[kTile / 32], s_q[kTile / 32];
+    __syncthreads();
+    Points pts{sV, sSh, a.key, a.sampler, a.ntab};
+    const long long nb = a.st->n_bank;
+    const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
+    const long long N = nb + nbirth;
+    const double wbar = nbirth ? a.st->remap_W / (double)a.n_hist : 0.0;
+    const double w_ref = a.st->w_ref;
+    const int comb = a.st->comb_on;
+    const long long M = a.cap, o = a.st->comb_o, Ttot = a.st->comb_T;
+    const T wcopy = (T)a.st->wcopy;
+    long long run_c = a.blk[4 * (size_t)blockIdx.x], run_q = a.blk[4 * (size_t)blockIdx.x + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double wmax = 0;
+    const long long base = (long long)blockIdx.x * kSlotsPerBlock;
+    for (int r = 0; r < kRounds; ++r) {
+        const long long j = base + r * kTile + threadIdx.x;
+        Particle<T> pr;
+        pr.alive = false;
+        if (j < N) {
+            double d0, d1 = 0, d2 = 0, d3 = 0;
+            int i0 = 0, i1 = 0, i2 = 0, i3 = 0;
+            pr = remap_slot<T>(a, pts, j, nb, wbar, &d0, &d1, &d2, &d3, &i0, &i1, &i2, &i3);
+        }
+        long long c = pr.alive ? 1 : 0;
+        long long q = pr.alive ? quant_w<T>(pr.w, w_ref) : 0;
+        // block exclusive scan of (c, q) in slot order
+        long long ic = c, iq = q;
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long vc = __shfl_up_sync(0xffffffffu, ic, off), vq = __shfl_up_sync(0xffffffffu, iq, off);
+            if (lane >= off) { ic += vc; iq += vq; }
+        }
+        if (lane == 31) { s_c[wid] = ic; s_q[wid] = iq; }
+        __syncthreads();
+        long long wc = 0, wq = 0, tc = 0, tq = 0;
+        for (int ww = 0; ww < kTile / 32; ++ww) {
+            if (ww < wid) { wc += s_c[ww]; wq += s_q[ww]; }
+            tc += s_c[ww]; tq += s_q[ww];
+        }
+        const long long pos_c = run_c + wc + ic - c;
+        const long long S = run_q + wq + iq - q;
+        if (pr.alive) {
+            if (comb && Ttot > 0) {
+                const long long t0 = first_tooth(S, M, o, Ttot), t1 = first_tooth(S + q, M, o, Ttot);
+                const T wc_ = pr.w < T(0) ? -wcopy : wcopy;
+                for (long long t = t0; t < t1 && t < M; ++t) {
+                    a.out.cell[t] = pr.cell; a.out.fx[t] = pr.fx; a.out.fy[t] = pr.fy;
+                    a.out.ox[t] = pr.ox; a.out.oy[t] = pr.oy; a.out.w[t] = wc_;
+                }
+            } else if (pos_c < M) {
+                a.out.cell[pos_c] = pr.cell; a.out.fx[pos_c] = pr.fx; a.out.fy[pos_c] = pr.fy;
+                a.out.ox[pos_c] = pr.ox; a.out.oy[pos_c] = pr.oy; a.out.w[pos_c] = pr.w;
+                wmax = fmax(wmax, fabs((double)pr.w));
+            }
+        }
+        run_c += tc;
+        run_q += tq;
+        __syncthreads();
+    }
+    for (int off = 16; off > 0; off >>= 1) wmax = fmax(wmax, __shfl_down_sync(0xffffffffu, wmax, off));
+    if (lane == 0 && wmax > 0)
+        atomicMax((unsigned long long*)&a.st->bank_wmax, (unsigned long long)__double_as_longlong(wmax));
+}
+
+__global__ void remap_finish_kernel(DevState* st) {
+    st->n_bank = st->out_count;
+}
+
+template <typename T>
+static cudaError_t remap_t(hyb_problem* p) {
+    cudaStream_t s = p->stream;
+    // remap density and its CDF
+    const int g = (p->ncells + 255) / 256;
+    cudaError_t e = cudaMemsetAsync(&p->st->remap_rmax, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_d, p->post_d,
+                                           p->sn_phi_d, p->rem_f, p->rem_q, p->st);
+    e = launch_cdf_build(p, p->rem_q, p->rem_cdf, &p->st->remap_W, &p->st->remap_qmax);
+    if (e != cudaSuccess) return e;
+    remap_prep_kernel<<<1, 1, 0, s>>>(p->st, p->d.n_hist);
+
+    RemapArgs<T> a;
+    a.nx = p->nx; a.ny = p->ny;
+    a.dx = (T)p->dx; a.dy = (T)p->dy;
+    a.cdt = (T)(p->d.c * p->d.dt);
+    a.w_min = (T)p->d.w_min;
+    a.sig = (const T*)p->sig;
+    a.in = bank_view<T>(p, p->cur);
+    a.out = bank_view<T>(p, 1 - p->cur);
+    a.cdf = p->rem_cdf;
+    a.f = p->rem_f;
+    a.n_hist = p->d.n_hist;
+    a.cap = p->d.census_cap > 0 ? p->d.census_cap : p->d.n_hist;
+    if (a.cap > p->bank_cap) a.cap = p->bank_cap;
+    a.V = p->sobolV;
+    a.ntab = p->d.sampler == HYB_SOBOL_DS ? 5 : 0;
+    a.sampler = p->d.sampler;
+    a.key = stream_key(p->d.seed, (uint64_t)p->step, HYB_STREAM_REMAP_SOURCE);
+    const uint64_t kc = stream_key(p->d.seed, (uint64_t)p->step, HYB_STREAM_REMAP_COMB);
+    a.x_off = p->d.sampler == HYB_SOBOL_DS ? dshift(kc, 0)
+                                           : (uint32_t)(dmix64(dmix64(kc ^ (0ull + kGamma)) ^ (0ull + kGamma)) >> 32);
+    a.st = p->st;
+    a.blk = p->blk;
+    const long long maxN = p->bank_cap + p->d.n_hist;
+    const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
+    const size_t smem = (size_t)(a.ntab * 32 + a.ntab + 1) * sizeof(uint32_t);
+    // zero the remap counters
+    e = cudaMemsetAsync(&p->st->r_histories, 0,
+                        (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
+    if (e != cudaSuccess) return e;
+    remap_count_kernel<T><<<nblk, kTile, smem, s>>>(a);
+    remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nblk, p->st, a.cap, a.x_off, p->d.n_hist);
+    remap_write_kernel<T><<<nblk, kTile, smem, s>>>(a);
+    remap_finish_kernel<<<1, 1, 0, s>>>(p->st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_remap(hyb_problem* p) { return p->prec == HYB_FP64 ? remap_t<double>(p) : remap_t<float>(p); }
+
+// step flux phi_pre + phi_post + phi_c0 (cell averages)
+__global__ void flux_kernel(int ncells, const double* pre, const double* post, const double* phi, double* flux) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < ncells) flux[k] = pre[k] + post[k] + phi[4 * k];
+}
+
+cudaError_t launch_flux(hyb_problem* p) {
+    flux_kernel<<<(p->ncells + 255) / 256, 256, 0, p->stream>>>(p->ncells, p->pre_d, p->post_d, p->sn_phi_d,
+                                                                p->flux_d);
+    return cudaGetLastError();
+}
+
+}  // namespace hyb

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C ABI in ``include/hyb.h`` (argument marshalling only).
+
+Every step of the hybrid path runs in the sm_103a kernels of ``libhyb.so``; PyTorch provides the
+device workspace (one caching-allocator block per problem) and the CUDA stream. There is no CPU
+fallback: without the library or a CUDA device every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+from .workloads import ProblemSpec
+
+HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ETIMEOUT, HYB_ESTATE, HYB_EBOUNDS, HYB_ECAPACITY = range(8)
+FP32, FP64 = 0, 1
+SOBOL, PRNG = 0, 1
+NS_INF = 2147483647
+STREAM_INIT, STREAM_LEG_CENSUS, STREAM_LEG_SOURCE, STREAM_REMAP_SOURCE, STREAM_REMAP_COMB = range(5)
+TALLY = {"pre": 0, "post": 1, "handoff": 2, "sn_phi": 3, "flux": 4, "pre_raw": 5, "post_raw": 6}
+SOBOL_DIMS = 65
+
+
+class HybError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"hyb status {status}: {msg}")
+        self.status = status
+
+
+class Desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("lx", C.c_double), ("ly", C.c_double),
+                ("sigma_a", C.POINTER(C.c_double)), ("sigma_s", C.POINTER(C.c_double)),
+                ("Q", C.POINTER(C.c_double)), ("ic_cell_w", C.POINTER(C.c_double)),
+                ("c", C.c_double), ("dt", C.c_double), ("n_s", C.c_int32), ("sampler", C.c_int32),
+                ("n_hist", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int32),
+                ("sn_order", C.c_int32), ("handoff_full", C.c_int32), ("sn_max_iter", C.c_int32),
+                ("sn_tol", C.c_double), ("w_min", C.c_double), ("census_cap", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("histories", "segments", "collisions", "leaked", "census",
+                                         "killed", "reached_limit", "errors")] + \
+               [(k, C.c_double) for k in ("w_source", "w_absorbed", "w_leaked", "w_census",
+                                          "w_handoff", "w_killed")] + \
+               [("sn_iterations", C.c_int32), ("combed", C.c_int32), ("bank_size", C.c_int64),
+                ("ms", C.c_float), ("pad", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+_lib = None
+
+
+def lib():
+    """Load libhyb.so (building it in-tree first when the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.OUT
+        if _build.stale():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libhyb.so is missing; run __graft_entry__.build()")
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.hyb_status_string.restype = C.c_char_p
+        L.hyb_last_error.restype = C.c_char_p
+        L.hyb_last_error.argtypes = [P]
+        L.hyb_workspace_size.argtypes = [C.POINTER(Desc), C.POINTER(C.c_size_t)]
+        L.hyb_create_problem.argtypes = [C.POINTER(Desc), P, C.c_size_t, P, C.POINTER(P)]
+        L.hyb_destroy_problem.argtypes = [P]
+        L.hyb_mc_leg.argtypes = [P, C.POINTER(Stats)]
+        L.hyb_mc_leg_trace.argtypes = [P, P, C.POINTER(Stats)]
+        L.hyb_collided_solve.argtypes = [P, C.POINTER(Stats)]
+        L.hyb_remap.argtypes = [P, C.POINTER(Stats)]
+        L.hyb_step.argtypes = [P, C.c_int32, C.POINTER(Stats)]
+        L.hyb_get_tally.argtypes = [P, C.c_int32, P, C.c_size_t, C.c_int32]
+        L.hyb_set_sn_phi.argtypes = [P, P, C.c_size_t]
+        L.hyb_get_bank.argtypes = [P] + [P] * 6 + [C.POINTER(C.c_int64)]
+        L.hyb_set_bank.argtypes = [P] + [P] * 6 + [C.c_int64]
+        L.hyb_bank_capacity.argtypes = [P, C.POINTER(C.c_int64)]
+        L.hyb_set_step.argtypes = [P, C.c_int64]
+        L.hyb_get_step.argtypes = [P, C.POINTER(C.c_int64)]
+        L.hyb_points.argtypes = [C.c_uint64, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
+                                 C.c_int32, P, P]
+        L.hyb_sobol_table.argtypes = [C.c_int32, P]
+        L.hyb_quadrature.argtypes = [C.c_int32, P, P, P, C.POINTER(C.c_int32)]
+        _lib = L
+    return _lib
+
+
+def _check(status: int, handle=None) -> None:
+    if status != HYB_OK:
+        msg = lib().hyb_last_error(handle).decode()
+        raise HybError(status, msg or lib().hyb_status_string(status).decode())
+
+
+def _torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required: the hybrid path has no CPU fallback")
+    return torch
+
+
+def _dptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_desc(spec: ProblemSpec) -> tuple[Desc, list]:
+    keep = []
+
+    def arr(x):
+        if x is None:
+            return None
+        a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).ravel())
+        keep.append(a)
+        return _dptr(a)
+
+    d = Desc(nx=spec.nx, ny=spec.ny, lx=spec.lx, ly=spec.ly, sigma_a=arr(spec.sigma_a),
+             sigma_s=arr(spec.sigma_s), Q=arr(spec.Q), ic_cell_w=arr(spec.ic), c=spec.c, dt=spec.dt,
+             n_s=spec.n_s, sampler=spec.sampler, n_hist=spec.n_hist, seed=spec.seed,
+             precision=spec.precision, sn_order=spec.sn_order, handoff_full=spec.handoff_full,
+             sn_max_iter=spec.sn_max_iter, sn_tol=spec.sn_tol, w_min=spec.w_min,
+             census_cap=spec.census_cap)
+    return d, keep
+
+
+def workspace_size(spec: ProblemSpec) -> int:
+    d, keep = make_desc(spec)
+    n = C.c_size_t(0)
+    _check(lib().hyb_workspace_size(C.byref(d), C.byref(n)))
+    return int(n.value)
+
+
+class Problem:
+    """One hybrid problem resident on the device (bank, tallies, CDFs, S_N state)."""
+
+    def __init__(self, spec: ProblemSpec, stream=None, workspace=None):
+        torch = _torch_cuda()
+        self.spec = spec
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        d, keep = make_desc(spec)
+        nbytes = C.c_size_t(0)
+        _check(lib().hyb_workspace_size(C.byref(d), C.byref(nbytes)))
+        self.ws_bytes = int(nbytes.value)
+        if workspace is None:
+            workspace = torch.empty(self.ws_bytes, dtype=torch.uint8, device="cuda")
+        elif workspace.numel() * workspace.element_size() < self.ws_bytes:
+            raise ValueError("workspace tensor too small")
+        self.workspace = workspace
+        h = C.c_void_p()
+        _check(lib().hyb_create_problem(C.byref(d), C.c_void_p(workspace.data_ptr()), self.ws_bytes,
+                                        C.c_void_p(self.stream.cuda_stream), C.byref(h)))
+        self.h = h
+        self.ncells = spec.nx * spec.ny
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            lib().hyb_destroy_problem(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- the hybrid step -------------------------------------------------------------------
+    def mc_leg(self, stats: bool = True, trace=None) -> dict | None:
+        s = Stats()
+        ps = C.byref(s) if stats else None
+        if trace is not None:
+            _check(lib().hyb_mc_leg_trace(self.h, C.c_void_p(trace.data_ptr()), ps), self.h)
+        else:
+            _check(lib().hyb_mc_leg(self.h, ps), self.h)
+        return s.as_dict() if stats else None
+
+    def collided_solve(self, stats: bool = True) -> dict | None:
+        s = Stats()
+        _check(lib().hyb_collided_solve(self.h, C.byref(s) if stats else None), self.h)
+        return s.as_dict() if stats else None
+
+    def remap(self, stats: bool = True) -> dict | None:
+        s = Stats()
+        _check(lib().hyb_remap(self.h, C.byref(s) if stats else None), self.h)
+        return s.as_dict() if stats else None
+
+    def step(self, n: int = 1, stats: bool = True) -> list[dict] | None:
+        arr = (Stats * max(n, 1))()
+        _check(lib().hyb_step(self.h, n, arr if stats else None), self.h)
+        return [arr[i].as_dict() for i in range(n)] if stats else None
+
+    # --- data ------------------------------------------------------------------------------
+    def tally(self, which: str) -> np.ndarray:
+        n = self.ncells * (4 if which in ("handoff", "sn_phi") else 1)
+        out = np.zeros(n)
+        _check(lib().hyb_get_tally(self.h, TALLY[which], out.ctypes.data_as(C.c_void_p), n, 0), self.h)
+        return out.reshape(self.ncells, 4) if n != self.ncells else out
+
+    def tally_to(self, which: str, dst) -> None:
+        """Copy a tally into a device tensor (float64, right size)."""
+        _check(lib().hyb_get_tally(self.h, TALLY[which], C.c_void_p(dst.data_ptr()), dst.numel(), 1), self.h)
+
+    def set_sn_phi(self, phi: np.ndarray) -> None:
+        a = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+        _check(lib().hyb_set_sn_phi(self.h, a.ctypes.data_as(C.c_void_p), a.size), self.h)
+
+    def capacity(self) -> int:
+        c = C.c_int64(0)
+        _check(lib().hyb_bank_capacity(self.h, C.byref(c)), self.h)
+        return int(c.value)
+
+    def bank(self) -> dict:
+        cap = self.capacity()
+        cell = np.zeros(cap, np.int32)
+        f = [np.zeros(cap) for _ in range(5)]
+        n = C.c_int64(cap)
+        _check(lib().hyb_get_bank(self.h, cell.ctypes.data_as(C.c_void_p),
+                                  *[a.ctypes.data_as(C.c_void_p) for a in f], C.byref(n)), self.h)
+        k = int(n.value)
+        return {"cell": cell[:k], "fx": f[0][:k], "fy": f[1][:k], "ox": f[2][:k], "oy": f[3][:k],
+                "w": f[4][:k], "n": k}
+
+    def set_bank(self, b: dict) -> None:
+        n = int(b.get("n", len(b["w"])))
+        cell = np.ascontiguousarray(b["cell"][:n], dtype=np.int32)
+        f = [np.ascontiguousarray(b[k][:n], dtype=np.float64) for k in ("fx", "fy", "ox", "oy", "w")]
+        _check(lib().hyb_set_bank(self.h, cell.ctypes.data_as(C.c_void_p),
+                                  *[a.ctypes.data_as(C.c_void_p) for a in f], n), self.h)
+
+    def set_step(self, k: int) -> None:
+        _check(lib().hyb_set_step(self.h, k), self.h)
+
+    @property
+    def step_index(self) -> int:
+        s = C.c_int64(0)
+        _check(lib().hyb_get_step(self.h, C.byref(s)), self.h)
+        return int(s.value)
+
+
+def sobol_table(ndims: int) -> np.ndarray:
+    out = np.zeros((ndims, 32), np.uint32)
+    _check(lib().hyb_sobol_table(ndims, out.ctypes.data_as(C.c_void_p)))
+    return out
+
+
+def quadrature(order: int):
+    ox, oy, w = np.zeros(40), np.zeros(40), np.zeros(40)
+    m = C.c_int32(40)
+    _check(lib().hyb_quadrature(order, ox.ctypes.data_as(C.c_void_p), oy.ctypes.data_as(C.c_void_p),
+                                w.ctypes.data_as(C.c_void_p), C.byref(m)))
+    return ox[:m.value], oy[:m.value], w[:m.value]
+
+
+def points(seed: int, step: int, stream_id: int, sampler: int, i0: int, n: int, ndims: int, stream=None):
+    """Point-set integers on the device, shape (n, ndims), as a torch int32 tensor (bit pattern)."""
+    torch = _torch_cuda()
+    out = torch.empty((n, ndims), dtype=torch.int32, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().hyb_points(C.c_uint64(seed), step, stream_id, sampler, i0, n, ndims,
+                            C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream)))
+    return out

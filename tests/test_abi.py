@@ -1,0 +1,97 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports every entry point
+that include/hyb.h declares, and its host-side tables and validation behave."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2511_16821_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hyb():
+    from paper_2511_16821_gb300 import build, hyb as H
+    build.build()
+    return H
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "hyb.h")).read()
+    return sorted(set(re.findall(r"HYB_API\s+[\w\s\*]+?\b(hyb_\w+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(hyb):
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    L = C.CDLL(hyb.lib()._name)
+    for s in syms:
+        assert hasattr(L, s), s
+
+
+def test_sobol_table_matches_oracle(hyb, orc):
+    assert np.array_equal(hyb.sobol_table(65), orc.sobol_table(65))
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_quadrature_matches_oracle(hyb, orc, order):
+    ox, oy, w = hyb.quadrature(order)
+    a, b, _, c = orc.quadrature(order)
+    assert np.allclose(ox, a, atol=1e-14) and np.allclose(oy, b, atol=1e-14)
+    assert np.allclose(w, c, rtol=1e-13)
+
+
+def _bad(spec, **kw):
+    return spec.with_(**kw)
+
+
+@pytest.mark.parametrize("mut", [
+    dict(nx=0), dict(ny=5000), dict(dt=0.0), dict(c=-1.0), dict(n_s=-1), dict(sn_order=6),
+    dict(n_hist=0), dict(sampler=7), dict(precision=3), dict(w_min=1.5), dict(sn_max_iter=0),
+])
+def test_workspace_size_rejects_bad_descriptors(hyb, mut):
+    spec = W.pulse(n_hist=100)
+    if "nx" in mut or "ny" in mut:
+        n = mut.get("nx", spec.nx) * mut.get("ny", spec.ny)
+        spec = spec.with_(sigma_a=np.ones(max(n, 1)), sigma_s=np.ones(max(n, 1)), ic=None)
+    with pytest.raises(hyb.HybError) as e:
+        hyb.workspace_size(spec.with_(**mut))
+    assert e.value.status == hyb.HYB_EINVAL
+
+
+@pytest.mark.parametrize("field", ["sigma_a", "sigma_s", "Q"])
+def test_rejects_nonfinite_or_negative_data(hyb, field):
+    spec = W.homogeneous(n=4, Q=1.0)
+    for bad in (np.nan, -1.0, np.inf):
+        arr = np.array(getattr(spec, field), dtype=float)
+        arr[3] = bad
+        with pytest.raises(hyb.HybError):
+            hyb.workspace_size(spec.with_(**{field: arr}))
+
+
+def test_workspace_size_scales_with_histories(hyb):
+    a = hyb.workspace_size(W.checkerboard(n_hist=10_000))
+    b = hyb.workspace_size(W.checkerboard(n_hist=1_000_000))
+    c = hyb.workspace_size(W.checkerboard(n_hist=1_000_000, precision=W.FP32))
+    assert a < b and c < b
+
+
+def test_no_cpu_fallback_without_gpu(hyb):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(RuntimeError):
+        hyb.Problem(W.pulse(n_hist=10))
+
+
+def test_input_generators_are_deterministic():
+    a = W.random_batch_problem(0, 5)
+    b = W.random_batch_problem(0, 5)
+    assert a.nx == b.nx and np.array_equal(a.sigma_a, b.sigma_a) and a.n_hist == b.n_hist
+    c = W.checkerboard(cells_per_block=4)
+    assert c.nx == 28 and c.Q.sum() == 16 and c.sigma_s.reshape(28, 28)[13, 13] == 1.0
+    big = W.large(n=64, block=8, n_hist=10)
+    assert set(np.round(big.sigma_a + big.sigma_s, 6)) <= {1.0, 10.0, 1000.0}

@@ -1,0 +1,279 @@
+"""GPU parity: the sm_103a path through the C ABI against the FP64 oracle, element by element.
+
+Bar (integers bit-exact; FP64 tallies within 1e-12 relative per cell; FP32 within 1e-4 relative on
+cells above 1e-3 of the peak, with the FP32 error reported for every tally):
+  * point sets (Sobol + digital shift, counter PRNG, PRNG fallback past the table) bit-exact
+  * MC leg: per-history (final cell, fate, scatter count, segments) and all counters bit-exact,
+    pre/post tallies and hand-off moments within the tolerance, balance
+  * collided S_N-DG solve, remap (with the comb), and whole multi-step runs
+Sizes span several S_N tiles and a ragged tail; edge cases: 1x1 mesh, one history, empty bank,
+N_s = 0, killing, no source.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2511_16821_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_RTOL = 1e-12
+FP32_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    hyb.lib()
+    return hyb
+
+
+def n_hist_total(spec, bank):
+    nb = 0 if bank is None else int(bank["n"])
+    return nb + (spec.n_hist if spec.Q is not None and np.sum(spec.Q) > 0 else 0)
+
+
+def gpu_leg(H, spec, bank, step=0):
+    import torch
+    P = H.Problem(spec.with_(ic=None))
+    P.set_bank(bank if bank is not None else {"cell": np.zeros(0, np.int32), **{k: np.zeros(0) for k in ("fx", "fy", "ox", "oy", "w")}, "n": 0})
+    P.set_step(step)
+    N = n_hist_total(spec, bank)
+    tr = torch.full((max(N, 1), 4), -7, dtype=torch.int32, device="cuda")
+    st = P.mc_leg(trace=tr)
+    out = dict(pre=P.tally("pre_raw"), post=P.tally("post_raw"), mom=P.tally("handoff"), stats=st,
+               hist=tr.cpu().numpy()[:N], P=P)
+    return out
+
+
+def check_counts(g, o):
+    for k in ("histories", "segments", "collisions", "leaked", "census", "killed", "reached_limit", "errors"):
+        assert g[k] == o[k], (k, g[k], o[k])
+    for k in ("w_source", "w_absorbed", "w_leaked", "w_census", "w_handoff", "w_killed"):
+        assert math.isclose(g[k], o[k], rel_tol=1e-12, abs_tol=1e-14 * max(1.0, abs(o["w_source"]))), (k, g[k], o[k])
+
+
+def rel_err(g, o, floor):
+    return np.abs(g - o) / np.maximum(np.abs(o), floor)
+
+
+def check_fp64_tallies(g, o):
+    for key in ("pre", "post"):
+        a, b = g[key], o[key]
+        assert np.all(np.abs(a - b) <= FP64_RTOL * np.abs(b) + 1e-300), (key, np.max(rel_err(a, b, 1e-300)))
+        assert np.all((a == 0) == (b == 0)), key
+    m_g, m_o = g["mom"], o["mom"]
+    bound = np.abs(m_o[:, :1])            # |m_j| <= m_0 since |P_j| <= 1 on the cell
+    assert np.all(np.abs(m_g[:, 0] - m_o[:, 0]) <= FP64_RTOL * np.abs(m_o[:, 0]) + 1e-300)
+    assert np.all(np.abs(m_g[:, 1:] - m_o[:, 1:]) <= FP64_RTOL * (np.abs(m_o[:, 1:]) + bound) + 1e-300)
+
+
+def fp32_report(g, o):
+    """Max relative error of every FP32 tally on cells above 1e-3 of its peak."""
+    rep = {}
+    for key in ("pre", "post"):
+        a, b = g[key], o[key]
+        peak = np.max(np.abs(b)) if b.size else 0
+        sel = np.abs(b) >= 1e-3 * peak if peak > 0 else np.zeros_like(b, bool)
+        rep[key] = float(np.max(rel_err(a[sel], b[sel], 1e-300))) if sel.any() else 0.0
+    for j in range(4):
+        a, b = g["mom"][:, j], o["mom"][:, j]
+        peak = np.max(np.abs(o["mom"][:, 0])) if o["mom"].size else 0
+        sel = np.abs(o["mom"][:, 0]) >= 1e-3 * peak if peak > 0 else np.zeros_like(b, bool)
+        rep[f"mom{j}"] = float(np.max(np.abs(a[sel] - b[sel]) / np.abs(o["mom"][sel, 0]))) if sel.any() else 0.0
+    return rep
+
+
+# ------------------------------------------------------------------------------------------------
+# point sets
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("sampler", [0, 1])
+@pytest.mark.parametrize("i0,n,nd", [(0, 4097, 29), (123456, 3000, 70), (2 ** 31 - 5, 10, 8)])
+def test_points_bitexact(H, orc, sampler, i0, n, nd):
+    g = H.points(99, 7, 3, sampler, i0, n, nd).cpu().numpy().view(np.uint32)
+    o = orc.points(99, 7, 3, sampler, i0, n, nd)
+    assert np.array_equal(g, o)
+
+
+# ------------------------------------------------------------------------------------------------
+# MC leg, FP64
+# ------------------------------------------------------------------------------------------------
+def leg_cases():
+    cb = W.checkerboard(n_s=2, n_hist=20_000, cells_per_block=5)   # 35x35: ragged vs 32-tiles
+    rng = np.random.default_rng(0)
+    het = W.ProblemSpec(nx=37, ny=23, lx=3.7, ly=2.0, sigma_a=rng.uniform(0, 2, 37 * 23),
+                        sigma_s=rng.uniform(0, 4, 37 * 23), Q=rng.uniform(0, 1, 37 * 23) ** 2, dt=0.3,
+                        n_s=3, n_hist=30_000, seed=5, w_min=0.05)
+    return [
+        ("pulse", W.pulse(n_hist=10_000), "ic", 0),
+        ("cb_ns0", cb.with_(n_s=0), 5000, 3),
+        ("cb_ns1", cb.with_(n_s=1), 5000, 1),
+        ("cb_ns2", cb, 5000, 2),
+        ("cb_ns4_prng", cb.with_(n_s=4, sampler=W.PRNG), 5000, 4),
+        ("het_kill", het, 4000, 6),
+        ("one_cell", W.homogeneous(n=1, L=0.5, sigma_a=0.3, sigma_s=2.0, Q=1.0, n_hist=1, dt=1.0, n_s=2), 1, 0),
+        ("no_source_empty", W.homogeneous(n=3, Q=None, n_hist=5), 0, 0),
+        ("n_s_20", W.homogeneous(n=6, L=1.0, sigma_a=0.1, sigma_s=30.0, Q=1.0, n_hist=3000, dt=0.5, n_s=20), 500, 1),
+    ]
+
+
+def bank_for(orc, spec, nb):
+    if nb == "ic":
+        return orc.init_bank(spec, spec.ic)
+    if nb == 0:
+        return None
+    return W.random_bank(spec, nb, seed=nb + 1)
+
+
+@pytest.mark.parametrize("case", leg_cases(), ids=lambda c: c[0])
+def test_mc_leg_fp64_parity(H, orc, case):
+    name, spec, nb, step = case
+    bank = bank_for(orc, spec, nb)
+    o = orc.mc_leg(spec, step, bank, want_hist=True)
+    g = gpu_leg(H, spec, bank, step)
+    assert o["rc"] in (0, 3)
+    if g["hist"].size:
+        mism = np.nonzero(np.any(g["hist"] != o["hist"], axis=1))[0]
+        assert mism.size == 0, f"{mism.size} history records differ, first {mism[:5]}: " \
+                               f"{g['hist'][mism[:3]]} vs {o['hist'][mism[:3]]}"
+    check_counts(g["stats"], o["stats"])
+    check_fp64_tallies(g, o)
+
+
+def test_initial_bank_parity(H, orc):
+    spec = W.pulse(n_hist=4096)
+    P = H.Problem(spec)
+    g = P.bank()
+    o = orc.init_bank(spec, spec.ic)
+    assert g["n"] == o["n"] == 4096
+    assert np.array_equal(g["cell"], o["cell"])
+    for k in ("fx", "fy", "ox", "oy", "w"):
+        assert np.allclose(g[k], o[k], rtol=1e-14, atol=1e-16), k
+
+
+# ------------------------------------------------------------------------------------------------
+# MC leg, FP32 tracking (cell-local coordinates, int64 fixed-point tallies)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("case", [c for c in leg_cases() if c[0] in ("pulse", "cb_ns0", "cb_ns2", "het_kill")],
+                         ids=lambda c: c[0])
+def test_mc_leg_fp32_tolerance(H, orc, case):
+    name, spec, nb, step = case
+    bank = bank_for(orc, spec, nb)
+    o = orc.mc_leg(spec, step, bank, want_hist=True)
+    g = gpu_leg(H, spec.with_(precision=W.FP32), bank, step)
+    flips = int(np.sum(np.any(g["hist"] != o["hist"], axis=1)))
+    rep = fp32_report(g, o)
+    print(f"\nFP32 {name}: history flips {flips}/{len(o['hist'])}, max rel err {rep}")
+    assert flips <= max(2, len(o["hist"]) // 20000)
+    for k, v in rep.items():
+        assert v < FP32_RTOL, (k, v)
+    # birth cells come from the 32-bit point integers: identical to the FP64 path
+    s = g["stats"]
+    tot = s["w_absorbed"] + s["w_leaked"] + s["w_census"] + s["w_handoff"] + s["w_killed"]
+    assert math.isclose(s["w_source"], tot, rel_tol=1e-5)
+
+
+# ------------------------------------------------------------------------------------------------
+# collided S_N-DG and remap
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("order,n", [(4, 35), (8, 40), (8, 7)])
+def test_collided_solve_parity(H, orc, order, n):
+    spec = W.checkerboard(n_s=1, n_hist=20_000, cells_per_block=max(1, n // 7)).with_(sn_order=order, sn_tol=1e-13)
+    bank = W.random_bank(spec, 4000, seed=3)
+    o = orc.mc_leg(spec, 0, bank)
+    phi_o, it_o = orc.sn_solve(spec, o["mom"])
+    g = gpu_leg(H, spec, bank, 0)
+    st = g["P"].collided_solve()
+    phi_g = g["P"].tally("sn_phi")
+    scale = np.max(np.abs(phi_o[:, 0]))
+    assert abs(st["sn_iterations"] - it_o) <= 1
+    assert np.allclose(phi_g, phi_o, rtol=1e-9, atol=1e-10 * scale)
+
+
+@pytest.mark.parametrize("cap", [0, 10 ** 7])
+def test_remap_parity(H, orc, cap):
+    spec = W.checkerboard(n_s=2, n_hist=20_000, cells_per_block=4).with_(census_cap=cap)
+    bank = W.random_bank(spec, 15_000, seed=8)
+    o = orc.mc_leg(spec, 2, bank)
+    phi_o, _ = orc.sn_solve(spec, o["mom"])
+    ob, ost, ocomb = orc.remap(spec, 2, bank, o["pre"], o["post"], phi_o)
+    g = gpu_leg(H, spec, bank, 2)
+    P = g["P"]
+    P.set_sn_phi(phi_o)
+    rs = P.remap()
+    gb = P.bank()
+    assert bool(rs["combed"]) == ocomb
+    assert gb["n"] == ob["n"]
+    assert np.array_equal(gb["cell"], ob["cell"])
+    d = spec.lx / spec.nx
+    for k in ("fx", "fy"):
+        assert np.allclose(gb[k], ob[k], rtol=0, atol=1e-10 * d), k
+    for k in ("ox", "oy"):
+        assert np.allclose(gb[k], ob[k], rtol=0, atol=1e-12), k
+    assert np.allclose(gb["w"], ob["w"], rtol=1e-10, atol=0)
+    assert rs["histories"] == ost["histories"] and rs["leaked"] == ost["leaked"]
+    assert math.isclose(rs["w_source"], ost["w_source"], rel_tol=1e-10)
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32])
+def test_multistep_hybrid(H, orc, prec):
+    spec = W.pulse(n_hist=8192).with_(precision=prec, sn_tol=1e-12 if prec == W.FP64 else 1e-7)
+    ospec = spec.with_(precision=W.FP64, sn_tol=1e-12)
+    P = H.Problem(spec)
+    ob = orc.init_bank(ospec, ospec.ic)
+    errs = []
+    for k in range(4):
+        stats = P.step(1)[0]
+        r = orc.step(ospec, k, ob)
+        ob = r["bank"]
+        flux_g = P.tally("flux")
+        peak = np.max(np.abs(r["flux"]))
+        sel = np.abs(r["flux"]) >= 1e-3 * peak
+        err = float(np.max(np.abs(flux_g[sel] - r["flux"][sel]) / np.abs(r["flux"][sel])))
+        errs.append(err)
+        assert stats["bank_size"] == ob["n"]
+    print(f"\nmulti-step flux max rel err per step ({'FP64' if prec else 'FP32'}): {errs}")
+    assert max(errs) < (1e-9 if prec == W.FP64 else 2e-3)
+
+
+# ------------------------------------------------------------------------------------------------
+# full-size configurations
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n_s", [0, 1, 2, 4])
+def test_checkerboard_full_size_leg(H, orc, n_s):
+    """112x112 checkerboard, 10^6 source histories + a 10^6 bank (the benchmark leg)."""
+    spec = W.checkerboard(n_s=n_s, n_hist=1_000_000)
+    bank = W.random_bank(spec, 1_000_000, seed=n_s)
+    o = orc.mc_leg(spec, 1, bank, want_hist=True)
+    g = gpu_leg(H, spec, bank, 1)
+    mism = int(np.sum(np.any(g["hist"] != o["hist"], axis=1)))
+    assert mism == 0, mism
+    check_counts(g["stats"], o["stats"])
+    check_fp64_tallies(g, o)
+    g32 = gpu_leg(H, spec.with_(precision=W.FP32), bank, 1)
+    rep = fp32_report(g32, o)
+    flips = int(np.sum(np.any(g32["hist"] != o["hist"], axis=1)))
+    print(f"\nFP32 checkerboard N_s={n_s}: flips {flips}/{len(o['hist'])}, max rel err {rep}")
+    for k, v in rep.items():
+        assert v < FP32_RTOL, (k, v)
+
+
+def test_large_mesh_sampled_records(H, orc):
+    """1024x1024 diffusive mesh, N_s = 8: the first 2^16 source histories of a 2^22-history FP64
+    leg match the oracle's records one by one (records do not depend on the history count)."""
+    import torch
+    spec = W.large(n=1024, n_hist=2 ** 22, precision=W.FP64)
+    P = H.Problem(spec)
+    N = spec.n_hist
+    tr = torch.zeros((N, 4), dtype=torch.int32, device="cuda")
+    st = P.mc_leg(trace=tr)
+    o = orc.mc_leg(spec.with_(n_hist=2 ** 16), 0, None, want_hist=True)
+    g = tr[: 2 ** 16].cpu().numpy()
+    assert np.array_equal(g, o["hist"])
+    s = st
+    tot = s["w_absorbed"] + s["w_leaked"] + s["w_census"] + s["w_handoff"] + s["w_killed"]
+    assert math.isclose(s["w_source"], tot, rel_tol=1e-12)
+    assert s["histories"] == N and s["errors"] == 0
