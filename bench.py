@@ -1,0 +1,350 @@
+"""Benchmark of the GB300 hybrid (Q)MC / S_N step.
+
+Workload (the one-GPU benchmark configuration): the 7x7-block checkerboard on a 112x112 mesh
+(absorber sigma_a = 10 / scatterer sigma_s = 1, Q = 1 in the centre block, vacuum boundaries),
+10^6 source histories per step plus the census bank (10^6 after the comb), dt = 0.1, S8, Sobol
+points with a digital shift. One step = the whole hybrid step: MC leg, collided S_N-DG solve,
+remap and census (Sec. 2.2 steps 1-4). Headline: FP32 tracking with int64 fixed-point tallies;
+the FP64 path is measured beside it.
+
+value     = MC-leg histories per second of whole-step time (device events, L2 flushed between
+            steps; inputs resident in HBM)
+e2e       = the same through the public C ABI with the census bank copied in from host memory and
+            the step flux copied back every step
+cpu_baseline / --impl reference = the single-threaded FP64 oracle on the host cores, on a
+            bounded sample of the same workload.
+Under torchrun (N > 1) each rank runs an independent problem replica (weak scaling, no
+data-path collective); the barrier and the max over ranks of the timed region are kept.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_16821_gb300 import workloads as W  # noqa: E402
+
+N_S = 2
+N_HIST = 1_000_000
+L2_FLUSH_BYTES = 512 << 20
+METRIC = "histories/s"
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs", 6800.0), "src": "measured", "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
+    return {"hbm_gbs": 6800.0, "src": "fallback", "sm_max_mhz": 2070.0}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.rows = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0, warm: int = 1) -> W.ProblemSpec:
+    """The benchmark workload; source iteration starts from the previous step's collided flux
+    (the same fixed point, fewer sweeps)."""
+    return W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision).with_(sn_warm_start=warm)
+
+
+def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
+    leg = 2                                   # leg kernel + normalisation
+    sn = 4 * sn_iters + 2                     # source, sweep, reduce, norm per SI iteration; copy, flux
+    remap = 1 + 4 + 1 + 3 + 1                 # density, CDF (4), prep, count/scan/write, finish
+    return leg + sn + remap
+
+
+def run_gpu(args, rank: int, world: int) -> dict:
+    import torch
+    from paper_2511_16821_gb300 import hyb
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    res = {}
+    for prec in ([W.FP32, W.FP64] if not args.fp32_only else [W.FP32]):
+        spec = spec_for(prec, seed=rank)
+        with torch.cuda.stream(stream):
+            P = hyb.Problem(spec, stream=stream)
+            for _ in range(args.warmup):
+                P.step(1)
+            torch.cuda.synchronize()
+            if world > 1:
+                import torch.distributed as dist
+                dist.barrier()
+            e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+            hist = segs = 0
+            phase = {"mc_leg": [], "collided_sn": [], "remap": []}
+            sn_it = []
+            clk = Clocks(dev.index)
+            with clk:
+                t0 = time.perf_counter()
+                for k in range(args.steps):
+                    flush.zero_()
+                    e0[k].record(stream)
+                    ls = P.mc_leg()
+                    cs = P.collided_solve()
+                    rs = P.remap()
+                    e1[k].record(stream)
+                    hist += ls["histories"]
+                    segs += ls["segments"] + rs["segments"]
+                    phase["mc_leg"].append(ls["ms"])
+                    phase["collided_sn"].append(cs["ms"])
+                    phase["remap"].append(rs["ms"])
+                    sn_it.append(cs["sn_iterations"])
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+            step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+            res[prec] = dict(spec=spec, P=P, hist=hist, segs=segs, step_ms=step_ms, wall=wall,
+                             clocks=clk.summary(), sn_iters=sn_it, bank=rs["bank_size"],
+                             phase_ms={k: statistics.median(v) for k, v in phase.items()})
+    return res
+
+
+def leg_profile(prec: int, reps: int = 5) -> dict:
+    """Device time of the MC leg alone (events recorded by the library around the leg kernel and
+    its normalisation, on the problem's stream) at the benchmark workload."""
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    spec = spec_for(prec)
+    P = hyb.Problem(spec)
+    P.step(2)                      # a steady-state census bank
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ms, hist, segs, nb = [], 0, 0, 0
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        P.set_step(2)
+        st = P.mc_leg()
+        ms.append(st["ms"])
+        hist, segs = st["histories"], st["segments"]
+    bank = P.bank()
+    nb = bank["n"]
+    return dict(ms=statistics.median(ms), histories=hist, segments=segs, bank=nb)
+
+
+def e2e_measure(spec: W.ProblemSpec, steps: int) -> dict:
+    """Public-API end to end: per step the census bank is copied in from host memory
+    (hyb_set_bank), one hybrid step runs, and the step flux is read back (hyb_get_tally)."""
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    P = hyb.Problem(spec)
+    P.step(1)
+    host_bank = P.bank()
+    esz = 4 if spec.precision == W.FP32 else 8
+    hist = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        P.set_bank(host_bank)
+        st = P.step(1)[0]
+        flux = P.tally("flux")
+        hist += st["histories"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    assert np.isfinite(flux).all()
+    return {"value": hist / dt, "unit": METRIC,
+            "h2d_bytes_per_step": int(host_bank["n"]) * (4 + 5 * esz),
+            "d2h_bytes_per_step": int(spec.nx * spec.ny * 8)}
+
+
+def cpu_baseline(n_hist: int, steps: int) -> dict:
+    """The FP64 oracle, single-threaded, on a bounded sample of the workload (same mesh, N_s,
+    dt and quadrature; n_hist histories per step)."""
+    import oracle
+    oracle.build()
+    spec = spec_for(W.FP64, n_hist=n_hist, warm=0)
+    bank = None
+    hist = 0
+    t0 = time.perf_counter()
+    for k in range(steps):
+        r = oracle.step(spec, k, bank)
+        bank = r["bank"]
+        hist += r["leg"]["histories"]
+    dt = time.perf_counter() - t0
+    return {"value": hist / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full hybrid steps of the checkerboard-112 workload at {n_hist} "
+                      f"histories/step (FP64 oracle, one thread)", "seconds": round(dt, 2)}
+
+
+def reference_arm(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    n_hist = 200_000
+    import oracle
+    oracle.build()
+    spec = spec_for(W.FP64, n_hist=n_hist, warm=0)
+    bank = None
+    for k in range(args.warmup):
+        bank = oracle.step(spec, k, bank)["bank"]
+    hist = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r = oracle.step(spec, args.warmup + k, bank)
+        bank = r["bank"]
+        hist += r["leg"]["histories"]
+    dt = time.perf_counter() - t0
+    v = hist / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_block(),
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} hybrid steps at {n_hist} histories/step"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_block() -> dict:
+    return {"workload": "checkerboard 7x7 blocks, 112x112 mesh, N_s=2, 1e6 histories/step, dt=0.1, S8",
+            "mesh": "112x112", "n_s": N_S, "n_hist": N_HIST, "sampler": "sobol+digital shift",
+            "sn_order": 8, "dt": 0.1, "l2": "flushed (512 MiB write) before every timed step"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--fp32-only", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lean", action="store_true",
+                    help="timed steps only (FP32, no profile/e2e/CPU legs): the case used for ncu captures")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="gloo" if args.impl == "reference" else "nccl")
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+
+    import torch
+    if args.lean:
+        args.fp32_only = args.no_cpu = args.no_e2e = True
+    res = run_gpu(args, rank, world)
+    if args.lean:
+        if rank == 0:
+            r = res[W.FP32]
+            print(json.dumps({"lean": True, "ms_per_step": sum(r["step_ms"]) / args.steps,
+                              "phase_ms": r["phase_ms"], "sn_iterations": r["sn_iters"]}), flush=True)
+        return
+    r32 = res[W.FP32]
+    tot_ms = sum(r32["step_ms"])
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        h = torch.tensor([float(r32["hist"]), float(r32["segs"])], dtype=torch.float64, device="cuda")
+        dist.all_reduce(h)
+        hist_all, segs_all = h[0].item(), h[1].item()
+    else:
+        hist_all, segs_all = r32["hist"], r32["segs"]
+    if rank != 0:
+        return
+    value = hist_all / (tot_ms / 1000.0)
+    pk = peaks()
+    prof = leg_profile(W.FP32)
+    # MC-leg algorithmic HBM bytes: census pickup (24 B per bank particle), one 8-byte fixed-point
+    # add per pre-limit segment and five per post-limit segment are not HBM traffic after L2
+    # aggregation, so the algorithmic bytes are the bank stream plus the tally arrays.
+    nc = 112 * 112
+    leg_bytes = prof["bank"] * 24 + 3 * nc * 8 + 4 * nc * 8
+    achieved = leg_bytes / (prof["ms"] / 1000.0) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_block(),
+        "segments_per_s": segs_all / (tot_ms / 1000.0),
+        "sn_iterations": r32["sn_iters"],
+        "phase_ms": r32["phase_ms"],
+        "roofline": {"bound": "hbm", "kernel": "mc_leg_kernel<float>", "achieved": achieved,
+                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                     "traffic": None, "leg_ms": prof["ms"], "leg_histories": prof["histories"],
+                     "leg_segments": prof["segments"], "peak_src": pk["src"]},
+        "gpu_launches": launches_per_step(r32["spec"], int(np.mean(r32["sn_iters"]) + 0.5)) * args.steps,
+        "clocks": r32["clocks"],
+    }
+    if W.FP64 in res:
+        r64 = res[W.FP64]
+        ms64 = sum(r64["step_ms"])
+        line["fp64"] = {"value": r64["hist"] / (ms64 / 1000.0), "unit": METRIC,
+                        "segments_per_s": r64["segs"] / (ms64 / 1000.0), "ms_per_step": ms64 / args.steps,
+                        "phase_ms": r64["phase_ms"]}
+    if not args.no_e2e:
+        line["e2e"] = e2e_measure(spec_for(W.FP32), max(2, min(args.steps, 5)))
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(n_hist=200_000, steps=2)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -92,6 +92,9 @@ typedef struct {
     double sn_tol;            /* SI stop: ||phi_new - phi_old|| <= sn_tol ||phi_new|| */
     double w_min;             /* relative kill threshold (w < w_min * w_start); 0 = never */
     int64_t census_cap;       /* census capacity after the comb; 0 = n_hist */
+    int32_t sn_warm_start;    /* 1: source iteration starts from the previous step's collided
+                                 flux (same fixed point, fewer iterations); 0: from zero */
+    int32_t pad0;
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */

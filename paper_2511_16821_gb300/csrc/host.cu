@@ -222,7 +222,6 @@ Sizes sizes(const hyb_problem_desc* d) {
     const size_t T = d->precision == HYB_FP64 ? 8 : 4;
     const size_t acc = d->precision == HYB_FP64 ? 16 : 8;
     const int nord = d->sn_order == 8 ? 40 : 12;
-    const size_t ntx = (d->nx + kSnTile - 1) / kSnTile, nty = (d->ny + kSnTile - 1) / kSnTile;
     z.cap = eff_cap(d);
     z.st = sizeof(DevState);
     z.sobol = HYB_SOBOL_DIMS * 32 * 4;
@@ -240,9 +239,9 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.d1 = nc * 8;
     z.d4 = 4 * nc * 8;
     z.sn4 = 4 * nc * T;
-    z.sn16 = 16 * nc * T;
-    z.sntx = (size_t)nord * d->ny * ntx * 2 * T;
-    z.snty = (size_t)nord * d->nx * nty * 2 * T;
+    z.sn16 = 5 * nc * T;                          // source (4) and sigma* A (1) per cell
+    z.sntx = (size_t)nord * nc * 4 * T;           // w_m psi_m per ordinate and cell
+    z.snty = (size_t)nord * d->nx * 2 * T;        // strip-top traces per ordinate
     z.snqb = 3 * kMaxOrd * T;
     z.snnorm = 2 * ((nc + 255) / 256) * 8;
     z.nblk = (z.cap + d->n_hist + 2047) / 2048;
@@ -295,7 +294,7 @@ void assign(hyb_problem* p) {
     p->sn_phi = take(z.sn4);
     p->sn_phi_old = take(z.sn4);
     p->sn_quad = take(z.sn16);
-    p->sn_tx = take(z.sntx);
+    p->sn_psi = take(z.sntx);
     p->sn_ty = take(z.snty);
     p->sn_quadbuf = take(z.snqb);
     p->sn_phi_d = (double*)take(z.d4);
@@ -514,6 +513,7 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     p->cur = 0;
     p->ndims = 5 + 3 * d->n_s;
     p->leg_done = p->sn_done = false;
+    p->sn_warm = false;
     p->ev0 = p->ev1 = nullptr;
     p->st_host = nullptr;
     if (workspace) { p->ws = workspace; p->ws_bytes = ws_bytes; p->owns_ws = false; }
@@ -633,6 +633,7 @@ hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
     if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
     if (!p->leg_done) return fail(p, HYB_ESTATE, "collided solve needs an MC leg of this step");
     HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
+    HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
     const double tol = p->prec == HYB_FP64 ? p->d.sn_tol : std::max(p->d.sn_tol, 2e-6);
     int it = 0;
     for (it = 1; it <= p->d.sn_max_iter; ++it) {
@@ -643,11 +644,15 @@ hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
         const double num = p->st_host->sn_norm_num, den = p->st_host->sn_norm_den;
         if (den == 0.0 || std::sqrt(num) <= tol * std::sqrt(den)) break;
     }
+    HYB_CU(p, cudaMemcpyAsync(&p->st_host->status, &p->st->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    HYB_CU(p, cudaStreamSynchronize(p->stream));
+    if (p->st_host->status & kStSegments) return fail(p, HYB_ETIMEOUT, "S_N sweep pipeline wait exhausted");
     if (it > p->d.sn_max_iter) it = p->d.sn_max_iter;
     HYB_CU(p, sn_finish(p));
     HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
     p->last_sn_iters = it;
     p->sn_done = true;
+    p->sn_warm = p->d.sn_warm_start != 0;
     if (out) {
         std::memset(out, 0, sizeof(*out));
         HYB_CU(p, cudaEventSynchronize(p->ev1));
@@ -747,9 +752,11 @@ hyb_status hyb_set_bank(hyb_problem* p, const int32_t* cell, const double* fx, c
     if (n > p->bank_cap) return fail(p, HYB_ECAPACITY, "bank larger than its capacity");
     for (int64_t i = 0; i < n; ++i) {
         if (cell[i] < 0 || cell[i] >= p->ncells) return fail(p, HYB_EINVAL, "bank cell index out of range");
-        if (!(fx[i] >= 0 && fx[i] <= p->dx && fy[i] >= 0 && fy[i] <= p->dy))
+        // FP32 banks read back in FP64 carry float rounding: allow a few float ulps
+        const double tx = p->dx * (1.0 + 1e-6), ty = p->dy * (1.0 + 1e-6);
+        if (!(fx[i] >= 0 && fx[i] <= tx && fy[i] >= 0 && fy[i] <= ty))
             return fail(p, HYB_EINVAL, "bank in-cell offset out of [0, dx] x [0, dy]");
-        if (!std::isfinite(ox[i]) || !std::isfinite(oy[i]) || ox[i] * ox[i] + oy[i] * oy[i] > 1.0 + 1e-12 || !std::isfinite(w[i]))
+        if (!std::isfinite(ox[i]) || !std::isfinite(oy[i]) || ox[i] * ox[i] + oy[i] * oy[i] > 1.0 + 1e-6 || !std::isfinite(w[i]))
             return fail(p, HYB_EINVAL, "bank direction or weight invalid");
     }
     return p->prec == HYB_FP64 ? set_bank_t<double>(p, cell, fx, fy, ox, oy, w, n)

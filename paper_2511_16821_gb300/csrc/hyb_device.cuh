@@ -68,8 +68,11 @@ template <typename T> struct Prec;
 template <> struct Prec<float> {
     using acc_t = unsigned long long;
     static constexpr int kbits = 61;
-    // u in (0,1): (2 (x >> 9) + 1) 2^-24, exact in FP32
-    static __device__ __forceinline__ float unit(uint32_t x) { return (float)(2u * (x >> 9) + 1u) * 0x1p-24f; }
+    // u in (0,1): x 2^-32 + 2^-33 with x rounded toward zero to 24 bits, so u keeps 2^-24
+    // relative precision near 0 (-log u stays accurate) and never rounds up to 1
+    static __device__ __forceinline__ float unit(uint32_t x) { return fmaf(__uint2float_rz(x), 0x1p-32f, 0x1p-33f); }
+    // 1 - u with the same relative precision: the complement ~x maps to 1 - u exactly
+    static __device__ __forceinline__ float unit_c(uint32_t x) { return unit(~x); }
     static __device__ __forceinline__ float neglog(float u) { return -logf(u); }
     static __device__ __forceinline__ float ex(float x) { return expf(x); }
     static __device__ __forceinline__ float exm1(float x) { return expm1f(x); }
@@ -125,6 +128,7 @@ template <> struct Prec<double> {
     using acc_t = Acc128;
     static constexpr int kbits = 125;
     static __device__ __forceinline__ double unit(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
+    static __device__ __forceinline__ double unit_c(uint32_t x) { return 1.0 - unit(x); }   // exact in FP64
     static __device__ __forceinline__ double neglog(double u) { return -log(u); }
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
     static __device__ __forceinline__ double exm1(double x) { return expm1(x); }
@@ -178,12 +182,13 @@ __device__ __forceinline__ void gfun(T x, T* g0, T* g1, T* g2) {
     }
 }
 
-// isotropic direction: mu = 2u - 1, phi = 2 pi u'; returns the in-plane components
+// isotropic direction from two point integers: mu = 2u - 1, phi = 2 pi u'; returns the in-plane
+// components, sin(theta) = 2 sqrt(u (1 - u)) with 1 - u formed without cancellation
 template <typename T>
-__device__ __forceinline__ void iso_dir(T u_mu, T u_phi, T* ox, T* oy) {
-    const T st = T(2) * Prec<T>::sqrt_(u_mu * (T(1) - u_mu));
+__device__ __forceinline__ void iso_dir(uint32_t x_mu, uint32_t x_phi, T* ox, T* oy) {
+    const T st = T(2) * Prec<T>::sqrt_(Prec<T>::unit(x_mu) * Prec<T>::unit_c(x_mu));
     T s, c;
-    Prec<T>::sincos2pi(u_phi, &s, &c);
+    Prec<T>::sincos2pi(Prec<T>::unit(x_phi), &s, &c);
     *ox = st * c;
     *oy = st * s;
 }

@@ -13,7 +13,6 @@ namespace hyb {
 constexpr int kTile = 256;               // threads per block of the streaming kernels
 constexpr int64_t kMaxSegments = 1 << 20;
 constexpr int kFateLeaked = 0, kFateCensus = 1, kFateKilled = 2, kFateError = 3;
-constexpr int kSnTile = 32;              // S_N-DG sweep tile (cells per side)
 constexpr int kMaxOrd = 40;              // S8 upper hemisphere
 constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
 
@@ -79,6 +78,7 @@ struct hyb_problem {
     int n_ord;                // S_N ordinates
     double quad_ox[hyb::kMaxOrd], quad_oy[hyb::kMaxOrd], quad_w[hyb::kMaxOrd];
     bool leg_done, sn_done;
+    bool sn_warm;             // start source iteration from the previous step's collided flux
     int last_sn_iters;
     std::string err;
     // device pointers (into ws)
@@ -95,7 +95,10 @@ struct hyb_problem {
     double *pre_d, *post_d, *mom_d, *flux_d;        // normalised tallies (FP64)
     double *pre_raw, *post_raw;                     // raw track-length sums (FP64)
     double sig_s_max;         // max sigma_s (bound of the hand-off moments)
-    void* sn_phi; void* sn_phi_old; void* sn_quad; void* sn_tx; void* sn_ty;  // S_N state (T)
+    void* sn_phi; void* sn_phi_old;   // collided flux, 4 Legendre coefficients per cell (T)
+    void* sn_quad;            // per-iteration source (4 per cell) and sigma* A (1 per cell) (T)
+    void* sn_psi;             // w_m psi_m per ordinate and cell (T)
+    void* sn_ty;              // strip-top y traces per ordinate (T)
     void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, precision T
     double* sn_phi_d;         // collided flux, FP64 copy (4 x ncells)
     double* sn_norm;          // per-block norm partials

@@ -92,10 +92,9 @@ __global__ void __launch_bounds__(kTile) mc_leg_kernel(LegArgs<T> a) {
             const int k = sample_cell<T>(a.cdf, nx, ny, pts(idx, 0), pts(idx, 1), &frx, &fry);
             ix = k % nx; iy = k / nx;
             fx = frx * DX; fy = fry * DY;
-            const T tf = P::unit(pts(idx, 2));
-            iso_dir<T>(P::unit(pts(idx, 3)), P::unit(pts(idx, 4)), &ox, &oy);
+            iso_dir<T>(pts(idx, 3), pts(idx, 4), &ox, &oy);
             w = a.w0;
-            srem = a.cdt * (T(1) - tf);
+            srem = a.cdt * P::unit_c(pts(idx, 2));
         }
         ++c_hist;
         const T w_start = w;
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(kTile) mc_leg_kernel(LegArgs<T> a) {
                 fy = clamp_(fy, T(0), DY);
                 ++n; ++c_col;
                 const int base = 5 + 3 * (n - 1);
-                iso_dir<T>(P::unit(pts(idx, base + 1)), P::unit(pts(idx, base + 2)), &ox, &oy);
+                iso_dir<T>(pts(idx, base + 1), pts(idx, base + 2), &ox, &oy);
                 if (n < Ns) tau = P::neglog(P::unit(pts(idx, 5 + 3 * n)));
                 else { tau = T(0); ++c_reach; }
             }
@@ -265,7 +264,7 @@ __global__ void init_bank_kernel(BankView<T> b, Cdf2DView cdf, int nx, int ny, T
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         T frx, fry, ox, oy;
         const int k = sample_cell<T>(cdf, nx, ny, pts((uint32_t)i, 0), pts((uint32_t)i, 1), &frx, &fry);
-        iso_dir<T>(Prec<T>::unit(pts((uint32_t)i, 3)), Prec<T>::unit(pts((uint32_t)i, 4)), &ox, &oy);
+        iso_dir<T>(pts((uint32_t)i, 3), pts((uint32_t)i, 4), &ox, &oy);
         b.cell[i] = k;
         b.fx[i] = frx * dx;
         b.fy[i] = fry * dy;

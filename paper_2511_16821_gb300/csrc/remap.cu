@@ -235,9 +235,8 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
         }
         fx = T(0.5) * (xi + T(1)) * a.dx;
         fy = T(0.5) * (eta + T(1)) * a.dy;
-        const T tf = P::unit(pts(i, 2));
-        iso_dir<T>(P::unit(pts(i, 3)), P::unit(pts(i, 4)), &ox, &oy);
-        srem = a.cdt * (T(1) - tf);
+        iso_dir<T>(pts(i, 3), pts(i, 4), &ox, &oy);
+        srem = a.cdt * P::unit_c(pts(i, 2));
     }
     *w_start = (double)w;
     const T w0 = w;

@@ -7,13 +7,14 @@
 // psi = a0 + a1 xi + a2 eta + a3 xi eta, upwind traces, level-symmetric quadrature; source
 // iteration on phi_c.
 //
-// Sweep: every ordinate of a quadrant shares one dependency order, so one CTA sweeps a 32x32 tile
-// for all ordinates of its quadrant (thread = (tile row, ordinate), cells along the row in
-// registers, the row-to-row trace through shared memory, one anti-diagonal per step). Tiles on
-// one tile anti-diagonal run concurrently (one launch per tile anti-diagonal, the four quadrants in
-// the same launch). Coordinates are mirrored per quadrant so that each sweep runs towards +x,+y;
-// in mirrored coordinates the 4x4 cell system is the same for every quadrant and is diagonally
-// dominant, so it is solved by elimination without pivoting.
+// Sweep: one CTA per ordinate; its warps walk 32-row strips as wavefronts (lane = row, one
+// anti-diagonal per step); the trace entering a row from below comes from the neighbouring lane by
+// shuffle (from the strip below through a shared-memory ring), the trace from the left stays in
+// registers, so a step needs no block barrier. Strips are pipelined across the warps, so the
+// critical path is about (nx + 31) + 32 (ceil(ny/32) - 1) cell solves per sweep. Coordinates are mirrored per quadrant so that every
+// sweep runs towards +x,+y; in mirrored coordinates the 4x4 cell system is the same for every
+// quadrant and is diagonally dominant, so it is solved by elimination without pivoting. The
+// per-ordinate results are summed over ordinates in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -24,153 +25,185 @@ namespace hyb {
 
 template <typename T>
 struct SweepArgs {
-    int nx, ny, ntx, nty, nq, diag;
-    T dx, dy, area, inv_cdt;
-    const T* sig;            // (sigma_a, sigma_s) per cell
-    const T* phi_old;        // 4 per cell
-    const double* mom;       // hand-off moments, 4 per cell
-    T inv_4pi_dt;
+    int nx, ny, nq, nord, W;
+    T dx, dy;
+    const T* sgA;            // (sigma_t + 1/(c dt)) A per cell
+    const T* src;            // per cell the four source integrals S_i (un-mirrored)
     const T* qox; const T* qoy; const T* qw;   // ordinates by quadrant: m = quad * nq + q
-    T* phi_quad;             // 4 quadrants x ncells x 4
-    T* tx;                   // outgoing x traces at tile columns: nord x ny x ntx x 2
-    T* ty;                   // outgoing y traces at tile rows:    nord x nx x nty x 2
+    T* psi;                  // per ordinate and cell: w_m psi (4 Legendre coefficients)
+    int* status;             // device status word (bounded waits)
 };
 
+// source integrals against P_i: sigma_s A n_i phi_i / (4 pi) + m_i / (4 pi dt)
+template <typename T>
+__device__ __forceinline__ void source4(T ss, T area, const T* po, const double* mm, T inv_4pi_dt, T* S) {
+    const T cs = ss * area * T(0.07957747154594767);   // sigma_s A / (4 pi)
+    S[0] = cs * po[0] + (T)mm[0] * inv_4pi_dt;
+    S[1] = cs * po[1] * T(1.0 / 3.0) + (T)mm[1] * inv_4pi_dt;
+    S[2] = cs * po[2] * T(1.0 / 3.0) + (T)mm[2] * inv_4pi_dt;
+    S[3] = cs * po[3] * T(1.0 / 9.0) + (T)mm[3] * inv_4pi_dt;
+}
+
+template <typename T>
+__global__ void sn_source_kernel(int ncells, const T* sig, const T* phi_old, const double* mom, T area,
+                                 T inv_4pi_dt, T inv_cdt, T* src, T* sgA) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ncells) return;
+    const T sa = sig[2 * k], ss = sig[2 * k + 1];
+    source4<T>(ss, area, phi_old + 4 * (size_t)k, mom + 4 * (size_t)k, inv_4pi_dt, src + 4 * (size_t)k);
+    sgA[k] = (sa + ss + inv_cdt) * area;
+}
+
+// Gaussian elimination without pivoting (the mirrored cell matrix is diagonally dominant)
 template <typename T>
 __device__ __forceinline__ void solve4(T m[4][4], T b[4], T x[4]) {
+    T inv[4];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
+        inv[c] = T(1) / m[c][c];
 #pragma unroll
         for (int r = c + 1; r < 4; ++r) {
-            const T f = m[r][c] / m[c][c];
+            const T f = m[r][c] * inv[c];
 #pragma unroll
             for (int k = c; k < 4; ++k) m[r][k] -= f * m[c][k];
             b[r] -= f * b[c];
         }
     }
+    inv[3] = T(1) / m[3][3];
 #pragma unroll
     for (int r = 3; r >= 0; --r) {
         T s = b[r];
 #pragma unroll
         for (int k = r + 1; k < 4; ++k) s -= m[r][k] * x[k];
-        x[r] = s / m[r][r];
+        x[r] = s * inv[r];
     }
 }
 
+// Pipelined strip sweep, one CTA per ordinate, W warps. Warp w sweeps strips w, w+W, ... (lane =
+// row, one anti-diagonal per step). The trace leaving the top row of strip s goes through a
+// shared-memory ring slot (s mod W) to the first row of strip s+1, guarded by produced/consumed
+// counters; every wait is bounded and records kStSegments on exhaustion. Dependencies only point
+// to lower strips, and all warps of the CTA are resident, so the pipeline always advances.
 template <typename T>
-__global__ void sweep_tile_kernel(SweepArgs<T> a) {
+__global__ void sweep_pipe_kernel(SweepArgs<T> a) {
     extern __shared__ unsigned char smraw[];
-    T* ytr = (T*)smraw;                       // [nq][32][2]: y trace entering row r+1
-    T* acc = ytr + a.nq * kSnTile * 2;        // [nq][32][4]: weighted psi of the step
-    const int quad = blockIdx.y;
+    const int W = a.W;
+    volatile int* prod = (volatile int*)smraw;
+    volatile int* cons = prod + W;
+    T* ring = (T*)(smraw + ((2 * W * sizeof(int) + 15) / 16) * 16);   // W x nx x 2
+    const int m = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x < W) { prod[threadIdx.x] = 0; cons[threadIdx.x] = 0; }
+    __syncthreads();
+    const int quad = m / a.nq;
     const int sx = (quad == 0 || quad == 3) ? 1 : -1;
     const int sy = (quad <= 1) ? 1 : -1;
-    const int tlx = max(0, a.diag - (a.nty - 1)) + blockIdx.x;
-    const int tly = a.diag - tlx;
-    if (tlx >= a.ntx || tly < 0 || tly >= a.nty) return;
-    const int q = threadIdx.x / kSnTile, r = threadIdx.x % kSnTile;
-    const int m = quad * a.nq + q;
-    const T ox = a.qox[m], oy = a.qoy[m], wq = a.qw[m];
-    const T X = fabs(ox) * a.dy * T(0.5), Y = fabs(oy) * a.dx * T(0.5);
-    const int lx0 = tlx * kSnTile, ly0 = tly * kSnTile;
-    const int ncx = min(kSnTile, a.nx - lx0), ncy = min(kSnTile, a.ny - ly0);
-    const int ly = ly0 + r;
-    const bool row_ok = r < ncy;
-    const int iy = sy > 0 ? ly : a.ny - 1 - ly;
-    // incoming x trace of this row (from the tile to the left, or vacuum)
-    T bx0 = 0, bx1 = 0;
-    if (row_ok && tlx > 0) {
-        const T* s = a.tx + (((size_t)m * a.ny + ly) * a.ntx + (tlx - 1)) * 2;
-        bx0 = s[0]; bx1 = s[1];
-    }
-    // incoming y traces of the tile's bottom row (from the tile below, or vacuum)
-    for (int c = r; c < kSnTile; c += kSnTile) {
-        T v0 = 0, v1 = 0;
-        if (c < ncx && tly > 0) {
-            const T* s = a.ty + (((size_t)m * a.nx + (lx0 + c)) * a.nty + (tly - 1)) * 2;
-            v0 = s[0]; v1 = s[1];
-        }
-        ytr[(q * kSnTile + c) * 2] = v0;
-        ytr[(q * kSnTile + c) * 2 + 1] = v1;
-    }
-    __syncthreads();
     const T sxf = (T)sx, syf = (T)sy, sxy = (T)(sx * sy);
-    for (int step = 0; step < ncx + ncy - 1; ++step) {
-        const int c = step - r;
-        const bool act = row_ok && c >= 0 && c < ncx;
-        T psi[4] = {0, 0, 0, 0};
-        if (act) {
-            const int lx = lx0 + c;
-            const int ix = sx > 0 ? lx : a.nx - 1 - lx;
-            const int k = iy * a.nx + ix;
-            const T sa = a.sig[2 * k], ss = a.sig[2 * k + 1];
-            const T sg = sa + ss + a.inv_cdt;
-            const T sA = sg * a.area;
-            const T* po = a.phi_old + 4 * (size_t)k;
-            const double* mm = a.mom + 4 * (size_t)k;
-            const T cs = ss * a.area * T(0.07957747154594767);   // sigma_s A / (4 pi)
-            const T S0 = cs * po[0] + (T)mm[0] * a.inv_4pi_dt;
-            const T S1 = cs * po[1] * T(1.0 / 3.0) + (T)mm[1] * a.inv_4pi_dt;
-            const T S2 = cs * po[2] * T(1.0 / 3.0) + (T)mm[2] * a.inv_4pi_dt;
-            const T S3 = cs * po[3] * T(1.0 / 9.0) + (T)mm[3] * a.inv_4pi_dt;
-            const T by0 = ytr[(q * kSnTile + c) * 2], by1 = ytr[(q * kSnTile + c) * 2 + 1];
-            T M[4][4] = {{sA + T(2) * X + T(2) * Y, T(2) * X, T(2) * Y, T(0)},
-                         {T(-2) * X, sA / T(3) + T(2) * X + T(2.0 / 3.0) * Y, T(0), T(2.0 / 3.0) * Y},
-                         {T(-2) * Y, T(0), sA / T(3) + T(2.0 / 3.0) * X + T(2) * Y, T(2.0 / 3.0) * X},
-                         {T(0), T(-2.0 / 3.0) * Y, T(-2.0 / 3.0) * X, sA / T(9) + T(2.0 / 3.0) * (X + Y)}};
-            T b[4] = {S0 + T(2) * X * bx0 + T(2) * Y * by0,
-                      sxf * S1 - T(2) * X * bx0 + T(2.0 / 3.0) * Y * by1,
-                      syf * S2 + T(2.0 / 3.0) * X * bx1 - T(2) * Y * by0,
-                      sxy * S3 - T(2.0 / 3.0) * X * bx1 - T(2.0 / 3.0) * Y * by1};
-            T ap[4];
-            solve4<T>(M, b, ap);
-            // outgoing traces in mirrored coordinates
-            bx0 = ap[0] + ap[1]; bx1 = ap[2] + ap[3];
-            ytr[(q * kSnTile + c) * 2] = ap[0] + ap[2];
-            ytr[(q * kSnTile + c) * 2 + 1] = ap[1] + ap[3];
-            psi[0] = wq * ap[0]; psi[1] = wq * sxf * ap[1]; psi[2] = wq * syf * ap[2]; psi[3] = wq * sxy * ap[3];
-            if (c == ncx - 1) {
-                T* d = a.tx + (((size_t)m * a.ny + ly) * a.ntx + tlx) * 2;
-                d[0] = bx0; d[1] = bx1;
+    const T wq = a.qw[m];
+    const T X = fabs(a.qox[m]) * a.dy * T(0.5), Y = fabs(a.qoy[m]) * a.dx * T(0.5);
+    const T twoX = T(2) * X, twoY = T(2) * Y, tX = T(2.0 / 3.0) * X, tY = T(2.0 / 3.0) * Y;
+    T* out = a.psi + (size_t)m * a.nx * a.ny * 4;
+    const int nx = a.nx, ny = a.ny;
+    const int nstrip = (ny + 31) / 32;
+    bool timed_out = false;
+    for (int s = warp; s < nstrip; s += W) {
+        const int ly = 32 * s + lane;
+        const bool row_ok = ly < ny;
+        const int iy = sy > 0 ? ly : ny - 1 - ly;
+        const int bin = (s - 1 + W) % W, bout = s % W;
+        const int qin = ((s - 1) / W) * nx, qout = (s / W) * nx;   // sequence bases of the ring slots
+        const bool has_in = s > 0, has_out = s + 1 < nstrip;
+        volatile T* rin = ring + (size_t)bin * nx * 2;
+        volatile T* rout = ring + (size_t)bout * nx * 2;
+        T bx0 = 0, bx1 = 0, oy0 = 0, oy1 = 0;
+        int c = -lane;
+        T nS[4] = {0, 0, 0, 0}, nsg = 1;
+        auto load = [&](int col) {
+            if (row_ok && col >= 0 && col < nx) {
+                const int ix = sx > 0 ? col : nx - 1 - col;
+                const size_t k = (size_t)iy * nx + ix;
+                const T* sp = a.src + 4 * k;
+                nS[0] = sp[0]; nS[1] = sp[1]; nS[2] = sp[2]; nS[3] = sp[3];
+                nsg = a.sgA[k];
             }
-            if (r == ncy - 1) {
-                T* d = a.ty + (((size_t)m * a.nx + (lx0 + c)) * a.nty + tly) * 2;
-                d[0] = ap[0] + ap[2]; d[1] = ap[1] + ap[3];
+        };
+        load(c);
+        for (int t = 0; t < nx + 31; ++t, ++c) {
+            const T S0 = nS[0], S1 = nS[1], S2 = nS[2], S3 = nS[3], sA = nsg;
+            load(c + 1);
+            const bool act = row_ok && c >= 0 && c < nx;
+            // lane 0 needs the trace of column c from strip s-1; the top lane must not overwrite
+            // ring slot column c before strip s+1-W's consumer has read it
+            const bool wait_in = has_in && lane == 0 && act;
+            const bool wait_out = has_out && lane == 31 && act;
+            int spins = 0;
+            while (__any_sync(0xffffffffu, (wait_in && prod[bin] < qin + c + 1) ||
+                                               (wait_out && cons[bout] < qout + c + 1 - nx))) {
+                if (++spins > (1 << 22)) { timed_out = true; break; }
+                __nanosleep(32);
             }
+            const T u0 = __shfl_up_sync(0xffffffffu, oy0, 1);
+            const T u1 = __shfl_up_sync(0xffffffffu, oy1, 1);
+            if (act) {
+                T by0, by1;
+                if (lane == 0) {
+                    if (has_in) {
+                        by0 = rin[2 * c]; by1 = rin[2 * c + 1];
+                        __threadfence_block();
+                        cons[bin] = qin + c + 1;
+                    } else { by0 = 0; by1 = 0; }
+                } else { by0 = u0; by1 = u1; }
+                if (c == 0) { bx0 = 0; bx1 = 0; }
+                T M[4][4] = {{sA + twoX + twoY, twoX, twoY, T(0)},
+                             {-twoX, sA * T(1.0 / 3.0) + twoX + tY, T(0), tY},
+                             {-twoY, T(0), sA * T(1.0 / 3.0) + tX + twoY, tX},
+                             {T(0), -tY, -tX, sA * T(1.0 / 9.0) + tX + tY}};
+                T b[4] = {S0 + twoX * bx0 + twoY * by0,
+                          sxf * S1 - twoX * bx0 + tY * by1,
+                          syf * S2 + tX * bx1 - twoY * by0,
+                          sxy * S3 - tX * bx1 - tY * by1};
+                T ap[4];
+                solve4<T>(M, b, ap);
+                bx0 = ap[0] + ap[1]; bx1 = ap[2] + ap[3];
+                oy0 = ap[0] + ap[2]; oy1 = ap[1] + ap[3];
+                const int ix = sx > 0 ? c : nx - 1 - c;
+                T* d = out + ((size_t)iy * nx + ix) * 4;
+                d[0] = wq * ap[0]; d[1] = wq * sxf * ap[1]; d[2] = wq * syf * ap[2]; d[3] = wq * sxy * ap[3];
+                if (lane == 31 && has_out) {
+                    rout[2 * c] = oy0; rout[2 * c + 1] = oy1;
+                    __threadfence_block();
+                    prod[bout] = qout + c + 1;
+                }
+            }
+            __syncwarp();
+            if (timed_out) break;
         }
-        T* ac = acc + (q * kSnTile + r) * 4;
-        ac[0] = psi[0]; ac[1] = psi[1]; ac[2] = psi[2]; ac[3] = psi[3];
-        __syncthreads();
-        if (q == 0 && act) {
-            T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-            for (int qq = 0; qq < a.nq; ++qq) {
-                const T* v = acc + (qq * kSnTile + r) * 4;
-                s0 += v[0]; s1 += v[1]; s2 += v[2]; s3 += v[3];
-            }
-            const int lx = lx0 + c;
-            const int ix = sx > 0 ? lx : a.nx - 1 - lx;
-            T* d = a.phi_quad + ((size_t)quad * a.nx * a.ny + (size_t)iy * a.nx + ix) * 4;
-            d[0] = s0; d[1] = s1; d[2] = s2; d[3] = s3;
-        }
-        __syncthreads();
+        if (timed_out) break;
     }
+    if (timed_out && lane == 0) atomicOr(a.status, kStSegments);
 }
 
-// phi_new = sum of the quadrant partials; norm partials of the change (block order)
+// phi_new = sum over ordinates of w_m psi_m (fixed order); norm partials of the change; the next
+// iteration's source integrals from phi_new
 template <typename T>
-__global__ void sn_reduce_kernel(const T* phi_quad, const T* phi_old, T* phi_new, int ncells, double* part) {
+__global__ void sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, double* part,
+                                 const T* sig, const double* mom, T area, T inv_4pi_dt, T* src) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double num = 0, den = 0;
     if (k < ncells) {
         const double nrm[4] = {1.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0};
-        for (int i = 0; i < 4; ++i) {
-            T s = 0;
-            for (int qd = 0; qd < 4; ++qd) s += phi_quad[((size_t)qd * ncells + k) * 4 + i];
-            phi_new[4 * (size_t)k + i] = s;
-            const double d = (double)s - (double)phi_old[4 * (size_t)k + i];
-            num += nrm[i] * d * d;
-            den += nrm[i] * (double)s * (double)s;
+        T s[4] = {0, 0, 0, 0};
+        for (int m = 0; m < nord; ++m) {
+            const T* v = psi + ((size_t)m * ncells + k) * 4;
+            s[0] += v[0]; s[1] += v[1]; s[2] += v[2]; s[3] += v[3];
         }
+        for (int i = 0; i < 4; ++i) {
+            phi_new[4 * (size_t)k + i] = s[i];
+            const double d = (double)s[i] - (double)phi_old[4 * (size_t)k + i];
+            num += nrm[i] * d * d;
+            den += nrm[i] * (double)s[i] * (double)s[i];
+        }
+        source4<T>(sig[2 * k + 1], area, s, mom + 4 * (size_t)k, inv_4pi_dt, src + 4 * (size_t)k);
     }
     num = warp_sum(num);
     den = warp_sum(den);
@@ -201,47 +234,57 @@ __global__ void sn_to_double_kernel(const T* phi, double* out, int n) {
 }
 
 template <typename T>
-static cudaError_t sn_iteration_t(hyb_problem* p) {
+static int sweep_warps(const hyb_problem* p, size_t* smem) {
+    const int nstrip = (p->ny + 31) / 32;
+    const size_t per = (size_t)p->nx * 2 * sizeof(T);
+    int W = nstrip < 16 ? nstrip : 16;
+    while (W > 1 && (size_t)W * per + 256 > 160 * 1024) --W;
+    *smem = ((2 * W * sizeof(int) + 15) / 16) * 16 + (size_t)W * per;
+    return W;
+}
+
+template <typename T>
+static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     cudaStream_t s = p->stream;
-    const int nq = p->n_ord / 4;
+    const int g = (p->ncells + 255) / 256;
+    T* src = (T*)p->sn_quad;                      // 4 per cell
+    T* sgA = src + 4 * (size_t)p->ncells;         // 1 per cell
+    const T inv4pidt = (T)(1.0 / (4.0 * 3.14159265358979323846 * p->d.dt));
+    if (first)
+        sn_source_kernel<T><<<g, 256, 0, s>>>(p->ncells, (const T*)p->sig, (const T*)p->sn_phi_old, p->mom_d,
+                                              (T)p->area, inv4pidt, (T)(1.0 / (p->d.c * p->d.dt)), src, sgA);
     SweepArgs<T> a;
     a.nx = p->nx; a.ny = p->ny;
-    a.ntx = (p->nx + kSnTile - 1) / kSnTile;
-    a.nty = (p->ny + kSnTile - 1) / kSnTile;
-    a.nq = nq;
-    a.dx = (T)p->dx; a.dy = (T)p->dy; a.area = (T)p->area;
-    a.inv_cdt = (T)(1.0 / (p->d.c * p->d.dt));
-    a.sig = (const T*)p->sig;
-    a.phi_old = (const T*)p->sn_phi_old;
-    a.mom = p->mom_d;
-    a.inv_4pi_dt = (T)(1.0 / (4.0 * 3.14159265358979323846 * p->d.dt));
+    a.nq = p->n_ord / 4;
+    a.nord = p->n_ord;
+    a.dx = (T)p->dx; a.dy = (T)p->dy;
+    a.sgA = sgA;
+    a.src = src;
     T* qbuf = (T*)p->sn_quadbuf;
     a.qox = qbuf; a.qoy = qbuf + kMaxOrd; a.qw = qbuf + 2 * kMaxOrd;
-    a.phi_quad = (T*)p->sn_quad;
-    a.tx = (T*)p->sn_tx;
-    a.ty = (T*)p->sn_ty;
-    const size_t smem = (size_t)nq * kSnTile * (2 + 4) * sizeof(T);
-    for (int d = 0; d < a.ntx + a.nty - 1; ++d) {
-        a.diag = d;
-        const int lo = d - (a.nty - 1) > 0 ? d - (a.nty - 1) : 0;
-        const int hi = d < a.ntx - 1 ? d : a.ntx - 1;
-        dim3 grid(hi - lo + 1, 4);
-        sweep_tile_kernel<T><<<grid, nq * kSnTile, smem, s>>>(a);
+    a.psi = (T*)p->sn_psi;
+    a.status = &p->st->status;
+    size_t smem = 0;
+    a.W = sweep_warps<T>(p, &smem);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_pipe_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
-    const int g = (p->ncells + 255) / 256;
-    sn_reduce_kernel<T><<<g, 256, 0, s>>>((const T*)p->sn_quad, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells,
-                                          p->sn_norm);
+    sweep_pipe_kernel<T><<<p->n_ord, 32 * a.W, smem, s>>>(a);
+    sn_reduce_kernel<T><<<g, 256, 0, s>>>((const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old, (T*)p->sn_phi,
+                                          p->ncells, p->sn_norm, (const T*)p->sig, p->mom_d, (T)p->area, inv4pidt,
+                                          src);
     sn_norm_final_kernel<<<1, 32, 0, s>>>(p->sn_norm, g, p->st);
     return cudaGetLastError();
 }
 
 cudaError_t sn_iteration(hyb_problem* p, int first) {
-    if (first) {
+    if (first && !p->sn_warm) {
         const size_t bytes = (size_t)4 * p->ncells * (p->prec == HYB_FP64 ? 8 : 4);
         cudaError_t e = cudaMemsetAsync(p->sn_phi_old, 0, bytes, p->stream);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t e = p->prec == HYB_FP64 ? sn_iteration_t<double>(p) : sn_iteration_t<float>(p);
+    cudaError_t e = p->prec == HYB_FP64 ? sn_iteration_t<double>(p, first) : sn_iteration_t<float>(p, first);
     if (e != cudaSuccess) return e;
     void* t = p->sn_phi; p->sn_phi = p->sn_phi_old; p->sn_phi_old = t;   // newest is now sn_phi_old
     return cudaSuccess;

@@ -36,7 +36,8 @@ class Desc(C.Structure):
                 ("c", C.c_double), ("dt", C.c_double), ("n_s", C.c_int32), ("sampler", C.c_int32),
                 ("n_hist", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int32),
                 ("sn_order", C.c_int32), ("handoff_full", C.c_int32), ("sn_max_iter", C.c_int32),
-                ("sn_tol", C.c_double), ("w_min", C.c_double), ("census_cap", C.c_int64)]
+                ("sn_tol", C.c_double), ("w_min", C.c_double), ("census_cap", C.c_int64),
+                ("sn_warm_start", C.c_int32), ("pad0", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -123,7 +124,7 @@ def make_desc(spec: ProblemSpec) -> tuple[Desc, list]:
              n_s=spec.n_s, sampler=spec.sampler, n_hist=spec.n_hist, seed=spec.seed,
              precision=spec.precision, sn_order=spec.sn_order, handoff_full=spec.handoff_full,
              sn_max_iter=spec.sn_max_iter, sn_tol=spec.sn_tol, w_min=spec.w_min,
-             census_cap=spec.census_cap)
+             census_cap=spec.census_cap, sn_warm_start=spec.sn_warm_start, pad0=0)
     return d, keep
 
 

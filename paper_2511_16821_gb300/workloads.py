@@ -50,6 +50,7 @@ class ProblemSpec:
     census_cap: int = 0
     sn_tol: float = 1e-10
     sn_max_iter: int = 500
+    sn_warm_start: int = 0
     name: str = field(default="problem")
 
     @property
