@@ -183,6 +183,18 @@ HYB_API hyb_status hyb_get_step(const hyb_problem* p, int64_t* step);
 HYB_API hyb_status hyb_points(uint64_t seed, int64_t step, int32_t stream_id, int32_t sampler, int64_t i0,
                       int64_t n, int32_t ndims, uint32_t* out_dev, void* cuda_stream);
 
+/* Integer 2-D CDF over cells (the sampling map of Sec. 2.3 births and of the Eq. (R) remap):
+ * q_k = rint(|w_k| / max|w| 2^40); col_pre: per row the exclusive prefix of q over the row's cells
+ * (ny x (nx+1), last entry = row total); row_pre: exclusive prefix of the row totals (ny+1).
+ * w_dev: nx*ny FP64 cell weights (device, sign ignored). W_qmax_dev: two device doubles written
+ * with sum|w| and max|w|. scratch_dev: caller-owned device scratch of >= hyb_cdf_scratch_bytes
+ * bytes (block partial sums and row totals). Asynchronous on cuda_stream. EINVAL: nx, ny outside
+ * [1, 4096] or a null pointer; ENOMEM: scratch too small. */
+HYB_API hyb_status hyb_cdf_scratch_bytes(int32_t nx, int32_t ny, size_t* bytes);
+HYB_API hyb_status hyb_build_cdf(const double* w_dev, int32_t nx, int32_t ny, int64_t* q_dev, int64_t* row_pre_dev,
+                                 int64_t* col_pre_dev, double* W_qmax_dev, void* scratch_dev, size_t scratch_bytes,
+                                 void* cuda_stream);
+
 /* The generated Sobol direction numbers, host out[d*32 + b], d < ndims <= HYB_SOBOL_DIMS. */
 HYB_API hyb_status hyb_sobol_table(int32_t ndims, uint32_t* out_host);
 

@@ -260,3 +260,15 @@ def step(spec, step_index: int, bank: dict | None):
     assert rc == 0, rc
     return dict(bank=_trim(out, co.n), flux=flux, pre=pre, post=post, mom=mom.reshape(nc, 4),
                 phi=phi.reshape(nc, 4), leg=_stats_dict(ls), remap=_stats_dict(rs))
+
+
+def build_cdf(nx: int, ny: int, w: np.ndarray):
+    """The integer 2-D CDF (q, row_pre, col_pre) of the cell weights w (sign ignored)."""
+    w = np.ascontiguousarray(w, dtype=np.float64).ravel()
+    q = np.zeros(nx * ny, np.int64)
+    rp = np.zeros(ny + 1, np.int64)
+    cp = np.zeros(ny * (nx + 1), np.int64)
+    P = C.POINTER(C.c_int64)
+    lib().or_build_cdf(C.c_int32(nx), C.c_int32(ny), _dp(w), q.ctypes.data_as(P), rp.ctypes.data_as(P),
+                       cp.ctypes.data_as(P))
+    return q, rp, cp

@@ -812,6 +812,18 @@ int or_points(uint64_t seed, int64_t step, int32_t stream, int32_t sampler, int6
     return 0;
 }
 
+// The integer CDF of Sec. 2.3 births / Eq. (R) remap births (exposed for the CDF parity test).
+int or_build_cdf(int32_t nx, int32_t ny, const double* w, int64_t* q, int64_t* row_pre, int64_t* col_pre) {
+    or_problem P{}; P.nx = nx; P.ny = ny; P.lx = 1.0; P.ly = 1.0;
+    Mesh M(&P);
+    std::vector<double> wv(w, w + (size_t)nx * ny);
+    Cdf2D C = build_cdf(M, wv);
+    std::copy(C.q.begin(), C.q.end(), q);
+    std::copy(C.row_pre.begin(), C.row_pre.end(), row_pre);
+    std::copy(C.col_pre.begin(), C.col_pre.end(), col_pre);
+    return 0;
+}
+
 int or_quadrature(int order, double* ox, double* oy, double* oz, double* w) {
     Quad Q;
     if (!build_quadrature(order, &Q)) return -1;

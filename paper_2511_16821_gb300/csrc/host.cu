@@ -782,6 +782,28 @@ hyb_status hyb_get_step(const hyb_problem* p, int64_t* step) {
     return HYB_OK;
 }
 
+hyb_status hyb_cdf_scratch_bytes(int32_t nx, int32_t ny, size_t* bytes) {
+    if (nx < 1 || ny < 1 || nx > 4096 || ny > 4096 || !bytes) return fail(nullptr, HYB_EINVAL, "nx, ny must be in [1, 4096]");
+    *bytes = (size_t)(kCdfParts + ny) * 8;
+    return HYB_OK;
+}
+
+hyb_status hyb_build_cdf(const double* w_dev, int32_t nx, int32_t ny, int64_t* q_dev, int64_t* row_pre_dev,
+                         int64_t* col_pre_dev, double* W_qmax_dev, void* scratch_dev, size_t scratch_bytes,
+                         void* cuda_stream) {
+    size_t need = 0;
+    hyb_status s = hyb_cdf_scratch_bytes(nx, ny, &need);
+    if (s != HYB_OK) return s;
+    if (!w_dev || !q_dev || !row_pre_dev || !col_pre_dev || !W_qmax_dev || !scratch_dev)
+        return fail(nullptr, HYB_EINVAL, "null device pointer");
+    if (scratch_bytes < need) return fail(nullptr, HYB_ENOMEM, "scratch smaller than hyb_cdf_scratch_bytes");
+    Cdf2DView cdf{(long long*)q_dev, (long long*)row_pre_dev, (long long*)col_pre_dev};
+    cudaError_t e = launch_cdf_build_raw(w_dev, nx, ny, cdf, W_qmax_dev, W_qmax_dev + 1, (double*)scratch_dev,
+                                         (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) return fail(nullptr, HYB_ECUDA, cudaGetErrorString(e));
+    return HYB_OK;
+}
+
 hyb_status hyb_points(uint64_t seed, int64_t step, int32_t stream_id, int32_t sampler, int64_t i0, int64_t n,
                       int32_t ndims, uint32_t* out_dev, void* cuda_stream) {
     if (i0 < 0 || n < 0 || i0 + n > ((int64_t)1 << 32) || ndims < 1 || ndims > 1024 || !out_dev ||

@@ -14,6 +14,7 @@ constexpr int kTile = 256;               // threads per block of the streaming k
 constexpr int64_t kMaxSegments = 1 << 20;
 constexpr int kFateLeaked = 0, kFateCensus = 1, kFateKilled = 2, kFateError = 3;
 constexpr int kMaxOrd = 40;              // S8 upper hemisphere
+constexpr int kCdfParts = 256;           // block partial sums of the CDF build
 constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
 
 // status bits written by kernels (device status word)
@@ -118,6 +119,8 @@ cudaError_t launch_remap(hyb_problem* p);
 cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView cdf, double* W_out_dev,
                              double* qmax_out_dev);
 cudaError_t launch_flux(hyb_problem* p);
+cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
+                                 double* qmax_out, double* scratch, cudaStream_t stream);
 cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0);
 cudaError_t launch_bank_stats(hyb_problem* p);
 cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,

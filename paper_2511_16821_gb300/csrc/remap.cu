@@ -115,17 +115,22 @@ __global__ void cdf_rowpre_kernel(const long long* row_tot, int ny, long long* r
     }
 }
 
-cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w, Cdf2DView cdf, double* W_out, double* qmax_out) {
-    const int nparts = 256;
-    cudaError_t e = cudaMemsetAsync(qmax_out, 0, sizeof(double), p->stream);
+// scratch: kCdfParts doubles of block partial sums, then ny int64 row totals
+cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
+                                 double* qmax_out, double* scratch, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(qmax_out, 0, sizeof(double), stream);
     if (e != cudaSuccess) return e;
-    double* part = p->cell_scratch;                     // nparts doubles
-    long long* row_tot = (long long*)(p->cell_scratch + nparts);  // ny
-    cdf_reduce_kernel<<<nparts, 256, 0, p->stream>>>(cell_w, p->ncells, part, qmax_out);
-    cdf_total_kernel<<<1, 32, 0, p->stream>>>(part, nparts, W_out);
-    cdf_rows_kernel<<<p->ny, 256, 0, p->stream>>>(cell_w, qmax_out, p->nx, cdf, row_tot);
-    cdf_rowpre_kernel<<<1, 32, 0, p->stream>>>(row_tot, p->ny, cdf.row_pre);
+    double* part = scratch;
+    long long* row_tot = (long long*)(scratch + kCdfParts);
+    cdf_reduce_kernel<<<kCdfParts, 256, 0, stream>>>(cell_w, nx * ny, part, qmax_out);
+    cdf_total_kernel<<<1, 32, 0, stream>>>(part, kCdfParts, W_out);
+    cdf_rows_kernel<<<ny, 256, 0, stream>>>(cell_w, qmax_out, nx, cdf, row_tot);
+    cdf_rowpre_kernel<<<1, 32, 0, stream>>>(row_tot, ny, cdf.row_pre);
     return cudaGetLastError();
+}
+
+cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w, Cdf2DView cdf, double* W_out, double* qmax_out) {
+    return launch_cdf_build_raw(cell_w, p->nx, p->ny, cdf, W_out, qmax_out, p->cell_scratch, p->stream);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -87,6 +87,8 @@ def lib():
         L.hyb_points.argtypes = [C.c_uint64, C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
                                  C.c_int32, P, P]
         L.hyb_sobol_table.argtypes = [C.c_int32, P]
+        L.hyb_cdf_scratch_bytes.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
+        L.hyb_build_cdf.argtypes = [P, C.c_int32, C.c_int32, P, P, P, P, P, C.c_size_t, P]
         L.hyb_quadrature.argtypes = [C.c_int32, P, P, P, C.POINTER(C.c_int32)]
         _lib = L
     return _lib
@@ -269,3 +271,21 @@ def points(seed: int, step: int, stream_id: int, sampler: int, i0: int, n: int, 
     _check(lib().hyb_points(C.c_uint64(seed), step, stream_id, sampler, i0, n, ndims,
                             C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream)))
     return out
+
+
+def build_cdf(w, nx: int, ny: int, stream=None):
+    """Integer 2-D CDF of the device cell weights w (torch float64, nx*ny) with a torch-owned
+    scratch block; returns (q, row_pre, col_pre, W_qmax) device tensors."""
+    torch = _torch_cuda()
+    nbytes = C.c_size_t(0)
+    _check(lib().hyb_cdf_scratch_bytes(nx, ny, C.byref(nbytes)))
+    scratch = torch.empty(int(nbytes.value), dtype=torch.uint8, device="cuda")
+    q = torch.empty(nx * ny, dtype=torch.int64, device="cuda")
+    rp = torch.empty(ny + 1, dtype=torch.int64, device="cuda")
+    cp = torch.empty(ny * (nx + 1), dtype=torch.int64, device="cuda")
+    wq = torch.empty(2, dtype=torch.float64, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().hyb_build_cdf(C.c_void_p(w.data_ptr()), nx, ny, C.c_void_p(q.data_ptr()),
+                               C.c_void_p(rp.data_ptr()), C.c_void_p(cp.data_ptr()), C.c_void_p(wq.data_ptr()),
+                               C.c_void_p(scratch.data_ptr()), scratch.numel(), C.c_void_p(s.cuda_stream)))
+    return q, rp, cp, wq

@@ -99,6 +99,24 @@ def test_points_bitexact(H, orc, sampler, i0, n, nd):
 
 
 # ------------------------------------------------------------------------------------------------
+# integer 2-D CDF (birth and remap sampling map)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nx,ny", [(1, 1), (37, 5), (112, 112), (300, 2)])
+def test_cdf_bitexact(H, orc, nx, ny):
+    import torch
+    rng = np.random.default_rng(nx * 1000 + ny)
+    w = rng.uniform(-1, 1, nx * ny) ** 3
+    w[rng.integers(0, nx * ny, max(1, nx * ny // 7))] = 0.0
+    q, rp, cp, wq = H.build_cdf(torch.tensor(w, device="cuda"), nx, ny)
+    oq, orp, ocp = orc.build_cdf(nx, ny, w)
+    assert np.array_equal(q.cpu().numpy(), oq)
+    assert np.array_equal(rp.cpu().numpy(), orp)
+    assert np.array_equal(cp.cpu().numpy(), ocp)
+    assert wq[1].item() == np.max(np.abs(w))
+    assert math.isclose(wq[0].item(), float(np.sum(np.abs(w))), rel_tol=1e-13)
+
+
+# ------------------------------------------------------------------------------------------------
 # MC leg, FP64
 # ------------------------------------------------------------------------------------------------
 def leg_cases():
