@@ -195,6 +195,20 @@ HYB_API hyb_status hyb_build_cdf(const double* w_dev, int32_t nx, int32_t ny, in
                                  int64_t* col_pre_dev, double* W_qmax_dev, void* scratch_dev, size_t scratch_bytes,
                                  void* cuda_stream);
 
+/* The same CDF build without any device allocation, for callers that cannot call cudaMalloc or
+ * hand out scratch memory: code that runs while a stream is being captured into a CUDA graph,
+ * serving loops that must not allocate on their hot path, and hosts whose device memory is owned
+ * by another allocator with a fixed budget. (This entry point has no counterpart in the paper.)
+ * Its scratch is one fixed __device__ array of 34,816 bytes, resident on every GPU that loads the
+ * library until the process exits; ny is limited to 4096 rows (EINVAL beyond, like nx). The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture. All calls share the array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller. Outputs as hyb_build_cdf;
+ * asynchronous on cuda_stream; allocates nothing. */
+HYB_API hyb_status hyb_build_cdf_noalloc(const double* w_dev, int32_t nx, int32_t ny, int64_t* q_dev,
+                                         int64_t* row_pre_dev, int64_t* col_pre_dev, double* W_qmax_dev,
+                                         void* cuda_stream);
+
 /* The generated Sobol direction numbers, host out[d*32 + b], d < ndims <= HYB_SOBOL_DIMS. */
 HYB_API hyb_status hyb_sobol_table(int32_t ndims, uint32_t* out_host);
 
