@@ -188,10 +188,14 @@ def mc_leg(spec, step: int, bank: dict | None, want_hist: bool = False, want_cen
     hist = np.zeros((max(nh, 1), 4), np.int32) if want_hist else None
     cens = empty_bank(max(nh, 1)) if want_census else None
     cc = _bank(cens)
-    rc = lib().or_mc_leg(C.byref(p), C.c_int64(step), C.byref(cb) if cb else None, _dp(pre), _dp(post),
-                         _dp(mom), C.byref(st), _ip(hist) if hist is not None else None,
-                         C.byref(cc) if cc else None)
-    out = dict(pre=pre, post=post, mom=mom.reshape(nc, 4), stats=_stats_dict(st), rc=rc)
+    pre_n, post_n = np.zeros(nc, np.int64), np.zeros(nc, np.int64)
+    P64 = C.POINTER(C.c_int64)
+    rc = lib().or_mc_leg_counts(C.byref(p), C.c_int64(step), C.byref(cb) if cb else None, _dp(pre), _dp(post),
+                                _dp(mom), C.byref(st), _ip(hist) if hist is not None else None,
+                                C.byref(cc) if cc else None, pre_n.ctypes.data_as(P64),
+                                post_n.ctypes.data_as(P64))
+    out = dict(pre=pre, post=post, mom=mom.reshape(nc, 4), stats=_stats_dict(st), rc=rc,
+               pre_n=pre_n, post_n=post_n)
     if want_hist:
         out["hist"] = hist[:nh]
     if want_census:
@@ -272,3 +276,17 @@ def build_cdf(nx: int, ny: int, w: np.ndarray):
     lib().or_build_cdf(C.c_int32(nx), C.c_int32(ny), _dp(w), q.ctypes.data_as(P), rp.ctypes.data_as(P),
                        cp.ctypes.data_as(P))
     return q, rp, cp
+
+
+def sincos_2pi(u: np.ndarray):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    s, c = np.zeros_like(u), np.zeros_like(u)
+    lib().or_sincos_2pi(_dp(u), C.c_int64(u.size), _dp(s), _dp(c))
+    return s, c
+
+
+def neg_log(u: np.ndarray):
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.zeros_like(u)
+    lib().or_neg_log(_dp(u), C.c_int64(u.size), _dp(out))
+    return out

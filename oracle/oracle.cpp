@@ -320,13 +320,65 @@ int sample_cell(const Cdf2D& C, uint32_t x0, uint32_t x1, double* frac_x, double
     return iy * C.nx + ix;
 }
 
+// sin and cos of 2 pi u for a point uniform u, and -log u, evaluated by explicit series with
+// IEEE operations in a fixed order (so that any implementation written to the same recipe gives
+// the same bits):
+//   2 pi u = 2 pi r + q pi/2 with q = rint(4u), r = u - q/4 in [-1/8, 1/8] (both exact), Taylor
+//   series of sin and cos of a = 2 pi r to a^17 / a^18, then the quadrant rotation;
+//   u = m 2^e with m in [1/sqrt2, sqrt2), log m = 2 atanh(s), s = (m-1)/(m+1), series to s^23.
+struct SeriesCoef {
+    double sinc[9], cosc[10], logc[12];
+    SeriesCoef() {
+        double f = 1.0;  // n!, exact in FP64 up to 18!
+        for (int n = 1; n <= 18; ++n) {
+            f *= n;
+            if (n % 2 == 1) sinc[(n - 1) / 2] = (((n - 1) / 2) % 2 ? -1.0 : 1.0) / f;
+            else cosc[n / 2] = ((n / 2) % 2 ? -1.0 : 1.0) / f;
+        }
+        cosc[0] = 1.0;
+        for (int k = 0; k < 12; ++k) logc[k] = 1.0 / (2.0 * k + 1.0);
+    }
+};
+const SeriesCoef kSer;
+
+void sincos_2pi(double u, double* s_out, double* c_out) {
+    const double q = std::nearbyint(4.0 * u);
+    const double r = u - 0.25 * q;
+    const double a = 6.283185307179586 * r;
+    const double a2 = a * a;
+    double S = kSer.sinc[8];
+    for (int k = 7; k >= 0; --k) S = S * a2 + kSer.sinc[k];
+    double Cc = kSer.cosc[9];
+    for (int k = 8; k >= 0; --k) Cc = Cc * a2 + kSer.cosc[k];
+    const double sa = a * S, ca = Cc;
+    switch (((int)q) & 3) {
+        case 0: *s_out = sa; *c_out = ca; break;
+        case 1: *s_out = ca; *c_out = -sa; break;
+        case 2: *s_out = -sa; *c_out = -ca; break;
+        default: *s_out = -ca; *c_out = sa; break;
+    }
+}
+
+double neg_log(double u) {
+    int e = 0;
+    double m = std::frexp(u, &e);
+    if (m < 0.7071067811865476) { m = 2.0 * m; e -= 1; }
+    const double s = (m - 1.0) / (m + 1.0);
+    const double s2 = s * s;
+    double P = kSer.logc[11];
+    for (int k = 10; k >= 0; --k) P = P * s2 + kSer.logc[k];
+    const double lm = 2.0 * s * P;
+    return -((double)e * 0.6931471805599453 + lm);
+}
+
 // Isotropic direction: mu = 2u - 1, phi = 2 pi u'; the 2-D motion uses (Omega_x, Omega_y) and
 // the path length is the 3-D one (the domain is extruded in z).
 void iso_direction(double u_mu, double u_phi, double* ox, double* oy) {
     double sin_theta = 2.0 * std::sqrt(u_mu * (1.0 - u_mu));
-    double ph = 2.0 * kPi * u_phi;
-    *ox = sin_theta * std::cos(ph);
-    *oy = sin_theta * std::sin(ph);
+    double sp, cp;
+    sincos_2pi(u_phi, &sp, &cp);
+    *ox = sin_theta * cp;
+    *oy = sin_theta * sp;
 }
 
 // g_n(x) = int_0^1 t^n e^{-x t} dt, n = 0, 1, 2 (exact segment integrals of the decaying weight)
@@ -353,6 +405,7 @@ void gfun(double x, double* g0, double* g1, double* g2) {
 struct Leg {
     const or_problem* P; Mesh M; Points pts;
     std::vector<long double> pre, post, mom;
+    std::vector<int64_t> pre_n, post_n;   // segments scored per cell (statistical support of a tally)
     long double w_source = 0, w_absorbed = 0, w_leaked = 0, w_census = 0, w_handoff = 0, w_killed = 0;
     int64_t segments = 0, collisions = 0, leaked = 0, census = 0, killed = 0, reached = 0, errors = 0;
     or_bank* census_out = nullptr;
@@ -360,6 +413,7 @@ struct Leg {
     explicit Leg(const or_problem* p) : P(p), M(p), pts{0, p->sampler} {
         size_t nc = (size_t)M.nx * M.ny;
         pre.assign(nc, 0); post.assign(nc, 0); mom.assign(nc * 4, 0);
+        pre_n.assign(nc, 0); post_n.assign(nc, 0);
     }
 
     // Track one history from its start state to termination; returns the fate and fills the
@@ -373,7 +427,7 @@ struct Leg {
         int n = 0;
         if (Ns == 0) ++reached;
         double tau = 0.0;
-        if (Ns > 0) tau = -std::log(unit(pts(idx, 5)));
+        if (Ns > 0) tau = neg_log(unit(pts(idx, 5)));
         int64_t seg = 0;
         int fate = kFateError;
         while (seg < kMaxSegments) {
@@ -395,6 +449,7 @@ struct Leg {
                 // pre-limit: implicit capture with sigma_a, tally <Psi>_pre
                 const double att = -std::expm1(-sa * l);
                 pre[k] += (sa > 0) ? (long double)(w * att / sa) : (long double)(w * l);
+                ++pre_n[k];
                 w_absorbed += w * att;
                 w = w * std::exp(-sa * l);
                 tau -= ss * l;
@@ -403,6 +458,7 @@ struct Leg {
                 // deposit the (N_s+1)-th collision density into the bilinear moments
                 const double att = -std::expm1(-st * l);
                 post[k] += (st > 0) ? (long double)(w * att / st) : (long double)(w * l);
+                ++post_n[k];
                 double g0, g1, g2;
                 gfun(st * l, &g0, &g1, &g2);
                 const double I0 = l * g0, I1 = l * l * g1, I2 = l * l * l * g2;
@@ -445,7 +501,7 @@ struct Leg {
                 ++n; ++collisions;
                 const int base = 5 + 3 * (n - 1);
                 iso_direction(unit(pts(idx, base + 1)), unit(pts(idx, base + 2)), &ox, &oy);
-                if (n < Ns) tau = -std::log(unit(pts(idx, 5 + 3 * n)));
+                if (n < Ns) tau = neg_log(unit(pts(idx, 5 + 3 * n)));
                 else { tau = 0.0; ++reached; }
             }
             if (P->w_min > 0 && w < P->w_min * w_start) {
@@ -794,6 +850,14 @@ extern "C" {
 
 uint64_t or_mix64(uint64_t z) { return mix64(z); }
 
+// the direction and optical-depth maps, exposed for their accuracy pins
+void or_sincos_2pi(const double* u, int64_t n, double* s, double* c) {
+    for (int64_t i = 0; i < n; ++i) sincos_2pi(u[i], &s[i], &c[i]);
+}
+void or_neg_log(const double* u, int64_t n, double* out) {
+    for (int64_t i = 0; i < n; ++i) out[i] = neg_log(u[i]);
+}
+
 int or_sobol_table(int ndims, uint32_t* V) {
     if (ndims < 1 || ndims > kDimMax) return 1;
     build_sobol_table();
@@ -884,8 +948,17 @@ int or_sample_births(const or_problem* P, int64_t step, int64_t n, int32_t* cell
 // pre/post: track-length integrals sum w l g0 per cell; mom: hand-off moments (4 per cell).
 // hist (optional): 4 int32 per history (final cell, fate, final n, segments).
 // census_out (optional): the MC-leg census survivors.
+int or_mc_leg_counts(const or_problem* P, int64_t step, const or_bank* census, double* pre, double* post,
+                     double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n, int64_t* post_n);
+
 int or_mc_leg(const or_problem* P, int64_t step, const or_bank* census, double* pre, double* post,
               double* mom, or_stats* st, int32_t* hist, or_bank* census_out) {
+    return or_mc_leg_counts(P, step, census, pre, post, mom, st, hist, census_out, nullptr, nullptr);
+}
+
+// The MC leg with, per cell, the number of segments scored into the pre and post tallies.
+int or_mc_leg_counts(const or_problem* P, int64_t step, const or_bank* census, double* pre, double* post,
+                     double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n, int64_t* post_n) {
     build_sobol_table();
     Leg L(P);
     const Mesh& M = L.M;
@@ -921,6 +994,8 @@ int or_mc_leg(const or_problem* P, int64_t step, const or_bank* census, double* 
     for (size_t k = 0; k < nc; ++k) {
         pre[k] = (double)L.pre[k]; post[k] = (double)L.post[k];
         for (int i = 0; i < 4; ++i) mom[4 * k + i] = (double)L.mom[4 * k + i];
+        if (pre_n) pre_n[k] = L.pre_n[k];
+        if (post_n) post_n[k] = L.post_n[k];
     }
     fill_stats(L, h, st);
     if (L.census_overflow) return 3;

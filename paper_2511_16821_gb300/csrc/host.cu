@@ -211,7 +211,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 }
 
 struct Sizes {
-    size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, acc1, acc4, d1, d4,
+    size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
         sn4, sn16, sntx, snty, snqb, snnorm, blk;
     int64_t cap, nblk;
 };
@@ -234,6 +234,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.rem_q = nc * 8;
     z.scratch = (256 + d->ny + nc) * 8;
     z.bank = bank_cell_bytes(z.cap) + 5 * (size_t)z.cap * T;
+    z.stage = bank_cell_bytes(z.cap + d->n_hist) + 5 * (size_t)(z.cap + d->n_hist) * T;
     z.acc1 = nc * acc;
     z.acc4 = 4 * nc * acc;
     z.d1 = nc * 8;
@@ -253,7 +254,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
     const Sizes z = sizes(d);
     Layout L;
     const size_t parts[] = {z.st, z.sobol, z.sig, z.sa, z.ss, z.Q, z.cdf_q, z.cdf_row, z.cdf_col, z.cdf_q, z.cdf_row,
-                            z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.acc1, z.acc1, z.acc4, z.d1,
+                            z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4,
                             z.snnorm, z.blk};
     for (size_t b : parts) L.add(b);
@@ -282,6 +283,7 @@ void assign(hyb_problem* p) {
     p->cell_scratch = (double*)take(z.scratch);
     p->bank[0] = take(z.bank);
     p->bank[1] = take(z.bank);
+    p->stage = take(z.stage);
     p->acc_pre = take(z.acc1);
     p->acc_post = take(z.acc1);
     p->acc_mom = take(z.acc4);
@@ -636,8 +638,12 @@ hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
     HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
     const double tol = p->prec == HYB_FP64 ? p->d.sn_tol : std::max(p->d.sn_tol, 2e-6);
     int it = 0;
+    // with a warm start the previous step's count predicts this one: the first (count - 2)
+    // iterations run without a convergence read-back
+    const int unchecked = (p->sn_warm && p->last_sn_iters > 2) ? p->last_sn_iters - 2 : 0;
     for (it = 1; it <= p->d.sn_max_iter; ++it) {
         HYB_CU(p, sn_iteration(p, it == 1));
+        if (it <= unchecked) continue;
         HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_norm_num, &p->st->sn_norm_num, 2 * sizeof(double),
                                   cudaMemcpyDeviceToHost, p->stream));
         HYB_CU(p, cudaStreamSynchronize(p->stream));

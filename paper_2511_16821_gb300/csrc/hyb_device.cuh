@@ -124,15 +124,60 @@ __host__ __device__ __forceinline__ double acc128_to_double(unsigned long long l
     return neg ? -v : v;
 }
 
+// FP64 direction and optical-depth maps by explicit series in separately rounded operations, so the
+// FP64 geometry is reproducible bit for bit by any implementation of the same recipe:
+//   sin/cos(2 pi u): q = rint(4u), r = u - q/4 (exact), a = 2 pi r, Taylor series to a^17 / a^18
+//   (coefficients 1/n! from exact factorials), quadrant rotation by q mod 4;
+//   -log u: u = m 2^e, m in [1/sqrt2, sqrt2), log m = 2 s sum_k s^2k/(2k+1), s = (m-1)/(m+1).
+__device__ __forceinline__ void sincos_2pi_series(double u, double* s_out, double* c_out) {
+    const double q = rint(4.0 * u);
+    const double r = __dsub_rn(u, __dmul_rn(0.25, q));
+    const double a = __dmul_rn(6.283185307179586, r);
+    const double a2 = __dmul_rn(a, a);
+    constexpr double ks[9] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0, -1.0 / 39916800.0,
+                              1.0 / 6227020800.0, -1.0 / 1307674368000.0, 1.0 / 355687428096000.0};
+    constexpr double kc[10] = {1.0, -1.0 / 2.0, 1.0 / 24.0, -1.0 / 720.0, 1.0 / 40320.0, -1.0 / 3628800.0,
+                               1.0 / 479001600.0, -1.0 / 87178291200.0, 1.0 / 20922789888000.0,
+                               -1.0 / 6402373705728000.0};
+    double S = ks[8];
+#pragma unroll
+    for (int k = 7; k >= 0; --k) S = __dadd_rn(__dmul_rn(S, a2), ks[k]);
+    double Cc = kc[9];
+#pragma unroll
+    for (int k = 8; k >= 0; --k) Cc = __dadd_rn(__dmul_rn(Cc, a2), kc[k]);
+    const double sa = __dmul_rn(a, S), ca = Cc;
+    switch (((int)q) & 3) {
+        case 0: *s_out = sa; *c_out = ca; break;
+        case 1: *s_out = ca; *c_out = -sa; break;
+        case 2: *s_out = -sa; *c_out = -ca; break;
+        default: *s_out = -ca; *c_out = sa; break;
+    }
+}
+
+__device__ __forceinline__ double neg_log_series(double u) {
+    int e = 0;
+    double m = frexp(u, &e);
+    if (m < 0.7071067811865476) { m = 2.0 * m; e -= 1; }
+    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double s2 = __dmul_rn(s, s);
+    constexpr double kl[12] = {1.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 7.0, 1.0 / 9.0, 1.0 / 11.0,
+                               1.0 / 13.0, 1.0 / 15.0, 1.0 / 17.0, 1.0 / 19.0, 1.0 / 21.0, 1.0 / 23.0};
+    double P = kl[11];
+#pragma unroll
+    for (int k = 10; k >= 0; --k) P = __dadd_rn(__dmul_rn(P, s2), kl[k]);
+    const double lm = __dmul_rn(__dmul_rn(2.0, s), P);
+    return -__dadd_rn(__dmul_rn((double)e, 0.6931471805599453), lm);
+}
+
 template <> struct Prec<double> {
     using acc_t = Acc128;
     static constexpr int kbits = 125;
     static __device__ __forceinline__ double unit(uint32_t x) { return ((double)x + 0.5) * 0x1p-32; }
     static __device__ __forceinline__ double unit_c(uint32_t x) { return 1.0 - unit(x); }   // exact in FP64
-    static __device__ __forceinline__ double neglog(double u) { return -log(u); }
+    static __device__ __forceinline__ double neglog(double u) { return neg_log_series(u); }
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
     static __device__ __forceinline__ double exm1(double x) { return expm1(x); }
-    static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincospi(2.0 * u, s, c); }
+    static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincos_2pi_series(u, s, c); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     // separately rounded product and sum: FP64 geometry follows IEEE order exactly
     static __device__ __forceinline__ double madd(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }

@@ -91,6 +91,7 @@ struct hyb_problem {
     double* rem_q;            // ncells signed remap cell weights q = f0 A dt
     double* cell_scratch;     // per-row partials for the CDF build
     void* bank[2];            // two SoA banks (T)
+    void* stage;              // remap staging SoA, bank_cap + n_hist slots (T)
     int cur;                  // current bank index
     void* acc_pre; void* acc_post; void* acc_mom;   // fixed-point tallies
     double *pre_d, *post_d, *mom_d, *flux_d;        // normalised tallies (FP64)

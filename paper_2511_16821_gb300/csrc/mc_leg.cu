@@ -35,8 +35,22 @@ struct LegArgs {
     double sig_s_max, w_src_total, cdt_d;
 };
 
+// State of one live history in a lane.
 template <typename T>
-__global__ void __launch_bounds__(kTile) mc_leg_kernel(LegArgs<T> a) {
+struct Hist {
+    int ix, iy, n, seg;
+    T fx, fy, ox, oy, w, w_start, srem, tau;
+    uint32_t idx;
+    long long j;
+    bool census_stream;
+};
+
+// Refilled-lane leg: each warp owns a contiguous slice of [bank slots | births]; a lane whose
+// history ends takes the next index of the slice at once (ranks by ballot, deterministic order),
+// so the warp keeps all lanes on segments instead of waiting for its longest history. Weight
+// totals of each finished history go to int64 fixed point (order-free, deterministic).
+template <typename T>
+__global__ void __launch_bounds__(kTile, 2) mc_leg_kernel(LegArgs<T> a) {
     using P = Prec<T>;
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
@@ -55,155 +69,186 @@ __global__ void __launch_bounds__(kTile) mc_leg_kernel(LegArgs<T> a) {
     const int kt = scale_exponent(Wstep * a.cdt_d, P::kbits);
     const int km = scale_exponent(Wstep * a.cdt_d * a.sig_s_max, P::kbits);
     const T sc_t = (T)ldexp(1.0, kt), sc_m = (T)ldexp(1.0, km);
+    const int kw = scale_exponent(Wstep, 61);
+    const double scw = ldexp(1.0, kw);
 
     unsigned long long c_hist = 0, c_seg = 0, c_col = 0, c_leak = 0, c_cen = 0, c_kill = 0, c_reach = 0, c_err = 0;
-    double w_src = 0, w_abs = 0, w_leak = 0, w_cen = 0, w_hand = 0, w_kill = 0;
+    long long f_src = 0, f_abs = 0, f_leak = 0, f_cen = 0, f_hand = 0, f_kill = 0;
     int status = 0;
     const T DX = a.dx, DY = a.dy;
     const T INF = (T)INFINITY;
     const int Ns = a.n_s;
     const int nx = a.nx, ny = a.ny;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long per = (N + nwarps - 1) / nwarps;
+    long long next = wid * per;
+    const long long last = next + per < N ? next + per : N;
 
-    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N;
-         j += (long long)gridDim.x * blockDim.x) {
-        int ix, iy;
-        T fx, fy, ox, oy, w, srem;
-        uint32_t idx;
-        Points pts;
-        pts.V = sV;
-        pts.sampler = a.sampler;
-        pts.ntab = a.ntab;
-        if (j < nb) {
-            idx = (uint32_t)j;
-            pts.key = a.key_c;
-            pts.shift = sShC;
-            const int k = a.bank.cell[j];
-            if (k < 0 || k >= nx * ny) { status |= kStBounds; continue; }
-            ix = k % nx; iy = k / nx;
-            fx = a.bank.fx[j]; fy = a.bank.fy[j];
-            ox = a.bank.ox[j]; oy = a.bank.oy[j];
-            w = a.bank.w[j];
-            srem = a.cdt;
-        } else {
-            idx = (uint32_t)(j - nb);
-            pts.key = a.key_s;
-            pts.shift = sShS;
-            T frx, fry;
-            const int k = sample_cell<T>(a.cdf, nx, ny, pts(idx, 0), pts(idx, 1), &frx, &fry);
-            ix = k % nx; iy = k / nx;
-            fx = frx * DX; fy = fry * DY;
-            iso_dir<T>(pts(idx, 3), pts(idx, 4), &ox, &oy);
-            w = a.w0;
-            srem = a.cdt * P::unit_c(pts(idx, 2));
-        }
-        ++c_hist;
-        const T w_start = w;
-        w_src += (double)w;
-        int n = 0;
-        if (Ns == 0) ++c_reach;
-        T tau = 0;
-        if (Ns > 0) tau = P::neglog(P::unit(pts(idx, 5)));
-        int seg = 0, fate = kFateError;
-        while (seg < (int)kMaxSegments) {
-            ++seg;
-            const int k = iy * nx + ix;
-            const T sa = a.sig[2 * k], ss = a.sig[2 * k + 1], st = sa + ss;
-            const T dxf = ox > T(0) ? (DX - fx) / ox : (ox < T(0) ? fx / (-ox) : INF);
-            const T dyf = oy > T(0) ? (DY - fy) / oy : (oy < T(0) ? fy / (-oy) : INF);
-            const T dcol = (n < Ns && ss > T(0)) ? tau / ss : INF;
-            T l;
-            int ev;
-            bool xc = false, yc = false;
-            if (dcol <= dxf && dcol <= dyf && dcol <= srem) { l = dcol; ev = 0; }
-            else if (dxf <= srem || dyf <= srem) {
-                l = dxf < dyf ? dxf : dyf; ev = 1; xc = (dxf == l); yc = (dyf == l);
-            } else { l = srem; ev = 2; }
+    Points pts;
+    pts.V = sV;
+    pts.sampler = a.sampler;
+    pts.ntab = a.ntab;
+    Hist<T> h;
+    bool alive = false;
+    double d_abs = 0, d_hand = 0;   // weight removed from the live history so far
 
-            if (n < Ns) {
-                const T att = -P::exm1(-sa * l);
-                P::add(&a.pre[k], sa > T(0) ? w * att / sa : w * l, sc_t);
-                w_abs += (double)(w * att);
-                w = w * P::ex(-sa * l);
-                tau = P::msub(tau, ss, l);
-            } else {
-                const T att = -P::exm1(-st * l);
-                P::add(&a.post[k], st > T(0) ? w * att / st : w * l, sc_t);
-                if (ss > T(0)) {
-                    T g0, g1, g2;
-                    gfun<T>(st * l, &g0, &g1, &g2);
-                    const T I0 = l * g0, I1 = l * l * g1, I2 = l * l * l * g2;
-                    const T sw = ss * w;
-                    P::add(&a.mom[4 * k + 0], sw * I0, sc_m);
-                    if (a.handoff_full) {
-                        const T xi0 = T(2) * fx / DX - T(1), eta0 = T(2) * fy / DY - T(1);
-                        const T axi = T(2) * ox / DX, aeta = T(2) * oy / DY;
-                        P::add(&a.mom[4 * k + 1], sw * (xi0 * I0 + axi * I1), sc_m);
-                        P::add(&a.mom[4 * k + 2], sw * (eta0 * I0 + aeta * I1), sc_m);
-                        P::add(&a.mom[4 * k + 3],
-                               sw * (xi0 * eta0 * I0 + (xi0 * aeta + eta0 * axi) * I1 + axi * aeta * I2), sc_m);
+    for (;;) {
+        const unsigned need = __ballot_sync(0xffffffffu, !alive);
+        if (need) {
+            const long long j = next + __popc(need & lt_mask);
+            next += __popc(need);
+            if (!alive && j < last) {
+                // ---- start a history: bank pick-up or birth from Q -----------------------------
+                h.j = j;
+                bool ok = true;
+                if (j < nb) {
+                    h.idx = (uint32_t)j;
+                    h.census_stream = true;
+                    const int k = a.bank.cell[j];
+                    if (k < 0 || k >= nx * ny) { status |= kStBounds; ok = false; }
+                    else {
+                        h.ix = k % nx; h.iy = k / nx;
+                        h.fx = a.bank.fx[j]; h.fy = a.bank.fy[j];
+                        h.ox = a.bank.ox[j]; h.oy = a.bank.oy[j];
+                        h.w = a.bank.w[j];
+                        h.srem = a.cdt;
                     }
+                } else {
+                    h.idx = (uint32_t)(j - nb);
+                    h.census_stream = false;
+                    pts.key = a.key_s; pts.shift = sShS;
+                    T frx, fry;
+                    const int k = sample_cell<T>(a.cdf, nx, ny, pts(h.idx, 0), pts(h.idx, 1), &frx, &fry);
+                    h.ix = k % nx; h.iy = k / nx;
+                    h.fx = frx * DX; h.fy = fry * DY;
+                    iso_dir<T>(pts(h.idx, 3), pts(h.idx, 4), &h.ox, &h.oy);
+                    h.w = a.w0;
+                    h.srem = a.cdt * P::unit_c(pts(h.idx, 2));
                 }
-                if (st > T(0)) {
-                    w_hand += (double)(w * att * (ss / st));
-                    w_abs += (double)(w * att * (sa / st));
+                if (ok) {
+                    pts.key = h.census_stream ? a.key_c : a.key_s;
+                    pts.shift = h.census_stream ? sShC : sShS;
+                    ++c_hist;
+                    h.w_start = h.w;
+                    f_src += __double2ll_rn((double)h.w * scw);
+                    d_abs = 0; d_hand = 0;
+                    h.n = 0;
+                    h.seg = 0;
+                    if (Ns == 0) ++c_reach;
+                    h.tau = Ns > 0 ? P::neglog(P::unit(pts(h.idx, 5))) : T(0);
+                    alive = true;
                 }
-                w = w * P::ex(-st * l);
-            }
-            fx = P::madd(ox, l, fx);
-            fy = P::madd(oy, l, fy);
-            srem = srem - l;
-
-            if (ev == 2) {
-                fate = kFateCensus; ++c_cen; w_cen += (double)w;
-                break;
-            }
-            if (ev == 1) {
-                if (xc) { ix += ox > T(0) ? 1 : -1; fx = ox > T(0) ? T(0) : DX; }
-                else fx = clamp_(fx, T(0), DX);
-                if (yc) { iy += oy > T(0) ? 1 : -1; fy = oy > T(0) ? T(0) : DY; }
-                else fy = clamp_(fy, T(0), DY);
-                if (ix < 0 || ix >= nx || iy < 0 || iy >= ny) {
-                    fate = kFateLeaked; ++c_leak; w_leak += (double)w;
-                    ix = ix < 0 ? 0 : (ix >= nx ? nx - 1 : ix);
-                    iy = iy < 0 ? 0 : (iy >= ny ? ny - 1 : iy);
-                    break;
-                }
-            } else {
-                fx = clamp_(fx, T(0), DX);
-                fy = clamp_(fy, T(0), DY);
-                ++n; ++c_col;
-                const int base = 5 + 3 * (n - 1);
-                iso_dir<T>(pts(idx, base + 1), pts(idx, base + 2), &ox, &oy);
-                if (n < Ns) tau = P::neglog(P::unit(pts(idx, 5 + 3 * n)));
-                else { tau = T(0); ++c_reach; }
-            }
-            if (a.w_min > T(0) && w < a.w_min * w_start) {
-                fate = kFateKilled; ++c_kill; w_kill += (double)w;
-                break;
             }
         }
-        c_seg += (unsigned long long)seg;
-        if (fate == kFateError) { ++c_err; status |= kStSegments; }
-        if (a.hist) {
-            int4 r = make_int4(iy * nx + ix, fate, n, seg);
-            reinterpret_cast<int4*>(a.hist)[j] = r;
+        if (!__any_sync(0xffffffffu, alive)) break;
+        if (!alive) continue;
+        pts.key = h.census_stream ? a.key_c : a.key_s;
+        pts.shift = h.census_stream ? sShC : sShS;
+
+        // ---- one segment ----------------------------------------------------------------------
+        ++h.seg;
+        const int k = h.iy * nx + h.ix;
+        const T sa = a.sig[2 * k], ss = a.sig[2 * k + 1], st = sa + ss;
+        const T dxf = h.ox > T(0) ? (DX - h.fx) / h.ox : (h.ox < T(0) ? h.fx / (-h.ox) : INF);
+        const T dyf = h.oy > T(0) ? (DY - h.fy) / h.oy : (h.oy < T(0) ? h.fy / (-h.oy) : INF);
+        const T dcol = (h.n < Ns && ss > T(0)) ? h.tau / ss : INF;
+        T l;
+        int ev;
+        bool xc = false, yc = false;
+        if (dcol <= dxf && dcol <= dyf && dcol <= h.srem) { l = dcol; ev = 0; }
+        else if (dxf <= h.srem || dyf <= h.srem) {
+            l = dxf < dyf ? dxf : dyf; ev = 1; xc = (dxf == l); yc = (dyf == l);
+        } else { l = h.srem; ev = 2; }
+
+        if (h.n < Ns) {
+            const T att = -P::exm1(-sa * l);
+            P::add(&a.pre[k], sa > T(0) ? h.w * att / sa : h.w * l, sc_t);
+            d_abs += (double)(h.w * att);
+            h.w = h.w * P::ex(-sa * l);
+            h.tau = P::msub(h.tau, ss, l);
+        } else {
+            const T att = -P::exm1(-st * l);
+            P::add(&a.post[k], st > T(0) ? h.w * att / st : h.w * l, sc_t);
+            if (ss > T(0)) {
+                T g0, g1, g2;
+                gfun<T>(st * l, &g0, &g1, &g2);
+                const T I0 = l * g0, I1 = l * l * g1, I2 = l * l * l * g2;
+                const T sw = ss * h.w;
+                P::add(&a.mom[4 * k + 0], sw * I0, sc_m);
+                if (a.handoff_full) {
+                    const T xi0 = T(2) * h.fx / DX - T(1), eta0 = T(2) * h.fy / DY - T(1);
+                    const T axi = T(2) * h.ox / DX, aeta = T(2) * h.oy / DY;
+                    P::add(&a.mom[4 * k + 1], sw * (xi0 * I0 + axi * I1), sc_m);
+                    P::add(&a.mom[4 * k + 2], sw * (eta0 * I0 + aeta * I1), sc_m);
+                    P::add(&a.mom[4 * k + 3],
+                           sw * (xi0 * eta0 * I0 + (xi0 * aeta + eta0 * axi) * I1 + axi * aeta * I2), sc_m);
+                }
+            }
+            if (st > T(0)) {
+                d_hand += (double)(h.w * att * (ss / st));
+                d_abs += (double)(h.w * att * (sa / st));
+            }
+            h.w = h.w * P::ex(-st * l);
+        }
+        h.fx = P::madd(h.ox, l, h.fx);
+        h.fy = P::madd(h.oy, l, h.fy);
+        h.srem = h.srem - l;
+
+        int fate = -1;
+        if (ev == 2) {
+            fate = kFateCensus;
+        } else if (ev == 1) {
+            if (xc) { h.ix += h.ox > T(0) ? 1 : -1; h.fx = h.ox > T(0) ? T(0) : DX; }
+            else h.fx = clamp_(h.fx, T(0), DX);
+            if (yc) { h.iy += h.oy > T(0) ? 1 : -1; h.fy = h.oy > T(0) ? T(0) : DY; }
+            else h.fy = clamp_(h.fy, T(0), DY);
+            if (h.ix < 0 || h.ix >= nx || h.iy < 0 || h.iy >= ny) {
+                fate = kFateLeaked;
+                h.ix = h.ix < 0 ? 0 : (h.ix >= nx ? nx - 1 : h.ix);
+                h.iy = h.iy < 0 ? 0 : (h.iy >= ny ? ny - 1 : h.iy);
+            }
+        } else {
+            h.fx = clamp_(h.fx, T(0), DX);
+            h.fy = clamp_(h.fy, T(0), DY);
+            ++h.n; ++c_col;
+            const int base = 5 + 3 * (h.n - 1);
+            iso_dir<T>(pts(h.idx, base + 1), pts(h.idx, base + 2), &h.ox, &h.oy);
+            if (h.n < Ns) h.tau = P::neglog(P::unit(pts(h.idx, 5 + 3 * h.n)));
+            else { h.tau = T(0); ++c_reach; }
+        }
+        if (fate < 0 && a.w_min > T(0) && h.w < a.w_min * h.w_start) fate = kFateKilled;
+        if (fate < 0 && h.seg >= (int)kMaxSegments) fate = kFateError;
+        if (fate >= 0) {
+            // ---- end of the history ------------------------------------------------------------
+            const long long fw = __double2ll_rn((double)h.w * scw);
+            if (fate == kFateCensus) { ++c_cen; f_cen += fw; }
+            else if (fate == kFateLeaked) { ++c_leak; f_leak += fw; }
+            else if (fate == kFateKilled) { ++c_kill; f_kill += fw; }
+            else { ++c_err; status |= kStSegments; }
+            f_abs += __double2ll_rn(d_abs * scw);
+            f_hand += __double2ll_rn(d_hand * scw);
+            c_seg += (unsigned long long)h.seg;
+            if (a.hist) {
+                const int4 r = make_int4(h.iy * nx + h.ix, fate, h.n, h.seg);
+                reinterpret_cast<int4*>(a.hist)[h.j] = r;
+            }
+            alive = false;
         }
     }
 
-    // block reduction of the statistics (fixed order for a fixed launch shape)
-    __shared__ double s_w[kTile / 32][6];
-    __shared__ unsigned long long s_c[kTile / 32][8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long cs[8] = {c_hist, c_seg, c_col, c_leak, c_cen, c_kill, c_reach, c_err};
-    double ws[6] = {w_src, w_abs, w_leak, w_cen, w_hand, w_kill};
+    // block reduction of the statistics (integers: order-free)
+    __shared__ unsigned long long s_c[kTile / 32][14];
+    const int wl = threadIdx.x >> 5;
+    unsigned long long cs[14] = {c_hist, c_seg, c_col, c_leak, c_cen, c_kill, c_reach, c_err,
+                                 (unsigned long long)f_src, (unsigned long long)f_abs, (unsigned long long)f_leak,
+                                 (unsigned long long)f_cen, (unsigned long long)f_hand, (unsigned long long)f_kill};
 #pragma unroll
-    for (int q = 0; q < 8; ++q) cs[q] = warp_sum_u64(cs[q]);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) ws[q] = warp_sum(ws[q]);
-    if (lane == 0) {
-        for (int q = 0; q < 8; ++q) s_c[wid][q] = cs[q];
-        for (int q = 0; q < 6; ++q) s_w[wid][q] = ws[q];
-    }
+    for (int q = 0; q < 14; ++q) cs[q] = warp_sum_u64(cs[q]);
+    if (lane == 0)
+        for (int q = 0; q < 14; ++q) s_c[wl][q] = cs[q];
     if (status) atomicOr(&a.st->status, status);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -211,19 +256,14 @@ __global__ void __launch_bounds__(kTile) mc_leg_kernel(LegArgs<T> a) {
                                        &a.st->census, &a.st->killed, &a.st->reached, &a.st->errors};
         Acc128* wdst[6] = {&a.st->w_source, &a.st->w_absorbed, &a.st->w_leaked, &a.st->w_census,
                            &a.st->w_handoff, &a.st->w_killed};
-        const int kw = scale_exponent(Wstep, 125);
-        const double scw = ldexp(1.0, kw);
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 14; ++q) {
             unsigned long long v = 0;
             for (int ww = 0; ww < kTile / 32; ++ww) v += s_c[ww][q];
-            if (v) atomicAdd(cdst[q], v);
-        }
-        for (int q = 0; q < 6; ++q) {
-            double v = 0;
-            for (int ww = 0; ww < kTile / 32; ++ww) v += s_w[ww][q];
-            unsigned long long lo, hi;
-            to_i128(v * scw, &lo, &hi);
-            atomic_add128(wdst[q], lo, hi);
+            if (q < 8) { if (v) atomicAdd(cdst[q], v); }
+            else {
+                const long long sv = (long long)v;
+                atomic_add128(wdst[q - 8], (unsigned long long)sv, sv < 0 ? ~0ull : 0ull);
+            }
         }
         if (blockIdx.x == 0) {
             a.st->k_track = kt;

@@ -8,11 +8,13 @@
 // Remap: slot j in [bank slots | births] is re-streamed straight with sigma_t attenuation from its
 // step-start state (bank particles are copied, births come from the remap source density
 // Q + sigma_s (phi_pre + phi_post + phi_c), bilinear within a cell). Three launches:
-//   pass A  re-stream, count survivors, sum quantised |w| and |w| per block (no bank writes)
+//   pass A  re-stream every slot, stage its end state (24 B/slot FP32), count survivors, sum
+//           quantised |w| and |w| per block
 //   scan    one block: block offsets, totals, comb decision and tooth offset
-//   pass B  re-stream again (same arithmetic), block scan, write survivors (or their comb
-//           copies) into the other bank in slot order.
-// Recomputing the straight-line stream is cheaper than staging the state through HBM.
+//   pass B  read the staged states, block scan, write survivors (or their comb copies) into the
+//           other bank in slot order.
+// Staging costs ~48 B of HBM traffic per slot, far less than redoing a birth (two CDF searches,
+// the point draws, sincos) and its stream.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -181,7 +183,7 @@ struct RemapArgs {
     int nx, ny;
     T dx, dy, cdt, w_min;
     const T* sig;
-    BankView<T> in, out;
+    BankView<T> in, out, stg;   // stg: staged end states, one per slot (cell -1 = not alive)
     Cdf2DView cdf;
     const double* f;
     long long n_hist, cap;
@@ -315,6 +317,8 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
         const Particle<T> pr = remap_slot<T>(a, pts, j, nb, wbar, &wst, &w_abs, &w_leak, &w_kill, &leaked, &killed,
                                              &segs, &err);
         w_src += wst;
+        a.stg.cell[j] = pr.alive ? pr.cell : -1;
+        a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
         if (pr.alive) {
             ++cnt;
             qs += quant_w<T>(pr.w, w_ref);
@@ -460,18 +464,10 @@ __device__ __forceinline__ long long first_tooth(long long S, long long M, long 
 
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
-    extern __shared__ uint32_t sm[];
-    uint32_t* sV = sm;
-    uint32_t* sSh = sm + a.ntab * 32;
-    for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
-    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(a.key, (uint64_t)d);
     __shared__ long long s_c[kTile / 32], s_q[kTile / 32];
-    __syncthreads();
-    Points pts{sV, sSh, a.key, a.sampler, a.ntab};
     const long long nb = a.st->n_bank;
     const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
     const long long N = nb + nbirth;
-    const double wbar = nbirth ? a.st->remap_W / (double)a.n_hist : 0.0;
     const double w_ref = a.st->w_ref;
     const int comb = a.st->comb_on;
     const long long M = a.cap, o = a.st->comb_o, Ttot = a.st->comb_T;
@@ -485,9 +481,9 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
         Particle<T> pr;
         pr.alive = false;
         if (j < N) {
-            double d0, d1 = 0, d2 = 0, d3 = 0;
-            int i0 = 0, i1 = 0, i2 = 0, i3 = 0;
-            pr = remap_slot<T>(a, pts, j, nb, wbar, &d0, &d1, &d2, &d3, &i0, &i1, &i2, &i3);
+            pr.cell = a.stg.cell[j];
+            pr.alive = pr.cell >= 0;
+            pr.fx = a.stg.fx[j]; pr.fy = a.stg.fy[j]; pr.ox = a.stg.ox[j]; pr.oy = a.stg.oy[j]; pr.w = a.stg.w[j];
         }
         long long c = pr.alive ? 1 : 0;
         long long q = pr.alive ? quant_w<T>(pr.w, w_ref) : 0;
@@ -569,6 +565,12 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.st = p->st;
     a.blk = p->blk;
     const long long maxN = p->bank_cap + p->d.n_hist;
+    {
+        char* bk = (char*)p->stage;
+        a.stg.cell = (int32_t*)bk;
+        T* f = (T*)(bk + bank_cell_bytes(maxN));
+        a.stg.fx = f; a.stg.fy = f + maxN; a.stg.ox = f + 2 * maxN; a.stg.oy = f + 3 * maxN; a.stg.w = f + 4 * maxN;
+    }
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
     const size_t smem = (size_t)(a.ntab * 32 + a.ntab + 1) * sizeof(uint32_t);
     // zero the remap counters
@@ -577,7 +579,7 @@ static cudaError_t remap_t(hyb_problem* p) {
     if (e != cudaSuccess) return e;
     remap_count_kernel<T><<<nblk, kTile, smem, s>>>(a);
     remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nblk, p->st, a.cap, a.x_off, p->d.n_hist);
-    remap_write_kernel<T><<<nblk, kTile, smem, s>>>(a);
+    remap_write_kernel<T><<<nblk, kTile, 0, s>>>(a);
     remap_finish_kernel<<<1, 1, 0, s>>>(p->st);
     return cudaGetLastError();
 }

@@ -54,29 +54,36 @@ __global__ void sn_source_kernel(int ncells, const T* sig, const T* phi_old, con
     sgA[k] = (sa + ss + inv_cdt) * area;
 }
 
-// Gaussian elimination without pivoting (the mirrored cell matrix is diagonally dominant)
+template <typename T> __device__ __forceinline__ T rcp_(T x) { return T(1) / x; }
+template <> __device__ __forceinline__ float rcp_<float>(float x) { return __frcp_rn(x); }
+
+// The mirrored cell system couples {a0, a3} only to {a1, a2}:
+//   [ d0  2X  2Y   0 ]        d0 = sA + 2X + 2Y,       d1 = sA/3 + 2X + (2/3)Y,
+//   [-2X  d1   0  tY ]        d2 = sA/3 + (2/3)X + 2Y, d3 = sA/9 + (2/3)(X + Y),
+//   [-2Y   0  d2  tX ]        tX = (2/3)X, tY = (2/3)Y;
+//   [  0 -tY -tX  d3 ]
+// eliminating a0 and a3 leaves a symmetric positive 2x2 system for (a1, a2) (Schur complement),
+// a short dependency chain: two reciprocals, one 2x2 determinant, back substitution.
 template <typename T>
-__device__ __forceinline__ void solve4(T m[4][4], T b[4], T x[4]) {
-    T inv[4];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        inv[c] = T(1) / m[c][c];
-#pragma unroll
-        for (int r = c + 1; r < 4; ++r) {
-            const T f = m[r][c] * inv[c];
-#pragma unroll
-            for (int k = c; k < 4; ++k) m[r][k] -= f * m[c][k];
-            b[r] -= f * b[c];
-        }
-    }
-    inv[3] = T(1) / m[3][3];
-#pragma unroll
-    for (int r = 3; r >= 0; --r) {
-        T s = b[r];
-#pragma unroll
-        for (int k = r + 1; k < 4; ++k) s -= m[r][k] * x[k];
-        x[r] = s * inv[r];
-    }
+__device__ __forceinline__ void solve_mirrored(T sA, T X, T Y, const T b[4], T ap[4]) {
+    const T twoX = T(2) * X, twoY = T(2) * Y, tX = T(2.0 / 3.0) * X, tY = T(2.0 / 3.0) * Y;
+    const T d0 = sA + twoX + twoY;
+    const T d1 = sA * T(1.0 / 3.0) + twoX + tY;
+    const T d2 = sA * T(1.0 / 3.0) + tX + twoY;
+    const T d3 = sA * T(1.0 / 9.0) + tX + tY;
+    const T i0 = rcp_(d0), i3 = rcp_(d3);
+    const T A = d1 + twoX * twoX * i0 + tY * tY * i3;
+    const T B = twoX * twoY * i0 + tX * tY * i3;
+    const T D = d2 + twoY * twoY * i0 + tX * tX * i3;
+    const T r1 = b[1] + twoX * b[0] * i0 - tY * b[3] * i3;
+    const T r2 = b[2] + twoY * b[0] * i0 - tX * b[3] * i3;
+    const T idet = rcp_(A * D - B * B);
+    const T a1 = (D * r1 - B * r2) * idet;
+    const T a2 = (A * r2 - B * r1) * idet;
+    ap[0] = (b[0] - twoX * a1 - twoY * a2) * i0;
+    ap[1] = a1;
+    ap[2] = a2;
+    ap[3] = (b[3] + tY * a1 + tX * a2) * i3;
 }
 
 // Pipelined strip sweep, one CTA per ordinate, W warps. Warp w sweeps strips w, w+W, ... (lane =
@@ -154,16 +161,12 @@ __global__ void sweep_pipe_kernel(SweepArgs<T> a) {
                     } else { by0 = 0; by1 = 0; }
                 } else { by0 = u0; by1 = u1; }
                 if (c == 0) { bx0 = 0; bx1 = 0; }
-                T M[4][4] = {{sA + twoX + twoY, twoX, twoY, T(0)},
-                             {-twoX, sA * T(1.0 / 3.0) + twoX + tY, T(0), tY},
-                             {-twoY, T(0), sA * T(1.0 / 3.0) + tX + twoY, tX},
-                             {T(0), -tY, -tX, sA * T(1.0 / 9.0) + tX + tY}};
-                T b[4] = {S0 + twoX * bx0 + twoY * by0,
-                          sxf * S1 - twoX * bx0 + tY * by1,
-                          syf * S2 + tX * bx1 - twoY * by0,
-                          sxy * S3 - tX * bx1 - tY * by1};
+                const T b[4] = {S0 + twoX * bx0 + twoY * by0,
+                                sxf * S1 - twoX * bx0 + tY * by1,
+                                syf * S2 + tX * bx1 - twoY * by0,
+                                sxy * S3 - tX * bx1 - tY * by1};
                 T ap[4];
-                solve4<T>(M, b, ap);
+                solve_mirrored<T>(sA, X, Y, b, ap);
                 bx0 = ap[0] + ap[1]; bx1 = ap[2] + ap[3];
                 oy0 = ap[0] + ap[2]; oy1 = ap[1] + ap[3];
                 const int ix = sx > 0 ? c : nx - 1 - c;

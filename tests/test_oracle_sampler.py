@@ -149,3 +149,21 @@ def test_prng_uniformity(orc):
         assert chi2 < 50.0            # 15 dof; p ~ 1e-5 tail
     # distinct (i, d) give distinct values (no accidental sharing of the hash)
     assert len(np.unique(P[:1000].ravel())) > 3990
+
+
+def test_direction_and_depth_maps_accuracy(orc):
+    # the series evaluations of sin/cos(2 pi u) and -log u against 40-digit arithmetic over the
+    # point lattice, including the quadrant boundaries and u -> 0, 1
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    x = np.concatenate([np.arange(0, 2 ** 32, 2 ** 32 // 2003, dtype=np.uint64),
+                        np.array([0, 1, 2 ** 30 - 1, 2 ** 30, 2 ** 31, 3 * 2 ** 30, 2 ** 32 - 1], np.uint64)])
+    u = (x.astype(np.float64) + 0.5) * 2.0 ** -32
+    s, c = orc.sincos_2pi(u)
+    t = orc.neg_log(u)
+    for i in range(u.size):
+        a = 2 * mpmath.pi * mpmath.mpf(float(u[i]))
+        assert abs(s[i] - float(mpmath.sin(a))) < 3e-16
+        assert abs(c[i] - float(mpmath.cos(a))) < 3e-16
+        ref = -mpmath.log(mpmath.mpf(float(u[i])))
+        assert abs(t[i] - float(ref)) <= 3e-16 * abs(float(ref))
