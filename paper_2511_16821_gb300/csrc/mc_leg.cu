@@ -50,7 +50,7 @@ struct Hist {
 // so the warp keeps all lanes on segments instead of waiting for its longest history. Weight
 // totals of each finished history go to int64 fixed point (order-free, deterministic).
 template <typename T>
-__global__ void __launch_bounds__(kTile, 2) mc_leg_kernel(LegArgs<T> a) {
+__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(LegArgs<T> a) {
     using P = Prec<T>;
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;

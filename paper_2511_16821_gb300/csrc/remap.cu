@@ -51,12 +51,12 @@ __global__ void cdf_reduce_kernel(const double* __restrict__ w, int ncells, doub
     }
 }
 
+// one warp: strided partial sums, then a fixed-order shuffle tree (deterministic)
 __global__ void cdf_total_kernel(const double* part_sum, int nparts, double* W) {
-    if (threadIdx.x == 0) {
-        double t = 0;
-        for (int i = 0; i < nparts; ++i) t += part_sum[i];
-        *W = t;
-    }
+    double t = 0;
+    for (int i = threadIdx.x; i < nparts; i += 32) t += part_sum[i];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) *W = t;
 }
 
 // one block per row: q_int and the exclusive column scan of the row
@@ -106,15 +106,42 @@ __global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax
     }
 }
 
-__global__ void cdf_rowpre_kernel(const long long* row_tot, int ny, long long* row_pre) {
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        row_pre[0] = 0;
-        for (int i = 0; i < ny; ++i) {
-            acc += row_tot[i];
-            row_pre[i + 1] = acc;
-        }
+// block inclusive scan of a per-thread total (int64, exact); returns the exclusive prefix
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long* total) {
+    __shared__ long long sw[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
     }
+    if (lane == 31) sw[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        long long x = lane < nw ? sw[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += u;
+        }
+        if (lane < nw) sw[lane] = x;
+    }
+    __syncthreads();
+    const long long ex = (wid > 0 ? sw[wid - 1] : 0) + inc - v;
+    *total = sw[nw - 1];
+    __syncthreads();
+    return ex;
+}
+
+// row marginal: exclusive prefix of the row totals (one block, contiguous chunks per thread)
+__global__ void cdf_rowpre_kernel(const long long* row_tot, int ny, long long* row_pre) {
+    const int per = (ny + blockDim.x - 1) / blockDim.x;
+    const int r0 = threadIdx.x * per;
+    long long local = 0;
+    for (int r = r0; r < r0 + per && r < ny; ++r) local += row_tot[r];
+    long long total;
+    long long run = block_exclusive_scan(local, &total);
+    for (int r = r0; r < r0 + per && r < ny; ++r) { row_pre[r] = run; run += row_tot[r]; }
+    if (threadIdx.x == 0) row_pre[ny] = total;
 }
 
 // scratch: kCdfParts doubles of block partial sums, then ny int64 row totals
@@ -127,7 +154,7 @@ cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView
     cdf_reduce_kernel<<<kCdfParts, 256, 0, stream>>>(cell_w, nx * ny, part, qmax_out);
     cdf_total_kernel<<<1, 32, 0, stream>>>(part, kCdfParts, W_out);
     cdf_rows_kernel<<<ny, 256, 0, stream>>>(cell_w, qmax_out, nx, cdf, row_tot);
-    cdf_rowpre_kernel<<<1, 32, 0, stream>>>(row_tot, ny, cdf.row_pre);
+    cdf_rowpre_kernel<<<1, 1024, 0, stream>>>(row_tot, ny, cdf.row_pre);
     return cudaGetLastError();
 }
 
@@ -391,15 +418,15 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
         hi += h + (nl < lo ? 1ull : 0ull);
         lo = nl;
     }
-    sc[t] = c; sq[t] = q; slo[t] = lo; shi[t] = hi;
+    slo[t] = lo; shi[t] = hi;
+    long long ac, aq;
+    const long long exc = block_exclusive_scan(c, &ac);
+    const long long exq = block_exclusive_scan(q, &aq);
+    sc[t] = exc; sq[t] = exq;
     __syncthreads();
     if (t == 0) {
-        long long ac = 0, aq = 0;
         unsigned long long al = 0, ah = 0;
         for (int u = 0; u < nt; ++u) {
-            const long long cc = sc[u], qq = sq[u];
-            sc[u] = ac; sq[u] = aq;
-            ac += cc; aq += qq;
             const unsigned long long nl = al + slo[u];
             ah += shi[u] + (nl < al ? 1ull : 0ull);
             al = nl;

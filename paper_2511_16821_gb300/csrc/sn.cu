@@ -124,20 +124,25 @@ __global__ void sweep_pipe_kernel(SweepArgs<T> a) {
         volatile T* rout = ring + (size_t)bout * nx * 2;
         T bx0 = 0, bx1 = 0, oy0 = 0, oy1 = 0;
         int c = -lane;
-        T nS[4] = {0, 0, 0, 0}, nsg = 1;
-        auto load = [&](int col) {
+        // cell data three steps ahead (L2 latency spans several wavefront steps)
+        T q0[5] = {0, 0, 0, 0, 1}, q1[5] = {0, 0, 0, 0, 1}, q2[5] = {0, 0, 0, 0, 1};
+        auto load = [&](int col, T* d) {
             if (row_ok && col >= 0 && col < nx) {
                 const int ix = sx > 0 ? col : nx - 1 - col;
                 const size_t k = (size_t)iy * nx + ix;
                 const T* sp = a.src + 4 * k;
-                nS[0] = sp[0]; nS[1] = sp[1]; nS[2] = sp[2]; nS[3] = sp[3];
-                nsg = a.sgA[k];
+                d[0] = __ldg(sp); d[1] = __ldg(sp + 1); d[2] = __ldg(sp + 2); d[3] = __ldg(sp + 3);
+                d[4] = __ldg(a.sgA + k);
             }
         };
-        load(c);
+        load(c, q0);
+        load(c + 1, q1);
+        load(c + 2, q2);
         for (int t = 0; t < nx + 31; ++t, ++c) {
-            const T S0 = nS[0], S1 = nS[1], S2 = nS[2], S3 = nS[3], sA = nsg;
-            load(c + 1);
+            const T S0 = q0[0], S1 = q0[1], S2 = q0[2], S3 = q0[3], sA = q0[4];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) { q0[i] = q1[i]; q1[i] = q2[i]; }
+            load(c + 3, q2);
             const bool act = row_ok && c >= 0 && c < nx;
             // lane 0 needs the trace of column c from strip s-1; the top lane must not overwrite
             // ring slot column c before strip s+1-W's consumer has read it
@@ -222,9 +227,11 @@ __global__ void sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* ph
 }
 
 __global__ void sn_norm_final_kernel(const double* part, int nparts, DevState* st) {
+    double a = 0, b = 0;
+    for (int i = threadIdx.x; i < nparts; i += 32) { a += part[2 * i]; b += part[2 * i + 1]; }
+    a = warp_sum(a);
+    b = warp_sum(b);
     if (threadIdx.x == 0) {
-        double a = 0, b = 0;
-        for (int i = 0; i < nparts; ++i) { a += part[2 * i]; b += part[2 * i + 1]; }
         st->sn_norm_num = a;
         st->sn_norm_den = b;
     }
