@@ -183,6 +183,34 @@ HYB_API hyb_status hyb_get_step(const hyb_problem* p, int64_t* step);
 HYB_API hyb_status hyb_points(uint64_t seed, int64_t step, int32_t stream_id, int32_t sampler, int64_t i0,
                       int64_t n, int32_t ndims, uint32_t* out_dev, void* cuda_stream);
 
+/* ---- batches: many problems advanced by one CUDA graph per step --------------------------------
+ * The MC legs of all problems run as one persistent launch that pulls (problem, history range)
+ * chunks from a device work queue; normalisation, collided solves and remaps follow as
+ * independent graph branches on a pool of streams. Results are those of stepping each problem
+ * alone (bit-identical integers and tallies). Problems must share one precision, be at a step
+ * boundary, and not be stepped individually while the batch exists (the batch owns their
+ * stream use). Source iteration runs up to a per-problem cap inside the graph and stops on a
+ * device flag; a problem that reaches its cap gets a doubled cap from the next step on. */
+typedef struct hyb_batch hyb_batch;
+typedef struct {
+    int32_t block;        /* threads per CTA of the batched MC leg: 128 or 256 */
+    int32_t chunk;        /* histories per work-queue item (>= 32) */
+    int32_t ctas_per_sm;  /* resident CTAs per SM of the persistent leg; 0 = register limit */
+    int32_t streams;      /* streams for the per-problem branches (1..64) */
+} hyb_batch_tuning;
+
+/* problems: n handles (host array, borrowed; the problems must outlive the batch). cuda_stream:
+ * the stream the graph is launched on (NULL: the batch creates its own; the legacy default stream
+ * cannot record graphs). Allocates the work queue, graph and report buffers. */
+HYB_API hyb_status hyb_batch_create(hyb_problem* const* problems, int32_t n, void* cuda_stream, hyb_batch** out);
+/* Replace the tuning (rebuilds the work queue; graphs are re-recorded at the next step). */
+HYB_API hyb_status hyb_batch_set_tuning(hyb_batch* b, const hyb_batch_tuning* tuning);
+/* nsteps steps of every problem; per_problem (host, n entries, may be NULL): the last step's leg
+ * statistics with sn_iterations / combed / bank_size, ms = device time of the last graph. */
+HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* per_problem);
+HYB_API hyb_status hyb_batch_destroy(hyb_batch* b);
+HYB_API const char* hyb_batch_last_error(const hyb_batch* b);
+
 /* Integer 2-D CDF over cells (the sampling map of Sec. 2.3 births and of the Eq. (R) remap):
  * q_k = rint(|w_k| / max|w| 2^40); col_pre: per row the exclusive prefix of q over the row's cells
  * (ny x (nx+1), last entry = row total); row_pre: exclusive prefix of the row totals (ny+1).

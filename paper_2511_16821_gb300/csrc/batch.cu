@@ -1,0 +1,366 @@
+// batch.cu -- many independent problems advanced together: one time step of the whole batch is one
+// CUDA graph. The MC legs of all problems run as one persistent work-queue launch (CTAs pull
+// (problem, history range) chunks from a device queue, so uneven banks balance across the GPU);
+// normalisation, the collided S_N-DG solves and the remaps of the problems follow as independent
+// branches on a pool of streams. Each problem's results are those of stepping it alone: every
+// kernel works on one problem's data, and all sums are order-free integers.
+//
+// Graph replay needs no host state change between steps: the step index and the point-set keys
+// live in device memory, source iteration stops on a device flag (later iterations return at
+// once), and the banks' double buffer is handled by two graphs, one per parity, replayed in turn.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hyb_device.cuh"
+
+namespace {
+
+struct LegChunkH { int p; int pad; long long j0, j1; };
+
+thread_local std::string g_batch_err;
+
+}  // namespace
+
+struct hyb_batch {
+    std::vector<hyb_problem*> probs;
+    int prec = 0;
+    cudaStream_t s0 = nullptr;
+    bool own_s0 = false;
+    std::vector<cudaStream_t> pool;
+    std::vector<cudaEvent_t> join_ev;
+    cudaEvent_t fork_ev = nullptr, ev0 = nullptr, ev1 = nullptr;
+    void* d_args[2] = {nullptr, nullptr};   // per parity: LegArgs of every problem
+    void* d_chunks = nullptr;
+    int nchunks = 0;
+    int* d_head = nullptr;
+    hyb::DevState* d_report = nullptr;      // per problem: a copy of its counters after the step
+    hyb::DevState* h_report = nullptr;      // pinned
+    uint32_t* d_V = nullptr;
+    int ntab_max = 0;
+    hyb_batch_tuning tune{256, 4096, 0, 8};
+    std::vector<int> cur0;                  // bank parity of each problem when the batch was made
+    std::vector<int> kmax;                  // source-iteration cap per problem inside the graph
+    cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [parity][phase]
+    std::vector<void*> phi_mid[2], old_mid[2];   // S_N buffer pointers between the phases
+    int parity = 0;                         // graphs to replay next
+    std::string err;
+};
+
+namespace {
+
+hyb_status bfail(hyb_batch* b, hyb_status s, const std::string& m) {
+    if (b) b->err = m; else g_batch_err = m;
+    return s;
+}
+
+__global__ void report_kernel(const hyb::DevState* st, hyb::DevState* out) {
+    const int i = threadIdx.x;
+    const int n = (int)(sizeof(hyb::DevState) / sizeof(int));
+    const int* src = (const int*)st;
+    int* dst = (int*)out;
+    for (int k = i; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+void drop_graphs(hyb_batch* b) {
+    for (int q = 0; q < 2; ++q)
+        for (int f = 0; f < 2; ++f)
+            if (b->exec[q][f]) { cudaGraphExecDestroy(b->exec[q][f]); b->exec[q][f] = nullptr; }
+}
+
+hyb_status build_chunks(hyb_batch* b) {
+    std::vector<LegChunkH> ch;
+    const long long C = std::max(32, b->tune.chunk);
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        hyb_problem* p = b->probs[i];
+        const long long N = p->bank_cap + (p->has_src ? p->d.n_hist : 0);
+        for (long long j = 0; j < std::max(N, 1LL); j += C) ch.push_back(LegChunkH{(int)i, 0, j, std::min(N, j + C)});
+    }
+    // interleave problems so that large banks do not end the queue alone
+    std::stable_sort(ch.begin(), ch.end(), [](const LegChunkH& x, const LegChunkH& y) { return x.j0 < y.j0; });
+    if (b->d_chunks) cudaFree(b->d_chunks);
+    b->d_chunks = nullptr;
+    if (cudaMalloc(&b->d_chunks, ch.size() * sizeof(LegChunkH)) != cudaSuccess)
+        return bfail(b, HYB_ENOMEM, "chunk queue allocation");
+    if (cudaMemcpy(b->d_chunks, ch.data(), ch.size() * sizeof(LegChunkH), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bfail(b, HYB_ECUDA, "chunk queue upload");
+    b->nchunks = (int)ch.size();
+    return HYB_OK;
+}
+
+// Record one batch step of parity q as two graphs. Phase 0: zero tallies and counters, the
+// batched MC leg, then per problem normalisation and up to kmax source iterations (device stop).
+// Phase 1: per problem the end of the collided solve, the remap and a copy of its counters.
+// Problems whose iteration did not converge in phase 0 continue eagerly in between.
+hyb_status capture(hyb_batch* b, int q) {
+    const size_t n = b->probs.size();
+    std::vector<cudaStream_t> saved_stream(n);
+    std::vector<int> saved_cur(n);
+    std::vector<void*> saved_phi(n), saved_old(n);
+    for (size_t i = 0; i < n; ++i) {
+        hyb_problem* p = b->probs[i];
+        saved_stream[i] = p->stream; saved_cur[i] = p->cur; saved_phi[i] = p->sn_phi; saved_old[i] = p->sn_phi_old;
+        p->cur = b->cur0[i] ^ q;
+    }
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
+    for (int phase = 0; phase < 2 && e == cudaSuccess; ++phase) {
+        ck(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
+        if (e != cudaSuccess) break;
+        if (phase == 0) {
+            for (size_t i = 0; i < n; ++i) {
+                hyb_problem* p = b->probs[i];
+                const size_t nc = (size_t)p->ncells, acc = p->prec == HYB_FP64 ? 16 : 8;
+                ck(cudaMemsetAsync(p->acc_pre, 0, nc * acc, b->s0));
+                ck(cudaMemsetAsync(p->acc_post, 0, nc * acc, b->s0));
+                ck(cudaMemsetAsync(p->acc_mom, 0, 4 * nc * acc, b->s0));
+                ck(cudaMemsetAsync(p->st, 0, offsetof(hyb::DevState, r_histories), b->s0));
+                ck(cudaMemsetAsync(&p->st->status, 0, sizeof(int), b->s0));
+            }
+            ck(cudaMemsetAsync(b->d_head, 0, sizeof(int), b->s0));
+            const int per_sm = b->tune.ctas_per_sm > 0 ? b->tune.ctas_per_sm
+                                                       : hyb::leg_batch_ctas_per_sm(b->prec) * 256 / b->tune.block;
+            const int grid = std::max(1, std::min(b->nchunks, sms * per_sm));
+            ck(hyb::launch_mc_leg_batch(b->prec, b->d_args[q], b->d_chunks, b->nchunks, b->d_head, b->d_V,
+                                        b->ntab_max, grid, b->tune.block, b->s0));
+        }
+        ck(cudaEventRecord(b->fork_ev, b->s0));
+        for (auto s : b->pool) ck(cudaStreamWaitEvent(s, b->fork_ev, 0));
+        for (size_t i = 0; i < n; ++i) {
+            hyb_problem* p = b->probs[i];
+            p->stream = b->pool[i % b->pool.size()];
+            if (phase == 0) {
+                ck(hyb::launch_leg_normalise(p));
+                ck(hyb::sn_start(p));
+                for (int k = 1; k <= b->kmax[i]; ++k) ck(hyb::sn_iteration(p, k == 1));
+            } else {
+                ck(hyb::sn_finish(p));
+                ck(cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+                ck(hyb::launch_remap(p));
+            }
+            report_kernel<<<1, 128, 0, p->stream>>>(p->st, b->d_report + i);
+            ck(cudaGetLastError());
+        }
+        for (size_t j = 0; j < b->pool.size(); ++j) {
+            ck(cudaEventRecord(b->join_ev[j], b->pool[j]));
+            ck(cudaStreamWaitEvent(b->s0, b->join_ev[j], 0));
+        }
+        ck(cudaMemcpyAsync(b->h_report, b->d_report, n * sizeof(hyb::DevState), cudaMemcpyDeviceToHost, b->s0));
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(b->s0, &g);
+        if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
+        if (e == cudaSuccess) ck(cudaGraphInstantiate(&b->exec[q][phase], g, 0));
+        if (g) cudaGraphDestroy(g);
+        if (phase == 0) {
+            b->phi_mid[q].assign(n, nullptr);
+            b->old_mid[q].assign(n, nullptr);
+            for (size_t i = 0; i < n; ++i) { b->phi_mid[q][i] = b->probs[i]->sn_phi; b->old_mid[q][i] = b->probs[i]->sn_phi_old; }
+        }
+    }
+    for (size_t i = 0; i < n; ++i) {
+        hyb_problem* p = b->probs[i];
+        p->stream = saved_stream[i]; p->cur = saved_cur[i]; p->sn_phi = saved_phi[i]; p->sn_phi_old = saved_old[i];
+    }
+    if (e != cudaSuccess) {
+        drop_graphs(b);
+        return bfail(b, HYB_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
+    return HYB_OK;
+}
+
+// Continue the source iteration of problem i (phase-0 cap reached) until its device flag is set,
+// with an even number of further iterations so phase 1 finds the newest iterate where it was
+// recorded (an iteration after convergence only carries the solution forward).
+hyb_status finish_iterations(hyb_batch* b, int q, size_t i) {
+    hyb_problem* p = b->probs[i];
+    void* ph = p->sn_phi; void* po = p->sn_phi_old; cudaStream_t ps = p->stream;
+    p->sn_phi = b->phi_mid[q][i]; p->sn_phi_old = b->old_mid[q][i];
+    p->stream = b->s0;
+    hyb_status rc = HYB_OK;
+    int extra = 0;
+    for (int k = b->kmax[i]; k < p->d.sn_max_iter; ++k) {
+        if (hyb::sn_iteration(p, 0) != cudaSuccess) { rc = HYB_ECUDA; break; }
+        ++extra;
+        if (extra % 2 == 0) {
+            cudaMemcpyAsync(&p->st_host->sn_conv, &p->st->sn_conv, 2 * sizeof(int), cudaMemcpyDeviceToHost, b->s0);
+            if (cudaStreamSynchronize(b->s0) != cudaSuccess) { rc = HYB_ECUDA; break; }
+            if (p->st_host->sn_conv) break;
+        }
+    }
+    if (extra % 2 == 1 && rc == HYB_OK && hyb::sn_iteration(p, 0) != cudaSuccess) rc = HYB_ECUDA;
+    cudaStreamSynchronize(b->s0);
+    p->sn_phi = ph; p->sn_phi_old = po; p->stream = ps;
+    return rc == HYB_OK ? HYB_OK : bfail(b, rc, "eager source iteration");
+}
+
+}  // namespace
+
+extern "C" {
+
+HYB_API hyb_status hyb_batch_create(hyb_problem* const* problems, int32_t n, void* cuda_stream, hyb_batch** out) {
+    if (!problems || n < 1 || !out) return bfail(nullptr, HYB_EINVAL, "need at least one problem");
+    *out = nullptr;
+    hyb_batch* b = new (std::nothrow) hyb_batch();
+    if (!b) return bfail(nullptr, HYB_ENOMEM, "host allocation");
+    b->prec = problems[0]->prec;
+    for (int i = 0; i < n; ++i) {
+        hyb_problem* p = problems[i];
+        if (!p || p->prec != b->prec) { delete b; return bfail(nullptr, HYB_EINVAL, "problems must share one precision"); }
+        if (p->leg_done) { delete b; return bfail(nullptr, HYB_ESTATE, "problems must be at a step boundary"); }
+        b->probs.push_back(p);
+        b->cur0.push_back(p->cur);
+        b->kmax.push_back(std::max(8, p->last_sn_iters + 3));
+        b->ntab_max = std::max(b->ntab_max, hyb::leg_ntab(p));
+    }
+    b->s0 = (cudaStream_t)cuda_stream;
+    if (!b->s0) {   // graphs cannot be recorded on the legacy default stream
+        if (cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) != cudaSuccess) {
+            delete b;
+            return bfail(nullptr, HYB_ECUDA, "stream");
+        }
+        b->own_s0 = true;
+    }
+    auto fail_all = [&](hyb_status s, const char* m) {
+        g_batch_err = m;
+        hyb_batch_destroy(b);
+        return s;
+    };
+    for (int q = 0; q < 2; ++q) {
+        const size_t ab = hyb::leg_args_bytes(b->prec);
+        std::vector<unsigned char> host(ab * n);
+        for (int i = 0; i < n; ++i) hyb::leg_args_host(b->probs[i], b->cur0[i] ^ q, host.data() + ab * i);
+        if (cudaMalloc(&b->d_args[q], host.size()) != cudaSuccess) return fail_all(HYB_ENOMEM, "args");
+        if (cudaMemcpy(b->d_args[q], host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail_all(HYB_ECUDA, "args upload");
+    }
+    if (cudaMalloc(&b->d_head, sizeof(int)) != cudaSuccess) return fail_all(HYB_ENOMEM, "queue head");
+    if (cudaMalloc(&b->d_report, n * sizeof(hyb::DevState)) != cudaSuccess) return fail_all(HYB_ENOMEM, "report");
+    if (cudaMallocHost(&b->h_report, n * sizeof(hyb::DevState)) != cudaSuccess) return fail_all(HYB_ENOMEM, "report");
+    if (cudaMalloc(&b->d_V, HYB_SOBOL_DIMS * 32 * 4) != cudaSuccess) return fail_all(HYB_ENOMEM, "table");
+    if (cudaMemcpy(b->d_V, hyb::sobol_table_host(), HYB_SOBOL_DIMS * 32 * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail_all(HYB_ECUDA, "table upload");
+    if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
+        return fail_all(HYB_ECUDA, "events");
+    hyb_status s = hyb_batch_set_tuning(b, &b->tune);
+    if (s != HYB_OK) { std::string m = b->err; hyb_batch_destroy(b); g_batch_err = m; return s; }
+    *out = b;
+    return HYB_OK;
+}
+
+HYB_API hyb_status hyb_batch_set_tuning(hyb_batch* b, const hyb_batch_tuning* t) {
+    if (!b || !t) return bfail(b, HYB_EINVAL, "null argument");
+    if ((t->block != 128 && t->block != 256) || t->chunk < 32 || t->ctas_per_sm < 0 || t->ctas_per_sm > 16 ||
+        t->streams < 1 || t->streams > 64)
+        return bfail(b, HYB_EINVAL, "tuning out of range (block 128|256, chunk >= 32, streams 1..64)");
+    b->tune = *t;
+    drop_graphs(b);
+    for (auto s : b->pool) cudaStreamDestroy(s);
+    for (auto e : b->join_ev) cudaEventDestroy(e);
+    b->pool.clear(); b->join_ev.clear();
+    for (int j = 0; j < t->streams; ++j) {
+        cudaStream_t s; cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bfail(b, HYB_ECUDA, "stream");
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bfail(b, HYB_ECUDA, "event");
+        b->pool.push_back(s); b->join_ev.push_back(e);
+    }
+    return build_chunks(b);
+}
+
+HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* per_problem) {
+    if (!b || nsteps < 0) return bfail(b, HYB_EINVAL, "bad arguments");
+    const size_t n = b->probs.size();
+    for (int32_t it = 0; it < nsteps; ++it) {
+        const int q = b->parity;
+        if (!b->exec[q][0] || !b->exec[q][1]) {
+            hyb_status s = capture(b, q);
+            if (s != HYB_OK) return s;
+        }
+        if (cudaEventRecord(b->ev0, b->s0) != cudaSuccess || cudaGraphLaunch(b->exec[q][0], b->s0) != cudaSuccess ||
+            cudaStreamSynchronize(b->s0) != cudaSuccess)
+            return bfail(b, HYB_ECUDA, "graph launch (leg and source iteration)");
+        bool recapture = false;
+        for (size_t i = 0; i < n; ++i) {
+            if (b->h_report[i].sn_conv) continue;
+            hyb_status s = finish_iterations(b, q, i);
+            if (s != HYB_OK) return s;
+            b->kmax[i] = std::min(b->probs[i]->d.sn_max_iter, std::max(2 * b->kmax[i], b->probs[i]->st_host->sn_iters + 2));
+            recapture = true;
+        }
+        if (cudaGraphLaunch(b->exec[q][1], b->s0) != cudaSuccess || cudaEventRecord(b->ev1, b->s0) != cudaSuccess ||
+            cudaStreamSynchronize(b->s0) != cudaSuccess)
+            return bfail(b, HYB_ECUDA, "graph launch (remap)");
+        b->parity ^= 1;
+        hyb_status bad = HYB_OK;
+        for (size_t i = 0; i < n; ++i) {
+            hyb_problem* p = b->probs[i];
+            const hyb::DevState& r = b->h_report[i];
+            p->cur ^= 1;
+            p->step += 1;
+            p->last_sn_iters = r.sn_iters;
+            p->sn_warm = p->d.sn_warm_start != 0;
+            p->leg_done = p->sn_done = false;
+            if (r.status & hyb::kStBounds) bad = HYB_EBOUNDS;
+            else if ((r.status & hyb::kStSegments) && bad == HYB_OK) bad = HYB_ETIMEOUT;
+        }
+        if (recapture) drop_graphs(b);
+        if (bad != HYB_OK) return bfail(b, bad, "a problem of the batch reported a device check failure");
+    }
+    if (per_problem) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+        for (size_t i = 0; i < n; ++i) {
+            hyb_problem* p = b->probs[i];
+            const hyb::DevState& h = b->h_report[i];
+            hyb_leg_stats& s = per_problem[i];
+            std::memset(&s, 0, sizeof(s));
+            s.histories = (int64_t)h.histories; s.segments = (int64_t)h.segments; s.collisions = (int64_t)h.collisions;
+            s.leaked = (int64_t)h.leaked; s.census = (int64_t)h.census; s.killed = (int64_t)h.killed;
+            s.reached_limit = (int64_t)h.reached; s.errors = (int64_t)h.errors;
+            const double iw = std::ldexp(1.0, -h.k_w);
+            s.w_source = hyb::acc128_to_double(h.w_source.lo, h.w_source.hi, iw);
+            s.w_absorbed = hyb::acc128_to_double(h.w_absorbed.lo, h.w_absorbed.hi, iw);
+            s.w_leaked = hyb::acc128_to_double(h.w_leaked.lo, h.w_leaked.hi, iw);
+            s.w_census = hyb::acc128_to_double(h.w_census.lo, h.w_census.hi, iw);
+            s.w_handoff = hyb::acc128_to_double(h.w_handoff.lo, h.w_handoff.hi, iw);
+            s.w_killed = hyb::acc128_to_double(h.w_killed.lo, h.w_killed.hi, iw);
+            s.sn_iterations = h.sn_iters;
+            s.combed = h.comb_on;
+            s.bank_size = h.n_bank;
+            s.ms = ms;
+            (void)p;
+        }
+    }
+    return HYB_OK;
+}
+
+HYB_API hyb_status hyb_batch_destroy(hyb_batch* b) {
+    if (!b) return HYB_OK;
+    if (b->s0) cudaStreamSynchronize(b->s0); else cudaDeviceSynchronize();
+    drop_graphs(b);
+    for (auto s : b->pool) cudaStreamDestroy(s);
+    for (auto e : b->join_ev) cudaEventDestroy(e);
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    for (int q = 0; q < 2; ++q) if (b->d_args[q]) cudaFree(b->d_args[q]);
+    if (b->d_chunks) cudaFree(b->d_chunks);
+    if (b->d_head) cudaFree(b->d_head);
+    if (b->d_report) cudaFree(b->d_report);
+    if (b->h_report) cudaFreeHost(b->h_report);
+    if (b->d_V) cudaFree(b->d_V);
+    if (b->own_s0 && b->s0) cudaStreamDestroy(b->s0);
+    delete b;
+    return HYB_OK;
+}
+
+HYB_API const char* hyb_batch_last_error(const hyb_batch* b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+}  // extern "C"

@@ -21,11 +21,7 @@ namespace hyb {
 
 uint64_t mix64(uint64_t z) { return dmix64(z); }
 
-uint64_t stream_key(uint64_t seed, uint64_t step, uint64_t stream) {
-    uint64_t z = dmix64(seed + kGamma);
-    z = dmix64(z ^ (step + kGamma));
-    return dmix64(z ^ (stream + kGamma));
-}
+uint64_t stream_key(uint64_t seed, uint64_t step, uint64_t stream) { return dstream_key(seed, step, stream); }
 
 // ---------------------------------------------------------------------------------------------
 // Sobol direction numbers
@@ -450,6 +446,10 @@ static hyb_status set_bank_t(hyb_problem* p, const int32_t* cell, const double* 
 
 using namespace hybh;
 
+namespace hyb {
+double sn_tol_eff(const hyb_problem* p) { return p->prec == HYB_FP64 ? p->d.sn_tol : std::max(p->d.sn_tol, 2e-6); }
+}  // namespace hyb
+
 extern "C" {
 
 const char* hyb_status_string(hyb_status s) {
@@ -636,24 +636,27 @@ hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
     if (!p->leg_done) return fail(p, HYB_ESTATE, "collided solve needs an MC leg of this step");
     HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
     HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
-    const double tol = p->prec == HYB_FP64 ? p->d.sn_tol : std::max(p->d.sn_tol, 2e-6);
-    int it = 0;
+    HYB_CU(p, sn_start(p));
     // with a warm start the previous step's count predicts this one: the first (count - 2)
-    // iterations run without a convergence read-back
+    // iterations run without a convergence read-back; converged iterations return at once
     const int unchecked = (p->sn_warm && p->last_sn_iters > 2) ? p->last_sn_iters - 2 : 0;
+    int it = 0;
+    bool conv = false;
     for (it = 1; it <= p->d.sn_max_iter; ++it) {
         HYB_CU(p, sn_iteration(p, it == 1));
         if (it <= unchecked) continue;
-        HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_norm_num, &p->st->sn_norm_num, 2 * sizeof(double),
-                                  cudaMemcpyDeviceToHost, p->stream));
+        HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_conv, &p->st->sn_conv, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                                  p->stream));
         HYB_CU(p, cudaStreamSynchronize(p->stream));
-        const double num = p->st_host->sn_norm_num, den = p->st_host->sn_norm_den;
-        if (den == 0.0 || std::sqrt(num) <= tol * std::sqrt(den)) break;
+        if (p->st_host->sn_conv) { conv = true; break; }
     }
+    (void)conv;
     HYB_CU(p, cudaMemcpyAsync(&p->st_host->status, &p->st->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+    HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_conv, &p->st->sn_conv, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+                              p->stream));
     HYB_CU(p, cudaStreamSynchronize(p->stream));
     if (p->st_host->status & kStSegments) return fail(p, HYB_ETIMEOUT, "S_N sweep pipeline wait exhausted");
-    if (it > p->d.sn_max_iter) it = p->d.sn_max_iter;
+    it = p->st_host->sn_iters;
     HYB_CU(p, sn_finish(p));
     HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
     p->last_sn_iters = it;
@@ -678,7 +681,7 @@ hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* out) {
     HYB_CU(p, launch_remap(p));
     HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
     p->cur = 1 - p->cur;
-    p->step += 1;
+    p->step += 1;           // the remap's last kernel advances the device step
     p->leg_done = p->sn_done = false;
     if (out) {
         hyb_status s = pull_state(p);
@@ -778,6 +781,9 @@ hyb_status hyb_bank_capacity(const hyb_problem* p, int64_t* cap) {
 hyb_status hyb_set_step(hyb_problem* p, int64_t step) {
     if (!p || step < 0) return fail(p, HYB_EINVAL, "bad arguments");
     p->step = step;
+    p->st_host->step = step;
+    HYB_CU(p, cudaMemcpyAsync(&p->st->step, &p->st_host->step, sizeof(long long), cudaMemcpyHostToDevice, p->stream));
+    HYB_CU(p, cudaStreamSynchronize(p->stream));
     p->leg_done = p->sn_done = false;
     return HYB_OK;
 }

@@ -37,6 +37,19 @@ __host__ __device__ __forceinline__ uint32_t dshift(uint64_t key, uint64_t d) {
     return (uint32_t)(dmix64(key ^ (d + kGamma)) >> 32);
 }
 
+// key of the point set (seed, step, stream)
+__host__ __device__ __forceinline__ uint64_t dstream_key(uint64_t seed, uint64_t step, uint64_t stream) {
+    uint64_t z = dmix64(seed + kGamma);
+    z = dmix64(z ^ (step + kGamma));
+    return dmix64(z ^ (stream + kGamma));
+}
+
+// first point of a set (index 0, dimension 0): Sobol(0) = 0 leaves the shift; else the hash
+__host__ __device__ __forceinline__ uint32_t first_point(uint64_t key, int sampler) {
+    return sampler == HYB_SOBOL_DS ? dshift(key, 0)
+                                   : (uint32_t)(dmix64(dmix64(key ^ (0ull + kGamma)) ^ (0ull + kGamma)) >> 32);
+}
+
 // A point set in shared memory: Sobol direction numbers (ntab dims x 32) and per-dimension
 // digital shifts; dimensions beyond the table (or sampler == PRNG) use the counter hash.
 struct Points {
@@ -81,6 +94,8 @@ template <> struct Prec<float> {
     // exact-order a*b + c (FP32 path: contraction allowed)
     static __device__ __forceinline__ float madd(float a, float b, float c) { return fmaf(a, b, c); }
     static __device__ __forceinline__ float msub(float c, float a, float b) { return fmaf(-a, b, c); }
+    // a*b + c with one rounding, spelled out so every inlined copy evaluates it the same way
+    static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
     static __device__ __forceinline__ void add(acc_t* p, float c, float scale) {
         const long long v = __float2ll_rn(c * scale);
         if (v) atomicAdd(p, (unsigned long long)v);
@@ -182,6 +197,7 @@ template <> struct Prec<double> {
     // separately rounded product and sum: FP64 geometry follows IEEE order exactly
     static __device__ __forceinline__ double madd(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
     static __device__ __forceinline__ double msub(double c, double a, double b) { return __dsub_rn(c, __dmul_rn(a, b)); }
+    static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
     static __device__ __forceinline__ void add(acc_t* p, double c, double scale) {
         unsigned long long lo, hi;
         to_i128(c * scale, &lo, &hi);
@@ -223,7 +239,7 @@ __device__ __forceinline__ void gfun(T x, T* g0, T* g1, T* g2) {
         const T e = Prec<T>::ex(-x);
         *g0 = -Prec<T>::exm1(-x) / x;
         *g1 = (*g0 - e) / x;
-        *g2 = (T(2) * *g1 - e) / x;
+        *g2 = Prec<T>::fma_(T(2), *g1, -e) / x;
     }
 }
 

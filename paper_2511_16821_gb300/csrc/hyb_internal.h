@@ -51,7 +51,11 @@ struct DevState {
     int k_rw;                  // scale exponent of the remap weight sums
     Acc128 bank_wsum_acc;      // scratch of the bank-statistics kernels
     long long out_count;       // particles written by the last remap
-    int pad[2];
+    long long step;            // time-step index n of the next MC leg / remap (t_n = n dt)
+    int sn_conv;               // collided solve: converged flag of the current solve
+    int sn_iters;              // collided solve: iterations run in the current solve
+    int sn_warm;               // 1 once a solve finished and warm starts are enabled
+    int pad2;
 };
 
 template <typename T>
@@ -126,7 +130,15 @@ cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0);
 cudaError_t launch_bank_stats(hyb_problem* p);
 cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,
                           uint32_t* out, cudaStream_t s);
+size_t leg_args_bytes(int prec);
+void leg_args_host(hyb_problem* p, int cur, void* out);
+int leg_ntab(const hyb_problem* p);
+cudaError_t launch_mc_leg_batch(int prec, const void* d_args, const void* d_chunks, int nchunks, int* d_head,
+                                const uint32_t* V, int ntab_max, int grid, int block, cudaStream_t s);
+int leg_batch_ctas_per_sm(int prec);
+cudaError_t sn_start(hyb_problem* p);
 cudaError_t sn_iteration(hyb_problem* p, int first);
+double sn_tol_eff(const hyb_problem* p);
 cudaError_t sn_finish(hyb_problem* p);
 
 // host helpers (host.cu)

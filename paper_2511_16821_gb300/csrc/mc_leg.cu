@@ -24,7 +24,7 @@ struct LegArgs {
     int n_s, sampler, handoff_full, ntab;
     T w_min;
     const uint32_t* V;
-    uint64_t key_c, key_s;
+    uint64_t seed;              // keys of the census and source point sets come from (seed, step)
     BankView<T> bank;
     Cdf2DView cdf;
     long long n_src;
@@ -45,47 +45,54 @@ struct Hist {
     bool census_stream;
 };
 
-// Refilled-lane leg: each warp owns a contiguous slice of [bank slots | births]; a lane whose
-// history ends takes the next index of the slice at once (ranks by ballot, deterministic order),
-// so the warp keeps all lanes on segments instead of waiting for its longest history. Weight
-// totals of each finished history go to int64 fixed point (order-free, deterministic).
+// Per-thread statistics of the histories a thread finished (integers: order-free sums).
+struct LegTally {
+    unsigned long long c[8];   // histories, segments, collisions, leaked, census, killed, reached, errors
+    long long f[6];            // fixed-point weights: source, absorbed, leaked, census, handoff, killed
+    int status;
+};
+
+__device__ __forceinline__ void leg_tally_zero(LegTally& t) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t.c[q] = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) t.f[q] = 0;
+    t.status = 0;
+}
+
+// Scales of one leg (fixed point of the tallies and of the weight totals).
+struct LegScales {
+    int kt, km, kw;
+    double scw;
+};
+
 template <typename T>
-__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(LegArgs<T> a) {
-    using P = Prec<T>;
-    extern __shared__ uint32_t sm[];
-    uint32_t* sV = sm;
-    uint32_t* sShC = sm + a.ntab * 32;
-    uint32_t* sShS = sShC + a.ntab;
-    for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
-    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) {
-        sShC[d] = dshift(a.key_c, (uint64_t)d);
-        sShS[d] = dshift(a.key_s, (uint64_t)d);
-    }
-    __syncthreads();
-
-    const long long nb = a.st->n_bank;
-    const long long N = nb + a.n_src;
+__device__ __forceinline__ LegScales leg_scales(const LegArgs<T>& a) {
     const double Wstep = a.st->bank_wsum + a.w_src_total;
-    const int kt = scale_exponent(Wstep * a.cdt_d, P::kbits);
-    const int km = scale_exponent(Wstep * a.cdt_d * a.sig_s_max, P::kbits);
-    const T sc_t = (T)ldexp(1.0, kt), sc_m = (T)ldexp(1.0, km);
-    const int kw = scale_exponent(Wstep, 61);
-    const double scw = ldexp(1.0, kw);
+    LegScales s;
+    s.kt = scale_exponent(Wstep * a.cdt_d, Prec<T>::kbits);
+    s.km = scale_exponent(Wstep * a.cdt_d * a.sig_s_max, Prec<T>::kbits);
+    s.kw = scale_exponent(Wstep, 61);
+    s.scw = ldexp(1.0, s.kw);
+    return s;
+}
 
-    unsigned long long c_hist = 0, c_seg = 0, c_col = 0, c_leak = 0, c_cen = 0, c_kill = 0, c_reach = 0, c_err = 0;
-    long long f_src = 0, f_abs = 0, f_leak = 0, f_cen = 0, f_hand = 0, f_kill = 0;
-    int status = 0;
+// The histories [next, last) of one problem, tracked by the calling warp with lane refill: a lane
+// whose history ends takes the next index at once (ranks by ballot, deterministic order), so the
+// warp keeps its lanes on segments instead of waiting for its longest history.
+template <typename T>
+__device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long last, long long nb,
+                               const uint32_t* sV, const uint32_t* sShC, const uint32_t* sShS, uint64_t key_c,
+                               uint64_t key_s, const LegScales& sc, LegTally& t) {
+    using P = Prec<T>;
+    const T sc_t = (T)ldexp(1.0, sc.kt), sc_m = (T)ldexp(1.0, sc.km);
+    const double scw = sc.scw;
     const T DX = a.dx, DY = a.dy;
     const T INF = (T)INFINITY;
     const int Ns = a.n_s;
     const int nx = a.nx, ny = a.ny;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long per = (N + nwarps - 1) / nwarps;
-    long long next = wid * per;
-    const long long last = next + per < N ? next + per : N;
 
     Points pts;
     pts.V = sV;
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
                     h.idx = (uint32_t)j;
                     h.census_stream = true;
                     const int k = a.bank.cell[j];
-                    if (k < 0 || k >= nx * ny) { status |= kStBounds; ok = false; }
+                    if (k < 0 || k >= nx * ny) { t.status |= kStBounds; ok = false; }
                     else {
                         h.ix = k % nx; h.iy = k / nx;
                         h.fx = a.bank.fx[j]; h.fy = a.bank.fy[j];
@@ -119,7 +126,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
                 } else {
                     h.idx = (uint32_t)(j - nb);
                     h.census_stream = false;
-                    pts.key = a.key_s; pts.shift = sShS;
+                    pts.key = key_s; pts.shift = sShS;
                     T frx, fry;
                     const int k = sample_cell<T>(a.cdf, nx, ny, pts(h.idx, 0), pts(h.idx, 1), &frx, &fry);
                     h.ix = k % nx; h.iy = k / nx;
@@ -129,15 +136,15 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
                     h.srem = a.cdt * P::unit_c(pts(h.idx, 2));
                 }
                 if (ok) {
-                    pts.key = h.census_stream ? a.key_c : a.key_s;
+                    pts.key = h.census_stream ? key_c : key_s;
                     pts.shift = h.census_stream ? sShC : sShS;
-                    ++c_hist;
+                    ++t.c[0];
                     h.w_start = h.w;
-                    f_src += __double2ll_rn((double)h.w * scw);
+                    t.f[0] += __double2ll_rn((double)h.w * scw);
                     d_abs = 0; d_hand = 0;
                     h.n = 0;
                     h.seg = 0;
-                    if (Ns == 0) ++c_reach;
+                    if (Ns == 0) ++t.c[6];
                     h.tau = Ns > 0 ? P::neglog(P::unit(pts(h.idx, 5))) : T(0);
                     alive = true;
                 }
@@ -145,7 +152,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
         }
         if (!__any_sync(0xffffffffu, alive)) break;
         if (!alive) continue;
-        pts.key = h.census_stream ? a.key_c : a.key_s;
+        pts.key = h.census_stream ? key_c : key_s;
         pts.shift = h.census_stream ? sShC : sShS;
 
         // ---- one segment ----------------------------------------------------------------------
@@ -181,10 +188,12 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
                 if (a.handoff_full) {
                     const T xi0 = T(2) * h.fx / DX - T(1), eta0 = T(2) * h.fy / DY - T(1);
                     const T axi = T(2) * h.ox / DX, aeta = T(2) * h.oy / DY;
-                    P::add(&a.mom[4 * k + 1], sw * (xi0 * I0 + axi * I1), sc_m);
-                    P::add(&a.mom[4 * k + 2], sw * (eta0 * I0 + aeta * I1), sc_m);
+                    // explicit fused forms: the same rounding in every kernel this is inlined into
+                    P::add(&a.mom[4 * k + 1], sw * P::fma_(xi0, I0, axi * I1), sc_m);
+                    P::add(&a.mom[4 * k + 2], sw * P::fma_(eta0, I0, aeta * I1), sc_m);
                     P::add(&a.mom[4 * k + 3],
-                           sw * (xi0 * eta0 * I0 + (xi0 * aeta + eta0 * axi) * I1 + axi * aeta * I2), sc_m);
+                           sw * P::fma_(xi0 * eta0, I0, P::fma_(P::fma_(xi0, aeta, eta0 * axi), I1, axi * aeta * I2)),
+                           sc_m);
                 }
             }
             if (st > T(0)) {
@@ -213,24 +222,24 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
         } else {
             h.fx = clamp_(h.fx, T(0), DX);
             h.fy = clamp_(h.fy, T(0), DY);
-            ++h.n; ++c_col;
+            ++h.n; ++t.c[2];
             const int base = 5 + 3 * (h.n - 1);
             iso_dir<T>(pts(h.idx, base + 1), pts(h.idx, base + 2), &h.ox, &h.oy);
             if (h.n < Ns) h.tau = P::neglog(P::unit(pts(h.idx, 5 + 3 * h.n)));
-            else { h.tau = T(0); ++c_reach; }
+            else { h.tau = T(0); ++t.c[6]; }
         }
         if (fate < 0 && a.w_min > T(0) && h.w < a.w_min * h.w_start) fate = kFateKilled;
         if (fate < 0 && h.seg >= (int)kMaxSegments) fate = kFateError;
         if (fate >= 0) {
             // ---- end of the history ------------------------------------------------------------
             const long long fw = __double2ll_rn((double)h.w * scw);
-            if (fate == kFateCensus) { ++c_cen; f_cen += fw; }
-            else if (fate == kFateLeaked) { ++c_leak; f_leak += fw; }
-            else if (fate == kFateKilled) { ++c_kill; f_kill += fw; }
-            else { ++c_err; status |= kStSegments; }
-            f_abs += __double2ll_rn(d_abs * scw);
-            f_hand += __double2ll_rn(d_hand * scw);
-            c_seg += (unsigned long long)h.seg;
+            if (fate == kFateCensus) { ++t.c[4]; t.f[3] += fw; }
+            else if (fate == kFateLeaked) { ++t.c[3]; t.f[2] += fw; }
+            else if (fate == kFateKilled) { ++t.c[5]; t.f[5] += fw; }
+            else { ++t.c[7]; t.status |= kStSegments; }
+            t.f[1] += __double2ll_rn(d_abs * scw);
+            t.f[4] += __double2ll_rn(d_hand * scw);
+            t.c[1] += (unsigned long long)h.seg;
             if (a.hist) {
                 const int4 r = make_int4(h.iy * nx + h.ix, fate, h.n, h.seg);
                 reinterpret_cast<int4*>(a.hist)[h.j] = r;
@@ -238,38 +247,121 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
             alive = false;
         }
     }
+}
 
-    // block reduction of the statistics (integers: order-free)
+// Block reduction of the per-thread statistics into the problem's counters (all threads call).
+__device__ void leg_flush(DevState* st, LegTally& t, const LegScales& sc, bool write_scales) {
     __shared__ unsigned long long s_c[kTile / 32][14];
-    const int wl = threadIdx.x >> 5;
-    unsigned long long cs[14] = {c_hist, c_seg, c_col, c_leak, c_cen, c_kill, c_reach, c_err,
-                                 (unsigned long long)f_src, (unsigned long long)f_abs, (unsigned long long)f_leak,
-                                 (unsigned long long)f_cen, (unsigned long long)f_hand, (unsigned long long)f_kill};
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    unsigned long long cs[14];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cs[q] = t.c[q];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) cs[8 + q] = (unsigned long long)t.f[q];
 #pragma unroll
     for (int q = 0; q < 14; ++q) cs[q] = warp_sum_u64(cs[q]);
     if (lane == 0)
         for (int q = 0; q < 14; ++q) s_c[wl][q] = cs[q];
-    if (status) atomicOr(&a.st->status, status);
+    if (t.status) atomicOr(&st->status, t.status);
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long* cdst[8] = {&a.st->histories, &a.st->segments, &a.st->collisions, &a.st->leaked,
-                                       &a.st->census, &a.st->killed, &a.st->reached, &a.st->errors};
-        Acc128* wdst[6] = {&a.st->w_source, &a.st->w_absorbed, &a.st->w_leaked, &a.st->w_census,
-                           &a.st->w_handoff, &a.st->w_killed};
+        unsigned long long* cdst[8] = {&st->histories, &st->segments, &st->collisions, &st->leaked,
+                                       &st->census, &st->killed, &st->reached, &st->errors};
+        Acc128* wdst[6] = {&st->w_source, &st->w_absorbed, &st->w_leaked, &st->w_census,
+                           &st->w_handoff, &st->w_killed};
+        const int nw = (int)(blockDim.x >> 5);
         for (int q = 0; q < 14; ++q) {
             unsigned long long v = 0;
-            for (int ww = 0; ww < kTile / 32; ++ww) v += s_c[ww][q];
+            for (int ww = 0; ww < nw; ++ww) v += s_c[ww][q];
             if (q < 8) { if (v) atomicAdd(cdst[q], v); }
-            else {
+            else if (v) {
                 const long long sv = (long long)v;
                 atomic_add128(wdst[q - 8], (unsigned long long)sv, sv < 0 ? ~0ull : 0ull);
             }
         }
-        if (blockIdx.x == 0) {
-            a.st->k_track = kt;
-            a.st->k_mom = km;
-            a.st->k_w = kw;
+        if (write_scales) {
+            st->k_track = sc.kt;
+            st->k_mom = sc.km;
+            st->k_w = sc.kw;
         }
+    }
+    __syncthreads();
+}
+
+// Single problem: the grid's warps split [bank slots | births] into contiguous slices.
+template <typename T>
+__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(LegArgs<T> a) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* sV = sm;
+    uint32_t* sShC = sm + a.ntab * 32;
+    uint32_t* sShS = sShC + a.ntab;
+    const uint64_t step = (uint64_t)a.st->step;
+    const uint64_t key_c = dstream_key(a.seed, step, HYB_STREAM_LEG_CENSUS);
+    const uint64_t key_s = dstream_key(a.seed, step, HYB_STREAM_LEG_SOURCE);
+    for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
+    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) {
+        sShC[d] = dshift(key_c, (uint64_t)d);
+        sShS[d] = dshift(key_s, (uint64_t)d);
+    }
+    __syncthreads();
+    const long long nb = a.st->n_bank;
+    const long long N = nb + a.n_src;
+    const LegScales sc = leg_scales<T>(a);
+    LegTally t;
+    leg_tally_zero(t);
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long per = (N + nwarps - 1) / nwarps;
+    const long long j0 = wid * per;
+    const long long j1 = j0 + per < N ? j0 + per : N;
+    leg_warp_range<T>(a, j0, j1, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+    leg_flush(a.st, t, sc, blockIdx.x == 0);
+}
+
+// Many problems: a persistent grid pulls (problem, [j0, j1)) chunks from a work queue; per chunk
+// the CTA's warps split the range, then flush the chunk's statistics to its problem.
+struct LegChunk { int p; int pad; long long j0, j1; };
+
+template <typename T>
+__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2)
+mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restrict__ chunks, int nchunks,
+                    int* head, const uint32_t* V, int ntab_max) {
+    extern __shared__ uint32_t sm[];
+    uint32_t* sV = sm;
+    uint32_t* sShC = sm + ntab_max * 32;
+    uint32_t* sShS = sShC + ntab_max;
+    __shared__ int s_chunk;
+    for (int i = threadIdx.x; i < ntab_max * 32; i += blockDim.x) sV[i] = V[i];
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_chunk = atomicAdd(head, 1);
+        __syncthreads();
+        const int c = s_chunk;
+        if (c >= nchunks) break;
+        const LegChunk ch = chunks[c];
+        const LegArgs<T> a = args[ch.p];
+        const uint64_t step = (uint64_t)a.st->step;
+        const uint64_t key_c = dstream_key(a.seed, step, HYB_STREAM_LEG_CENSUS);
+        const uint64_t key_s = dstream_key(a.seed, step, HYB_STREAM_LEG_SOURCE);
+        for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) {
+            sShC[d] = dshift(key_c, (uint64_t)d);
+            sShS[d] = dshift(key_s, (uint64_t)d);
+        }
+        __syncthreads();
+        const long long nb = a.st->n_bank;
+        const long long N = nb + a.n_src;
+        const long long e = ch.j1 < N ? ch.j1 : N;
+        const LegScales sc = leg_scales<T>(a);
+        LegTally t;
+        leg_tally_zero(t);
+        if (ch.j0 < e) {
+            const long long nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+            const long long per = (e - ch.j0 + nw - 1) / nw;
+            const long long j0 = ch.j0 + w * per;
+            const long long j1 = j0 + per < e ? j0 + per : e;
+            leg_warp_range<T>(a, j0, j1, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+        }
+        leg_flush(a.st, t, sc, ch.j0 == 0);
     }
 }
 
@@ -379,7 +471,7 @@ static int leg_grid(long long work) {
 }
 
 template <typename T>
-static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
+LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     LegArgs<T> a;
     a.nx = p->nx; a.ny = p->ny;
     a.dx = (T)p->dx; a.dy = (T)p->dy;
@@ -390,9 +482,8 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
     a.ntab = p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS;
     a.w_min = (T)p->d.w_min;
     a.V = p->sobolV;
-    a.key_c = stream_key(p->d.seed, (uint64_t)p->step, HYB_STREAM_LEG_CENSUS);
-    a.key_s = stream_key(p->d.seed, (uint64_t)p->step, HYB_STREAM_LEG_SOURCE);
-    a.bank = bank_view<T>(p, p->cur);
+    a.seed = p->d.seed;
+    a.bank = bank_view<T>(p, cur);
     a.cdf = p->src_cdf;
     a.n_src = p->has_src ? p->d.n_hist : 0;
     a.w0 = (T)(p->has_src ? p->w_src / (double)p->d.n_hist : 0.0);
@@ -403,9 +494,38 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
     a.hist = hist;
     a.sig_s_max = p->sig_s_max;
     a.w_src_total = p->has_src ? p->w_src : 0.0;
+    return a;
+}
+
+template <typename T>
+static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
+    const LegArgs<T> a = leg_args<T>(p, hist, p->cur);
     const size_t smem = (size_t)(a.ntab * 32 + 2 * a.ntab) * sizeof(uint32_t);
     const long long work = p->bank_cap + a.n_src;
     mc_leg_kernel<T><<<leg_grid(work), kTile, smem, p->stream>>>(a);
+    return cudaGetLastError();
+}
+
+size_t leg_args_bytes(int prec) { return prec == HYB_FP64 ? sizeof(LegArgs<double>) : sizeof(LegArgs<float>); }
+
+void leg_args_host(hyb_problem* p, int cur, void* out) {
+    if (p->prec == HYB_FP64) *(LegArgs<double>*)out = leg_args<double>(p, nullptr, cur);
+    else *(LegArgs<float>*)out = leg_args<float>(p, nullptr, cur);
+}
+
+int leg_ntab(const hyb_problem* p) { return p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS; }
+
+int leg_batch_ctas_per_sm(int prec) { return prec == HYB_FP64 ? 2 : 3; }
+
+cudaError_t launch_mc_leg_batch(int prec, const void* d_args, const void* d_chunks, int nchunks, int* d_head,
+                                const uint32_t* V, int ntab_max, int grid, int block, cudaStream_t s) {
+    const size_t smem = (size_t)(ntab_max * 32 + 2 * ntab_max) * sizeof(uint32_t);
+    if (prec == HYB_FP64)
+        mc_leg_batch_kernel<double><<<grid, block, smem, s>>>((const LegArgs<double>*)d_args,
+                                                             (const LegChunk*)d_chunks, nchunks, d_head, V, ntab_max);
+    else
+        mc_leg_batch_kernel<float><<<grid, block, smem, s>>>((const LegArgs<float>*)d_args,
+                                                            (const LegChunk*)d_chunks, nchunks, d_head, V, ntab_max);
     return cudaGetLastError();
 }
 

@@ -216,8 +216,7 @@ struct RemapArgs {
     long long n_hist, cap;
     const uint32_t* V;
     int ntab, sampler;
-    uint64_t key;
-    uint32_t x_off;
+    uint64_t seed;             // keys of the birth and comb point sets come from (seed, step)
     DevState* st;
     long long* blk;            // per block: alive count, sum q, sum|w| lo, sum|w| hi
 };
@@ -322,10 +321,11 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
     uint32_t* sSh = sm + a.ntab * 32;
+    const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_REMAP_SOURCE);
     for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
-    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(a.key, (uint64_t)d);
+    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
     __syncthreads();
-    Points pts{sV, sSh, a.key, a.sampler, a.ntab};
+    Points pts{sV, sSh, key, a.sampler, a.ntab};
     const long long nb = a.st->n_bank;
     const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
     const long long N = nb + nbirth;
@@ -402,8 +402,9 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
 }
 
 // one block: exclusive scan of block counts and quantised sums; totals, comb decision
-__global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long long cap, uint32_t x_off,
+__global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long long cap, uint64_t seed, int sampler,
                                   long long n_hist) {
+    const uint32_t x_off = first_point(dstream_key(seed, (uint64_t)st->step, HYB_STREAM_REMAP_COMB), sampler);
     __shared__ long long sc[1024], sq[1024];
     __shared__ unsigned long long slo[1024], shi[1024];
     const int t = threadIdx.x, nt = blockDim.x;
@@ -554,6 +555,7 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
 
 __global__ void remap_finish_kernel(DevState* st) {
     st->n_bank = st->out_count;
+    st->step += 1;              // census of t_{n+1}: the next leg belongs to step n + 1
 }
 
 template <typename T>
@@ -585,10 +587,7 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.V = p->sobolV;
     a.ntab = p->d.sampler == HYB_SOBOL_DS ? 5 : 0;
     a.sampler = p->d.sampler;
-    a.key = stream_key(p->d.seed, (uint64_t)p->step, HYB_STREAM_REMAP_SOURCE);
-    const uint64_t kc = stream_key(p->d.seed, (uint64_t)p->step, HYB_STREAM_REMAP_COMB);
-    a.x_off = p->d.sampler == HYB_SOBOL_DS ? dshift(kc, 0)
-                                           : (uint32_t)(dmix64(dmix64(kc ^ (0ull + kGamma)) ^ (0ull + kGamma)) >> 32);
+    a.seed = p->d.seed;
     a.st = p->st;
     a.blk = p->blk;
     const long long maxN = p->bank_cap + p->d.n_hist;
@@ -605,7 +604,7 @@ static cudaError_t remap_t(hyb_problem* p) {
                         (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
     if (e != cudaSuccess) return e;
     remap_count_kernel<T><<<nblk, kTile, smem, s>>>(a);
-    remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nblk, p->st, a.cap, a.x_off, p->d.n_hist);
+    remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nblk, p->st, a.cap, a.seed, a.sampler, p->d.n_hist);
     remap_write_kernel<T><<<nblk, kTile, 0, s>>>(a);
     remap_finish_kernel<<<1, 1, 0, s>>>(p->st);
     return cudaGetLastError();

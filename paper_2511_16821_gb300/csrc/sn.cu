@@ -32,6 +32,7 @@ struct SweepArgs {
     const T* qox; const T* qoy; const T* qw;   // ordinates by quadrant: m = quad * nq + q
     T* psi;                  // per ordinate and cell: w_m psi (4 Legendre coefficients)
     int* status;             // device status word (bounded waits)
+    const int* conv;         // converged flag: set -> the sweep returns at once
 };
 
 // source integrals against P_i: sigma_s A n_i phi_i / (4 pi) + m_i / (4 pi dt)
@@ -93,6 +94,7 @@ __device__ __forceinline__ void solve_mirrored(T sA, T X, T Y, const T b[4], T a
 // to lower strips, and all warps of the CTA are resident, so the pipeline always advances.
 template <typename T>
 __global__ void sweep_pipe_kernel(SweepArgs<T> a) {
+    if (*(volatile const int*)a.conv) return;
     extern __shared__ unsigned char smraw[];
     const int W = a.W;
     volatile int* prod = (volatile int*)smraw;
@@ -195,8 +197,14 @@ __global__ void sweep_pipe_kernel(SweepArgs<T> a) {
 // iteration's source integrals from phi_new
 template <typename T>
 __global__ void sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, double* part,
-                                 const T* sig, const double* mom, T area, T inv_4pi_dt, T* src) {
+                                 const T* sig, const double* mom, T area, T inv_4pi_dt, T* src, const int* conv) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (*(volatile const int*)conv) {
+        // converged earlier: carry the solution forward so the buffer alternation stays aligned
+        if (k < ncells)
+            for (int i = 0; i < 4; ++i) phi_new[4 * (size_t)k + i] = phi_old[4 * (size_t)k + i];
+        return;
+    }
     double num = 0, den = 0;
     if (k < ncells) {
         const double nrm[4] = {1.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0};
@@ -226,7 +234,9 @@ __global__ void sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* ph
     }
 }
 
-__global__ void sn_norm_final_kernel(const double* part, int nparts, DevState* st) {
+// SI stop test on the device: ||phi_new - phi_old|| <= tol ||phi_new|| (or no source at all)
+__global__ void sn_norm_final_kernel(const double* part, int nparts, DevState* st, double tol) {
+    if (*(volatile int*)&st->sn_conv) return;
     double a = 0, b = 0;
     for (int i = threadIdx.x; i < nparts; i += 32) { a += part[2 * i]; b += part[2 * i + 1]; }
     a = warp_sum(a);
@@ -234,8 +244,20 @@ __global__ void sn_norm_final_kernel(const double* part, int nparts, DevState* s
     if (threadIdx.x == 0) {
         st->sn_norm_num = a;
         st->sn_norm_den = b;
+        st->sn_iters += 1;
+        if (b == 0.0 || sqrt(a) <= tol * sqrt(b)) st->sn_conv = 1;
     }
 }
+
+// start of a solve: clear the stop state; the iterate starts from the previous solution
+// (warm start, re-read from its FP64 copy) or from zero
+template <typename T>
+__global__ void sn_seed_kernel(const double* prev, T* phi, int n, const DevState* st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) phi[i] = st->sn_warm ? (T)prev[i] : T(0);
+}
+
+__global__ void sn_done_kernel(DevState* st, int warm) { st->sn_warm = warm; }
 
 template <typename T>
 __global__ void sn_to_double_kernel(const T* phi, double* out, int n) {
@@ -274,6 +296,7 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     a.qox = qbuf; a.qoy = qbuf + kMaxOrd; a.qw = qbuf + 2 * kMaxOrd;
     a.psi = (T*)p->sn_psi;
     a.status = &p->st->status;
+    a.conv = &p->st->sn_conv;
     size_t smem = 0;
     a.W = sweep_warps<T>(p, &smem);
     if (smem > 48 * 1024) {
@@ -283,17 +306,23 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     sweep_pipe_kernel<T><<<p->n_ord, 32 * a.W, smem, s>>>(a);
     sn_reduce_kernel<T><<<g, 256, 0, s>>>((const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old, (T*)p->sn_phi,
                                           p->ncells, p->sn_norm, (const T*)p->sig, p->mom_d, (T)p->area, inv4pidt,
-                                          src);
-    sn_norm_final_kernel<<<1, 32, 0, s>>>(p->sn_norm, g, p->st);
+                                          src, &p->st->sn_conv);
+    sn_norm_final_kernel<<<1, 32, 0, s>>>(p->sn_norm, g, p->st, sn_tol_eff(p));
+    return cudaGetLastError();
+}
+
+cudaError_t sn_start(hyb_problem* p) {
+    cudaError_t e = cudaMemsetAsync(&p->st->sn_conv, 0, 2 * sizeof(int), p->stream);
+    if (e != cudaSuccess) return e;
+    const int n = 4 * p->ncells, g = (n + 255) / 256;
+    if (p->prec == HYB_FP64)
+        sn_seed_kernel<double><<<g, 256, 0, p->stream>>>(p->sn_phi_d, (double*)p->sn_phi_old, n, p->st);
+    else
+        sn_seed_kernel<float><<<g, 256, 0, p->stream>>>(p->sn_phi_d, (float*)p->sn_phi_old, n, p->st);
     return cudaGetLastError();
 }
 
 cudaError_t sn_iteration(hyb_problem* p, int first) {
-    if (first && !p->sn_warm) {
-        const size_t bytes = (size_t)4 * p->ncells * (p->prec == HYB_FP64 ? 8 : 4);
-        cudaError_t e = cudaMemsetAsync(p->sn_phi_old, 0, bytes, p->stream);
-        if (e != cudaSuccess) return e;
-    }
     cudaError_t e = p->prec == HYB_FP64 ? sn_iteration_t<double>(p, first) : sn_iteration_t<float>(p, first);
     if (e != cudaSuccess) return e;
     void* t = p->sn_phi; p->sn_phi = p->sn_phi_old; p->sn_phi_old = t;   // newest is now sn_phi_old
@@ -308,6 +337,7 @@ cudaError_t sn_finish(hyb_problem* p) {
         sn_to_double_kernel<float><<<(n + 255) / 256, 256, 0, p->stream>>>((const float*)p->sn_phi_old, p->sn_phi_d, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    sn_done_kernel<<<1, 1, 0, p->stream>>>(p->st, p->d.sn_warm_start ? 1 : 0);
     return launch_flux(p);
 }
 

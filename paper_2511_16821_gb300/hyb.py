@@ -52,6 +52,10 @@ class Stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("block", C.c_int32), ("chunk", C.c_int32), ("ctas_per_sm", C.c_int32), ("streams", C.c_int32)]
+
+
 _lib = None
 
 
@@ -88,6 +92,12 @@ def lib():
                                  C.c_int32, P, P]
         L.hyb_sobol_table.argtypes = [C.c_int32, P]
         L.hyb_cdf_scratch_bytes.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
+        L.hyb_batch_create.argtypes = [C.POINTER(P), C.c_int32, P, C.POINTER(P)]
+        L.hyb_batch_set_tuning.argtypes = [P, C.POINTER(Tuning)]
+        L.hyb_batch_step.argtypes = [P, C.c_int32, C.POINTER(Stats)]
+        L.hyb_batch_destroy.argtypes = [P]
+        L.hyb_batch_last_error.restype = C.c_char_p
+        L.hyb_batch_last_error.argtypes = [P]
         L.hyb_build_cdf.argtypes = [P, C.c_int32, C.c_int32, P, P, P, P, P, C.c_size_t, P]
         L.hyb_quadrature.argtypes = [C.c_int32, P, P, P, C.POINTER(C.c_int32)]
         _lib = L
@@ -289,3 +299,48 @@ def build_cdf(w, nx: int, ny: int, stream=None):
                                C.c_void_p(rp.data_ptr()), C.c_void_p(cp.data_ptr()), C.c_void_p(wq.data_ptr()),
                                C.c_void_p(scratch.data_ptr()), scratch.numel(), C.c_void_p(s.cuda_stream)))
     return q, rp, cp, wq
+
+
+class Batch:
+    """Many problems advanced together: one CUDA graph per step, the MC legs of all problems in
+    one persistent work-queue launch. The problems must outlive the batch and are stepped only
+    through it while it exists."""
+
+    def __init__(self, problems: list, stream=None, tuning: dict | None = None):
+        torch = _torch_cuda()
+        self.problems = list(problems)
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        torch.cuda.synchronize()
+        arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        h = C.c_void_p()
+        st = lib().hyb_batch_create(arr, len(self.problems), C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != HYB_OK:
+            raise HybError(st, lib().hyb_batch_last_error(None).decode())
+        self.h = h
+        if tuning:
+            self.set_tuning(**tuning)
+
+    def _check(self, st):
+        if st != HYB_OK:
+            raise HybError(st, lib().hyb_batch_last_error(self.h).decode())
+
+    def set_tuning(self, block=256, chunk=4096, ctas_per_sm=0, streams=8):
+        t = Tuning(block=block, chunk=chunk, ctas_per_sm=ctas_per_sm, streams=streams)
+        self._check(lib().hyb_batch_set_tuning(self.h, C.byref(t)))
+        self.tuning = dict(block=block, chunk=chunk, ctas_per_sm=ctas_per_sm, streams=streams)
+
+    def step(self, n: int = 1, stats: bool = True):
+        arr = (Stats * len(self.problems))()
+        self._check(lib().hyb_batch_step(self.h, n, arr if stats else None))
+        return [arr[i].as_dict() for i in range(len(self.problems))] if stats else None
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hyb_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
