@@ -228,6 +228,57 @@ def cpu_baseline(n_hist: int, steps: int) -> dict:
                       f"histories/step (FP64 oracle, one thread)", "seconds": round(dt, 2)}
 
 
+def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0) -> dict:
+    """The batched workload: n problems of the batched distribution (FP32 tracking, int64
+    tallies), one graph per step after autotuning, against the plain single-problem path over the
+    same problems (each stepped alone, one after the other)."""
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    from paper_2511_16821_gb300.autotune import tune_batch
+    specs = [W.random_batch_problem(seed, p).with_(sn_warm_start=1) for p in range(n_problems)]
+    stream = torch.cuda.Stream()
+    probs = [hyb.Problem(sp, stream=stream) for sp in specs]
+    B = hyb.Batch(probs, stream=stream)
+    tune = tune_batch(B, steps=1, space={"block": (256,), "chunk": (2048, 8192, 32768), "streams": (16, 48)})
+    B.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = B.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    hist = sum(x["histories"] for x in st)
+    B.close()
+    for P in probs:
+        P.close()
+    # plain path: each problem alone, the same number of steps, one after the other
+    alone = [hyb.Problem(sp, stream=stream) for sp in specs]
+    for P in alone:
+        P.step(1, stats=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2 = 0
+    for P in alone:
+        for x in P.step(steps):
+            h2 += x["histories"]
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    for P in alone:
+        P.close()
+    return {"problems": n_problems, "histories_per_step": hist, "ms_per_step": ms,
+            "histories_per_s": hist / (ms / 1e3), "tuning": tune["best"],
+            "single_problem_path": {"histories_per_s": h2 / dt, "ms_per_step_all": 1e3 * dt / steps}}
+
+
+def serving_measure(lam: float, duration: float, seed: int = 0, hist_cap: int | None = None) -> dict:
+    from paper_2511_16821_gb300.serve import Server
+    srv = Server(budget_bytes=120e9)
+    res = srv.run_poisson(lam, duration, seed=seed, hist_cap=hist_cap)
+    srv.close()
+    return res
+
+
 def reference_arm(args, rank: int, world: int) -> None:
     if rank != 0:
         return
@@ -271,6 +322,9 @@ def main():
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--serve-sweep", default="", help="comma-separated arrival rates: run only the serving sweep")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (FP32, no profile/e2e/CPU legs): the case used for ncu captures")
     args = ap.parse_args()
@@ -286,8 +340,13 @@ def main():
         return
 
     import torch
+    if args.serve_sweep:
+        if rank == 0:
+            for lam in [float(x) for x in args.serve_sweep.split(",")]:
+                print(json.dumps({"serving": serving_measure(lam, args.serve_seconds)}), flush=True)
+        return
     if args.lean:
-        args.fp32_only = args.no_cpu = args.no_e2e = True
+        args.fp32_only = args.no_cpu = args.no_e2e = args.no_batch = True
     res = run_gpu(args, rank, world)
     if args.lean:
         if rank == 0:
@@ -341,6 +400,9 @@ def main():
                         "phase_ms": r64["phase_ms"]}
     if not args.no_e2e:
         line["e2e"] = e2e_measure(spec_for(W.FP32), max(2, min(args.steps, 5)))
+    if not args.no_batch:
+        line["batched"] = batched_measure()
+        line["serving"] = serving_measure(100.0, 3.0)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n_hist=200_000, steps=2)
     print(json.dumps(line), flush=True)

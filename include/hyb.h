@@ -197,6 +197,9 @@ typedef struct {
     int32_t chunk;        /* histories per work-queue item (>= 32) */
     int32_t ctas_per_sm;  /* resident CTAs per SM of the persistent leg; 0 = register limit */
     int32_t streams;      /* streams for the per-problem branches (1..64) */
+    int32_t use_graph;    /* 1: record each step as CUDA graphs and replay them (fixed membership);
+                             0: issue the same work directly (cheap to build, for changing sets) */
+    int32_t pad;
 } hyb_batch_tuning;
 
 /* problems: n handles (host array, borrowed; the problems must outlive the batch). cuda_stream:

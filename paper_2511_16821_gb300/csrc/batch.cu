@@ -42,7 +42,7 @@ struct hyb_batch {
     hyb::DevState* h_report = nullptr;      // pinned
     uint32_t* d_V = nullptr;
     int ntab_max = 0;
-    hyb_batch_tuning tune{256, 4096, 0, 8};
+    hyb_batch_tuning tune{256, 4096, 0, 8, 1, 0};
     std::vector<int> cur0;                  // bank parity of each problem when the batch was made
     std::vector<int> kmax;                  // source-iteration cap per problem inside the graph
     cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [parity][phase]
@@ -92,82 +92,106 @@ hyb_status build_chunks(hyb_batch* b) {
     return HYB_OK;
 }
 
-// Record one batch step of parity q as two graphs. Phase 0: zero tallies and counters, the
-// batched MC leg, then per problem normalisation and up to kmax source iterations (device stop).
-// Phase 1: per problem the end of the collided solve, the remap and a copy of its counters.
-// Problems whose iteration did not converge in phase 0 continue eagerly in between.
-hyb_status capture(hyb_batch* b, int q) {
+// One phase of a batch step of parity q, issued on the batch streams (recorded into a graph by
+// capture(), or run directly in eager mode). Phase 0: zero tallies and counters, the batched MC
+// leg, then per problem normalisation and up to kmax source iterations (device stop). Phase 1: per
+// problem the end of the collided solve, the remap and a copy of its counters. Problems whose
+// iteration did not converge in phase 0 continue eagerly in between.
+cudaError_t issue_phase(hyb_batch* b, int q, int phase) {
     const size_t n = b->probs.size();
-    std::vector<cudaStream_t> saved_stream(n);
-    std::vector<int> saved_cur(n);
-    std::vector<void*> saved_phi(n), saved_old(n);
-    for (size_t i = 0; i < n; ++i) {
-        hyb_problem* p = b->probs[i];
-        saved_stream[i] = p->stream; saved_cur[i] = p->cur; saved_phi[i] = p->sn_phi; saved_old[i] = p->sn_phi_old;
-        p->cur = b->cur0[i] ^ q;
-    }
+    cudaError_t e = cudaSuccess;
+    auto ck = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e = cudaSuccess;
-    auto ck = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
-    for (int phase = 0; phase < 2 && e == cudaSuccess; ++phase) {
-        ck(cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal));
-        if (e != cudaSuccess) break;
-        if (phase == 0) {
-            for (size_t i = 0; i < n; ++i) {
-                hyb_problem* p = b->probs[i];
-                const size_t nc = (size_t)p->ncells, acc = p->prec == HYB_FP64 ? 16 : 8;
-                ck(cudaMemsetAsync(p->acc_pre, 0, nc * acc, b->s0));
-                ck(cudaMemsetAsync(p->acc_post, 0, nc * acc, b->s0));
-                ck(cudaMemsetAsync(p->acc_mom, 0, 4 * nc * acc, b->s0));
-                ck(cudaMemsetAsync(p->st, 0, offsetof(hyb::DevState, r_histories), b->s0));
-                ck(cudaMemsetAsync(&p->st->status, 0, sizeof(int), b->s0));
-            }
-            ck(cudaMemsetAsync(b->d_head, 0, sizeof(int), b->s0));
-            const int per_sm = b->tune.ctas_per_sm > 0 ? b->tune.ctas_per_sm
-                                                       : hyb::leg_batch_ctas_per_sm(b->prec) * 256 / b->tune.block;
-            const int grid = std::max(1, std::min(b->nchunks, sms * per_sm));
-            ck(hyb::launch_mc_leg_batch(b->prec, b->d_args[q], b->d_chunks, b->nchunks, b->d_head, b->d_V,
-                                        b->ntab_max, grid, b->tune.block, b->s0));
-        }
-        ck(cudaEventRecord(b->fork_ev, b->s0));
-        for (auto s : b->pool) ck(cudaStreamWaitEvent(s, b->fork_ev, 0));
+    if (phase == 0) {
         for (size_t i = 0; i < n; ++i) {
             hyb_problem* p = b->probs[i];
-            p->stream = b->pool[i % b->pool.size()];
-            if (phase == 0) {
-                ck(hyb::launch_leg_normalise(p));
-                ck(hyb::sn_start(p));
-                for (int k = 1; k <= b->kmax[i]; ++k) ck(hyb::sn_iteration(p, k == 1));
-            } else {
-                ck(hyb::sn_finish(p));
-                ck(cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
-                ck(hyb::launch_remap(p));
-            }
-            report_kernel<<<1, 128, 0, p->stream>>>(p->st, b->d_report + i);
-            ck(cudaGetLastError());
+            const size_t nc = (size_t)p->ncells, acc = p->prec == HYB_FP64 ? 16 : 8;
+            ck(cudaMemsetAsync(p->acc_pre, 0, nc * acc, b->s0));
+            ck(cudaMemsetAsync(p->acc_post, 0, nc * acc, b->s0));
+            ck(cudaMemsetAsync(p->acc_mom, 0, 4 * nc * acc, b->s0));
+            ck(cudaMemsetAsync(p->st, 0, offsetof(hyb::DevState, r_histories), b->s0));
+            ck(cudaMemsetAsync(&p->st->status, 0, sizeof(int), b->s0));
         }
-        for (size_t j = 0; j < b->pool.size(); ++j) {
-            ck(cudaEventRecord(b->join_ev[j], b->pool[j]));
-            ck(cudaStreamWaitEvent(b->s0, b->join_ev[j], 0));
-        }
-        ck(cudaMemcpyAsync(b->h_report, b->d_report, n * sizeof(hyb::DevState), cudaMemcpyDeviceToHost, b->s0));
-        cudaGraph_t g = nullptr;
-        const cudaError_t e2 = cudaStreamEndCapture(b->s0, &g);
-        if (e == cudaSuccess && e2 != cudaSuccess) e = e2;
-        if (e == cudaSuccess) ck(cudaGraphInstantiate(&b->exec[q][phase], g, 0));
-        if (g) cudaGraphDestroy(g);
-        if (phase == 0) {
-            b->phi_mid[q].assign(n, nullptr);
-            b->old_mid[q].assign(n, nullptr);
-            for (size_t i = 0; i < n; ++i) { b->phi_mid[q][i] = b->probs[i]->sn_phi; b->old_mid[q][i] = b->probs[i]->sn_phi_old; }
-        }
+        ck(cudaMemsetAsync(b->d_head, 0, sizeof(int), b->s0));
+        const int per_sm = b->tune.ctas_per_sm > 0 ? b->tune.ctas_per_sm
+                                                   : hyb::leg_batch_ctas_per_sm(b->prec) * 256 / b->tune.block;
+        const int grid = std::max(1, std::min(b->nchunks, sms * per_sm));
+        ck(hyb::launch_mc_leg_batch(b->prec, b->d_args[q], b->d_chunks, b->nchunks, b->d_head, b->d_V, b->ntab_max,
+                                    grid, b->tune.block, b->s0));
     }
+    ck(cudaEventRecord(b->fork_ev, b->s0));
+    for (auto s : b->pool) ck(cudaStreamWaitEvent(s, b->fork_ev, 0));
     for (size_t i = 0; i < n; ++i) {
         hyb_problem* p = b->probs[i];
-        p->stream = saved_stream[i]; p->cur = saved_cur[i]; p->sn_phi = saved_phi[i]; p->sn_phi_old = saved_old[i];
+        p->stream = b->pool[i % b->pool.size()];
+        if (phase == 0) {
+            ck(hyb::launch_leg_normalise(p));
+            ck(hyb::sn_start(p));
+            for (int k = 1; k <= b->kmax[i]; ++k) ck(hyb::sn_iteration(p, k == 1));
+        } else {
+            ck(hyb::sn_finish(p));
+            ck(cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+            ck(hyb::launch_remap(p));
+        }
+        report_kernel<<<1, 128, 0, p->stream>>>(p->st, b->d_report + i);
+        ck(cudaGetLastError());
     }
+    for (size_t j = 0; j < b->pool.size(); ++j) {
+        ck(cudaEventRecord(b->join_ev[j], b->pool[j]));
+        ck(cudaStreamWaitEvent(b->s0, b->join_ev[j], 0));
+    }
+    ck(cudaMemcpyAsync(b->h_report, b->d_report, n * sizeof(hyb::DevState), cudaMemcpyDeviceToHost, b->s0));
+    return e;
+}
+
+struct SavedState {
+    std::vector<cudaStream_t> stream;
+    std::vector<int> cur;
+    std::vector<void*> phi, old;
+};
+
+SavedState enter(hyb_batch* b, int q) {
+    SavedState sv;
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        hyb_problem* p = b->probs[i];
+        sv.stream.push_back(p->stream); sv.cur.push_back(p->cur); sv.phi.push_back(p->sn_phi); sv.old.push_back(p->sn_phi_old);
+        p->cur = b->cur0[i] ^ q;
+    }
+    return sv;
+}
+
+void leave(hyb_batch* b, const SavedState& sv) {
+    for (size_t i = 0; i < b->probs.size(); ++i) {
+        hyb_problem* p = b->probs[i];
+        p->stream = sv.stream[i]; p->cur = sv.cur[i]; p->sn_phi = sv.phi[i]; p->sn_phi_old = sv.old[i];
+    }
+}
+
+void record_mid(hyb_batch* b, int q) {
+    const size_t n = b->probs.size();
+    b->phi_mid[q].assign(n, nullptr);
+    b->old_mid[q].assign(n, nullptr);
+    for (size_t i = 0; i < n; ++i) { b->phi_mid[q][i] = b->probs[i]->sn_phi; b->old_mid[q][i] = b->probs[i]->sn_phi_old; }
+}
+
+// Record one batch step of parity q as two graphs (phases 0 and 1).
+hyb_status capture(hyb_batch* b, int q) {
+    const SavedState sv = enter(b, q);
+    cudaError_t e = cudaSuccess;
+    for (int phase = 0; phase < 2 && e == cudaSuccess; ++phase) {
+        e = cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        cudaError_t ei = issue_phase(b, q, phase);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(b->s0, &g);
+        e = ei != cudaSuccess ? ei : e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec[q][phase], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (phase == 0) record_mid(b, q);
+    }
+    leave(b, sv);
     if (e != cudaSuccess) {
         drop_graphs(b);
         return bfail(b, HYB_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -258,8 +282,8 @@ HYB_API hyb_status hyb_batch_create(hyb_problem* const* problems, int32_t n, voi
 HYB_API hyb_status hyb_batch_set_tuning(hyb_batch* b, const hyb_batch_tuning* t) {
     if (!b || !t) return bfail(b, HYB_EINVAL, "null argument");
     if ((t->block != 128 && t->block != 256) || t->chunk < 32 || t->ctas_per_sm < 0 || t->ctas_per_sm > 16 ||
-        t->streams < 1 || t->streams > 64)
-        return bfail(b, HYB_EINVAL, "tuning out of range (block 128|256, chunk >= 32, streams 1..64)");
+        t->streams < 1 || t->streams > 64 || (t->use_graph != 0 && t->use_graph != 1))
+        return bfail(b, HYB_EINVAL, "tuning out of range (block 128|256, chunk >= 32, streams 1..64, use_graph 0|1)");
     b->tune = *t;
     drop_graphs(b);
     for (auto s : b->pool) cudaStreamDestroy(s);
@@ -279,13 +303,24 @@ HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* p
     const size_t n = b->probs.size();
     for (int32_t it = 0; it < nsteps; ++it) {
         const int q = b->parity;
-        if (!b->exec[q][0] || !b->exec[q][1]) {
+        const bool graph = b->tune.use_graph != 0;
+        SavedState sv;
+        if (graph && (!b->exec[q][0] || !b->exec[q][1])) {
             hyb_status s = capture(b, q);
             if (s != HYB_OK) return s;
         }
-        if (cudaEventRecord(b->ev0, b->s0) != cudaSuccess || cudaGraphLaunch(b->exec[q][0], b->s0) != cudaSuccess ||
-            cudaStreamSynchronize(b->s0) != cudaSuccess)
-            return bfail(b, HYB_ECUDA, "graph launch (leg and source iteration)");
+        if (cudaEventRecord(b->ev0, b->s0) != cudaSuccess) return bfail(b, HYB_ECUDA, "event");
+        if (graph) {
+            if (cudaGraphLaunch(b->exec[q][0], b->s0) != cudaSuccess || cudaStreamSynchronize(b->s0) != cudaSuccess)
+                return bfail(b, HYB_ECUDA, "graph launch (leg and source iteration)");
+        } else {
+            sv = enter(b, q);
+            const cudaError_t e = issue_phase(b, q, 0);
+            record_mid(b, q);
+            leave(b, sv);
+            if (e != cudaSuccess || cudaStreamSynchronize(b->s0) != cudaSuccess)
+                return bfail(b, HYB_ECUDA, "eager phase 0");
+        }
         bool recapture = false;
         for (size_t i = 0; i < n; ++i) {
             if (b->h_report[i].sn_conv) continue;
@@ -294,9 +329,17 @@ HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* p
             b->kmax[i] = std::min(b->probs[i]->d.sn_max_iter, std::max(2 * b->kmax[i], b->probs[i]->st_host->sn_iters + 2));
             recapture = true;
         }
-        if (cudaGraphLaunch(b->exec[q][1], b->s0) != cudaSuccess || cudaEventRecord(b->ev1, b->s0) != cudaSuccess ||
-            cudaStreamSynchronize(b->s0) != cudaSuccess)
-            return bfail(b, HYB_ECUDA, "graph launch (remap)");
+        if (graph) {
+            if (cudaGraphLaunch(b->exec[q][1], b->s0) != cudaSuccess) return bfail(b, HYB_ECUDA, "graph launch (remap)");
+        } else {
+            sv = enter(b, q);
+            for (size_t i = 0; i < n; ++i) { b->probs[i]->sn_phi = b->phi_mid[q][i]; b->probs[i]->sn_phi_old = b->old_mid[q][i]; }
+            const cudaError_t e = issue_phase(b, q, 1);
+            leave(b, sv);
+            if (e != cudaSuccess) return bfail(b, HYB_ECUDA, "eager phase 1");
+        }
+        if (cudaEventRecord(b->ev1, b->s0) != cudaSuccess || cudaStreamSynchronize(b->s0) != cudaSuccess)
+            return bfail(b, HYB_ECUDA, "step completion");
         b->parity ^= 1;
         hyb_status bad = HYB_OK;
         for (size_t i = 0; i < n; ++i) {
@@ -310,7 +353,7 @@ HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* p
             if (r.status & hyb::kStBounds) bad = HYB_EBOUNDS;
             else if ((r.status & hyb::kStSegments) && bad == HYB_OK) bad = HYB_ETIMEOUT;
         }
-        if (recapture) drop_graphs(b);
+        if (recapture && graph) drop_graphs(b);
         if (bad != HYB_OK) return bfail(b, bad, "a problem of the batch reported a device check failure");
     }
     if (per_problem) {

@@ -53,7 +53,8 @@ class Stats(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("block", C.c_int32), ("chunk", C.c_int32), ("ctas_per_sm", C.c_int32), ("streams", C.c_int32)]
+    _fields_ = [("block", C.c_int32), ("chunk", C.c_int32), ("ctas_per_sm", C.c_int32), ("streams", C.c_int32),
+                ("use_graph", C.c_int32), ("pad", C.c_int32)]
 
 
 _lib = None
@@ -324,10 +325,10 @@ class Batch:
         if st != HYB_OK:
             raise HybError(st, lib().hyb_batch_last_error(self.h).decode())
 
-    def set_tuning(self, block=256, chunk=4096, ctas_per_sm=0, streams=8):
-        t = Tuning(block=block, chunk=chunk, ctas_per_sm=ctas_per_sm, streams=streams)
+    def set_tuning(self, block=256, chunk=4096, ctas_per_sm=0, streams=8, use_graph=1):
+        t = Tuning(block=block, chunk=chunk, ctas_per_sm=ctas_per_sm, streams=streams, use_graph=int(use_graph), pad=0)
         self._check(lib().hyb_batch_set_tuning(self.h, C.byref(t)))
-        self.tuning = dict(block=block, chunk=chunk, ctas_per_sm=ctas_per_sm, streams=streams)
+        self.tuning = dict(block=block, chunk=chunk, ctas_per_sm=ctas_per_sm, streams=streams, use_graph=int(use_graph))
 
     def step(self, n: int = 1, stats: bool = True):
         arr = (Stats * len(self.problems))()

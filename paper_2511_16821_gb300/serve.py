@@ -1,0 +1,188 @@
+"""Continuous-batching server for hybrid solves.
+
+Requests (a problem description and a number of time steps) arrive over time. The server admits
+them as device memory (a fixed budget, counted from each problem's workspace size) and slots free
+up, keeps their census banks, tallies and collided-flux state resident between steps, and on each
+tick advances every resident problem by one step together: one batched MC-leg launch over all
+their histories, then their collided solves and remaps as concurrent branches (``hyb.Batch`` in
+eager mode, rebuilt when the resident set changes). Requests that arrive while others are on the
+GPU join at the next tick, so their work overlaps on the device.
+
+Step latency of a request's step k = completion time of that step minus the time it became
+eligible (arrival for k = 0, completion of step k - 1 otherwise); p50/p99 are over all steps.
+Each request's results are those of solving it alone (the batch is exact per problem).
+"""
+from __future__ import annotations
+
+import math
+import random
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import hyb
+from . import workloads as W
+
+
+@dataclass
+class Request:
+    rid: int
+    spec: W.ProblemSpec
+    steps: int
+    t_arrival: float
+    problem: object = None
+    ws_bytes: int = 0
+    done_steps: int = 0
+    t_ready: float = 0.0
+    t_admit: float = -1.0
+    t_done: float = -1.0
+    step_latency: list = field(default_factory=list)
+    histories: int = 0
+    flux: np.ndarray | None = None
+
+
+class Server:
+    def __init__(self, budget_bytes: float = 120e9, max_active: int = 512, tuning: dict | None = None,
+                 clock=None):
+        import torch
+        self.torch = torch
+        self.budget = float(budget_bytes)
+        self.max_active = max_active
+        self.tuning = dict(block=256, chunk=4096, streams=16, use_graph=0)
+        if tuning:
+            self.tuning.update(tuning)
+            self.tuning["use_graph"] = 0
+        self.clock = clock or time.perf_counter
+        self.stream = torch.cuda.Stream()
+        self.queue: list[Request] = []
+        self.active: list[Request] = []
+        self.finished: list[Request] = []
+        self.used = 0.0
+        self.batch = None
+        self.members: tuple = ()
+        self.ticks = 0
+        self.peak_used = 0.0
+        self.rebuilds = 0
+
+    # ---- admission --------------------------------------------------------------------------
+    def submit(self, spec: W.ProblemSpec, steps: int, t_arrival: float | None = None, rid: int | None = None) -> Request:
+        r = Request(rid=len(self.finished) + len(self.active) + len(self.queue) if rid is None else rid,
+                    spec=spec, steps=int(steps), t_arrival=self.clock() if t_arrival is None else t_arrival)
+        r.ws_bytes = hyb.workspace_size(spec)
+        if r.ws_bytes > self.budget:
+            raise ValueError(f"request {r.rid} needs {r.ws_bytes} bytes, above the whole budget")
+        r.t_ready = r.t_arrival
+        self.queue.append(r)
+        return r
+
+    def _admit(self) -> None:
+        while self.queue and len(self.active) < self.max_active and self.used + self.queue[0].ws_bytes <= self.budget:
+            r = self.queue.pop(0)
+            with self.torch.cuda.stream(self.stream):
+                r.problem = hyb.Problem(r.spec, stream=self.stream)
+            self.used += r.ws_bytes
+            self.peak_used = max(self.peak_used, self.used)
+            r.t_admit = self.clock()
+            self.active.append(r)
+
+    def _retire(self) -> None:
+        keep = []
+        for r in self.active:
+            if r.done_steps >= r.steps:
+                r.flux = r.problem.tally("flux")
+                r.problem.close()
+                r.problem = None
+                self.used -= r.ws_bytes
+                r.t_done = self.clock()
+                self.finished.append(r)
+            else:
+                keep.append(r)
+        self.active = keep
+
+    # ---- one tick: every resident problem advances one step ----------------------------------
+    def tick(self) -> int:
+        self._admit()
+        if not self.active:
+            return 0
+        members = tuple(r.rid for r in self.active)
+        if members != self.members:
+            if self.batch is not None:
+                self.batch.close()
+            self.batch = hyb.Batch([r.problem for r in self.active], stream=self.stream, tuning=self.tuning)
+            self.members = members
+            self.rebuilds += 1
+        stats = self.batch.step(1)
+        t = self.clock()
+        for r, s in zip(self.active, stats):
+            r.step_latency.append(t - r.t_ready)
+            r.t_ready = t
+            r.done_steps += 1
+            r.histories += s["histories"]
+        self.ticks += 1
+        n = len(self.active)
+        self._retire()
+        if self.batch is not None and tuple(r.rid for r in self.active) != self.members:
+            self.batch.close()
+            self.batch = None
+            self.members = ()
+        return n
+
+    # ---- drivers ----------------------------------------------------------------------------
+    def run_schedule(self, schedule: list[tuple[int, W.ProblemSpec, int]]) -> list[Request]:
+        """Deterministic driver: schedule entries (tick, spec, steps) are submitted at that tick."""
+        pending = sorted(enumerate(schedule), key=lambda e: e[1][0])
+        k = 0
+        tick = 0
+        while k < len(pending) or self.queue or self.active:
+            while k < len(pending) and pending[k][1][0] <= tick:
+                i, (_, spec, steps) = pending[k]
+                self.submit(spec, steps, rid=i)
+                k += 1
+            self.tick()
+            tick += 1
+        return sorted(self.finished, key=lambda r: r.rid)
+
+    def run_poisson(self, lam: float, duration: float, seed: int = 0, max_side: int = 256,
+                    hist_cap: int | None = None) -> dict:
+        """Wall-clock driver: Poisson arrivals of rate lam for `duration` seconds, each request drawn
+        from the batched distribution with 1..64 steps and dt in [0.05, 0.2]; runs until drained."""
+        rng = random.Random(seed)
+        arrivals = []
+        t = 0.0
+        i = 0
+        while True:
+            t += rng.expovariate(lam)
+            if t > duration:
+                break
+            spec = W.random_batch_problem(seed, i, dt=rng.uniform(0.05, 0.2), max_side=max_side)
+            if hist_cap:
+                spec = spec.with_(n_hist=min(spec.n_hist, hist_cap))
+            arrivals.append((t, spec.with_(sn_warm_start=1), rng.randint(1, 64)))
+            i += 1
+        t0 = self.clock()
+        k = 0
+        while k < len(arrivals) or self.queue or self.active:
+            now = self.clock() - t0
+            while k < len(arrivals) and arrivals[k][0] <= now:
+                ta, spec, steps = arrivals[k]
+                self.submit(spec, steps, t_arrival=t0 + ta, rid=k)
+                k += 1
+            if not self.tick() and k < len(arrivals):
+                time.sleep(max(0.0, min(arrivals[k][0] - (self.clock() - t0), 0.01)))
+        wall = self.clock() - t0
+        lat = np.array([x for r in self.finished for x in r.step_latency])
+        hist = sum(r.histories for r in self.finished)
+        return {"lambda": lam, "requests": len(self.finished), "steps": int(lat.size), "wall_s": wall,
+                "histories_per_s": hist / wall if wall > 0 else 0.0,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3) if lat.size else math.nan,
+                "p99_ms": float(np.percentile(lat, 99) * 1e3) if lat.size else math.nan,
+                "ticks": self.ticks, "rebuilds": self.rebuilds, "peak_bytes": self.peak_used}
+
+    def close(self) -> None:
+        if self.batch is not None:
+            self.batch.close()
+            self.batch = None
+        for r in self.active + self.queue:
+            if r.problem is not None:
+                r.problem.close()

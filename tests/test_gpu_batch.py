@@ -43,10 +43,12 @@ def test_batch_equals_alone(prec):
         assert bst[i]["bank_size"] == st["bank_size"]
         assert bst[i]["w_source"] == st["w_source"] and bst[i]["w_census"] == st["w_census"]
     B.close()
-    # tuning does not change results
-    probs2 = [hyb.Problem(sp) for sp in specs]
-    B2 = hyb.Batch(probs2, tuning=dict(block=128, chunk=8192, streams=1))
-    B2.step(3)
-    for i, P in enumerate(probs2):
-        assert np.array_equal(P.tally("flux"), alone[i][0]), i
-    B2.close()
+    # tuning (including eager, graph-free issue) does not change results
+    for tun in (dict(block=128, chunk=8192, streams=1), dict(block=256, chunk=2048, streams=3, use_graph=0)):
+        probs2 = [hyb.Problem(sp) for sp in specs]
+        B2 = hyb.Batch(probs2, tuning=tun)
+        B2.step(3)
+        for i, P in enumerate(probs2):
+            assert np.array_equal(P.tally("flux"), alone[i][0]), (i, tun)
+            assert np.array_equal(P.bank()["w"], alone[i][1]["w"]), (i, tun)
+        B2.close()
