@@ -171,17 +171,18 @@ def leg_profile(prec: int, reps: int = 5) -> dict:
     P = hyb.Problem(spec)
     P.step(2)                      # a steady-state census bank
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    ms, hist, segs, nb = [], 0, 0, 0
+    ms, hist, segs, adds, nb = [], 0, 0, 0, 0
     for _ in range(reps):
         flush.zero_()
         torch.cuda.synchronize()
         P.set_step(2)
         st = P.mc_leg()
         ms.append(st["ms"])
-        hist, segs = st["histories"], st["segments"]
+        hist, segs, adds = st["histories"], st["segments"], st["tally_adds"]
     bank = P.bank()
     nb = bank["n"]
-    return dict(ms=statistics.median(ms), histories=hist, segments=segs, bank=nb)
+    return dict(ms=statistics.median(ms), histories=hist, segments=segs, tally_adds=adds, bank=nb,
+                ncells=spec.ncells)
 
 
 def e2e_measure(spec: W.ProblemSpec, steps: int) -> dict:

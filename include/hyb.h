@@ -106,6 +106,8 @@ typedef struct {
     int64_t bank_size;        /* particles in the census bank after the call */
     float ms;                 /* device time of the call (events), 0 if not measured */
     int32_t pad;
+    int64_t tally_adds;       /* MC leg: fixed-point tally additions issued (global 64-bit atomics;
+                                 the FP64 path adds up to two words per contribution) */
 } hyb_leg_stats;
 
 typedef struct hyb_problem hyb_problem;
@@ -246,6 +248,13 @@ HYB_API hyb_status hyb_sobol_table(int32_t ndims, uint32_t* out_host);
 /* The S_N quadrature used (upper hemisphere, weights summing to 4 pi); returns the count in
  * *m (capacity in, count out). */
 HYB_API hyb_status hyb_quadrature(int32_t order, double* ox, double* oy, double* w, int32_t* m);
+
+/* Measurement helper, no counterpart in the paper: throughput of 64-bit global integer atomic
+ * additions (the MC leg's fixed-point tally updates) to n_addr addresses chosen uniformly at
+ * random, about n_ops additions per timed launch (best of 3 after a warm-up), on `stream`.
+ * Allocates and frees n_addr * 8 bytes; synchronises the stream. Result in *ops_per_s.
+ * EINVAL: n_addr < 1 or n_ops < 1; ENOMEM / ECUDA on failure. */
+HYB_API hyb_status hyb_atomic_rate(int64_t n_addr, int64_t n_ops, void* stream, double* ops_per_s);
 
 HYB_API const char* hyb_status_string(hyb_status s);
 /* Last error message of a problem (valid until the next call on it); p = NULL: the last error

@@ -1,0 +1,65 @@
+"""QMC versus pseudorandom error convergence of the hybrid on the GPU.
+
+The paper compares the error of the hybrid's scalar flux against the particle count for Halton
+points and pseudorandom numbers and fits err ~ c N^alpha (Sec. 3, Table 1: alpha near -0.5 for
+MC and -0.6 to -0.7 for QMC). Here the same study runs on a synthetic heterogeneous problem with
+Sobol points under a digital shift and with the counter PRNG: for every history count N and seed
+the hybrid advances `steps` time steps, and the error is the relative L2 norm, over cells, of the
+end-of-step scalar flux (MC pre + post tallies and the collided S_N flux) against a reference
+computed with many more histories (the mean over a few Sobol shifts). The error at each N is the
+root mean square over seeds, and alpha is the least-squares slope of log(error) against log(N).
+
+    python -m paper_2511_16821_gb300.convergence            # the full study, printed as JSON
+"""
+from __future__ import annotations
+
+import json
+import math
+
+import numpy as np
+
+from . import hyb
+from . import workloads as W
+
+
+def problem(n_hist: int, seed: int, sampler: int, precision: int = W.FP32) -> W.ProblemSpec:
+    """Checkerboard of 7x7 one-centimetre blocks at 4 cells per block (28x28), N_s = 2, S4,
+    absorber / scatterer blocks, Q = 1 in the centre block, dt = 0.1."""
+    return W.checkerboard(n_s=2, n_hist=n_hist, seed=seed, precision=precision, sampler=sampler,
+                          cells_per_block=4).with_(sn_order=4, sn_tol=1e-6, name="checkerboard28")
+
+
+def end_flux(spec: W.ProblemSpec, steps: int) -> np.ndarray:
+    with hyb.Problem(spec) as p:
+        p.step(steps, stats=False)
+        return p.tally("flux")
+
+
+def fit_alpha(ns, errs) -> float:
+    x = np.log(np.asarray(ns, dtype=float))
+    y = np.log(np.asarray(errs, dtype=float))
+    return float(np.polyfit(x, y, 1)[0])
+
+
+def study(log2_n=range(10, 21), seeds=range(16), steps: int = 4, ref_log2: int = 24, ref_seeds=range(100, 104),
+          spec_fn=problem) -> dict:
+    import torch
+    ref = np.mean([end_flux(spec_fn(1 << ref_log2, s, W.SOBOL), steps) for s in ref_seeds], axis=0)
+    nref = float(np.linalg.norm(ref))
+    out = {"workload": spec_fn(1, 0, W.SOBOL).name, "steps": steps, "reference_histories": 1 << ref_log2,
+           "reference_shifts": len(list(ref_seeds)), "seeds": len(list(seeds)), "metric": "relative L2 error of the "
+           "end-of-step scalar flux, RMS over seeds"}
+    for name, sampler in (("sobol", W.SOBOL), ("prng", W.PRNG)):
+        ns, errs = [], []
+        for k in log2_n:
+            n = 1 << k
+            e2 = [float(np.linalg.norm(end_flux(spec_fn(n, s, sampler), steps) - ref)) ** 2 for s in seeds]
+            ns.append(n)
+            errs.append(math.sqrt(sum(e2) / len(e2)) / nref)
+        out[name] = {"n": ns, "err": errs, "alpha": fit_alpha(ns, errs)}
+    torch.cuda.synchronize()
+    return out
+
+
+if __name__ == "__main__":
+    print(json.dumps(study()))

@@ -366,7 +366,7 @@ HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* p
             std::memset(&s, 0, sizeof(s));
             s.histories = (int64_t)h.histories; s.segments = (int64_t)h.segments; s.collisions = (int64_t)h.collisions;
             s.leaked = (int64_t)h.leaked; s.census = (int64_t)h.census; s.killed = (int64_t)h.killed;
-            s.reached_limit = (int64_t)h.reached; s.errors = (int64_t)h.errors;
+            s.reached_limit = (int64_t)h.reached; s.errors = (int64_t)h.errors; s.tally_adds = (int64_t)h.tally_adds;
             const double iw = std::ldexp(1.0, -h.k_w);
             s.w_source = hyb::acc128_to_double(h.w_source.lo, h.w_source.hi, iw);
             s.w_absorbed = hyb::acc128_to_double(h.w_absorbed.lo, h.w_absorbed.hi, iw);

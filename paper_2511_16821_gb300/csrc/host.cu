@@ -208,8 +208,9 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
-        sn4, sn16, sntx, snty, snqb, snnorm, blk;
+        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol;
     int64_t cap, nblk;
+    int gr, gc;
 };
 
 Sizes sizes(const hyb_problem_desc* d) {
@@ -243,6 +244,10 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.snnorm = 2 * ((nc + 255) / 256) * 8;
     z.nblk = (z.cap + d->n_hist + 2047) / 2048;
     z.blk = 4 * (size_t)z.nblk * 8;
+    z.gr = hyb::guide_bits(d->ny);
+    z.gc = hyb::guide_bits(d->nx);
+    z.grow = ((size_t(1) << z.gr) + 1) * 4;
+    z.gcol = (size_t)d->ny * ((size_t(1) << z.gc) + 1) * 4;
     return z;
 }
 
@@ -252,7 +257,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
     const size_t parts[] = {z.st, z.sobol, z.sig, z.sa, z.ss, z.Q, z.cdf_q, z.cdf_row, z.cdf_col, z.cdf_q, z.cdf_row,
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4,
-                            z.snnorm, z.blk};
+                            z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -298,6 +303,12 @@ void assign(hyb_problem* p) {
     p->sn_phi_d = (double*)take(z.d4);
     p->sn_norm = (double*)take(z.snnorm);
     p->blk = (long long*)take(z.blk);
+    p->src_cdf.row_g = (int*)take(z.grow);
+    p->src_cdf.col_g = (int*)take(z.gcol);
+    p->rem_cdf.row_g = (int*)take(z.grow);
+    p->rem_cdf.col_g = (int*)take(z.gcol);
+    p->src_cdf.gr = p->rem_cdf.gr = z.gr;
+    p->src_cdf.gc = p->rem_cdf.gc = z.gc;
     p->bank_cap = z.cap;
     p->nblk_max = z.nblk;
 }
@@ -375,7 +386,7 @@ void fill_leg_stats(const hyb_problem* p, hyb_leg_stats* s) {
     std::memset(s, 0, sizeof(*s));
     s->histories = (int64_t)h.histories; s->segments = (int64_t)h.segments; s->collisions = (int64_t)h.collisions;
     s->leaked = (int64_t)h.leaked; s->census = (int64_t)h.census; s->killed = (int64_t)h.killed;
-    s->reached_limit = (int64_t)h.reached; s->errors = (int64_t)h.errors;
+    s->reached_limit = (int64_t)h.reached; s->errors = (int64_t)h.errors; s->tally_adds = (int64_t)h.tally_adds;
     s->w_source = stat_w(h.w_source, h.k_w); s->w_absorbed = stat_w(h.w_absorbed, h.k_w);
     s->w_leaked = stat_w(h.w_leaked, h.k_w); s->w_census = stat_w(h.w_census, h.k_w);
     s->w_handoff = stat_w(h.w_handoff, h.k_w); s->w_killed = stat_w(h.w_killed, h.k_w);

@@ -50,23 +50,45 @@ __host__ __device__ __forceinline__ uint32_t first_point(uint64_t key, int sampl
                                    : (uint32_t)(dmix64(dmix64(key ^ (0ull + kGamma)) ^ (0ull + kGamma)) >> 32);
 }
 
-// A point set in shared memory: Sobol direction numbers (ntab dims x 32) and per-dimension
-// digital shifts; dimensions beyond the table (or sampler == PRNG) use the counter hash.
+// Sobol direction numbers as nibble tables: for dimension d and nibble k of the index, entry v is
+// the XOR of the direction numbers of the set bits of v (bits 4k..4k+3 of the index). A point is
+// then eight table reads whatever the index, and the 16 entries of one nibble table sit in 16
+// distinct shared-memory banks, so a warp's reads never conflict.
+constexpr int kNibbleWords = 128;   // 8 nibbles x 16 entries per dimension
+
+// builds the tables of dimensions [0, ntab) from the direction numbers V (ntab x 32) into sNT
+// (ntab x kNibbleWords); all threads of the block call it, the caller synchronises
+__device__ __forceinline__ void build_nibble_tables(const uint32_t* __restrict__ V, int ntab, uint32_t* sNT) {
+    for (int e = threadIdx.x; e < ntab * kNibbleWords; e += blockDim.x) {
+        const int d = e / kNibbleWords, k = (e / 16) & 7, v = e & 15;
+        const uint32_t* vd = V + d * 32 + 4 * k;
+        uint32_t x = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if ((v >> j) & 1) x ^= __ldg(vd + j);
+        sNT[e] = x;
+    }
+}
+
+// A point set in shared memory: Sobol nibble tables (ntab dims) and per-dimension digital shifts;
+// dimensions beyond the table (or sampler == PRNG) use the counter hash.
 struct Points {
-    const uint32_t* V;
+    const uint32_t* NT;
     const uint32_t* shift;
     uint64_t key;
     int sampler;
     int ntab;
     __device__ __forceinline__ uint32_t operator()(uint32_t i, int d) const {
         if (sampler == HYB_SOBOL_DS && d < ntab) {
-            const uint32_t* v = V + d * 32;
-            uint32_t x = 0, m = i;
-            while (m) {
-                x ^= v[__ffs(m) - 1];
-                m &= m - 1;
+            const uint32_t* t = NT + d * kNibbleWords;
+            uint32_t x = shift[d];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) x ^= t[16 * k + ((i >> (4 * k)) & 15u)];
+            if (i >> 24) {
+                x ^= t[96 + ((i >> 24) & 15u)];
+                x ^= t[112 + (i >> 28)];
             }
-            return x ^ shift[d];
+            return x;
         }
         const uint64_t h = dmix64(key ^ ((uint64_t)i + kGamma));
         return (uint32_t)(dmix64(h ^ ((uint64_t)d + kGamma)) >> 32);
@@ -96,9 +118,11 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ float msub(float c, float a, float b) { return fmaf(-a, b, c); }
     // a*b + c with one rounding, spelled out so every inlined copy evaluates it the same way
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
-    static __device__ __forceinline__ void add(acc_t* p, float c, float scale) {
+    // returns the number of global additions issued (0 or 1)
+    static __device__ __forceinline__ int add(acc_t* p, float c, float scale) {
         const long long v = __float2ll_rn(c * scale);
         if (v) atomicAdd(p, (unsigned long long)v);
+        return v != 0;
     }
     static __device__ __forceinline__ double to_double(const acc_t* p, double inv_scale) {
         return (double)(long long)(*p) * inv_scale;
@@ -120,12 +144,14 @@ __device__ __forceinline__ void to_i128(double v, unsigned long long* lo, unsign
     *hi = H;
 }
 
-__device__ __forceinline__ void atomic_add128(Acc128* p, unsigned long long lo, unsigned long long hi) {
+// returns the number of global additions issued (0 to 2)
+__device__ __forceinline__ int atomic_add128(Acc128* p, unsigned long long lo, unsigned long long hi) {
     if (lo) {
         const unsigned long long old = atomicAdd(&p->lo, lo);
         if (old + lo < old) hi += 1ull;
     }
     if (hi) atomicAdd(&p->hi, hi);
+    return (lo != 0ull) + (hi != 0ull);
 }
 
 __host__ __device__ __forceinline__ double acc128_to_double(unsigned long long lo, unsigned long long hi,
@@ -198,10 +224,10 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double madd(double a, double b, double c) { return __dadd_rn(__dmul_rn(a, b), c); }
     static __device__ __forceinline__ double msub(double c, double a, double b) { return __dsub_rn(c, __dmul_rn(a, b)); }
     static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
-    static __device__ __forceinline__ void add(acc_t* p, double c, double scale) {
+    static __device__ __forceinline__ int add(acc_t* p, double c, double scale) {
         unsigned long long lo, hi;
         to_i128(c * scale, &lo, &hi);
-        atomic_add128(p, lo, hi);
+        return atomic_add128(p, lo, hi);
     }
     static __device__ __forceinline__ double to_double(const acc_t* p, double inv_scale) {
         return acc128_to_double(p->lo, p->hi, inv_scale);
@@ -255,16 +281,14 @@ __device__ __forceinline__ void iso_dir(uint32_t x_mu, uint32_t x_phi, T* ox, T*
 }
 
 // ---------------------------------------------------------------------------------------------
-// integer CDF pick: bin j of pre[0..n] with pre[j] 2^33 <= (2x+1) total < pre[j+1] 2^33;
-// a, b: the remainder split as rem = a 2^33 + b; W: the bin weight
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ int pick_bin(const long long* __restrict__ pre, int n, uint32_t x,
+// integer CDF pick: bin j of pre[0..n] with pre[j] 2^33 <= (2x+1) total < pre[j+1] 2^33, searched
+// in [lo, hi] (which must hold it); a, b: the remainder split as rem = a 2^33 + b; W: the bin weight
+__device__ __forceinline__ int pick_bin(const long long* __restrict__ pre, int n, uint32_t x, int lo, int hi,
                                         unsigned long long* a, unsigned long long* b,
                                         unsigned long long* W) {
     const unsigned long long total = (unsigned long long)pre[n];
     const unsigned long long m = 2ull * (unsigned long long)x + 1ull;
     const unsigned long long Plo = m * total, Phi = __umul64hi(m, total);
-    int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         const unsigned long long v = (unsigned long long)pre[mid];
@@ -279,6 +303,18 @@ __device__ __forceinline__ int pick_bin(const long long* __restrict__ pre, int n
     *b = rlo & ((1ull << 33) - 1ull);
     *W = (unsigned long long)(pre[lo + 1] - pre[lo]);
     return lo;
+}
+
+// the search range of point x from a guide table of 2^g buckets (the whole range without one)
+__device__ __forceinline__ void guide_range(const int* guide, int g, int n, uint32_t x, int* lo, int* hi) {
+    if (guide) {
+        const uint32_t bkt = g ? (x >> (32 - g)) : 0u;
+        *lo = __ldg(guide + bkt);
+        *hi = __ldg(guide + bkt + 1);
+    } else {
+        *lo = 0;
+        *hi = n - 1;
+    }
 }
 
 template <typename T>
@@ -296,9 +332,12 @@ template <typename T>
 __device__ __forceinline__ int sample_cell(const Cdf2DView& C, int nx, int ny, uint32_t x0, uint32_t x1,
                                            T* frx, T* fry) {
     unsigned long long a, b, W;
-    const int iy = pick_bin(C.row_pre, ny, x1, &a, &b, &W);
+    int lo, hi;
+    guide_range(C.row_g, C.gr, ny, x1, &lo, &hi);
+    const int iy = pick_bin(C.row_pre, ny, x1, lo, hi, &a, &b, &W);
     *fry = bin_frac<T>(a, b, W);
-    const int ix = pick_bin(C.col_pre + (size_t)iy * (nx + 1), nx, x0, &a, &b, &W);
+    guide_range(C.col_g ? C.col_g + (size_t)iy * ((1 << C.gc) + 1) : nullptr, C.gc, nx, x0, &lo, &hi);
+    const int ix = pick_bin(C.col_pre + (size_t)iy * (nx + 1), nx, x0, lo, hi, &a, &b, &W);
     *frx = bin_frac<T>(a, b, W);
     return iy * nx + ix;
 }

@@ -27,6 +27,7 @@ struct Acc128 { unsigned long long lo, hi; };
 struct DevState {
     // counters of the last MC leg
     unsigned long long histories, segments, collisions, leaked, census, killed, reached, errors;
+    unsigned long long tally_adds;   // fixed-point tally additions (global atomics) issued
     Acc128 w_source, w_absorbed, w_leaked, w_census, w_handoff, w_killed;
     // counters of the last remap
     unsigned long long r_histories, r_segments, r_leaked, r_killed, r_errors, r_alive;
@@ -61,7 +62,23 @@ struct DevState {
 template <typename T>
 struct BankView { int32_t* cell; T *fx, *fy, *ox, *oy, *w; };
 
-struct Cdf2DView { long long* q; long long* row_pre; long long* col_pre; };
+// Integer 2-D CDF: per-cell integer weights q, row marginal row_pre (ny + 1), per-row column
+// conditionals col_pre (ny x (nx + 1)). Optional guide tables (Chen & Asau 1974) narrow each pick:
+// for 2^g equal buckets of the 32-bit point, entry b holds the bin picked by the bucket's smallest
+// point, so the bin of any point in bucket b lies in [guide[b], guide[b + 1]] (the pick is
+// monotone); row_g has 2^gr + 1 entries, col_g 2^gc + 1 per row. Null guides: full search.
+struct Cdf2DView {
+    long long* q; long long* row_pre; long long* col_pre;
+    int* row_g = nullptr; int* col_g = nullptr;
+    int gr = 0, gc = 0;
+};
+
+// guide table bits for n bins: the smallest g with 2^g >= n (at most 20)
+inline int guide_bits(int n) {
+    int g = 0;
+    while ((1 << g) < n && g < 20) ++g;
+    return g;
+}
 
 }  // namespace hyb
 

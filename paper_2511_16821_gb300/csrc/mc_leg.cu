@@ -47,14 +47,15 @@ struct Hist {
 
 // Per-thread statistics of the histories a thread finished (integers: order-free sums).
 struct LegTally {
-    unsigned long long c[8];   // histories, segments, collisions, leaked, census, killed, reached, errors
+    unsigned long long c[9];   // histories, segments, collisions, leaked, census, killed, reached, errors,
+                               // fixed-point tally additions issued
     long long f[6];            // fixed-point weights: source, absorbed, leaked, census, handoff, killed
     int status;
 };
 
 __device__ __forceinline__ void leg_tally_zero(LegTally& t) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) t.c[q] = 0;
+    for (int q = 0; q < 9; ++q) t.c[q] = 0;
 #pragma unroll
     for (int q = 0; q < 6; ++q) t.f[q] = 0;
     t.status = 0;
@@ -95,7 +96,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
     const unsigned lt_mask = (1u << lane) - 1u;
 
     Points pts;
-    pts.V = sV;
+    pts.NT = sV;
     pts.sampler = a.sampler;
     pts.ntab = a.ntab;
     Hist<T> h;
@@ -172,26 +173,26 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
 
         if (h.n < Ns) {
             const T att = -P::exm1(-sa * l);
-            P::add(&a.pre[k], sa > T(0) ? h.w * att / sa : h.w * l, sc_t);
+            t.c[8] += P::add(&a.pre[k], sa > T(0) ? h.w * att / sa : h.w * l, sc_t);
             d_abs += (double)(h.w * att);
             h.w = h.w * P::ex(-sa * l);
             h.tau = P::msub(h.tau, ss, l);
         } else {
             const T att = -P::exm1(-st * l);
-            P::add(&a.post[k], st > T(0) ? h.w * att / st : h.w * l, sc_t);
+            t.c[8] += P::add(&a.post[k], st > T(0) ? h.w * att / st : h.w * l, sc_t);
             if (ss > T(0)) {
                 T g0, g1, g2;
                 gfun<T>(st * l, &g0, &g1, &g2);
                 const T I0 = l * g0, I1 = l * l * g1, I2 = l * l * l * g2;
                 const T sw = ss * h.w;
-                P::add(&a.mom[4 * k + 0], sw * I0, sc_m);
+                t.c[8] += P::add(&a.mom[4 * k + 0], sw * I0, sc_m);
                 if (a.handoff_full) {
                     const T xi0 = T(2) * h.fx / DX - T(1), eta0 = T(2) * h.fy / DY - T(1);
                     const T axi = T(2) * h.ox / DX, aeta = T(2) * h.oy / DY;
                     // explicit fused forms: the same rounding in every kernel this is inlined into
-                    P::add(&a.mom[4 * k + 1], sw * P::fma_(xi0, I0, axi * I1), sc_m);
-                    P::add(&a.mom[4 * k + 2], sw * P::fma_(eta0, I0, aeta * I1), sc_m);
-                    P::add(&a.mom[4 * k + 3],
+                    t.c[8] += P::add(&a.mom[4 * k + 1], sw * P::fma_(xi0, I0, axi * I1), sc_m);
+                    t.c[8] += P::add(&a.mom[4 * k + 2], sw * P::fma_(eta0, I0, aeta * I1), sc_m);
+                    t.c[8] += P::add(&a.mom[4 * k + 3],
                            sw * P::fma_(xi0 * eta0, I0, P::fma_(P::fma_(xi0, aeta, eta0 * axi), I1, axi * aeta * I2)),
                            sc_m);
                 }
@@ -251,32 +252,32 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
 
 // Block reduction of the per-thread statistics into the problem's counters (all threads call).
 __device__ void leg_flush(DevState* st, LegTally& t, const LegScales& sc, bool write_scales) {
-    __shared__ unsigned long long s_c[kTile / 32][14];
+    __shared__ unsigned long long s_c[kTile / 32][15];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    unsigned long long cs[14];
+    unsigned long long cs[15];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) cs[q] = t.c[q];
+    for (int q = 0; q < 9; ++q) cs[q] = t.c[q];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) cs[8 + q] = (unsigned long long)t.f[q];
+    for (int q = 0; q < 6; ++q) cs[9 + q] = (unsigned long long)t.f[q];
 #pragma unroll
-    for (int q = 0; q < 14; ++q) cs[q] = warp_sum_u64(cs[q]);
+    for (int q = 0; q < 15; ++q) cs[q] = warp_sum_u64(cs[q]);
     if (lane == 0)
-        for (int q = 0; q < 14; ++q) s_c[wl][q] = cs[q];
+        for (int q = 0; q < 15; ++q) s_c[wl][q] = cs[q];
     if (t.status) atomicOr(&st->status, t.status);
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned long long* cdst[8] = {&st->histories, &st->segments, &st->collisions, &st->leaked,
-                                       &st->census, &st->killed, &st->reached, &st->errors};
+        unsigned long long* cdst[9] = {&st->histories, &st->segments, &st->collisions, &st->leaked,
+                                       &st->census, &st->killed, &st->reached, &st->errors, &st->tally_adds};
         Acc128* wdst[6] = {&st->w_source, &st->w_absorbed, &st->w_leaked, &st->w_census,
                            &st->w_handoff, &st->w_killed};
         const int nw = (int)(blockDim.x >> 5);
-        for (int q = 0; q < 14; ++q) {
+        for (int q = 0; q < 15; ++q) {
             unsigned long long v = 0;
             for (int ww = 0; ww < nw; ++ww) v += s_c[ww][q];
-            if (q < 8) { if (v) atomicAdd(cdst[q], v); }
+            if (q < 9) { if (v) atomicAdd(cdst[q], v); }
             else if (v) {
                 const long long sv = (long long)v;
-                atomic_add128(wdst[q - 8], (unsigned long long)sv, sv < 0 ? ~0ull : 0ull);
+                atomic_add128(wdst[q - 9], (unsigned long long)sv, sv < 0 ? ~0ull : 0ull);
             }
         }
         if (write_scales) {
@@ -293,12 +294,12 @@ template <typename T>
 __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(LegArgs<T> a) {
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
-    uint32_t* sShC = sm + a.ntab * 32;
+    uint32_t* sShC = sm + a.ntab * kNibbleWords;
     uint32_t* sShS = sShC + a.ntab;
     const uint64_t step = (uint64_t)a.st->step;
     const uint64_t key_c = dstream_key(a.seed, step, HYB_STREAM_LEG_CENSUS);
     const uint64_t key_s = dstream_key(a.seed, step, HYB_STREAM_LEG_SOURCE);
-    for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
+    build_nibble_tables(a.V, a.ntab, sV);
     for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) {
         sShC[d] = dshift(key_c, (uint64_t)d);
         sShS[d] = dshift(key_s, (uint64_t)d);
@@ -328,10 +329,10 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
                     int* head, const uint32_t* V, int ntab_max) {
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
-    uint32_t* sShC = sm + ntab_max * 32;
+    uint32_t* sShC = sm + ntab_max * kNibbleWords;
     uint32_t* sShS = sShC + ntab_max;
     __shared__ int s_chunk;
-    for (int i = threadIdx.x; i < ntab_max * 32; i += blockDim.x) sV[i] = V[i];
+    build_nibble_tables(V, ntab_max, sV);
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) s_chunk = atomicAdd(head, 1);
@@ -386,10 +387,10 @@ __global__ void leg_normalise_kernel(const typename Prec<T>::acc_t* pre, const t
 template <typename T>
 __global__ void init_bank_kernel(BankView<T> b, Cdf2DView cdf, int nx, int ny, T dx, T dy, long long n, T w0,
                                  const uint32_t* V, int ntab, int sampler, uint64_t key) {
-    __shared__ uint32_t sV[5 * 32];
+    __shared__ uint32_t sV[5 * kNibbleWords];
     __shared__ uint32_t sSh[5];
     const int nt = ntab < 5 ? ntab : 5;
-    for (int i = threadIdx.x; i < nt * 32; i += blockDim.x) sV[i] = V[i];
+    build_nibble_tables(V, nt, sV);
     if (threadIdx.x < nt) sSh[threadIdx.x] = dshift(key, threadIdx.x);
     __syncthreads();
     Points pts{sV, sSh, key, sampler, nt};
@@ -448,8 +449,8 @@ __global__ void points_kernel(uint64_t key, int sampler, const uint32_t* V, long
     extern __shared__ uint32_t sm[];
     const int ntab = ndims < HYB_SOBOL_DIMS ? ndims : HYB_SOBOL_DIMS;
     uint32_t* sV = sm;
-    uint32_t* sSh = sm + ntab * 32;
-    for (int i = threadIdx.x; i < ntab * 32; i += blockDim.x) sV[i] = V[i];
+    uint32_t* sSh = sm + ntab * kNibbleWords;
+    build_nibble_tables(V, ntab, sV);
     for (int d = threadIdx.x; d < ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
     __syncthreads();
     Points pts{sV, sSh, key, sampler, ntab};
@@ -500,7 +501,7 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
 template <typename T>
 static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
     const LegArgs<T> a = leg_args<T>(p, hist, p->cur);
-    const size_t smem = (size_t)(a.ntab * 32 + 2 * a.ntab) * sizeof(uint32_t);
+    const size_t smem = (size_t)(a.ntab * kNibbleWords + 2 * a.ntab) * sizeof(uint32_t);
     const long long work = p->bank_cap + a.n_src;
     mc_leg_kernel<T><<<leg_grid(work), kTile, smem, p->stream>>>(a);
     return cudaGetLastError();
@@ -519,7 +520,7 @@ int leg_batch_ctas_per_sm(int prec) { return prec == HYB_FP64 ? 2 : 3; }
 
 cudaError_t launch_mc_leg_batch(int prec, const void* d_args, const void* d_chunks, int nchunks, int* d_head,
                                 const uint32_t* V, int ntab_max, int grid, int block, cudaStream_t s) {
-    const size_t smem = (size_t)(ntab_max * 32 + 2 * ntab_max) * sizeof(uint32_t);
+    const size_t smem = (size_t)(ntab_max * kNibbleWords + 2 * ntab_max) * sizeof(uint32_t);
     if (prec == HYB_FP64)
         mc_leg_batch_kernel<double><<<grid, block, smem, s>>>((const LegArgs<double>*)d_args,
                                                              (const LegChunk*)d_chunks, nchunks, d_head, V, ntab_max);
@@ -585,7 +586,7 @@ cudaError_t launch_bank_stats(hyb_problem* p) {
 cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,
                           uint32_t* out, cudaStream_t s) {
     const int ntab = ndims < HYB_SOBOL_DIMS ? ndims : HYB_SOBOL_DIMS;
-    const size_t smem = (size_t)(ntab * 32 + ntab) * sizeof(uint32_t);
+    const size_t smem = (size_t)(ntab * kNibbleWords + ntab) * sizeof(uint32_t);
     points_kernel<<<leg_grid(n), kTile, smem, s>>>(key, sampler, V, i0, n, ndims, out);
     return cudaGetLastError();
 }

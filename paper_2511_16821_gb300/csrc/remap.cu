@@ -144,6 +144,24 @@ __global__ void cdf_rowpre_kernel(const long long* row_tot, int ny, long long* r
     if (threadIdx.x == 0) row_pre[ny] = total;
 }
 
+// guide tables: thread t < 2^gr + 1 fills row-guide entry t, the others the column guides row by
+// row; entry b is the pick of the bucket's smallest point b 2^(32-g), the last entry the last bin
+__global__ void cdf_guide_kernel(Cdf2DView C, int nx, int ny) {
+    const long long Gr = 1ll << C.gr, Gc = 1ll << C.gc;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nrow = Gr + 1;
+    if (t >= nrow + (long long)ny * (Gc + 1)) return;
+    unsigned long long a, b, W;
+    if (t < nrow) {
+        C.row_g[t] = t == Gr ? ny - 1 : pick_bin(C.row_pre, ny, (uint32_t)(t << (32 - C.gr)), 0, ny - 1, &a, &b, &W);
+    } else {
+        const long long u = t - nrow;
+        const long long r = u / (Gc + 1), g = u % (Gc + 1);
+        C.col_g[u] = g == Gc ? nx - 1
+                             : pick_bin(C.col_pre + r * (nx + 1), nx, (uint32_t)(g << (32 - C.gc)), 0, nx - 1, &a, &b, &W);
+    }
+}
+
 // scratch: kCdfParts doubles of block partial sums, then ny int64 row totals
 cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
                                  double* qmax_out, double* scratch, cudaStream_t stream) {
@@ -155,6 +173,10 @@ cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView
     cdf_total_kernel<<<1, 32, 0, stream>>>(part, kCdfParts, W_out);
     cdf_rows_kernel<<<ny, 256, 0, stream>>>(cell_w, qmax_out, nx, cdf, row_tot);
     cdf_rowpre_kernel<<<1, 1024, 0, stream>>>(row_tot, ny, cdf.row_pre);
+    if (cdf.row_g && cdf.col_g) {
+        const long long n = (1ll << cdf.gr) + 1 + (long long)ny * ((1ll << cdf.gc) + 1);
+        cdf_guide_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(cdf, nx, ny);
+    }
     return cudaGetLastError();
 }
 
@@ -320,9 +342,9 @@ template <typename T>
 __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
-    uint32_t* sSh = sm + a.ntab * 32;
+    uint32_t* sSh = sm + a.ntab * kNibbleWords;
     const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_REMAP_SOURCE);
-    for (int i = threadIdx.x; i < a.ntab * 32; i += blockDim.x) sV[i] = a.V[i];
+    build_nibble_tables(a.V, a.ntab, sV);
     for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
     __syncthreads();
     Points pts{sV, sSh, key, a.sampler, a.ntab};
@@ -598,7 +620,7 @@ static cudaError_t remap_t(hyb_problem* p) {
         a.stg.fx = f; a.stg.fy = f + maxN; a.stg.ox = f + 2 * maxN; a.stg.oy = f + 3 * maxN; a.stg.w = f + 4 * maxN;
     }
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
-    const size_t smem = (size_t)(a.ntab * 32 + a.ntab + 1) * sizeof(uint32_t);
+    const size_t smem = (size_t)(a.ntab * kNibbleWords + a.ntab + 1) * sizeof(uint32_t);
     // zero the remap counters
     e = cudaMemsetAsync(&p->st->r_histories, 0,
                         (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);

@@ -55,55 +55,139 @@ __global__ void sn_source_kernel(int ncells, const T* sig, const T* phi_old, con
     sgA[k] = (sa + ss + inv_cdt) * area;
 }
 
-template <typename T> __device__ __forceinline__ T rcp_(T x) { return T(1) / x; }
-template <> __device__ __forceinline__ float rcp_<float>(float x) { return __frcp_rn(x); }
+// Cell data of one wavefront step: the four source integrals (un-mirrored) and (sigma_t + 1/(c dt)) A.
+template <typename T> struct CellIn { T s0, s1, s2, s3, sA; };
+
+template <typename T>
+__device__ __forceinline__ void load_cell(const T* src, const T* sgA, size_t k, CellIn<T>& d);
+template <>
+__device__ __forceinline__ void load_cell<float>(const float* src, const float* sgA, size_t k, CellIn<float>& d) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src) + k);
+    d.s0 = v.x; d.s1 = v.y; d.s2 = v.z; d.s3 = v.w;
+    d.sA = __ldg(sgA + k);
+}
+template <>
+__device__ __forceinline__ void load_cell<double>(const double* src, const double* sgA, size_t k, CellIn<double>& d) {
+    const double2 v0 = __ldg(reinterpret_cast<const double2*>(src) + 2 * k);
+    const double2 v1 = __ldg(reinterpret_cast<const double2*>(src) + 2 * k + 1);
+    d.s0 = v0.x; d.s1 = v0.y; d.s2 = v1.x; d.s3 = v1.y;
+    d.sA = __ldg(sgA + k);
+}
+
+__device__ __forceinline__ void store_cell(float* d, float a0, float a1, float a2, float a3) {
+    *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
+}
+__device__ __forceinline__ void store_cell(double* d, double a0, double a1, double a2, double a3) {
+    reinterpret_cast<double2*>(d)[0] = make_double2(a0, a1);
+    reinterpret_cast<double2*>(d)[1] = make_double2(a2, a3);
+}
+
+// Strip-to-strip trace ring: each 32-bit piece of the two traces of a column travels with a 32-bit
+// sequence tag in one 64-bit shared-memory word (a single-copy-atomic access), so a reader that
+// sees the expected tag in every word of the entry has the values, with no fence and no counter.
+template <typename T> struct Ring;
+template <> struct Ring<float> {
+    static constexpr int kWords = 2;
+    static __device__ __forceinline__ void put(volatile unsigned long long* e, float v0, float v1, uint32_t tag) {
+        const unsigned long long hi = (unsigned long long)tag << 32;
+        e[0] = hi | __float_as_uint(v0);
+        e[1] = hi | __float_as_uint(v1);
+    }
+    // true when both words carry the tag; the values in v0, v1
+    static __device__ __forceinline__ bool get(const volatile unsigned long long* e, uint32_t tag, float* v0, float* v1) {
+        const unsigned long long a = e[0], b = e[1];
+        *v0 = __uint_as_float((uint32_t)a);
+        *v1 = __uint_as_float((uint32_t)b);
+        return (uint32_t)(a >> 32) == tag && (uint32_t)(b >> 32) == tag;
+    }
+};
+template <> struct Ring<double> {
+    static constexpr int kWords = 4;
+    static __device__ __forceinline__ void put(volatile unsigned long long* e, double v0, double v1, uint32_t tag) {
+        const unsigned long long hi = (unsigned long long)tag << 32;
+        e[0] = hi | (uint32_t)__double2loint(v0);
+        e[1] = hi | (uint32_t)__double2hiint(v0);
+        e[2] = hi | (uint32_t)__double2loint(v1);
+        e[3] = hi | (uint32_t)__double2hiint(v1);
+    }
+    static __device__ __forceinline__ bool get(const volatile unsigned long long* e, uint32_t tag, double* v0, double* v1) {
+        const unsigned long long a = e[0], b = e[1], c = e[2], d = e[3];
+        *v0 = __hiloint2double((int)(uint32_t)b, (int)(uint32_t)a);
+        *v1 = __hiloint2double((int)(uint32_t)d, (int)(uint32_t)c);
+        return (uint32_t)(a >> 32) == tag && (uint32_t)(b >> 32) == tag && (uint32_t)(c >> 32) == tag &&
+               (uint32_t)(d >> 32) == tag;
+    }
+};
+
+// reciprocals of the sweep's cell solve: FP32 takes the single-instruction approximation
+// (relative error below 2^-22), FP64 the correctly rounded quotient
+__device__ __forceinline__ float sweep_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double sweep_rcp(double x) { return 1.0 / x; }
 
 // The mirrored cell system couples {a0, a3} only to {a1, a2}:
 //   [ d0  2X  2Y   0 ]        d0 = sA + 2X + 2Y,       d1 = sA/3 + 2X + (2/3)Y,
 //   [-2X  d1   0  tY ]        d2 = sA/3 + (2/3)X + 2Y, d3 = sA/9 + (2/3)(X + Y),
 //   [-2Y   0  d2  tX ]        tX = (2/3)X, tY = (2/3)Y;
 //   [  0 -tY -tX  d3 ]
-// eliminating a0 and a3 leaves a symmetric positive 2x2 system for (a1, a2) (Schur complement),
-// a short dependency chain: two reciprocals, one 2x2 determinant, back substitution.
+// eliminating a0 and a3 leaves a symmetric positive 2x2 system for (a1, a2) (Schur complement).
+// Per cell and ordinate, the coefficients that do not depend on the incoming traces are computed
+// ahead, off the wavefront chain; with b the right-hand side,
+//   r1 = b1 + k1 b0 - k2 b3,  r2 = b2 + k3 b0 - k4 b3,  a1 = Di r1 - Bi r2,  a2 = Ai r2 - Bi r1,
+//   a0 = (b0 - 2X a1 - 2Y a2) i0,  a3 = (b3 + tY a1 + tX a2) i3.
 template <typename T>
-__device__ __forceinline__ void solve_mirrored(T sA, T X, T Y, const T b[4], T ap[4]) {
+struct CellSolve { T k1, k2, k3, k4, Ai, Bi, Di, i0, i3; };
+
+template <typename T>
+__device__ __forceinline__ CellSolve<T> cell_solve(T sA, T X, T Y) {
     const T twoX = T(2) * X, twoY = T(2) * Y, tX = T(2.0 / 3.0) * X, tY = T(2.0 / 3.0) * Y;
     const T d0 = sA + twoX + twoY;
     const T d1 = sA * T(1.0 / 3.0) + twoX + tY;
     const T d2 = sA * T(1.0 / 3.0) + tX + twoY;
     const T d3 = sA * T(1.0 / 9.0) + tX + tY;
-    const T i0 = rcp_(d0), i3 = rcp_(d3);
-    const T A = d1 + twoX * twoX * i0 + tY * tY * i3;
-    const T B = twoX * twoY * i0 + tX * tY * i3;
-    const T D = d2 + twoY * twoY * i0 + tX * tX * i3;
-    const T r1 = b[1] + twoX * b[0] * i0 - tY * b[3] * i3;
-    const T r2 = b[2] + twoY * b[0] * i0 - tX * b[3] * i3;
-    const T idet = rcp_(A * D - B * B);
-    const T a1 = (D * r1 - B * r2) * idet;
-    const T a2 = (A * r2 - B * r1) * idet;
-    ap[0] = (b[0] - twoX * a1 - twoY * a2) * i0;
-    ap[1] = a1;
-    ap[2] = a2;
-    ap[3] = (b[3] + tY * a1 + tX * a2) * i3;
+    CellSolve<T> c;
+    c.i0 = sweep_rcp(d0);
+    c.i3 = sweep_rcp(d3);
+    const T A = d1 + twoX * twoX * c.i0 + tY * tY * c.i3;
+    const T B = twoX * twoY * c.i0 + tX * tY * c.i3;
+    const T D = d2 + twoY * twoY * c.i0 + tX * tX * c.i3;
+    const T idet = sweep_rcp(A * D - B * B);
+    c.k1 = twoX * c.i0; c.k2 = tY * c.i3; c.k3 = twoY * c.i0; c.k4 = tX * c.i3;
+    c.Ai = A * idet; c.Bi = B * idet; c.Di = D * idet;
+    return c;
 }
 
+// cell data prefetch depth of the sweep, in wavefront steps (a ring of register sets, unrolled so
+// that no value moves between registers while its load is in flight)
+template <typename T> struct SweepDepth { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
+
 // Pipelined strip sweep, one CTA per ordinate, W warps. Warp w sweeps strips w, w+W, ... (lane =
-// row, one anti-diagonal per step). The trace leaving the top row of strip s goes through a
-// shared-memory ring slot (s mod W) to the first row of strip s+1, guarded by produced/consumed
-// counters; every wait is bounded and records kStSegments on exhaustion. Dependencies only point
-// to lower strips, and all warps of the CTA are resident, so the pipeline always advances.
+// row, one anti-diagonal per step). The trace leaving the top row of strip s goes through entry
+// (slot s mod W, column c) of a tagged shared-memory ring to the first row of strip s+1; the
+// reader waits until the entry carries its sequence number. When strips outnumber the warps a
+// slot is reused, and its writer first waits for the previous reader's consumed-column counter
+// (published once per prefetch block). Every wait is bounded and records kStSegments on
+// exhaustion. Dependencies only point to lower strips, and all warps of the CTA are resident, so
+// the pipeline always advances. The step body is branch-free apart from the (uniform) waits.
 template <typename T>
-__global__ void sweep_pipe_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
+    constexpr int PF = SweepDepth<T>::value;
+    constexpr int RW = Ring<T>::kWords;
     if (*(volatile const int*)a.conv) return;
     extern __shared__ unsigned char smraw[];
     const int W = a.W;
-    volatile int* prod = (volatile int*)smraw;
-    volatile int* cons = prod + W;
-    T* ring = (T*)(smraw + ((2 * W * sizeof(int) + 15) / 16) * 16);   // W x nx x 2
+    const int nx = a.nx, ny = a.ny;
+    volatile int* cons = (volatile int*)smraw;
+    volatile unsigned long long* ring =
+        (volatile unsigned long long*)(smraw + ((W * sizeof(int) + 15) / 16) * 16);   // W x nx x RW
+    for (int i = threadIdx.x; i < W; i += blockDim.x) cons[i] = 0;
+    for (int i = threadIdx.x; i < W * nx * RW; i += blockDim.x) ring[i] = 0ull;   // no tag is 0
+    __syncthreads();
     const int m = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x < W) { prod[threadIdx.x] = 0; cons[threadIdx.x] = 0; }
-    __syncthreads();
     const int quad = m / a.nq;
     const int sx = (quad == 0 || quad == 3) ? 1 : -1;
     const int sy = (quad <= 1) ? 1 : -1;
@@ -111,84 +195,92 @@ __global__ void sweep_pipe_kernel(SweepArgs<T> a) {
     const T wq = a.qw[m];
     const T X = fabs(a.qox[m]) * a.dy * T(0.5), Y = fabs(a.qoy[m]) * a.dx * T(0.5);
     const T twoX = T(2) * X, twoY = T(2) * Y, tX = T(2.0 / 3.0) * X, tY = T(2.0 / 3.0) * Y;
-    T* out = a.psi + (size_t)m * a.nx * a.ny * 4;
-    const int nx = a.nx, ny = a.ny;
+    const T w1 = wq * sxf, w2 = wq * syf, w3 = wq * sxy;
+    T* out = a.psi + (size_t)m * nx * ny * 4;
     const int nstrip = (ny + 31) / 32;
+    const bool reuse = nstrip > W;
+    const int nsteps = nx + 31;
     bool timed_out = false;
-    for (int s = warp; s < nstrip; s += W) {
+    for (int s = warp; s < nstrip && !timed_out; s += W) {
         const int ly = 32 * s + lane;
         const bool row_ok = ly < ny;
         const int iy = sy > 0 ? ly : ny - 1 - ly;
+        const size_t rowk = (size_t)iy * nx;
         const int bin = (s - 1 + W) % W, bout = s % W;
         const int qin = ((s - 1) / W) * nx, qout = (s / W) * nx;   // sequence bases of the ring slots
         const bool has_in = s > 0, has_out = s + 1 < nstrip;
-        volatile T* rin = ring + (size_t)bin * nx * 2;
-        volatile T* rout = ring + (size_t)bout * nx * 2;
+        const bool put = has_out && lane == 31;
+        volatile unsigned long long* rin = ring + (size_t)bin * nx * RW;
+        volatile unsigned long long* rout = ring + (size_t)bout * nx * RW;
         T bx0 = 0, bx1 = 0, oy0 = 0, oy1 = 0;
-        int c = -lane;
-        // cell data three steps ahead (L2 latency spans several wavefront steps)
-        T q0[5] = {0, 0, 0, 0, 1}, q1[5] = {0, 0, 0, 0, 1}, q2[5] = {0, 0, 0, 0, 1};
-        auto load = [&](int col, T* d) {
-            if (row_ok && col >= 0 && col < nx) {
-                const int ix = sx > 0 ? col : nx - 1 - col;
-                const size_t k = (size_t)iy * nx + ix;
-                const T* sp = a.src + 4 * k;
-                d[0] = __ldg(sp); d[1] = __ldg(sp + 1); d[2] = __ldg(sp + 2); d[3] = __ldg(sp + 3);
-                d[4] = __ldg(a.sgA + k);
-            }
-        };
-        load(c, q0);
-        load(c + 1, q1);
-        load(c + 2, q2);
-        for (int t = 0; t < nx + 31; ++t, ++c) {
-            const T S0 = q0[0], S1 = q0[1], S2 = q0[2], S3 = q0[3], sA = q0[4];
+        CellIn<T> q[PF];
 #pragma unroll
-            for (int i = 0; i < 5; ++i) { q0[i] = q1[i]; q1[i] = q2[i]; }
-            load(c + 3, q2);
-            const bool act = row_ok && c >= 0 && c < nx;
-            // lane 0 needs the trace of column c from strip s-1; the top lane must not overwrite
-            // ring slot column c before strip s+1-W's consumer has read it
-            const bool wait_in = has_in && lane == 0 && act;
-            const bool wait_out = has_out && lane == 31 && act;
-            int spins = 0;
-            while (__any_sync(0xffffffffu, (wait_in && prod[bin] < qin + c + 1) ||
-                                               (wait_out && cons[bout] < qout + c + 1 - nx))) {
-                if (++spins > (1 << 22)) { timed_out = true; break; }
-                __nanosleep(32);
-            }
-            const T u0 = __shfl_up_sync(0xffffffffu, oy0, 1);
-            const T u1 = __shfl_up_sync(0xffffffffu, oy1, 1);
-            if (act) {
-                T by0, by1;
-                if (lane == 0) {
-                    if (has_in) {
-                        by0 = rin[2 * c]; by1 = rin[2 * c + 1];
-                        __threadfence_block();
-                        cons[bin] = qin + c + 1;
-                    } else { by0 = 0; by1 = 0; }
-                } else { by0 = u0; by1 = u1; }
-                if (c == 0) { bx0 = 0; bx1 = 0; }
-                const T b[4] = {S0 + twoX * bx0 + twoY * by0,
-                                sxf * S1 - twoX * bx0 + tY * by1,
-                                syf * S2 + tX * bx1 - twoY * by0,
-                                sxy * S3 - tX * bx1 - tY * by1};
-                T ap[4];
-                solve_mirrored<T>(sA, X, Y, b, ap);
-                bx0 = ap[0] + ap[1]; bx1 = ap[2] + ap[3];
-                oy0 = ap[0] + ap[2]; oy1 = ap[1] + ap[3];
-                const int ix = sx > 0 ? c : nx - 1 - c;
-                T* d = out + ((size_t)iy * nx + ix) * 4;
-                d[0] = wq * ap[0]; d[1] = wq * sxf * ap[1]; d[2] = wq * syf * ap[2]; d[3] = wq * sxy * ap[3];
-                if (lane == 31 && has_out) {
-                    rout[2 * c] = oy0; rout[2 * c + 1] = oy1;
-                    __threadfence_block();
-                    prod[bout] = qout + c + 1;
+        for (int i = 0; i < PF; ++i) {
+            q[i] = CellIn<T>{0, 0, 0, 0, 1};
+            const int col = i - lane;
+            if (row_ok && col >= 0 && col < nx) load_cell<T>(a.src, a.sgA, rowk + (sx > 0 ? col : nx - 1 - col), q[i]);
+        }
+        for (int t0 = 0; t0 < nsteps; t0 += PF) {
+            // a reused slot: the previous reader must have taken the columns this block writes
+            if (reuse && has_out && s >= W) {
+                const int need = qout - nx + (t0 + PF - 31 < nx ? t0 + PF - 31 : nx);
+                int spins = 0;
+                while (cons[bout] < need) {
+                    if (++spins > (1 << 22)) { timed_out = true; break; }
+                    __nanosleep(20);
                 }
             }
-            __syncwarp();
-            if (timed_out) break;
+#pragma unroll
+            for (int i = 0; i < PF; ++i) {
+                const int t = t0 + i;
+                const int c = t - lane;
+                const bool act = row_ok && c >= 0 && c < nx;
+                const T u0 = __shfl_up_sync(0xffffffffu, oy0, 1);
+                const T u1 = __shfl_up_sync(0xffffffffu, oy1, 1);
+                T by0 = u0, by1 = u1;
+                if (has_in && t < nx) {
+                    // every lane reads lane 0's entry (one broadcast), so the wait is uniform
+                    T r0, r1;
+                    const uint32_t tag = (uint32_t)(qin + t + 1);
+                    int spins = 0;
+                    while (!Ring<T>::get(rin + (size_t)t * RW, tag, &r0, &r1) && !timed_out) {
+                        if (++spins > (1 << 22)) timed_out = true;
+                        __nanosleep(20);
+                    }
+                    if (lane == 0) { by0 = r0; by1 = r1; }
+                } else if (lane == 0) {
+                    by0 = 0; by1 = 0;
+                }
+                bx0 = c == 0 ? T(0) : bx0;
+                bx1 = c == 0 ? T(0) : bx1;
+                const CellSolve<T> cs = cell_solve<T>(q[i].sA, X, Y);
+                const T b0 = q[i].s0 + twoX * bx0 + twoY * by0;
+                const T b1 = sxf * q[i].s1 - twoX * bx0 + tY * by1;
+                const T b2 = syf * q[i].s2 + tX * bx1 - twoY * by0;
+                const T b3 = sxy * q[i].s3 - tX * bx1 - tY * by1;
+                const T r1 = b1 + cs.k1 * b0 - cs.k2 * b3;
+                const T r2 = b2 + cs.k3 * b0 - cs.k4 * b3;
+                const T a1 = cs.Di * r1 - cs.Bi * r2;
+                const T a2 = cs.Ai * r2 - cs.Bi * r1;
+                const T a0 = (b0 - twoX * a1 - twoY * a2) * cs.i0;
+                const T a3 = (b3 + tY * a1 + tX * a2) * cs.i3;
+                bx0 = a0 + a1; bx1 = a2 + a3;
+                oy0 = a0 + a2; oy1 = a1 + a3;
+                if (act) {
+                    const int ix = sx > 0 ? c : nx - 1 - c;
+                    store_cell(out + (rowk + ix) * 4, wq * a0, w1 * a1, w2 * a2, w3 * a3);
+                    if (put) Ring<T>::put(rout + (size_t)c * RW, oy0, oy1, (uint32_t)(qout + c + 1));
+                }
+                const int col = c + PF;
+                if (row_ok && col >= 0 && col < nx) load_cell<T>(a.src, a.sgA, rowk + (sx > 0 ? col : nx - 1 - col), q[i]);
+            }
+            // publish the columns this warp has taken from its input slot (only needed on reuse)
+            if (reuse && has_in && lane == 0) {
+                __threadfence_block();
+                cons[bin] = qin + (t0 + PF < nx ? t0 + PF : nx);
+            }
+            if (__any_sync(0xffffffffu, timed_out)) { timed_out = true; break; }
         }
-        if (timed_out) break;
     }
     if (timed_out && lane == 0) atomicOr(a.status, kStSegments);
 }
@@ -268,10 +360,10 @@ __global__ void sn_to_double_kernel(const T* phi, double* out, int n) {
 template <typename T>
 static int sweep_warps(const hyb_problem* p, size_t* smem) {
     const int nstrip = (p->ny + 31) / 32;
-    const size_t per = (size_t)p->nx * 2 * sizeof(T);
+    const size_t per = (size_t)p->nx * Ring<T>::kWords * sizeof(unsigned long long);
     int W = nstrip < 16 ? nstrip : 16;
     while (W > 1 && (size_t)W * per + 256 > 160 * 1024) --W;
-    *smem = ((2 * W * sizeof(int) + 15) / 16) * 16 + (size_t)W * per;
+    *smem = ((W * sizeof(int) + 15) / 16) * 16 + (size_t)W * per;
     return W;
 }
 

@@ -46,7 +46,7 @@ class Stats(C.Structure):
                [(k, C.c_double) for k in ("w_source", "w_absorbed", "w_leaked", "w_census",
                                           "w_handoff", "w_killed")] + \
                [("sn_iterations", C.c_int32), ("combed", C.c_int32), ("bank_size", C.c_int64),
-                ("ms", C.c_float), ("pad", C.c_int32)]
+                ("ms", C.c_float), ("pad", C.c_int32), ("tally_adds", C.c_int64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
@@ -101,6 +101,7 @@ def lib():
         L.hyb_batch_last_error.argtypes = [P]
         L.hyb_build_cdf.argtypes = [P, C.c_int32, C.c_int32, P, P, P, P, P, C.c_size_t, P]
         L.hyb_quadrature.argtypes = [C.c_int32, P, P, P, C.POINTER(C.c_int32)]
+        L.hyb_atomic_rate.argtypes = [C.c_int64, C.c_int64, P, C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -282,6 +283,15 @@ def points(seed: int, step: int, stream_id: int, sampler: int, i0: int, n: int, 
     _check(lib().hyb_points(C.c_uint64(seed), step, stream_id, sampler, i0, n, ndims,
                             C.c_void_p(out.data_ptr()), C.c_void_p(s.cuda_stream)))
     return out
+
+
+def atomic_rate(n_addr: int, n_ops: int = 1 << 28, stream=None) -> float:
+    """Measured 64-bit global atomic additions per second to n_addr random addresses."""
+    torch = _torch_cuda()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    r = C.c_double(0.0)
+    _check(lib().hyb_atomic_rate(n_addr, n_ops, C.c_void_p(s.cuda_stream), C.byref(r)))
+    return float(r.value)
 
 
 def build_cdf(w, nx: int, ny: int, stream=None):

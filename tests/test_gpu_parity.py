@@ -235,6 +235,44 @@ def test_collided_solve_parity(H, orc, order, n):
     assert np.allclose(phi_g, phi_o, rtol=1e-9, atol=1e-10 * scale)
 
 
+@pytest.mark.parametrize("order", [4, 8])
+def test_collided_solve_fp32(H, orc, order):
+    """FP32 collided stage: the GPU's own hand-off moments solved by the FP64 oracle; cells above
+    1e-3 of the peak agree within 1e-4 relative (stop test at 2e-6 relative change)."""
+    spec = W.checkerboard(n_s=1, n_hist=20_000, cells_per_block=5, precision=W.FP32).with_(sn_order=order,
+                                                                                          sn_tol=1e-7)
+    bank = W.random_bank(spec, 4000, seed=5)
+    g = gpu_leg(H, spec, bank, 0)
+    g["P"].collided_solve()
+    phi_g = g["P"].tally("sn_phi")
+    phi_o, _ = orc.sn_solve(spec.with_(precision=W.FP64, sn_tol=1e-13), g["mom"])
+    peak = np.max(np.abs(phi_o[:, 0]))
+    sel = np.abs(phi_o[:, 0]) >= 1e-3 * peak
+    err = np.max(np.abs(phi_g[sel, 0] - phi_o[sel, 0]) / np.abs(phi_o[sel, 0]))
+    print(f"\nFP32 collided S{order}: max rel err of phi_0 on resolved cells {err:.2e}")
+    assert err < 1e-4
+    assert np.allclose(phi_g[:, 1:], phi_o[:, 1:], rtol=0, atol=1e-4 * peak)
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32])
+def test_collided_solve_tall_mesh(H, orc, prec):
+    """8 x 700 cells: 22 row strips for at most 16 warps, so strip-to-strip ring slots are reused."""
+    n = 8
+    sa = np.full(n * 700, 0.2)
+    ss = np.full(n * 700, 0.8)
+    spec = W.ProblemSpec(nx=n, ny=700, lx=1.0, ly=87.5, sigma_a=sa, sigma_s=ss, Q=np.ones(n * 700), c=1.0, dt=0.5,
+                         n_s=0, n_hist=20_000, seed=2, precision=prec, sn_order=8, sn_tol=1e-13 if prec == W.FP64 else 1e-7)
+    g = gpu_leg(H, spec, None, 0)
+    g["P"].collided_solve()
+    phi_g = g["P"].tally("sn_phi")
+    phi_o, _ = orc.sn_solve(spec.with_(precision=W.FP64, sn_tol=1e-13), g["mom"])
+    scale = np.max(np.abs(phi_o[:, 0]))
+    if prec == W.FP64:
+        assert np.allclose(phi_g, phi_o, rtol=1e-9, atol=1e-10 * scale)
+    else:
+        assert np.allclose(phi_g, phi_o, rtol=1e-4, atol=1e-5 * scale)
+
+
 @pytest.mark.parametrize("cap", [0, 10 ** 7])
 def test_remap_parity(H, orc, cap):
     spec = W.checkerboard(n_s=2, n_hist=20_000, cells_per_block=4).with_(census_cap=cap)
