@@ -107,9 +107,10 @@ def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0
 
 
 def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
+    """Kernels of this library launched by one single-problem step (memsets not counted)."""
     leg = 2                                   # leg kernel + normalisation
-    sn = 4 * sn_iters + 2                     # source, sweep, reduce, norm per SI iteration; copy, flux
-    remap = 1 + 4 + 1 + 3 + 1                 # density, CDF (4), prep, count/scan/write, finish
+    sn = 1 + 1 + 2 * sn_iters + 3             # seed, source; sweep + reduce per iteration; copy, done, flux
+    remap = 1 + 5 + 1 + 3 + 1                 # density, CDF (5 with the guide tables), prep, count/scan/write, finish
     return leg + sn + remap
 
 
@@ -132,32 +133,28 @@ def run_gpu(args, rank: int, world: int) -> dict:
             if world > 1:
                 import torch.distributed as dist
                 dist.barrier()
-            e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-            e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
             hist = segs = 0
             phase = {"mc_leg": [], "collided_sn": [], "remap": []}
-            sn_it = []
+            sn_it, step_ms = [], []
             clk = Clocks(dev.index)
             with clk:
                 t0 = time.perf_counter()
                 for k in range(args.steps):
                     flush.zero_()
-                    e0[k].record(stream)
-                    ls = P.mc_leg()
-                    cs = P.collided_solve()
-                    rs = P.remap()
-                    e1[k].record(stream)
-                    hist += ls["histories"]
-                    segs += ls["segments"] + rs["segments"]
-                    phase["mc_leg"].append(ls["ms"])
-                    phase["collided_sn"].append(cs["ms"])
-                    phase["remap"].append(rs["ms"])
-                    sn_it.append(cs["sn_iterations"])
+                    st = P.step(1)[0]      # CUDA events on the problem stream around each phase
+                    step_ms.append(st["ms"])
+                    hist += st["histories"]
+                    segs += st["segments"]
+                    phase["mc_leg"].append(st["ms_leg"])
+                    phase["collided_sn"].append(st["ms_sn"])
+                    phase["remap"].append(st["ms_remap"])
+                    sn_it.append(st["sn_iterations"])
                 torch.cuda.synchronize()
+                if world > 1:
+                    dist.barrier()
                 wall = time.perf_counter() - t0
-            step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
             res[prec] = dict(spec=spec, P=P, hist=hist, segs=segs, step_ms=step_ms, wall=wall,
-                             clocks=clk.summary(), sn_iters=sn_it, bank=rs["bank_size"],
+                             clocks=clk.summary(), sn_iters=sn_it, bank=st["bank_size"],
                              phase_ms={k: statistics.median(v) for k, v in phase.items()})
     return res
 
@@ -372,12 +369,17 @@ def main():
     value = hist_all / (tot_ms / 1000.0)
     pk = peaks()
     prof = leg_profile(W.FP32)
-    # MC-leg algorithmic HBM bytes: census pickup (24 B per bank particle), one 8-byte fixed-point
-    # add per pre-limit segment and five per post-limit segment are not HBM traffic after L2
-    # aggregation, so the algorithmic bytes are the bank stream plus the tally arrays.
-    nc = 112 * 112
-    leg_bytes = prof["bank"] * 24 + 3 * nc * 8 + 4 * nc * 8
-    achieved = leg_bytes / (prof["ms"] / 1000.0) / 1e9
+    # The MC leg's roofline (the hot path's target): its algorithmic work is one fixed-point tally
+    # addition per pre-limit segment and five per post-limit segment (all counted by the kernel:
+    # hyb_leg_stats.tally_adds) plus the census pick-up stream of 24 B per bank particle. Its
+    # bound is the rate of 64-bit global atomic additions to the tally footprint (measured live
+    # with hyb_atomic_rate on 6 x ncells addresses); the HBM view is reported beside it.
+    from paper_2511_16821_gb300 import hyb
+    atomic_peak = hyb.atomic_rate(6 * prof["ncells"])
+    leg_s = prof["ms"] / 1000.0
+    adds_rate = prof["tally_adds"] / leg_s
+    leg_bytes = prof["bank"] * 24
+    hbm_achieved = leg_bytes / leg_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -386,10 +388,14 @@ def main():
         "segments_per_s": segs_all / (tot_ms / 1000.0),
         "sn_iterations": r32["sn_iters"],
         "phase_ms": r32["phase_ms"],
-        "roofline": {"bound": "hbm", "kernel": "mc_leg_kernel<float>", "achieved": achieved,
-                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                     "traffic": None, "leg_ms": prof["ms"], "leg_histories": prof["histories"],
-                     "leg_segments": prof["segments"], "peak_src": pk["src"]},
+        "roofline": {"bound": "atomic", "kernel": "mc_leg_kernel<float>", "achieved": adds_rate / 1e9,
+                     "peak": atomic_peak / 1e9, "unit": "Gatomic/s", "frac": adds_rate / atomic_peak,
+                     "traffic": None,
+                     "peak_src": "measured live: hyb_atomic_rate, 64-bit adds to 6 x ncells random addresses",
+                     "leg_ms": prof["ms"], "leg_histories": prof["histories"], "leg_segments": prof["segments"],
+                     "tally_adds": prof["tally_adds"],
+                     "hbm": {"achieved": hbm_achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                             "frac": hbm_achieved / pk["hbm_gbs"], "bytes": leg_bytes, "peak_src": pk["src"]}},
         "gpu_launches": launches_per_step(r32["spec"], int(np.mean(r32["sn_iters"]) + 0.5)) * args.steps,
         "clocks": r32["clocks"],
     }

@@ -108,6 +108,8 @@ typedef struct {
     int32_t pad;
     int64_t tally_adds;       /* MC leg: fixed-point tally additions issued (global 64-bit atomics;
                                  the FP64 path adds up to two words per contribution) */
+    float ms_leg, ms_sn, ms_remap;   /* hyb_step: device time of steps 1, 2 and 3-4 */
+    int32_t pad1;
 } hyb_leg_stats;
 
 typedef struct hyb_problem hyb_problem;
@@ -156,8 +158,12 @@ HYB_API hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* stats);
  * Needs an MC leg and a collided solve of the same step. stats as for hyb_mc_leg. */
 HYB_API hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* stats);
 
-/* nsteps full steps (1-4). per_step (host, may be NULL): nsteps entries, leg statistics with
- * sn_iterations / combed / bank_size of the step. */
+/* nsteps full steps (1-4, Sec. 2.2). per_step (host, may be NULL): nsteps entries, leg
+ * statistics with sn_iterations / combed / bank_size of the step, ms = whole step and
+ * ms_leg / ms_sn / ms_remap per phase. A step waits for the device once inside the source
+ * iteration (stop test) and, with per_step, once at its end; without per_step the call
+ * synchronises the stream at the end. Device loop bounds map to ETIMEOUT, index checks to
+ * EBOUNDS. */
 HYB_API hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step);
 
 /* Copy a tally (see HYB_TALLY_*) into dst (host if dst_on_device == 0, else device), n values.

@@ -203,6 +203,21 @@ def mc_leg(spec, step: int, bank: dict | None, want_hist: bool = False, want_cen
     return out
 
 
+def mc_leg_range(spec, step: int, bank: dict | None, h0: int, h1: int):
+    """The leg over global history indices [h0, h1) (bank slots first, then births), as one rank
+    of a history-sharded leg: dict(pre, post, mom, stats, hist) for that range only."""
+    p, keep = _problem(spec)
+    nc = spec.nx * spec.ny
+    pre, post, mom = np.zeros(nc), np.zeros(nc), np.zeros(4 * nc)
+    st = _Stats()
+    cb = _bank(bank)
+    hist = np.zeros((max(h1 - h0, 1), 4), np.int32)
+    rc = lib().or_mc_leg_range(C.byref(p), C.c_int64(step), C.byref(cb) if cb else None, C.c_int64(h0),
+                               C.c_int64(h1), _dp(pre), _dp(post), _dp(mom), C.byref(st), _ip(hist))
+    s = _stats_dict(st)
+    return dict(pre=pre, post=post, mom=mom.reshape(nc, 4), stats=s, rc=rc, hist=hist[: s["histories"]])
+
+
 def sn_solve(spec, mom: np.ndarray):
     p, keep = _problem(spec)
     nc = spec.nx * spec.ny

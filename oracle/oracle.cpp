@@ -957,8 +957,26 @@ int or_mc_leg(const or_problem* P, int64_t step, const or_bank* census, double* 
 }
 
 // The MC leg with, per cell, the number of segments scored into the pre and post tallies.
+// The MC leg over the histories with global index h in [h0, h1) only (index order: census bank
+// slots, then source births), as one rank of a history-sharded leg would run it; hist rows and
+// statistics cover that range.
+static int leg_range(const or_problem* P, int64_t step, const or_bank* census, int64_t h0, int64_t h1, double* pre,
+                     double* post, double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n,
+                     int64_t* post_n);
+
 int or_mc_leg_counts(const or_problem* P, int64_t step, const or_bank* census, double* pre, double* post,
                      double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n, int64_t* post_n) {
+    return leg_range(P, step, census, 0, INT64_MAX, pre, post, mom, st, hist, census_out, pre_n, post_n);
+}
+
+int or_mc_leg_range(const or_problem* P, int64_t step, const or_bank* census, int64_t h0, int64_t h1, double* pre,
+                    double* post, double* mom, or_stats* st, int32_t* hist) {
+    return leg_range(P, step, census, h0, h1, pre, post, mom, st, hist, nullptr, nullptr, nullptr);
+}
+
+static int leg_range(const or_problem* P, int64_t step, const or_bank* census, int64_t h0, int64_t h1, double* pre,
+                     double* post, double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n,
+                     int64_t* post_n) {
     build_sobol_table();
     Leg L(P);
     const Mesh& M = L.M;
@@ -966,13 +984,15 @@ int or_mc_leg_counts(const or_problem* P, int64_t step, const or_bank* census, d
     L.census_out = census_out;
     if (census_out) census_out->n = 0;
     const double cdt = P->c * P->dt;
-    int64_t h = 0;
+    int64_t h = 0, ran = 0;
     if (census && census->n > 0) {
         L.pts.key = stream_key(P->seed, (uint64_t)step, kStreamLegCensus);
         for (int64_t j = 0; j < census->n; ++j, ++h) {
+            if (h < h0 || h >= h1) continue;
             int k = census->cell[j];
             L.run((uint64_t)j, k % M.nx, k / M.nx, census->fx[j], census->fy[j], census->ox[j],
-                  census->oy[j], census->w[j], cdt, hist ? hist + 4 * h : nullptr);
+                  census->oy[j], census->w[j], cdt, hist ? hist + 4 * ran : nullptr);
+            ++ran;
         }
     }
     std::vector<double> q(nc, 0.0);
@@ -983,12 +1003,14 @@ int or_mc_leg_counts(const or_problem* P, int64_t step, const or_bank* census, d
         const double w0 = W / (double)P->n_hist;
         L.pts.key = stream_key(P->seed, (uint64_t)step, kStreamLegSource);
         for (int64_t i = 0; i < P->n_hist; ++i, ++h) {
+            if (h < h0 || h >= h1) continue;
             double frx, fry, ox, oy;
             int k = sample_cell(C, L.pts(i, 0), L.pts(i, 1), &frx, &fry);
             const double tf = unit(L.pts(i, 2));
             iso_direction(unit(L.pts(i, 3)), unit(L.pts(i, 4)), &ox, &oy);
             L.run((uint64_t)i, k % M.nx, k / M.nx, frx * M.dx, fry * M.dy, ox, oy, w0,
-                  cdt * (1.0 - tf), hist ? hist + 4 * h : nullptr);
+                  cdt * (1.0 - tf), hist ? hist + 4 * ran : nullptr);
+            ++ran;
         }
     }
     for (size_t k = 0; k < nc; ++k) {
@@ -997,7 +1019,7 @@ int or_mc_leg_counts(const or_problem* P, int64_t step, const or_bank* census, d
         if (pre_n) pre_n[k] = L.pre_n[k];
         if (post_n) post_n[k] = L.post_n[k];
     }
-    fill_stats(L, h, st);
+    fill_stats(L, ran, st);
     if (L.census_overflow) return 3;
     return L.errors ? 4 : 0;
 }

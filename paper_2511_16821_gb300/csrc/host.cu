@@ -208,7 +208,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
-        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol;
+        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos;
     int64_t cap, nblk;
     int gr, gc;
 };
@@ -241,13 +241,15 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.sntx = (size_t)nord * nc * 4 * T;           // w_m psi_m per ordinate and cell
     z.snty = (size_t)nord * d->nx * 2 * T;        // strip-top traces per ordinate
     z.snqb = 3 * kMaxOrd * T;
-    z.snnorm = 2 * ((nc + 255) / 256) * 8;
+    z.snnorm = 2 * ((nc + 31) / 32) * 8;          // per reduction block (32 cells)
     z.nblk = (z.cap + d->n_hist + 2047) / 2048;
     z.blk = 4 * (size_t)z.nblk * 8;
     z.gr = hyb::guide_bits(d->ny);
     z.gc = hyb::guide_bits(d->nx);
     z.grow = ((size_t(1) << z.gr) + 1) * 4;
     z.gcol = (size_t)d->ny * ((size_t(1) << z.gc) + 1) * 4;
+    z.remf32 = 4 * nc * 4;
+    z.rempos = nc * 4;
     return z;
 }
 
@@ -257,7 +259,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
     const size_t parts[] = {z.st, z.sobol, z.sig, z.sa, z.ss, z.Q, z.cdf_q, z.cdf_row, z.cdf_col, z.cdf_q, z.cdf_row,
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4,
-                            z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol};
+                            z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -309,6 +311,8 @@ void assign(hyb_problem* p) {
     p->rem_cdf.col_g = (int*)take(z.gcol);
     p->src_cdf.gr = p->rem_cdf.gr = z.gr;
     p->src_cdf.gc = p->rem_cdf.gc = z.gc;
+    p->rem_f32 = (float*)take(z.remf32);
+    p->rem_pos = (int*)take(z.rempos);
     p->bank_cap = z.cap;
     p->nblk_max = z.nblk;
 }
@@ -528,6 +532,7 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     p->leg_done = p->sn_done = false;
     p->sn_warm = false;
     p->ev0 = p->ev1 = nullptr;
+    for (auto& e : p->evs) e = nullptr;
     p->st_host = nullptr;
     if (workspace) { p->ws = workspace; p->ws_bytes = ws_bytes; p->owns_ws = false; }
     else {
@@ -544,6 +549,8 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     if (cudaMallocHost((void**)&p->st_host, sizeof(DevState)) != cudaSuccess) return bail(fail(p, HYB_ENOMEM, "pinned alloc"));
     if (cudaEventCreate(&p->ev0) != cudaSuccess || cudaEventCreate(&p->ev1) != cudaSuccess)
         return bail(fail(p, HYB_ECUDA, "event create"));
+    for (auto& e : p->evs)
+        if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(p, HYB_ECUDA, "event create"));
     const size_t nc = (size_t)p->ncells;
     p->sig_s_max = 0;
     for (size_t k = 0; k < nc; ++k) p->sig_s_max = std::max(p->sig_s_max, d->sigma_s[k]);
@@ -609,15 +616,16 @@ hyb_status hyb_destroy_problem(hyb_problem* p) {
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
+    for (auto e : p->evs)
+        if (e) cudaEventDestroy(e);
     delete p;
     return HYB_OK;
 }
 
-static hyb_status leg_impl(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) {
-    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+// step 1 launches (no host synchronisation)
+static hyb_status leg_launch(hyb_problem* p, int32_t* hist) {
     const size_t nc = (size_t)p->ncells;
     const size_t acc = p->prec == HYB_FP64 ? 16 : 8;
-    HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->acc_pre, 0, nc * acc, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->acc_post, 0, nc * acc, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, 4 * nc * acc, p->stream));
@@ -625,9 +633,17 @@ static hyb_status leg_impl(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) {
     HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
     HYB_CU(p, launch_mc_leg(p, hist));
     HYB_CU(p, launch_leg_normalise(p));
-    HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
     p->leg_done = true;
     p->sn_done = false;
+    return HYB_OK;
+}
+
+static hyb_status leg_impl(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) {
+    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
+    hyb_status s0 = leg_launch(p, hist);
+    if (s0 != HYB_OK) return s0;
+    HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
     if (out) {
         hyb_status s = pull_state(p);
         fill_leg_stats(p, out);
@@ -642,37 +658,48 @@ static hyb_status leg_impl(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) {
 hyb_status hyb_mc_leg(hyb_problem* p, hyb_leg_stats* out) { return leg_impl(p, nullptr, out); }
 hyb_status hyb_mc_leg_trace(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) { return leg_impl(p, hist, out); }
 
-hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
-    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
-    if (!p->leg_done) return fail(p, HYB_ESTATE, "collided solve needs an MC leg of this step");
-    HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
-    HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+// step 2: source iteration with a device-side stop test. With a warm start the previous step's
+// count predicts this one: that many iterations are queued without a read-back (iterations after
+// convergence return at once), then the flag is read once, and only a solve that needs more
+// iterations reads it after each further one. *iters: iterations taken. keep_status: the status
+// word still holds the leg's bits of this step (checked here together with the sweep's).
+static hyb_status sn_run(hyb_problem* p, int* iters, bool keep_status) {
+    if (!keep_status) HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
     HYB_CU(p, sn_start(p));
-    // with a warm start the previous step's count predicts this one: the first (count - 2)
-    // iterations run without a convergence read-back; converged iterations return at once
-    const int unchecked = (p->sn_warm && p->last_sn_iters > 2) ? p->last_sn_iters - 2 : 0;
-    int it = 0;
-    bool conv = false;
-    for (it = 1; it <= p->d.sn_max_iter; ++it) {
+    const int unchecked = (p->sn_warm && p->last_sn_iters > 0) ? std::min(p->last_sn_iters, p->d.sn_max_iter) : 0;
+    for (int it = 1; it <= p->d.sn_max_iter; ++it) {
         HYB_CU(p, sn_iteration(p, it == 1));
-        if (it <= unchecked) continue;
+        if (it < unchecked) continue;
         HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_conv, &p->st->sn_conv, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                                   p->stream));
         HYB_CU(p, cudaStreamSynchronize(p->stream));
-        if (p->st_host->sn_conv) { conv = true; break; }
+        if (p->st_host->sn_conv) break;
     }
-    (void)conv;
     HYB_CU(p, cudaMemcpyAsync(&p->st_host->status, &p->st->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
     HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_conv, &p->st->sn_conv, 2 * sizeof(int), cudaMemcpyDeviceToHost,
                               p->stream));
     HYB_CU(p, cudaStreamSynchronize(p->stream));
-    if (p->st_host->status & kStSegments) return fail(p, HYB_ETIMEOUT, "S_N sweep pipeline wait exhausted");
-    it = p->st_host->sn_iters;
+    if (p->st_host->status & kStBounds) return fail(p, HYB_EBOUNDS, "device index check failed (bank cell out of range)");
+    if (p->st_host->status & kStSegments)
+        return fail(p, HYB_ETIMEOUT, keep_status ? "a device loop bound was exhausted (history segments or sweep wait)"
+                                                 : "S_N sweep pipeline wait exhausted");
+    const int it = p->st_host->sn_iters;
     HYB_CU(p, sn_finish(p));
-    HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
     p->last_sn_iters = it;
     p->sn_done = true;
     p->sn_warm = p->d.sn_warm_start != 0;
+    *iters = it;
+    return HYB_OK;
+}
+
+hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
+    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    if (!p->leg_done) return fail(p, HYB_ESTATE, "collided solve needs an MC leg of this step");
+    HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
+    int it = 0;
+    hyb_status s = sn_run(p, &it, false);
+    if (s != HYB_OK) return s;
+    HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
     if (out) {
         std::memset(out, 0, sizeof(*out));
         HYB_CU(p, cudaEventSynchronize(p->ev1));
@@ -684,16 +711,23 @@ hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
     return HYB_OK;
 }
 
+// steps 3-4 launches (no host synchronisation)
+static hyb_status remap_launch(hyb_problem* p) {
+    HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+    HYB_CU(p, launch_remap(p));
+    p->cur = 1 - p->cur;
+    p->step += 1;           // the remap's last kernel advances the device step
+    p->leg_done = p->sn_done = false;
+    return HYB_OK;
+}
+
 hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* out) {
     if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
     if (!p->leg_done || !p->sn_done) return fail(p, HYB_ESTATE, "remap needs an MC leg and a collided solve of this step");
     HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
-    HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
-    HYB_CU(p, launch_remap(p));
+    hyb_status s0 = remap_launch(p);
+    if (s0 != HYB_OK) return s0;
     HYB_CU(p, cudaEventRecord(p->ev1, p->stream));
-    p->cur = 1 - p->cur;
-    p->step += 1;           // the remap's last kernel advances the device step
-    p->leg_done = p->sn_done = false;
     if (out) {
         hyb_status s = pull_state(p);
         fill_remap_stats(p, out);
@@ -705,26 +739,47 @@ hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* out) {
     return HYB_OK;
 }
 
+// A whole step synchronises with the host twice: once inside the source iteration (stop test)
+// and, with statistics, once at the end, when the leg and remap counters (kept apart in the
+// device state) are read together. The leg's status bits are checked with the remap's.
 hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
     if (!p || nsteps < 0) return fail(p, HYB_EINVAL, "bad arguments");
     for (int32_t i = 0; i < nsteps; ++i) {
-        hyb_leg_stats ls, ss, rs;
-        hyb_status s = hyb_mc_leg(p, per_step ? &ls : nullptr);
+        HYB_CU(p, cudaEventRecord(p->evs[0], p->stream));
+        hyb_status s = leg_launch(p, nullptr);
         if (s != HYB_OK) return s;
-        s = hyb_collided_solve(p, per_step ? &ss : nullptr);
+        HYB_CU(p, cudaEventRecord(p->evs[1], p->stream));
+        int it = 0;
+        s = sn_run(p, &it, true);
         if (s != HYB_OK) return s;
-        s = hyb_remap(p, per_step ? &rs : nullptr);
+        HYB_CU(p, cudaEventRecord(p->evs[2], p->stream));
+        s = remap_launch(p);
         if (s != HYB_OK) return s;
+        HYB_CU(p, cudaEventRecord(p->evs[3], p->stream));
         if (per_step) {
-            per_step[i] = ls;
-            per_step[i].sn_iterations = ss.sn_iterations;
+            s = pull_state(p);
+            hyb_leg_stats rs;
+            fill_leg_stats(p, &per_step[i]);
+            fill_remap_stats(p, &rs);
+            float m0 = 0, m1 = 0, m2 = 0;
+            cudaEventElapsedTime(&m0, p->evs[0], p->evs[1]);
+            cudaEventElapsedTime(&m1, p->evs[1], p->evs[2]);
+            cudaEventElapsedTime(&m2, p->evs[2], p->evs[3]);
+            per_step[i].sn_iterations = it;
             per_step[i].combed = rs.combed;
             per_step[i].bank_size = rs.bank_size;
-            per_step[i].ms = ls.ms + ss.ms + rs.ms;
+            per_step[i].ms = m0 + m1 + m2;
+            per_step[i].pad = 0;
+            per_step[i].ms_leg = m0; per_step[i].ms_sn = m1; per_step[i].ms_remap = m2;
+            if (s != HYB_OK) return s;
         }
     }
     if (!per_step) {
         HYB_CU(p, cudaStreamSynchronize(p->stream));
+        HYB_CU(p, cudaMemcpyAsync(&p->st_host->status, &p->st->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+        HYB_CU(p, cudaStreamSynchronize(p->stream));
+        if (p->st_host->status & kStBounds) return fail(p, HYB_EBOUNDS, "device index check failed");
+        if (p->st_host->status & kStSegments) return fail(p, HYB_ETIMEOUT, "a history exceeded the segment bound");
     }
     return HYB_OK;
 }

@@ -56,7 +56,7 @@ struct DevState {
     int sn_conv;               // collided solve: converged flag of the current solve
     int sn_iters;              // collided solve: iterations run in the current solve
     int sn_warm;               // 1 once a solve finished and warm starts are enabled
-    int pad2;
+    unsigned int sn_blocks_done;   // source-iteration reduction: blocks finished (last one resets it)
 };
 
 template <typename T>
@@ -109,6 +109,8 @@ struct hyb_problem {
     double *sa_d, *ss_d, *Q_d;  // FP64 copies for the remap density
     hyb::Cdf2DView src_cdf, rem_cdf;
     double* rem_f;            // 4 x ncells remap density coefficients
+    float* rem_f32;           // the same in FP32 (FP32 path)
+    int* rem_pos;             // ncells: 1 where the bilinear remap density is non-negative
     double* rem_q;            // ncells signed remap cell weights q = f0 A dt
     double* cell_scratch;     // per-row partials for the CDF build
     void* bank[2];            // two SoA banks (T)
@@ -130,6 +132,7 @@ struct hyb_problem {
     hyb::DevState* st;        // device counters
     hyb::DevState* st_host;   // pinned host mirror
     cudaEvent_t ev0, ev1;
+    cudaEvent_t evs[4];       // hyb_step phase boundaries: leg start, solve start, remap start, end
 };
 
 namespace hyb {

@@ -61,7 +61,9 @@ __device__ __forceinline__ void leg_tally_zero(LegTally& t) {
     t.status = 0;
 }
 
-// Scales of one leg (fixed point of the tallies and of the weight totals).
+// Scales of one leg (fixed point of the tallies and of the weight totals). On the FP32 path the
+// exponents are capped at 126 so that every scale is a finite float: a float product by a power of
+// two is exact, and the per-segment bookkeeping then needs no FP64 arithmetic.
 struct LegScales {
     int kt, km, kw;
     double scw;
@@ -74,9 +76,18 @@ __device__ __forceinline__ LegScales leg_scales(const LegArgs<T>& a) {
     s.kt = scale_exponent(Wstep * a.cdt_d, Prec<T>::kbits);
     s.km = scale_exponent(Wstep * a.cdt_d * a.sig_s_max, Prec<T>::kbits);
     s.kw = scale_exponent(Wstep, 61);
+    if (sizeof(T) == 4) {
+        s.kt = min(s.kt, 126);
+        s.km = min(s.km, 126);
+        s.kw = min(s.kw, 126);
+    }
     s.scw = ldexp(1.0, s.kw);
     return s;
 }
+
+// weight x in the fixed point of scale 2^kw: FP32 by an exact float product, FP64 as before
+__device__ __forceinline__ long long fix_w(float x, double, float scw_f) { return __float2ll_rn(x * scw_f); }
+__device__ __forceinline__ long long fix_w(double x, double scw, float) { return __double2ll_rn(x * scw); }
 
 // The histories [next, last) of one problem, tracked by the calling warp with lane refill: a lane
 // whose history ends takes the next index at once (ranks by ballot, deterministic order), so the
@@ -88,6 +99,8 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
     using P = Prec<T>;
     const T sc_t = (T)ldexp(1.0, sc.kt), sc_m = (T)ldexp(1.0, sc.km);
     const double scw = sc.scw;
+    const float scw_f = (float)sc.scw;     // used on the FP32 path only (kw <= 126 there)
+    constexpr bool kF32 = sizeof(T) == 4;
     const T DX = a.dx, DY = a.dy;
     const T INF = (T)INFINITY;
     const int Ns = a.n_s;
@@ -101,7 +114,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
     pts.ntab = a.ntab;
     Hist<T> h;
     bool alive = false;
-    double d_abs = 0, d_hand = 0;   // weight removed from the live history so far
+    double d_abs = 0, d_hand = 0;   // FP64 path: weight removed from the live history so far
 
     for (;;) {
         const unsigned need = __ballot_sync(0xffffffffu, !alive);
@@ -141,7 +154,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
                     pts.shift = h.census_stream ? sShC : sShS;
                     ++t.c[0];
                     h.w_start = h.w;
-                    t.f[0] += __double2ll_rn((double)h.w * scw);
+                    t.f[0] += fix_w(h.w, scw, scw_f);
                     d_abs = 0; d_hand = 0;
                     h.n = 0;
                     h.seg = 0;
@@ -174,7 +187,8 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
         if (h.n < Ns) {
             const T att = -P::exm1(-sa * l);
             t.c[8] += P::add(&a.pre[k], sa > T(0) ? h.w * att / sa : h.w * l, sc_t);
-            d_abs += (double)(h.w * att);
+            if constexpr (kF32) t.f[1] += fix_w(h.w * att, scw, scw_f);
+            else d_abs += (double)(h.w * att);
             h.w = h.w * P::ex(-sa * l);
             h.tau = P::msub(h.tau, ss, l);
         } else {
@@ -198,8 +212,13 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
                 }
             }
             if (st > T(0)) {
-                d_hand += (double)(h.w * att * (ss / st));
-                d_abs += (double)(h.w * att * (sa / st));
+                if constexpr (kF32) {
+                    t.f[4] += fix_w(h.w * att * (ss / st), scw, scw_f);
+                    t.f[1] += fix_w(h.w * att * (sa / st), scw, scw_f);
+                } else {
+                    d_hand += (double)(h.w * att * (ss / st));
+                    d_abs += (double)(h.w * att * (sa / st));
+                }
             }
             h.w = h.w * P::ex(-st * l);
         }
@@ -233,13 +252,15 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
         if (fate < 0 && h.seg >= (int)kMaxSegments) fate = kFateError;
         if (fate >= 0) {
             // ---- end of the history ------------------------------------------------------------
-            const long long fw = __double2ll_rn((double)h.w * scw);
+            const long long fw = fix_w(h.w, scw, scw_f);
             if (fate == kFateCensus) { ++t.c[4]; t.f[3] += fw; }
             else if (fate == kFateLeaked) { ++t.c[3]; t.f[2] += fw; }
             else if (fate == kFateKilled) { ++t.c[5]; t.f[5] += fw; }
             else { ++t.c[7]; t.status |= kStSegments; }
-            t.f[1] += __double2ll_rn(d_abs * scw);
-            t.f[4] += __double2ll_rn(d_hand * scw);
+            if constexpr (!kF32) {
+                t.f[1] += __double2ll_rn(d_abs * scw);
+                t.f[4] += __double2ll_rn(d_hand * scw);
+            }
             t.c[1] += (unsigned long long)h.seg;
             if (a.hist) {
                 const int4 r = make_int4(h.iy * nx + h.ix, fate, h.n, h.seg);

@@ -189,7 +189,8 @@ cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w, Cdf2DView cdf
 // ---------------------------------------------------------------------------------------------
 __global__ void remap_density_kernel(int ncells, double adt, const double* __restrict__ Q, const double* __restrict__ ss,
                                      const double* __restrict__ pre, const double* __restrict__ post,
-                                     const double* __restrict__ phi, double* f, double* q, DevState* st) {
+                                     const double* __restrict__ phi, double* f, float* f32, int* fpos, double* q,
+                                     DevState* st) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double r = 0;
     if (k < ncells) {
@@ -197,13 +198,14 @@ __global__ void remap_density_kernel(int ncells, double adt, const double* __res
         const double f0 = Q[k] + s * (pre[k] + post[k]) + s * phi[4 * k];
         const double f1 = s * phi[4 * k + 1], f2 = s * phi[4 * k + 2], f3 = s * phi[4 * k + 3];
         f[4 * k] = f0; f[4 * k + 1] = f1; f[4 * k + 2] = f2; f[4 * k + 3] = f3;
+        reinterpret_cast<float4*>(f32)[k] = make_float4((float)f0, (float)f1, (float)f2, (float)f3);
         const double qc = f0 * adt;
         q[k] = qc;
-        if (qc != 0.0) {
-            const bool pos = f0 - f1 - f2 + f3 >= 0 && f0 + f1 - f2 - f3 >= 0 && f0 - f1 + f2 - f3 >= 0 &&
-                             f0 + f1 + f2 + f3 >= 0;
-            r = pos ? 1.0 : (fabs(f0) + fabs(f1) + fabs(f2) + fabs(f3)) / fabs(f0);
-        }
+        // all four nodal values >= 0: births sampled from the bilinear density itself
+        const bool pos = f0 - f1 - f2 + f3 >= 0 && f0 + f1 - f2 - f3 >= 0 && f0 - f1 + f2 - f3 >= 0 &&
+                         f0 + f1 + f2 + f3 >= 0;
+        fpos[k] = pos ? 1 : 0;
+        if (qc != 0.0) r = pos ? 1.0 : (fabs(f0) + fabs(f1) + fabs(f2) + fabs(f3)) / fabs(f0);
     }
     for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
     if ((threadIdx.x & 31) == 0 && r > 0)
@@ -234,7 +236,9 @@ struct RemapArgs {
     const T* sig;
     BankView<T> in, out, stg;   // stg: staged end states, one per slot (cell -1 = not alive)
     Cdf2DView cdf;
-    const double* f;
+    const double* f;           // remap density, 4 Legendre coefficients per cell (FP64)
+    const float* f32;          // the same in FP32 (FP32 path)
+    const int* fpos;           // per cell: 1 if all four nodal values of f are >= 0
     long long n_hist, cap;
     const uint32_t* V;
     int ntab, sampler;
@@ -256,11 +260,34 @@ __device__ __forceinline__ T inv_linear(T a, T b, T u) {
     return clamp_(t - T(1), T(-1), T(1));
 }
 
+// 2^k as a float for k in [-126, 126] (exact: the exponent field only)
+__device__ __forceinline__ float pow2f(int k) {
+    k = k < -126 ? -126 : (k > 126 ? 126 : k);
+    return __int_as_float((k + 127) << 23);
+}
+
+// Per-thread weight sums of the remap statistics (start, absorbed, leaked, killed). FP64 path:
+// doubles, scaled to 128-bit fixed point per block. FP32 path: int64 fixed point of scale 2^kf
+// built from exact float products (kf = the block scale - 64, capped at 126), so the per-slot
+// bookkeeping needs no FP64 arithmetic; a block sum v stands for v 2^(k - kf) at the block scale.
+template <typename T> struct RemapSums;
+template <> struct RemapSums<double> {
+    double v[4] = {0, 0, 0, 0};
+    __device__ void init(int) {}
+    __device__ void add(int i, double x) { v[i] += x; }
+};
+template <> struct RemapSums<float> {
+    long long v[4] = {0, 0, 0, 0};
+    float sc = 1.f;
+    __device__ void init(int kf) { sc = pow2f(kf); }
+    __device__ void add(int i, float x) { v[i] += __float2ll_rn(x * sc); }
+};
+enum { kRsSrc = 0, kRsAbs = 1, kRsLeak = 2, kRsKill = 3 };
+
 // start state of slot j and its straight-line stream to t_{n+1} with sigma_t attenuation
 template <typename T>
-__device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long long j, long long nb, double wbar,
-                                  double* w_start, double* w_abs, double* w_leak, double* w_kill, int* leaked,
-                                  int* killed, int* segs, int* err) {
+__device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long long j, long long nb, T wbar,
+                                  RemapSums<T>& sums, int* leaked, int* killed, int* segs, int* err) {
     using P = Prec<T>;
     int ix, iy;
     T fx, fy, ox, oy, w, srem;
@@ -274,26 +301,30 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
         T frx, fry;
         const int k = sample_cell<T>(a.cdf, a.nx, a.ny, pts(i, 0), pts(i, 1), &frx, &fry);
         ix = k % a.nx; iy = k / a.nx;
-        const double* fk = a.f + 4 * (size_t)k;
-        const T f0 = (T)fk[0], f1 = (T)fk[1], f2 = (T)fk[2], f3 = (T)fk[3];
-        const bool pos = fk[0] - fk[1] - fk[2] + fk[3] >= 0 && fk[0] + fk[1] - fk[2] - fk[3] >= 0 &&
-                         fk[0] - fk[1] + fk[2] - fk[3] >= 0 && fk[0] + fk[1] + fk[2] + fk[3] >= 0;
+        T f0, f1, f2, f3;
+        if constexpr (sizeof(T) == 4) {
+            const float4 fk = __ldg(reinterpret_cast<const float4*>(a.f32) + k);
+            f0 = fk.x; f1 = fk.y; f2 = fk.z; f3 = fk.w;
+        } else {
+            const double* fk = a.f + 4 * (size_t)k;
+            f0 = fk[0]; f1 = fk[1]; f2 = fk[2]; f3 = fk[3];
+        }
         T xi, eta;
-        if (pos) {
+        if (a.fpos[k]) {
             xi = inv_linear<T>(f0, f1, frx);
             eta = inv_linear<T>(f0 + f1 * xi, f2 + f3 * xi, fry);
-            w = (T)wbar;
+            w = wbar;
         } else {
             xi = T(2) * frx - T(1);
             eta = T(2) * fry - T(1);
-            w = (T)wbar * (f0 + f1 * xi + f2 * eta + f3 * xi * eta) / (f0 < T(0) ? -f0 : f0);
+            w = wbar * (f0 + f1 * xi + f2 * eta + f3 * xi * eta) / (f0 < T(0) ? -f0 : f0);
         }
         fx = T(0.5) * (xi + T(1)) * a.dx;
         fy = T(0.5) * (eta + T(1)) * a.dy;
         iso_dir<T>(pts(i, 3), pts(i, 4), &ox, &oy);
         srem = a.cdt * P::unit_c(pts(i, 2));
     }
-    *w_start = (double)w;
+    sums.add(kRsSrc, w);
     const T w0 = w;
     const T INF = (T)INFINITY;
     Particle<T> r;
@@ -310,7 +341,7 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
         bool face = false, xc = false, yc = false;
         if (dxf <= srem || dyf <= srem) { l = dxf < dyf ? dxf : dyf; face = true; xc = dxf == l; yc = dyf == l; }
         else l = srem;
-        *w_abs += (double)(w * (-P::exm1(-st * l)));
+        sums.add(kRsAbs, w * (-P::exm1(-st * l)));
         w = w * P::ex(-st * l);
         fx = P::madd(ox, l, fx);
         fy = P::madd(oy, l, fy);
@@ -324,18 +355,32 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
         }
         if (xc) { ix += ox > T(0) ? 1 : -1; fx = ox > T(0) ? T(0) : a.dx; } else fx = clamp_(fx, T(0), a.dx);
         if (yc) { iy += oy > T(0) ? 1 : -1; fy = oy > T(0) ? T(0) : a.dy; } else fy = clamp_(fy, T(0), a.dy);
-        if (ix < 0 || ix >= a.nx || iy < 0 || iy >= a.ny) { *w_leak += (double)w; ++*leaked; *segs += s; return r; }
+        if (ix < 0 || ix >= a.nx || iy < 0 || iy >= a.ny) { sums.add(kRsLeak, w); ++*leaked; *segs += s; return r; }
         const T aw = w < T(0) ? -w : w, aw0 = w0 < T(0) ? -w0 : w0;
-        if (a.w_min > T(0) && aw < a.w_min * aw0) { *w_kill += (double)w; ++*killed; *segs += s; return r; }
+        if (a.w_min > T(0) && aw < a.w_min * aw0) { sums.add(kRsKill, w); ++*killed; *segs += s; return r; }
     }
     ++*err;
     *segs += s;
     return r;
 }
 
+// comb quantisation rint(|w| / w_ref 2^32) with w_ref a power of two: the FP32 path multiplies by
+// the exact float 2^(32 - log2 w_ref) (same integer as the FP64 quotient), the FP64 path divides
+__device__ __forceinline__ long long quant_w(float w, double, float qsc) { return __float2ll_rn(fabsf(w) * qsc); }
+__device__ __forceinline__ long long quant_w(double w, double w_ref, float) {
+    return __double2ll_rn((fabs(w) / w_ref) * 0x1p32);
+}
+
+// float 2^(32 - log2 w_ref), or 0 when it is not a normal float (the FP32 path then divides)
+__device__ __forceinline__ float quant_scale(double w_ref) {
+    const int e = ilogb(w_ref);
+    return (32 - e) <= 126 && (32 - e) >= -126 ? pow2f(32 - e) : 0.f;
+}
+
 template <typename T>
-__device__ __forceinline__ long long quant_w(T w, double w_ref) {
-    return __double2ll_rn((fabs((double)w) / w_ref) * 0x1p32);
+__device__ __forceinline__ long long quant(T w, double w_ref, float qsc) {
+    if (sizeof(T) == 4 && qsc == 0.f) return quant_w((double)w, w_ref, 0.f);
+    return quant_w(w, w_ref, qsc);
 }
 
 template <typename T>
@@ -353,66 +398,94 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     const long long N = nb + nbirth;
     const double wbar = nbirth ? a.st->remap_W / (double)a.n_hist : 0.0;
     const double w_ref = a.st->w_ref;
+    const float qsc = quant_scale(w_ref);
+    // block scales (128-bit): krw for the survivors' sum |w|, kw for the statistics
     const int krw = scale_exponent((double)(N > 0 ? N : 1) * w_ref, 125);
-    const double scw = ldexp(1.0, krw);
-    long long cnt = 0, qs = 0;
-    double ws = 0, w_src = 0, w_abs = 0, w_leak = 0, w_kill = 0;
+    const int kw = scale_exponent((double)(N > 0 ? N : 1) * fmax(w_ref, 1e-300) * 4.0, 125);
+    constexpr bool kF32 = sizeof(T) == 4;
+    const int kfa = min(krw - 64, 126), kf = min(kw - 64, 126);   // FP32 per-thread scales
+    const float sca = pow2f(kfa);
+    RemapSums<T> sums;
+    sums.init(kf);
+    long long cnt = 0, qs = 0, wsf = 0;
+    double ws = 0;
     int leaked = 0, killed = 0, segs = 0, err = 0;
     const long long base = (long long)blockIdx.x * kSlotsPerBlock;
     for (int r = 0; r < kRounds; ++r) {
         const long long j = base + r * kTile + threadIdx.x;
         if (j >= N) break;
-        double wst;
-        const Particle<T> pr = remap_slot<T>(a, pts, j, nb, wbar, &wst, &w_abs, &w_leak, &w_kill, &leaked, &killed,
-                                             &segs, &err);
-        w_src += wst;
+        const Particle<T> pr = remap_slot<T>(a, pts, j, nb, (T)wbar, sums, &leaked, &killed, &segs, &err);
         a.stg.cell[j] = pr.alive ? pr.cell : -1;
         a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
         if (pr.alive) {
             ++cnt;
-            qs += quant_w<T>(pr.w, w_ref);
-            ws += fabs((double)pr.w);
+            qs += quant<T>(pr.w, w_ref, qsc);
+            if constexpr (kF32) wsf += __float2ll_rn(fabsf(pr.w) * sca);
+            else ws += fabs((double)pr.w);
         }
     }
     // block sums in fixed order
-    __shared__ long long s_l[kTile / 32][2];
+    __shared__ long long s_l[kTile / 32][3];
     __shared__ double s_d[kTile / 32][5];
+    __shared__ long long s_f[kTile / 32][4];
     __shared__ int s_i[kTile / 32][4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) {
         cnt += __shfl_down_sync(0xffffffffu, cnt, o);
         qs += __shfl_down_sync(0xffffffffu, qs, o);
+        wsf += __shfl_down_sync(0xffffffffu, wsf, o);
         leaked += __shfl_down_sync(0xffffffffu, leaked, o);
         killed += __shfl_down_sync(0xffffffffu, killed, o);
         segs += __shfl_down_sync(0xffffffffu, segs, o);
         err += __shfl_down_sync(0xffffffffu, err, o);
     }
-    ws = warp_sum(ws); w_src = warp_sum(w_src); w_abs = warp_sum(w_abs); w_leak = warp_sum(w_leak);
-    w_kill = warp_sum(w_kill);
+    if constexpr (kF32) {
+        for (int t = 0; t < 4; ++t) sums.v[t] = (long long)warp_sum_u64((unsigned long long)sums.v[t]);
+    } else {
+        ws = warp_sum(ws);
+        for (int t = 0; t < 4; ++t) sums.v[t] = warp_sum(sums.v[t]);
+    }
     if (lane == 0) {
-        s_l[wid][0] = cnt; s_l[wid][1] = qs;
-        s_d[wid][0] = ws; s_d[wid][1] = w_src; s_d[wid][2] = w_abs; s_d[wid][3] = w_leak; s_d[wid][4] = w_kill;
+        s_l[wid][0] = cnt; s_l[wid][1] = qs; s_l[wid][2] = wsf;
+        s_d[wid][0] = ws;
+        for (int t = 0; t < 4; ++t) {
+            if constexpr (kF32) s_f[wid][t] = sums.v[t];
+            else s_d[wid][t + 1] = sums.v[t];
+        }
         s_i[wid][0] = leaked; s_i[wid][1] = killed; s_i[wid][2] = segs; s_i[wid][3] = err;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        long long c = 0, q = 0;
+        long long c = 0, q = 0, af = 0;
         double d[5] = {0, 0, 0, 0, 0};
+        long long fv[4] = {0, 0, 0, 0};
         long long iv[4] = {0, 0, 0, 0};
         for (int ww = 0; ww < kTile / 32; ++ww) {
-            c += s_l[ww][0]; q += s_l[ww][1];
+            c += s_l[ww][0]; q += s_l[ww][1]; af += s_l[ww][2];
             for (int t = 0; t < 5; ++t) d[t] += s_d[ww][t];
+            for (int t = 0; t < 4; ++t) fv[t] += s_f[ww][t];
             for (int t = 0; t < 4; ++t) iv[t] += s_i[ww][t];
         }
         unsigned long long lo, hi;
-        to_i128(d[0] * scw, &lo, &hi);
         long long* b = a.blk + 4 * (size_t)blockIdx.x;
+        if constexpr (kF32) {
+            // af 2^-kfa = af 2^(krw - kfa) 2^-krw: the 128-bit value is af shifted left by krw - kfa >= 64
+            const int sh = krw - kfa - 64;
+            lo = 0ull;
+            hi = sh < 63 ? (unsigned long long)af << sh : 0ull;
+        } else {
+            to_i128(d[0] * ldexp(1.0, krw), &lo, &hi);
+        }
         b[0] = c; b[1] = q; b[2] = (long long)lo; b[3] = (long long)hi;
-        const int kw = scale_exponent((double)(N > 0 ? N : 1) * fmax(w_ref, 1e-300) * 4.0, 125);
-        const double sc = ldexp(1.0, kw);
         Acc128* wd[4] = {&a.st->r_w_source, &a.st->r_w_absorbed, &a.st->r_w_leaked, &a.st->r_w_killed};
         for (int t = 0; t < 4; ++t) {
-            to_i128(d[t + 1] * sc, &lo, &hi);
+            if constexpr (kF32) {
+                const int sh = kw - kf - 64;
+                lo = 0ull;
+                hi = sh < 63 ? (unsigned long long)fv[t] << sh : 0ull;   // two's complement: signed sums too
+            } else {
+                to_i128(d[t + 1] * ldexp(1.0, kw), &lo, &hi);
+            }
             atomic_add128(wd[t], lo, hi);
         }
         if (iv[0]) atomicAdd(&a.st->r_leaked, (unsigned long long)iv[0]);
@@ -482,11 +555,28 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
     }
 }
 
-// ceil(num / T) for num = hi 2^64 + lo >= 0 with quotient < 2^40, T > 0 (T < 2^63)
+// ceil(num / T) for num = hi 2^64 + lo >= 0 with quotient < 2^40, 0 < T < 2^63, without FP64: a
+// float estimate (relative error below 2^-21) is refined once from the exact 128-bit remainder
+// (leaving an error of at most one) and finished by exact integer steps.
 __device__ __forceinline__ long long ceil_div(unsigned long long hi, unsigned long long lo, unsigned long long T) {
-    const double est = ((double)hi * 0x1p64 + (double)lo) / (double)T;
-    long long q = (long long)est;
+    const float fT = __ull2float_rn(T);
+    const float fN = fmaf(__ull2float_rn(hi), 0x1p64f, __ull2float_rn(lo));
+    long long q = (long long)(fN / fT);
     if (q < 0) q = 0;
+    {
+        const unsigned long long plo = (unsigned long long)q * T, phi = __umul64hi((unsigned long long)q, T);
+        unsigned long long rlo = lo - plo;
+        unsigned long long rhi = hi - phi - (lo < plo ? 1ull : 0ull);
+        const bool neg = (long long)rhi < 0;
+        if (neg) {                       // |r| of the two's-complement remainder
+            rlo = ~rlo + 1ull;
+            rhi = ~rhi + (rlo == 0ull ? 1ull : 0ull);
+        }
+        const float fr = fmaf(__ull2float_rn(rhi), 0x1p64f, __ull2float_rn(rlo));
+        const long long dq = (long long)rintf(fr / fT);
+        q = neg ? q - dq : q + dq;
+        if (q < 0) q = 0;
+    }
     for (int it = 0; it < 16; ++it) {
         // prod = q T
         const unsigned long long plo = (unsigned long long)q * T, phi = __umul64hi((unsigned long long)q, T);
@@ -519,12 +609,13 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
     const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
     const long long N = nb + nbirth;
     const double w_ref = a.st->w_ref;
+    const float qsc = quant_scale(w_ref);
     const int comb = a.st->comb_on;
     const long long M = a.cap, o = a.st->comb_o, Ttot = a.st->comb_T;
     const T wcopy = (T)a.st->wcopy;
     long long run_c = a.blk[4 * (size_t)blockIdx.x], run_q = a.blk[4 * (size_t)blockIdx.x + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double wmax = 0;
+    T wmax = 0;
     const long long base = (long long)blockIdx.x * kSlotsPerBlock;
     for (int r = 0; r < kRounds; ++r) {
         const long long j = base + r * kTile + threadIdx.x;
@@ -536,7 +627,7 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
             pr.fx = a.stg.fx[j]; pr.fy = a.stg.fy[j]; pr.ox = a.stg.ox[j]; pr.oy = a.stg.oy[j]; pr.w = a.stg.w[j];
         }
         long long c = pr.alive ? 1 : 0;
-        long long q = pr.alive ? quant_w<T>(pr.w, w_ref) : 0;
+        long long q = pr.alive ? quant<T>(pr.w, w_ref, qsc) : 0;
         // block exclusive scan of (c, q) in slot order
         long long ic = c, iq = q;
         for (int off = 1; off < 32; off <<= 1) {
@@ -563,7 +654,7 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
             } else if (pos_c < M) {
                 a.out.cell[pos_c] = pr.cell; a.out.fx[pos_c] = pr.fx; a.out.fy[pos_c] = pr.fy;
                 a.out.ox[pos_c] = pr.ox; a.out.oy[pos_c] = pr.oy; a.out.w[pos_c] = pr.w;
-                wmax = fmax(wmax, fabs((double)pr.w));
+                wmax = fmax(wmax, fabs(pr.w));
             }
         }
         run_c += tc;
@@ -571,8 +662,8 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
         __syncthreads();
     }
     for (int off = 16; off > 0; off >>= 1) wmax = fmax(wmax, __shfl_down_sync(0xffffffffu, wmax, off));
-    if (lane == 0 && wmax > 0)
-        atomicMax((unsigned long long*)&a.st->bank_wmax, (unsigned long long)__double_as_longlong(wmax));
+    if (lane == 0 && wmax > T(0))
+        atomicMax((unsigned long long*)&a.st->bank_wmax, (unsigned long long)__double_as_longlong((double)wmax));
 }
 
 __global__ void remap_finish_kernel(DevState* st) {
@@ -588,7 +679,7 @@ static cudaError_t remap_t(hyb_problem* p) {
     cudaError_t e = cudaMemsetAsync(&p->st->remap_rmax, 0, sizeof(double), s);
     if (e != cudaSuccess) return e;
     remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_d, p->post_d,
-                                           p->sn_phi_d, p->rem_f, p->rem_q, p->st);
+                                           p->sn_phi_d, p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st);
     e = launch_cdf_build(p, p->rem_q, p->rem_cdf, &p->st->remap_W, &p->st->remap_qmax);
     if (e != cudaSuccess) return e;
     remap_prep_kernel<<<1, 1, 0, s>>>(p->st, p->d.n_hist);
@@ -603,6 +694,8 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.out = bank_view<T>(p, 1 - p->cur);
     a.cdf = p->rem_cdf;
     a.f = p->rem_f;
+    a.f32 = p->rem_f32;
+    a.fpos = p->rem_pos;
     a.n_hist = p->d.n_hist;
     a.cap = p->d.census_cap > 0 ? p->d.census_cap : p->d.n_hist;
     if (a.cap > p->bank_cap) a.cap = p->bank_cap;

@@ -285,59 +285,112 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
     if (timed_out && lane == 0) atomicOr(a.status, kStSegments);
 }
 
-// phi_new = sum over ordinates of w_m psi_m (fixed order); norm partials of the change; the next
-// iteration's source integrals from phi_new
+// One source iteration's reduction. A block covers 32 cells: thread (g, c) sums the weighted
+// ordinate solutions of cell c over ordinates g, g+8, ... (vector loads, coalesced across c); the
+// 8 partials of a cell are added in g order in shared memory, then thread (c, i) forms coefficient
+// i of phi_new, its contribution to the change norm and the next iteration's source integral i.
+// The block's norm partials go to part[]; the last block to finish (counter in the device state)
+// adds all partials in block order and applies the stop test
+//   ||phi_new - phi_old|| <= tol ||phi_new||   (or no source at all),
+// so the reduction and the test are one launch and the result does not depend on block order.
+constexpr int kRedCells = 32, kRedGroups = 8;
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float* p, float* v) {
+        const float4 x = *reinterpret_cast<const float4*>(p);
+        v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+    }
+};
+template <> struct Vec4<double> {
+    static __device__ __forceinline__ void load(const double* p, double* v) {
+        const double2 x = reinterpret_cast<const double2*>(p)[0], y = reinterpret_cast<const double2*>(p)[1];
+        v[0] = x.x; v[1] = x.y; v[2] = y.x; v[3] = y.y;
+    }
+};
+
 template <typename T>
-__global__ void sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, double* part,
-                                 const T* sig, const double* mom, T area, T inv_4pi_dt, T* src, const int* conv) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (*(volatile const int*)conv) {
+__global__ void __launch_bounds__(kRedCells * kRedGroups)
+sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, double* part, const T* sig,
+                 const double* mom, T area, T inv_4pi_dt, T* src, DevState* st, double tol) {
+    __shared__ T sp[kRedGroups][kRedCells][4];
+    __shared__ double sred[2][kRedCells * 4 / 32];
+    __shared__ bool s_last;
+    const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
+    const int k0 = blockIdx.x * kRedCells;
+    if (*(volatile const int*)&st->sn_conv) {
         // converged earlier: carry the solution forward so the buffer alternation stays aligned
-        if (k < ncells)
-            for (int i = 0; i < 4; ++i) phi_new[4 * (size_t)k + i] = phi_old[4 * (size_t)k + i];
+        if (threadIdx.x < kRedCells * 4) {
+            const size_t e = (size_t)k0 * 4 + threadIdx.x;
+            if (e < (size_t)ncells * 4) phi_new[e] = phi_old[e];
+        }
         return;
     }
-    double num = 0, den = 0;
-    if (k < ncells) {
-        const double nrm[4] = {1.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 9.0};
-        T s[4] = {0, 0, 0, 0};
-        for (int m = 0; m < nord; ++m) {
-            const T* v = psi + ((size_t)m * ncells + k) * 4;
-            s[0] += v[0]; s[1] += v[1]; s[2] += v[2]; s[3] += v[3];
-        }
-        for (int i = 0; i < 4; ++i) {
-            phi_new[4 * (size_t)k + i] = s[i];
-            const double d = (double)s[i] - (double)phi_old[4 * (size_t)k + i];
-            num += nrm[i] * d * d;
-            den += nrm[i] * (double)s[i] * (double)s[i];
-        }
-        source4<T>(sig[2 * k + 1], area, s, mom + 4 * (size_t)k, inv_4pi_dt, src + 4 * (size_t)k);
+    {
+        const int k = k0 + c;
+        T acc[4] = {0, 0, 0, 0};
+        if (k < ncells)
+            for (int m = g; m < nord; m += kRedGroups) {
+                T v[4];
+                Vec4<T>::load(psi + ((size_t)m * ncells + k) * 4, v);
+                acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2]; acc[3] += v[3];
+            }
+        sp[g][c][0] = acc[0]; sp[g][c][1] = acc[1]; sp[g][c][2] = acc[2]; sp[g][c][3] = acc[3];
     }
-    num = warp_sum(num);
-    den = warp_sum(den);
-    __shared__ double sn[32], sd[32];
-    if ((threadIdx.x & 31) == 0) { sn[threadIdx.x >> 5] = num; sd[threadIdx.x >> 5] = den; }
+    __syncthreads();
+    if (threadIdx.x < kRedCells * 4) {
+        const int cc = threadIdx.x >> 2, i = threadIdx.x & 3;
+        const int k = k0 + cc;
+        T num = 0, den = 0;
+        if (k < ncells) {
+            T v = 0;
+#pragma unroll
+            for (int q = 0; q < kRedGroups; ++q) v += sp[q][cc][i];
+            const size_t e = (size_t)k * 4 + i;
+            phi_new[e] = v;
+            const T nrm = i == 0 ? T(1) : (i == 3 ? T(1.0 / 9.0) : T(1.0 / 3.0));
+            const T n_i = nrm;   // the Legendre norm of coefficient i is the same factor
+            const T d = v - phi_old[e];
+            num = nrm * d * d;
+            den = nrm * v * v;
+            // source integral i: sigma_s A n_i phi_i / (4 pi) + m_i / (4 pi dt)
+            const T cs = sig[2 * (size_t)k + 1] * area * T(0.07957747154594767);
+            src[e] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
+        }
+        // warp sums (fixed tree), then block sum in warp order
+        for (int o = 16; o > 0; o >>= 1) {
+            num += __shfl_down_sync(0xffffffffu, num, o);
+            den += __shfl_down_sync(0xffffffffu, den, o);
+        }
+        if ((threadIdx.x & 31) == 0) { sred[0][threadIdx.x >> 5] = (double)num; sred[1][threadIdx.x >> 5] = (double)den; }
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0, b = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += sn[q]; b += sd[q]; }
+        for (int q = 0; q < kRedCells * 4 / 32; ++q) { a += sred[0][q]; b += sred[1][q]; }
         part[2 * blockIdx.x] = a;
         part[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        const unsigned done = atomicAdd(&st->sn_blocks_done, 1u);
+        s_last = done == gridDim.x - 1;
     }
-}
-
-// SI stop test on the device: ||phi_new - phi_old|| <= tol ||phi_new|| (or no source at all)
-__global__ void sn_norm_final_kernel(const double* part, int nparts, DevState* st, double tol) {
-    if (*(volatile int*)&st->sn_conv) return;
-    double a = 0, b = 0;
-    for (int i = threadIdx.x; i < nparts; i += 32) { a += part[2 * i]; b += part[2 * i + 1]; }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    if (threadIdx.x == 0) {
-        st->sn_norm_num = a;
-        st->sn_norm_den = b;
-        st->sn_iters += 1;
-        if (b == 0.0 || sqrt(a) <= tol * sqrt(b)) st->sn_conv = 1;
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        __threadfence();
+        double a = 0, b = 0;
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) {
+            a += ((volatile double*)part)[2 * q];
+            b += ((volatile double*)part)[2 * q + 1];
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        if (threadIdx.x == 0) {
+            st->sn_norm_num = a;
+            st->sn_norm_den = b;
+            st->sn_iters += 1;
+            if (b == 0.0 || sqrt(a) <= tol * sqrt(b)) st->sn_conv = 1;
+            st->sn_blocks_done = 0u;
+        }
     }
 }
 
@@ -396,10 +449,11 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
         if (e != cudaSuccess) return e;
     }
     sweep_pipe_kernel<T><<<p->n_ord, 32 * a.W, smem, s>>>(a);
-    sn_reduce_kernel<T><<<g, 256, 0, s>>>((const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old, (T*)p->sn_phi,
-                                          p->ncells, p->sn_norm, (const T*)p->sig, p->mom_d, (T)p->area, inv4pidt,
-                                          src, &p->st->sn_conv);
-    sn_norm_final_kernel<<<1, 32, 0, s>>>(p->sn_norm, g, p->st, sn_tol_eff(p));
+    const int gr = (p->ncells + kRedCells - 1) / kRedCells;
+    sn_reduce_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old,
+                                                              (T*)p->sn_phi, p->ncells, p->sn_norm, (const T*)p->sig,
+                                                              p->mom_d, (T)p->area, inv4pidt, src, p->st,
+                                                              sn_tol_eff(p));
     return cudaGetLastError();
 }
 
