@@ -100,10 +100,14 @@ class Clocks:
                 "samples": len(sm)}
 
 
+CENSUS_ORDER = 0
+
+
 def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0, warm: int = 1) -> W.ProblemSpec:
     """The benchmark workload; source iteration starts from the previous step's collided flux
     (the same fixed point, fewer sweeps)."""
-    return W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision).with_(sn_warm_start=warm)
+    return W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision).with_(sn_warm_start=warm,
+                                                                                       census_order=CENSUS_ORDER)
 
 
 def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
@@ -269,6 +273,37 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0) -> dic
             "single_problem_path": {"histories_per_s": h2 / dt, "ms_per_step_all": 1e3 * dt / steps}}
 
 
+def large_measure(steps: int = 2, n_hist: int = 100_000_000) -> dict:
+    """The large diffusive workload: 1024^2 cells over 10 x 10 cm, random 8 x 8-cell blocks with
+    sigma_t in {1, 10, 1000} (scattering ratio 0.999 in the thickest, 0.5 elsewhere), N_s = 8,
+    10^8 births per step, dt = 0.01, S8, FP32 tracking. One untimed step fills the census; the
+    timed steps carry 10^8 census particles plus 10^8 births each."""
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    spec = W.large(n=1024, n_hist=n_hist, precision=W.FP32).with_(sn_warm_start=1)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        P = hyb.Problem(spec, stream=stream)
+        P.step(1)
+        ms, hist, segs, it, phase = 0.0, 0, 0, [], {"mc_leg": 0.0, "collided_sn": 0.0, "remap": 0.0}
+        for _ in range(steps):
+            flush.zero_()
+            st = P.step(1)[0]
+            ms += st["ms"]
+            hist += st["histories"]
+            segs += st["segments"]
+            it.append(st["sn_iterations"])
+            phase["mc_leg"] += st["ms_leg"] / steps
+            phase["collided_sn"] += st["ms_sn"] / steps
+            phase["remap"] += st["ms_remap"] / steps
+        P.close()
+    torch.cuda.synchronize()
+    return {"workload": "large diffusive 1024x1024, N_s=8, 1e8 births/step + census, dt=0.01, S8, FP32",
+            "histories_per_s": hist / (ms / 1e3), "segments_per_s": segs / (ms / 1e3), "ms_per_step": ms / steps,
+            "phase_ms": phase, "sn_iterations": it}
+
+
 def serving_measure(lam: float, duration: float, seed: int = 0, hist_cap: int | None = None) -> dict:
     from paper_2511_16821_gb300.serve import Server
     srv = Server(budget_bytes=120e9)
@@ -321,12 +356,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched and serving measurements")
+    ap.add_argument("--no-large", action="store_true", help="skip the large-mesh measurement")
     ap.add_argument("--serve-sweep", default="", help="comma-separated arrival rates: run only the serving sweep")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (FP32, no profile/e2e/CPU legs): the case used for ncu captures")
+    ap.add_argument("--census-order", type=int, default=0, choices=[0, 1],
+                    help="census in slot order (0) or sorted by cell before the comb (1)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global CENSUS_ORDER
+    CENSUS_ORDER = args.census_order
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -344,7 +384,7 @@ def main():
                 print(json.dumps({"serving": serving_measure(lam, args.serve_seconds)}), flush=True)
         return
     if args.lean:
-        args.fp32_only = args.no_cpu = args.no_e2e = args.no_batch = True
+        args.fp32_only = args.no_cpu = args.no_e2e = args.no_batch = args.no_large = True
     res = run_gpu(args, rank, world)
     if args.lean:
         if rank == 0:
@@ -407,6 +447,8 @@ def main():
                         "phase_ms": r64["phase_ms"]}
     if not args.no_e2e:
         line["e2e"] = e2e_measure(spec_for(W.FP32), max(2, min(args.steps, 5)))
+    if not args.no_large:
+        line["large"] = large_measure()
     if not args.no_batch:
         line["batched"] = batched_measure()
         line["serving"] = serving_measure(100.0, 3.0)

@@ -94,7 +94,11 @@ typedef struct {
     int64_t census_cap;       /* census capacity after the comb; 0 = n_hist */
     int32_t sn_warm_start;    /* 1: source iteration starts from the previous step's collided
                                  flux (same fixed point, fewer iterations); 0: from zero */
-    int32_t pad0;
+    int32_t census_order;     /* 0: the census keeps slot order (re-streamed bank slots, then
+                                 births); 1: survivors in cell order (stable within a cell)
+                                 before the comb, so the systematic comb samples each cell's
+                                 weight to within one copy and the next leg's bank is
+                                 cell-coherent */
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */
@@ -216,6 +220,11 @@ typedef struct {
 HYB_API hyb_status hyb_batch_create(hyb_problem* const* problems, int32_t n, void* cuda_stream, hyb_batch** out);
 /* Replace the tuning (rebuilds the work queue; graphs are re-recorded at the next step). */
 HYB_API hyb_status hyb_batch_set_tuning(hyb_batch* b, const hyb_batch_tuning* tuning);
+/* Replace the batch's problems (same rules as hyb_batch_create; the problems must share the
+ * batch's precision). Streams, events and device buffers are kept (per-problem buffers grow
+ * only), so a serving loop can change the resident set every step without re-creating them.
+ * Synchronises the batch stream. */
+HYB_API hyb_status hyb_batch_set_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n);
 /* nsteps steps of every problem; per_problem (host, n entries, may be NULL): the last step's leg
  * statistics with sn_iterations / combed / bank_size, ms = device time of the last graph. */
 HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* per_problem);

@@ -43,7 +43,7 @@ class _Problem(C.Structure):
                 ("n_s", C.c_int32), ("sampler", C.c_int32), ("n_hist", C.c_int64),
                 ("seed", C.c_uint64), ("sn_order", C.c_int32), ("handoff_full", C.c_int32),
                 ("w_min", C.c_double), ("census_cap", C.c_int64), ("sn_tol", C.c_double),
-                ("sn_max_iter", C.c_int32), ("pad", C.c_int32)]
+                ("sn_max_iter", C.c_int32), ("census_order", C.c_int32)]
 
 
 class _Bank(C.Structure):
@@ -101,7 +101,8 @@ def _problem(spec) -> tuple[_Problem, _Keep]:
                  Q=_dp(q), c=spec.c, dt=spec.dt, n_s=spec.n_s, sampler=spec.sampler,
                  n_hist=spec.n_hist, seed=spec.seed, sn_order=spec.sn_order,
                  handoff_full=spec.handoff_full, w_min=spec.w_min, census_cap=spec.census_cap,
-                 sn_tol=spec.sn_tol, sn_max_iter=spec.sn_max_iter, pad=0)
+                 sn_tol=spec.sn_tol, sn_max_iter=spec.sn_max_iter,
+                 census_order=getattr(spec, "census_order", 0))
     return p, _Keep(sa, ss, q)
 
 

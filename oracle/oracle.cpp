@@ -223,7 +223,7 @@ typedef struct {
     int64_t census_cap;     // 0 = n_hist
     double sn_tol;          // source-iteration relative-change tolerance
     int32_t sn_max_iter;
-    int32_t pad;
+    int32_t census_order;   // 0: census in slot order (bank slots, then births); 1: stable by cell
 } or_problem;
 
 typedef struct {
@@ -1119,8 +1119,11 @@ int or_remap(const or_problem* P, int64_t step, const or_bank* census, const dou
             if (r.alive) surv.push_back(r);
         }
     }
-    // (iii) census of step 4, combed to census_cap when above it
+    // (iii) census of step 4, combed to census_cap when above it; in cell order (stable within a
+    // cell) when asked, so that the systematic comb samples each cell's weight to within one copy
     const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
+    if (P->census_order == 1)
+        std::stable_sort(surv.begin(), surv.end(), [](const Streamed& a, const Streamed& b) { return a.cell < b.cell; });
     std::vector<Streamed> fin;
     int did_comb = 0;
     if ((int64_t)surv.size() > cap) {
@@ -1163,6 +1166,8 @@ int or_step(const or_problem* P, int64_t step, const or_bank* bank, or_bank* out
         std::fill(phi, phi + 4 * nc, 0.0);
         std::vector<Streamed> s, fin;
         for (int64_t j = 0; j < tmp.n; ++j) s.push_back(Streamed{true, c[j], a[j], b[j], d[j], e[j], g[j]});
+        if (P->census_order == 1)
+            std::stable_sort(s.begin(), s.end(), [](const Streamed& x, const Streamed& y) { return x.cell < y.cell; });
         const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
         if ((int64_t)s.size() > cap) {
             double wmax = 0.0;

@@ -22,11 +22,14 @@ from . import hyb
 from . import workloads as W
 
 
-def problem(n_hist: int, seed: int, sampler: int, n_s: int = 2, precision: int = W.FP32) -> W.ProblemSpec:
+def problem(n_hist: int, seed: int, sampler: int, n_s: int = 2, precision: int = W.FP32,
+            census_order: int = 0) -> W.ProblemSpec:
     """Checkerboard of 7x7 one-centimetre blocks at 4 cells per block (28x28), S4, absorber /
     scatterer blocks, Q = 1 in the centre block, dt = 0.1."""
+    order = "cell" if census_order else "slot"
     return W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision, sampler=sampler,
-                          cells_per_block=4).with_(sn_order=4, sn_tol=1e-6, name=f"checkerboard28 N_s={n_s}")
+                          cells_per_block=4).with_(sn_order=4, sn_tol=1e-6, census_order=census_order,
+                                                   name=f"checkerboard28 N_s={n_s}, census in {order} order")
 
 
 def end_flux(spec: W.ProblemSpec, steps: int) -> np.ndarray:
@@ -42,18 +45,19 @@ def fit_alpha(ns, errs) -> float:
 
 
 def study(log2_n=range(10, 21), seeds=range(16), steps: int = 4, ref_log2: int = 24, ref_seeds=range(100, 104),
-          n_s: int = 2, spec_fn=problem) -> dict:
+          n_s: int = 2, census_order: int = 0, spec_fn=problem) -> dict:
     import torch
-    ref = np.mean([end_flux(spec_fn(1 << ref_log2, s, W.SOBOL, n_s), steps) for s in ref_seeds], axis=0)
+    mk = lambda n, s, smp: spec_fn(n, s, smp, n_s, census_order=census_order)   # noqa: E731
+    ref = np.mean([end_flux(mk(1 << ref_log2, s, W.SOBOL), steps) for s in ref_seeds], axis=0)
     nref = float(np.linalg.norm(ref))
-    out = {"workload": spec_fn(1, 0, W.SOBOL, n_s).name, "steps": steps, "reference_histories": 1 << ref_log2,
+    out = {"workload": mk(1, 0, W.SOBOL).name, "steps": steps, "reference_histories": 1 << ref_log2,
            "reference_shifts": len(list(ref_seeds)), "seeds": len(list(seeds)), "metric": "relative L2 error of the "
            "end-of-step scalar flux, RMS over seeds"}
     for name, sampler in (("sobol", W.SOBOL), ("prng", W.PRNG)):
         ns, errs = [], []
         for k in log2_n:
             n = 1 << k
-            e2 = [float(np.linalg.norm(end_flux(spec_fn(n, s, sampler, n_s), steps) - ref)) ** 2 for s in seeds]
+            e2 = [float(np.linalg.norm(end_flux(mk(n, s, sampler), steps) - ref)) ** 2 for s in seeds]
             ns.append(n)
             errs.append(math.sqrt(sum(e2) / len(e2)) / nref)
         out[name] = {"n": ns, "err": errs, "alpha": fit_alpha(ns, errs)}
@@ -63,7 +67,9 @@ def study(log2_n=range(10, 21), seeds=range(16), steps: int = 4, ref_log2: int =
 
 if __name__ == "__main__":
     # one step (the MC leg from the source, then the collided solve) and four steps (census
-    # particles re-streamed through the remap), at N_s = 0 (5 point dimensions) and N_s = 2 (11)
+    # particles re-streamed through the remap), at N_s = 0 (5 point dimensions) and N_s = 2 (11),
+    # and four steps with the census in cell order
     for n_s in (0, 2):
         for steps in (1, 4):
             print(json.dumps(study(steps=steps, n_s=n_s)), flush=True)
+    print(json.dumps(study(steps=4, n_s=2, census_order=1)), flush=True)

@@ -35,9 +35,13 @@ struct hyb_batch {
     std::vector<cudaEvent_t> join_ev;
     cudaEvent_t fork_ev = nullptr, ev0 = nullptr, ev1 = nullptr;
     void* d_args[2] = {nullptr, nullptr};   // per parity: LegArgs of every problem
+    size_t cap_probs = 0;                   // problems the per-problem buffers hold (grow-only)
+    size_t cap_chunks = 0, cap_bchunks = 0; // chunk queue capacities (grow-only)
     void* d_chunks = nullptr;
     int nchunks = 0;
-    int* d_head = nullptr;
+    void* d_bchunks = nullptr;              // birth chunks: (problem, [i0, i1) of its births)
+    int nbchunks = 0;
+    int* d_head = nullptr;                  // two queue heads: leg, births
     hyb::DevState* d_report = nullptr;      // per problem: a copy of its counters after the step
     hyb::DevState* h_report = nullptr;      // pinned
     uint32_t* d_V = nullptr;
@@ -73,22 +77,36 @@ void drop_graphs(hyb_batch* b) {
 }
 
 hyb_status build_chunks(hyb_batch* b) {
-    std::vector<LegChunkH> ch;
+    std::vector<LegChunkH> ch, bch;
     const long long C = std::max(32, b->tune.chunk);
     for (size_t i = 0; i < b->probs.size(); ++i) {
         hyb_problem* p = b->probs[i];
-        const long long N = p->bank_cap + (p->has_src ? p->d.n_hist : 0);
+        const long long nsrc = p->has_src ? p->d.n_hist : 0;
+        const long long N = p->bank_cap + nsrc;
         for (long long j = 0; j < std::max(N, 1LL); j += C) ch.push_back(LegChunkH{(int)i, 0, j, std::min(N, j + C)});
+        for (long long j = 0; j < nsrc; j += C) bch.push_back(LegChunkH{(int)i, 0, j, std::min(nsrc, j + C)});
     }
     // interleave problems so that large banks do not end the queue alone
     std::stable_sort(ch.begin(), ch.end(), [](const LegChunkH& x, const LegChunkH& y) { return x.j0 < y.j0; });
-    if (b->d_chunks) cudaFree(b->d_chunks);
-    b->d_chunks = nullptr;
-    if (cudaMalloc(&b->d_chunks, ch.size() * sizeof(LegChunkH)) != cudaSuccess)
+    std::stable_sort(bch.begin(), bch.end(), [](const LegChunkH& x, const LegChunkH& y) { return x.j0 < y.j0; });
+    auto ensure = [](void** d, size_t* cap, size_t need) {
+        need = std::max<size_t>(need, 1);
+        if (*cap >= need) return true;
+        if (*d) cudaFree(*d);
+        *d = nullptr;
+        *cap = 0;
+        if (cudaMalloc(d, need * sizeof(LegChunkH)) != cudaSuccess) return false;
+        *cap = need;
+        return true;
+    };
+    if (!ensure(&b->d_chunks, &b->cap_chunks, ch.size()) || !ensure(&b->d_bchunks, &b->cap_bchunks, bch.size()))
         return bfail(b, HYB_ENOMEM, "chunk queue allocation");
-    if (cudaMemcpy(b->d_chunks, ch.data(), ch.size() * sizeof(LegChunkH), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (cudaMemcpy(b->d_chunks, ch.data(), ch.size() * sizeof(LegChunkH), cudaMemcpyHostToDevice) != cudaSuccess ||
+        (!bch.empty() && cudaMemcpy(b->d_bchunks, bch.data(), bch.size() * sizeof(LegChunkH),
+                                    cudaMemcpyHostToDevice) != cudaSuccess))
         return bfail(b, HYB_ECUDA, "chunk queue upload");
     b->nchunks = (int)ch.size();
+    b->nbchunks = (int)bch.size();
     return HYB_OK;
 }
 
@@ -114,12 +132,12 @@ cudaError_t issue_phase(hyb_batch* b, int q, int phase) {
             ck(cudaMemsetAsync(p->st, 0, offsetof(hyb::DevState, r_histories), b->s0));
             ck(cudaMemsetAsync(&p->st->status, 0, sizeof(int), b->s0));
         }
-        ck(cudaMemsetAsync(b->d_head, 0, sizeof(int), b->s0));
+        ck(cudaMemsetAsync(b->d_head, 0, 2 * sizeof(int), b->s0));
         const int per_sm = b->tune.ctas_per_sm > 0 ? b->tune.ctas_per_sm
                                                    : hyb::leg_batch_ctas_per_sm(b->prec) * 256 / b->tune.block;
         const int grid = std::max(1, std::min(b->nchunks, sms * per_sm));
         ck(hyb::launch_mc_leg_batch(b->prec, b->d_args[q], b->d_chunks, b->nchunks, b->d_head, b->d_V, b->ntab_max,
-                                    grid, b->tune.block, b->s0));
+                                    grid, b->tune.block, b->s0, b->d_bchunks, b->nbchunks, b->d_head + 1));
     }
     ck(cudaEventRecord(b->fork_ev, b->s0));
     for (auto s : b->pool) ck(cudaStreamWaitEvent(s, b->fork_ev, 0));
@@ -224,6 +242,52 @@ hyb_status finish_iterations(hyb_batch* b, int q, size_t i) {
     return rc == HYB_OK ? HYB_OK : bfail(b, rc, "eager source iteration");
 }
 
+// Takes the batch's problem set: per-problem device buffers grow only, so replacing the set
+// (continuous batching) allocates nothing once the largest set has been seen.
+hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) {
+    const int prec = problems[0] ? problems[0]->prec : 0;
+    std::vector<hyb_problem*> probs;
+    for (int i = 0; i < n; ++i) {
+        hyb_problem* p = problems[i];
+        if (!p || p->prec != prec) return bfail(b, HYB_EINVAL, "problems must share one precision");
+        if (p->leg_done) return bfail(b, HYB_ESTATE, "problems must be at a step boundary");
+        probs.push_back(p);
+    }
+    if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");
+    b->prec = prec;
+    b->probs = probs;
+    b->cur0.clear(); b->kmax.clear();
+    b->ntab_max = 0;
+    for (hyb_problem* p : probs) {
+        b->cur0.push_back(p->cur);
+        b->kmax.push_back(std::max(8, p->last_sn_iters + 3));
+        b->ntab_max = std::max(b->ntab_max, hyb::leg_ntab(p));
+    }
+    b->parity = 0;
+    const size_t ab = hyb::leg_args_bytes(b->prec);
+    if ((size_t)n > b->cap_probs) {
+        const size_t cap = std::max<size_t>((size_t)n, 2 * b->cap_probs);
+        for (int q = 0; q < 2; ++q) { if (b->d_args[q]) cudaFree(b->d_args[q]); b->d_args[q] = nullptr; }
+        if (b->d_report) cudaFree(b->d_report);
+        if (b->h_report) cudaFreeHost(b->h_report);
+        b->d_report = nullptr; b->h_report = nullptr;
+        b->cap_probs = 0;
+        for (int q = 0; q < 2; ++q)
+            if (cudaMalloc(&b->d_args[q], ab * cap) != cudaSuccess) return bfail(b, HYB_ENOMEM, "args");
+        if (cudaMalloc(&b->d_report, cap * sizeof(hyb::DevState)) != cudaSuccess ||
+            cudaMallocHost(&b->h_report, cap * sizeof(hyb::DevState)) != cudaSuccess)
+            return bfail(b, HYB_ENOMEM, "report");
+        b->cap_probs = cap;
+    }
+    std::vector<unsigned char> host(ab * n);
+    for (int q = 0; q < 2; ++q) {
+        for (int i = 0; i < n; ++i) hyb::leg_args_host(b->probs[i], b->cur0[i] ^ q, host.data() + ab * i);
+        if (cudaMemcpy(b->d_args[q], host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bfail(b, HYB_ECUDA, "args upload");
+    }
+    return HYB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -233,16 +297,7 @@ HYB_API hyb_status hyb_batch_create(hyb_problem* const* problems, int32_t n, voi
     *out = nullptr;
     hyb_batch* b = new (std::nothrow) hyb_batch();
     if (!b) return bfail(nullptr, HYB_ENOMEM, "host allocation");
-    b->prec = problems[0]->prec;
-    for (int i = 0; i < n; ++i) {
-        hyb_problem* p = problems[i];
-        if (!p || p->prec != b->prec) { delete b; return bfail(nullptr, HYB_EINVAL, "problems must share one precision"); }
-        if (p->leg_done) { delete b; return bfail(nullptr, HYB_ESTATE, "problems must be at a step boundary"); }
-        b->probs.push_back(p);
-        b->cur0.push_back(p->cur);
-        b->kmax.push_back(std::max(8, p->last_sn_iters + 3));
-        b->ntab_max = std::max(b->ntab_max, hyb::leg_ntab(p));
-    }
+    b->prec = problems[0] ? problems[0]->prec : 0;
     b->s0 = (cudaStream_t)cuda_stream;
     if (!b->s0) {   // graphs cannot be recorded on the legacy default stream
         if (cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) != cudaSuccess) {
@@ -251,32 +306,32 @@ HYB_API hyb_status hyb_batch_create(hyb_problem* const* problems, int32_t n, voi
         }
         b->own_s0 = true;
     }
-    auto fail_all = [&](hyb_status s, const char* m) {
-        g_batch_err = m;
+    auto fail_all = [&](hyb_status s, const std::string& m) {
         hyb_batch_destroy(b);
+        g_batch_err = m;
         return s;
     };
-    for (int q = 0; q < 2; ++q) {
-        const size_t ab = hyb::leg_args_bytes(b->prec);
-        std::vector<unsigned char> host(ab * n);
-        for (int i = 0; i < n; ++i) hyb::leg_args_host(b->probs[i], b->cur0[i] ^ q, host.data() + ab * i);
-        if (cudaMalloc(&b->d_args[q], host.size()) != cudaSuccess) return fail_all(HYB_ENOMEM, "args");
-        if (cudaMemcpy(b->d_args[q], host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
-            return fail_all(HYB_ECUDA, "args upload");
-    }
-    if (cudaMalloc(&b->d_head, sizeof(int)) != cudaSuccess) return fail_all(HYB_ENOMEM, "queue head");
-    if (cudaMalloc(&b->d_report, n * sizeof(hyb::DevState)) != cudaSuccess) return fail_all(HYB_ENOMEM, "report");
-    if (cudaMallocHost(&b->h_report, n * sizeof(hyb::DevState)) != cudaSuccess) return fail_all(HYB_ENOMEM, "report");
+    if (cudaMalloc(&b->d_head, 2 * sizeof(int)) != cudaSuccess) return fail_all(HYB_ENOMEM, "queue heads");
     if (cudaMalloc(&b->d_V, HYB_SOBOL_DIMS * 32 * 4) != cudaSuccess) return fail_all(HYB_ENOMEM, "table");
     if (cudaMemcpy(b->d_V, hyb::sobol_table_host(), HYB_SOBOL_DIMS * 32 * 4, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail_all(HYB_ECUDA, "table upload");
     if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
         return fail_all(HYB_ECUDA, "events");
-    hyb_status s = hyb_batch_set_tuning(b, &b->tune);
-    if (s != HYB_OK) { std::string m = b->err; hyb_batch_destroy(b); g_batch_err = m; return s; }
+    hyb_status s = load_problems(b, problems, n);
+    if (s == HYB_OK) s = hyb_batch_set_tuning(b, &b->tune);
+    if (s != HYB_OK) return fail_all(s, b->err);
     *out = b;
     return HYB_OK;
+}
+
+HYB_API hyb_status hyb_batch_set_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) {
+    if (!b || !problems || n < 1) return bfail(b, HYB_EINVAL, "need at least one problem");
+    if (b->s0 && cudaStreamSynchronize(b->s0) != cudaSuccess) return bfail(b, HYB_ECUDA, "stream");
+    drop_graphs(b);
+    hyb_status s = load_problems(b, problems, n);
+    if (s != HYB_OK) return s;
+    return build_chunks(b);
 }
 
 HYB_API hyb_status hyb_batch_set_tuning(hyb_batch* b, const hyb_batch_tuning* t) {
@@ -396,6 +451,7 @@ HYB_API hyb_status hyb_batch_destroy(hyb_batch* b) {
     for (int q = 0; q < 2; ++q) if (b->d_args[q]) cudaFree(b->d_args[q]);
     if (b->d_chunks) cudaFree(b->d_chunks);
     if (b->d_head) cudaFree(b->d_head);
+    if (b->d_bchunks) cudaFree(b->d_bchunks);
     if (b->d_report) cudaFree(b->d_report);
     if (b->h_report) cudaFreeHost(b->h_report);
     if (b->d_V) cudaFree(b->d_V);

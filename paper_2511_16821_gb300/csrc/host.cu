@@ -208,7 +208,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
-        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos;
+        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv;
     int64_t cap, nblk;
     int gr, gc;
 };
@@ -249,7 +249,11 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.grow = ((size_t(1) << z.gr) + 1) * 4;
     z.gcol = (size_t)d->ny * ((size_t(1) << z.gc) + 1) * 4;
     z.remf32 = 4 * nc * 4;
+    z.siginv = 4 * nc * 4;
     z.rempos = nc * 4;
+    const size_t nslots = (size_t)(z.cap + d->n_hist);
+    z.sortkv = d->census_order == 1 ? nslots * 4 : 0;                    // x4: keys, slots, ping-pong
+    z.sortc = d->census_order == 1 ? 256 * ((nslots + 2047) / 2048) * 4 : 0;
     return z;
 }
 
@@ -259,7 +263,8 @@ size_t layout_bytes(const hyb_problem_desc* d) {
     const size_t parts[] = {z.st, z.sobol, z.sig, z.sa, z.ss, z.Q, z.cdf_q, z.cdf_row, z.cdf_col, z.cdf_q, z.cdf_row,
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4,
-                            z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos};
+                            z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
+                            z.sortkv, z.sortkv, z.sortkv, z.sortc, z.siginv};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -313,6 +318,10 @@ void assign(hyb_problem* p) {
     p->src_cdf.gc = p->rem_cdf.gc = z.gc;
     p->rem_f32 = (float*)take(z.remf32);
     p->rem_pos = (int*)take(z.rempos);
+    for (int i = 0; i < 2; ++i) p->sort_keys[i] = z.sortkv ? (uint32_t*)take(z.sortkv) : nullptr;
+    for (int i = 0; i < 2; ++i) p->sort_vals[i] = z.sortkv ? (uint32_t*)take(z.sortkv) : nullptr;
+    p->sort_counts = z.sortc ? (uint32_t*)take(z.sortc) : nullptr;
+    p->sig_inv = (float*)take(z.siginv);
     p->bank_cap = z.cap;
     p->nblk_max = z.nblk;
 }
@@ -346,6 +355,7 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->precision != HYB_FP32 && d->precision != HYB_FP64) { *why = "unknown precision"; return HYB_EINVAL; }
     if (d->sn_order != 4 && d->sn_order != 8) { *why = "sn_order must be 4 or 8"; return HYB_EINVAL; }
     if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
+    if (d->census_order != 0 && d->census_order != 1) { *why = "census_order must be 0 or 1"; return HYB_EINVAL; }
     if (!(d->sn_tol >= 0) || !(d->w_min >= 0) || !(d->w_min < 1)) { *why = "sn_tol >= 0 and 0 <= w_min < 1 required"; return HYB_EINVAL; }
     if (!d->sigma_a || !d->sigma_s) { *why = "sigma_a and sigma_s are required"; return HYB_EINVAL; }
     const size_t nc = (size_t)d->nx * d->ny;
@@ -563,6 +573,15 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     if (chk(cudaMemsetAsync(p->st, 0, sizeof(DevState), st), "memset state") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->sobolV, sobol_table_host(), HYB_SOBOL_DIMS * 32 * 4, cudaMemcpyHostToDevice, st), "copy sobol") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->sig, sig.data(), sig.size(), cudaMemcpyHostToDevice, st), "copy sigma") != HYB_OK) return bail(HYB_ECUDA);
+    // FP32 path: per-cell reciprocals (1/sigma_a, 1/sigma_s, 1/sigma_t, 0), 0 where the cross section is 0
+    std::vector<float> sinv(4 * nc, 0.0f);
+    for (size_t k = 0; k < nc; ++k) {
+        const double sa = d->sigma_a[k], ss = d->sigma_s[k], stt = sa + ss;
+        sinv[4 * k] = sa > 0 ? (float)(1.0 / sa) : 0.0f;
+        sinv[4 * k + 1] = ss > 0 ? (float)(1.0 / ss) : 0.0f;
+        sinv[4 * k + 2] = stt > 0 ? (float)(1.0 / stt) : 0.0f;
+    }
+    if (chk(cudaMemcpyAsync(p->sig_inv, sinv.data(), sinv.size() * 4, cudaMemcpyHostToDevice, st), "copy 1/sigma") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->sa_d, d->sigma_a, nc * 8, cudaMemcpyHostToDevice, st), "copy sa") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->ss_d, d->sigma_s, nc * 8, cudaMemcpyHostToDevice, st), "copy ss") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->Q_d, d->Q ? d->Q : zeros.data(), nc * 8, cudaMemcpyHostToDevice, st), "copy Q") != HYB_OK) return bail(HYB_ECUDA);

@@ -24,6 +24,20 @@ inline BankView<T> bank_view(hyb_problem* p, int which) {
     return b;
 }
 
+// Birth staging inside the remap staging buffer (idle during the leg): cell (int32, n_hist, padded
+// to 256 B), then fx, fy, ox, oy, srem, tau (n_hist each). The staging buffer holds at least
+// 2 n_hist slots of 4 + 5 sizeof(T) bytes, more than this needs.
+template <typename T>
+inline BirthView<T> birth_view(hyb_problem* p) {
+    BirthView<T> b;
+    const int64_t n = p->d.n_hist;
+    char* base = (char*)p->stage;
+    b.cell = (int32_t*)base;
+    T* f = (T*)(base + bank_cell_bytes(n));
+    b.fx = f; b.fy = f + n; b.ox = f + 2 * n; b.oy = f + 3 * n; b.srem = f + 4 * n; b.tau = f + 5 * n;
+    return b;
+}
+
 // ---------------------------------------------------------------------------------------------
 // splitmix64 output function (Steele, Lea & Flood 2014) and the point-set keys
 // ---------------------------------------------------------------------------------------------
@@ -96,6 +110,46 @@ struct Points {
 };
 
 // ---------------------------------------------------------------------------------------------
+// Integer <-> float conversions on the integer pipe. The conversion instructions count against
+// the FP64 pipe on this GPU (a small fraction of the FP32 rate; measured as FP64-pipe activity in
+// FP32-only kernels), so the FP32 path composes the values from IEEE-754 fields instead.
+// ---------------------------------------------------------------------------------------------
+// float -> int64, rounding to nearest, ties to even (|x| < 2^63; equals __float2ll_rn there)
+__device__ __forceinline__ long long f2ll_rn(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const int e = (int)((u >> 23) & 0xFFu);
+    const uint32_t m = (u & 0x7FFFFFu) | 0x800000u;
+    int sh = e - 150;                       // x = +-m 2^sh for normal x
+    long long v = 0;
+    if (sh >= 0) {
+        sh = sh > 39 ? 39 : sh;             // |x| < 2^63 keeps sh <= 39
+        v = (long long)((unsigned long long)m << sh);
+    } else if (sh >= -24) {
+        const int r = -sh;                  // 1..24 fraction bits
+        const uint32_t q = m >> r, rem = m & ((1u << r) - 1u), half = 1u << (r - 1);
+        v = (long long)(q + ((rem > half || (rem == half && (q & 1u))) ? 1u : 0u));
+    }                                       // else |x| < 1/2 (or 0, subnormal): 0
+    return (u >> 31) ? -v : v;
+}
+
+// uint32 -> float rounded toward zero (equals __uint2float_rz): the leading bit gives the
+// exponent, the next 23 bits the fraction
+__device__ __forceinline__ float u32_to_f_rz(uint32_t x) {
+    if (x == 0u) return 0.0f;
+    const int p = 31 - __clz(x);                              // leading bit
+    const uint32_t m = p >= 23 ? (x >> (p - 23)) : (x << (23 - p));
+    return __uint_as_float(((uint32_t)(127 + p) << 23) | (m & 0x7FFFFFu));
+}
+
+// uint64 -> float rounded toward zero (within 1 ulp)
+__device__ __forceinline__ float u64_to_f(unsigned long long x) {
+    if (x == 0ull) return 0.0f;
+    const int p = 63 - __clzll(x);
+    const uint32_t m = p >= 23 ? (uint32_t)(x >> (p - 23)) : (uint32_t)(x << (23 - p));
+    return __uint_as_float(((uint32_t)(127 + p) << 23) | (m & 0x7FFFFFu));
+}
+
+// ---------------------------------------------------------------------------------------------
 // precision traits: FP32 path (int64 fixed point), FP64 path (128-bit fixed point)
 // ---------------------------------------------------------------------------------------------
 template <typename T> struct Prec;
@@ -105,12 +159,35 @@ template <> struct Prec<float> {
     static constexpr int kbits = 61;
     // u in (0,1): x 2^-32 + 2^-33 with x rounded toward zero to 24 bits, so u keeps 2^-24
     // relative precision near 0 (-log u stays accurate) and never rounds up to 1
-    static __device__ __forceinline__ float unit(uint32_t x) { return fmaf(__uint2float_rz(x), 0x1p-32f, 0x1p-33f); }
+    static __device__ __forceinline__ float unit(uint32_t x) { return fmaf(u32_to_f_rz(x), 0x1p-32f, 0x1p-33f); }
     // 1 - u with the same relative precision: the complement ~x maps to 1 - u exactly
     static __device__ __forceinline__ float unit_c(uint32_t x) { return unit(~x); }
     static __device__ __forceinline__ float neglog(float u) { return -logf(u); }
     static __device__ __forceinline__ float ex(float x) { return expf(x); }
     static __device__ __forceinline__ float exm1(float x) { return expm1f(x); }
+    // e = e^{-x} and att = 1 - e^{-x} for x = sigma l >= 0 in one evaluation: below x = 1/4 the
+    // Taylor series of 1 - e^{-x} in nested form (nine terms, truncation below 1e-10 relative),
+    // above it the hardware exponential (relative error ~1e-7 for the x of a few mean free paths
+    // that carry weight)
+    static __device__ __forceinline__ void att_e(float x, float* att, float* e) {
+        if (x < 0.25f) {
+            float s = 1.0f - x * (1.0f / 9.0f);
+            s = 1.0f - x * (1.0f / 8.0f) * s;
+            s = 1.0f - x * (1.0f / 7.0f) * s;
+            s = 1.0f - x * (1.0f / 6.0f) * s;
+            s = 1.0f - x * (1.0f / 5.0f) * s;
+            s = 1.0f - x * (1.0f / 4.0f) * s;
+            s = 1.0f - x * (1.0f / 3.0f) * s;
+            s = 1.0f - x * 0.5f * s;
+            *att = x * s;
+            *e = 1.0f - *att;
+        } else {
+            *e = __expf(-x);
+            *att = 1.0f - *e;
+        }
+    }
+    // reciprocal of a flight direction component (used for face distances on the FP32 path)
+    static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
     static __device__ __forceinline__ void sincos2pi(float u, float* s, float* c) { sincospif(2.0f * u, s, c); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     // exact-order a*b + c (FP32 path: contraction allowed)
@@ -120,7 +197,7 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
     // returns the number of global additions issued (0 or 1)
     static __device__ __forceinline__ int add(acc_t* p, float c, float scale) {
-        const long long v = __float2ll_rn(c * scale);
+        const long long v = f2ll_rn(c * scale);
         if (v) atomicAdd(p, (unsigned long long)v);
         return v != 0;
     }
@@ -218,6 +295,11 @@ template <> struct Prec<double> {
     static __device__ __forceinline__ double neglog(double u) { return neg_log_series(u); }
     static __device__ __forceinline__ double ex(double x) { return exp(x); }
     static __device__ __forceinline__ double exm1(double x) { return expm1(x); }
+    static __device__ __forceinline__ void att_e(double x, double* att, double* e) {
+        *att = -expm1(-x);
+        *e = exp(-x);
+    }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
     static __device__ __forceinline__ void sincos2pi(double u, double* s, double* c) { sincos_2pi_series(u, s, c); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     // separately rounded product and sum: FP64 geometry follows IEEE order exactly
@@ -249,21 +331,45 @@ __host__ __device__ __forceinline__ int scale_exponent(double B, int kbits) {
 // ---------------------------------------------------------------------------------------------
 // g_n(x) = int_0^1 t^n e^{-x t} dt, n = 0,1,2: series below x = 1, closed form above
 // ---------------------------------------------------------------------------------------------
+// coefficient of x^k in g_n(x) = int_0^1 t^n e^{-x t} dt = sum_k (-x)^k / (k! (n + k + 1))
+__host__ __device__ constexpr double gcoef(int n, int k) {
+    double f = 1.0;
+    for (int i = 2; i <= k; ++i) f *= (double)i;
+    return ((k & 1) ? -1.0 : 1.0) / (f * (double)(n + k + 1));
+}
+
+// Horner steps k = K, K-1, ..., 0 for g_0, g_1, g_2 together (coefficients fixed at compile time)
+template <typename T, int K>
+struct GHorner {
+    static __device__ __forceinline__ void run(T x, T* s0, T* s1, T* s2) {
+        constexpr double c0 = gcoef(0, K), c1 = gcoef(1, K), c2 = gcoef(2, K);
+        *s0 = Prec<T>::fma_(*s0, x, T(c0));
+        *s1 = Prec<T>::fma_(*s1, x, T(c1));
+        *s2 = Prec<T>::fma_(*s2, x, T(c2));
+        GHorner<T, K - 1>::run(x, s0, s1, s2);
+    }
+};
 template <typename T>
-__device__ __forceinline__ void gfun(T x, T* g0, T* g1, T* g2) {
+struct GHorner<T, -1> {
+    static __device__ __forceinline__ void run(T, T*, T*, T*) {}
+};
+
+// g_0, g_1, g_2 at x = sigma l >= 0, given e = e^{-x} and att = 1 - e^{-x} of the same x:
+// the power series (Horner, kSeries terms) below x = 1, the closed forms above
+template <typename T>
+__device__ __forceinline__ void gfun(T x, T e, T att, T* g0, T* g1, T* g2) {
     if (x < T(1)) {
-        T s0 = 0, s1 = 0, s2 = 0, term = 1;
-#pragma unroll
-        for (int k = 0; k < Prec<T>::kSeries; ++k) {
-            s0 += term / T(k + 1);
-            s1 += term / T(k + 2);
-            s2 += term / T(k + 3);
-            term *= -x / T(k + 1);
-        }
+        constexpr int K = Prec<T>::kSeries - 1;
+        T s0 = T(gcoef(0, K)), s1 = T(gcoef(1, K)), s2 = T(gcoef(2, K));
+        GHorner<T, K - 1>::run(x, &s0, &s1, &s2);
         *g0 = s0; *g1 = s1; *g2 = s2;
+    } else if (sizeof(T) == 4) {
+        const T rx = T(1) / x;
+        *g0 = att * rx;
+        *g1 = (*g0 - e) * rx;
+        *g2 = Prec<T>::fma_(T(2), *g1, -e) * rx;
     } else {
-        const T e = Prec<T>::ex(-x);
-        *g0 = -Prec<T>::exm1(-x) / x;
+        *g0 = att / x;
         *g1 = (*g0 - e) / x;
         *g2 = Prec<T>::fma_(T(2), *g1, -e) / x;
     }
@@ -324,7 +430,7 @@ __device__ __forceinline__ T bin_frac(unsigned long long a, unsigned long long b
 
 template <>
 __device__ __forceinline__ float bin_frac<float>(unsigned long long a, unsigned long long b, unsigned long long W) {
-    return ((float)a + (float)b * 0x1p-33f) / (float)W;
+    return fmaf(u64_to_f(b), 0x1p-33f, u64_to_f(a)) / u64_to_f(W);
 }
 
 // cell and in-cell fractions from the 2-D CDF: row from x1, column within the row from x0

@@ -28,6 +28,7 @@ struct DevState {
     // counters of the last MC leg
     unsigned long long histories, segments, collisions, leaked, census, killed, reached, errors;
     unsigned long long tally_adds;   // fixed-point tally additions (global atomics) issued
+    unsigned long long leg_next;     // next history index handed to a warp (single-problem leg)
     Acc128 w_source, w_absorbed, w_leaked, w_census, w_handoff, w_killed;
     // counters of the last remap
     unsigned long long r_histories, r_segments, r_leaked, r_killed, r_errors, r_alive;
@@ -61,6 +62,11 @@ struct DevState {
 
 template <typename T>
 struct BankView { int32_t* cell; T *fx, *fy, *ox, *oy, *w; };
+
+// Start states of a leg's source births (cell, in-cell position, direction, remaining flight
+// c (t_{n+1} - t), first optical depth), written ahead of the leg by a converged kernel.
+template <typename T>
+struct BirthView { int32_t* cell; T *fx, *fy, *ox, *oy, *srem, *tau; };
 
 // Integer 2-D CDF: per-cell integer weights q, row marginal row_pre (ny + 1), per-row column
 // conditionals col_pre (ny x (nx + 1)). Optional guide tables (Chen & Asau 1974) narrow each pick:
@@ -106,10 +112,14 @@ struct hyb_problem {
     // device pointers (into ws)
     uint32_t* sobolV;         // HYB_SOBOL_DIMS x 32
     void* sig;                // ncells x 2 (T): sigma_a, sigma_s
+    float* sig_inv;           // ncells x 4: 1/sigma_a, 1/sigma_s, 1/sigma_t, 0 (FP32 leg; 0 where sigma = 0)
     double *sa_d, *ss_d, *Q_d;  // FP64 copies for the remap density
     hyb::Cdf2DView src_cdf, rem_cdf;
     double* rem_f;            // 4 x ncells remap density coefficients
     float* rem_f32;           // the same in FP32 (FP32 path)
+    uint32_t* sort_keys[2];   // census sort (census_order 1): ping-pong keys and slots, and the
+    uint32_t* sort_vals[2];   //   per-tile digit counts; null when the census keeps slot order
+    uint32_t* sort_counts;
     int* rem_pos;             // ncells: 1 where the bilinear remap density is non-negative
     double* rem_q;            // ncells signed remap cell weights q = f0 A dt
     double* cell_scratch;     // per-row partials for the CDF build
@@ -147,14 +157,20 @@ cudaError_t launch_flux(hyb_problem* p);
 cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
                                  double* qmax_out, double* scratch, cudaStream_t stream);
 cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0);
+cudaError_t launch_census_sort(const int32_t* cells, long long n, uint32_t ncells, uint32_t* const keys[2],
+                               uint32_t* const vals[2], uint32_t* counts, cudaStream_t s, const uint32_t** perm,
+                               const uint32_t** sorted_keys);
 cudaError_t launch_bank_stats(hyb_problem* p);
 cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,
                           uint32_t* out, cudaStream_t s);
 size_t leg_args_bytes(int prec);
 void leg_args_host(hyb_problem* p, int cur, void* out);
 int leg_ntab(const hyb_problem* p);
+// the batched births (chunks over each problem's birth indices, queue head d_bhead) and then the
+// batched leg (chunks over [bank | births], queue head d_head)
 cudaError_t launch_mc_leg_batch(int prec, const void* d_args, const void* d_chunks, int nchunks, int* d_head,
-                                const uint32_t* V, int ntab_max, int grid, int block, cudaStream_t s);
+                                const uint32_t* V, int ntab_max, int grid, int block, cudaStream_t s,
+                                const void* d_bchunks, int nbchunks, int* d_bhead);
 int leg_batch_ctas_per_sm(int prec);
 cudaError_t sn_start(hyb_problem* p);
 cudaError_t sn_iteration(hyb_problem* p, int first);

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "hyb_device.cuh"
 
@@ -21,11 +22,13 @@ struct LegArgs {
     int nx, ny;
     T dx, dy, cdt;
     const T* sig;               // (sigma_a, sigma_s) per cell
+    const float4* sig_inv;      // FP32 path: (1/sigma_a, 1/sigma_s, 1/sigma_t, 0) per cell (0 where sigma = 0)
     int n_s, sampler, handoff_full, ntab;
     T w_min;
     const uint32_t* V;
     uint64_t seed;              // keys of the census and source point sets come from (seed, step)
     BankView<T> bank;
+    BirthView<T> births;        // staged source births (cell == nullptr: drawn inside the leg)
     Cdf2DView cdf;
     long long n_src;
     T w0;
@@ -40,6 +43,7 @@ template <typename T>
 struct Hist {
     int ix, iy, n, seg;
     T fx, fy, ox, oy, w, w_start, srem, tau;
+    T rox, roy;                 // 1/ox, 1/oy (FP32 face distances)
     uint32_t idx;
     long long j;
     bool census_stream;
@@ -47,7 +51,7 @@ struct Hist {
 
 // Per-thread statistics of the histories a thread finished (integers: order-free sums).
 struct LegTally {
-    unsigned long long c[9];   // histories, segments, collisions, leaked, census, killed, reached, errors,
+    unsigned int c[9];         // histories, segments, collisions, leaked, census, killed, reached, errors,
                                // fixed-point tally additions issued
     long long f[6];            // fixed-point weights: source, absorbed, leaked, census, handoff, killed
     int status;
@@ -86,16 +90,74 @@ __device__ __forceinline__ LegScales leg_scales(const LegArgs<T>& a) {
 }
 
 // weight x in the fixed point of scale 2^kw: FP32 by an exact float product, FP64 as before
-__device__ __forceinline__ long long fix_w(float x, double, float scw_f) { return __float2ll_rn(x * scw_f); }
+__device__ __forceinline__ long long fix_w(float x, double, float scw_f) { return f2ll_rn(x * scw_f); }
 __device__ __forceinline__ long long fix_w(double x, double scw, float) { return __double2ll_rn(x * scw); }
 
-// The histories [next, last) of one problem, tracked by the calling warp with lane refill: a lane
-// whose history ends takes the next index at once (ranks by ballot, deterministic order), so the
-// warp keeps its lanes on segments instead of waiting for its longest history.
+// Start state of source birth i (Sec. 2.3): cell and in-cell position from the integer source CDF
+// (dims 0, 1), remaining flight c dt (1 - u) from the birth time (dim 2), isotropic direction
+// (dims 3, 4), first optical depth -log u (dim 5) when N_s > 0. Used by the birth kernel and by
+// the leg when births are not staged, so both give the same state bit for bit.
 template <typename T>
-__device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long last, long long nb,
-                               const uint32_t* sV, const uint32_t* sShC, const uint32_t* sShS, uint64_t key_c,
-                               uint64_t key_s, const LegScales& sc, LegTally& t) {
+__device__ __forceinline__ void birth_state(const LegArgs<T>& a, const Points& pts, uint32_t i, int* ix, int* iy, T* fx,
+                                            T* fy, T* ox, T* oy, T* srem, T* tau) {
+    using P = Prec<T>;
+    T frx, fry;
+    const int k = sample_cell<T>(a.cdf, a.nx, a.ny, pts(i, 0), pts(i, 1), &frx, &fry);
+    *ix = k % a.nx; *iy = k / a.nx;
+    *fx = frx * a.dx; *fy = fry * a.dy;
+    iso_dir<T>(pts(i, 3), pts(i, 4), ox, oy);
+    *srem = a.cdt * P::unit_c(pts(i, 2));
+    *tau = a.n_s > 0 ? P::neglog(P::unit(pts(i, 5))) : T(0);
+}
+
+// Work sources of a warp: a fixed range (one chunk of a batch), or chunks of kWarpChunk histories
+// taken from the problem's device counter until [0, N) is exhausted (the single-problem leg, so
+// warps that drew short histories take more and none waits at the end). Integer tallies make the
+// results independent of which warp runs which history.
+struct FixedRange {
+    long long j0, j1;
+    bool given = false;
+    __device__ bool operator()(long long* next, long long* last) {
+        if (given) return false;
+        given = true;
+        *next = j0; *last = j1;
+        return j0 < j1;
+    }
+};
+
+constexpr long long kWarpChunk = 64;
+
+struct CounterChunks {
+    unsigned long long* counter;
+    long long N;
+    __device__ bool operator()(long long* next, long long* last) {
+        long long s = 0;
+        if ((threadIdx.x & 31) == 0) s = (long long)atomicAdd(counter, (unsigned long long)kWarpChunk);
+        s = __shfl_sync(0xffffffffu, s, 0);
+        if (s >= N) return false;
+        *next = s;
+        *last = s + kWarpChunk < N ? s + kWarpChunk : N;
+        return true;
+    }
+};
+
+// sigma_a, sigma_s of cell k (one vector load through the read-only path)
+__device__ __forceinline__ void load_sig(const float* sig, int k, float* sa, float* ss) {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(sig) + k);
+    *sa = v.x; *ss = v.y;
+}
+__device__ __forceinline__ void load_sig(const double* sig, int k, double* sa, double* ss) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(sig) + k);
+    *sa = v.x; *ss = v.y;
+}
+
+// The histories of one problem that `src` hands out, tracked by the calling warp with lane refill:
+// a lane whose history ends takes the next index at once (ranks by ballot, deterministic order),
+// so the warp keeps its lanes on segments instead of waiting for its longest history.
+template <typename T, typename Src>
+__device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const uint32_t* sV, const uint32_t* sShC,
+                               const uint32_t* sShS, uint64_t key_c, uint64_t key_s, const LegScales& sc,
+                               LegTally& t) {
     using P = Prec<T>;
     const T sc_t = (T)ldexp(1.0, sc.kt), sc_m = (T)ldexp(1.0, sc.km);
     const double scw = sc.scw;
@@ -114,14 +176,24 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
     pts.ntab = a.ntab;
     Hist<T> h;
     bool alive = false;
-    double d_abs = 0, d_hand = 0;   // FP64 path: weight removed from the live history so far
+    // weight removed from the live history so far (FP32 path: float, one conversion per history)
+    using wacc_t = typename std::conditional<sizeof(T) == 4, float, double>::type;
+    wacc_t d_abs = 0, d_hand = 0;
+    long long next = 0, last = 0;
+    bool exhausted = false;
 
     for (;;) {
-        const unsigned need = __ballot_sync(0xffffffffu, !alive);
-        if (need) {
-            const long long j = next + __popc(need & lt_mask);
-            next += __popc(need);
-            if (!alive && j < last) {
+        unsigned need = __ballot_sync(0xffffffffu, !alive);
+        while (need && !exhausted) {
+            if (next >= last && !src(&next, &last)) { exhausted = true; break; }
+            const int cnt = __popc(need);
+            const int take = last - next < (long long)cnt ? (int)(last - next) : cnt;
+            const int rank = __popc(need & lt_mask);
+            const bool mine = ((need >> lane) & 1u) && rank < take;
+            const long long j = next + rank;
+            next += take;
+            need &= ~__ballot_sync(0xffffffffu, mine);
+            if (mine) {
                 // ---- start a history: bank pick-up or birth from Q -----------------------------
                 h.j = j;
                 bool ok = true;
@@ -140,18 +212,23 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
                 } else {
                     h.idx = (uint32_t)(j - nb);
                     h.census_stream = false;
-                    pts.key = key_s; pts.shift = sShS;
-                    T frx, fry;
-                    const int k = sample_cell<T>(a.cdf, nx, ny, pts(h.idx, 0), pts(h.idx, 1), &frx, &fry);
-                    h.ix = k % nx; h.iy = k / nx;
-                    h.fx = frx * DX; h.fy = fry * DY;
-                    iso_dir<T>(pts(h.idx, 3), pts(h.idx, 4), &h.ox, &h.oy);
+                    if (a.births.cell) {
+                        const int k = a.births.cell[h.idx];
+                        h.ix = k % nx; h.iy = k / nx;
+                        h.fx = a.births.fx[h.idx]; h.fy = a.births.fy[h.idx];
+                        h.ox = a.births.ox[h.idx]; h.oy = a.births.oy[h.idx];
+                        h.srem = a.births.srem[h.idx];
+                        h.tau = a.births.tau[h.idx];
+                    } else {
+                        pts.key = key_s; pts.shift = sShS;
+                        birth_state<T>(a, pts, h.idx, &h.ix, &h.iy, &h.fx, &h.fy, &h.ox, &h.oy, &h.srem, &h.tau);
+                    }
                     h.w = a.w0;
-                    h.srem = a.cdt * P::unit_c(pts(h.idx, 2));
                 }
                 if (ok) {
                     pts.key = h.census_stream ? key_c : key_s;
                     pts.shift = h.census_stream ? sShC : sShS;
+                    if constexpr (kF32) { h.rox = P::rcp(h.ox); h.roy = P::rcp(h.oy); }
                     ++t.c[0];
                     h.w_start = h.w;
                     t.f[0] += fix_w(h.w, scw, scw_f);
@@ -159,12 +236,15 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
                     h.n = 0;
                     h.seg = 0;
                     if (Ns == 0) ++t.c[6];
-                    h.tau = Ns > 0 ? P::neglog(P::unit(pts(h.idx, 5))) : T(0);
+                    if (h.census_stream) h.tau = Ns > 0 ? P::neglog(P::unit(pts(h.idx, 5))) : T(0);
                     alive = true;
                 }
             }
         }
-        if (!__any_sync(0xffffffffu, alive)) break;
+        if (!__any_sync(0xffffffffu, alive)) {
+            if (exhausted) break;
+            continue;
+        }
         if (!alive) continue;
         pts.key = h.census_stream ? key_c : key_s;
         pts.shift = h.census_stream ? sShC : sShS;
@@ -172,10 +252,23 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
         // ---- one segment ----------------------------------------------------------------------
         ++h.seg;
         const int k = h.iy * nx + h.ix;
-        const T sa = a.sig[2 * k], ss = a.sig[2 * k + 1], st = sa + ss;
-        const T dxf = h.ox > T(0) ? (DX - h.fx) / h.ox : (h.ox < T(0) ? h.fx / (-h.ox) : INF);
-        const T dyf = h.oy > T(0) ? (DY - h.fy) / h.oy : (h.oy < T(0) ? h.fy / (-h.oy) : INF);
-        const T dcol = (h.n < Ns && ss > T(0)) ? h.tau / ss : INF;
+        T sa, ss;
+        load_sig(a.sig, k, &sa, &ss);
+        const T st = sa + ss;
+        T dxf, dyf, dcol, isa = 0, iss = 0, ist = 0;
+        if constexpr (kF32) {
+            // FP32: products with per-cell and per-flight reciprocals instead of divisions
+            const float4 iv = __ldg(a.sig_inv + k);
+            isa = iv.x; iss = iv.y; ist = iv.z;
+            dxf = h.ox > T(0) ? (DX - h.fx) * h.rox : (h.ox < T(0) ? h.fx * (-h.rox) : INF);
+            dyf = h.oy > T(0) ? (DY - h.fy) * h.roy : (h.oy < T(0) ? h.fy * (-h.roy) : INF);
+            dcol = (h.n < Ns && ss > T(0)) ? h.tau * iss : INF;
+        } else {
+            // FP64: the same divisions as the oracle (bit-identical geometry)
+            dxf = h.ox > T(0) ? (DX - h.fx) / h.ox : (h.ox < T(0) ? h.fx / (-h.ox) : INF);
+            dyf = h.oy > T(0) ? (DY - h.fy) / h.oy : (h.oy < T(0) ? h.fy / (-h.oy) : INF);
+            dcol = (h.n < Ns && ss > T(0)) ? h.tau / ss : INF;
+        }
         T l;
         int ev;
         bool xc = false, yc = false;
@@ -185,18 +278,21 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
         } else { l = h.srem; ev = 2; }
 
         if (h.n < Ns) {
-            const T att = -P::exm1(-sa * l);
-            t.c[8] += P::add(&a.pre[k], sa > T(0) ? h.w * att / sa : h.w * l, sc_t);
-            if constexpr (kF32) t.f[1] += fix_w(h.w * att, scw, scw_f);
-            else d_abs += (double)(h.w * att);
-            h.w = h.w * P::ex(-sa * l);
+            T att, e;
+            P::att_e(sa * l, &att, &e);
+            const T pre_c = sa > T(0) ? (kF32 ? h.w * att * isa : h.w * att / sa) : h.w * l;
+            t.c[8] += P::add(&a.pre[k], pre_c, sc_t);
+            d_abs += (wacc_t)(h.w * att);
+            h.w = h.w * e;
             h.tau = P::msub(h.tau, ss, l);
         } else {
-            const T att = -P::exm1(-st * l);
-            t.c[8] += P::add(&a.post[k], st > T(0) ? h.w * att / st : h.w * l, sc_t);
+            T att, e;
+            P::att_e(st * l, &att, &e);
+            const T post_c = st > T(0) ? (kF32 ? h.w * att * ist : h.w * att / st) : h.w * l;
+            t.c[8] += P::add(&a.post[k], post_c, sc_t);
             if (ss > T(0)) {
                 T g0, g1, g2;
-                gfun<T>(st * l, &g0, &g1, &g2);
+                gfun<T>(st * l, e, att, &g0, &g1, &g2);
                 const T I0 = l * g0, I1 = l * l * g1, I2 = l * l * l * g2;
                 const T sw = ss * h.w;
                 t.c[8] += P::add(&a.mom[4 * k + 0], sw * I0, sc_m);
@@ -212,15 +308,10 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
                 }
             }
             if (st > T(0)) {
-                if constexpr (kF32) {
-                    t.f[4] += fix_w(h.w * att * (ss / st), scw, scw_f);
-                    t.f[1] += fix_w(h.w * att * (sa / st), scw, scw_f);
-                } else {
-                    d_hand += (double)(h.w * att * (ss / st));
-                    d_abs += (double)(h.w * att * (sa / st));
-                }
+                d_hand += (wacc_t)(h.w * att * (kF32 ? ss * ist : ss / st));
+                d_abs += (wacc_t)(h.w * att * (kF32 ? sa * ist : sa / st));
             }
-            h.w = h.w * P::ex(-st * l);
+            h.w = h.w * e;
         }
         h.fx = P::madd(h.ox, l, h.fx);
         h.fy = P::madd(h.oy, l, h.fy);
@@ -245,6 +336,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
             ++h.n; ++t.c[2];
             const int base = 5 + 3 * (h.n - 1);
             iso_dir<T>(pts(h.idx, base + 1), pts(h.idx, base + 2), &h.ox, &h.oy);
+            if constexpr (kF32) { h.rox = P::rcp(h.ox); h.roy = P::rcp(h.oy); }
             if (h.n < Ns) h.tau = P::neglog(P::unit(pts(h.idx, 5 + 3 * h.n)));
             else { h.tau = T(0); ++t.c[6]; }
         }
@@ -257,11 +349,9 @@ __device__ void leg_warp_range(const LegArgs<T>& a, long long next, long long la
             else if (fate == kFateLeaked) { ++t.c[3]; t.f[2] += fw; }
             else if (fate == kFateKilled) { ++t.c[5]; t.f[5] += fw; }
             else { ++t.c[7]; t.status |= kStSegments; }
-            if constexpr (!kF32) {
-                t.f[1] += __double2ll_rn(d_abs * scw);
-                t.f[4] += __double2ll_rn(d_hand * scw);
-            }
-            t.c[1] += (unsigned long long)h.seg;
+            t.f[1] += fix_w(d_abs, scw, scw_f);
+            t.f[4] += fix_w(d_hand, scw, scw_f);
+            t.c[1] += (unsigned int)h.seg;
             if (a.hist) {
                 const int4 r = make_int4(h.iy * nx + h.ix, fate, h.n, h.seg);
                 reinterpret_cast<int4*>(a.hist)[h.j] = r;
@@ -277,7 +367,7 @@ __device__ void leg_flush(DevState* st, LegTally& t, const LegScales& sc, bool w
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     unsigned long long cs[15];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) cs[q] = t.c[q];
+    for (int q = 0; q < 9; ++q) cs[q] = (unsigned long long)t.c[q];
 #pragma unroll
     for (int q = 0; q < 6; ++q) cs[9 + q] = (unsigned long long)t.f[q];
 #pragma unroll
@@ -331,12 +421,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
     const LegScales sc = leg_scales<T>(a);
     LegTally t;
     leg_tally_zero(t);
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long per = (N + nwarps - 1) / nwarps;
-    const long long j0 = wid * per;
-    const long long j1 = j0 + per < N ? j0 + per : N;
-    leg_warp_range<T>(a, j0, j1, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+    leg_warp_range<T>(a, CounterChunks{&a.st->leg_next, N}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
     leg_flush(a.st, t, sc, blockIdx.x == 0);
 }
 
@@ -345,7 +430,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
 struct LegChunk { int p; int pad; long long j0, j1; };
 
 template <typename T>
-__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kTile, 2)
 mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restrict__ chunks, int nchunks,
                     int* head, const uint32_t* V, int ntab_max) {
     extern __shared__ uint32_t sm[];
@@ -353,6 +438,9 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
     uint32_t* sShC = sm + ntab_max * kNibbleWords;
     uint32_t* sShS = sShC + ntab_max;
     __shared__ int s_chunk;
+    // the chunk's problem descriptor lives in shared memory (read on use, not held in registers)
+    __shared__ __align__(16) unsigned int s_args[(sizeof(LegArgs<T>) + 3) / 4];
+    __shared__ unsigned long long s_next;   // warps take kWarpChunk histories of the chunk at a time
     build_nibble_tables(V, ntab_max, sV);
     for (;;) {
         __syncthreads();
@@ -361,7 +449,11 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
         const int c = s_chunk;
         if (c >= nchunks) break;
         const LegChunk ch = chunks[c];
-        const LegArgs<T> a = args[ch.p];
+        const unsigned int* src = reinterpret_cast<const unsigned int*>(args + ch.p);
+        for (int i = threadIdx.x; i < (int)(sizeof(LegArgs<T>) / 4); i += blockDim.x) s_args[i] = src[i];
+        if (threadIdx.x == 0) s_next = (unsigned long long)ch.j0;
+        __syncthreads();
+        const LegArgs<T>& a = *reinterpret_cast<const LegArgs<T>*>(s_args);
         const uint64_t step = (uint64_t)a.st->step;
         const uint64_t key_c = dstream_key(a.seed, step, HYB_STREAM_LEG_CENSUS);
         const uint64_t key_s = dstream_key(a.seed, step, HYB_STREAM_LEG_SOURCE);
@@ -376,14 +468,70 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
         const LegScales sc = leg_scales<T>(a);
         LegTally t;
         leg_tally_zero(t);
-        if (ch.j0 < e) {
-            const long long nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-            const long long per = (e - ch.j0 + nw - 1) / nw;
-            const long long j0 = ch.j0 + w * per;
-            const long long j1 = j0 + per < e ? j0 + per : e;
-            leg_warp_range<T>(a, j0, j1, nb, sV, sShC, sShS, key_c, key_s, sc, t);
-        }
+        if (ch.j0 < e) leg_warp_range<T>(a, CounterChunks{&s_next, e}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
         leg_flush(a.st, t, sc, ch.j0 == 0);
+    }
+}
+
+// Source births of one problem, [i0, i1) of its birth indices, into its birth staging arrays.
+template <typename T>
+__device__ __forceinline__ void births_range(const LegArgs<T>& a, const Points& pts, long long i0, long long i1,
+                                             long long stride) {
+    for (long long i = i0; i < i1; i += stride) {
+        int ix, iy;
+        T fx, fy, ox, oy, srem, tau;
+        birth_state<T>(a, pts, (uint32_t)i, &ix, &iy, &fx, &fy, &ox, &oy, &srem, &tau);
+        a.births.cell[i] = iy * a.nx + ix;
+        a.births.fx[i] = fx; a.births.fy[i] = fy;
+        a.births.ox[i] = ox; a.births.oy[i] = oy;
+        a.births.srem[i] = srem; a.births.tau[i] = tau;
+    }
+}
+
+// The births of a leg, one per thread: every lane does the same work (no divergence between
+// births and bank pick-ups, no refill), and the leg then reads them like bank particles.
+template <typename T>
+__global__ void __launch_bounds__(kTile) mc_birth_kernel(LegArgs<T> a) {
+    __shared__ uint32_t sV[6 * kNibbleWords];
+    __shared__ uint32_t sSh[6];
+    const int nt = a.ntab < 6 ? a.ntab : 6;
+    const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_LEG_SOURCE);
+    build_nibble_tables(a.V, nt, sV);
+    if (threadIdx.x < nt) sSh[threadIdx.x] = dshift(key, (uint64_t)threadIdx.x);
+    __syncthreads();
+    const Points pts{sV, sSh, key, a.sampler, nt};
+    births_range<T>(a, pts, (long long)blockIdx.x * blockDim.x + threadIdx.x, a.n_src,
+                    (long long)gridDim.x * blockDim.x);
+}
+
+// The births of many problems: CTAs pull (problem, [i0, i1)) chunks from a queue.
+template <typename T>
+__global__ void __launch_bounds__(kTile)
+mc_birth_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restrict__ chunks, int nchunks,
+                      int* head) {
+    __shared__ uint32_t sV[6 * kNibbleWords];
+    __shared__ uint32_t sSh[6];
+    __shared__ int s_chunk;
+    bool have_tables = false;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_chunk = atomicAdd(head, 1);
+        __syncthreads();
+        const int c = s_chunk;
+        if (c >= nchunks) break;
+        const LegChunk ch = chunks[c];
+        const LegArgs<T> a = args[ch.p];
+        const int nt = a.ntab < 6 ? a.ntab : 6;
+        const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_LEG_SOURCE);
+        if (!have_tables) {           // the direction numbers are the same for every problem
+            build_nibble_tables(a.V, 6, sV);
+            have_tables = true;
+        }
+        if (threadIdx.x < nt) sSh[threadIdx.x] = dshift(key, (uint64_t)threadIdx.x);
+        __syncthreads();
+        const Points pts{sV, sSh, key, a.sampler, nt};
+        const long long e = ch.j1 < a.n_src ? ch.j1 : a.n_src;
+        births_range<T>(a, pts, ch.j0 + threadIdx.x, e, blockDim.x);
     }
 }
 
@@ -484,9 +632,26 @@ __global__ void points_kernel(uint64_t key, int sampler, const uint32_t* V, long
 // ---------------------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------------------
-static int leg_grid(long long work) {
+// grid of the grid-stride kernels: up to 8 CTAs of kTile threads per SM
+static int stride_grid(long long work) {
     long long g = (work + kTile - 1) / kTile;
     const long long cap = 152LL * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// resident CTAs of kTile threads per SM: the single-problem leg keeps its descriptor in constant
+// memory and fits 3 (FP32); the batched leg holds a chunk's descriptor in registers and runs 2
+static int leg_ctas_per_sm(int prec) { return prec == HYB_FP64 ? 2 : 3; }
+
+// persistent grid: every CTA resident at once (warps then take history chunks from the counter)
+static int leg_grid(long long work, int prec) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long g = (work + kTile - 1) / kTile;
+    const long long cap = (long long)sms * leg_ctas_per_sm(prec);
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (int)g;
@@ -500,12 +665,14 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.cdt = (T)(p->d.c * p->d.dt);
     a.cdt_d = p->d.c * p->d.dt;
     a.sig = (const T*)p->sig;
+    a.sig_inv = (const float4*)p->sig_inv;
     a.n_s = p->d.n_s; a.sampler = p->d.sampler; a.handoff_full = p->d.handoff_full;
     a.ntab = p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS;
     a.w_min = (T)p->d.w_min;
     a.V = p->sobolV;
     a.seed = p->d.seed;
     a.bank = bank_view<T>(p, cur);
+    a.births = birth_view<T>(p);
     a.cdf = p->src_cdf;
     a.n_src = p->has_src ? p->d.n_hist : 0;
     a.w0 = (T)(p->has_src ? p->w_src / (double)p->d.n_hist : 0.0);
@@ -524,7 +691,11 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
     const LegArgs<T> a = leg_args<T>(p, hist, p->cur);
     const size_t smem = (size_t)(a.ntab * kNibbleWords + 2 * a.ntab) * sizeof(uint32_t);
     const long long work = p->bank_cap + a.n_src;
-    mc_leg_kernel<T><<<leg_grid(work), kTile, smem, p->stream>>>(a);
+    if (a.n_src > 0) {
+        const long long g = (a.n_src + kTile - 1) / kTile;
+        mc_birth_kernel<T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kTile, 0, p->stream>>>(a);
+    }
+    mc_leg_kernel<T><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
     return cudaGetLastError();
 }
 
@@ -537,11 +708,21 @@ void leg_args_host(hyb_problem* p, int cur, void* out) {
 
 int leg_ntab(const hyb_problem* p) { return p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS; }
 
-int leg_batch_ctas_per_sm(int prec) { return prec == HYB_FP64 ? 2 : 3; }
+int leg_batch_ctas_per_sm(int) { return 2; }
 
 cudaError_t launch_mc_leg_batch(int prec, const void* d_args, const void* d_chunks, int nchunks, int* d_head,
-                                const uint32_t* V, int ntab_max, int grid, int block, cudaStream_t s) {
+                                const uint32_t* V, int ntab_max, int grid, int block, cudaStream_t s,
+                                const void* d_bchunks, int nbchunks, int* d_bhead) {
     const size_t smem = (size_t)(ntab_max * kNibbleWords + 2 * ntab_max) * sizeof(uint32_t);
+    if (nbchunks > 0) {
+        const int bg = grid < nbchunks ? grid : nbchunks;
+        if (prec == HYB_FP64)
+            mc_birth_batch_kernel<double><<<bg, kTile, 0, s>>>((const LegArgs<double>*)d_args,
+                                                               (const LegChunk*)d_bchunks, nbchunks, d_bhead);
+        else
+            mc_birth_batch_kernel<float><<<bg, kTile, 0, s>>>((const LegArgs<float>*)d_args,
+                                                              (const LegChunk*)d_bchunks, nbchunks, d_bhead);
+    }
     if (prec == HYB_FP64)
         mc_leg_batch_kernel<double><<<grid, block, smem, s>>>((const LegArgs<double>*)d_args,
                                                              (const LegChunk*)d_chunks, nchunks, d_head, V, ntab_max);
@@ -574,7 +755,7 @@ cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0) {
     const uint64_t key = stream_key(p->d.seed, 0, HYB_STREAM_INIT);
     const int ntab = p->d.sampler == HYB_SOBOL_DS ? 5 : 0;
     const long long n = p->d.n_hist;
-    const int g = leg_grid(n);
+    const int g = stride_grid(n);
     if (p->prec == HYB_FP64)
         init_bank_kernel<double><<<g, kTile, 0, p->stream>>>(bank_view<double>(p, p->cur), cdf, p->nx, p->ny, p->dx,
                                                              p->dy, n, w0, p->sobolV, ntab, p->d.sampler, key);
@@ -590,7 +771,7 @@ cudaError_t launch_bank_stats(hyb_problem* p) {
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(&p->st->bank_wsum_acc, 0, sizeof(Acc128), p->stream);
     if (e != cudaSuccess) return e;
-    const int g = leg_grid(p->bank_cap);
+    const int g = stride_grid(p->bank_cap);
     if (p->prec == HYB_FP64) {
         BankView<double> b = bank_view<double>(p, p->cur);
         bank_wmax_kernel<double><<<g, kTile, 0, p->stream>>>(b.w, p->st);
@@ -608,7 +789,7 @@ cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t 
                           uint32_t* out, cudaStream_t s) {
     const int ntab = ndims < HYB_SOBOL_DIMS ? ndims : HYB_SOBOL_DIMS;
     const size_t smem = (size_t)(ntab * kNibbleWords + ntab) * sizeof(uint32_t);
-    points_kernel<<<leg_grid(n), kTile, smem, s>>>(key, sampler, V, i0, n, ndims, out);
+    points_kernel<<<stride_grid(n), kTile, smem, s>>>(key, sampler, V, i0, n, ndims, out);
     return cudaGetLastError();
 }
 

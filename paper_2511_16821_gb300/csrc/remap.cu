@@ -245,6 +245,9 @@ struct RemapArgs {
     uint64_t seed;             // keys of the birth and comb point sets come from (seed, step)
     DevState* st;
     long long* blk;            // per block: alive count, sum q, sum|w| lo, sum|w| hi
+    const uint32_t* perm;      // census in cell order: slot of every sorted position (else null)
+    long long nslots;          // staging slots (bank capacity + n_hist); the sort covers all of them
+    int perm_slots;            // 1: the census is sorted by cell after the count pass
 };
 
 template <typename T>
@@ -280,7 +283,7 @@ template <> struct RemapSums<float> {
     long long v[4] = {0, 0, 0, 0};
     float sc = 1.f;
     __device__ void init(int kf) { sc = pow2f(kf); }
-    __device__ void add(int i, float x) { v[i] += __float2ll_rn(x * sc); }
+    __device__ void add(int i, float x) { v[i] += f2ll_rn(x * sc); }
 };
 enum { kRsSrc = 0, kRsAbs = 1, kRsLeak = 2, kRsKill = 3 };
 
@@ -327,6 +330,9 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
     sums.add(kRsSrc, w);
     const T w0 = w;
     const T INF = (T)INFINITY;
+    constexpr bool kF32 = sizeof(T) == 4;
+    // FP32: face distances from the flight's reciprocals (FP64: divisions, as the oracle)
+    const T rox = kF32 ? P::rcp(ox) : T(0), roy = kF32 ? P::rcp(oy) : T(0);
     Particle<T> r;
     r.alive = false;
     r.cell = iy * a.nx + ix;
@@ -335,14 +341,22 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
         ++s;
         const int k = iy * a.nx + ix;
         const T st = a.sig[2 * k] + a.sig[2 * k + 1];
-        const T dxf = ox > T(0) ? (a.dx - fx) / ox : (ox < T(0) ? fx / (-ox) : INF);
-        const T dyf = oy > T(0) ? (a.dy - fy) / oy : (oy < T(0) ? fy / (-oy) : INF);
+        T dxf, dyf;
+        if constexpr (kF32) {
+            dxf = ox > T(0) ? (a.dx - fx) * rox : (ox < T(0) ? fx * (-rox) : INF);
+            dyf = oy > T(0) ? (a.dy - fy) * roy : (oy < T(0) ? fy * (-roy) : INF);
+        } else {
+            dxf = ox > T(0) ? (a.dx - fx) / ox : (ox < T(0) ? fx / (-ox) : INF);
+            dyf = oy > T(0) ? (a.dy - fy) / oy : (oy < T(0) ? fy / (-oy) : INF);
+        }
         T l;
         bool face = false, xc = false, yc = false;
         if (dxf <= srem || dyf <= srem) { l = dxf < dyf ? dxf : dyf; face = true; xc = dxf == l; yc = dyf == l; }
         else l = srem;
-        sums.add(kRsAbs, w * (-P::exm1(-st * l)));
-        w = w * P::ex(-st * l);
+        T att, e;
+        P::att_e(st * l, &att, &e);
+        sums.add(kRsAbs, w * att);
+        w = w * e;
         fx = P::madd(ox, l, fx);
         fy = P::madd(oy, l, fy);
         srem = srem - l;
@@ -366,7 +380,7 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
 
 // comb quantisation rint(|w| / w_ref 2^32) with w_ref a power of two: the FP32 path multiplies by
 // the exact float 2^(32 - log2 w_ref) (same integer as the FP64 quotient), the FP64 path divides
-__device__ __forceinline__ long long quant_w(float w, double, float qsc) { return __float2ll_rn(fabsf(w) * qsc); }
+__device__ __forceinline__ long long quant_w(float w, double, float qsc) { return f2ll_rn(fabsf(w) * qsc); }
 __device__ __forceinline__ long long quant_w(double w, double w_ref, float) {
     return __double2ll_rn((fabs(w) / w_ref) * 0x1p32);
 }
@@ -413,14 +427,17 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     const long long base = (long long)blockIdx.x * kSlotsPerBlock;
     for (int r = 0; r < kRounds; ++r) {
         const long long j = base + r * kTile + threadIdx.x;
-        if (j >= N) break;
+        if (j >= N) {
+            if (a.perm_slots && j < a.nslots) a.stg.cell[j] = -1;   // unused slots sort last, as dead
+            continue;
+        }
         const Particle<T> pr = remap_slot<T>(a, pts, j, nb, (T)wbar, sums, &leaked, &killed, &segs, &err);
         a.stg.cell[j] = pr.alive ? pr.cell : -1;
         a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
         if (pr.alive) {
             ++cnt;
             qs += quant<T>(pr.w, w_ref, qsc);
-            if constexpr (kF32) wsf += __float2ll_rn(fabsf(pr.w) * sca);
+            if constexpr (kF32) wsf += f2ll_rn(fabsf(pr.w) * sca);
             else ws += fabs((double)pr.w);
         }
     }
@@ -496,6 +513,62 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     }
 }
 
+// Census in cell order: the per-block partials (alive count, quantised |w| sum, fixed-point |w|
+// sum) of the sorted positions, replacing the slot-order partials of the count pass (the totals
+// are the same integers in any order).
+template <typename T>
+__global__ void __launch_bounds__(kTile) remap_partials_kernel(RemapArgs<T> a) {
+    const long long nb = a.st->n_bank;
+    const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
+    const long long N = nb + nbirth;
+    const double w_ref = a.st->w_ref;
+    const float qsc = quant_scale(w_ref);
+    const int krw = scale_exponent((double)(N > 0 ? N : 1) * w_ref, 125);
+    const int kfa = min(krw - 64, 126);
+    const float sca = pow2f(kfa);
+    constexpr bool kF32 = sizeof(T) == 4;
+    long long cnt = 0, qs = 0, wsf = 0;
+    double ws = 0;
+    const long long base = (long long)blockIdx.x * kSlotsPerBlock;
+    for (int r = 0; r < kRounds; ++r) {
+        const long long j = base + r * kTile + threadIdx.x;
+        if (j >= N) break;
+        const long long js = (long long)a.perm[j];
+        if (a.stg.cell[js] < 0) continue;
+        const T w = a.stg.w[js];
+        ++cnt;
+        qs += quant<T>(w, w_ref, qsc);
+        if constexpr (kF32) wsf += f2ll_rn(fabsf(w) * sca);
+        else ws += fabs((double)w);
+    }
+    __shared__ long long s_l[kTile / 32][3];
+    __shared__ double s_d[kTile / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        qs += __shfl_down_sync(0xffffffffu, qs, o);
+        wsf += __shfl_down_sync(0xffffffffu, wsf, o);
+    }
+    if constexpr (!kF32) ws = warp_sum(ws);
+    if (lane == 0) { s_l[wid][0] = cnt; s_l[wid][1] = qs; s_l[wid][2] = wsf; s_d[wid] = ws; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long c = 0, q = 0, af = 0;
+        double d = 0;
+        for (int ww = 0; ww < kTile / 32; ++ww) { c += s_l[ww][0]; q += s_l[ww][1]; af += s_l[ww][2]; d += s_d[ww]; }
+        unsigned long long lo, hi;
+        if constexpr (kF32) {
+            const int sh = krw - kfa - 64;
+            lo = 0ull;
+            hi = sh < 63 ? (unsigned long long)af << sh : 0ull;
+        } else {
+            to_i128(d * ldexp(1.0, krw), &lo, &hi);
+        }
+        long long* b = a.blk + 4 * (size_t)blockIdx.x;
+        b[0] = c; b[1] = q; b[2] = (long long)lo; b[3] = (long long)hi;
+    }
+}
+
 // one block: exclusive scan of block counts and quantised sums; totals, comb decision
 __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long long cap, uint64_t seed, int sampler,
                                   long long n_hist) {
@@ -559,9 +632,9 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
 // float estimate (relative error below 2^-21) is refined once from the exact 128-bit remainder
 // (leaving an error of at most one) and finished by exact integer steps.
 __device__ __forceinline__ long long ceil_div(unsigned long long hi, unsigned long long lo, unsigned long long T) {
-    const float fT = __ull2float_rn(T);
-    const float fN = fmaf(__ull2float_rn(hi), 0x1p64f, __ull2float_rn(lo));
-    long long q = (long long)(fN / fT);
+    const float fT = u64_to_f(T);
+    const float fN = fmaf(u64_to_f(hi), 0x1p64f, u64_to_f(lo));
+    long long q = f2ll_rn(fN / fT);
     if (q < 0) q = 0;
     {
         const unsigned long long plo = (unsigned long long)q * T, phi = __umul64hi((unsigned long long)q, T);
@@ -572,8 +645,8 @@ __device__ __forceinline__ long long ceil_div(unsigned long long hi, unsigned lo
             rlo = ~rlo + 1ull;
             rhi = ~rhi + (rlo == 0ull ? 1ull : 0ull);
         }
-        const float fr = fmaf(__ull2float_rn(rhi), 0x1p64f, __ull2float_rn(rlo));
-        const long long dq = (long long)rintf(fr / fT);
+        const float fr = fmaf(u64_to_f(rhi), 0x1p64f, u64_to_f(rlo));
+        const long long dq = f2ll_rn(fr / fT);
         q = neg ? q - dq : q + dq;
         if (q < 0) q = 0;
     }
@@ -622,13 +695,14 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
         Particle<T> pr;
         pr.alive = false;
         if (j < N) {
-            pr.cell = a.stg.cell[j];
+            const long long js = a.perm ? (long long)a.perm[j] : j;
+            pr.cell = a.stg.cell[js];
             pr.alive = pr.cell >= 0;
-            pr.fx = a.stg.fx[j]; pr.fy = a.stg.fy[j]; pr.ox = a.stg.ox[j]; pr.oy = a.stg.oy[j]; pr.w = a.stg.w[j];
+            pr.fx = a.stg.fx[js]; pr.fy = a.stg.fy[js]; pr.ox = a.stg.ox[js]; pr.oy = a.stg.oy[js]; pr.w = a.stg.w[js];
         }
         long long c = pr.alive ? 1 : 0;
         long long q = pr.alive ? quant<T>(pr.w, w_ref, qsc) : 0;
-        // block exclusive scan of (c, q) in slot order
+        // block exclusive scan of (c, q) in census order
         long long ic = c, iq = q;
         for (int off = 1; off < 32; off <<= 1) {
             const long long vc = __shfl_up_sync(0xffffffffu, ic, off), vq = __shfl_up_sync(0xffffffffu, iq, off);
@@ -718,7 +792,20 @@ static cudaError_t remap_t(hyb_problem* p) {
     e = cudaMemsetAsync(&p->st->r_histories, 0,
                         (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
     if (e != cudaSuccess) return e;
+    a.perm = nullptr;
+    a.nslots = maxN;
+    a.perm_slots = p->d.census_order == 1 ? 1 : 0;
     remap_count_kernel<T><<<nblk, kTile, smem, s>>>(a);
+    if (p->d.census_order == 1) {
+        // survivors in cell order (stable): the comb and the census write then follow that order
+        const uint32_t* sorted_keys = nullptr;
+        uint32_t* const keys[2] = {p->sort_keys[0], p->sort_keys[1]};
+        uint32_t* const vals[2] = {p->sort_vals[0], p->sort_vals[1]};
+        e = launch_census_sort(a.stg.cell, maxN, (uint32_t)p->ncells, keys, vals, p->sort_counts, s, &a.perm,
+                               &sorted_keys);
+        if (e != cudaSuccess) return e;
+        remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);
+    }
     remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nblk, p->st, a.cap, a.seed, a.sampler, p->d.n_hist);
     remap_write_kernel<T><<<nblk, kTile, 0, s>>>(a);
     remap_finish_kernel<<<1, 1, 0, s>>>(p->st);

@@ -88,6 +88,14 @@ __device__ __forceinline__ void store_cell(double* d, double a0, double a1, doub
 template <typename T> struct Ring;
 template <> struct Ring<float> {
     static constexpr int kWords = 2;
+    static __device__ __forceinline__ void load(const volatile unsigned long long* e, unsigned long long* w) {
+        w[0] = e[0]; w[1] = e[1];
+    }
+    static __device__ __forceinline__ bool decode(const unsigned long long* w, uint32_t tag, float* v0, float* v1) {
+        *v0 = __uint_as_float((uint32_t)w[0]);
+        *v1 = __uint_as_float((uint32_t)w[1]);
+        return (uint32_t)(w[0] >> 32) == tag && (uint32_t)(w[1] >> 32) == tag;
+    }
     static __device__ __forceinline__ void put(volatile unsigned long long* e, float v0, float v1, uint32_t tag) {
         const unsigned long long hi = (unsigned long long)tag << 32;
         e[0] = hi | __float_as_uint(v0);
@@ -103,6 +111,15 @@ template <> struct Ring<float> {
 };
 template <> struct Ring<double> {
     static constexpr int kWords = 4;
+    static __device__ __forceinline__ void load(const volatile unsigned long long* e, unsigned long long* w) {
+        w[0] = e[0]; w[1] = e[1]; w[2] = e[2]; w[3] = e[3];
+    }
+    static __device__ __forceinline__ bool decode(const unsigned long long* w, uint32_t tag, double* v0, double* v1) {
+        *v0 = __hiloint2double((int)(uint32_t)w[1], (int)(uint32_t)w[0]);
+        *v1 = __hiloint2double((int)(uint32_t)w[3], (int)(uint32_t)w[2]);
+        return (uint32_t)(w[0] >> 32) == tag && (uint32_t)(w[1] >> 32) == tag && (uint32_t)(w[2] >> 32) == tag &&
+               (uint32_t)(w[3] >> 32) == tag;
+    }
     static __device__ __forceinline__ void put(volatile unsigned long long* e, double v0, double v1, uint32_t tag) {
         const unsigned long long hi = (unsigned long long)tag << 32;
         e[0] = hi | (uint32_t)__double2loint(v0);
@@ -220,6 +237,12 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
             const int col = i - lane;
             if (row_ok && col >= 0 && col < nx) load_cell<T>(a.src, a.sgA, rowk + (sx > 0 ? col : nx - 1 - col), q[i]);
         }
+        // incoming ring entries are read two steps ahead (the writer runs ~32 steps ahead, so the
+        // entry is nearly always there; a tag mismatch falls back to waiting on the entry)
+        unsigned long long rr[2][RW];
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+            if (has_in && i < nx) Ring<T>::load(rin + (size_t)i * RW, rr[i]);
         for (int t0 = 0; t0 < nsteps; t0 += PF) {
             // a reused slot: the previous reader must have taken the columns this block writes
             if (reuse && has_out && s >= W) {
@@ -239,15 +262,17 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
                 const T u1 = __shfl_up_sync(0xffffffffu, oy1, 1);
                 T by0 = u0, by1 = u1;
                 if (has_in && t < nx) {
-                    // every lane reads lane 0's entry (one broadcast), so the wait is uniform
+                    // every lane holds lane 0's entry (one broadcast read), so the wait is uniform
                     T r0, r1;
                     const uint32_t tag = (uint32_t)(qin + t + 1);
                     int spins = 0;
-                    while (!Ring<T>::get(rin + (size_t)t * RW, tag, &r0, &r1) && !timed_out) {
+                    while (!Ring<T>::decode(rr[i & 1], tag, &r0, &r1) && !timed_out) {
                         if (++spins > (1 << 22)) timed_out = true;
                         __nanosleep(20);
+                        Ring<T>::load(rin + (size_t)t * RW, rr[i & 1]);
                     }
                     if (lane == 0) { by0 = r0; by1 = r1; }
+                    if (t + 2 < nx) Ring<T>::load(rin + (size_t)(t + 2) * RW, rr[i & 1]);
                 } else if (lane == 0) {
                     by0 = 0; by1 = 0;
                 }

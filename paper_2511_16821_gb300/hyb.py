@@ -37,7 +37,7 @@ class Desc(C.Structure):
                 ("n_hist", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int32),
                 ("sn_order", C.c_int32), ("handoff_full", C.c_int32), ("sn_max_iter", C.c_int32),
                 ("sn_tol", C.c_double), ("w_min", C.c_double), ("census_cap", C.c_int64),
-                ("sn_warm_start", C.c_int32), ("pad0", C.c_int32)]
+                ("sn_warm_start", C.c_int32), ("census_order", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -96,6 +96,7 @@ def lib():
         L.hyb_cdf_scratch_bytes.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]
         L.hyb_batch_create.argtypes = [C.POINTER(P), C.c_int32, P, C.POINTER(P)]
         L.hyb_batch_set_tuning.argtypes = [P, C.POINTER(Tuning)]
+        L.hyb_batch_set_problems.argtypes = [P, C.POINTER(P), C.c_int32]
         L.hyb_batch_step.argtypes = [P, C.c_int32, C.POINTER(Stats)]
         L.hyb_batch_destroy.argtypes = [P]
         L.hyb_batch_last_error.restype = C.c_char_p
@@ -139,7 +140,7 @@ def make_desc(spec: ProblemSpec) -> tuple[Desc, list]:
              n_s=spec.n_s, sampler=spec.sampler, n_hist=spec.n_hist, seed=spec.seed,
              precision=spec.precision, sn_order=spec.sn_order, handoff_full=spec.handoff_full,
              sn_max_iter=spec.sn_max_iter, sn_tol=spec.sn_tol, w_min=spec.w_min,
-             census_cap=spec.census_cap, sn_warm_start=spec.sn_warm_start, pad0=0)
+             census_cap=spec.census_cap, sn_warm_start=spec.sn_warm_start, census_order=spec.census_order)
     return d, keep
 
 
@@ -340,6 +341,12 @@ class Batch:
         t = Tuning(block=block, chunk=chunk, ctas_per_sm=ctas_per_sm, streams=streams, use_graph=int(use_graph), pad=0)
         self._check(lib().hyb_batch_set_tuning(self.h, C.byref(t)))
         self.tuning = dict(block=block, chunk=chunk, ctas_per_sm=ctas_per_sm, streams=streams, use_graph=int(use_graph))
+
+    def set_problems(self, problems: list) -> None:
+        """Replace the resident problems, keeping streams, events and device buffers."""
+        self.problems = list(problems)
+        arr = (C.c_void_p * len(self.problems))(*[p.h.value for p in self.problems])
+        self._check(lib().hyb_batch_set_problems(self.h, arr, len(self.problems)))
 
     def step(self, n: int = 1, stats: bool = True):
         arr = (Stats * len(self.problems))()

@@ -107,9 +107,11 @@ class Server:
             return 0
         members = tuple(r.rid for r in self.active)
         if members != self.members:
-            if self.batch is not None:
-                self.batch.close()
-            self.batch = hyb.Batch([r.problem for r in self.active], stream=self.stream, tuning=self.tuning)
+            # the resident set changed: the batch keeps its streams and buffers, takes the new set
+            if self.batch is None:
+                self.batch = hyb.Batch([r.problem for r in self.active], stream=self.stream, tuning=self.tuning)
+            else:
+                self.batch.set_problems([r.problem for r in self.active])
             self.members = members
             self.rebuilds += 1
         stats = self.batch.step(1)
@@ -122,10 +124,6 @@ class Server:
         self.ticks += 1
         n = len(self.active)
         self._retire()
-        if self.batch is not None and tuple(r.rid for r in self.active) != self.members:
-            self.batch.close()
-            self.batch = None
-            self.members = ()
         return n
 
     # ---- drivers ----------------------------------------------------------------------------

@@ -51,6 +51,7 @@ class ProblemSpec:
     sn_tol: float = 1e-10
     sn_max_iter: int = 500
     sn_warm_start: int = 0
+    census_order: int = 0
     name: str = field(default="problem")
 
     @property

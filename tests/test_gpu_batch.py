@@ -16,11 +16,11 @@ def _problems(n, seed, **kw):
             for p in range(n)]
 
 
-@pytest.mark.parametrize("prec", [W.FP32, W.FP64])
-def test_batch_equals_alone(prec):
+@pytest.mark.parametrize("prec,order", [(W.FP32, 0), (W.FP64, 0), (W.FP32, 1)])
+def test_batch_equals_alone(prec, order):
     import torch
     from paper_2511_16821_gb300 import hyb
-    specs = _problems(6, 3, precision=prec)
+    specs = [sp.with_(census_order=order) for sp in _problems(6, 3, precision=prec)]
     alone = []
     for sp in specs:
         P = hyb.Problem(sp)

@@ -273,9 +273,11 @@ def test_collided_solve_tall_mesh(H, orc, prec):
         assert np.allclose(phi_g, phi_o, rtol=1e-4, atol=1e-5 * scale)
 
 
-@pytest.mark.parametrize("cap", [0, 10 ** 7])
-def test_remap_parity(H, orc, cap):
-    spec = W.checkerboard(n_s=2, n_hist=20_000, cells_per_block=4).with_(census_cap=cap)
+@pytest.mark.parametrize("cap,order", [(0, 0), (10 ** 7, 0), (0, 1), (10 ** 7, 1), (9000, 1)])
+def test_remap_parity(H, orc, cap, order):
+    """The remap's census against the oracle: comb or not, slot order or cell order (a stable
+    sort by cell before the comb), element by element."""
+    spec = W.checkerboard(n_s=2, n_hist=20_000, cells_per_block=4).with_(census_cap=cap, census_order=order)
     bank = W.random_bank(spec, 15_000, seed=8)
     o = orc.mc_leg(spec, 2, bank)
     phi_o, _ = orc.sn_solve(spec, o["mom"])
@@ -298,9 +300,9 @@ def test_remap_parity(H, orc, cap):
     assert math.isclose(rs["w_source"], ost["w_source"], rel_tol=1e-10)
 
 
-@pytest.mark.parametrize("prec", [W.FP64, W.FP32])
-def test_multistep_hybrid(H, orc, prec):
-    spec = W.pulse(n_hist=8192).with_(precision=prec, sn_tol=1e-12 if prec == W.FP64 else 1e-7)
+@pytest.mark.parametrize("prec,order", [(W.FP64, 0), (W.FP32, 0), (W.FP64, 1)])
+def test_multistep_hybrid(H, orc, prec, order):
+    spec = W.pulse(n_hist=8192).with_(precision=prec, sn_tol=1e-12 if prec == W.FP64 else 1e-7, census_order=order)
     ospec = spec.with_(precision=W.FP64, sn_tol=1e-12)
     P = H.Problem(spec)
     ob = orc.init_bank(ospec, ospec.ic)
