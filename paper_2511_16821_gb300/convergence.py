@@ -65,6 +65,26 @@ def study(log2_n=range(10, 21), seeds=range(16), steps: int = 4, ref_log2: int =
     return out
 
 
+def ns_sweep(n_s_values=(0, 1, 2, 5, 10, 20, W.NS_INF), log2_n=range(10, 19, 2), seeds=range(8),
+             ref_log2: int = 22, ref_seeds=range(100, 104)) -> list:
+    """The analogue of the paper's Table 1 on the synthetic problem: for each scatter limit N_s,
+    the source iterations of the collided solve (from zero, stop at 1e-6 relative change) and the
+    convergence rates alpha of one step's flux error with Sobol points and with the counter PRNG.
+    N_s = infinity is the pure (Q)MC method (no collided stage)."""
+    import torch
+    rows = []
+    for n_s in n_s_values:
+        with hyb.Problem(problem(1 << 16, 0, W.SOBOL, n_s).with_(sn_warm_start=0)) as p:
+            st = p.step(1)[0]
+        r = study(log2_n=log2_n, seeds=seeds, steps=1, ref_log2=ref_log2, ref_seeds=ref_seeds, n_s=n_s)
+        rows.append({"n_s": "inf" if n_s == W.NS_INF else n_s, "sn_iterations": st["sn_iterations"],
+                     "alpha_sobol": r["sobol"]["alpha"], "alpha_prng": r["prng"]["alpha"],
+                     "err_sobol": r["sobol"]["err"][-1], "err_prng": r["prng"]["err"][-1],
+                     "n_max": r["sobol"]["n"][-1]})
+    torch.cuda.synchronize()
+    return rows
+
+
 if __name__ == "__main__":
     # one step (the MC leg from the source, then the collided solve) and four steps (census
     # particles re-streamed through the remap), at N_s = 0 (5 point dimensions) and N_s = 2 (11),
@@ -73,3 +93,4 @@ if __name__ == "__main__":
         for steps in (1, 4):
             print(json.dumps(study(steps=steps, n_s=n_s)), flush=True)
     print(json.dumps(study(steps=4, n_s=2, census_order=1)), flush=True)
+    print(json.dumps({"ns_sweep": ns_sweep()}), flush=True)

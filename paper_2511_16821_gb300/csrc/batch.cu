@@ -251,6 +251,7 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         hyb_problem* p = problems[i];
         if (!p || p->prec != prec) return bfail(b, HYB_EINVAL, "problems must share one precision");
         if (p->leg_done) return bfail(b, HYB_ESTATE, "problems must be at a step boundary");
+        if (p->d.n_s == HYB_NS_INF) return bfail(b, HYB_EINVAL, "N_s = infinity problems are stepped alone");
         probs.push_back(p);
     }
     if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");

@@ -252,8 +252,8 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.siginv = 4 * nc * 4;
     z.rempos = nc * 4;
     const size_t nslots = (size_t)(z.cap + d->n_hist);
-    z.sortkv = d->census_order == 1 ? nslots * 4 : 0;                    // x4: keys, slots, ping-pong
-    z.sortc = d->census_order == 1 ? 256 * ((nslots + 2047) / 2048) * 4 : 0;
+    z.sortkv = d->census_order == 1 ? nslots * 8 : 0;                    // x2: (cell, slot) pairs, ping-pong
+    z.sortc = d->census_order == 1 ? 256 * ((nslots + 2047) / 2048 + 1) * 4 : 0;
     return z;
 }
 
@@ -264,7 +264,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
-                            z.sortkv, z.sortkv, z.sortkv, z.sortc, z.siginv};
+                            z.sortkv, z.sortc, z.siginv};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -318,8 +318,7 @@ void assign(hyb_problem* p) {
     p->src_cdf.gc = p->rem_cdf.gc = z.gc;
     p->rem_f32 = (float*)take(z.remf32);
     p->rem_pos = (int*)take(z.rempos);
-    for (int i = 0; i < 2; ++i) p->sort_keys[i] = z.sortkv ? (uint32_t*)take(z.sortkv) : nullptr;
-    for (int i = 0; i < 2; ++i) p->sort_vals[i] = z.sortkv ? (uint32_t*)take(z.sortkv) : nullptr;
+    for (int i = 0; i < 2; ++i) p->sort_pairs[i] = z.sortkv ? (unsigned long long*)take(z.sortkv) : nullptr;
     p->sort_counts = z.sortc ? (uint32_t*)take(z.sortc) : nullptr;
     p->sig_inv = (float*)take(z.siginv);
     p->bank_cap = z.cap;
@@ -348,7 +347,7 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (!(d->c > 0) || !std::isfinite(d->c)) { *why = "c must be finite and > 0"; return HYB_EINVAL; }
     if (!(d->dt > 0) || !std::isfinite(d->dt)) { *why = "dt must be finite and > 0"; return HYB_EINVAL; }
     if (d->n_s < 0) { *why = "N_s must be >= 0"; return HYB_EINVAL; }
-    if (d->n_s == HYB_NS_INF) { *why = "N_s = infinity is not supported by this build"; return HYB_EINVAL; }
+    if (d->n_s != HYB_NS_INF && d->n_s > (1 << 20)) { *why = "N_s must be <= 2^20 or HYB_NS_INF"; return HYB_EINVAL; }
     if (d->n_hist < 1 || d->n_hist >= (int64_t)1 << 31) { *why = "n_hist must be in [1, 2^31)"; return HYB_EINVAL; }
     if (d->census_cap < 0 || d->census_cap >= (int64_t)1 << 31) { *why = "census_cap must be in [0, 2^31)"; return HYB_EINVAL; }
     if (d->sampler != HYB_SOBOL_DS && d->sampler != HYB_PRNG) { *why = "unknown sampler"; return HYB_EINVAL; }
@@ -538,7 +537,7 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     p->stream = (cudaStream_t)cuda_stream;
     p->step = 0;
     p->cur = 0;
-    p->ndims = 5 + 3 * d->n_s;
+    p->ndims = d->n_s == HYB_NS_INF ? HYB_SOBOL_DIMS : 5 + 3 * d->n_s;   // dims past the table: counter hash
     p->leg_done = p->sn_done = false;
     p->sn_warm = false;
     p->ev0 = p->ev1 = nullptr;
@@ -714,6 +713,11 @@ static hyb_status sn_run(hyb_problem* p, int* iters, bool keep_status) {
 hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
     if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
     if (!p->leg_done) return fail(p, HYB_ESTATE, "collided solve needs an MC leg of this step");
+    if (p->d.n_s == HYB_NS_INF) {   // nothing is handed off: the collided flux stays zero
+        p->sn_done = true;
+        if (out) std::memset(out, 0, sizeof(*out));
+        return HYB_OK;
+    }
     HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
     int it = 0;
     hyb_status s = sn_run(p, &it, false);
@@ -730,10 +734,16 @@ hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
     return HYB_OK;
 }
 
-// steps 3-4 launches (no host synchronisation)
+// steps 3-4 launches (no host synchronisation); for N_s = infinity the MC-leg census is the new
+// bank (no remap) and the step flux is the MC tally alone
 static hyb_status remap_launch(hyb_problem* p) {
     HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
-    HYB_CU(p, launch_remap(p));
+    if (p->d.n_s == HYB_NS_INF) {
+        HYB_CU(p, launch_census(p));
+        HYB_CU(p, launch_flux(p));
+    } else {
+        HYB_CU(p, launch_remap(p));
+    }
     p->cur = 1 - p->cur;
     p->step += 1;           // the remap's last kernel advances the device step
     p->leg_done = p->sn_done = false;
@@ -742,7 +752,8 @@ static hyb_status remap_launch(hyb_problem* p) {
 
 hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* out) {
     if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
-    if (!p->leg_done || !p->sn_done) return fail(p, HYB_ESTATE, "remap needs an MC leg and a collided solve of this step");
+    if (!p->leg_done || (!p->sn_done && p->d.n_s != HYB_NS_INF))
+        return fail(p, HYB_ESTATE, "remap needs an MC leg and a collided solve of this step");
     HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
     hyb_status s0 = remap_launch(p);
     if (s0 != HYB_OK) return s0;
@@ -769,8 +780,12 @@ hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
         if (s != HYB_OK) return s;
         HYB_CU(p, cudaEventRecord(p->evs[1], p->stream));
         int it = 0;
-        s = sn_run(p, &it, true);
-        if (s != HYB_OK) return s;
+        if (p->d.n_s != HYB_NS_INF) {
+            s = sn_run(p, &it, true);
+            if (s != HYB_OK) return s;
+        } else {
+            p->sn_done = true;
+        }
         HYB_CU(p, cudaEventRecord(p->evs[2], p->stream));
         s = remap_launch(p);
         if (s != HYB_OK) return s;

@@ -24,6 +24,19 @@ inline BankView<T> bank_view(hyb_problem* p, int which) {
     return b;
 }
 
+// The remap staging SoA: one end state per slot (bank capacity + n_hist slots), same layout as a
+// bank (cell -1 = not alive)
+template <typename T>
+inline BankView<T> stage_view(hyb_problem* p) {
+    BankView<T> b;
+    const int64_t n = p->bank_cap + p->d.n_hist;
+    char* base = (char*)p->stage;
+    b.cell = (int32_t*)base;
+    T* f = (T*)(base + bank_cell_bytes(n));
+    b.fx = f; b.fy = f + n; b.ox = f + 2 * n; b.oy = f + 3 * n; b.w = f + 4 * n;
+    return b;
+}
+
 // Birth staging inside the remap staging buffer (idle during the leg): cell (int32, n_hist, padded
 // to 256 B), then fx, fy, ox, oy, srem, tau (n_hist each). The staging buffer holds at least
 // 2 n_hist slots of 4 + 5 sizeof(T) bytes, more than this needs.

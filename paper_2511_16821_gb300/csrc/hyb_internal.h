@@ -117,9 +117,8 @@ struct hyb_problem {
     hyb::Cdf2DView src_cdf, rem_cdf;
     double* rem_f;            // 4 x ncells remap density coefficients
     float* rem_f32;           // the same in FP32 (FP32 path)
-    uint32_t* sort_keys[2];   // census sort (census_order 1): ping-pong keys and slots, and the
-    uint32_t* sort_vals[2];   //   per-tile digit counts; null when the census keeps slot order
-    uint32_t* sort_counts;
+    unsigned long long* sort_pairs[2];   // census sort (census_order 1): ping-pong (cell, slot) pairs
+    uint32_t* sort_counts;               //   and the per-tile digit counts; null for slot order
     int* rem_pos;             // ncells: 1 where the bilinear remap density is non-negative
     double* rem_q;            // ncells signed remap cell weights q = f0 A dt
     double* cell_scratch;     // per-row partials for the CDF build
@@ -151,15 +150,15 @@ namespace hyb {
 cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev);
 cudaError_t launch_leg_normalise(hyb_problem* p);
 cudaError_t launch_remap(hyb_problem* p);
+cudaError_t launch_census(hyb_problem* p);   // N_s = infinity: MC-leg census -> new bank
 cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView cdf, double* W_out_dev,
                              double* qmax_out_dev);
 cudaError_t launch_flux(hyb_problem* p);
 cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
                                  double* qmax_out, double* scratch, cudaStream_t stream);
 cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0);
-cudaError_t launch_census_sort(const int32_t* cells, long long n, uint32_t ncells, uint32_t* const keys[2],
-                               uint32_t* const vals[2], uint32_t* counts, cudaStream_t s, const uint32_t** perm,
-                               const uint32_t** sorted_keys);
+cudaError_t launch_census_sort(const int32_t* cells, long long n, uint32_t ncells, unsigned long long* const pairs[2],
+                               uint32_t* counts, cudaStream_t s, const unsigned long long** sorted);
 cudaError_t launch_bank_stats(hyb_problem* p);
 cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,
                           uint32_t* out, cudaStream_t s);

@@ -29,6 +29,9 @@ struct LegArgs {
     uint64_t seed;              // keys of the census and source point sets come from (seed, step)
     BankView<T> bank;
     BirthView<T> births;        // staged source births (cell == nullptr: drawn inside the leg)
+    int spread_bank;            // 1: bank slots taken in transposed order (the bank is sorted by cell)
+    BankView<T> cens;           // N_s = infinity: end state of history j at slot j (cell -1 unless census)
+    int stage_census;
     Cdf2DView cdf;
     long long n_src;
     T w0;
@@ -141,6 +144,16 @@ struct CounterChunks {
     }
 };
 
+// Processing order of the bank slots when the bank is sorted by cell: with nb = 32 q + r, index
+// i < 32 q goes to slot (i mod 32) q + i / 32, so the 32 lanes that take consecutive indices hold
+// particles a 32nd of the bank apart (different cells: no lanes adding to one tally address at
+// once); the last r slots keep their place. A bijection, and the results do not depend on which
+// lane runs which history (integer tallies; the point index is the slot).
+__device__ __forceinline__ long long spread_slot(long long i, long long nb) {
+    const long long q = nb >> 5;
+    return i < (q << 5) ? (i & 31) * q + (i >> 5) : i;
+}
+
 // sigma_a, sigma_s of cell k (one vector load through the read-only path)
 __device__ __forceinline__ void load_sig(const float* sig, int k, float* sa, float* ss) {
     const float2 v = __ldg(reinterpret_cast<const float2*>(sig) + k);
@@ -190,7 +203,8 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             const int take = last - next < (long long)cnt ? (int)(last - next) : cnt;
             const int rank = __popc(need & lt_mask);
             const bool mine = ((need >> lane) & 1u) && rank < take;
-            const long long j = next + rank;
+            long long j = next + rank;
+            if (a.spread_bank && j < nb) j = spread_slot(j, nb);
             next += take;
             need &= ~__ballot_sync(0xffffffffu, mine);
             if (mine) {
@@ -345,6 +359,17 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
         if (fate >= 0) {
             // ---- end of the history ------------------------------------------------------------
             const long long fw = fix_w(h.w, scw, scw_f);
+            if (a.stage_census) {
+                // N_s = infinity: the census survivors become the next bank (history order)
+                const long long j = h.j;
+                if (fate == kFateCensus) {
+                    a.cens.cell[j] = h.iy * nx + h.ix;
+                    a.cens.fx[j] = clamp_(h.fx, T(0), DX); a.cens.fy[j] = clamp_(h.fy, T(0), DY);
+                    a.cens.ox[j] = h.ox; a.cens.oy[j] = h.oy; a.cens.w[j] = h.w;
+                } else {
+                    a.cens.cell[j] = -1;
+                }
+            }
             if (fate == kFateCensus) { ++t.c[4]; t.f[3] += fw; }
             else if (fate == kFateLeaked) { ++t.c[3]; t.f[2] += fw; }
             else if (fate == kFateKilled) { ++t.c[5]; t.f[5] += fw; }
@@ -673,6 +698,10 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.seed = p->d.seed;
     a.bank = bank_view<T>(p, cur);
     a.births = birth_view<T>(p);
+    a.spread_bank = p->d.census_order == 1 ? 1 : 0;
+    a.stage_census = p->d.n_s == HYB_NS_INF ? 1 : 0;
+    a.cens = stage_view<T>(p);
+    if (a.stage_census) a.births.cell = nullptr;   // the staging buffer holds the census instead
     a.cdf = p->src_cdf;
     a.n_src = p->has_src ? p->d.n_hist : 0;
     a.w0 = (T)(p->has_src ? p->w_src / (double)p->d.n_hist : 0.0);
@@ -691,7 +720,7 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
     const LegArgs<T> a = leg_args<T>(p, hist, p->cur);
     const size_t smem = (size_t)(a.ntab * kNibbleWords + 2 * a.ntab) * sizeof(uint32_t);
     const long long work = p->bank_cap + a.n_src;
-    if (a.n_src > 0) {
+    if (a.n_src > 0 && a.births.cell) {
         const long long g = (a.n_src + kTile - 1) / kTile;
         mc_birth_kernel<T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kTile, 0, p->stream>>>(a);
     }

@@ -245,7 +245,7 @@ struct RemapArgs {
     uint64_t seed;             // keys of the birth and comb point sets come from (seed, step)
     DevState* st;
     long long* blk;            // per block: alive count, sum q, sum|w| lo, sum|w| hi
-    const uint32_t* perm;      // census in cell order: slot of every sorted position (else null)
+    const unsigned long long* perm;   // census in cell order: (cell << 32 | slot) of every sorted position (else null)
     long long nslots;          // staging slots (bank capacity + n_hist); the sort covers all of them
     int perm_slots;            // 1: the census is sorted by cell after the count pass
 };
@@ -513,9 +513,10 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     }
 }
 
-// Census in cell order: the per-block partials (alive count, quantised |w| sum, fixed-point |w|
-// sum) of the sorted positions, replacing the slot-order partials of the count pass (the totals
-// are the same integers in any order).
+// The per-block partials (alive count, quantised |w| sum, fixed-point |w| sum) of the staged end
+// states in census order (sorted positions, or slots when perm is null). For a cell-ordered
+// remap census they replace the slot-order partials of the count pass (the totals are the same
+// integers in any order); for N_s = infinity they are the only partials.
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_partials_kernel(RemapArgs<T> a) {
     const long long nb = a.st->n_bank;
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(kTile) remap_partials_kernel(RemapArgs<T> a) {
     for (int r = 0; r < kRounds; ++r) {
         const long long j = base + r * kTile + threadIdx.x;
         if (j >= N) break;
-        const long long js = (long long)a.perm[j];
+        const long long js = a.perm ? (long long)(uint32_t)a.perm[j] : j;
         if (a.stg.cell[js] < 0) continue;
         const T w = a.stg.w[js];
         ++cnt;
@@ -695,7 +696,7 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
         Particle<T> pr;
         pr.alive = false;
         if (j < N) {
-            const long long js = a.perm ? (long long)a.perm[j] : j;
+            const long long js = a.perm ? (long long)(uint32_t)a.perm[j] : j;
             pr.cell = a.stg.cell[js];
             pr.alive = pr.cell >= 0;
             pr.fx = a.stg.fx[js]; pr.fy = a.stg.fy[js]; pr.ox = a.stg.ox[js]; pr.oy = a.stg.oy[js]; pr.w = a.stg.w[js];
@@ -780,12 +781,7 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.st = p->st;
     a.blk = p->blk;
     const long long maxN = p->bank_cap + p->d.n_hist;
-    {
-        char* bk = (char*)p->stage;
-        a.stg.cell = (int32_t*)bk;
-        T* f = (T*)(bk + bank_cell_bytes(maxN));
-        a.stg.fx = f; a.stg.fy = f + maxN; a.stg.ox = f + 2 * maxN; a.stg.oy = f + 3 * maxN; a.stg.w = f + 4 * maxN;
-    }
+    a.stg = stage_view<T>(p);
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
     const size_t smem = (size_t)(a.ntab * kNibbleWords + a.ntab + 1) * sizeof(uint32_t);
     // zero the remap counters
@@ -798,11 +794,8 @@ static cudaError_t remap_t(hyb_problem* p) {
     remap_count_kernel<T><<<nblk, kTile, smem, s>>>(a);
     if (p->d.census_order == 1) {
         // survivors in cell order (stable): the comb and the census write then follow that order
-        const uint32_t* sorted_keys = nullptr;
-        uint32_t* const keys[2] = {p->sort_keys[0], p->sort_keys[1]};
-        uint32_t* const vals[2] = {p->sort_vals[0], p->sort_vals[1]};
-        e = launch_census_sort(a.stg.cell, maxN, (uint32_t)p->ncells, keys, vals, p->sort_counts, s, &a.perm,
-                               &sorted_keys);
+        unsigned long long* const pairs[2] = {p->sort_pairs[0], p->sort_pairs[1]};
+        e = launch_census_sort(a.stg.cell, maxN, (uint32_t)p->ncells, pairs, p->sort_counts, s, &a.perm);
         if (e != cudaSuccess) return e;
         remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);
     }
@@ -813,6 +806,62 @@ static cudaError_t remap_t(hyb_problem* p) {
 }
 
 cudaError_t launch_remap(hyb_problem* p) { return p->prec == HYB_FP64 ? remap_t<double>(p) : remap_t<float>(p); }
+
+// N_s = infinity: the census scalars. N = bank + births (remap_W stands for the birth weight),
+// w_ref = the power of two at or above max(|w| of the step-start bank, source weight per birth).
+__global__ void census_prep_kernel(DevState* st, double w_src, long long n_hist) {
+    st->remap_W = w_src;
+    const double wmax = fmax(st->bank_wmax, w_src > 0 ? w_src / (double)n_hist : 0.0);
+    st->w_ref = wmax > 0 ? pow2_ceil(wmax) : 1.0;
+}
+
+// staging slots past the leg's histories hold nothing: mark them dead (they sort last)
+__global__ void stage_tail_kernel(int32_t* cell, const DevState* st, long long n_src, long long nslots) {
+    const long long N = st->n_bank + n_src;
+    for (long long j = N + (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nslots;
+         j += (long long)gridDim.x * blockDim.x)
+        cell[j] = -1;
+}
+
+// N_s = infinity (pure (Q)MC, no hand-off, no collided stage, no remap births): the leg staged
+// every history's end state at its index (census survivors alive, the rest dead); the census of
+// t_{n+1} is those survivors in slot order or in cell order, combed to census_cap with the
+// remap's comb (Sec. 2.2 with the remap replaced by the MC census).
+template <typename T>
+static cudaError_t census_t(hyb_problem* p) {
+    cudaStream_t s = p->stream;
+    census_prep_kernel<<<1, 1, 0, s>>>(p->st, p->has_src ? p->w_src : 0.0, p->d.n_hist);
+    RemapArgs<T> a;
+    a.out = bank_view<T>(p, 1 - p->cur);
+    a.stg = stage_view<T>(p);
+    a.n_hist = p->d.n_hist;
+    a.cap = p->d.census_cap > 0 ? p->d.census_cap : p->d.n_hist;
+    if (a.cap > p->bank_cap) a.cap = p->bank_cap;
+    a.sampler = p->d.sampler;
+    a.seed = p->d.seed;
+    a.st = p->st;
+    a.blk = p->blk;
+    a.perm = nullptr;
+    const long long maxN = p->bank_cap + p->d.n_hist;
+    a.nslots = maxN;
+    a.perm_slots = 0;
+    const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
+    cudaError_t e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
+    if (e != cudaSuccess) return e;
+    if (p->d.census_order == 1) {
+        stage_tail_kernel<<<152, 256, 0, s>>>(a.stg.cell, p->st, p->has_src ? p->d.n_hist : 0, maxN);
+        unsigned long long* const pairs[2] = {p->sort_pairs[0], p->sort_pairs[1]};
+        e = launch_census_sort(a.stg.cell, maxN, (uint32_t)p->ncells, pairs, p->sort_counts, s, &a.perm);
+        if (e != cudaSuccess) return e;
+    }
+    remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);
+    remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nblk, p->st, a.cap, a.seed, a.sampler, p->d.n_hist);
+    remap_write_kernel<T><<<nblk, kTile, 0, s>>>(a);
+    remap_finish_kernel<<<1, 1, 0, s>>>(p->st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_census(hyb_problem* p) { return p->prec == HYB_FP64 ? census_t<double>(p) : census_t<float>(p); }
 
 // step flux phi_pre + phi_post + phi_c0 (cell averages)
 __global__ void flux_kernel(int ncells, const double* pre, const double* post, const double* phi, double* flux) {

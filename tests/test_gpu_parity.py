@@ -371,3 +371,29 @@ def test_large_mesh_sampled_records(H, orc):
     tot = s["w_absorbed"] + s["w_leaked"] + s["w_census"] + s["w_handoff"] + s["w_killed"]
     assert math.isclose(s["w_source"], tot, rel_tol=1e-12)
     assert s["histories"] == N and s["errors"] == 0
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_ns_infinity_pure_mc(H, orc, order):
+    """N_s = infinity (pure (Q)MC, no hand-off, no collided stage): the MC-leg census survivors,
+    combed to census_cap, are the next bank. Three steps of a pulse (bank only) and of a small
+    checkerboard (bank + births) against the oracle: banks cell for cell, fluxes to rounding."""
+    for spec, bank0 in ((W.pulse(n_hist=4096), None),
+                        (W.checkerboard(n_s=0, n_hist=6000, cells_per_block=2), None)):
+        spec = spec.with_(n_s=W.NS_INF, precision=W.FP64, census_order=order)
+        P = H.Problem(spec)
+        ob = orc.init_bank(spec, spec.ic) if spec.ic is not None else None
+        for k in range(3):
+            st = P.step(1)[0]
+            r = orc.step(spec, k, ob)
+            ob = r["bank"]
+            gb = P.bank()
+            assert st["sn_iterations"] == 0
+            assert gb["n"] == ob["n"], (spec.name, k)
+            assert np.array_equal(gb["cell"], ob["cell"]), (spec.name, k)
+            for q in ("fx", "fy", "ox", "oy"):
+                assert np.allclose(gb[q], ob[q], rtol=0, atol=1e-12 * max(spec.lx, 1.0)), (spec.name, k, q)
+            assert np.allclose(gb["w"], ob["w"], rtol=1e-10, atol=0), (spec.name, k)
+            f = P.tally("flux")
+            assert np.allclose(f, r["flux"], rtol=1e-9, atol=1e-12 * np.max(np.abs(r["flux"]))), (spec.name, k)
+        P.close()
