@@ -273,6 +273,28 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0) -> dic
             "single_problem_path": {"histories_per_s": h2 / dt, "ms_per_step_all": 1e3 * dt / steps}}
 
 
+def census_order_measure(steps: int = 5) -> dict:
+    """The benchmark workload with the census sorted by cell before the comb (FP32): device time
+    per step. At equal histories its multi-step flux error is lower (convergence.py)."""
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    spec = spec_for(W.FP32).with_(census_order=1)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        P = hyb.Problem(spec, stream=stream)
+        P.step(3)
+        ms, hist = 0.0, 0
+        for _ in range(steps):
+            flush.zero_()
+            st = P.step(1)[0]
+            ms += st["ms"]
+            hist += st["histories"]
+        P.close()
+    torch.cuda.synchronize()
+    return {"census_order": "cell", "histories_per_s": hist / (ms / 1e3), "ms_per_step": ms / steps}
+
+
 def large_measure(steps: int = 2, n_hist: int = 100_000_000) -> dict:
     """The large diffusive workload: 1024^2 cells over 10 x 10 cm, random 8 x 8-cell blocks with
     sigma_t in {1, 10, 1000} (scattering ratio 0.999 in the thickest, 0.5 elsewhere), N_s = 8,
@@ -447,6 +469,8 @@ def main():
                         "phase_ms": r64["phase_ms"]}
     if not args.no_e2e:
         line["e2e"] = e2e_measure(spec_for(W.FP32), max(2, min(args.steps, 5)))
+    if CENSUS_ORDER == 0:
+        line["census_cell_order"] = census_order_measure()
     if not args.no_large:
         line["large"] = large_measure()
     if not args.no_batch:

@@ -23,13 +23,14 @@ from . import workloads as W
 
 
 def problem(n_hist: int, seed: int, sampler: int, n_s: int = 2, precision: int = W.FP32,
-            census_order: int = 0) -> W.ProblemSpec:
+            census_order: int = 0, sigma_scale: float = 1.0) -> W.ProblemSpec:
     """Checkerboard of 7x7 one-centimetre blocks at 4 cells per block (28x28), S4, absorber /
-    scatterer blocks, Q = 1 in the centre block, dt = 0.1."""
+    scatterer blocks (cross sections times sigma_scale), Q = 1 in the centre block, dt = 0.1."""
     order = "cell" if census_order else "slot"
-    return W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision, sampler=sampler,
-                          cells_per_block=4).with_(sn_order=4, sn_tol=1e-6, census_order=census_order,
-                                                   name=f"checkerboard28 N_s={n_s}, census in {order} order")
+    sp = W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision, sampler=sampler, cells_per_block=4)
+    return sp.with_(sigma_a=sp.sigma_a * sigma_scale, sigma_s=sp.sigma_s * sigma_scale, sn_order=4, sn_tol=1e-6,
+                    census_order=census_order,
+                    name=f"checkerboard28 x{sigma_scale:g} N_s={'inf' if n_s == W.NS_INF else n_s}, census in {order} order")
 
 
 def end_flux(spec: W.ProblemSpec, steps: int) -> np.ndarray:
@@ -45,9 +46,9 @@ def fit_alpha(ns, errs) -> float:
 
 
 def study(log2_n=range(10, 21), seeds=range(16), steps: int = 4, ref_log2: int = 24, ref_seeds=range(100, 104),
-          n_s: int = 2, census_order: int = 0, spec_fn=problem) -> dict:
+          n_s: int = 2, census_order: int = 0, sigma_scale: float = 1.0, spec_fn=problem) -> dict:
     import torch
-    mk = lambda n, s, smp: spec_fn(n, s, smp, n_s, census_order=census_order)   # noqa: E731
+    mk = lambda n, s, smp: spec_fn(n, s, smp, n_s, census_order=census_order, sigma_scale=sigma_scale)   # noqa: E731
     ref = np.mean([end_flux(mk(1 << ref_log2, s, W.SOBOL), steps) for s in ref_seeds], axis=0)
     nref = float(np.linalg.norm(ref))
     out = {"workload": mk(1, 0, W.SOBOL).name, "steps": steps, "reference_histories": 1 << ref_log2,
@@ -66,7 +67,7 @@ def study(log2_n=range(10, 21), seeds=range(16), steps: int = 4, ref_log2: int =
 
 
 def ns_sweep(n_s_values=(0, 1, 2, 5, 10, 20, W.NS_INF), log2_n=range(10, 19, 2), seeds=range(8),
-             ref_log2: int = 22, ref_seeds=range(100, 104)) -> list:
+             ref_log2: int = 22, ref_seeds=range(100, 104), sigma_scale: float = 1.0) -> list:
     """The analogue of the paper's Table 1 on the synthetic problem: for each scatter limit N_s,
     the source iterations of the collided solve (from zero, stop at 1e-6 relative change) and the
     convergence rates alpha of one step's flux error with Sobol points and with the counter PRNG.
@@ -74,13 +75,14 @@ def ns_sweep(n_s_values=(0, 1, 2, 5, 10, 20, W.NS_INF), log2_n=range(10, 19, 2),
     import torch
     rows = []
     for n_s in n_s_values:
-        with hyb.Problem(problem(1 << 16, 0, W.SOBOL, n_s).with_(sn_warm_start=0)) as p:
+        with hyb.Problem(problem(1 << 16, 0, W.SOBOL, n_s, sigma_scale=sigma_scale).with_(sn_warm_start=0)) as p:
             st = p.step(1)[0]
-        r = study(log2_n=log2_n, seeds=seeds, steps=1, ref_log2=ref_log2, ref_seeds=ref_seeds, n_s=n_s)
+        r = study(log2_n=log2_n, seeds=seeds, steps=1, ref_log2=ref_log2, ref_seeds=ref_seeds, n_s=n_s,
+                  sigma_scale=sigma_scale)
         rows.append({"n_s": "inf" if n_s == W.NS_INF else n_s, "sn_iterations": st["sn_iterations"],
                      "alpha_sobol": r["sobol"]["alpha"], "alpha_prng": r["prng"]["alpha"],
                      "err_sobol": r["sobol"]["err"][-1], "err_prng": r["prng"]["err"][-1],
-                     "n_max": r["sobol"]["n"][-1]})
+                     "n_max": r["sobol"]["n"][-1], "workload": r["workload"]})
     torch.cuda.synchronize()
     return rows
 
@@ -94,3 +96,4 @@ if __name__ == "__main__":
             print(json.dumps(study(steps=steps, n_s=n_s)), flush=True)
     print(json.dumps(study(steps=4, n_s=2, census_order=1)), flush=True)
     print(json.dumps({"ns_sweep": ns_sweep()}), flush=True)
+    print(json.dumps({"ns_sweep": ns_sweep(sigma_scale=10.0)}), flush=True)

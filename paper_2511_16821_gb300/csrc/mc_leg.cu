@@ -73,7 +73,7 @@ __device__ __forceinline__ void leg_tally_zero(LegTally& t) {
 // two is exact, and the per-segment bookkeeping then needs no FP64 arithmetic.
 struct LegScales {
     int kt, km, kw;
-    double scw;
+    double scw, sct, scm;     // 2^kw, 2^kt, 2^km
 };
 
 template <typename T>
@@ -89,6 +89,8 @@ __device__ __forceinline__ LegScales leg_scales(const LegArgs<T>& a) {
         s.kw = min(s.kw, 126);
     }
     s.scw = ldexp(1.0, s.kw);
+    s.sct = ldexp(1.0, s.kt);
+    s.scm = ldexp(1.0, s.km);
     return s;
 }
 
@@ -172,7 +174,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                                const uint32_t* sShS, uint64_t key_c, uint64_t key_s, const LegScales& sc,
                                LegTally& t) {
     using P = Prec<T>;
-    const T sc_t = (T)ldexp(1.0, sc.kt), sc_m = (T)ldexp(1.0, sc.km);
+    const T sc_t = (T)sc.sct, sc_m = (T)sc.scm;
     const double scw = sc.scw;
     const float scw_f = (float)sc.scw;     // used on the FP32 path only (kw <= 126 there)
     constexpr bool kF32 = sizeof(T) == 4;
@@ -440,10 +442,12 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
         sShC[d] = dshift(key_c, (uint64_t)d);
         sShS[d] = dshift(key_s, (uint64_t)d);
     }
+    __shared__ LegScales s_sc;   // formed once per block (FP64 work)
+    if (threadIdx.x == 0) s_sc = leg_scales<T>(a);
     __syncthreads();
     const long long nb = a.st->n_bank;
     const long long N = nb + a.n_src;
-    const LegScales sc = leg_scales<T>(a);
+    const LegScales sc = s_sc;
     LegTally t;
     leg_tally_zero(t);
     leg_warp_range<T>(a, CounterChunks{&a.st->leg_next, N}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
@@ -466,6 +470,7 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
     // the chunk's problem descriptor lives in shared memory (read on use, not held in registers)
     __shared__ __align__(16) unsigned int s_args[(sizeof(LegArgs<T>) + 3) / 4];
     __shared__ unsigned long long s_next;   // warps take kWarpChunk histories of the chunk at a time
+    __shared__ LegScales s_sc;              // the chunk problem's scales, formed by one thread
     build_nibble_tables(V, ntab_max, sV);
     for (;;) {
         __syncthreads();
@@ -486,11 +491,12 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
             sShC[d] = dshift(key_c, (uint64_t)d);
             sShS[d] = dshift(key_s, (uint64_t)d);
         }
+        if (threadIdx.x == 0) s_sc = leg_scales<T>(a);
         __syncthreads();
         const long long nb = a.st->n_bank;
         const long long N = nb + a.n_src;
         const long long e = ch.j1 < N ? ch.j1 : N;
-        const LegScales sc = leg_scales<T>(a);
+        const LegScales sc = s_sc;
         LegTally t;
         leg_tally_zero(t);
         if (ch.j0 < e) leg_warp_range<T>(a, CounterChunks{&s_next, e}, nb, sV, sShC, sShS, key_c, key_s, sc, t);

@@ -397,6 +397,31 @@ __device__ __forceinline__ long long quant(T w, double w_ref, float qsc) {
     return quant_w(w, w_ref, qsc);
 }
 
+// Per-step scalars of the remap kernels, formed once per block by one thread (FP64 work that
+// every thread repeating it would cost more than its slots' arithmetic on this GPU).
+struct RemapScal {
+    long long N;               // slots: bank + births
+    double wbar, w_ref;        // birth weight, comb quantisation base
+    float qsc, sca;            // FP32 comb scale 2^(32 - log2 w_ref), FP32 |w|-sum scale 2^kfa
+    int krw, kw, kfa, kf;      // 128-bit scales of sum |w| and of the statistics; FP32 per-thread ones
+};
+
+__device__ __forceinline__ RemapScal remap_scalars(const DevState* st, long long n_hist) {
+    RemapScal r;
+    const long long nb = st->n_bank;
+    const long long nbirth = st->remap_W > 0 ? n_hist : 0;
+    r.N = nb + nbirth;
+    r.wbar = nbirth ? st->remap_W / (double)n_hist : 0.0;
+    r.w_ref = st->w_ref;
+    r.qsc = quant_scale(r.w_ref);
+    r.krw = scale_exponent((double)(r.N > 0 ? r.N : 1) * r.w_ref, 125);
+    r.kw = scale_exponent((double)(r.N > 0 ? r.N : 1) * fmax(r.w_ref, 1e-300) * 4.0, 125);
+    r.kfa = min(r.krw - 64, 126);
+    r.kf = min(r.kw - 64, 126);
+    r.sca = pow2f(r.kfa);
+    return r;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     extern __shared__ uint32_t sm[];
@@ -405,20 +430,20 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_REMAP_SOURCE);
     build_nibble_tables(a.V, a.ntab, sV);
     for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
+    __shared__ RemapScal s_rs;
+    if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
     __syncthreads();
     Points pts{sV, sSh, key, a.sampler, a.ntab};
     const long long nb = a.st->n_bank;
-    const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
-    const long long N = nb + nbirth;
-    const double wbar = nbirth ? a.st->remap_W / (double)a.n_hist : 0.0;
-    const double w_ref = a.st->w_ref;
-    const float qsc = quant_scale(w_ref);
+    const long long N = s_rs.N;
+    const T wbar_t = (T)s_rs.wbar;
+    const double w_ref = s_rs.w_ref;
+    const float qsc = s_rs.qsc;
     // block scales (128-bit): krw for the survivors' sum |w|, kw for the statistics
-    const int krw = scale_exponent((double)(N > 0 ? N : 1) * w_ref, 125);
-    const int kw = scale_exponent((double)(N > 0 ? N : 1) * fmax(w_ref, 1e-300) * 4.0, 125);
+    const int krw = s_rs.krw, kw = s_rs.kw;
     constexpr bool kF32 = sizeof(T) == 4;
-    const int kfa = min(krw - 64, 126), kf = min(kw - 64, 126);   // FP32 per-thread scales
-    const float sca = pow2f(kfa);
+    const int kfa = s_rs.kfa, kf = s_rs.kf;   // FP32 per-thread scales
+    const float sca = s_rs.sca;
     RemapSums<T> sums;
     sums.init(kf);
     long long cnt = 0, qs = 0, wsf = 0;
@@ -431,7 +456,7 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
             if (a.perm_slots && j < a.nslots) a.stg.cell[j] = -1;   // unused slots sort last, as dead
             continue;
         }
-        const Particle<T> pr = remap_slot<T>(a, pts, j, nb, (T)wbar, sums, &leaked, &killed, &segs, &err);
+        const Particle<T> pr = remap_slot<T>(a, pts, j, nb, wbar_t, sums, &leaked, &killed, &segs, &err);
         a.stg.cell[j] = pr.alive ? pr.cell : -1;
         a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
         if (pr.alive) {
@@ -519,14 +544,15 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
 // integers in any order); for N_s = infinity they are the only partials.
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_partials_kernel(RemapArgs<T> a) {
-    const long long nb = a.st->n_bank;
-    const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
-    const long long N = nb + nbirth;
-    const double w_ref = a.st->w_ref;
-    const float qsc = quant_scale(w_ref);
-    const int krw = scale_exponent((double)(N > 0 ? N : 1) * w_ref, 125);
-    const int kfa = min(krw - 64, 126);
-    const float sca = pow2f(kfa);
+    __shared__ RemapScal s_rs;
+    if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
+    __syncthreads();
+    const long long N = s_rs.N;
+    const double w_ref = s_rs.w_ref;
+    const float qsc = s_rs.qsc;
+    const int krw = s_rs.krw;
+    const int kfa = s_rs.kfa;
+    const float sca = s_rs.sca;
     constexpr bool kF32 = sizeof(T) == 4;
     long long cnt = 0, qs = 0, wsf = 0;
     double ws = 0;
@@ -679,11 +705,12 @@ __device__ __forceinline__ long long first_tooth(long long S, long long M, long 
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
     __shared__ long long s_c[kTile / 32], s_q[kTile / 32];
-    const long long nb = a.st->n_bank;
-    const long long nbirth = a.st->remap_W > 0 ? a.n_hist : 0;
-    const long long N = nb + nbirth;
-    const double w_ref = a.st->w_ref;
-    const float qsc = quant_scale(w_ref);
+    __shared__ RemapScal s_rs;
+    if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
+    __syncthreads();
+    const long long N = s_rs.N;
+    const double w_ref = s_rs.w_ref;
+    const float qsc = s_rs.qsc;
     const int comb = a.st->comb_on;
     const long long M = a.cap, o = a.st->comb_o, Ttot = a.st->comb_T;
     const T wcopy = (T)a.st->wcopy;
