@@ -101,13 +101,15 @@ class Clocks:
 
 
 CENSUS_ORDER = 0
+SN_ACCEL = 0
 
 
 def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0, warm: int = 1) -> W.ProblemSpec:
     """The benchmark workload; source iteration starts from the previous step's collided flux
     (the same fixed point, fewer sweeps)."""
     return W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision).with_(sn_warm_start=warm,
-                                                                                       census_order=CENSUS_ORDER)
+                                                                                       census_order=CENSUS_ORDER,
+                                                                                       sn_accel=SN_ACCEL)
 
 
 def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
@@ -295,14 +297,15 @@ def census_order_measure(steps: int = 5) -> dict:
     return {"census_order": "cell", "histories_per_s": hist / (ms / 1e3), "ms_per_step": ms / steps}
 
 
-def large_measure(steps: int = 2, n_hist: int = 100_000_000) -> dict:
+def large_measure(steps: int = 2, n_hist: int = 100_000_000, sn_accel: int = 0) -> dict:
     """The large diffusive workload: 1024^2 cells over 10 x 10 cm, random 8 x 8-cell blocks with
     sigma_t in {1, 10, 1000} (scattering ratio 0.999 in the thickest, 0.5 elsewhere), N_s = 8,
     10^8 births per step, dt = 0.01, S8, FP32 tracking. One untimed step fills the census; the
-    timed steps carry 10^8 census particles plus 10^8 births each."""
+    timed steps carry 10^8 census particles plus 10^8 births each. sn_accel: Anderson depth of
+    the collided solve (0: plain source iteration)."""
     import torch
     from paper_2511_16821_gb300 import hyb
-    spec = W.large(n=1024, n_hist=n_hist, precision=W.FP32).with_(sn_warm_start=1)
+    spec = W.large(n=1024, n_hist=n_hist, precision=W.FP32).with_(sn_warm_start=1, sn_accel=sn_accel)
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     with torch.cuda.stream(stream):
@@ -322,6 +325,7 @@ def large_measure(steps: int = 2, n_hist: int = 100_000_000) -> dict:
         P.close()
     torch.cuda.synchronize()
     return {"workload": "large diffusive 1024x1024, N_s=8, 1e8 births/step + census, dt=0.01, S8, FP32",
+            "sn_accel": sn_accel,
             "histories_per_s": hist / (ms / 1e3), "segments_per_s": segs / (ms / 1e3), "ms_per_step": ms / steps,
             "phase_ms": phase, "sn_iterations": it}
 
@@ -383,12 +387,14 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (FP32, no profile/e2e/CPU legs): the case used for ncu captures")
+    ap.add_argument("--sn-accel", type=int, default=0, help="Anderson depth of the collided solve (0: plain SI)")
     ap.add_argument("--census-order", type=int, default=0, choices=[0, 1],
                     help="census in slot order (0) or sorted by cell before the comb (1)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    global CENSUS_ORDER
+    global CENSUS_ORDER, SN_ACCEL
     CENSUS_ORDER = args.census_order
+    SN_ACCEL = args.sn_accel
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -472,7 +478,8 @@ def main():
     if CENSUS_ORDER == 0:
         line["census_cell_order"] = census_order_measure()
     if not args.no_large:
-        line["large"] = large_measure()
+        line["large"] = large_measure(sn_accel=4)
+        line["large_plain_si"] = large_measure(sn_accel=0)
     if not args.no_batch:
         line["batched"] = batched_measure()
         line["serving"] = serving_measure(100.0, 3.0)

@@ -99,6 +99,10 @@ typedef struct {
                                  before the comb, so the systematic comb samples each cell's
                                  weight to within one copy and the next leg's bank is
                                  cell-coherent */
+    int32_t sn_accel;         /* 0: plain source iteration (the paper); 1..8: Anderson acceleration
+                                 of that depth (the same fixed point, fewer sweeps in diffusive
+                                 problems) */
+    int32_t pad1;
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */

@@ -208,7 +208,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
-        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv;
+        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas;
     int64_t cap, nblk;
     int gr, gc;
 };
@@ -241,7 +241,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.sntx = (size_t)nord * nc * 4 * T;           // w_m psi_m per ordinate and cell
     z.snty = (size_t)nord * d->nx * 2 * T;        // strip-top traces per ordinate
     z.snqb = 3 * kMaxOrd * T;
-    z.snnorm = 2 * ((nc + 31) / 32) * 8;          // per reduction block (32 cells)
+    z.snnorm = 10 * ((nc + 31) / 32) * 8;         // per reduction block (32 cells): up to kAAMax + 2 sums
     z.nblk = (z.cap + d->n_hist + 2047) / 2048;
     z.blk = 4 * (size_t)z.nblk * 8;
     z.gr = hyb::guide_bits(d->ny);
@@ -250,6 +250,8 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.gcol = (size_t)d->ny * ((size_t(1) << z.gc) + 1) * 4;
     z.remf32 = 4 * nc * 4;
     z.siginv = 4 * nc * 4;
+    z.aah = d->sn_accel > 0 ? 2 * (size_t)(d->sn_accel + 1) * 4 * nc * T : 0;   // Anderson history
+    z.aas = d->sn_accel > 0 ? sn_accel_state_bytes() : 0;
     z.rempos = nc * 4;
     const size_t nslots = (size_t)(z.cap + d->n_hist);
     z.sortkv = d->census_order == 1 ? nslots * 8 : 0;                    // x2: (cell, slot) pairs, ping-pong
@@ -264,7 +266,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
-                            z.sortkv, z.sortc, z.siginv};
+                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -321,6 +323,8 @@ void assign(hyb_problem* p) {
     for (int i = 0; i < 2; ++i) p->sort_pairs[i] = z.sortkv ? (unsigned long long*)take(z.sortkv) : nullptr;
     p->sort_counts = z.sortc ? (uint32_t*)take(z.sortc) : nullptr;
     p->sig_inv = (float*)take(z.siginv);
+    p->aa_hist = z.aah ? take(z.aah) : nullptr;
+    p->aa_state = z.aas ? take(z.aas) : nullptr;
     p->bank_cap = z.cap;
     p->nblk_max = z.nblk;
 }
@@ -355,6 +359,7 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->sn_order != 4 && d->sn_order != 8) { *why = "sn_order must be 4 or 8"; return HYB_EINVAL; }
     if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
     if (d->census_order != 0 && d->census_order != 1) { *why = "census_order must be 0 or 1"; return HYB_EINVAL; }
+    if (d->sn_accel < 0 || d->sn_accel > 8) { *why = "sn_accel must be in [0, 8]"; return HYB_EINVAL; }
     if (!(d->sn_tol >= 0) || !(d->w_min >= 0) || !(d->w_min < 1)) { *why = "sn_tol >= 0 and 0 <= w_min < 1 required"; return HYB_EINVAL; }
     if (!d->sigma_a || !d->sigma_s) { *why = "sigma_a and sigma_s are required"; return HYB_EINVAL; }
     const size_t nc = (size_t)d->nx * d->ny;

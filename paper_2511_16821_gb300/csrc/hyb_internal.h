@@ -135,7 +135,9 @@ struct hyb_problem {
     void* sn_ty;              // strip-top y traces per ordinate (T)
     void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, precision T
     double* sn_phi_d;         // collided flux, FP64 copy (4 x ncells)
-    double* sn_norm;          // per-block norm partials
+    double* sn_norm;          // per-block norm partials (Anderson: kAAMax + 2 per block)
+    void* aa_hist;            // Anderson acceleration: (depth + 1) iterates g, then residuals f (T)
+    void* aa_state;           // Anderson: slots, Gram matrix, mixing weights
     long long* blk;           // remap block partials (4 x nblk)
     int64_t nblk_max;
     hyb::DevState* st;        // device counters
@@ -150,7 +152,8 @@ namespace hyb {
 cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev);
 cudaError_t launch_leg_normalise(hyb_problem* p);
 cudaError_t launch_remap(hyb_problem* p);
-cudaError_t launch_census(hyb_problem* p);   // N_s = infinity: MC-leg census -> new bank
+cudaError_t launch_census(hyb_problem* p);
+size_t sn_accel_state_bytes();               // device bytes of the Anderson state   // N_s = infinity: MC-leg census -> new bank
 cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView cdf, double* W_out_dev,
                              double* qmax_out_dev);
 cudaError_t launch_flux(hyb_problem* p);

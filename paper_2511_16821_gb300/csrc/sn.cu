@@ -319,6 +319,7 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
 //   ||phi_new - phi_old|| <= tol ||phi_new||   (or no source at all),
 // so the reduction and the test are one launch and the result does not depend on block order.
 constexpr int kRedCells = 32, kRedGroups = 8;
+constexpr int kAAMax = 8;   // deepest Anderson history
 
 template <typename T> struct Vec4;
 template <> struct Vec4<float> {
@@ -419,6 +420,200 @@ sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncell
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Anderson acceleration of the source iteration (optional, depth 1..kAAMax). With G the
+// iteration map (source -> sweep -> ordinate sum), g_k = G(phi_k) and residual f_k = g_k - phi_k,
+// the next iterate is phi_{k+1} = sum_j alpha_j g_j over the last n stored iterates, alpha
+// minimising || sum_j alpha_j f_j || with sum_j alpha_j = 1 (weighted L2 norm of the bilinear
+// fields, as in the stop test). A fixed point of the map is a fixed point of the mixed
+// iteration, so the converged flux is the plain iteration's; the stop test is the same
+// ||f_k|| <= tol ||g_k||, and a converged solve returns g_k.
+// ---------------------------------------------------------------------------------------------
+struct AAState {
+    int n, head, ok, pad;                     // stored iterates, next slot, mixing weights valid
+    double gram[kAAMax + 1][kAAMax + 1];      // <f_s, f_t> over stored slots
+    double alpha[kAAMax + 1];                 // mixing weights by slot (0 for empty slots)
+};
+constexpr int kAAPart = kAAMax + 2;           // per reduction block: dots with every slot, then <g, g>
+
+// The constrained least squares of the mixing weights over the n valid slots (one thread):
+// (G + eps I) y = 1, alpha = y / sum y, by elimination with partial pivoting.
+__device__ void aa_solve(AAState* aa, const int* slots, int n) {
+    double G[kAAMax + 1][kAAMax + 2];
+    double dmax = 0;
+    for (int a = 0; a < n; ++a) dmax = fmax(dmax, aa->gram[slots[a]][slots[a]]);
+    for (int a = 0; a < n; ++a) {
+        for (int b = 0; b < n; ++b) G[a][b] = aa->gram[slots[a]][slots[b]];
+        G[a][a] += 1e-12 * dmax;
+        G[a][n] = 1.0;
+    }
+    bool ok = dmax > 0;
+    for (int c = 0; c < n && ok; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(G[r][c]) > fabs(G[piv][c])) piv = r;
+        if (!(fabs(G[piv][c]) > 0)) { ok = false; break; }
+        if (piv != c)
+            for (int q = c; q <= n; ++q) { const double t = G[c][q]; G[c][q] = G[piv][q]; G[piv][q] = t; }
+        for (int r = c + 1; r < n; ++r) {
+            const double f = G[r][c] / G[c][c];
+            for (int q = c; q <= n; ++q) G[r][q] -= f * G[c][q];
+        }
+    }
+    double y[kAAMax + 1];
+    double sy = 0;
+    for (int r = n - 1; r >= 0 && ok; --r) {
+        double v = G[r][n];
+        for (int q = r + 1; q < n; ++q) v -= G[r][q] * y[q];
+        y[r] = v / G[r][r];
+        sy += y[r];
+    }
+    ok = ok && isfinite(sy) && fabs(sy) > 1e-300;
+    for (int q = 0; q <= kAAMax; ++q) aa->alpha[q] = 0.0;
+    if (ok)
+        for (int a = 0; a < n; ++a) aa->alpha[slots[a]] = y[a] / sy;
+    aa->ok = ok ? 1 : 0;
+}
+
+// The reduction of an accelerated iteration: g = sum of w_m psi_m (into phi_new and the history),
+// f = g - phi_old, the weighted dots of f with every stored residual and <g, g>; the last block
+// completes the Gram matrix, applies the stop test and, if the solve goes on, forms the weights.
+template <typename T>
+__global__ void __launch_bounds__(kRedCells * kRedGroups)
+sn_reduce_aa_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, double* part, T* g_hist,
+                    T* f_hist, int depth, AAState* aa, DevState* st, double tol) {
+    __shared__ T sp[kRedGroups][kRedCells][4];
+    __shared__ double sred[kAAPart][kRedCells * 4 / 32];
+    __shared__ bool s_last;
+    const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
+    const int k0 = blockIdx.x * kRedCells;
+    if (*(volatile const int*)&st->sn_conv) {
+        if (threadIdx.x < kRedCells * 4) {
+            const size_t e = (size_t)k0 * 4 + threadIdx.x;
+            if (e < (size_t)ncells * 4) phi_new[e] = phi_old[e];
+        }
+        return;
+    }
+    const int nslot = depth + 1;
+    const int head = aa->head, n_new = aa->n + 1 < nslot ? aa->n + 1 : nslot;
+    const size_t nv = (size_t)ncells * 4;
+    {
+        const int k = k0 + c;
+        T acc[4] = {0, 0, 0, 0};
+        if (k < ncells)
+            for (int m = g; m < nord; m += kRedGroups) {
+                T v[4];
+                Vec4<T>::load(psi + ((size_t)m * ncells + k) * 4, v);
+                acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2]; acc[3] += v[3];
+            }
+        sp[g][c][0] = acc[0]; sp[g][c][1] = acc[1]; sp[g][c][2] = acc[2]; sp[g][c][3] = acc[3];
+    }
+    __syncthreads();
+    if (threadIdx.x < kRedCells * 4) {
+        const int cc = threadIdx.x >> 2, i = threadIdx.x & 3;
+        const int k = k0 + cc;
+        T dots[kAAMax + 1];
+        T den = 0;
+#pragma unroll
+        for (int q = 0; q <= kAAMax; ++q) dots[q] = 0;
+        if (k < ncells) {
+            T v = 0;
+#pragma unroll
+            for (int q = 0; q < kRedGroups; ++q) v += sp[q][cc][i];
+            const size_t e = (size_t)k * 4 + i;
+            const T nrm = i == 0 ? T(1) : (i == 3 ? T(1.0 / 9.0) : T(1.0 / 3.0));
+            const T f = v - phi_old[e];
+            phi_new[e] = v;
+            g_hist[head * nv + e] = v;
+            f_hist[head * nv + e] = f;
+            den = nrm * v * v;
+            // the stored slots: head and the n_new - 1 before it in ring order
+#pragma unroll
+            for (int q = 0; q <= kAAMax; ++q) {
+                const int j = (head - q + nslot) % nslot;
+                if (q < nslot && j < n_new) dots[q] = nrm * f * (q == head ? f : f_hist[q * nv + e]);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            den += __shfl_down_sync(0xffffffffu, den, o);
+#pragma unroll
+            for (int q = 0; q <= kAAMax; ++q) dots[q] += __shfl_down_sync(0xffffffffu, dots[q], o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            const int w = threadIdx.x >> 5;
+#pragma unroll
+            for (int q = 0; q <= kAAMax; ++q) sred[q][w] = (double)dots[q];
+            sred[kAAMax + 1][w] = (double)den;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kAAPart) {
+        double a = 0;
+        for (int w = 0; w < kRedCells * 4 / 32; ++w) a += sred[threadIdx.x][w];
+        part[(size_t)blockIdx.x * kAAPart + threadIdx.x] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(&st->sn_blocks_done, 1u);
+        s_last = done == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32) {
+        __threadfence();
+        // totals in block order: one lane per entry (entries < 32)
+        double tot = 0;
+        if (threadIdx.x < kAAPart)
+            for (int b = 0; b < (int)gridDim.x; ++b) tot += ((volatile double*)part)[(size_t)b * kAAPart + threadIdx.x];
+        __shared__ double s_tot[kAAPart];
+        if (threadIdx.x < kAAPart) s_tot[threadIdx.x] = tot;
+        __syncwarp();
+        if (threadIdx.x == 0) {
+            int slots[kAAMax + 1];
+            for (int j = 0; j < n_new; ++j) {
+                const int sl = (head - j + nslot) % nslot;
+                slots[j] = sl;
+                aa->gram[head][sl] = s_tot[sl];
+                aa->gram[sl][head] = s_tot[sl];
+            }
+            const double num = s_tot[head], d = s_tot[kAAMax + 1];
+            st->sn_norm_num = num;
+            st->sn_norm_den = d;
+            st->sn_iters += 1;
+            if (d == 0.0 || sqrt(num) <= tol * sqrt(d)) st->sn_conv = 1;
+            else aa_solve(aa, slots, n_new);
+            aa->n = n_new;
+            aa->head = (head + 1) % nslot;
+            st->sn_blocks_done = 0u;
+        }
+    }
+}
+
+// The mixed iterate phi_{k+1} = sum alpha_s g_s (plain step g when the weights failed) and the
+// source integrals of the next sweep from it.
+template <typename T>
+__global__ void sn_mix_kernel(T* phi_new, const T* g_hist, int ncells, int depth, const AAState* aa,
+                              const DevState* st, const T* sig, const double* mom, T area, T inv_4pi_dt, T* src) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nv = (size_t)ncells * 4;
+    if (e >= nv || *(volatile const int*)&st->sn_conv) return;
+    T v = phi_new[e];
+    if (aa->ok) {
+        double acc = 0;
+        for (int q = 0; q <= depth; ++q) {
+            const double al = aa->alpha[q];
+            if (al != 0.0) acc += al * (double)g_hist[q * nv + e];
+        }
+        v = (T)acc;
+        phi_new[e] = v;
+    }
+    const int i = (int)(e & 3);
+    const size_t k = e >> 2;
+    const T n_i = i == 0 ? T(1) : (i == 3 ? T(1.0 / 9.0) : T(1.0 / 3.0));
+    const T cs = sig[2 * k + 1] * area * T(0.07957747154594767);
+    src[e] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
+}
+
 // start of a solve: clear the stop state; the iterate starts from the previous solution
 // (warm start, re-read from its FP64 copy) or from zero
 template <typename T>
@@ -475,6 +670,20 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     }
     sweep_pipe_kernel<T><<<p->n_ord, 32 * a.W, smem, s>>>(a);
     const int gr = (p->ncells + kRedCells - 1) / kRedCells;
+    if (p->d.sn_accel > 0) {
+        const int depth = p->d.sn_accel;
+        const size_t nv = 4 * (size_t)p->ncells;
+        T* gh = (T*)p->aa_hist;
+        T* fh = gh + (size_t)(depth + 1) * nv;
+        sn_reduce_aa_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>(
+            (const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, p->sn_norm, gh, fh, depth,
+            (AAState*)p->aa_state, p->st, sn_tol_eff(p));
+        sn_mix_kernel<T><<<(unsigned)((nv + 255) / 256), 256, 0, s>>>((T*)p->sn_phi, gh, p->ncells, depth,
+                                                                      (const AAState*)p->aa_state, p->st,
+                                                                      (const T*)p->sig, p->mom_d, (T)p->area,
+                                                                      inv4pidt, src);
+        return cudaGetLastError();
+    }
     sn_reduce_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old,
                                                               (T*)p->sn_phi, p->ncells, p->sn_norm, (const T*)p->sig,
                                                               p->mom_d, (T)p->area, inv4pidt, src, p->st,
@@ -482,9 +691,15 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     return cudaGetLastError();
 }
 
+size_t sn_accel_state_bytes() { return sizeof(AAState); }
+
 cudaError_t sn_start(hyb_problem* p) {
     cudaError_t e = cudaMemsetAsync(&p->st->sn_conv, 0, 2 * sizeof(int), p->stream);
     if (e != cudaSuccess) return e;
+    if (p->d.sn_accel > 0) {   // an empty history for this solve
+        e = cudaMemsetAsync(p->aa_state, 0, sizeof(AAState), p->stream);
+        if (e != cudaSuccess) return e;
+    }
     const int n = 4 * p->ncells, g = (n + 255) / 256;
     if (p->prec == HYB_FP64)
         sn_seed_kernel<double><<<g, 256, 0, p->stream>>>(p->sn_phi_d, (double*)p->sn_phi_old, n, p->st);

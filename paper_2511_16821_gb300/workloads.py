@@ -52,6 +52,7 @@ class ProblemSpec:
     sn_max_iter: int = 500
     sn_warm_start: int = 0
     census_order: int = 0
+    sn_accel: int = 0
     name: str = field(default="problem")
 
     @property

@@ -397,3 +397,30 @@ def test_ns_infinity_pure_mc(H, orc, order):
             f = P.tally("flux")
             assert np.allclose(f, r["flux"], rtol=1e-9, atol=1e-12 * np.max(np.abs(r["flux"]))), (spec.name, k)
         P.close()
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32])
+def test_collided_solve_anderson(H, orc, prec):
+    """Anderson-accelerated source iteration on a diffusive problem (effective scattering ratio
+    ~0.9): the same fixed point as the oracle's plain iteration, in fewer sweeps."""
+    base = W.checkerboard(n_s=1, n_hist=20_000, cells_per_block=4)
+    spec = base.with_(sigma_a=base.sigma_a * 10, sigma_s=base.sigma_s * 10, dt=1.0, sn_order=4,
+                      precision=prec, sn_tol=1e-12 if prec == W.FP64 else 1e-7, sn_max_iter=2000)
+    bank = W.random_bank(spec, 4000, seed=9)
+    g = gpu_leg(H, spec, bank, 0)
+    phi_o, it_o = orc.sn_solve(spec.with_(precision=W.FP64, sn_tol=1e-13, sn_max_iter=5000), g["mom"])
+    iters = {}
+    for depth in (0, 4):
+        P = H.Problem(spec.with_(sn_accel=depth, ic=None))
+        P.set_bank(bank)
+        P.set_step(0)
+        P.mc_leg()
+        st = P.collided_solve()
+        iters[depth] = st["sn_iterations"]
+        phi_g = P.tally("sn_phi")
+        scale = np.max(np.abs(phi_o[:, 0]))
+        tol = 1e-8 if prec == W.FP64 else 2e-4
+        assert np.allclose(phi_g, phi_o, rtol=0, atol=tol * scale), (depth, np.max(np.abs(phi_g - phi_o)) / scale)
+        P.close()
+    print(f"\nSI iterations plain {iters[0]} (oracle {it_o}), Anderson(4) {iters[4]}")
+    assert iters[4] < iters[0] / 2
