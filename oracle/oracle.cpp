@@ -185,13 +185,47 @@ uint32_t sobol_int(int d, uint64_t i) {
     return x;
 }
 
+// ------------------------------------------------------------------------------------------
+// Halton points (the paper's QMC, Sec. 2.4). Coordinate d of point i is the radical inverse of
+// i in the d-th prime base b: for i = sum_k a_k b^k (digits 0 <= a_k < b, K of them),
+// phi_b(i) = sum_k a_k b^-(k+1) = R / b^K with R the digits read in reverse. It is kept as the
+// 32-bit fixed-point value floor(2^32 phi_b(i)), formed exactly in 128-bit integers. A replica
+// is randomised by a shift modulo 1 (Cranley & Patterson 1976) of that value by the same
+// per-(key, dimension) 32-bit hash the Sobol sets use as their digital shift.
+// ------------------------------------------------------------------------------------------
+uint32_t g_prime[kDimMax];
+bool g_prime_ready = false;
+
+void build_primes() {
+    if (g_prime_ready) return;
+    int n = 0;
+    for (uint32_t c = 2; n < kDimMax; ++c) {
+        bool prime = true;
+        for (uint32_t q = 2; q * q <= c; ++q)
+            if (c % q == 0) { prime = false; break; }
+        if (prime) g_prime[n++] = c;
+    }
+    g_prime_ready = true;
+}
+
+uint32_t halton_int(int d, uint64_t i) {
+    const uint64_t b = g_prime[d];
+    unsigned __int128 R = 0, D = 1;
+    for (uint64_t n = i; n > 0; n /= b) {
+        R = R * b + n % b;
+        D *= b;
+    }
+    return (uint32_t)((R << 32) / D);
+}
+
 // One point coordinate as a 32-bit integer (Sec. 2.4: the low-discrepancy points replace the
-// pseudorandom draws inside the same maps). Sobol + digital shift, or the counter PRNG.
-// Sobol dimensions beyond the table fall back to the counter PRNG.
+// pseudorandom draws inside the same maps). Sobol + digital shift, Halton + shift modulo 1, or
+// the counter PRNG. Dimensions beyond the tables fall back to the counter PRNG.
 struct Points {
     uint64_t key; int sampler;
     uint32_t operator()(uint64_t i, int d) const {
         if (sampler == 0 && d < kDimMax) return sobol_int(d, i) ^ digital_shift(key, (uint64_t)d);
+        if (sampler == 2 && d < kDimMax) return halton_int(d, i) + digital_shift(key, (uint64_t)d);
         return prng_int(key, i, (uint64_t)d);
     }
 };
@@ -214,7 +248,7 @@ typedef struct {
     const double* Q;        // nx*ny emission rate density, may be NULL
     double c, dt;
     int32_t n_s;            // N_s, kNsInf = unlimited
-    int32_t sampler;        // 0 Sobol + digital shift, 1 counter PRNG
+    int32_t sampler;        // 0 Sobol + digital shift, 1 counter PRNG, 2 Halton + shift modulo 1
     int64_t n_hist;         // births per step (MC-leg source and remap source)
     uint64_t seed;
     int32_t sn_order;       // 4 or 8
@@ -861,6 +895,7 @@ void or_neg_log(const double* u, int64_t n, double* out) {
 int or_sobol_table(int ndims, uint32_t* V) {
     if (ndims < 1 || ndims > kDimMax) return 1;
     build_sobol_table();
+    build_primes();
     for (int d = 0; d < ndims; ++d) for (int b = 0; b < 32; ++b) V[d * 32 + b] = g_V[d][b];
     return 0;
 }
@@ -870,6 +905,7 @@ int or_points(uint64_t seed, int64_t step, int32_t stream, int32_t sampler, int6
               int32_t ndims, uint32_t* out) {
     if (i0 < 0 || n < 0 || i0 + n > (int64_t)1 << 32) return 1;
     build_sobol_table();
+    build_primes();
     Points pts{stream_key(seed, (uint64_t)step, (uint64_t)stream), sampler};
     for (int64_t i = 0; i < n; ++i)
         for (int d = 0; d < ndims; ++d) out[i * ndims + d] = pts((uint64_t)(i0 + i), d);
@@ -899,6 +935,7 @@ int or_quadrature(int order, double* ox, double* oy, double* oz, double* w) {
 // uniform in each cell and isotropic, at t = 0 (stream INIT, dims 0-1 position, 3-4 direction).
 int or_init_bank(const or_problem* P, const double* ic_cell_w, or_bank* out) {
     build_sobol_table();
+    build_primes();
     Mesh M(P);
     const size_t nc = (size_t)M.nx * M.ny;
     std::vector<double> w(ic_cell_w, ic_cell_w + nc);
@@ -924,6 +961,7 @@ int or_init_bank(const or_problem* P, const double* ic_cell_w, or_bank* out) {
 int or_sample_births(const or_problem* P, int64_t step, int64_t n, int32_t* cell, double* fx,
                      double* fy, double* ox, double* oy, double* t_frac, double* w0_out) {
     build_sobol_table();
+    build_primes();
     Mesh M(P);
     const size_t nc = (size_t)M.nx * M.ny;
     std::vector<double> q(nc, 0.0);
@@ -978,6 +1016,7 @@ static int leg_range(const or_problem* P, int64_t step, const or_bank* census, i
                      double* post, double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n,
                      int64_t* post_n) {
     build_sobol_table();
+    build_primes();
     Leg L(P);
     const Mesh& M = L.M;
     const size_t nc = (size_t)M.nx * M.ny;
@@ -1059,6 +1098,7 @@ void or_remap_density(const or_problem* P, const double* pre, const double* post
 int or_remap(const or_problem* P, int64_t step, const or_bank* census, const double* pre,
              const double* post, const double* phi, or_bank* out, or_stats* st, int32_t* combed) {
     build_sobol_table();
+    build_primes();
     Mesh M(P);
     const size_t nc = (size_t)M.nx * M.ny;
     if (st) std::memset(st, 0, sizeof(*st));

@@ -167,3 +167,107 @@ def test_direction_and_depth_maps_accuracy(orc):
         assert abs(c[i] - float(mpmath.cos(a))) < 3e-16
         ref = -mpmath.log(mpmath.mpf(float(u[i])))
         assert abs(t[i] - float(ref)) <= 3e-16 * abs(float(ref))
+
+
+# ---------------------------------------------------------------------------------------------
+# Halton points with a shift modulo 1 (sampler 2)
+# ---------------------------------------------------------------------------------------------
+HALTON = 2
+
+
+def _primes(n):
+    out, c = [], 2
+    while len(out) < n:
+        if all(c % q for q in range(2, int(math.isqrt(c)) + 1)):
+            out.append(c)
+        c += 1
+    return out
+
+
+def _unshifted(orc, i0, n, ndims, seed=1, step=0, stream=0):
+    """Halton coordinates minus the shift: point 0 is the origin, so its value is the shift."""
+    u = orc.points(seed, step, stream, HALTON, i0, n, ndims).astype(np.int64)
+    s = orc.points(seed, step, stream, HALTON, 0, 1, ndims).astype(np.int64)[0]
+    return (u - s) % 2 ** 32
+
+
+def test_halton_primes():
+    p = _primes(65)
+    assert p[:10] == [2, 3, 5, 7, 11, 13, 17, 19, 23, 29] and p[64] == 313   # the 65th prime is 313
+
+
+def test_halton_radical_inverse_exact(orc):
+    """floor(2^32 phi_b(i)) against the radical inverse in exact rational arithmetic."""
+    from fractions import Fraction
+    primes = _primes(65)
+    dims = [0, 1, 2, 5, 17, 40, 64]
+    idx = list(range(0, 300)) + [4095, 4096, 59049, 12345678, 2 ** 31 - 1, 2 ** 32 - 1]
+    for i in idx:
+        got = _unshifted(orc, i, 1, 65)[0]
+        for d in dims:
+            b, n, phi, k = primes[d], i, Fraction(0), 1
+            while n:
+                phi += Fraction(n % b, b ** k)
+                n //= b
+                k += 1
+            assert got[d] == math.floor(phi * 2 ** 32), (i, d)
+
+
+def test_halton_matches_scipy_unscrambled(orc):
+    """The unscrambled Halton sequence of scipy.stats.qmc (index 0 first) to within FP64 rounding."""
+    qmc = pytest.importorskip("scipy.stats.qmc")
+    ref = qmc.Halton(d=65, scramble=False).random(2048)
+    got = _unshifted(orc, 0, 2048, 65) / 2.0 ** 32
+    assert np.max(np.abs(got - ref)) < 2.0 ** -31
+
+
+@pytest.mark.parametrize("d", [0, 1, 2, 3, 6, 20, 64])
+def test_halton_first_b_to_the_k_points_are_a_grid(orc, d):
+    """Van der Corput in base b: points 0 .. b^k - 1 are the grid {j / b^k} in some order."""
+    b = _primes(65)[d]
+    k = 1
+    while b ** (k + 1) <= 4096:
+        k += 1
+    m = b ** k
+    u = np.sort(_unshifted(orc, 0, m, 65)[:, d])
+    assert np.array_equal(u, [(j << 32) // m for j in range(m)])
+
+
+def test_halton_shift_is_modular_and_shared(orc):
+    """The randomisation adds one 32-bit value per dimension modulo 2^32 (the same value as the
+    Sobol set's digital shift of that point set), so differences between points do not depend on
+    the seed."""
+    a = _unshifted(orc, 0, 512, 65, seed=3)
+    b = _unshifted(orc, 0, 512, 65, seed=99, step=7, stream=2)
+    assert np.array_equal(a, b)
+    for seed, step, stream in ((3, 0, 0), (99, 7, 2)):
+        h0 = orc.points(seed, step, stream, HALTON, 0, 1, 65)[0]
+        s0 = orc.points(seed, step, stream, 0, 0, 1, 65)[0]
+        assert np.array_equal(h0, s0)
+    # past the 65 tabulated dimensions both fall back to the counter PRNG
+    assert np.array_equal(orc.points(5, 1, 1, HALTON, 10, 50, 70)[:, 65:], orc.points(5, 1, 1, 1, 10, 50, 70)[:, 65:])
+
+
+def test_halton_planted_mistakes_fail():
+    """The exact-rational check separates the radical inverse from its usual slips (digits read in
+    the wrong order, a dropped digit, the wrong base)."""
+    from fractions import Fraction
+
+    def phi(i, b):
+        r, n, k = Fraction(0), i, 1
+        while n:
+            r += Fraction(n % b, b ** k)
+            n //= b
+            k += 1
+        return r
+
+    def forward_digits(i, b):      # digits not reversed
+        ds = []
+        while i:
+            ds.append(i % b)
+            i //= b
+        return sum(Fraction(a, b ** (len(ds) - j)) for j, a in enumerate(ds))
+
+    assert any(phi(i, 3) != forward_digits(i, 3) for i in range(1, 30))
+    assert any(phi(i, 5) != phi(i, 7) for i in range(1, 30))
+    assert any(phi(i, 3) != phi(i // 3, 3) for i in range(1, 30))
