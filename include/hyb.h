@@ -11,8 +11,9 @@
  *   3. Remap, Eq. (R): scatter-free re-streaming of the step-start particles plus new births from
  *      Q + sigma_s (phi_pre + phi_post + phi_c), attenuated with sigma_t.
  *   4. The survivors (combed to census_cap) become the census of t_{n+1}.
- * Points are Sobol with a per-(seed, step, stream, dimension) digital shift, or a counter PRNG
- * (Sec. 2.4 replaces pseudorandom draws with low-discrepancy points inside the same maps).
+ * Points are Sobol with a per-(seed, step, stream, dimension) digital shift, Halton with a
+ * per-(seed, step, stream, dimension) shift modulo 1, or a counter PRNG (Sec. 2.4 replaces
+ * pseudorandom draws with low-discrepancy points inside the same maps).
  *
  * Conventions (all entry points):
  *   - Every function returns hyb_status and never throws. Pointers are plain host or device
@@ -52,7 +53,10 @@ typedef enum {
 } hyb_status;
 
 typedef enum { HYB_FP32 = 0, HYB_FP64 = 1 } hyb_precision;
-typedef enum { HYB_SOBOL_DS = 0, HYB_PRNG = 1 } hyb_sampler;
+/* HYB_SOBOL_DS: Sobol, XOR of a 32-bit digital shift. HYB_HALTON: Halton (Sec. 2.4), coordinate d
+ * = floor(2^32 phi_b(i)) + shift mod 2^32, phi_b the radical inverse in the d-th prime base b.
+ * HYB_PRNG: the counter hash. Both QMC sets use the counter hash past HYB_SOBOL_DIMS dims. */
+typedef enum { HYB_SOBOL_DS = 0, HYB_PRNG = 1, HYB_HALTON = 2 } hyb_sampler;
 
 /* N_s = infinity: pure (Q)MC, no hand-off, no collided solve, no remap (the MC-leg census is
  * the next bank); Sec. 3 non-hybrid runs. */
@@ -65,7 +69,7 @@ typedef enum { HYB_SOBOL_DS = 0, HYB_PRNG = 1 } hyb_sampler;
 #define HYB_STREAM_REMAP_SOURCE 3  /* remap births */
 #define HYB_STREAM_REMAP_COMB 4    /* census comb offset (index 0, dim 0) */
 
-/* Largest tabulated Sobol dimension count; dims >= this use the counter PRNG. */
+/* Largest tabulated QMC dimension count (Sobol and Halton); dims >= this use the counter PRNG. */
 #define HYB_SOBOL_DIMS 65
 
 /* Problem descriptor (Sec. 2.1: mesh, sigma_a, sigma_s, c, Q, initial data; Sec. 2.2: dt;
@@ -195,7 +199,7 @@ HYB_API hyb_status hyb_set_step(hyb_problem* p, int64_t step);
 HYB_API hyb_status hyb_get_step(const hyb_problem* p, int64_t* step);
 
 /* Point sets (Sec. 2.4): out_dev[(i - i0)*ndims + d] for i in [i0, i0+n), d < ndims, as 32-bit
- * integers; i0 + n <= 2^32. Asynchronous on cuda_stream. */
+ * integers; i0 + n <= 2^32; sampler a hyb_sampler. Asynchronous on cuda_stream. */
 HYB_API hyb_status hyb_points(uint64_t seed, int64_t step, int32_t stream_id, int32_t sampler, int64_t i0,
                       int64_t n, int32_t ndims, uint32_t* out_dev, void* cuda_stream);
 
@@ -206,7 +210,8 @@ HYB_API hyb_status hyb_points(uint64_t seed, int64_t step, int32_t stream_id, in
  * alone (bit-identical integers and tallies). Problems must share one precision, be at a step
  * boundary, and not be stepped individually while the batch exists (the batch owns their
  * stream use). Source iteration runs up to a per-problem cap inside the graph and stops on a
- * device flag; a problem that reaches its cap gets a doubled cap from the next step on. */
+ * device flag; a problem that reaches its cap gets a doubled cap from the next step on. Batched
+ * problems use Sobol or PRNG points (HYB_HALTON returns HYB_EINVAL). */
 typedef struct hyb_batch hyb_batch;
 typedef struct {
     int32_t block;        /* threads per CTA of the batched MC leg: 128 or 256 */

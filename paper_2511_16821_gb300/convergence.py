@@ -3,7 +3,8 @@
 The paper compares the error of the hybrid's scalar flux against the particle count for Halton
 points and pseudorandom numbers and fits err ~ c N^alpha (Sec. 3, Table 1: alpha near -0.5 for
 MC and -0.6 to -0.7 for QMC). Here the same study runs on a synthetic heterogeneous problem with
-Sobol points under a digital shift and with the counter PRNG: for every history count N and seed
+Sobol points under a digital shift, Halton points under a shift modulo 1 and the counter PRNG:
+for every history count N and seed
 the hybrid advances `steps` time steps, and the error is the relative L2 norm, over cells, of the
 end-of-step scalar flux (MC pre + post tallies and the collided S_N flux) against a reference
 computed with many more histories (the mean over a few Sobol shifts). The error at each N is the
@@ -54,7 +55,7 @@ def study(log2_n=range(10, 21), seeds=range(16), steps: int = 4, ref_log2: int =
     out = {"workload": mk(1, 0, W.SOBOL).name, "steps": steps, "reference_histories": 1 << ref_log2,
            "reference_shifts": len(list(ref_seeds)), "seeds": len(list(seeds)), "metric": "relative L2 error of the "
            "end-of-step scalar flux, RMS over seeds"}
-    for name, sampler in (("sobol", W.SOBOL), ("prng", W.PRNG)):
+    for name, sampler in (("sobol", W.SOBOL), ("halton", W.HALTON), ("prng", W.PRNG)):
         ns, errs = [], []
         for k in log2_n:
             n = 1 << k
@@ -70,7 +71,8 @@ def ns_sweep(n_s_values=(0, 1, 2, 5, 10, 20, W.NS_INF), log2_n=range(10, 19, 2),
              ref_log2: int = 22, ref_seeds=range(100, 104), sigma_scale: float = 1.0) -> list:
     """The analogue of the paper's Table 1 on the synthetic problem: for each scatter limit N_s,
     the source iterations of the collided solve (from zero, stop at 1e-6 relative change) and the
-    convergence rates alpha of one step's flux error with Sobol points and with the counter PRNG.
+    convergence rates alpha of one step's flux error with Sobol points, Halton points and the
+    counter PRNG.
     N_s = infinity is the pure (Q)MC method (no collided stage)."""
     import torch
     rows = []
@@ -80,8 +82,9 @@ def ns_sweep(n_s_values=(0, 1, 2, 5, 10, 20, W.NS_INF), log2_n=range(10, 19, 2),
         r = study(log2_n=log2_n, seeds=seeds, steps=1, ref_log2=ref_log2, ref_seeds=ref_seeds, n_s=n_s,
                   sigma_scale=sigma_scale)
         rows.append({"n_s": "inf" if n_s == W.NS_INF else n_s, "sn_iterations": st["sn_iterations"],
-                     "alpha_sobol": r["sobol"]["alpha"], "alpha_prng": r["prng"]["alpha"],
-                     "err_sobol": r["sobol"]["err"][-1], "err_prng": r["prng"]["err"][-1],
+                     "alpha_sobol": r["sobol"]["alpha"], "alpha_halton": r["halton"]["alpha"],
+                     "alpha_prng": r["prng"]["alpha"], "err_sobol": r["sobol"]["err"][-1],
+                     "err_halton": r["halton"]["err"][-1], "err_prng": r["prng"]["err"][-1],
                      "n_max": r["sobol"]["n"][-1], "workload": r["workload"]})
     torch.cuda.synchronize()
     return rows

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "hyb_device.cuh"
@@ -252,6 +253,7 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         if (!p || p->prec != prec) return bfail(b, HYB_EINVAL, "problems must share one precision");
         if (p->leg_done) return bfail(b, HYB_ESTATE, "problems must be at a step boundary");
         if (p->d.n_s == HYB_NS_INF) return bfail(b, HYB_EINVAL, "N_s = infinity problems are stepped alone");
+        if (p->d.sampler == HYB_HALTON) return bfail(b, HYB_EINVAL, "Halton problems are stepped alone");
         probs.push_back(p);
     }
     if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");
@@ -307,9 +309,9 @@ HYB_API hyb_status hyb_batch_create(hyb_problem* const* problems, int32_t n, voi
         }
         b->own_s0 = true;
     }
-    auto fail_all = [&](hyb_status s, const std::string& m) {
+    auto fail_all = [&](hyb_status s, std::string m) {   // m by value: it may be b->err
         hyb_batch_destroy(b);
-        g_batch_err = m;
+        g_batch_err = std::move(m);
         return s;
     };
     if (cudaMalloc(&b->d_head, 2 * sizeof(int)) != cudaSuccess) return fail_all(HYB_ENOMEM, "queue heads");

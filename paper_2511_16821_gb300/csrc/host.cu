@@ -120,6 +120,65 @@ const uint32_t* sobol_table_host() {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Halton tables: per dimension d (prime base b, the d-th prime), kHaltonWords words: b, B = b^m
+// (largest power of b not above 256), m, floor(2^32 / B), 2^32 mod B, ceil(2^64 / B) as two words,
+// the bits per packed base-B chunk, then for m > 1 the reversal of m base-b digits as B bytes.
+// ---------------------------------------------------------------------------------------------
+namespace haltongen {
+
+uint32_t g_tab[HYB_SOBOL_DIMS][kHaltonWords];
+std::once_flag g_once;
+
+void build_table() {
+    uint32_t b = 1;
+    for (int d = 0; d < HYB_SOBOL_DIMS; ++d) {
+        bool prime;
+        do {
+            ++b;
+            prime = true;
+            for (uint32_t q = 2; q * q <= b; ++q)
+                if (b % q == 0) { prime = false; break; }
+        } while (!prime);
+        uint32_t B = b, m = 1;
+        while (B * b <= 256u) { B *= b; ++m; }
+        const uint64_t two32 = 1ull << 32;
+        const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+        const uint64_t c = (uint64_t)((two64 + B - 1) / B);
+        uint32_t* t = g_tab[d];
+        std::memset(t, 0, sizeof(g_tab[d]));
+        t[0] = b; t[1] = B; t[2] = m;
+        t[3] = (uint32_t)(two32 / B); t[4] = (uint32_t)(two32 % B);
+        t[5] = (uint32_t)c; t[6] = (uint32_t)(c >> 32);
+        t[7] = B > 256u ? 9u : 8u;
+        if (m > 1) {
+            unsigned char* rv = reinterpret_cast<unsigned char*>(t + 8);
+            for (uint32_t v = 0; v < B; ++v) {
+                uint32_t r = 0, x = v;
+                for (uint32_t k = 0; k < m; ++k) { r = r * b + x % b; x /= b; }
+                rv[v] = (unsigned char)r;
+            }
+        }
+    }
+}
+
+}  // namespace haltongen
+
+const uint32_t* halton_table_host() {
+    std::call_once(haltongen::g_once, haltongen::build_table);
+    return &haltongen::g_tab[0][0];
+}
+
+// the point table a problem uploads for its sampler (Sobol direction numbers or Halton tables)
+static const uint32_t* point_table_host(int sampler, size_t* bytes) {
+    if (sampler == HYB_HALTON) {
+        *bytes = (size_t)HYB_SOBOL_DIMS * kHaltonWords * 4;
+        return halton_table_host();
+    }
+    *bytes = (size_t)HYB_SOBOL_DIMS * 32 * 4;
+    return sobol_table_host();
+}
+
+// ---------------------------------------------------------------------------------------------
 // level-symmetric quadrature (upper hemisphere; weights summing to 4 pi)
 // ---------------------------------------------------------------------------------------------
 void quadrature_host(int order, double* ox, double* oy, double* w, int* m_out) {
@@ -221,7 +280,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     const int nord = d->sn_order == 8 ? 40 : 12;
     z.cap = eff_cap(d);
     z.st = sizeof(DevState);
-    z.sobol = HYB_SOBOL_DIMS * 32 * 4;
+    z.sobol = HYB_SOBOL_DIMS * kHaltonWords * 4;  // the larger of the two point tables
     z.sig = nc * 2 * T;
     z.sa = z.ss = z.Q = nc * 8;
     z.cdf_q = nc * 8;
@@ -241,7 +300,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.sntx = (size_t)nord * nc * 4 * T;           // w_m psi_m per ordinate and cell
     z.snty = (size_t)nord * d->nx * 2 * T;        // strip-top traces per ordinate
     z.snqb = 3 * kMaxOrd * T;
-    z.snnorm = 10 * ((nc + 31) / 32) * 8;         // per reduction block (32 cells): up to kAAMax + 2 sums
+    z.snnorm = hyb::sn_norm_bytes((int)nc);       // reduction partials per block and group, group counters
     z.nblk = (z.cap + d->n_hist + 2047) / 2048;
     z.blk = 4 * (size_t)z.nblk * 8;
     z.gr = hyb::guide_bits(d->ny);
@@ -277,7 +336,7 @@ void assign(hyb_problem* p) {
     char* b = (char*)p->ws;
     auto take = [&](size_t bytes) { return (void*)(b + L.add(bytes)); };
     p->st = (DevState*)take(z.st);
-    p->sobolV = (uint32_t*)take(z.sobol);
+    p->point_tab = (uint32_t*)take(z.sobol);
     p->sig = take(z.sig);
     p->sa_d = (double*)take(z.sa);
     p->ss_d = (double*)take(z.ss);
@@ -354,7 +413,10 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->n_s != HYB_NS_INF && d->n_s > (1 << 20)) { *why = "N_s must be <= 2^20 or HYB_NS_INF"; return HYB_EINVAL; }
     if (d->n_hist < 1 || d->n_hist >= (int64_t)1 << 31) { *why = "n_hist must be in [1, 2^31)"; return HYB_EINVAL; }
     if (d->census_cap < 0 || d->census_cap >= (int64_t)1 << 31) { *why = "census_cap must be in [0, 2^31)"; return HYB_EINVAL; }
-    if (d->sampler != HYB_SOBOL_DS && d->sampler != HYB_PRNG) { *why = "unknown sampler"; return HYB_EINVAL; }
+    if (d->sampler != HYB_SOBOL_DS && d->sampler != HYB_PRNG && d->sampler != HYB_HALTON) {
+        *why = "unknown sampler";
+        return HYB_EINVAL;
+    }
     if (d->precision != HYB_FP32 && d->precision != HYB_FP64) { *why = "unknown precision"; return HYB_EINVAL; }
     if (d->sn_order != 4 && d->sn_order != 8) { *why = "sn_order must be 4 or 8"; return HYB_EINVAL; }
     if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
@@ -575,7 +637,9 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     cudaStream_t st = p->stream;
     auto chk = [&](cudaError_t e, const char* w) { return e == cudaSuccess ? HYB_OK : cuda_fail(p, e, w); };
     if (chk(cudaMemsetAsync(p->st, 0, sizeof(DevState), st), "memset state") != HYB_OK) return bail(HYB_ECUDA);
-    if (chk(cudaMemcpyAsync(p->sobolV, sobol_table_host(), HYB_SOBOL_DIMS * 32 * 4, cudaMemcpyHostToDevice, st), "copy sobol") != HYB_OK) return bail(HYB_ECUDA);
+    size_t ptab_bytes = 0;
+    const uint32_t* ptab = point_table_host(d->sampler, &ptab_bytes);
+    if (chk(cudaMemcpyAsync(p->point_tab, ptab, ptab_bytes, cudaMemcpyHostToDevice, st), "copy point table") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->sig, sig.data(), sig.size(), cudaMemcpyHostToDevice, st), "copy sigma") != HYB_OK) return bail(HYB_ECUDA);
     // FP32 path: per-cell reciprocals (1/sigma_a, 1/sigma_s, 1/sigma_t, 0), 0 where the cross section is 0
     std::vector<float> sinv(4 * nc, 0.0f);
@@ -590,6 +654,7 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     if (chk(cudaMemcpyAsync(p->ss_d, d->sigma_s, nc * 8, cudaMemcpyHostToDevice, st), "copy ss") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->Q_d, d->Q ? d->Q : zeros.data(), nc * 8, cudaMemcpyHostToDevice, st), "copy Q") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemsetAsync(p->sn_phi_d, 0, 4 * nc * 8, st), "memset phi") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(sn_clear_counters(p), "memset reduction counters") != HYB_OK) return bail(HYB_ECUDA);
     // quadrature
     p->n_ord = 0;
     quadrature_host(d->sn_order, p->quad_ox, p->quad_oy, p->quad_w, &p->n_ord);
@@ -924,21 +989,24 @@ hyb_status hyb_build_cdf(const double* w_dev, int32_t nx, int32_t ny, int64_t* q
 hyb_status hyb_points(uint64_t seed, int64_t step, int32_t stream_id, int32_t sampler, int64_t i0, int64_t n,
                       int32_t ndims, uint32_t* out_dev, void* cuda_stream) {
     if (i0 < 0 || n < 0 || i0 + n > ((int64_t)1 << 32) || ndims < 1 || ndims > 1024 || !out_dev ||
-        (sampler != HYB_SOBOL_DS && sampler != HYB_PRNG))
+        (sampler != HYB_SOBOL_DS && sampler != HYB_PRNG && sampler != HYB_HALTON))
         return fail(nullptr, HYB_EINVAL, "bad point-set arguments");
     if (n == 0) return HYB_OK;
-    static uint32_t* dev_tab[64] = {nullptr};
+    static uint32_t* dev_tab[2][64] = {{nullptr}};   // Sobol, Halton tables per device
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return fail(nullptr, HYB_EINVAL, "device index");
-    if (!dev_tab[dev]) {
-        cudaError_t e = cudaMalloc(&dev_tab[dev], HYB_SOBOL_DIMS * 32 * 4);
+    const int h = sampler == HYB_HALTON ? 1 : 0;
+    if (!dev_tab[h][dev]) {
+        size_t bytes = 0;
+        const uint32_t* tab = point_table_host(sampler, &bytes);
+        cudaError_t e = cudaMalloc(&dev_tab[h][dev], bytes);
         if (e != cudaSuccess) return fail(nullptr, HYB_ENOMEM, "table alloc");
-        e = cudaMemcpy(dev_tab[dev], sobol_table_host(), HYB_SOBOL_DIMS * 32 * 4, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(dev_tab[h][dev], tab, bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(nullptr, HYB_ECUDA, cudaGetErrorString(e));
     }
     const uint64_t key = stream_key(seed, (uint64_t)step, (uint64_t)stream_id);
-    cudaError_t e = launch_points(key, sampler, dev_tab[dev], i0, n, ndims, out_dev, (cudaStream_t)cuda_stream);
+    cudaError_t e = launch_points(key, sampler, dev_tab[h][dev], i0, n, ndims, out_dev, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) return fail(nullptr, HYB_ECUDA, cudaGetErrorString(e));
     return HYB_OK;
 }

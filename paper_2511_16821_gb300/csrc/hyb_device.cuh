@@ -71,9 +71,10 @@ __host__ __device__ __forceinline__ uint64_t dstream_key(uint64_t seed, uint64_t
     return dmix64(z ^ (stream + kGamma));
 }
 
-// first point of a set (index 0, dimension 0): Sobol(0) = 0 leaves the shift; else the hash
+// first point of a set (index 0, dimension 0): Sobol(0) = Halton(0) = 0 leaves the shift; else
+// the hash
 __host__ __device__ __forceinline__ uint32_t first_point(uint64_t key, int sampler) {
-    return sampler == HYB_SOBOL_DS ? dshift(key, 0)
+    return sampler != HYB_PRNG ? dshift(key, 0)
                                    : (uint32_t)(dmix64(dmix64(key ^ (0ull + kGamma)) ^ (0ull + kGamma)) >> 32);
 }
 
@@ -82,6 +83,7 @@ __host__ __device__ __forceinline__ uint32_t first_point(uint64_t key, int sampl
 // then eight table reads whatever the index, and the 16 entries of one nibble table sit in 16
 // distinct shared-memory banks, so a warp's reads never conflict.
 constexpr int kNibbleWords = 128;   // 8 nibbles x 16 entries per dimension
+static_assert(kNibbleWords == kHaltonWords, "Sobol and Halton tables share the per-dimension stride");
 
 // builds the tables of dimensions [0, ntab) from the direction numbers V (ntab x 32) into sNT
 // (ntab x kNibbleWords); all threads of the block call it, the caller synchronises
@@ -97,8 +99,62 @@ __device__ __forceinline__ void build_nibble_tables(const uint32_t* __restrict__
     }
 }
 
-// A point set in shared memory: Sobol nibble tables (ntab dims) and per-dimension digital shifts;
-// dimensions beyond the table (or sampler == PRNG) use the counter hash.
+// the shared-memory tables of a point set: Sobol nibble tables built from the direction numbers,
+// or the Halton tables copied as they are (tab: the problem's point table, ntab x 32 Sobol
+// direction numbers or ntab x kNibbleWords Halton words)
+__device__ __forceinline__ void build_point_tables(const uint32_t* __restrict__ tab, int ntab, uint32_t* sNT,
+                                                   int sampler) {
+    if (sampler == HYB_HALTON) {
+        for (int e = threadIdx.x; e < ntab * kNibbleWords; e += blockDim.x) sNT[e] = __ldg(tab + e);
+    } else if (sampler == HYB_SOBOL_DS) {
+        build_nibble_tables(tab, ntab, sNT);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Halton coordinates. Dimension d uses the d-th prime b; the radical inverse phi_b(i) is formed in
+// base B = b^m (the largest power of b up to 256, so m base-b digits per chunk): with i's base-B
+// chunks c_0 (least significant) .. c_{J-1} and C_j = c_j with its m base-b digits reversed,
+// phi = (C_0 + (C_1 + ... (C_{J-1})/B ...)/B)/B. The 32-bit value floor(2^32 phi) is built from the
+// innermost chunk outwards, u <- floor((C 2^32 + u) / B): the fraction dropped at each level is
+// below one and cannot change a later floor, so the result is exact. Divisions by B use the
+// direct-computation method of Lemire, Kaser and Kurz (2019): n / B = floor(c n / 2^64) for all
+// 32-bit n with c = ceil(2^64 / B).
+// Per-dimension table (kNibbleWords words): [0] b, [1] B, [2] m, [3] floor(2^32 / B),
+// [4] 2^32 mod B, [5..6] c (low, high), [7] bits per packed chunk, then the chunk reversal as
+// bytes (m > 1 only).
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t div_direct(uint32_t c_lo, uint32_t c_hi, uint32_t n) {
+    return (uint32_t)(((unsigned long long)c_hi * n + __umulhi(c_lo, n)) >> 32);
+}
+
+__device__ __forceinline__ uint32_t halton_u(const uint32_t* t, uint32_t i) {
+    if (t[0] == 2u) return __brev(i);   // base 2: the bit reversal is floor(2^32 phi_2(i))
+    const uint32_t B = t[1], QB = t[3], RB = t[4], c_lo = t[5], c_hi = t[6], fb = t[7];
+    const bool rev = t[2] > 1u;
+    const unsigned char* rv = reinterpret_cast<const unsigned char*>(t + 8);
+    unsigned long long pk = 0;   // chunks, least significant first, fb bits each
+    int J = 0;
+    for (uint32_t n = i; n != 0u; ++J) {
+        const uint32_t q = div_direct(c_lo, c_hi, n);
+        pk |= (unsigned long long)(n - q * B) << (fb * J);
+        n = q;
+    }
+    const uint32_t mask = (1u << fb) - 1u;
+    uint32_t u = 0;
+    for (int j = J - 1; j >= 0; --j) {
+        uint32_t C = (uint32_t)(pk >> (fb * j)) & mask;
+        if (rev) C = rv[C];
+        // floor((C 2^32 + u) / B) with 2^32 = QB B + RB and u = uq B + ur
+        const uint32_t uq = div_direct(c_lo, c_hi, u), ur = u - uq * B;
+        u = C * QB + uq + div_direct(c_lo, c_hi, C * RB + ur);
+    }
+    return u;
+}
+
+// A point set in shared memory: per-dimension tables of ntab dims (Sobol nibble tables or Halton
+// tables) and per-dimension shifts; dimensions beyond the table (or sampler == PRNG) use the
+// counter hash.
 struct Points {
     const uint32_t* NT;
     const uint32_t* shift;
@@ -117,6 +173,7 @@ struct Points {
             }
             return x;
         }
+        if (sampler == HYB_HALTON && d < ntab) return halton_u(NT + d * kNibbleWords, i) + shift[d];
         const uint64_t h = dmix64(key ^ ((uint64_t)i + kGamma));
         return (uint32_t)(dmix64(h ^ ((uint64_t)d + kGamma)) >> 32);
     }

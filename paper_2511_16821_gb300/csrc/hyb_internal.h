@@ -14,6 +14,7 @@ constexpr int kTile = 256;               // threads per block of the streaming k
 constexpr int64_t kMaxSegments = 1 << 20;
 constexpr int kFateLeaked = 0, kFateCensus = 1, kFateKilled = 2, kFateError = 3;
 constexpr int kMaxOrd = 40;              // S8 upper hemisphere
+constexpr int kHaltonWords = 128;        // words per dimension of the Halton tables
 constexpr int kCdfParts = 256;           // block partial sums of the CDF build
 constexpr uint64_t kGamma = 0x9e3779b97f4a7c15ULL;
 
@@ -110,7 +111,8 @@ struct hyb_problem {
     int last_sn_iters;
     std::string err;
     // device pointers (into ws)
-    uint32_t* sobolV;         // HYB_SOBOL_DIMS x 32
+    uint32_t* point_tab;      // Sobol direction numbers (HYB_SOBOL_DIMS x 32) or Halton tables
+                              // (HYB_SOBOL_DIMS x kHaltonWords), by the sampler
     void* sig;                // ncells x 2 (T): sigma_a, sigma_s
     float* sig_inv;           // ncells x 4: 1/sigma_a, 1/sigma_s, 1/sigma_t, 0 (FP32 leg; 0 where sigma = 0)
     double *sa_d, *ss_d, *Q_d;  // FP64 copies for the remap density
@@ -153,7 +155,9 @@ cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev);
 cudaError_t launch_leg_normalise(hyb_problem* p);
 cudaError_t launch_remap(hyb_problem* p);
 cudaError_t launch_census(hyb_problem* p);
-size_t sn_accel_state_bytes();               // device bytes of the Anderson state   // N_s = infinity: MC-leg census -> new bank
+size_t sn_accel_state_bytes();
+size_t sn_norm_bytes(int ncells);            // reduction scratch of the source iteration
+cudaError_t sn_clear_counters(hyb_problem* p);               // device bytes of the Anderson state   // N_s = infinity: MC-leg census -> new bank
 cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView cdf, double* W_out_dev,
                              double* qmax_out_dev);
 cudaError_t launch_flux(hyb_problem* p);
@@ -183,6 +187,7 @@ cudaError_t sn_finish(hyb_problem* p);
 uint64_t mix64(uint64_t z);
 uint64_t stream_key(uint64_t seed, uint64_t step, uint64_t stream);
 const uint32_t* sobol_table_host();
+const uint32_t* halton_table_host();          // HYB_SOBOL_DIMS x kHaltonWords
 void quadrature_host(int order, double* ox, double* oy, double* w, int* m);
 
 }  // namespace hyb

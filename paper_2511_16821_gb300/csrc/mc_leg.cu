@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
     const uint64_t step = (uint64_t)a.st->step;
     const uint64_t key_c = dstream_key(a.seed, step, HYB_STREAM_LEG_CENSUS);
     const uint64_t key_s = dstream_key(a.seed, step, HYB_STREAM_LEG_SOURCE);
-    build_nibble_tables(a.V, a.ntab, sV);
+    build_point_tables(a.V, a.ntab, sV, a.sampler);
     for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) {
         sShC[d] = dshift(key_c, (uint64_t)d);
         sShS[d] = dshift(key_s, (uint64_t)d);
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(kTile) mc_birth_kernel(LegArgs<T> a) {
     __shared__ uint32_t sSh[6];
     const int nt = a.ntab < 6 ? a.ntab : 6;
     const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_LEG_SOURCE);
-    build_nibble_tables(a.V, nt, sV);
+    build_point_tables(a.V, nt, sV, a.sampler);
     if (threadIdx.x < nt) sSh[threadIdx.x] = dshift(key, (uint64_t)threadIdx.x);
     __syncthreads();
     const Points pts{sV, sSh, key, a.sampler, nt};
@@ -590,7 +590,7 @@ __global__ void init_bank_kernel(BankView<T> b, Cdf2DView cdf, int nx, int ny, T
     __shared__ uint32_t sV[5 * kNibbleWords];
     __shared__ uint32_t sSh[5];
     const int nt = ntab < 5 ? ntab : 5;
-    build_nibble_tables(V, nt, sV);
+    build_point_tables(V, nt, sV, sampler);
     if (threadIdx.x < nt) sSh[threadIdx.x] = dshift(key, threadIdx.x);
     __syncthreads();
     Points pts{sV, sSh, key, sampler, nt};
@@ -650,7 +650,7 @@ __global__ void points_kernel(uint64_t key, int sampler, const uint32_t* V, long
     const int ntab = ndims < HYB_SOBOL_DIMS ? ndims : HYB_SOBOL_DIMS;
     uint32_t* sV = sm;
     uint32_t* sSh = sm + ntab * kNibbleWords;
-    build_nibble_tables(V, ntab, sV);
+    build_point_tables(V, ntab, sV, sampler);
     for (int d = threadIdx.x; d < ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
     __syncthreads();
     Points pts{sV, sSh, key, sampler, ntab};
@@ -700,7 +700,7 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.n_s = p->d.n_s; a.sampler = p->d.sampler; a.handoff_full = p->d.handoff_full;
     a.ntab = p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS;
     a.w_min = (T)p->d.w_min;
-    a.V = p->sobolV;
+    a.V = p->point_tab;
     a.seed = p->d.seed;
     a.bank = bank_view<T>(p, cur);
     a.births = birth_view<T>(p);
@@ -788,15 +788,15 @@ cudaError_t launch_leg_normalise(hyb_problem* p) {
 
 cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0) {
     const uint64_t key = stream_key(p->d.seed, 0, HYB_STREAM_INIT);
-    const int ntab = p->d.sampler == HYB_SOBOL_DS ? 5 : 0;
+    const int ntab = p->d.sampler != HYB_PRNG ? 5 : 0;
     const long long n = p->d.n_hist;
     const int g = stride_grid(n);
     if (p->prec == HYB_FP64)
         init_bank_kernel<double><<<g, kTile, 0, p->stream>>>(bank_view<double>(p, p->cur), cdf, p->nx, p->ny, p->dx,
-                                                             p->dy, n, w0, p->sobolV, ntab, p->d.sampler, key);
+                                                             p->dy, n, w0, p->point_tab, ntab, p->d.sampler, key);
     else
         init_bank_kernel<float><<<g, kTile, 0, p->stream>>>(bank_view<float>(p, p->cur), cdf, p->nx, p->ny,
-                                                            (float)p->dx, (float)p->dy, n, (float)w0, p->sobolV, ntab,
+                                                            (float)p->dx, (float)p->dy, n, (float)w0, p->point_tab, ntab,
                                                             p->d.sampler, key);
     return cudaGetLastError();
 }

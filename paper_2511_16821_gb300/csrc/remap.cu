@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     uint32_t* sV = sm;
     uint32_t* sSh = sm + a.ntab * kNibbleWords;
     const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_REMAP_SOURCE);
-    build_nibble_tables(a.V, a.ntab, sV);
+    build_point_tables(a.V, a.ntab, sV, a.sampler);
     for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
     __shared__ RemapScal s_rs;
     if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
@@ -801,8 +801,8 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.n_hist = p->d.n_hist;
     a.cap = p->d.census_cap > 0 ? p->d.census_cap : p->d.n_hist;
     if (a.cap > p->bank_cap) a.cap = p->bank_cap;
-    a.V = p->sobolV;
-    a.ntab = p->d.sampler == HYB_SOBOL_DS ? 5 : 0;
+    a.V = p->point_tab;
+    a.ntab = p->d.sampler != HYB_PRNG ? 5 : 0;
     a.sampler = p->d.sampler;
     a.seed = p->d.seed;
     a.st = p->st;

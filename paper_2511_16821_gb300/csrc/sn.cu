@@ -314,11 +314,89 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
 // ordinate solutions of cell c over ordinates g, g+8, ... (vector loads, coalesced across c); the
 // 8 partials of a cell are added in g order in shared memory, then thread (c, i) forms coefficient
 // i of phi_new, its contribution to the change norm and the next iteration's source integral i.
-// The block's norm partials go to part[]; the last block to finish (counter in the device state)
-// adds all partials in block order and applies the stop test
+// The block's norm partials go to part[]; reduce_partials (below) adds them in a fixed order in
+// the last block to finish, which applies the stop test
 //   ||phi_new - phi_old|| <= tol ||phi_new||   (or no source at all),
 // so the reduction and the test are one launch and the result does not depend on block order.
 constexpr int kRedCells = 32, kRedGroups = 8;
+constexpr int kRedThreads = kRedCells * kRedGroups;
+constexpr int kRedGroupBlocks = kRedThreads;   // blocks per group of the two-level completion
+
+// Sums NV values over the 256 threads of the block in a fixed tree (warp shuffles, then the 8 warp
+// sums in warp order); thread q < NV receives total q.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sw)[kRedThreads / 32], double* out) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+    if ((threadIdx.x & 31) == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) sw[q][threadIdx.x >> 5] = v[q];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double a = 0;
+        for (int w = 0; w < kRedThreads / 32; ++w) a += sw[threadIdx.x][w];
+        out[threadIdx.x] = a;
+    }
+}
+
+// Two-level completion of per-block partial sums, independent of the order in which blocks finish.
+// Block b has written its NV partials to part[b NV + q] (all threads call this after that).
+// Every kRedGroupBlocks consecutive blocks form a group; the last block of a group to arrive adds
+// the group's partials (one per thread, then block_sum) into gpart[g NV + q]; the last group to
+// arrive adds the group sums (a fixed sequence per thread, then block_sum) into s_tot. Returns
+// true in that one block, with the totals in s_tot (shared). The arrival counters gcnt[g] and
+// *top reset themselves. Partials are re-read with volatile loads after the writers' fences.
+template <int NV>
+__device__ bool reduce_partials(double* part, int nblk, double* gpart, unsigned* gcnt, unsigned* top,
+                                double* s_tot) {
+    __shared__ double sw[NV][kRedThreads / 32];
+    __shared__ bool s_go;
+    const int g = blockIdx.x / kRedGroupBlocks;
+    const int ngrp = (nblk + kRedGroupBlocks - 1) / kRedGroupBlocks;
+    const int b0 = g * kRedGroupBlocks;
+    const int gsize = nblk - b0 < kRedGroupBlocks ? nblk - b0 : kRedGroupBlocks;
+    __threadfence();   // every writer of part[] fences before the arrival
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_go = atomicAdd(&gcnt[g], 1u) == (unsigned)gsize - 1u;
+    }
+    __syncthreads();
+    if (!s_go) return false;
+    __threadfence();
+    double v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        v[q] = (int)threadIdx.x < gsize ? ((volatile double*)part)[(size_t)(b0 + threadIdx.x) * NV + q] : 0.0;
+    block_sum<NV>(v, sw, s_tot);
+    if (threadIdx.x < NV) gpart[(size_t)g * NV + threadIdx.x] = s_tot[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        gcnt[g] = 0u;
+        __threadfence();
+        s_go = atomicAdd(top, 1u) == (unsigned)ngrp - 1u;
+    }
+    __syncthreads();
+    if (!s_go) return false;
+    __threadfence();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0;
+    for (int j = threadIdx.x; j < ngrp; j += kRedThreads)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) v[q] += ((volatile double*)gpart)[(size_t)j * NV + q];
+    __syncthreads();
+    block_sum<NV>(v, sw, s_tot);
+    if (threadIdx.x == 0) *top = 0u;
+    __syncthreads();
+    return true;
+}
+
+// Scratch of the source-iteration reductions inside the sn_norm buffer: block partials (up to
+// kAAMax + 2 per block), group partials, group arrival counters.
+struct RedScratch {
+    double* part;
+    double* gpart;
+    unsigned* gcnt;
+};
 constexpr int kAAMax = 8;   // deepest Anderson history
 
 template <typename T> struct Vec4;
@@ -337,11 +415,11 @@ template <> struct Vec4<double> {
 
 template <typename T>
 __global__ void __launch_bounds__(kRedCells * kRedGroups)
-sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, double* part, const T* sig,
+sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, RedScratch rs, const T* sig,
                  const double* mom, T area, T inv_4pi_dt, T* src, DevState* st, double tol) {
     __shared__ T sp[kRedGroups][kRedCells][4];
     __shared__ double sred[2][kRedCells * 4 / 32];
-    __shared__ bool s_last;
+    __shared__ double s_tot[2];
     const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
     const int k0 = blockIdx.x * kRedCells;
     if (*(volatile const int*)&st->sn_conv) {
@@ -394,29 +472,16 @@ sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncell
     if (threadIdx.x == 0) {
         double a = 0, b = 0;
         for (int q = 0; q < kRedCells * 4 / 32; ++q) { a += sred[0][q]; b += sred[1][q]; }
-        part[2 * blockIdx.x] = a;
-        part[2 * blockIdx.x + 1] = b;
-        __threadfence();
-        const unsigned done = atomicAdd(&st->sn_blocks_done, 1u);
-        s_last = done == gridDim.x - 1;
+        rs.part[2 * blockIdx.x] = a;
+        rs.part[2 * blockIdx.x + 1] = b;
     }
-    __syncthreads();
-    if (s_last && threadIdx.x < 32) {
-        __threadfence();
-        double a = 0, b = 0;
-        for (int q = threadIdx.x; q < (int)gridDim.x; q += 32) {
-            a += ((volatile double*)part)[2 * q];
-            b += ((volatile double*)part)[2 * q + 1];
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        if (threadIdx.x == 0) {
-            st->sn_norm_num = a;
-            st->sn_norm_den = b;
-            st->sn_iters += 1;
-            if (b == 0.0 || sqrt(a) <= tol * sqrt(b)) st->sn_conv = 1;
-            st->sn_blocks_done = 0u;
-        }
+    if (reduce_partials<2>(rs.part, (int)gridDim.x, rs.gpart, rs.gcnt, &st->sn_blocks_done, s_tot) &&
+        threadIdx.x == 0) {
+        const double a = s_tot[0], b = s_tot[1];
+        st->sn_norm_num = a;
+        st->sn_norm_den = b;
+        st->sn_iters += 1;
+        if (b == 0.0 || sqrt(a) <= tol * sqrt(b)) st->sn_conv = 1;
     }
 }
 
@@ -480,11 +545,11 @@ __device__ void aa_solve(AAState* aa, const int* slots, int n) {
 // completes the Gram matrix, applies the stop test and, if the solve goes on, forms the weights.
 template <typename T>
 __global__ void __launch_bounds__(kRedCells * kRedGroups)
-sn_reduce_aa_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, double* part, T* g_hist,
+sn_reduce_aa_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, RedScratch rs, T* g_hist,
                     T* f_hist, int depth, AAState* aa, DevState* st, double tol) {
     __shared__ T sp[kRedGroups][kRedCells][4];
     __shared__ double sred[kAAPart][kRedCells * 4 / 32];
-    __shared__ bool s_last;
+    __shared__ double s_tot[kAAPart];
     const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
     const int k0 = blockIdx.x * kRedCells;
     if (*(volatile const int*)&st->sn_conv) {
@@ -550,42 +615,25 @@ sn_reduce_aa_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int nc
     if (threadIdx.x < kAAPart) {
         double a = 0;
         for (int w = 0; w < kRedCells * 4 / 32; ++w) a += sred[threadIdx.x][w];
-        part[(size_t)blockIdx.x * kAAPart + threadIdx.x] = a;
+        rs.part[(size_t)blockIdx.x * kAAPart + threadIdx.x] = a;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned done = atomicAdd(&st->sn_blocks_done, 1u);
-        s_last = done == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x < 32) {
-        __threadfence();
-        // totals in block order: one lane per entry (entries < 32)
-        double tot = 0;
-        if (threadIdx.x < kAAPart)
-            for (int b = 0; b < (int)gridDim.x; ++b) tot += ((volatile double*)part)[(size_t)b * kAAPart + threadIdx.x];
-        __shared__ double s_tot[kAAPart];
-        if (threadIdx.x < kAAPart) s_tot[threadIdx.x] = tot;
-        __syncwarp();
-        if (threadIdx.x == 0) {
-            int slots[kAAMax + 1];
-            for (int j = 0; j < n_new; ++j) {
-                const int sl = (head - j + nslot) % nslot;
-                slots[j] = sl;
-                aa->gram[head][sl] = s_tot[sl];
-                aa->gram[sl][head] = s_tot[sl];
-            }
-            const double num = s_tot[head], d = s_tot[kAAMax + 1];
-            st->sn_norm_num = num;
-            st->sn_norm_den = d;
-            st->sn_iters += 1;
-            if (d == 0.0 || sqrt(num) <= tol * sqrt(d)) st->sn_conv = 1;
-            else aa_solve(aa, slots, n_new);
-            aa->n = n_new;
-            aa->head = (head + 1) % nslot;
-            st->sn_blocks_done = 0u;
+    if (reduce_partials<kAAPart>(rs.part, (int)gridDim.x, rs.gpart, rs.gcnt, &st->sn_blocks_done, s_tot) &&
+        threadIdx.x == 0) {
+        int slots[kAAMax + 1];
+        for (int j = 0; j < n_new; ++j) {
+            const int sl = (head - j + nslot) % nslot;
+            slots[j] = sl;
+            aa->gram[head][sl] = s_tot[sl];
+            aa->gram[sl][head] = s_tot[sl];
         }
+        const double num = s_tot[head], d = s_tot[kAAMax + 1];
+        st->sn_norm_num = num;
+        st->sn_norm_den = d;
+        st->sn_iters += 1;
+        if (d == 0.0 || sqrt(num) <= tol * sqrt(d)) st->sn_conv = 1;
+        else aa_solve(aa, slots, n_new);
+        aa->n = n_new;
+        aa->head = (head + 1) % nslot;
     }
 }
 
@@ -630,6 +678,30 @@ __global__ void sn_to_double_kernel(const T* phi, double* out, int n) {
     if (i < n) out[i] = (double)phi[i];
 }
 
+// the sn_norm buffer: kAAPart partials per reduction block, then per group, then the group counters
+static RedScratch red_scratch(const hyb_problem* p) {
+    const size_t nblk = (p->ncells + kRedCells - 1) / kRedCells;
+    const size_t ngrp = (nblk + kRedGroupBlocks - 1) / kRedGroupBlocks;
+    RedScratch r;
+    r.part = p->sn_norm;
+    r.gpart = r.part + kAAPart * nblk;
+    r.gcnt = (unsigned*)(r.gpart + kAAPart * ngrp);
+    return r;
+}
+
+size_t sn_norm_bytes(int ncells) {
+    const size_t nblk = ((size_t)ncells + kRedCells - 1) / kRedCells;
+    const size_t ngrp = (nblk + kRedGroupBlocks - 1) / kRedGroupBlocks;
+    return kAAPart * (nblk + ngrp) * sizeof(double) + ngrp * sizeof(unsigned);
+}
+
+cudaError_t sn_clear_counters(hyb_problem* p) {
+    const RedScratch r = red_scratch(p);
+    const size_t nblk = (p->ncells + kRedCells - 1) / kRedCells;
+    const size_t ngrp = (nblk + kRedGroupBlocks - 1) / kRedGroupBlocks;
+    return cudaMemsetAsync(r.gcnt, 0, ngrp * sizeof(unsigned), p->stream);
+}
+
 template <typename T>
 static int sweep_warps(const hyb_problem* p, size_t* smem) {
     const int nstrip = (p->ny + 31) / 32;
@@ -670,13 +742,14 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     }
     sweep_pipe_kernel<T><<<p->n_ord, 32 * a.W, smem, s>>>(a);
     const int gr = (p->ncells + kRedCells - 1) / kRedCells;
+    const RedScratch rs = red_scratch(p);
     if (p->d.sn_accel > 0) {
         const int depth = p->d.sn_accel;
         const size_t nv = 4 * (size_t)p->ncells;
         T* gh = (T*)p->aa_hist;
         T* fh = gh + (size_t)(depth + 1) * nv;
         sn_reduce_aa_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>(
-            (const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, p->sn_norm, gh, fh, depth,
+            (const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, gh, fh, depth,
             (AAState*)p->aa_state, p->st, sn_tol_eff(p));
         sn_mix_kernel<T><<<(unsigned)((nv + 255) / 256), 256, 0, s>>>((T*)p->sn_phi, gh, p->ncells, depth,
                                                                       (const AAState*)p->aa_state, p->st,
@@ -685,7 +758,7 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
         return cudaGetLastError();
     }
     sn_reduce_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old,
-                                                              (T*)p->sn_phi, p->ncells, p->sn_norm, (const T*)p->sig,
+                                                              (T*)p->sn_phi, p->ncells, rs, (const T*)p->sig,
                                                               p->mom_d, (T)p->area, inv4pidt, src, p->st,
                                                               sn_tol_eff(p));
     return cudaGetLastError();

@@ -16,7 +16,7 @@ from .workloads import ProblemSpec
 
 HYB_OK, HYB_EINVAL, HYB_ENOMEM, HYB_ECUDA, HYB_ETIMEOUT, HYB_ESTATE, HYB_EBOUNDS, HYB_ECAPACITY = range(8)
 FP32, FP64 = 0, 1
-SOBOL, PRNG = 0, 1
+SOBOL, PRNG, HALTON = 0, 1, 2
 NS_INF = 2147483647
 STREAM_INIT, STREAM_LEG_CENSUS, STREAM_LEG_SOURCE, STREAM_REMAP_SOURCE, STREAM_REMAP_COMB = range(5)
 TALLY = {"pre": 0, "post": 1, "handoff": 2, "sn_phi": 3, "flux": 4, "pre_raw": 5, "post_raw": 6}

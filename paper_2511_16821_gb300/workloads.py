@@ -17,7 +17,7 @@ from dataclasses import dataclass, field, replace
 import numpy as np
 
 FP32, FP64 = 0, 1
-SOBOL, PRNG = 0, 1
+SOBOL, PRNG, HALTON = 0, 1, 2
 NS_INF = 2147483647
 
 

@@ -52,3 +52,15 @@ def test_batch_equals_alone(prec, order):
             assert np.array_equal(P.tally("flux"), alone[i][0]), (i, tun)
             assert np.array_equal(P.bank()["w"], alone[i][1]["w"]), (i, tun)
         B2.close()
+
+
+def test_batch_rejects_halton_and_infinite_ns():
+    from paper_2511_16821_gb300 import hyb
+    base = _problems(2, 5, precision=W.FP32)
+    for bad in (base[1].with_(sampler=W.HALTON), base[1].with_(n_s=W.NS_INF)):
+        probs = [hyb.Problem(base[0]), hyb.Problem(bad)]
+        with pytest.raises(hyb.HybError) as e:
+            hyb.Batch(probs)
+        assert e.value.status == hyb.HYB_EINVAL
+        for P in probs:
+            P.close()

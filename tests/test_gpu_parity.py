@@ -107,8 +107,9 @@ def fp32_weighted(g, o):
 # ------------------------------------------------------------------------------------------------
 # point sets
 # ------------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("sampler", [0, 1])
-@pytest.mark.parametrize("i0,n,nd", [(0, 4097, 29), (123456, 3000, 70), (2 ** 31 - 5, 10, 8)])
+@pytest.mark.parametrize("sampler", [0, 1, 2])
+@pytest.mark.parametrize("i0,n,nd", [(0, 4097, 29), (123456, 3000, 70), (2 ** 31 - 5, 10, 8),
+                                     (2 ** 32 - 3000, 3000, 65)])
 def test_points_bitexact(H, orc, sampler, i0, n, nd):
     g = H.points(99, 7, 3, sampler, i0, n, nd).cpu().numpy().view(np.uint32)
     o = orc.points(99, 7, 3, sampler, i0, n, nd)
@@ -148,6 +149,7 @@ def leg_cases():
         ("cb_ns1", cb.with_(n_s=1), 5000, 1),
         ("cb_ns2", cb, 5000, 2),
         ("cb_ns4_prng", cb.with_(n_s=4, sampler=W.PRNG), 5000, 4),
+        ("cb_ns3_halton", cb.with_(n_s=3, sampler=W.HALTON), 5000, 5),
         ("het_kill", het, 4000, 6),
         ("one_cell", W.homogeneous(n=1, L=0.5, sigma_a=0.3, sigma_s=2.0, Q=1.0, n_hist=1, dt=1.0, n_s=2), 1, 0),
         ("no_source_empty", W.homogeneous(n=3, Q=None, n_hist=5), 0, 0),
@@ -193,7 +195,8 @@ def test_initial_bank_parity(H, orc):
 # ------------------------------------------------------------------------------------------------
 # MC leg, FP32 tracking (cell-local coordinates, int64 fixed-point tallies)
 # ------------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("case", [c for c in leg_cases() if c[0] in ("pulse", "cb_ns0", "cb_ns2", "het_kill")],
+@pytest.mark.parametrize("case", [c for c in leg_cases() if c[0] in ("pulse", "cb_ns0", "cb_ns2", "het_kill",
+                                                                     "cb_ns3_halton")],
                          ids=lambda c: c[0])
 def test_mc_leg_fp32_tolerance(H, orc, case):
     """FP32 tracking vs the FP64 oracle: 1e-4 relative on every resolved cell above 1e-3 of the
@@ -300,9 +303,11 @@ def test_remap_parity(H, orc, cap, order):
     assert math.isclose(rs["w_source"], ost["w_source"], rel_tol=1e-10)
 
 
-@pytest.mark.parametrize("prec,order", [(W.FP64, 0), (W.FP32, 0), (W.FP64, 1)])
-def test_multistep_hybrid(H, orc, prec, order):
-    spec = W.pulse(n_hist=8192).with_(precision=prec, sn_tol=1e-12 if prec == W.FP64 else 1e-7, census_order=order)
+@pytest.mark.parametrize("prec,order,sampler", [(W.FP64, 0, W.SOBOL), (W.FP32, 0, W.SOBOL), (W.FP64, 1, W.SOBOL),
+                                                (W.FP64, 1, W.HALTON)])
+def test_multistep_hybrid(H, orc, prec, order, sampler):
+    spec = W.pulse(n_hist=8192).with_(precision=prec, sn_tol=1e-12 if prec == W.FP64 else 1e-7, census_order=order,
+                                      sampler=sampler)
     ospec = spec.with_(precision=W.FP64, sn_tol=1e-12)
     P = H.Problem(spec)
     ob = orc.init_bank(ospec, ospec.ic)
