@@ -43,7 +43,7 @@ class _Problem(C.Structure):
                 ("n_s", C.c_int32), ("sampler", C.c_int32), ("n_hist", C.c_int64),
                 ("seed", C.c_uint64), ("sn_order", C.c_int32), ("handoff_full", C.c_int32),
                 ("w_min", C.c_double), ("census_cap", C.c_int64), ("sn_tol", C.c_double),
-                ("sn_max_iter", C.c_int32), ("census_order", C.c_int32)]
+                ("sn_max_iter", C.c_int32), ("census_order", C.c_int32), ("remap_variant", C.c_int32)]
 
 
 class _Bank(C.Structure):
@@ -102,7 +102,8 @@ def _problem(spec) -> tuple[_Problem, _Keep]:
                  n_hist=spec.n_hist, seed=spec.seed, sn_order=spec.sn_order,
                  handoff_full=spec.handoff_full, w_min=spec.w_min, census_cap=spec.census_cap,
                  sn_tol=spec.sn_tol, sn_max_iter=spec.sn_max_iter,
-                 census_order=getattr(spec, "census_order", 0))
+                 census_order=getattr(spec, "census_order", 0),
+                 remap_variant=getattr(spec, "remap_variant", 0))
     return p, _Keep(sa, ss, q)
 
 
@@ -266,11 +267,29 @@ def remap(spec, step: int, bank: dict | None, pre, post, phi):
     return res, _stats_dict(st), bool(combed.value)
 
 
+def remap_additive(spec, step: int, bank: dict | None, leg_census: dict | None, post, phi):
+    """Steps 3' and 4' (the previous hybrids' remap): the leg census followed by the survivors of
+    births from sigma_s (phi_post + phi_c), combed. bank: the step-start bank."""
+    p, keep = _problem(spec)
+    nb = 0 if bank is None else int(bank.get("n", len(bank["w"])))
+    nl = 0 if leg_census is None else int(leg_census.get("n", len(leg_census["w"])))
+    out = empty_bank(max(nl + spec.n_hist, 1))
+    cb, cl, co = _bank(bank), _bank(leg_census), _bank(out)
+    st = _Stats()
+    combed = C.c_int32(0)
+    args = [np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (post, phi)]
+    rc = lib().or_remap_additive(C.byref(p), C.c_int64(step), C.byref(cb) if cb else None,
+                                 C.byref(cl) if cl else None, *[_dp(a) for a in args], C.byref(co),
+                                 C.byref(st), C.byref(combed))
+    assert rc == 0, rc
+    return _trim(out, co.n), _stats_dict(st), bool(combed.value)
+
+
 def step(spec, step_index: int, bank: dict | None):
     p, keep = _problem(spec)
     nc = spec.nx * spec.ny
     nb = 0 if bank is None else int(bank.get("n", len(bank["w"])))
-    cap = nb + spec.n_hist
+    cap = nb + 2 * spec.n_hist
     out = empty_bank(max(cap, 1))
     cb, co = _bank(bank), _bank(out)
     flux, pre, post, mom, phi = np.zeros(nc), np.zeros(nc), np.zeros(nc), np.zeros(4 * nc), np.zeros(4 * nc)

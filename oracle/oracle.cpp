@@ -258,6 +258,7 @@ typedef struct {
     double sn_tol;          // source-iteration relative-change tolerance
     int32_t sn_max_iter;
     int32_t census_order;   // 0: census in slot order (bank slots, then births); 1: stable by cell
+    int32_t remap_variant;  // 0: Eq. (R) relabelling remap; 1: steps 3'/4' (additive, previous hybrids)
 } or_problem;
 
 typedef struct {
@@ -1093,8 +1094,81 @@ void or_remap_density(const or_problem* P, const double* pre, const double* post
     }
 }
 
-// Remap (step 3) and census (step 4). out receives the new bank (capacity >= census_cap or
-// bank + births). combed: 1 if the comb ran.
+// Births of a remap (Eq. (R), or Eq. (R') for the additive variant): n_hist particles from the
+// bilinear density f (4 Legendre coefficients per cell), stream REMAP_SOURCE, each streamed
+// straight to t_{n+1} with sigma_t attenuation; survivors are appended to surv. Returns the total
+// |q| (0: no births); *wmax is raised to bound the birth weights.
+static double remap_births(const or_problem* P, const Mesh& M, int64_t step, const std::vector<double>& f,
+                           std::vector<Streamed>* surv, long double* w_src, or_stats* st, long double* acc,
+                           double* wmax) {
+    const size_t nc = (size_t)M.nx * M.ny;
+    const double cdt = P->c * P->dt;
+    std::vector<double> qc(nc);
+    double W = 0.0;
+    for (size_t k = 0; k < nc; ++k) { qc[k] = f[4 * k] * M.area * P->dt; W += std::fabs(qc[k]); }
+    if (!(W > 0.0)) return 0.0;
+    Cdf2D C = build_cdf(M, qc);
+    Points pts{stream_key(P->seed, (uint64_t)step, kStreamRemapSource), P->sampler};
+    const double wbar = W / (double)P->n_hist;
+    for (size_t k = 0; k < nc; ++k) {
+        if (qc[k] == 0.0) continue;
+        const double* fk = &f[4 * k];
+        const bool pos = fk[0] - fk[1] - fk[2] + fk[3] >= 0 && fk[0] + fk[1] - fk[2] - fk[3] >= 0 &&
+                         fk[0] - fk[1] + fk[2] - fk[3] >= 0 && fk[0] + fk[1] + fk[2] + fk[3] >= 0;
+        const double r = pos ? 1.0 : (std::fabs(fk[0]) + std::fabs(fk[1]) + std::fabs(fk[2]) +
+                                      std::fabs(fk[3])) / std::fabs(fk[0]);
+        *wmax = std::max(*wmax, wbar * r);
+    }
+    for (int64_t i = 0; i < P->n_hist; ++i) {
+        double frx, fry, ox, oy;
+        int k = sample_cell(C, pts(i, 0), pts(i, 1), &frx, &fry);
+        const double* fk = &f[4 * k];
+        const double nod[4] = {fk[0] - fk[1] - fk[2] + fk[3], fk[0] + fk[1] - fk[2] - fk[3],
+                               fk[0] - fk[1] + fk[2] - fk[3], fk[0] + fk[1] + fk[2] + fk[3]};
+        double xi, eta, w;
+        if (nod[0] >= 0 && nod[1] >= 0 && nod[2] >= 0 && nod[3] >= 0) {
+            xi = inv_linear(fk[0], fk[1], frx);
+            eta = inv_linear(fk[0] + fk[1] * xi, fk[2] + fk[3] * xi, fry);
+            w = wbar;
+        } else {
+            xi = 2.0 * frx - 1.0; eta = 2.0 * fry - 1.0;
+            w = wbar * (fk[0] + fk[1] * xi + fk[2] * eta + fk[3] * xi * eta) / std::fabs(fk[0]);
+        }
+        const double tf = unit(pts(i, 2));
+        iso_direction(unit(pts(i, 3)), unit(pts(i, 4)), &ox, &oy);
+        *w_src += w;
+        Streamed r = stream_free(P, M, k % M.nx, k / M.nx, 0.5 * (xi + 1.0) * M.dx,
+                                 0.5 * (eta + 1.0) * M.dy, ox, oy, w, cdt * (1.0 - tf), st, acc);
+        if (r.alive) surv->push_back(r);
+    }
+    return W;
+}
+
+// Census of step 4 from the survivors: in cell order (stable within a cell) when asked, so that
+// the systematic comb samples each cell's weight to within one copy; combed to census_cap (power-
+// of-two quantisation base at or above wmax, offset = point (REMAP_COMB, 0, 0)) when above it.
+static int census_from(const or_problem* P, int64_t step, std::vector<Streamed>& surv, double wmax,
+                       or_bank* out, int32_t* combed, long double* wc) {
+    const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
+    if (P->census_order == 1)
+        std::stable_sort(surv.begin(), surv.end(), [](const Streamed& a, const Streamed& b) { return a.cell < b.cell; });
+    std::vector<Streamed> fin;
+    int did_comb = 0;
+    if ((int64_t)surv.size() > cap) {
+        Points pc{stream_key(P->seed, (uint64_t)step, kStreamRemapComb), P->sampler};
+        comb(surv, cap, pc(0, 0), pow2_ceil(wmax), &fin);
+        did_comb = 1;
+    } else fin = surv;
+    out->n = 0;
+    if ((int64_t)fin.size() > out->cap) return 3;
+    *wc = 0;
+    for (auto& p : fin) { bank_push(out, p.cell, p.fx, p.fy, p.ox, p.oy, p.w); *wc += p.w; }
+    if (combed) *combed = did_comb;
+    return 0;
+}
+
+// Remap (step 3, Eq. (R)) and census (step 4). out receives the new bank (capacity >= census_cap
+// or bank + births). combed: 1 if the comb ran.
 int or_remap(const or_problem* P, int64_t step, const or_bank* census, const double* pre,
              const double* post, const double* phi, or_bank* out, or_stats* st, int32_t* combed) {
     build_sobol_table();
@@ -1118,71 +1192,68 @@ int or_remap(const or_problem* P, int64_t step, const or_bank* census, const dou
     double wmax = 0.0;  // bound on every |w| entering the comb
     if (census)
         for (int64_t j = 0; j < census->n; ++j) wmax = std::max(wmax, std::fabs(census->w[j]));
-    // (ii) births from the remap source
-    std::vector<double> f(4 * nc), qc(nc);
+    // (ii) births from the remap source Q + sigma_s (phi_pre + phi_post + phi_c)
+    std::vector<double> f(4 * nc);
     or_remap_density(P, pre, post, phi, f.data());
-    double W = 0.0;
-    for (size_t k = 0; k < nc; ++k) { qc[k] = f[4 * k] * M.area * P->dt; W += std::fabs(qc[k]); }
-    if (W > 0.0) {
-        Cdf2D C = build_cdf(M, qc);
-        Points pts{stream_key(P->seed, (uint64_t)step, kStreamRemapSource), P->sampler};
-        const double wbar = W / (double)P->n_hist;
-        for (size_t k = 0; k < nc; ++k) {
-            if (qc[k] == 0.0) continue;
-            const double* fk = &f[4 * k];
-            const bool pos = fk[0] - fk[1] - fk[2] + fk[3] >= 0 && fk[0] + fk[1] - fk[2] - fk[3] >= 0 &&
-                             fk[0] - fk[1] + fk[2] - fk[3] >= 0 && fk[0] + fk[1] + fk[2] + fk[3] >= 0;
-            const double r = pos ? 1.0 : (std::fabs(fk[0]) + std::fabs(fk[1]) + std::fabs(fk[2]) +
-                                          std::fabs(fk[3])) / std::fabs(fk[0]);
-            wmax = std::max(wmax, wbar * r);
-        }
-        for (int64_t i = 0; i < P->n_hist; ++i) {
-            double frx, fry, ox, oy;
-            int k = sample_cell(C, pts(i, 0), pts(i, 1), &frx, &fry);
-            const double* fk = &f[4 * k];
-            const double nod[4] = {fk[0] - fk[1] - fk[2] + fk[3], fk[0] + fk[1] - fk[2] - fk[3],
-                                   fk[0] - fk[1] + fk[2] - fk[3], fk[0] + fk[1] + fk[2] + fk[3]};
-            double xi, eta, w;
-            if (nod[0] >= 0 && nod[1] >= 0 && nod[2] >= 0 && nod[3] >= 0) {
-                xi = inv_linear(fk[0], fk[1], frx);
-                eta = inv_linear(fk[0] + fk[1] * xi, fk[2] + fk[3] * xi, fry);
-                w = wbar;
-            } else {
-                xi = 2.0 * frx - 1.0; eta = 2.0 * fry - 1.0;
-                w = wbar * (fk[0] + fk[1] * xi + fk[2] * eta + fk[3] * xi * eta) / std::fabs(fk[0]);
-            }
-            const double tf = unit(pts(i, 2));
-            iso_direction(unit(pts(i, 3)), unit(pts(i, 4)), &ox, &oy);
-            w_src += w;
-            Streamed r = stream_free(P, M, k % M.nx, k / M.nx, 0.5 * (xi + 1.0) * M.dx,
-                                     0.5 * (eta + 1.0) * M.dy, ox, oy, w, cdt * (1.0 - tf), st, acc);
-            if (r.alive) surv.push_back(r);
-        }
-    }
-    // (iii) census of step 4, combed to census_cap when above it; in cell order (stable within a
-    // cell) when asked, so that the systematic comb samples each cell's weight to within one copy
-    const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
-    if (P->census_order == 1)
-        std::stable_sort(surv.begin(), surv.end(), [](const Streamed& a, const Streamed& b) { return a.cell < b.cell; });
-    std::vector<Streamed> fin;
-    int did_comb = 0;
-    if ((int64_t)surv.size() > cap) {
-        Points pc{stream_key(P->seed, (uint64_t)step, kStreamRemapComb), P->sampler};
-        comb(surv, cap, pc(0, 0), pow2_ceil(wmax), &fin);
-        did_comb = 1;
-    } else fin = surv;
-    out->n = 0;
-    if ((int64_t)fin.size() > out->cap) return 3;
+    const double W = remap_births(P, M, step, f, &surv, &w_src, st, acc, &wmax);
+    // (iii) census
     long double wc = 0;
-    for (auto& p : fin) { bank_push(out, p.cell, p.fx, p.fy, p.ox, p.oy, p.w); wc += p.w; }
+    const int rc = census_from(P, step, surv, wmax, out, combed, &wc);
+    if (rc) return rc;
     if (st) {
         st->histories = (census ? census->n : 0) + (W > 0.0 ? P->n_hist : 0);
-        st->census = (int64_t)fin.size();
+        st->census = out->n;
         st->w_source = (double)w_src; st->w_absorbed = (double)acc[0];
         st->w_leaked = (double)acc[1]; st->w_killed = (double)acc[2];
         st->w_census = (double)wc;
     }
-    if (combed) *combed = did_comb;
+    return (st && st->errors) ? 4 : 0;
+}
+
+// The remap of the previous hybrids (steps 3' and 4' of Sec. 2.2): new particles from the
+// collided emission sigma_s (phi_post + phi_c) only (Eq. (R'): no Q, no pre-limit scattering,
+// zero initial data), streamed scatter-free with sigma_t; the new census is the MC leg's census
+// (pre- and post-limit particles alive at t_{n+1}, kept as they are) followed by those births'
+// survivors, combed like the census of Eq. (R). bank: the step-start bank (its max |w| bounds the
+// leg census weights, as does the leg's birth weight int Q / n_hist); leg_census: the leg's
+// census particles in history order.
+int or_remap_additive(const or_problem* P, int64_t step, const or_bank* bank, const or_bank* leg_census,
+                      const double* post, const double* phi, or_bank* out, or_stats* st, int32_t* combed) {
+    build_sobol_table();
+    build_primes();
+    Mesh M(P);
+    const size_t nc = (size_t)M.nx * M.ny;
+    if (st) std::memset(st, 0, sizeof(*st));
+    long double acc[3] = {0, 0, 0};
+    std::vector<Streamed> surv;
+    double wmax = 0.0;
+    if (bank)
+        for (int64_t j = 0; j < bank->n; ++j) wmax = std::max(wmax, std::fabs(bank->w[j]));
+    double Wq = 0.0;
+    for (size_t k = 0; k < nc; ++k) Wq += std::fabs(P->Q ? P->Q[k] : 0.0) * M.area * P->dt;
+    if (Wq > 0.0) wmax = std::max(wmax, Wq / (double)P->n_hist);
+    if (leg_census)
+        for (int64_t j = 0; j < leg_census->n; ++j)
+            surv.push_back(Streamed{true, leg_census->cell[j], leg_census->fx[j], leg_census->fy[j],
+                                    leg_census->ox[j], leg_census->oy[j], leg_census->w[j]});
+    std::vector<double> f(4 * nc);
+    for (size_t k = 0; k < nc; ++k) {
+        const double ss = P->sigma_s[k];
+        f[4 * k + 0] = ss * (post ? post[k] : 0.0) / (M.area * P->dt) + ss * (phi ? phi[4 * k] : 0.0);
+        for (int j = 1; j < 4; ++j) f[4 * k + j] = ss * (phi ? phi[4 * k + j] : 0.0);
+    }
+    long double w_src = 0;
+    const double W = remap_births(P, M, step, f, &surv, &w_src, st, acc, &wmax);
+    long double wc = 0;
+    const int rc = census_from(P, step, surv, wmax, out, combed, &wc);
+    if (rc) return rc;
+    if (st) {
+        st->histories = W > 0.0 ? P->n_hist : 0;
+        st->census = out->n;
+        st->w_source = (double)w_src; st->w_absorbed = (double)acc[0];
+        st->w_leaked = (double)acc[1]; st->w_killed = (double)acc[2];
+        st->w_census = (double)wc;
+    }
     return (st && st->errors) ? 4 : 0;
 }
 
@@ -1222,6 +1293,21 @@ int or_step(const or_problem* P, int64_t step, const or_bank* bank, or_bank* out
         if ((int64_t)fin.size() > out->cap) return 3;
         for (auto& p : fin) bank_push(out, p.cell, p.fx, p.fy, p.ox, p.oy, p.w);
         if (remap_st) std::memset(remap_st, 0, sizeof(*remap_st));
+    } else if (P->remap_variant == 1) {
+        // steps 3' and 4': the leg's census survives as particles beside the Eq. (R') births
+        or_bank lc;
+        const int64_t capt = (bank ? bank->n : 0) + P->n_hist;
+        std::vector<int32_t> c(capt); std::vector<double> a(capt), b(capt), d(capt), e(capt), g(capt);
+        lc.n = 0; lc.cap = capt; lc.cell = c.data(); lc.fx = a.data(); lc.fy = b.data();
+        lc.ox = d.data(); lc.oy = e.data(); lc.w = g.data();
+        rc = or_mc_leg(P, step, bank, pre, post, mom, leg_st, nullptr, &lc);
+        if (rc) return rc;
+        int32_t it = 0;
+        rc = or_sn_solve(P, mom, phi, &it);
+        if (rc) return rc;
+        if (leg_st) leg_st->sn_iterations = it;
+        rc = or_remap_additive(P, step, bank, &lc, post, phi, out, remap_st, nullptr);
+        if (rc) return rc;
     } else {
         rc = or_mc_leg(P, step, bank, pre, post, mom, leg_st, nullptr, nullptr);
         if (rc) return rc;

@@ -53,6 +53,7 @@ class ProblemSpec:
     sn_warm_start: int = 0
     census_order: int = 0
     sn_accel: int = 0
+    remap_variant: int = 0          # 0: Eq. (R) relabelling remap; 1: steps 3'/4' of the previous hybrids
     name: str = field(default="problem")
 
     @property

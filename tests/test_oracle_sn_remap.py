@@ -270,3 +270,83 @@ def test_cell_ordered_comb_keeps_each_cell_within_one_copy(orc):
         devs[order] = float(np.max(np.abs(got - want)) / wcopy)
     assert devs[1] <= 1.0 + 1e-6, devs
     assert devs[0] > 1.5, devs
+
+
+# ------------------------------------------------------------------------------------------------
+# steps 3'/4' of the previous hybrids (additive remap, remap_variant = 1)
+# ------------------------------------------------------------------------------------------------
+def test_additive_remap_pure_absorber_keeps_the_leg_census(orc):
+    """Without scattering the Eq. (R') source sigma_s (phi_post + phi_c) is zero whatever Q is:
+    the new census is the MC leg's census itself (the relabelling remap instead re-streams the
+    bank and adds births from Q)."""
+    spec = _absorber(n_hist=400, census_cap=10 ** 6).with_(Q=np.full(144, 0.7), remap_variant=1)
+    bank = W.random_bank(spec, 2000, seed=6)
+    r = orc.mc_leg(spec, 0, bank, want_census=True)
+    nc = spec.ncells
+    out, st, combed = orc.remap_additive(spec, 0, bank, r["census"], r["post"], np.zeros((nc, 4)))
+    c = r["census"]
+    assert not combed and st["histories"] == 0 and out["n"] == c["n"]
+    for k in ("cell", "fx", "fy", "ox", "oy", "w"):
+        assert np.array_equal(out[k], c[k]), k
+    rel, _, _ = orc.remap(spec, 0, bank, r["pre"], r["post"], np.zeros((nc, 4)))
+    assert rel["n"] > c["n"]
+
+
+def test_additive_step_is_pure_mc_when_no_history_reaches_the_limit(orc):
+    """When no history reaches N_s there is no hand-off, the collided flux is zero and so is the
+    Eq. (R') source: a 3'/4' step is then the N_s = infinity step, bank for bank (same comb
+    quantisation base: the step-start bank's max |w| and the birth weight)."""
+    n = 10
+    spec = W.homogeneous(n=n, L=2.0, sigma_a=0.3, sigma_s=0.05, Q=1.0, dt=0.2, n_s=12, n_hist=1500,
+                         census_cap=900)
+    bank = W.random_bank(spec, 1200, seed=8)
+    for order in (0, 1):
+        a = orc.step(spec.with_(remap_variant=1, census_order=order), 2, bank)
+        b = orc.step(spec.with_(n_s=W.NS_INF, census_order=order), 2, bank)
+        assert a["leg"]["reached_limit"] == 0 and np.all(a["phi"] == 0.0)
+        assert a["bank"]["n"] == b["bank"]["n"] == 900
+        for k in ("cell", "fx", "fy", "ox", "oy", "w"):
+            assert np.array_equal(a["bank"][k], b["bank"][k]), (order, k)
+        assert np.array_equal(a["flux"], b["flux"])
+
+
+def test_additive_births_integrate_the_collided_emission(orc):
+    """The Eq. (R') births carry sigma_s (phi_post + phi_c) A dt in total (each w = W / N for
+    cell-constant densities) and their weight is conserved: start = absorbed + leaked + census."""
+    spec = W.checkerboard(n_s=1, n_hist=4000, cells_per_block=4).with_(remap_variant=1, census_cap=10 ** 7)
+    bank = W.random_bank(spec, 1500, seed=2)
+    r = orc.mc_leg(spec, 0, bank, want_census=True)
+    phi, _ = orc.sn_solve(spec, r["mom"])
+    phi[:, 1:] = 0.0
+    phi[:, 0] = np.maximum(phi[:, 0], 0.0)   # non-negative densities: every birth carries +W / N
+    A = (spec.lx / spec.nx) * (spec.ly / spec.ny)
+    W_exp = float(np.sum(spec.sigma_s * (r["post"] / (A * spec.dt) + phi[:, 0]) * A * spec.dt))
+    assert W_exp > 0
+    out, st, combed = orc.remap_additive(spec, 0, bank, r["census"], r["post"], phi)
+    assert not combed and st["histories"] == spec.n_hist
+    assert math.isclose(st["w_source"], W_exp, rel_tol=1e-12)
+    w_births = out["w"][r["census"]["n"]:].sum()
+    assert math.isclose(st["w_source"], st["w_absorbed"] + st["w_leaked"] + st["w_killed"] + w_births,
+                        rel_tol=1e-12)
+    # the leg census leads the new census unchanged
+    assert np.array_equal(out["w"][:r["census"]["n"]], r["census"]["w"])
+
+
+def test_additive_hybrid_infinite_medium_decay(orc):
+    """Like the relabelling step, the 3'/4' step keeps the infinite-medium total decaying as
+    exp(-sigma_a c t) up to the step-averaging error of the collided emission, shrinking with dt."""
+    def run(dt, steps):
+        n = 16
+        spec = W.homogeneous(n=n, L=16.0, sigma_a=0.5, sigma_s=1.0, Q=None, dt=dt, n_s=1,
+                             n_hist=4000, sn_order=4, remap_variant=1, census_cap=6000)
+        ic = np.zeros(n * n)
+        ic[(n // 2) * n + n // 2] = 1.0
+        bank = orc.init_bank(spec, ic)
+        for k in range(steps):
+            bank = orc.step(spec, k, bank)["bank"]
+        return abs(bank["w"].sum() / math.exp(-0.5 * dt * steps) - 1.0)
+
+    e1 = run(0.1, 4)
+    e2 = run(0.05, 8)
+    assert e1 < 4 * 1.0 * 1.5 * 0.1 ** 2
+    assert e2 < e1
