@@ -106,7 +106,12 @@ typedef struct {
     int32_t sn_accel;         /* 0: plain source iteration (the paper); 1..8: Anderson acceleration
                                  of that depth (the same fixed point, fewer sweeps in diffusive
                                  problems) */
-    int32_t pad1;
+    int32_t remap_variant;    /* 0: the remap of Eq. (R) (Sec. 2.2 steps 3-4: re-stream the
+                                 step-start bank, births from Q + sigma_s (phi_pre + phi_post +
+                                 phi_c)); 1: steps 3'/4' of the previous hybrids (Eq. (R')):
+                                 births from sigma_s (phi_post + phi_c) only, zero initial data,
+                                 and the new census is the MC leg's census followed by those
+                                 births' survivors. Finite N_s only; not in batches */
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */

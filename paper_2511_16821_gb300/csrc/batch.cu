@@ -254,6 +254,7 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         if (p->leg_done) return bfail(b, HYB_ESTATE, "problems must be at a step boundary");
         if (p->d.n_s == HYB_NS_INF) return bfail(b, HYB_EINVAL, "N_s = infinity problems are stepped alone");
         if (p->d.sampler == HYB_HALTON) return bfail(b, HYB_EINVAL, "Halton problems are stepped alone");
+        if (p->d.remap_variant != 0) return bfail(b, HYB_EINVAL, "the additive remap variant is stepped alone");
         probs.push_back(p);
     }
     if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");

@@ -268,9 +268,15 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
         sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas;
-    int64_t cap, nblk;
+    int64_t cap, nblk, slots;
     int gr, gc;
 };
+
+// remap staging slots: the bank capacity and one per birth (Eq. (R)); for steps 3'/4' the MC leg
+// stages its census there too (bank slots, then its source births), ahead of the remap births
+static int64_t stage_slots(const hyb_problem_desc* d, int64_t cap) {
+    return cap + d->n_hist * (d->remap_variant == 1 ? 2 : 1);
+}
 
 Sizes sizes(const hyb_problem_desc* d) {
     Sizes z;
@@ -290,7 +296,8 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.rem_q = nc * 8;
     z.scratch = (256 + d->ny + nc) * 8;
     z.bank = bank_cell_bytes(z.cap) + 5 * (size_t)z.cap * T;
-    z.stage = bank_cell_bytes(z.cap + d->n_hist) + 5 * (size_t)(z.cap + d->n_hist) * T;
+    z.slots = stage_slots(d, z.cap);
+    z.stage = bank_cell_bytes(z.slots) + 5 * (size_t)z.slots * T;
     z.acc1 = nc * acc;
     z.acc4 = 4 * nc * acc;
     z.d1 = nc * 8;
@@ -301,7 +308,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.snty = (size_t)nord * d->nx * 2 * T;        // strip-top traces per ordinate
     z.snqb = 3 * kMaxOrd * T;
     z.snnorm = hyb::sn_norm_bytes((int)nc);       // reduction partials per block and group, group counters
-    z.nblk = (z.cap + d->n_hist + 2047) / 2048;
+    z.nblk = (z.slots + 2047) / 2048;
     z.blk = 4 * (size_t)z.nblk * 8;
     z.gr = hyb::guide_bits(d->ny);
     z.gc = hyb::guide_bits(d->nx);
@@ -312,7 +319,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.aah = d->sn_accel > 0 ? 2 * (size_t)(d->sn_accel + 1) * 4 * nc * T : 0;   // Anderson history
     z.aas = d->sn_accel > 0 ? sn_accel_state_bytes() : 0;
     z.rempos = nc * 4;
-    const size_t nslots = (size_t)(z.cap + d->n_hist);
+    const size_t nslots = (size_t)z.slots;
     z.sortkv = d->census_order == 1 ? nslots * 8 : 0;                    // x2: (cell, slot) pairs, ping-pong
     z.sortc = d->census_order == 1 ? 256 * ((nslots + 2047) / 2048 + 1) * 4 : 0;
     return z;
@@ -385,6 +392,7 @@ void assign(hyb_problem* p) {
     p->aa_hist = z.aah ? take(z.aah) : nullptr;
     p->aa_state = z.aas ? take(z.aas) : nullptr;
     p->bank_cap = z.cap;
+    p->stage_slots = z.slots;
     p->nblk_max = z.nblk;
 }
 
@@ -422,6 +430,11 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
     if (d->census_order != 0 && d->census_order != 1) { *why = "census_order must be 0 or 1"; return HYB_EINVAL; }
     if (d->sn_accel < 0 || d->sn_accel > 8) { *why = "sn_accel must be in [0, 8]"; return HYB_EINVAL; }
+    if (d->remap_variant != 0 && d->remap_variant != 1) { *why = "remap_variant must be 0 or 1"; return HYB_EINVAL; }
+    if (d->remap_variant == 1 && d->n_s == HYB_NS_INF) {
+        *why = "remap_variant 1 needs a finite N_s (N_s = infinity has no remap)";
+        return HYB_EINVAL;
+    }
     if (!(d->sn_tol >= 0) || !(d->w_min >= 0) || !(d->w_min < 1)) { *why = "sn_tol >= 0 and 0 <= w_min < 1 required"; return HYB_EINVAL; }
     if (!d->sigma_a || !d->sigma_s) { *why = "sigma_a and sigma_s are required"; return HYB_EINVAL; }
     const size_t nc = (size_t)d->nx * d->ny;

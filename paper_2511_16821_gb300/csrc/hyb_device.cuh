@@ -24,12 +24,12 @@ inline BankView<T> bank_view(hyb_problem* p, int which) {
     return b;
 }
 
-// The remap staging SoA: one end state per slot (bank capacity + n_hist slots), same layout as a
-// bank (cell -1 = not alive)
+// The remap staging SoA: one end state per slot (p->stage_slots: bank capacity + n_hist, plus
+// n_hist more for steps 3'/4'), same layout as a bank (cell -1 = not alive)
 template <typename T>
 inline BankView<T> stage_view(hyb_problem* p) {
     BankView<T> b;
-    const int64_t n = p->bank_cap + p->d.n_hist;
+    const int64_t n = p->stage_slots;
     char* base = (char*)p->stage;
     b.cell = (int32_t*)base;
     T* f = (T*)(base + bank_cell_bytes(n));

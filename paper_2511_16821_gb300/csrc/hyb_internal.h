@@ -54,6 +54,8 @@ struct DevState {
     int k_rw;                  // scale exponent of the remap weight sums
     Acc128 bank_wsum_acc;      // scratch of the bank-statistics kernels
     long long out_count;       // particles written by the last remap
+    long long r_lead;          // remap slots ahead of the births that hold the MC leg's staged census
+                               // (steps 3'/4'), after the step-start bank slots; 0 for Eq. (R)
     long long step;            // time-step index n of the next MC leg / remap (t_n = n dt)
     int sn_conv;               // collided solve: converged flag of the current solve
     int sn_iters;              // collided solve: iterations run in the current solve
@@ -96,6 +98,7 @@ struct hyb_problem {
     double dx, dy, area;
     int prec;                 // HYB_FP32 / HYB_FP64
     int64_t bank_cap;
+    int64_t stage_slots;      // remap staging slots: bank_cap + n_hist (+ n_hist for steps 3'/4')
     int64_t step;
     cudaStream_t stream;
     void* ws;                 // device workspace base

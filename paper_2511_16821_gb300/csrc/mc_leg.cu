@@ -362,7 +362,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             // ---- end of the history ------------------------------------------------------------
             const long long fw = fix_w(h.w, scw, scw_f);
             if (a.stage_census) {
-                // N_s = infinity: the census survivors become the next bank (history order)
+                // N_s = infinity or steps 3'/4': the census survivors are kept (history order)
                 const long long j = h.j;
                 if (fate == kFateCensus) {
                     a.cens.cell[j] = h.iy * nx + h.ix;
@@ -705,7 +705,8 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.bank = bank_view<T>(p, cur);
     a.births = birth_view<T>(p);
     a.spread_bank = p->d.census_order == 1 ? 1 : 0;
-    a.stage_census = p->d.n_s == HYB_NS_INF ? 1 : 0;
+    // N_s = infinity and steps 3'/4' keep the leg's census as particles
+    a.stage_census = p->d.n_s == HYB_NS_INF || p->d.remap_variant == 1 ? 1 : 0;
     a.cens = stage_view<T>(p);
     if (a.stage_census) a.births.cell = nullptr;   // the staging buffer holds the census instead
     a.cdf = p->src_cdf;

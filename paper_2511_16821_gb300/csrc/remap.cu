@@ -185,17 +185,18 @@ cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w, Cdf2DView cdf
 }
 
 // ---------------------------------------------------------------------------------------------
-// remap density: f = (Q + sigma_s (phi_pre + phi_post) + sigma_s phi_c0, sigma_s phi_c1..3)
+// remap density: f = (Q + sigma_s (phi_pre + phi_post) + sigma_s phi_c0, sigma_s phi_c1..3) for
+// Eq. (R); (sigma_s phi_post + sigma_s phi_c0, sigma_s phi_c1..3) for Eq. (R') (relabel = 0)
 // ---------------------------------------------------------------------------------------------
 __global__ void remap_density_kernel(int ncells, double adt, const double* __restrict__ Q, const double* __restrict__ ss,
                                      const double* __restrict__ pre, const double* __restrict__ post,
                                      const double* __restrict__ phi, double* f, float* f32, int* fpos, double* q,
-                                     DevState* st) {
+                                     DevState* st, int relabel) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double r = 0;
     if (k < ncells) {
         const double s = ss[k];
-        const double f0 = Q[k] + s * (pre[k] + post[k]) + s * phi[4 * k];
+        const double f0 = relabel ? Q[k] + s * (pre[k] + post[k]) + s * phi[4 * k] : s * post[k] + s * phi[4 * k];
         const double f1 = s * phi[4 * k + 1], f2 = s * phi[4 * k + 2], f3 = s * phi[4 * k + 3];
         f[4 * k] = f0; f[4 * k + 1] = f1; f[4 * k + 2] = f2; f[4 * k + 3] = f3;
         reinterpret_cast<float4*>(f32)[k] = make_float4((float)f0, (float)f1, (float)f2, (float)f3);
@@ -218,11 +219,14 @@ __host__ __device__ inline double pow2_ceil(double w) {
     return m == 0.5 ? w : ldexp(1.0, e);
 }
 
-// comb base w_ref and birth weight; runs after the CDF build
-__global__ void remap_prep_kernel(DevState* st, long long n_hist) {
+// comb base w_ref and birth weight; runs after the CDF build. lead: the leg-census slots ahead of
+// the births (steps 3'/4'), whose weights are bounded by the step-start bank's and by the leg's
+// birth weight w_lead
+__global__ void remap_prep_kernel(DevState* st, long long n_hist, long long lead, double w_lead) {
     const double W = st->remap_W;
     const double wbar = W > 0 ? W / (double)n_hist : 0.0;
-    double wmax = fmax(st->bank_wmax, wbar * st->remap_rmax);
+    st->r_lead = lead;
+    double wmax = fmax(fmax(st->bank_wmax, w_lead), wbar * st->remap_rmax);
     st->w_ref = wmax > 0 ? pow2_ceil(wmax) : 1.0;
 }
 
@@ -248,6 +252,7 @@ struct RemapArgs {
     const unsigned long long* perm;   // census in cell order: (cell << 32 | slot) of every sorted position (else null)
     long long nslots;          // staging slots (bank capacity + n_hist); the sort covers all of them
     int perm_slots;            // 1: the census is sorted by cell after the count pass
+    int lead_staged;           // 1 (steps 3'/4'): slots ahead of the births hold the MC leg's staged census
 };
 
 template <typename T>
@@ -408,7 +413,7 @@ struct RemapScal {
 
 __device__ __forceinline__ RemapScal remap_scalars(const DevState* st, long long n_hist) {
     RemapScal r;
-    const long long nb = st->n_bank;
+    const long long nb = st->n_bank + st->r_lead;
     const long long nbirth = st->remap_W > 0 ? n_hist : 0;
     r.N = nb + nbirth;
     r.wbar = nbirth ? st->remap_W / (double)n_hist : 0.0;
@@ -434,7 +439,8 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
     __syncthreads();
     Points pts{sV, sSh, key, a.sampler, a.ntab};
-    const long long nb = a.st->n_bank;
+    const long long nb = a.st->n_bank + a.st->r_lead;   // slots ahead of the births
+    const bool lead_staged = a.lead_staged != 0;
     const long long N = s_rs.N;
     const T wbar_t = (T)s_rs.wbar;
     const double w_ref = s_rs.w_ref;
@@ -456,9 +462,17 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
             if (a.perm_slots && j < a.nslots) a.stg.cell[j] = -1;   // unused slots sort last, as dead
             continue;
         }
-        const Particle<T> pr = remap_slot<T>(a, pts, j, nb, wbar_t, sums, &leaked, &killed, &segs, &err);
-        a.stg.cell[j] = pr.alive ? pr.cell : -1;
-        a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
+        Particle<T> pr;
+        if (lead_staged && j < nb) {
+            // steps 3'/4': the MC leg staged its census here; it enters the census as it is
+            pr.cell = a.stg.cell[j];
+            pr.alive = pr.cell >= 0;
+            pr.w = pr.alive ? a.stg.w[j] : T(0);
+        } else {
+            pr = remap_slot<T>(a, pts, j, nb, wbar_t, sums, &leaked, &killed, &segs, &err);
+            a.stg.cell[j] = pr.alive ? pr.cell : -1;
+            a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
+        }
         if (pr.alive) {
             ++cnt;
             qs += quant<T>(pr.w, w_ref, qsc);
@@ -534,7 +548,7 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
         if (iv[1]) atomicAdd(&a.st->r_killed, (unsigned long long)iv[1]);
         if (iv[2]) atomicAdd(&a.st->r_segments, (unsigned long long)iv[2]);
         if (iv[3]) { atomicAdd(&a.st->r_errors, (unsigned long long)iv[3]); atomicOr(&a.st->status, kStSegments); }
-        if (blockIdx.x == 0) { a.st->k_rw = kw; a.st->r_histories = (unsigned long long)N; }
+        if (blockIdx.x == 0) { a.st->k_rw = kw; a.st->r_histories = (unsigned long long)(N - a.st->r_lead); }
     }
 }
 
@@ -627,7 +641,7 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
             ah += shi[u] + (nl < al ? 1ull : 0ull);
             al = nl;
         }
-        const long long nb = st->n_bank;
+        const long long nb = st->n_bank + st->r_lead;
         const long long nbirth = st->remap_W > 0 ? n_hist : 0;
         const long long N = nb + nbirth;
         const int krw = scale_exponent((double)(N > 0 ? N : 1) * st->w_ref, 125);
@@ -780,11 +794,16 @@ static cudaError_t remap_t(hyb_problem* p) {
     const int g = (p->ncells + 255) / 256;
     cudaError_t e = cudaMemsetAsync(&p->st->remap_rmax, 0, sizeof(double), s);
     if (e != cudaSuccess) return e;
+    const bool additive = p->d.remap_variant == 1;
     remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_d, p->post_d,
-                                           p->sn_phi_d, p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st);
+                                           p->sn_phi_d, p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st,
+                                           additive ? 0 : 1);
     e = launch_cdf_build(p, p->rem_q, p->rem_cdf, &p->st->remap_W, &p->st->remap_qmax);
     if (e != cudaSuccess) return e;
-    remap_prep_kernel<<<1, 1, 0, s>>>(p->st, p->d.n_hist);
+    // steps 3'/4': the leg's census (bank slots, then its n_hist source births) leads the slots
+    const long long lead = additive && p->has_src ? p->d.n_hist : 0;
+    const double w_lead = additive && p->has_src ? p->w_src / (double)p->d.n_hist : 0.0;
+    remap_prep_kernel<<<1, 1, 0, s>>>(p->st, p->d.n_hist, lead, w_lead);
 
     RemapArgs<T> a;
     a.nx = p->nx; a.ny = p->ny;
@@ -807,8 +826,9 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.seed = p->d.seed;
     a.st = p->st;
     a.blk = p->blk;
-    const long long maxN = p->bank_cap + p->d.n_hist;
+    const long long maxN = p->stage_slots;
     a.stg = stage_view<T>(p);
+    a.lead_staged = additive ? 1 : 0;
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
     const size_t smem = (size_t)(a.ntab * kNibbleWords + a.ntab + 1) * sizeof(uint32_t);
     // zero the remap counters
@@ -838,6 +858,7 @@ cudaError_t launch_remap(hyb_problem* p) { return p->prec == HYB_FP64 ? remap_t<
 // w_ref = the power of two at or above max(|w| of the step-start bank, source weight per birth).
 __global__ void census_prep_kernel(DevState* st, double w_src, long long n_hist) {
     st->remap_W = w_src;
+    st->r_lead = 0;
     const double wmax = fmax(st->bank_wmax, w_src > 0 ? w_src / (double)n_hist : 0.0);
     st->w_ref = wmax > 0 ? pow2_ceil(wmax) : 1.0;
 }
@@ -869,9 +890,10 @@ static cudaError_t census_t(hyb_problem* p) {
     a.st = p->st;
     a.blk = p->blk;
     a.perm = nullptr;
-    const long long maxN = p->bank_cap + p->d.n_hist;
+    const long long maxN = p->stage_slots;
     a.nslots = maxN;
     a.perm_slots = 0;
+    a.lead_staged = 0;
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
     cudaError_t e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
     if (e != cudaSuccess) return e;

@@ -429,3 +429,52 @@ def test_collided_solve_anderson(H, orc, prec):
         P.close()
     print(f"\nSI iterations plain {iters[0]} (oracle {it_o}), Anderson(4) {iters[4]}")
     assert iters[4] < iters[0] / 2
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_additive_remap_variant(H, orc, order):
+    """Steps 3'/4' of the previous hybrids (Eq. (R')): the census is the MC leg's census followed
+    by the survivors of births from sigma_s (phi_post + phi_c). FP64 against the oracle over three
+    steps (banks cell for cell, fluxes to rounding), with and without a comb."""
+    cb = W.checkerboard(n_s=1, n_hist=6000, cells_per_block=2)
+    for spec in (W.pulse(n_hist=4096, n_s=1), cb, cb.with_(census_cap=4000)):
+        spec = spec.with_(remap_variant=1, precision=W.FP64, census_order=order, sn_tol=1e-12)
+        P = H.Problem(spec)
+        ob = orc.init_bank(spec, spec.ic) if spec.ic is not None else None
+        for k in range(3):
+            P.step(1)
+            r = orc.step(spec, k, ob)
+            ob = r["bank"]
+            gb = P.bank()
+            assert gb["n"] == ob["n"], (spec.name, k)
+            assert np.array_equal(gb["cell"], ob["cell"]), (spec.name, k)
+            for q in ("fx", "fy", "ox", "oy"):
+                assert np.allclose(gb[q], ob[q], rtol=0, atol=1e-12 * max(spec.lx, 1.0)), (spec.name, k, q)
+            assert np.allclose(gb["w"], ob["w"], rtol=1e-9, atol=0), (spec.name, k)
+            f = P.tally("flux")
+            assert np.allclose(f, r["flux"], rtol=1e-9, atol=1e-12 * np.max(np.abs(r["flux"]))), (spec.name, k)
+        P.close()
+
+
+def test_additive_remap_variant_fp32(H, orc):
+    """The FP32 path of steps 3'/4': step totals close to the FP64 oracle's."""
+    spec = W.checkerboard(n_s=1, n_hist=20_000, cells_per_block=2).with_(remap_variant=1, sn_tol=1e-7)
+    P = H.Problem(spec.with_(precision=W.FP32))
+    ob = None
+    for k in range(3):
+        P.step(1)
+        r = orc.step(spec.with_(precision=W.FP64, sn_tol=1e-12), k, ob)
+        ob = r["bank"]
+        gb = P.bank()
+        assert abs(gb["n"] - ob["n"]) <= max(3, ob["n"] // 1000)
+        assert abs(gb["w"].sum() / ob["w"].sum() - 1) < 1e-4
+        f = P.tally("flux")
+        assert abs(f.sum() / r["flux"].sum() - 1) < 1e-4
+    P.close()
+
+
+def test_remap_variant_validation(H):
+    with pytest.raises(H.HybError):
+        H.Problem(W.pulse(n_hist=100).with_(remap_variant=1, n_s=W.NS_INF))
+    with pytest.raises(H.HybError):
+        H.Problem(W.pulse(n_hist=100).with_(remap_variant=2))
