@@ -24,14 +24,22 @@ from . import workloads as W
 
 
 def problem(n_hist: int, seed: int, sampler: int, n_s: int = 2, precision: int = W.FP32,
-            census_order: int = 0, sigma_scale: float = 1.0) -> W.ProblemSpec:
+            census_order: int = 0, sigma_scale: float = 1.0, remap_variant: int = 0,
+            cap_factor: int = 1) -> W.ProblemSpec:
     """Checkerboard of 7x7 one-centimetre blocks at 4 cells per block (28x28), S4, absorber /
-    scatterer blocks (cross sections times sigma_scale), Q = 1 in the centre block, dt = 0.1."""
+    scatterer blocks (cross sections times sigma_scale), Q = 1 in the centre block, dt = 0.1.
+    remap_variant 1: steps 3'/4' of the previous hybrids; cap_factor: census cap in units of
+    n_hist (large: no comb)."""
     order = "cell" if census_order else "slot"
     sp = W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision, sampler=sampler, cells_per_block=4)
+    name = f"checkerboard28 x{sigma_scale:g} N_s={'inf' if n_s == W.NS_INF else n_s}, census in {order} order"
+    if remap_variant:
+        name += ", remap 3'/4'"
+    if cap_factor != 1:
+        name += f", census cap {cap_factor} n_hist"
     return sp.with_(sigma_a=sp.sigma_a * sigma_scale, sigma_s=sp.sigma_s * sigma_scale, sn_order=4, sn_tol=1e-6,
-                    census_order=census_order,
-                    name=f"checkerboard28 x{sigma_scale:g} N_s={'inf' if n_s == W.NS_INF else n_s}, census in {order} order")
+                    census_order=census_order, remap_variant=remap_variant, census_cap=cap_factor * n_hist,
+                    name=name)
 
 
 def end_flux(spec: W.ProblemSpec, steps: int) -> np.ndarray:
@@ -47,9 +55,11 @@ def fit_alpha(ns, errs) -> float:
 
 
 def study(log2_n=range(10, 21), seeds=range(16), steps: int = 4, ref_log2: int = 24, ref_seeds=range(100, 104),
-          n_s: int = 2, census_order: int = 0, sigma_scale: float = 1.0, spec_fn=problem) -> dict:
+          n_s: int = 2, census_order: int = 0, sigma_scale: float = 1.0, remap_variant: int = 0,
+          cap_factor: int = 1, spec_fn=problem) -> dict:
     import torch
-    mk = lambda n, s, smp: spec_fn(n, s, smp, n_s, census_order=census_order, sigma_scale=sigma_scale)   # noqa: E731
+    mk = lambda n, s, smp: spec_fn(n, s, smp, n_s, census_order=census_order, sigma_scale=sigma_scale,   # noqa: E731
+                                   remap_variant=remap_variant, cap_factor=cap_factor)
     ref = np.mean([end_flux(mk(1 << ref_log2, s, W.SOBOL), steps) for s in ref_seeds], axis=0)
     nref = float(np.linalg.norm(ref))
     out = {"workload": mk(1, 0, W.SOBOL).name, "steps": steps, "reference_histories": 1 << ref_log2,
@@ -98,5 +108,9 @@ if __name__ == "__main__":
         for steps in (1, 4):
             print(json.dumps(study(steps=steps, n_s=n_s)), flush=True)
     print(json.dumps(study(steps=4, n_s=2, census_order=1)), flush=True)
+    # the previous hybrids' remap (steps 3'/4'), and both remaps without a comb (census cap 8 n_hist)
+    print(json.dumps(study(steps=4, n_s=2, remap_variant=1)), flush=True)
+    print(json.dumps(study(steps=4, n_s=2, cap_factor=8, ref_log2=22)), flush=True)
+    print(json.dumps(study(steps=4, n_s=2, remap_variant=1, cap_factor=8, ref_log2=22)), flush=True)
     print(json.dumps({"ns_sweep": ns_sweep()}), flush=True)
     print(json.dumps({"ns_sweep": ns_sweep(sigma_scale=10.0)}), flush=True)
