@@ -43,7 +43,8 @@ class _Problem(C.Structure):
                 ("n_s", C.c_int32), ("sampler", C.c_int32), ("n_hist", C.c_int64),
                 ("seed", C.c_uint64), ("sn_order", C.c_int32), ("handoff_full", C.c_int32),
                 ("w_min", C.c_double), ("census_cap", C.c_int64), ("sn_tol", C.c_double),
-                ("sn_max_iter", C.c_int32), ("census_order", C.c_int32), ("remap_variant", C.c_int32)]
+                ("sn_max_iter", C.c_int32), ("census_order", C.c_int32), ("remap_variant", C.c_int32),
+                ("n_s_cell", C.POINTER(C.c_int32))]
 
 
 class _Bank(C.Structure):
@@ -91,20 +92,24 @@ class _Keep:
     sa: np.ndarray
     ss: np.ndarray
     q: np.ndarray | None
+    nsc: np.ndarray | None = None
 
 
 def _problem(spec) -> tuple[_Problem, _Keep]:
     sa = np.ascontiguousarray(spec.sigma_a, dtype=np.float64).ravel()
     ss = np.ascontiguousarray(spec.sigma_s, dtype=np.float64).ravel()
     q = None if spec.Q is None else np.ascontiguousarray(spec.Q, dtype=np.float64).ravel()
+    nsc = getattr(spec, "n_s_cell", None)
+    nsc = None if nsc is None else np.ascontiguousarray(nsc, dtype=np.int32).ravel()
     p = _Problem(nx=spec.nx, ny=spec.ny, lx=spec.lx, ly=spec.ly, sigma_a=_dp(sa), sigma_s=_dp(ss),
                  Q=_dp(q), c=spec.c, dt=spec.dt, n_s=spec.n_s, sampler=spec.sampler,
                  n_hist=spec.n_hist, seed=spec.seed, sn_order=spec.sn_order,
                  handoff_full=spec.handoff_full, w_min=spec.w_min, census_cap=spec.census_cap,
                  sn_tol=spec.sn_tol, sn_max_iter=spec.sn_max_iter,
                  census_order=getattr(spec, "census_order", 0),
-                 remap_variant=getattr(spec, "remap_variant", 0))
-    return p, _Keep(sa, ss, q)
+                 remap_variant=getattr(spec, "remap_variant", 0),
+                 n_s_cell=None if nsc is None else nsc.ctypes.data_as(C.POINTER(C.c_int32)))
+    return p, _Keep(sa, ss, q, nsc)
 
 
 def empty_bank(cap: int) -> dict:

@@ -259,6 +259,7 @@ typedef struct {
     int32_t sn_max_iter;
     int32_t census_order;   // 0: census in slot order (bank slots, then births); 1: stable by cell
     int32_t remap_variant;  // 0: Eq. (R) relabelling remap; 1: steps 3'/4' (additive, previous hybrids)
+    const int32_t* n_s_cell;  // nx*ny scatter limits per cell in [0, n_s] (space-dependent N_s), or NULL
 } or_problem;
 
 typedef struct {
@@ -453,14 +454,20 @@ struct Leg {
 
     // Track one history from its start state to termination; returns the fate and fills the
     // record (final cell, fate, final scatter count, segments).
+    // Space-dependent N_s (the paper's outlook, Sec. 4): a segment in cell k is pre-limit while
+    // the history's scatter count n is below N_s(k), post-limit otherwise; the optical depth to the
+    // next scatter is kept across post-limit stretches (exponential, so memoryless). Uniform N_s:
+    // N_s(k) = n_s everywhere.
+    int limit(int k) const { return P->n_s_cell ? P->n_s_cell[k] : P->n_s; }
+
     void run(uint64_t idx, int ix, int iy, double fx, double fy, double ox, double oy,
              double w, double s_rem, int32_t* rec) {
-        const int Ns = P->n_s;
+        const int Ns = P->n_s;   // the largest limit: sets the point dimensions
         const double DX = M.dx, DY = M.dy;
         const double w_start = w;
         w_source += w;
         int n = 0;
-        if (Ns == 0) ++reached;
+        if (limit(iy * M.nx + ix) == 0) ++reached;
         double tau = 0.0;
         if (Ns > 0) tau = neg_log(unit(pts(idx, 5)));
         int64_t seg = 0;
@@ -468,10 +475,11 @@ struct Leg {
         while (seg < kMaxSegments) {
             ++seg;
             const int k = iy * M.nx + ix;
+            const int Nk = limit(k);
             const double sa = P->sigma_a[k], ss = P->sigma_s[k], st = sa + ss;
             const double dxf = ox > 0 ? (DX - fx) / ox : (ox < 0 ? fx / (-ox) : kInf);
             const double dyf = oy > 0 ? (DY - fy) / oy : (oy < 0 ? fy / (-oy) : kInf);
-            const double dcol = (n < Ns && ss > 0) ? tau / ss : kInf;
+            const double dcol = (n < Nk && ss > 0) ? tau / ss : kInf;
             const double dcen = s_rem;
             // event: collision wins ties over faces, faces over census
             double l; int ev; bool xc = false, yc = false;
@@ -480,7 +488,7 @@ struct Leg {
                 l = std::min(dxf, dyf); ev = 1; xc = (dxf == l); yc = (dyf == l);
             } else { l = dcen; ev = 2; }
 
-            if (n < Ns) {
+            if (n < Nk) {
                 // pre-limit: implicit capture with sigma_a, tally <Psi>_pre
                 const double att = -std::expm1(-sa * l);
                 pre[k] += (sa > 0) ? (long double)(w * att / sa) : (long double)(w * l);
@@ -536,8 +544,8 @@ struct Leg {
                 ++n; ++collisions;
                 const int base = 5 + 3 * (n - 1);
                 iso_direction(unit(pts(idx, base + 1)), unit(pts(idx, base + 2)), &ox, &oy);
-                if (n < Ns) tau = neg_log(unit(pts(idx, 5 + 3 * n)));
-                else { tau = 0.0; ++reached; }
+                tau = n < Ns ? neg_log(unit(pts(idx, 5 + 3 * n))) : 0.0;
+                if (n >= Nk) ++reached;
             }
             if (P->w_min > 0 && w < P->w_min * w_start) {
                 fate = kFateKilled; ++killed; w_killed += w;

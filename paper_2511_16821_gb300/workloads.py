@@ -54,6 +54,7 @@ class ProblemSpec:
     census_order: int = 0
     sn_accel: int = 0
     remap_variant: int = 0          # 0: Eq. (R) relabelling remap; 1: steps 3'/4' of the previous hybrids
+    n_s_cell: np.ndarray | None = None   # per-cell scatter limits in [0, n_s] (space-dependent N_s)
     name: str = field(default="problem")
 
     @property

@@ -253,3 +253,73 @@ def test_direction_is_isotropic(orc):
     assert abs(np.mean(b["ox"] ** 2) - 1 / 3) < 1e-3 and abs(np.mean(b["oy"] ** 2) - 1 / 3) < 1e-3
     assert abs(np.mean(b["ox"])) < 1e-3 and abs(np.mean(b["oy"] * b["ox"])) < 1e-3
     assert abs(np.mean(b["t_frac"]) - 0.5) < 1e-4
+
+
+# ------------------------------------------------------------------------------------------------
+# space-dependent N_s (per-cell scatter limits)
+# ------------------------------------------------------------------------------------------------
+def _cb_limits(spec, scatter_limit, absorber_limit=0):
+    """Per-cell limits on the checkerboard: absorber cells (sigma_s = 0) and scatterer cells."""
+    return np.where(spec.sigma_s > 0, scatter_limit, absorber_limit).astype(np.int32)
+
+
+def test_uniform_cell_limits_equal_scalar_ns(orc):
+    spec = W.checkerboard(n_s=2, n_hist=3000, cells_per_block=4)
+    bank = W.random_bank(spec, 1500, seed=5)
+    a = orc.mc_leg(spec, 1, bank, want_hist=True)
+    b = orc.mc_leg(spec.with_(n_s_cell=np.full(spec.ncells, 2, np.int32)), 1, bank, want_hist=True)
+    for k in ("pre", "post", "mom", "hist"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["stats"] == b["stats"]
+
+
+def test_zero_cell_limits_equal_ns0(orc):
+    """All limits 0 under a larger n_s: no scatter anywhere, every segment post-limit: the N_s = 0
+    leg bit for bit (the optical depths drawn for the larger n_s are never used)."""
+    spec = W.checkerboard(n_s=3, n_hist=3000, cells_per_block=4)
+    bank = W.random_bank(spec, 1500, seed=6)
+    a = orc.mc_leg(spec.with_(n_s=0), 1, bank, want_hist=True)
+    b = orc.mc_leg(spec.with_(n_s_cell=np.zeros(spec.ncells, np.int32)), 1, bank, want_hist=True)
+    for k in ("pre", "post", "mom", "hist"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["stats"] == b["stats"]
+
+
+def test_cell_limits_split_the_tallies_by_region(orc):
+    """A segment is pre-limit exactly when the scatter count is below the limit of its cell: no
+    pre-limit track length in zero-limit cells, and no post-limit track length (nor hand-off) in
+    cells whose limit no history reaches; the leg balance still closes."""
+    spec = W.checkerboard(n_s=12, n_hist=4000, cells_per_block=4)
+    rng = np.random.default_rng(3)
+    lim = np.where(rng.uniform(size=spec.ncells) < 0.5, 0, 12).astype(np.int32)
+    spec = spec.with_(n_s_cell=lim)
+    bank = W.random_bank(spec, 2000, seed=7)
+    r = orc.mc_leg(spec, 1, bank, want_hist=True)
+    assert r["stats"]["collisions"] > 0
+    assert np.max(r["hist"][:, 2]) < 12
+    assert np.all(r["pre"][lim == 0] == 0.0)
+    assert np.all(r["post"][lim == 12] == 0.0) and np.all(r["mom"][lim == 12] == 0.0)
+    assert np.any(r["pre"][lim == 12] > 0) and np.any(r["post"][lim == 0] > 0)
+    s = r["stats"]
+    out = s["w_absorbed"] + s["w_leaked"] + s["w_census"] + s["w_handoff"] + s["w_killed"]
+    assert math.isclose(s["w_source"], out, rel_tol=1e-13)
+    assert math.isclose(s["w_handoff"], float(np.sum(r["mom"][:, 0])), rel_tol=1e-12)
+
+
+def test_zero_limits_in_non_scattering_cells_give_the_pure_mc_leg(orc):
+    """Limit 0 where sigma_s = 0 (nothing to hand off there: post-limit attenuation with sigma_t =
+    sigma_a is the pre-limit implicit capture) and a limit no history reaches elsewhere: the leg is
+    the N_s = infinity leg, its pre tally split into pre + post by region, weights and census alike."""
+    spec = W.checkerboard(n_s=20, n_hist=3000, cells_per_block=4)
+    bank = W.random_bank(spec, 1500, seed=8)
+    lim = _cb_limits(spec, 20, 0)
+    a = orc.mc_leg(spec.with_(n_s=W.NS_INF), 1, bank, want_hist=True, want_census=True)
+    b = orc.mc_leg(spec.with_(n_s_cell=lim), 1, bank, want_hist=True, want_census=True)
+    assert np.max(b["hist"][:, 2]) < 20
+    assert np.array_equal(a["pre"], b["pre"] + b["post"])
+    assert np.all(b["mom"] == 0.0) and b["stats"]["w_handoff"] == 0.0
+    assert np.array_equal(a["hist"][:, :2], b["hist"][:, :2]) and np.array_equal(a["hist"][:, 3], b["hist"][:, 3])
+    for k in ("cell", "fx", "fy", "ox", "oy", "w"):
+        assert np.array_equal(a["census"][k], b["census"][k]), k
+    for k in ("w_absorbed", "w_leaked", "w_census"):
+        assert a["stats"][k] == b["stats"][k], k
