@@ -102,11 +102,13 @@ class Clocks:
 
 CENSUS_ORDER = 0
 SN_ACCEL = 0
+WARM = 1
 
 
-def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0, warm: int = 1) -> W.ProblemSpec:
+def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0, warm: int | None = None) -> W.ProblemSpec:
     """The benchmark workload; source iteration starts from the previous step's collided flux
     (the same fixed point, fewer sweeps)."""
+    warm = WARM if warm is None else warm
     return W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision).with_(sn_warm_start=warm,
                                                                                        census_order=CENSUS_ORDER,
                                                                                        sn_accel=SN_ACCEL)
@@ -388,13 +390,16 @@ def main():
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (FP32, no profile/e2e/CPU legs): the case used for ncu captures")
     ap.add_argument("--sn-accel", type=int, default=0, help="Anderson depth of the collided solve (0: plain SI)")
+    ap.add_argument("--sn-warm", type=int, default=1, choices=[0, 1, 2],
+                    help="source-iteration start: 0 zero, 1 previous step's flux, 2 linear extrapolation")
     ap.add_argument("--census-order", type=int, default=0, choices=[0, 1],
                     help="census in slot order (0) or sorted by cell before the comb (1)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    global CENSUS_ORDER, SN_ACCEL
+    global CENSUS_ORDER, SN_ACCEL, WARM
     CENSUS_ORDER = args.census_order
     SN_ACCEL = args.sn_accel
+    WARM = args.sn_warm
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

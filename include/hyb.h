@@ -97,7 +97,9 @@ typedef struct {
     double w_min;             /* relative kill threshold (w < w_min * w_start); 0 = never */
     int64_t census_cap;       /* census capacity after the comb; 0 = n_hist */
     int32_t sn_warm_start;    /* 1: source iteration starts from the previous step's collided
-                                 flux (same fixed point, fewer iterations); 0: from zero */
+                                 flux (same fixed point, fewer iterations); 2: from the linear
+                                 extrapolation 2 phi_{n-1} - phi_{n-2} of the last two steps'
+                                 fluxes (the previous one on the first warm step); 0: from zero */
     int32_t census_order;     /* 0: the census keeps slot order (re-streamed bank slots, then
                                  births); 1: survivors in cell order (stable within a cell)
                                  before the comb, so the systematic comb samples each cell's
@@ -112,6 +114,12 @@ typedef struct {
                                  births from sigma_s (phi_post + phi_c) only, zero initial data,
                                  and the new census is the MC leg's census followed by those
                                  births' survivors. Finite N_s only; not in batches */
+    const int32_t* n_s_cell;  /* nx*ny per-cell scatter limits in [0, n_s] (space-dependent N_s,
+                                 the paper's Sec. 4 outlook), or NULL for n_s everywhere: a
+                                 segment in cell k is pre-limit while the history's scatter count
+                                 is below n_s_cell[k], post-limit otherwise; n_s (finite) is the
+                                 largest limit and fixes the point dimensions. Host pointer,
+                                 copied at creation */
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */

@@ -267,7 +267,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
-        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas;
+        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell;
     int64_t cap, nblk, slots;
     int gr, gc;
 };
@@ -316,6 +316,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.gcol = (size_t)d->ny * ((size_t(1) << z.gc) + 1) * 4;
     z.remf32 = 4 * nc * 4;
     z.siginv = 4 * nc * 4;
+    z.nscell = d->n_s_cell ? nc * 4 : 0;
     z.aah = d->sn_accel > 0 ? 2 * (size_t)(d->sn_accel + 1) * 4 * nc * T : 0;   // Anderson history
     z.aas = d->sn_accel > 0 ? sn_accel_state_bytes() : 0;
     z.rempos = nc * 4;
@@ -330,9 +331,9 @@ size_t layout_bytes(const hyb_problem_desc* d) {
     Layout L;
     const size_t parts[] = {z.st, z.sobol, z.sig, z.sa, z.ss, z.Q, z.cdf_q, z.cdf_row, z.cdf_col, z.cdf_q, z.cdf_row,
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
-                            z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4,
+                            z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
-                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas};
+                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -376,6 +377,7 @@ void assign(hyb_problem* p) {
     p->sn_ty = take(z.snty);
     p->sn_quadbuf = take(z.snqb);
     p->sn_phi_d = (double*)take(z.d4);
+    p->sn_phi_d2 = (double*)take(z.d4);
     p->sn_norm = (double*)take(z.snnorm);
     p->blk = (long long*)take(z.blk);
     p->src_cdf.row_g = (int*)take(z.grow);
@@ -391,6 +393,7 @@ void assign(hyb_problem* p) {
     p->sig_inv = (float*)take(z.siginv);
     p->aa_hist = z.aah ? take(z.aah) : nullptr;
     p->aa_state = z.aas ? take(z.aas) : nullptr;
+    p->ns_cell = z.nscell ? (int32_t*)take(z.nscell) : nullptr;
     p->bank_cap = z.cap;
     p->stage_slots = z.slots;
     p->nblk_max = z.nblk;
@@ -430,6 +433,7 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
     if (d->census_order != 0 && d->census_order != 1) { *why = "census_order must be 0 or 1"; return HYB_EINVAL; }
     if (d->sn_accel < 0 || d->sn_accel > 8) { *why = "sn_accel must be in [0, 8]"; return HYB_EINVAL; }
+    if (d->sn_warm_start < 0 || d->sn_warm_start > 2) { *why = "sn_warm_start must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->remap_variant != 0 && d->remap_variant != 1) { *why = "remap_variant must be 0 or 1"; return HYB_EINVAL; }
     if (d->remap_variant == 1 && d->n_s == HYB_NS_INF) {
         *why = "remap_variant 1 needs a finite N_s (N_s = infinity has no remap)";
@@ -438,6 +442,14 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (!(d->sn_tol >= 0) || !(d->w_min >= 0) || !(d->w_min < 1)) { *why = "sn_tol >= 0 and 0 <= w_min < 1 required"; return HYB_EINVAL; }
     if (!d->sigma_a || !d->sigma_s) { *why = "sigma_a and sigma_s are required"; return HYB_EINVAL; }
     const size_t nc = (size_t)d->nx * d->ny;
+    if (d->n_s_cell) {
+        if (d->n_s == HYB_NS_INF) { *why = "per-cell scatter limits need a finite n_s (their maximum)"; return HYB_EINVAL; }
+        for (size_t k = 0; k < nc; ++k)
+            if (d->n_s_cell[k] < 0 || d->n_s_cell[k] > d->n_s) {
+                *why = "per-cell scatter limits must lie in [0, n_s]";
+                return HYB_EINVAL;
+            }
+    }
     for (size_t k = 0; k < nc; ++k) {
         if (!std::isfinite(d->sigma_a[k]) || d->sigma_a[k] < 0 || !std::isfinite(d->sigma_s[k]) || d->sigma_s[k] < 0) {
             *why = "sigma_a, sigma_s must be finite and >= 0"; return HYB_EINVAL;
@@ -654,19 +666,27 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     const uint32_t* ptab = point_table_host(d->sampler, &ptab_bytes);
     if (chk(cudaMemcpyAsync(p->point_tab, ptab, ptab_bytes, cudaMemcpyHostToDevice, st), "copy point table") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->sig, sig.data(), sig.size(), cudaMemcpyHostToDevice, st), "copy sigma") != HYB_OK) return bail(HYB_ECUDA);
-    // FP32 path: per-cell reciprocals (1/sigma_a, 1/sigma_s, 1/sigma_t, 0), 0 where the cross section is 0
+    // FP32 path: per-cell reciprocals (1/sigma_a, 1/sigma_s, 1/sigma_t), 0 where the cross section is
+    // 0, and the cell's scatter limit as the bits of the fourth word (space-dependent N_s)
     std::vector<float> sinv(4 * nc, 0.0f);
     for (size_t k = 0; k < nc; ++k) {
         const double sa = d->sigma_a[k], ss = d->sigma_s[k], stt = sa + ss;
         sinv[4 * k] = sa > 0 ? (float)(1.0 / sa) : 0.0f;
         sinv[4 * k + 1] = ss > 0 ? (float)(1.0 / ss) : 0.0f;
         sinv[4 * k + 2] = stt > 0 ? (float)(1.0 / stt) : 0.0f;
+        const int32_t lim = d->n_s_cell ? d->n_s_cell[k] : 0;
+        std::memcpy(&sinv[4 * k + 3], &lim, 4);
     }
+    if (d->n_s_cell &&
+        chk(cudaMemcpyAsync(p->ns_cell, d->n_s_cell, nc * 4, cudaMemcpyHostToDevice, st), "copy limits") != HYB_OK)
+        return bail(HYB_ECUDA);
+    p->d.n_s_cell = nullptr;   // the caller's array is not kept: p->ns_cell holds the copy
     if (chk(cudaMemcpyAsync(p->sig_inv, sinv.data(), sinv.size() * 4, cudaMemcpyHostToDevice, st), "copy 1/sigma") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->sa_d, d->sigma_a, nc * 8, cudaMemcpyHostToDevice, st), "copy sa") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->ss_d, d->sigma_s, nc * 8, cudaMemcpyHostToDevice, st), "copy ss") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->Q_d, d->Q ? d->Q : zeros.data(), nc * 8, cudaMemcpyHostToDevice, st), "copy Q") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemsetAsync(p->sn_phi_d, 0, 4 * nc * 8, st), "memset phi") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(cudaMemsetAsync(p->sn_phi_d2, 0, 4 * nc * 8, st), "memset phi") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(sn_clear_counters(p), "memset reduction counters") != HYB_OK) return bail(HYB_ECUDA);
     // quadrature
     p->n_ord = 0;

@@ -59,7 +59,7 @@ struct DevState {
     long long step;            // time-step index n of the next MC leg / remap (t_n = n dt)
     int sn_conv;               // collided solve: converged flag of the current solve
     int sn_iters;              // collided solve: iterations run in the current solve
-    int sn_warm;               // 1 once a solve finished and warm starts are enabled
+    int sn_warm;               // solves finished with warm starts enabled (counted up to 2)
     unsigned int sn_blocks_done;   // source-iteration reduction: blocks finished (last one resets it)
 };
 
@@ -117,7 +117,9 @@ struct hyb_problem {
     uint32_t* point_tab;      // Sobol direction numbers (HYB_SOBOL_DIMS x 32) or Halton tables
                               // (HYB_SOBOL_DIMS x kHaltonWords), by the sampler
     void* sig;                // ncells x 2 (T): sigma_a, sigma_s
-    float* sig_inv;           // ncells x 4: 1/sigma_a, 1/sigma_s, 1/sigma_t, 0 (FP32 leg; 0 where sigma = 0)
+    float* sig_inv;           // ncells x 4: 1/sigma_a, 1/sigma_s, 1/sigma_t (FP32 leg; 0 where sigma = 0),
+                              // then the cell's scatter limit as int bits (space-dependent N_s)
+    int32_t* ns_cell;         // per-cell scatter limits (space-dependent N_s), or null
     double *sa_d, *ss_d, *Q_d;  // FP64 copies for the remap density
     hyb::Cdf2DView src_cdf, rem_cdf;
     double* rem_f;            // 4 x ncells remap density coefficients
@@ -140,6 +142,7 @@ struct hyb_problem {
     void* sn_ty;              // strip-top y traces per ordinate (T)
     void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, precision T
     double* sn_phi_d;         // collided flux, FP64 copy (4 x ncells)
+    double* sn_phi_d2;        // the solution of the step before (extrapolated warm start only)
     double* sn_norm;          // per-block norm partials (Anderson: kAAMax + 2 per block)
     void* aa_hist;            // Anderson acceleration: (depth + 1) iterates g, then residuals f (T)
     void* aa_state;           // Anderson: slots, Gram matrix, mixing weights

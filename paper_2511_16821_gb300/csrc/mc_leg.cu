@@ -32,6 +32,7 @@ struct LegArgs {
     int spread_bank;            // 1: bank slots taken in transposed order (the bank is sorted by cell)
     BankView<T> cens;           // N_s = infinity: end state of history j at slot j (cell -1 unless census)
     int stage_census;
+    const int32_t* ns_cell;     // per-cell scatter limits (space-dependent N_s), or null: n_s everywhere
     Cdf2DView cdf;
     long long n_src;
     T w0;
@@ -251,7 +252,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                     d_abs = 0; d_hand = 0;
                     h.n = 0;
                     h.seg = 0;
-                    if (Ns == 0) ++t.c[6];
+                    if ((a.ns_cell ? __ldg(a.ns_cell + h.iy * nx + h.ix) : Ns) == 0) ++t.c[6];
                     if (h.census_stream) h.tau = Ns > 0 ? P::neglog(P::unit(pts(h.idx, 5))) : T(0);
                     alive = true;
                 }
@@ -272,18 +273,22 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
         load_sig(a.sig, k, &sa, &ss);
         const T st = sa + ss;
         T dxf, dyf, dcol, isa = 0, iss = 0, ist = 0;
+        int Nk = Ns;   // the scatter limit of this cell (space-dependent N_s) or n_s
         if constexpr (kF32) {
-            // FP32: products with per-cell and per-flight reciprocals instead of divisions
+            // FP32: products with per-cell and per-flight reciprocals instead of divisions; the
+            // fourth word of the reciprocal record carries the cell's scatter limit
             const float4 iv = __ldg(a.sig_inv + k);
             isa = iv.x; iss = iv.y; ist = iv.z;
+            if (a.ns_cell) Nk = __float_as_int(iv.w);
             dxf = h.ox > T(0) ? (DX - h.fx) * h.rox : (h.ox < T(0) ? h.fx * (-h.rox) : INF);
             dyf = h.oy > T(0) ? (DY - h.fy) * h.roy : (h.oy < T(0) ? h.fy * (-h.roy) : INF);
-            dcol = (h.n < Ns && ss > T(0)) ? h.tau * iss : INF;
+            dcol = (h.n < Nk && ss > T(0)) ? h.tau * iss : INF;
         } else {
             // FP64: the same divisions as the oracle (bit-identical geometry)
+            if (a.ns_cell) Nk = __ldg(a.ns_cell + k);
             dxf = h.ox > T(0) ? (DX - h.fx) / h.ox : (h.ox < T(0) ? h.fx / (-h.ox) : INF);
             dyf = h.oy > T(0) ? (DY - h.fy) / h.oy : (h.oy < T(0) ? h.fy / (-h.oy) : INF);
-            dcol = (h.n < Ns && ss > T(0)) ? h.tau / ss : INF;
+            dcol = (h.n < Nk && ss > T(0)) ? h.tau / ss : INF;
         }
         T l;
         int ev;
@@ -293,7 +298,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             l = dxf < dyf ? dxf : dyf; ev = 1; xc = (dxf == l); yc = (dyf == l);
         } else { l = h.srem; ev = 2; }
 
-        if (h.n < Ns) {
+        if (h.n < Nk) {
             T att, e;
             P::att_e(sa * l, &att, &e);
             const T pre_c = sa > T(0) ? (kF32 ? h.w * att * isa : h.w * att / sa) : h.w * l;
@@ -353,8 +358,8 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             const int base = 5 + 3 * (h.n - 1);
             iso_dir<T>(pts(h.idx, base + 1), pts(h.idx, base + 2), &h.ox, &h.oy);
             if constexpr (kF32) { h.rox = P::rcp(h.ox); h.roy = P::rcp(h.oy); }
-            if (h.n < Ns) h.tau = P::neglog(P::unit(pts(h.idx, 5 + 3 * h.n)));
-            else { h.tau = T(0); ++t.c[6]; }
+            h.tau = h.n < Ns ? P::neglog(P::unit(pts(h.idx, 5 + 3 * h.n))) : T(0);
+            if (h.n >= Nk) ++t.c[6];
         }
         if (fate < 0 && a.w_min > T(0) && h.w < a.w_min * h.w_start) fate = kFateKilled;
         if (fate < 0 && h.seg >= (int)kMaxSegments) fate = kFateError;
@@ -698,6 +703,7 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.sig = (const T*)p->sig;
     a.sig_inv = (const float4*)p->sig_inv;
     a.n_s = p->d.n_s; a.sampler = p->d.sampler; a.handoff_full = p->d.handoff_full;
+    a.ns_cell = p->ns_cell;
     a.ntab = p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS;
     a.w_min = (T)p->d.w_min;
     a.V = p->point_tab;

@@ -662,20 +662,29 @@ __global__ void sn_mix_kernel(T* phi_new, const T* g_hist, int ncells, int depth
     src[e] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
 }
 
-// start of a solve: clear the stop state; the iterate starts from the previous solution
-// (warm start, re-read from its FP64 copy) or from zero
+// start of a solve: clear the stop state; the iterate starts from zero, from the previous step's
+// solution (warm start, re-read from its FP64 copy), or from the linear extrapolation
+// 2 phi_{n-1} - phi_{n-2} of the last two (extrap, once two solves exist). The fixed point is
+// the same whatever the start.
 template <typename T>
-__global__ void sn_seed_kernel(const double* prev, T* phi, int n, const DevState* st) {
+__global__ void sn_seed_kernel(const double* prev, const double* prev2, T* phi, int n, const DevState* st,
+                               int extrap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) phi[i] = st->sn_warm ? (T)prev[i] : T(0);
+    if (i >= n) return;
+    const int w = st->sn_warm;
+    phi[i] = w == 0 ? T(0) : (extrap && w >= 2 ? (T)(2.0 * prev[i] - prev2[i]) : (T)prev[i]);
 }
 
-__global__ void sn_done_kernel(DevState* st, int warm) { st->sn_warm = warm; }
+// solves finished with warm starts enabled, counted up to 2
+__global__ void sn_done_kernel(DevState* st, int warm) { st->sn_warm = warm ? min(st->sn_warm + 1, 2) : 0; }
 
+// the solution's FP64 copy; with keep, the copy it replaces moves to out_prev
 template <typename T>
-__global__ void sn_to_double_kernel(const T* phi, double* out, int n) {
+__global__ void sn_to_double_kernel(const T* phi, double* out, double* out_prev, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (double)phi[i];
+    if (i >= n) return;
+    if (out_prev) out_prev[i] = out[i];
+    out[i] = (double)phi[i];
 }
 
 // the sn_norm buffer: kAAPart partials per reduction block, then per group, then the group counters
@@ -774,10 +783,13 @@ cudaError_t sn_start(hyb_problem* p) {
         if (e != cudaSuccess) return e;
     }
     const int n = 4 * p->ncells, g = (n + 255) / 256;
+    const int extrap = p->d.sn_warm_start == 2 ? 1 : 0;
     if (p->prec == HYB_FP64)
-        sn_seed_kernel<double><<<g, 256, 0, p->stream>>>(p->sn_phi_d, (double*)p->sn_phi_old, n, p->st);
+        sn_seed_kernel<double><<<g, 256, 0, p->stream>>>(p->sn_phi_d, p->sn_phi_d2, (double*)p->sn_phi_old, n, p->st,
+                                                         extrap);
     else
-        sn_seed_kernel<float><<<g, 256, 0, p->stream>>>(p->sn_phi_d, (float*)p->sn_phi_old, n, p->st);
+        sn_seed_kernel<float><<<g, 256, 0, p->stream>>>(p->sn_phi_d, p->sn_phi_d2, (float*)p->sn_phi_old, n, p->st,
+                                                        extrap);
     return cudaGetLastError();
 }
 
@@ -790,10 +802,13 @@ cudaError_t sn_iteration(hyb_problem* p, int first) {
 
 cudaError_t sn_finish(hyb_problem* p) {
     const int n = 4 * p->ncells;
+    double* keep = p->d.sn_warm_start == 2 ? p->sn_phi_d2 : nullptr;
     if (p->prec == HYB_FP64)
-        sn_to_double_kernel<double><<<(n + 255) / 256, 256, 0, p->stream>>>((const double*)p->sn_phi_old, p->sn_phi_d, n);
+        sn_to_double_kernel<double><<<(n + 255) / 256, 256, 0, p->stream>>>((const double*)p->sn_phi_old, p->sn_phi_d,
+                                                                            keep, n);
     else
-        sn_to_double_kernel<float><<<(n + 255) / 256, 256, 0, p->stream>>>((const float*)p->sn_phi_old, p->sn_phi_d, n);
+        sn_to_double_kernel<float><<<(n + 255) / 256, 256, 0, p->stream>>>((const float*)p->sn_phi_old, p->sn_phi_d,
+                                                                           keep, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     sn_done_kernel<<<1, 1, 0, p->stream>>>(p->st, p->d.sn_warm_start ? 1 : 0);

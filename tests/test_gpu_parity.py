@@ -150,6 +150,8 @@ def leg_cases():
         ("cb_ns2", cb, 5000, 2),
         ("cb_ns4_prng", cb.with_(n_s=4, sampler=W.PRNG), 5000, 4),
         ("cb_ns3_halton", cb.with_(n_s=3, sampler=W.HALTON), 5000, 5),
+        ("cb_ns_cell", cb.with_(n_s=3, n_s_cell=np.random.default_rng(4).integers(0, 4, cb.ncells).astype(np.int32)),
+         5000, 7),
         ("het_kill", het, 4000, 6),
         ("one_cell", W.homogeneous(n=1, L=0.5, sigma_a=0.3, sigma_s=2.0, Q=1.0, n_hist=1, dt=1.0, n_s=2), 1, 0),
         ("no_source_empty", W.homogeneous(n=3, Q=None, n_hist=5), 0, 0),
@@ -196,7 +198,7 @@ def test_initial_bank_parity(H, orc):
 # MC leg, FP32 tracking (cell-local coordinates, int64 fixed-point tallies)
 # ------------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("case", [c for c in leg_cases() if c[0] in ("pulse", "cb_ns0", "cb_ns2", "het_kill",
-                                                                     "cb_ns3_halton")],
+                                                                     "cb_ns3_halton", "cb_ns_cell")],
                          ids=lambda c: c[0])
 def test_mc_leg_fp32_tolerance(H, orc, case):
     """FP32 tracking vs the FP64 oracle: 1e-4 relative on every resolved cell above 1e-3 of the
@@ -303,11 +305,14 @@ def test_remap_parity(H, orc, cap, order):
     assert math.isclose(rs["w_source"], ost["w_source"], rel_tol=1e-10)
 
 
-@pytest.mark.parametrize("prec,order,sampler", [(W.FP64, 0, W.SOBOL), (W.FP32, 0, W.SOBOL), (W.FP64, 1, W.SOBOL),
-                                                (W.FP64, 1, W.HALTON)])
-def test_multistep_hybrid(H, orc, prec, order, sampler):
+@pytest.mark.parametrize("prec,order,sampler,limits", [(W.FP64, 0, W.SOBOL, 0), (W.FP32, 0, W.SOBOL, 0),
+                                                       (W.FP64, 1, W.SOBOL, 0), (W.FP64, 1, W.HALTON, 0),
+                                                       (W.FP64, 0, W.SOBOL, 1)])
+def test_multistep_hybrid(H, orc, prec, order, sampler, limits):
     spec = W.pulse(n_hist=8192).with_(precision=prec, sn_tol=1e-12 if prec == W.FP64 else 1e-7, census_order=order,
                                       sampler=sampler)
+    if limits:   # space-dependent N_s: limit 2 in the left half, 0 in the right half
+        spec = spec.with_(n_s=2, n_s_cell=np.where(np.arange(spec.ncells) % spec.nx < spec.nx // 2, 2, 0))
     ospec = spec.with_(precision=W.FP64, sn_tol=1e-12)
     P = H.Problem(spec)
     ob = orc.init_bank(ospec, ospec.ic)
@@ -474,6 +479,8 @@ def test_additive_remap_variant_fp32(H, orc):
 
 
 def test_remap_variant_validation(H):
+    with pytest.raises(H.HybError):   # per-cell limits above n_s
+        H.Problem(W.pulse(n_hist=100).with_(n_s=1, n_s_cell=np.full(256, 2, np.int32)))
     with pytest.raises(H.HybError):
         H.Problem(W.pulse(n_hist=100).with_(remap_variant=1, n_s=W.NS_INF))
     with pytest.raises(H.HybError):
