@@ -127,9 +127,10 @@ cudaError_t issue_phase(hyb_batch* b, int q, int phase) {
         for (size_t i = 0; i < n; ++i) {
             hyb_problem* p = b->probs[i];
             const size_t nc = (size_t)p->ncells, acc = p->prec == HYB_FP64 ? 16 : 8;
-            ck(cudaMemsetAsync(p->acc_pre, 0, nc * acc, b->s0));
-            ck(cudaMemsetAsync(p->acc_post, 0, nc * acc, b->s0));
-            ck(cudaMemsetAsync(p->acc_mom, 0, 4 * nc * acc, b->s0));
+            const size_t ncp = (size_t)p->tally_copies;
+            ck(cudaMemsetAsync(p->acc_pre, 0, ncp * nc * acc, b->s0));
+            ck(cudaMemsetAsync(p->acc_post, 0, ncp * nc * acc, b->s0));
+            ck(cudaMemsetAsync(p->acc_mom, 0, ncp * 4 * nc * acc, b->s0));
             ck(cudaMemsetAsync(p->st, 0, offsetof(hyb::DevState, r_histories), b->s0));
             ck(cudaMemsetAsync(&p->st->status, 0, sizeof(int), b->s0));
         }

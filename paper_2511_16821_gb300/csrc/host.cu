@@ -278,6 +278,17 @@ static int64_t stage_slots(const hyb_problem_desc* d, int64_t cap) {
     return cap + d->n_hist * (d->remap_variant == 1 ? 2 : 1);
 }
 
+// Copies of the fixed-point tally arrays: the leg's warps add into copy (warp index mod copies),
+// so the adds to a hot cell (the source region) spread over several addresses; the normalisation
+// adds the copies exactly. Eight copies while they take at most 512 MB, fewer above.
+int tally_copies(const hyb_problem_desc* d) {
+    const size_t acc = d->precision == HYB_FP64 ? 16 : 8;
+    const size_t per = 6 * (size_t)d->nx * d->ny * acc;   // pre, post, 4 moments
+    int c = 8;
+    while (c > 1 && (size_t)c * per > ((size_t)512 << 20)) c >>= 1;
+    return c;
+}
+
 Sizes sizes(const hyb_problem_desc* d) {
     Sizes z;
     const size_t nc = (size_t)d->nx * d->ny;
@@ -298,8 +309,8 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.bank = bank_cell_bytes(z.cap) + 5 * (size_t)z.cap * T;
     z.slots = stage_slots(d, z.cap);
     z.stage = bank_cell_bytes(z.slots) + 5 * (size_t)z.slots * T;
-    z.acc1 = nc * acc;
-    z.acc4 = 4 * nc * acc;
+    z.acc1 = (size_t)tally_copies(d) * nc * acc;
+    z.acc4 = (size_t)tally_copies(d) * 4 * nc * acc;
     z.d1 = nc * 8;
     z.d4 = 4 * nc * 8;
     z.sn4 = 4 * nc * T;
@@ -361,6 +372,7 @@ void assign(hyb_problem* p) {
     p->bank[0] = take(z.bank);
     p->bank[1] = take(z.bank);
     p->stage = take(z.stage);
+    p->tally_copies = tally_copies(&p->d);
     p->acc_pre = take(z.acc1);
     p->acc_post = take(z.acc1);
     p->acc_mom = take(z.acc4);
@@ -747,9 +759,10 @@ hyb_status hyb_destroy_problem(hyb_problem* p) {
 static hyb_status leg_launch(hyb_problem* p, int32_t* hist) {
     const size_t nc = (size_t)p->ncells;
     const size_t acc = p->prec == HYB_FP64 ? 16 : 8;
-    HYB_CU(p, cudaMemsetAsync(p->acc_pre, 0, nc * acc, p->stream));
-    HYB_CU(p, cudaMemsetAsync(p->acc_post, 0, nc * acc, p->stream));
-    HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, 4 * nc * acc, p->stream));
+    const size_t ncp = (size_t)p->tally_copies;
+    HYB_CU(p, cudaMemsetAsync(p->acc_pre, 0, ncp * nc * acc, p->stream));
+    HYB_CU(p, cudaMemsetAsync(p->acc_post, 0, ncp * nc * acc, p->stream));
+    HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, ncp * 4 * nc * acc, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->st, 0, offsetof(DevState, r_histories), p->stream));
     HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
     HYB_CU(p, launch_mc_leg(p, hist));

@@ -274,6 +274,12 @@ template <> struct Prec<float> {
     static __device__ __forceinline__ double to_double(const acc_t* p, double inv_scale) {
         return (double)(long long)(*p) * inv_scale;
     }
+    // the sum of n copies stride apart, exact (int64 two's complement), as a double
+    static __device__ __forceinline__ double sum_to_double(const acc_t* p, size_t stride, int n, double inv_scale) {
+        unsigned long long v = 0;
+        for (int c = 0; c < n; ++c) v += p[c * stride];
+        return (double)(long long)v * inv_scale;
+    }
     static constexpr int kSeries = 11;
 };
 
@@ -383,6 +389,17 @@ template <> struct Prec<double> {
     }
     static __device__ __forceinline__ double to_double(const acc_t* p, double inv_scale) {
         return acc128_to_double(p->lo, p->hi, inv_scale);
+    }
+    // the sum of n copies stride apart, exact (128-bit two's complement), as a double
+    static __device__ __forceinline__ double sum_to_double(const acc_t* p, size_t stride, int n, double inv_scale) {
+        unsigned long long lo = 0, hi = 0;
+        for (int c = 0; c < n; ++c) {
+            const acc_t v = p[c * stride];
+            const unsigned long long nl = lo + v.lo;
+            hi += v.hi + (nl < lo ? 1ull : 0ull);
+            lo = nl;
+        }
+        return acc128_to_double(lo, hi, inv_scale);
     }
     static constexpr int kSeries = 19;
 };

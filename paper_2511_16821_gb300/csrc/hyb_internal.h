@@ -132,7 +132,8 @@ struct hyb_problem {
     void* bank[2];            // two SoA banks (T)
     void* stage;              // remap staging SoA, bank_cap + n_hist slots (T)
     int cur;                  // current bank index
-    void* acc_pre; void* acc_post; void* acc_mom;   // fixed-point tallies
+    void* acc_pre; void* acc_post; void* acc_mom;   // fixed-point tallies, tally_copies copies each
+    int tally_copies;         // copies of the tally arrays (spreads adds to hot cells over addresses)
     double *pre_d, *post_d, *mom_d, *flux_d;        // normalised tallies (FP64)
     double *pre_raw, *post_raw;                     // raw track-length sums (FP64)
     double sig_s_max;         // max sigma_s (bound of the hand-off moments)

@@ -36,7 +36,8 @@ struct LegArgs {
     Cdf2DView cdf;
     long long n_src;
     T w0;
-    typename Prec<T>::acc_t *pre, *post, *mom;
+    typename Prec<T>::acc_t *pre, *post, *mom;   // ncopy copies, ncells (pre, post) / 4 ncells (mom) apart
+    int ncopy;                  // tally copies: each warp adds into copy (global warp index mod ncopy)
     DevState* st;
     int32_t* hist;
     double sig_s_max, w_src_total, cdt_d;
@@ -185,6 +186,12 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
     const int nx = a.nx, ny = a.ny;
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
+    // this warp's tally copy: adds to a hot cell spread over ncopy addresses (integer sums, so
+    // the total does not depend on which copy an add lands in)
+    const size_t cp = (size_t)(((int)blockIdx.x * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5)) % a.ncopy);
+    typename P::acc_t* const pre_b = a.pre + cp * (size_t)nx * ny;
+    typename P::acc_t* const post_b = a.post + cp * (size_t)nx * ny;
+    typename P::acc_t* const mom_b = a.mom + cp * 4 * (size_t)nx * ny;
 
     Points pts;
     pts.NT = sV;
@@ -302,7 +309,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             T att, e;
             P::att_e(sa * l, &att, &e);
             const T pre_c = sa > T(0) ? (kF32 ? h.w * att * isa : h.w * att / sa) : h.w * l;
-            t.c[8] += P::add(&a.pre[k], pre_c, sc_t);
+            t.c[8] += P::add(&pre_b[k], pre_c, sc_t);
             d_abs += (wacc_t)(h.w * att);
             h.w = h.w * e;
             h.tau = P::msub(h.tau, ss, l);
@@ -310,20 +317,20 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             T att, e;
             P::att_e(st * l, &att, &e);
             const T post_c = st > T(0) ? (kF32 ? h.w * att * ist : h.w * att / st) : h.w * l;
-            t.c[8] += P::add(&a.post[k], post_c, sc_t);
+            t.c[8] += P::add(&post_b[k], post_c, sc_t);
             if (ss > T(0)) {
                 T g0, g1, g2;
                 gfun<T>(st * l, e, att, &g0, &g1, &g2);
                 const T I0 = l * g0, I1 = l * l * g1, I2 = l * l * l * g2;
                 const T sw = ss * h.w;
-                t.c[8] += P::add(&a.mom[4 * k + 0], sw * I0, sc_m);
+                t.c[8] += P::add(&mom_b[4 * k + 0], sw * I0, sc_m);
                 if (a.handoff_full) {
                     const T xi0 = T(2) * h.fx / DX - T(1), eta0 = T(2) * h.fy / DY - T(1);
                     const T axi = T(2) * h.ox / DX, aeta = T(2) * h.oy / DY;
                     // explicit fused forms: the same rounding in every kernel this is inlined into
-                    t.c[8] += P::add(&a.mom[4 * k + 1], sw * P::fma_(xi0, I0, axi * I1), sc_m);
-                    t.c[8] += P::add(&a.mom[4 * k + 2], sw * P::fma_(eta0, I0, aeta * I1), sc_m);
-                    t.c[8] += P::add(&a.mom[4 * k + 3],
+                    t.c[8] += P::add(&mom_b[4 * k + 1], sw * P::fma_(xi0, I0, axi * I1), sc_m);
+                    t.c[8] += P::add(&mom_b[4 * k + 2], sw * P::fma_(eta0, I0, aeta * I1), sc_m);
+                    t.c[8] += P::add(&mom_b[4 * k + 3],
                            sw * P::fma_(xi0 * eta0, I0, P::fma_(P::fma_(xi0, aeta, eta0 * axi), I1, axi * aeta * I2)),
                            sc_m);
                 }
@@ -571,21 +578,23 @@ mc_birth_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __res
     }
 }
 
-// fixed point -> FP64: raw track-length sums, step-average fluxes and hand-off moments
+// fixed point -> FP64: raw track-length sums, step-average fluxes and hand-off moments, each the
+// exact integer sum of the ncopy tally copies
 template <typename T>
 __global__ void leg_normalise_kernel(const typename Prec<T>::acc_t* pre, const typename Prec<T>::acc_t* post,
-                                     const typename Prec<T>::acc_t* mom, const DevState* st, int ncells,
+                                     const typename Prec<T>::acc_t* mom, int ncopy, const DevState* st, int ncells,
                                      double inv_adt, double* pre_raw, double* post_raw, double* pre_d,
                                      double* post_d, double* mom_d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ncells) return;
     const double it = ldexp(1.0, -st->k_track), im = ldexp(1.0, -st->k_mom);
-    const double a = Prec<T>::to_double(&pre[k], it), b = Prec<T>::to_double(&post[k], it);
+    const size_t n1 = (size_t)ncells, n4 = 4 * (size_t)ncells;
+    const double a = Prec<T>::sum_to_double(&pre[k], n1, ncopy, it), b = Prec<T>::sum_to_double(&post[k], n1, ncopy, it);
     pre_raw[k] = a;
     post_raw[k] = b;
     pre_d[k] = a * inv_adt;
     post_d[k] = b * inv_adt;
-    for (int j = 0; j < 4; ++j) mom_d[4 * k + j] = Prec<T>::to_double(&mom[4 * k + j], im);
+    for (int j = 0; j < 4; ++j) mom_d[4 * k + j] = Prec<T>::sum_to_double(&mom[4 * k + j], n4, ncopy, im);
 }
 
 // initial bank: n particles from the initial-weight CDF (stream INIT, step 0), isotropic, t = 0
@@ -719,6 +728,7 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.n_src = p->has_src ? p->d.n_hist : 0;
     a.w0 = (T)(p->has_src ? p->w_src / (double)p->d.n_hist : 0.0);
     a.pre = (typename Prec<T>::acc_t*)p->acc_pre;
+    a.ncopy = p->tally_copies;
     a.post = (typename Prec<T>::acc_t*)p->acc_post;
     a.mom = (typename Prec<T>::acc_t*)p->acc_mom;
     a.st = p->st;
@@ -783,12 +793,14 @@ cudaError_t launch_leg_normalise(hyb_problem* p) {
     const int g = (p->ncells + 255) / 256;
     if (p->prec == HYB_FP64)
         leg_normalise_kernel<double><<<g, 256, 0, p->stream>>>((const Acc128*)p->acc_pre, (const Acc128*)p->acc_post,
-                                                               (const Acc128*)p->acc_mom, p->st, p->ncells, inv_adt,
+                                                               (const Acc128*)p->acc_mom, p->tally_copies, p->st,
+                                                               p->ncells, inv_adt,
                                                                p->pre_raw, p->post_raw, p->pre_d, p->post_d, p->mom_d);
     else
         leg_normalise_kernel<float><<<g, 256, 0, p->stream>>>(
             (const unsigned long long*)p->acc_pre, (const unsigned long long*)p->acc_post,
-            (const unsigned long long*)p->acc_mom, p->st, p->ncells, inv_adt, p->pre_raw, p->post_raw, p->pre_d,
+            (const unsigned long long*)p->acc_mom, p->tally_copies, p->st, p->ncells, inv_adt, p->pre_raw,
+            p->post_raw, p->pre_d,
             p->post_d, p->mom_d);
     return cudaGetLastError();
 }
