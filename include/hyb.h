@@ -266,9 +266,10 @@ HYB_API hyb_status hyb_build_cdf(const double* w_dev, int32_t nx, int32_t ny, in
                                  void* cuda_stream);
 
 /* The same CDF build without any device allocation, for callers that cannot call cudaMalloc or
- * hand out scratch memory: code that runs while a stream is being captured into a CUDA graph,
- * serving loops that must not allocate on their hot path, and hosts whose device memory is owned
- * by another allocator with a fixed budget. (This entry point has no counterpart in the paper.)
+ * hand out scratch memory: serving loops that must not allocate on their hot path (an allocation
+ * can synchronise the device or fail under memory pressure mid-request), and hosts whose device
+ * memory is owned by another allocator with a fixed budget that this library may not draw from.
+ * (This entry point has no counterpart in the paper.)
  * Its scratch is one fixed __device__ array of 34,816 bytes, resident on every GPU that loads the
  * library until the process exits; ny is limited to 4096 rows (EINVAL beyond, like nx). The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress), so make that first

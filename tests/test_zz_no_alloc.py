@@ -1,5 +1,6 @@
 """The allocation-free CDF build (hyb_build_cdf_noalloc), for callers that cannot allocate device
-memory (stream capture, allocation-free serving loops, foreign allocators with fixed budgets).
+memory (serving loops that must not allocate on their hot path, hosts whose device memory belongs
+to a foreign allocator with a fixed budget).
 
 Calls it through the C ABI twice in a row on different inputs and checks each result against the
 scratch-taking hyb_build_cdf: the CDF integers must agree exactly and the weight sums to the last
