@@ -730,6 +730,14 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
     const T wcopy = (T)a.st->wcopy;
     long long run_c = a.blk[4 * (size_t)blockIdx.x], run_q = a.blk[4 * (size_t)blockIdx.x + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // Comb teeth: slot j takes teeth [first_tooth(S_j), first_tooth(S_j + q_j)) and S_j + q_j is
+    // the next slot's S, so each thread divides once (its end tooth) and takes its start from the
+    // slot before: the lane below, the last lane of the warp below, or the previous round's last
+    // slot (the block's first start is divided once by thread 0)
+    const bool combing = comb && Ttot > 0;
+    __shared__ long long s_t1[kTile / 32];
+    __shared__ long long s_carry;
+    if (combing && threadIdx.x == 0) s_carry = first_tooth(run_q, M, o, Ttot);
     T wmax = 0;
     const long long base = (long long)blockIdx.x * kSlotsPerBlock;
     for (int r = 0; r < kRounds; ++r) {
@@ -759,9 +767,16 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
         }
         const long long pos_c = run_c + wc + ic - c;
         const long long S = run_q + wq + iq - q;
+        long long t0 = 0, t1 = 0;
+        if (combing) {
+            t1 = first_tooth(S + q, M, o, Ttot);
+            const long long below = __shfl_up_sync(0xffffffffu, t1, 1);
+            if (lane == 31) s_t1[wid] = t1;
+            __syncthreads();
+            t0 = lane > 0 ? below : (wid > 0 ? s_t1[wid - 1] : s_carry);
+        }
         if (pr.alive) {
-            if (comb && Ttot > 0) {
-                const long long t0 = first_tooth(S, M, o, Ttot), t1 = first_tooth(S + q, M, o, Ttot);
+            if (combing) {
                 const T wc_ = pr.w < T(0) ? -wcopy : wcopy;
                 for (long long t = t0; t < t1 && t < M; ++t) {
                     a.out.cell[t] = pr.cell; a.out.fx[t] = pr.fx; a.out.fy[t] = pr.fy;
@@ -776,6 +791,7 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
         run_c += tc;
         run_q += tq;
         __syncthreads();
+        if (combing && threadIdx.x == kTile - 1) s_carry = t1;   // read after the next round's barrier
     }
     for (int off = 16; off > 0; off >>= 1) wmax = fmax(wmax, __shfl_down_sync(0xffffffffu, wmax, off));
     if (lane == 0 && wmax > T(0))
