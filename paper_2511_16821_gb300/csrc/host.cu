@@ -281,12 +281,14 @@ static int64_t stage_slots(const hyb_problem_desc* d, int64_t cap) {
 // Copies of the fixed-point tally arrays: the leg's warps add into copy (warp index mod copies),
 // so the adds to a hot cell (the source region) spread over several addresses; the normalisation
 // adds the copies exactly. Four copies (measured on the 112^2 benchmark: 1 copy 0.235 ms per leg,
-// 4 copies 0.205, 8 0.207, 16 0.211, 32 0.223) while they take at most 512 MB, fewer above.
+// 4 copies 0.205, 8 0.207, 16 0.211, 32 0.223) while they take at most 32 MB, fewer above: the
+// copies must stay in L2 with the rest of the leg's working set (on the 1024^2 mesh four copies,
+// 192 MB, made the leg 6 % slower than one).
 int tally_copies(const hyb_problem_desc* d) {
     const size_t acc = d->precision == HYB_FP64 ? 16 : 8;
     const size_t per = 6 * (size_t)d->nx * d->ny * acc;   // pre, post, 4 moments
     int c = 4;
-    while (c > 1 && (size_t)c * per > ((size_t)512 << 20)) c >>= 1;
+    while (c > 1 && (size_t)c * per > ((size_t)32 << 20)) c >>= 1;
     return c;
 }
 
