@@ -9,8 +9,9 @@ the FP64 path is measured beside it.
 
 value     = MC-leg histories per second of whole-step time (device events, L2 flushed between
             steps; inputs resident in HBM)
-e2e       = the same through the public C ABI with the census bank copied in from host memory and
-            the step flux copied back every step
+e2e       = the same through the public C ABI with the census bank copied in from page-locked host
+            memory (the problem's own layout, hyb_set_bank_native) and the step flux copied back
+            every step
 cpu_baseline / --impl reference = the single-threaded FP64 oracle on the host cores, on a
             bounded sample of the same workload.
 Under torchrun (N > 1) each rank runs an independent problem replica (weak scaling, no
@@ -191,19 +192,25 @@ def leg_profile(prec: int, reps: int = 5) -> dict:
 
 
 def e2e_measure(spec: W.ProblemSpec, steps: int) -> dict:
-    """Public-API end to end: per step the census bank is copied in from host memory
-    (hyb_set_bank), one hybrid step runs, and the step flux is read back (hyb_get_tally)."""
+    """Public-API end to end: per step the census bank is copied in from page-locked host memory
+    in the problem's layout (hyb_set_bank_native), one hybrid step runs with its statistics, and
+    the step flux is read back to the host (hyb_get_tally)."""
     import torch
     from paper_2511_16821_gb300 import hyb
     P = hyb.Problem(spec)
     P.step(1)
     host_bank = P.bank()
+    n = int(host_bank["n"])
     esz = 4 if spec.precision == W.FP32 else 8
+    fdt = np.float32 if spec.precision == W.FP32 else np.float64
+    pinned = [torch.from_numpy(np.ascontiguousarray(host_bank["cell"][:n], dtype=np.int32)).pin_memory()]
+    pinned += [torch.from_numpy(np.ascontiguousarray(host_bank[k][:n], dtype=fdt)).pin_memory()
+               for k in ("fx", "fy", "ox", "oy", "w")]
     hist = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(steps):
-        P.set_bank(host_bank)
+        P.set_bank_native(*pinned, n=n)
         st = P.step(1)[0]
         flux = P.tally("flux")
         hist += st["histories"]

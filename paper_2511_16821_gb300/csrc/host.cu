@@ -528,6 +528,11 @@ void fill_remap_stats(const hyb_problem* p, hyb_leg_stats* s) {
 hyb_status pull_state(hyb_problem* p) {
     HYB_CU(p, cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
     HYB_CU(p, cudaStreamSynchronize(p->stream));
+    if (p->st_host->bank_bad) {   // reported once, by the first check after the upload
+        HYB_CU(p, cudaMemsetAsync(&p->st->bank_bad, 0, sizeof(unsigned int), p->stream));
+        return fail(p, HYB_EINVAL, "the bank set with hyb_set_bank_native holds particles outside the problem "
+                                   "(cell index, in-cell offset, direction or weight)");
+    }
     if (p->st_host->status & kStBounds) return fail(p, HYB_EBOUNDS, "device index check failed (bank cell out of range)");
     if (p->st_host->status & kStSegments) return fail(p, HYB_ETIMEOUT, "a history exceeded the segment bound");
     return HYB_OK;
@@ -553,10 +558,51 @@ static hyb_status get_bank_t(hyb_problem* p, int32_t* cell, double* fx, double* 
     return HYB_OK;
 }
 
+// Particles of a bank outside the problem (the checks of hyb_set_bank, on the device): counted
+// into st->bank_bad, which the next synchronising call reports.
+template <typename T>
+__global__ void bank_check_kernel(BankView<T> b, long long n, int ncells, T dx, T dy, DevState* st) {
+    unsigned int bad = 0;
+    const T tx = dx * T(1.000001), ty = dy * T(1.000001), one = T(1.000001);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = b.cell[i];
+        const T fx = b.fx[i], fy = b.fy[i], ox = b.ox[i], oy = b.oy[i], w = b.w[i];
+        const bool ok = c >= 0 && c < ncells && fx >= T(0) && fx <= tx && fy >= T(0) && fy <= ty && isfinite(ox) &&
+                        isfinite(oy) && ox * ox + oy * oy <= one && isfinite(w);
+        bad += ok ? 0u : 1u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_down_sync(0xffffffffu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&st->bank_bad, bad);
+}
+
+// A bank already in the problem's layout and precision (host memory, pinned for an asynchronous
+// copy, or device memory): copied on the problem's stream and checked on the device.
+template <typename T>
+static hyb_status set_bank_native_t(hyb_problem* p, const int32_t* cell, const void* const* f, int64_t n) {
+    BankView<T> b = bank_view<T>(p, p->cur);
+    HYB_CU(p, cudaMemsetAsync(&p->st->bank_bad, 0, sizeof(unsigned int), p->stream));
+    if (n) {
+        HYB_CU(p, cudaMemcpyAsync(b.cell, cell, (size_t)n * 4, cudaMemcpyDefault, p->stream));
+        T* dst[5] = {b.fx, b.fy, b.ox, b.oy, b.w};
+        for (int q = 0; q < 5; ++q)
+            HYB_CU(p, cudaMemcpyAsync(dst[q], f[q], (size_t)n * sizeof(T), cudaMemcpyDefault, p->stream));
+        const long long g = (n + 255) / 256;
+        bank_check_kernel<T><<<(unsigned)(g < 152 * 4 ? g : 152 * 4), 256, 0, p->stream>>>(b, n, p->ncells, (T)p->dx,
+                                                                                            (T)p->dy, p->st);
+        HYB_CU(p, cudaGetLastError());
+    }
+    set_nbank_kernel<<<1, 1, 0, p->stream>>>(p->st, n);
+    HYB_CU(p, cudaGetLastError());
+    HYB_CU(p, launch_bank_stats(p));
+    return HYB_OK;
+}
+
 template <typename T>
 static hyb_status set_bank_t(hyb_problem* p, const int32_t* cell, const double* fx, const double* fy, const double* ox,
                              const double* oy, const double* w, int64_t n) {
     HYB_CU(p, cudaStreamSynchronize(p->stream));
+    HYB_CU(p, cudaMemsetAsync(&p->st->bank_bad, 0, sizeof(unsigned int), p->stream));
     BankView<T> b = bank_view<T>(p, p->cur);
     std::vector<T> tmp((size_t)n);
     if (n) HYB_CU(p, cudaMemcpy(b.cell, cell, (size_t)n * 4, cudaMemcpyHostToDevice));
@@ -927,13 +973,7 @@ hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
             if (s != HYB_OK) return s;
         }
     }
-    if (!per_step) {
-        HYB_CU(p, cudaStreamSynchronize(p->stream));
-        HYB_CU(p, cudaMemcpyAsync(&p->st_host->status, &p->st->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-        HYB_CU(p, cudaStreamSynchronize(p->stream));
-        if (p->st_host->status & kStBounds) return fail(p, HYB_EBOUNDS, "device index check failed");
-        if (p->st_host->status & kStSegments) return fail(p, HYB_ETIMEOUT, "a history exceeded the segment bound");
-    }
+    if (!per_step) return pull_state(p);
     return HYB_OK;
 }
 
@@ -989,6 +1029,14 @@ hyb_status hyb_set_bank(hyb_problem* p, const int32_t* cell, const double* fx, c
     }
     return p->prec == HYB_FP64 ? set_bank_t<double>(p, cell, fx, fy, ox, oy, w, n)
                                : set_bank_t<float>(p, cell, fx, fy, ox, oy, w, n);
+}
+
+hyb_status hyb_set_bank_native(hyb_problem* p, const int32_t* cell, const void* fx, const void* fy, const void* ox,
+                               const void* oy, const void* w, int64_t n) {
+    if (!p || n < 0 || (n > 0 && (!cell || !fx || !fy || !ox || !oy || !w))) return fail(p, HYB_EINVAL, "bad arguments");
+    if (n > p->bank_cap) return fail(p, HYB_ECAPACITY, "bank larger than its capacity");
+    const void* f[5] = {fx, fy, ox, oy, w};
+    return p->prec == HYB_FP64 ? set_bank_native_t<double>(p, cell, f, n) : set_bank_native_t<float>(p, cell, f, n);
 }
 
 hyb_status hyb_bank_capacity(const hyb_problem* p, int64_t* cap) {

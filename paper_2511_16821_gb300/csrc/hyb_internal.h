@@ -61,6 +61,7 @@ struct DevState {
     int sn_iters;              // collided solve: iterations run in the current solve
     int sn_warm;               // solves finished with warm starts enabled (counted up to 2)
     unsigned int sn_blocks_done;   // source-iteration reduction: blocks finished (last one resets it)
+    unsigned int bank_bad;     // particles of a native-layout bank upload outside the problem's domain
 };
 
 template <typename T>

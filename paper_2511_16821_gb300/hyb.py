@@ -88,6 +88,7 @@ def lib():
         L.hyb_set_sn_phi.argtypes = [P, P, C.c_size_t]
         L.hyb_get_bank.argtypes = [P] + [P] * 6 + [C.POINTER(C.c_int64)]
         L.hyb_set_bank.argtypes = [P] + [P] * 6 + [C.c_int64]
+        L.hyb_set_bank_native.argtypes = [P] + [P] * 6 + [C.c_int64]
         L.hyb_bank_capacity.argtypes = [P, C.POINTER(C.c_int64)]
         L.hyb_set_step.argtypes = [P, C.c_int64]
         L.hyb_get_step.argtypes = [P, C.POINTER(C.c_int64)]
@@ -258,6 +259,19 @@ class Problem:
         f = [np.ascontiguousarray(b[k][:n], dtype=np.float64) for k in ("fx", "fy", "ox", "oy", "w")]
         _check(lib().hyb_set_bank(self.h, cell.ctypes.data_as(C.c_void_p),
                                   *[a.ctypes.data_as(C.c_void_p) for a in f], n), self.h)
+
+    def set_bank_native(self, cell, fx, fy, ox, oy, w, n: int | None = None) -> None:
+        """Replace the bank from arrays already in the problem's layout (torch tensors, page-locked
+        host or device, int32 cells and float32/float64 values by the problem precision). The copy
+        is asynchronous on the problem's stream; invalid particles are reported by the next step."""
+        arrs = (cell, fx, fy, ox, oy, w)
+        n = int(cell.numel()) if n is None else n
+        want = "torch.float64" if self.spec.precision == FP64 else "torch.float32"
+        if str(cell.dtype) != "torch.int32" or any(str(a.dtype) != want for a in arrs[1:]):
+            raise TypeError(f"set_bank_native needs int32 cells and {want} values")
+        if any(not a.is_contiguous() or a.numel() < n for a in arrs):
+            raise ValueError("set_bank_native needs contiguous arrays of at least n values")
+        _check(lib().hyb_set_bank_native(self.h, *[C.c_void_p(a.data_ptr()) for a in arrs], n), self.h)
 
     def set_step(self, k: int) -> None:
         _check(lib().hyb_set_step(self.h, k), self.h)

@@ -485,3 +485,40 @@ def test_remap_variant_validation(H):
         H.Problem(W.pulse(n_hist=100).with_(remap_variant=1, n_s=W.NS_INF))
     with pytest.raises(H.HybError):
         H.Problem(W.pulse(n_hist=100).with_(remap_variant=2))
+
+
+@pytest.mark.parametrize("prec", [W.FP32, W.FP64])
+def test_set_bank_native_equals_set_bank(H, prec):
+    """A bank given in the problem's own layout (page-locked host arrays, asynchronous copy) steps
+    exactly like the same bank given through the checked FP64 host path; an invalid particle in a
+    native upload is reported by the next step."""
+    import torch
+    spec = W.checkerboard(n_s=2, n_hist=20_000, cells_per_block=2).with_(precision=prec)
+    bank = W.random_bank(spec, 5000, seed=3)
+    fdt = torch.float32 if prec == W.FP32 else torch.float64
+    npdt = np.float32 if prec == W.FP32 else np.float64
+    # values representable in the problem precision, so both paths hold the same bank
+    for k in ("fx", "fy", "ox", "oy", "w"):
+        bank[k] = bank[k].astype(npdt).astype(np.float64)
+    A = H.Problem(spec)
+    A.set_bank(bank)
+    A.step(2)
+    B = H.Problem(spec)
+    arrs = [torch.from_numpy(bank["cell"].astype(np.int32)).pin_memory()]
+    arrs += [torch.from_numpy(bank[k].astype(npdt)).pin_memory() for k in ("fx", "fy", "ox", "oy", "w")]
+    assert arrs[1].dtype == fdt
+    B.set_bank_native(*arrs)
+    B.step(2)
+    assert np.array_equal(A.tally("flux"), B.tally("flux"))
+    ba, bb = A.bank(), B.bank()
+    assert ba["n"] == bb["n"] and all(np.array_equal(ba[k], bb[k]) for k in ("cell", "fx", "fy", "ox", "oy", "w"))
+    bad = [a.clone() for a in arrs]
+    bad[1][7] = 1e3                       # an in-cell offset far outside the cell
+    B.set_bank_native(*bad)
+    with pytest.raises(H.HybError) as e:
+        B.step(1)
+    assert e.value.status == H.HYB_EINVAL
+    B.set_bank_native(*arrs)              # a valid bank clears the report
+    B.step(1)
+    A.close()
+    B.close()
