@@ -272,6 +272,16 @@ def remap(spec, step: int, bank: dict | None, pre, post, phi):
     return res, _stats_dict(st), bool(combed.value)
 
 
+def phase_keys(spec, bank: dict):
+    """The census_order-2 keys of the particles of a bank and the bits per coordinate."""
+    p, keep = _problem(spec)
+    cb = _bank(bank)
+    n = int(bank.get("n", len(bank["w"])))
+    out = np.zeros(max(n, 1), np.uint32)
+    bits = lib().or_phase_keys(C.byref(p), C.byref(cb), out.ctypes.data_as(C.c_void_p))
+    return out[:n], bits
+
+
 def remap_additive(spec, step: int, bank: dict | None, leg_census: dict | None, post, phi):
     """Steps 3' and 4' (the previous hybrids' remap): the leg census followed by the survivors of
     births from sigma_s (phi_post + phi_c), combed. bank: the step-start bank."""

@@ -257,7 +257,8 @@ typedef struct {
     int64_t census_cap;     // 0 = n_hist
     double sn_tol;          // source-iteration relative-change tolerance
     int32_t sn_max_iter;
-    int32_t census_order;   // 0: census in slot order (bank slots, then births); 1: stable by cell
+    int32_t census_order;   // 0: slot order (bank slots, then births); 1: stable by cell; 2: by cell, then
+                            // phase space (Morton order of in-cell x, y and direction angle)
     int32_t remap_variant;  // 0: Eq. (R) relabelling remap; 1: steps 3'/4' (additive, previous hybrids)
     const int32_t* n_s_cell;  // nx*ny scatter limits per cell in [0, n_s] (space-dependent N_s), or NULL
 } or_problem;
@@ -1152,14 +1153,62 @@ static double remap_births(const or_problem* P, const Mesh& M, int64_t step, con
     return W;
 }
 
-// Census of step 4 from the survivors: in cell order (stable within a cell) when asked, so that
-// the systematic comb samples each cell's weight to within one copy; combed to census_cap (power-
-// of-two quantisation base at or above wmax, offset = point (REMAP_COMB, 0, 0)) when above it.
+// Phase-space key of a census particle (census_order 2): the cell index, then a Morton (Z-order)
+// interleave of b bits each of the in-cell position x, y and the direction's polar angle, taken
+// as the "diamond angle" d in [0, 4) (monotone in the polar angle, one division, no arctangent);
+// b = min(5, (31 - cell bits) / 3) so that the key and its end-of-list sentinel fit in 32 bits.
+uint32_t phase_key_bits(int64_t ncells, int* cell_bits) {
+    int cb = 0;
+    while (((int64_t)1 << cb) < ncells) ++cb;
+    *cell_bits = cb;
+    const int b = (31 - cb) / 3;
+    return (uint32_t)(b < 0 ? 0 : (b > 5 ? 5 : b));
+}
+
+uint32_t phase_key(const Mesh& M, int cell, double fx, double fy, double ox, double oy, int b) {
+    const double s = (double)(1u << b);
+    auto quant = [&](double v) {
+        const double t = std::floor(v * s);
+        return (uint32_t)std::min(std::max(t, 0.0), s - 1.0);
+    };
+    double d;
+    if (ox == 0.0 && oy == 0.0) d = 0.0;
+    else if (oy >= 0.0) d = ox >= 0.0 ? oy / (ox + oy) : 1.0 + (-ox) / (oy - ox);
+    else d = ox < 0.0 ? 2.0 + (-oy) / (-ox - oy) : 3.0 + ox / (ox - oy);
+    const uint32_t qx = quant(fx / M.dx), qy = quant(fy / M.dy), qa = quant(d * 0.25);
+    uint32_t sub = 0;
+    for (int i = 0; i < b; ++i)
+        sub |= (((qx >> i) & 1u) << (3 * i)) | (((qy >> i) & 1u) << (3 * i + 1)) | (((qa >> i) & 1u) << (3 * i + 2));
+    return ((uint32_t)cell << (3 * b)) | sub;
+}
+
+// The census order of step 4: slot order (0), cell order (1), or cell then in-cell phase-space order
+// (2), each a stable sort, so that the systematic comb along it samples each cell (and, for 2, the
+// position and direction within it) in strata.
+void order_census(const or_problem* P, std::vector<Streamed>& v) {
+    if (P->census_order == 1) {
+        std::stable_sort(v.begin(), v.end(), [](const Streamed& a, const Streamed& b) { return a.cell < b.cell; });
+    } else if (P->census_order == 2) {
+        Mesh M(P);
+        int cb = 0;
+        const int b = (int)phase_key_bits((int64_t)M.nx * M.ny, &cb);
+        std::vector<std::pair<uint32_t, size_t>> key(v.size());
+        for (size_t i = 0; i < v.size(); ++i) key[i] = {phase_key(M, v[i].cell, v[i].fx, v[i].fy, v[i].ox, v[i].oy, b), i};
+        std::stable_sort(key.begin(), key.end(), [](const std::pair<uint32_t, size_t>& a,
+                                                    const std::pair<uint32_t, size_t>& b2) { return a.first < b2.first; });
+        std::vector<Streamed> o(v.size());
+        for (size_t i = 0; i < v.size(); ++i) o[i] = v[key[i].second];
+        v.swap(o);
+    }
+}
+
+// Census of step 4 from the survivors, in the requested order (order_census), combed to
+// census_cap (power-of-two quantisation base at or above wmax, offset = point (REMAP_COMB, 0, 0))
+// when above it.
 static int census_from(const or_problem* P, int64_t step, std::vector<Streamed>& surv, double wmax,
                        or_bank* out, int32_t* combed, long double* wc) {
     const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
-    if (P->census_order == 1)
-        std::stable_sort(surv.begin(), surv.end(), [](const Streamed& a, const Streamed& b) { return a.cell < b.cell; });
+    order_census(P, surv);
     std::vector<Streamed> fin;
     int did_comb = 0;
     if ((int64_t)surv.size() > cap) {
@@ -1265,6 +1314,15 @@ int or_remap_additive(const or_problem* P, int64_t step, const or_bank* bank, co
     return (st && st->errors) ? 4 : 0;
 }
 
+// the phase-space census key (census_order 2), exposed for its pins
+int or_phase_keys(const or_problem* P, const or_bank* b, uint32_t* keys) {
+    Mesh M(P);
+    int cb = 0;
+    const int bits = (int)phase_key_bits((int64_t)M.nx * M.ny, &cb);
+    for (int64_t i = 0; i < b->n; ++i) keys[i] = phase_key(M, b->cell[i], b->fx[i], b->fy[i], b->ox[i], b->oy[i], bits);
+    return bits;
+}
+
 // One hybrid time step (Sec. 2.2, steps 1-4). bank -> out. flux: step-average scalar flux per
 // cell, phi = (T_pre + T_post)/(A dt) + phi_c0. For N_s = infinity the remap is skipped and the
 // MC-leg census (combed to census_cap) is the new bank.
@@ -1285,8 +1343,7 @@ int or_step(const or_problem* P, int64_t step, const or_bank* bank, or_bank* out
         std::fill(phi, phi + 4 * nc, 0.0);
         std::vector<Streamed> s, fin;
         for (int64_t j = 0; j < tmp.n; ++j) s.push_back(Streamed{true, c[j], a[j], b[j], d[j], e[j], g[j]});
-        if (P->census_order == 1)
-            std::stable_sort(s.begin(), s.end(), [](const Streamed& x, const Streamed& y) { return x.cell < y.cell; });
+        order_census(P, s);
         const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
         if ((int64_t)s.size() > cap) {
             double wmax = 0.0;

@@ -350,3 +350,64 @@ def test_additive_hybrid_infinite_medium_decay(orc):
     e2 = run(0.05, 8)
     assert e1 < 4 * 1.0 * 1.5 * 0.1 ** 2
     assert e2 < e1
+
+
+# ------------------------------------------------------------------------------------------------
+# census in phase-space order (census_order = 2)
+# ------------------------------------------------------------------------------------------------
+def _deinterleave(sub, b):
+    q = [np.zeros_like(sub) for _ in range(3)]
+    for i in range(b):
+        for d in range(3):
+            q[d] |= ((sub >> (3 * i + d)) & 1) << i
+    return q
+
+
+def test_phase_key_groups_by_cell_and_orders_within_it(orc):
+    """The key is the cell index above a Morton interleave of three b-bit coordinates, and those
+    coordinates follow the in-cell x, the in-cell y and the polar angle of the direction
+    (checked against an arctangent), each cut into 2^b equal bins."""
+    spec = W.checkerboard(n_s=1, n_hist=10, cells_per_block=2)
+    bank = W.random_bank(spec, 20000, seed=11)
+    keys, b = orc.phase_keys(spec, bank)
+    assert b == 5                                     # 196 cells: 8 cell bits, 3 x 5 = 15 sub-key bits
+    keys = keys.astype(np.int64)
+    assert np.array_equal(keys >> (3 * b), bank["cell"])
+    qx, qy, qa = _deinterleave(keys & ((1 << 3 * b) - 1), b)
+    dx, dy = spec.lx / spec.nx, spec.ly / spec.ny
+    ang = np.mod(np.arctan2(bank["oy"], bank["ox"]), 2 * np.pi)
+    for q, v in ((qx, bank["fx"] / dx), (qy, bank["fy"] / dy), (qa, ang)):
+        o = np.argsort(v, kind="stable")
+        assert np.all(np.diff(q[o]) >= 0)             # monotone in the coordinate
+        counts = np.bincount(q, minlength=1 << b)
+        assert counts.min() > 0.5 * len(q) / (1 << b) if q is not qa else counts.min() > 0
+    # x and y bins are equal widths: the bin of a value is its fraction of the cell, scaled
+    assert np.all(np.abs(qx - bank["fx"] / dx * (1 << b)) <= 1.0)
+
+
+def test_phase_census_order_is_a_stable_sort_by_key(orc):
+    """Without a comb the phase-ordered census holds the slot-ordered census's particles, sorted
+    stably by their keys (so also by cell)."""
+    spec, bank, r, phi = _remap_inputs(orc)
+    spec = spec.with_(census_cap=10 ** 7)
+    a, _, ca = orc.remap(spec, 0, bank, r["pre"], r["post"], phi)
+    b, _, cb = orc.remap(spec.with_(census_order=2), 0, bank, r["pre"], r["post"], phi)
+    assert not ca and not cb and a["n"] == b["n"]
+    keys, _ = orc.phase_keys(spec, a)
+    order = np.argsort(keys, kind="stable")
+    for k in ("cell", "fx", "fy", "ox", "oy", "w"):
+        assert np.array_equal(b[k], a[k][order]), k
+    assert np.all(np.diff(b["cell"]) >= 0)
+
+
+def test_phase_ordered_comb_keeps_each_cell_within_one_copy(orc):
+    spec, bank, r, phi = _remap_inputs(orc)
+    full, _, _ = orc.remap(spec.with_(census_cap=10 ** 7), 0, bank, r["pre"], r["post"], phi)
+    cap = full["n"] // 3
+    out, _, combed = orc.remap(spec.with_(census_cap=cap, census_order=2), 0, bank, r["pre"], r["post"], phi)
+    assert combed and out["n"] == cap
+    wc = out["w"][0]
+    nc = spec.ncells
+    before = np.bincount(full["cell"], weights=full["w"], minlength=nc)
+    after = np.bincount(out["cell"], weights=out["w"], minlength=nc)
+    assert np.all(np.abs(after - before) <= wc * (1 + 1e-9))
