@@ -399,8 +399,9 @@ def main():
     ap.add_argument("--sn-accel", type=int, default=0, help="Anderson depth of the collided solve (0: plain SI)")
     ap.add_argument("--sn-warm", type=int, default=1, choices=[0, 1, 2],
                     help="source-iteration start: 0 zero, 1 previous step's flux, 2 linear extrapolation")
-    ap.add_argument("--census-order", type=int, default=0, choices=[0, 1],
-                    help="census in slot order (0) or sorted by cell before the comb (1)")
+    ap.add_argument("--census-order", type=int, default=0, choices=[0, 1, 2],
+                    help="census in slot order (0), sorted by cell (1) or by cell and phase space (2) "
+                         "before the comb")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     global CENSUS_ORDER, SN_ACCEL, WARM

@@ -104,7 +104,10 @@ typedef struct {
                                  births); 1: survivors in cell order (stable within a cell)
                                  before the comb, so the systematic comb samples each cell's
                                  weight to within one copy and the next leg's bank is
-                                 cell-coherent */
+                                 cell-coherent; 2: by cell, then within a cell along a Morton
+                                 curve over the in-cell position and the direction angle (b bits
+                                 each, b = min(5, (31 - cell bits) / 3)), so the comb samples
+                                 position and direction within a cell in strata too */
     int32_t sn_accel;         /* 0: plain source iteration (the paper); 1..8: Anderson acceleration
                                  of that depth (the same fixed point, fewer sweeps in diffusive
                                  problems) */

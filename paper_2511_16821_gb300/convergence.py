@@ -30,7 +30,7 @@ def problem(n_hist: int, seed: int, sampler: int, n_s: int = 2, precision: int =
     scatterer blocks (cross sections times sigma_scale), Q = 1 in the centre block, dt = 0.1.
     remap_variant 1: steps 3'/4' of the previous hybrids; cap_factor: census cap in units of
     n_hist (large: no comb)."""
-    order = "cell" if census_order else "slot"
+    order = ("slot", "cell", "phase-space")[census_order]
     sp = W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision, sampler=sampler, cells_per_block=4)
     name = f"checkerboard28 x{sigma_scale:g} N_s={'inf' if n_s == W.NS_INF else n_s}, census in {order} order"
     if remap_variant:
@@ -108,6 +108,7 @@ if __name__ == "__main__":
         for steps in (1, 4):
             print(json.dumps(study(steps=steps, n_s=n_s)), flush=True)
     print(json.dumps(study(steps=4, n_s=2, census_order=1)), flush=True)
+    print(json.dumps(study(steps=4, n_s=2, census_order=2)), flush=True)
     # the previous hybrids' remap (steps 3'/4'), and both remaps without a comb (census cap 8 n_hist)
     print(json.dumps(study(steps=4, n_s=2, remap_variant=1)), flush=True)
     print(json.dumps(study(steps=4, n_s=2, cap_factor=8, ref_log2=22)), flush=True)

@@ -267,7 +267,8 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
-        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell;
+        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell,
+        sortkey;
     int64_t cap, nblk, slots;
     int gr, gc;
 };
@@ -335,8 +336,9 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.aas = d->sn_accel > 0 ? sn_accel_state_bytes() : 0;
     z.rempos = nc * 4;
     const size_t nslots = (size_t)z.slots;
-    z.sortkv = d->census_order == 1 ? nslots * 8 : 0;                    // x2: (cell, slot) pairs, ping-pong
-    z.sortc = d->census_order == 1 ? 256 * ((nslots + 2047) / 2048 + 1) * 4 : 0;
+    z.sortkv = d->census_order >= 1 ? nslots * 8 : 0;                    // x2: (key, slot) pairs, ping-pong
+    z.sortc = d->census_order >= 1 ? 256 * ((nslots + 2047) / 2048 + 1) * 4 : 0;
+    z.sortkey = d->census_order == 2 ? nslots * 4 : 0;                   // phase-space keys per slot
     return z;
 }
 
@@ -347,7 +349,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
-                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell};
+                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -409,6 +411,7 @@ void assign(hyb_problem* p) {
     p->aa_hist = z.aah ? take(z.aah) : nullptr;
     p->aa_state = z.aas ? take(z.aas) : nullptr;
     p->ns_cell = z.nscell ? (int32_t*)take(z.nscell) : nullptr;
+    p->sort_keys = z.sortkey ? (int32_t*)take(z.sortkey) : nullptr;
     p->bank_cap = z.cap;
     p->stage_slots = z.slots;
     p->nblk_max = z.nblk;
@@ -446,7 +449,7 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->precision != HYB_FP32 && d->precision != HYB_FP64) { *why = "unknown precision"; return HYB_EINVAL; }
     if (d->sn_order != 4 && d->sn_order != 8) { *why = "sn_order must be 4 or 8"; return HYB_EINVAL; }
     if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
-    if (d->census_order != 0 && d->census_order != 1) { *why = "census_order must be 0 or 1"; return HYB_EINVAL; }
+    if (d->census_order < 0 || d->census_order > 2) { *why = "census_order must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->sn_accel < 0 || d->sn_accel > 8) { *why = "sn_accel must be in [0, 8]"; return HYB_EINVAL; }
     if (d->sn_warm_start < 0 || d->sn_warm_start > 2) { *why = "sn_warm_start must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->remap_variant != 0 && d->remap_variant != 1) { *why = "remap_variant must be 0 or 1"; return HYB_EINVAL; }

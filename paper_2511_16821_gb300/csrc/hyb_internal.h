@@ -121,6 +121,7 @@ struct hyb_problem {
     float* sig_inv;           // ncells x 4: 1/sigma_a, 1/sigma_s, 1/sigma_t (FP32 leg; 0 where sigma = 0),
                               // then the cell's scatter limit as int bits (space-dependent N_s)
     int32_t* ns_cell;         // per-cell scatter limits (space-dependent N_s), or null
+    int32_t* sort_keys;       // census in phase-space order: the sort key of every staging slot
     double *sa_d, *ss_d, *Q_d;  // FP64 copies for the remap density
     hyb::Cdf2DView src_cdf, rem_cdf;
     double* rem_f;            // 4 x ncells remap density coefficients

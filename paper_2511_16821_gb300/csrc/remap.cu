@@ -610,6 +610,67 @@ __global__ void __launch_bounds__(kTile) remap_partials_kernel(RemapArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// census in phase-space order (census_order 2): key = cell above a Morton interleave of b bits
+// each of the in-cell x, y and the direction's diamond angle d in [0, 4) (monotone in the polar
+// angle: one division, no arctangent); dead slots get -1 (sorted last). The FP64 path forms the
+// key with the same operations, in the same order, as the oracle.
+// ---------------------------------------------------------------------------------------------
+int phase_key_bits(int ncells, int* cell_bits) {
+    int cb = 0;
+    while (((long long)1 << cb) < ncells) ++cb;
+    *cell_bits = cb;
+    const int b = (31 - cb) / 3;
+    return b < 0 ? 0 : (b > 5 ? 5 : b);
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t phase_quant(T v, T s) {
+    T t = floor(v * s);
+    t = t < T(0) ? T(0) : (t > s - T(1) ? s - T(1) : t);
+    return (uint32_t)t;
+}
+
+template <typename T>
+__global__ void phase_key_kernel(BankView<T> stg, long long nslots, T dx, T dy, int b, int32_t* key) {
+    const T s = (T)(1u << b);
+    for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < nslots; j += (long long)gridDim.x * blockDim.x) {
+        const int c = stg.cell[j];
+        if (c < 0) { key[j] = -1; continue; }
+        const T ox = stg.ox[j], oy = stg.oy[j];
+        T d;
+        if (ox == T(0) && oy == T(0)) d = T(0);
+        else if (oy >= T(0)) d = ox >= T(0) ? oy / (ox + oy) : T(1) + (-ox) / (oy - ox);
+        else d = ox < T(0) ? T(2) + (-oy) / (-ox - oy) : T(3) + ox / (ox - oy);
+        const uint32_t qx = phase_quant<T>(stg.fx[j] / dx, s), qy = phase_quant<T>(stg.fy[j] / dy, s);
+        const uint32_t qa = phase_quant<T>(d * T(0.25), s);
+        uint32_t sub = 0;
+        for (int i = 0; i < b; ++i)
+            sub |= (((qx >> i) & 1u) << (3 * i)) | (((qy >> i) & 1u) << (3 * i + 1)) | (((qa >> i) & 1u) << (3 * i + 2));
+        key[j] = (int32_t)(((uint32_t)c << (3 * b)) | sub);
+    }
+}
+
+// The sort of the census (cell order, or phase-space order with its keys formed first) over the n
+// staging slots; *perm: the sorted (key << 32 | slot) pairs.
+template <typename T>
+static cudaError_t sort_census(hyb_problem* p, const BankView<T>& stg, long long n, cudaStream_t s,
+                               const unsigned long long** perm) {
+    unsigned long long* const pairs[2] = {p->sort_pairs[0], p->sort_pairs[1]};
+    if (p->d.census_order == 2) {
+        int cb = 0;
+        const int b = phase_key_bits(p->ncells, &cb);
+        const long long g = (n + 255) / 256;
+        phase_key_kernel<T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), 256, 0, s>>>(stg, n, (T)p->dx, (T)p->dy, b,
+                                                                                 p->sort_keys);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        // keys below 2^(cell bits + 3b) <= 2^31; that value is the sentinel of dead slots
+        return launch_census_sort(p->sort_keys, n, (uint32_t)1u << (cb + 3 * b), pairs, p->sort_counts, s, perm);
+    }
+    return launch_census_sort(stg.cell, n, (uint32_t)p->ncells, pairs, p->sort_counts, s, perm);
+}
+
 // one block: exclusive scan of block counts and quantised sums; totals, comb decision
 __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long long cap, uint64_t seed, int sampler,
                                   long long n_hist) {
@@ -853,12 +914,11 @@ static cudaError_t remap_t(hyb_problem* p) {
     if (e != cudaSuccess) return e;
     a.perm = nullptr;
     a.nslots = maxN;
-    a.perm_slots = p->d.census_order == 1 ? 1 : 0;
+    a.perm_slots = p->d.census_order >= 1 ? 1 : 0;
     remap_count_kernel<T><<<nblk, kTile, smem, s>>>(a);
-    if (p->d.census_order == 1) {
-        // survivors in cell order (stable): the comb and the census write then follow that order
-        unsigned long long* const pairs[2] = {p->sort_pairs[0], p->sort_pairs[1]};
-        e = launch_census_sort(a.stg.cell, maxN, (uint32_t)p->ncells, pairs, p->sort_counts, s, &a.perm);
+    if (p->d.census_order >= 1) {
+        // survivors in cell (or phase-space) order, stable: the comb and the census write follow it
+        e = sort_census<T>(p, a.stg, maxN, s, &a.perm);
         if (e != cudaSuccess) return e;
         remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);
     }
@@ -913,10 +973,9 @@ static cudaError_t census_t(hyb_problem* p) {
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
     cudaError_t e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
     if (e != cudaSuccess) return e;
-    if (p->d.census_order == 1) {
+    if (p->d.census_order >= 1) {
         stage_tail_kernel<<<152, 256, 0, s>>>(a.stg.cell, p->st, p->has_src ? p->d.n_hist : 0, maxN);
-        unsigned long long* const pairs[2] = {p->sort_pairs[0], p->sort_pairs[1]};
-        e = launch_census_sort(a.stg.cell, maxN, (uint32_t)p->ncells, pairs, p->sort_counts, s, &a.perm);
+        e = sort_census<T>(p, a.stg, maxN, s, &a.perm);
         if (e != cudaSuccess) return e;
     }
     remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);

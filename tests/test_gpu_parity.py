@@ -278,7 +278,8 @@ def test_collided_solve_tall_mesh(H, orc, prec):
         assert np.allclose(phi_g, phi_o, rtol=1e-4, atol=1e-5 * scale)
 
 
-@pytest.mark.parametrize("cap,order", [(0, 0), (10 ** 7, 0), (0, 1), (10 ** 7, 1), (9000, 1)])
+@pytest.mark.parametrize("cap,order", [(0, 0), (10 ** 7, 0), (0, 1), (10 ** 7, 1), (9000, 1), (0, 2), (10 ** 7, 2),
+                                       (9000, 2)])
 def test_remap_parity(H, orc, cap, order):
     """The remap's census against the oracle: comb or not, slot order or cell order (a stable
     sort by cell before the comb), element by element."""
@@ -307,7 +308,8 @@ def test_remap_parity(H, orc, cap, order):
 
 @pytest.mark.parametrize("prec,order,sampler,limits", [(W.FP64, 0, W.SOBOL, 0), (W.FP32, 0, W.SOBOL, 0),
                                                        (W.FP64, 1, W.SOBOL, 0), (W.FP64, 1, W.HALTON, 0),
-                                                       (W.FP64, 0, W.SOBOL, 1)])
+                                                       (W.FP64, 0, W.SOBOL, 1), (W.FP64, 2, W.SOBOL, 0),
+                                                       (W.FP32, 2, W.SOBOL, 0)])
 def test_multistep_hybrid(H, orc, prec, order, sampler, limits):
     spec = W.pulse(n_hist=8192).with_(precision=prec, sn_tol=1e-12 if prec == W.FP64 else 1e-7, census_order=order,
                                       sampler=sampler)
@@ -383,7 +385,7 @@ def test_large_mesh_sampled_records(H, orc):
     assert s["histories"] == N and s["errors"] == 0
 
 
-@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("order", [0, 1, 2])
 def test_ns_infinity_pure_mc(H, orc, order):
     """N_s = infinity (pure (Q)MC, no hand-off, no collided stage): the MC-leg census survivors,
     combed to census_cap, are the next bank. Three steps of a pulse (bank only) and of a small
