@@ -284,12 +284,13 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0) -> dic
             "single_problem_path": {"histories_per_s": h2 / dt, "ms_per_step_all": 1e3 * dt / steps}}
 
 
-def census_order_measure(steps: int = 5) -> dict:
-    """The benchmark workload with the census sorted by cell before the comb (FP32): device time
-    per step. At equal histories its multi-step flux error is lower (convergence.py)."""
+def census_order_measure(steps: int = 5, order: int = 1) -> dict:
+    """The benchmark workload with the census sorted before the comb (FP32), by cell (order 1) or by
+    cell and phase space (order 2): device time per step. At equal histories their multi-step
+    flux errors are lower (convergence.py)."""
     import torch
     from paper_2511_16821_gb300 import hyb
-    spec = spec_for(W.FP32).with_(census_order=1)
+    spec = spec_for(W.FP32).with_(census_order=order)
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     with torch.cuda.stream(stream):
@@ -303,7 +304,8 @@ def census_order_measure(steps: int = 5) -> dict:
             hist += st["histories"]
         P.close()
     torch.cuda.synchronize()
-    return {"census_order": "cell", "histories_per_s": hist / (ms / 1e3), "ms_per_step": ms / steps}
+    return {"census_order": ("slot", "cell", "phase space")[order], "histories_per_s": hist / (ms / 1e3),
+            "ms_per_step": ms / steps}
 
 
 def large_measure(steps: int = 2, n_hist: int = 100_000_000, sn_accel: int = 0) -> dict:
@@ -489,7 +491,8 @@ def main():
     if not args.no_e2e:
         line["e2e"] = e2e_measure(spec_for(W.FP32), max(2, min(args.steps, 5)))
     if CENSUS_ORDER == 0:
-        line["census_cell_order"] = census_order_measure()
+        line["census_cell_order"] = census_order_measure(order=1)
+        line["census_phase_order"] = census_order_measure(order=2)
     if not args.no_large:
         line["large"] = large_measure(sn_accel=4)
         line["large_plain_si"] = large_measure(sn_accel=0)
