@@ -326,7 +326,9 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sw)[kRedThre
 }
 
 // Two-level completion of per-block partial sums, independent of the order in which blocks finish.
-// Block b has written its NV partials to part[b NV + q] (all threads call this after that).
+// Block b has written its NV partials to part[b NV + q], each writing thread followed by a
+// __threadfence (only those threads: a fence in every thread would also wait for the block's other
+// stores); all threads call this after that.
 // Every kRedGroupBlocks consecutive blocks form a group; the last block of a group to arrive adds
 // the group's partials (one per thread, then block_sum) into gpart[g NV + q]; the last group to
 // arrive adds the group sums (a fixed sequence per thread, then block_sum) into s_tot. Returns
@@ -341,7 +343,6 @@ __device__ bool reduce_partials(double* part, int nblk, double* gpart, unsigned*
     const int ngrp = (nblk + kRedGroupBlocks - 1) / kRedGroupBlocks;
     const int b0 = g * kRedGroupBlocks;
     const int gsize = nblk - b0 < kRedGroupBlocks ? nblk - b0 : kRedGroupBlocks;
-    __threadfence();   // every writer of part[] fences before the arrival
     __syncthreads();
     if (threadIdx.x == 0) {
         s_go = atomicAdd(&gcnt[g], 1u) == (unsigned)gsize - 1u;
@@ -354,11 +355,13 @@ __device__ bool reduce_partials(double* part, int nblk, double* gpart, unsigned*
     for (int q = 0; q < NV; ++q)
         v[q] = (int)threadIdx.x < gsize ? ((volatile double*)part)[(size_t)(b0 + threadIdx.x) * NV + q] : 0.0;
     block_sum<NV>(v, sw, s_tot);
-    if (threadIdx.x < NV) gpart[(size_t)g * NV + threadIdx.x] = s_tot[threadIdx.x];
+    if (threadIdx.x < NV) {
+        gpart[(size_t)g * NV + threadIdx.x] = s_tot[threadIdx.x];
+        __threadfence();
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         gcnt[g] = 0u;
-        __threadfence();
         s_go = atomicAdd(top, 1u) == (unsigned)ngrp - 1u;
     }
     __syncthreads();
@@ -460,6 +463,7 @@ sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncell
         for (int q = 0; q < kRedCells * 4 / 32; ++q) { a += sred[0][q]; b += sred[1][q]; }
         rs.part[2 * blockIdx.x] = a;
         rs.part[2 * blockIdx.x + 1] = b;
+        __threadfence();
     }
     if (reduce_partials<2>(rs.part, (int)gridDim.x, rs.gpart, rs.gcnt, &st->sn_blocks_done, s_tot) &&
         threadIdx.x == 0) {
@@ -602,6 +606,7 @@ sn_reduce_aa_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int nc
         double a = 0;
         for (int w = 0; w < kRedCells * 4 / 32; ++w) a += sred[threadIdx.x][w];
         rs.part[(size_t)blockIdx.x * kAAPart + threadIdx.x] = a;
+        __threadfence();
     }
     if (reduce_partials<kAAPart>(rs.part, (int)gridDim.x, rs.gpart, rs.gcnt, &st->sn_blocks_done, s_tot) &&
         threadIdx.x == 0) {
