@@ -241,14 +241,16 @@ def cpu_baseline(n_hist: int, steps: int) -> dict:
                       f"histories/step (FP64 oracle, one thread)", "seconds": round(dt, 2)}
 
 
-def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0) -> dict:
+def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0, sn_accel: int = 0,
+                    single: bool = True) -> dict:
     """The batched workload: n problems of the batched distribution (FP32 tracking, int64
     tallies), one graph per step after autotuning, against the plain single-problem path over the
-    same problems (each stepped alone, one after the other)."""
+    same problems (each stepped alone, one after the other). sn_accel: Anderson depth of the
+    problems' collided solves (0: plain source iteration)."""
     import torch
     from paper_2511_16821_gb300 import hyb
     from paper_2511_16821_gb300.autotune import tune_batch
-    specs = [W.random_batch_problem(seed, p).with_(sn_warm_start=1) for p in range(n_problems)]
+    specs = [W.random_batch_problem(seed, p).with_(sn_warm_start=1, sn_accel=sn_accel) for p in range(n_problems)]
     stream = torch.cuda.Stream()
     probs = [hyb.Problem(sp, stream=stream) for sp in specs]
     B = hyb.Batch(probs, stream=stream)
@@ -265,6 +267,10 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0) -> dic
     B.close()
     for P in probs:
         P.close()
+    out = {"problems": n_problems, "sn_accel": sn_accel, "histories_per_step": hist, "ms_per_step": ms,
+           "histories_per_s": hist / (ms / 1e3), "tuning": tune["best"]}
+    if not single:
+        return out
     # plain path: each problem alone, the same number of steps, one after the other
     alone = [hyb.Problem(sp, stream=stream) for sp in specs]
     for P in alone:
@@ -279,9 +285,8 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0) -> dic
     dt = time.perf_counter() - t0
     for P in alone:
         P.close()
-    return {"problems": n_problems, "histories_per_step": hist, "ms_per_step": ms,
-            "histories_per_s": hist / (ms / 1e3), "tuning": tune["best"],
-            "single_problem_path": {"histories_per_s": h2 / dt, "ms_per_step_all": 1e3 * dt / steps}}
+    out["single_problem_path"] = {"histories_per_s": h2 / dt, "ms_per_step_all": 1e3 * dt / steps}
+    return out
 
 
 def census_order_measure(steps: int = 5, order: int = 1) -> dict:
@@ -498,6 +503,7 @@ def main():
         line["large_plain_si"] = large_measure(sn_accel=0)
     if not args.no_batch:
         line["batched"] = batched_measure()
+        line["batched_anderson"] = batched_measure(sn_accel=4, single=False)
         line["serving"] = serving_measure(100.0, 3.0)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(n_hist=200_000, steps=2)
