@@ -106,6 +106,29 @@ SN_ACCEL = 0
 WARM = 1
 
 
+# DRAM bytes (read + write) of one launch of the FP32 leg kernel on this workload, from one ncu
+# capture (profiles/mc_leg_kernel_fp32_checkerboard112_ns2.md), with the SHA-256 of the sources the
+# kernel is built from at that capture: the value is reported only while they are unchanged.
+LEG_TRAFFIC_BYTES = None
+LEG_TRAFFIC_SOURCES_SHA256 = None
+LEG_SOURCES = ("mc_leg.cu", "hyb_device.cuh", "hyb_internal.h")
+
+
+def leg_sources_sha256() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in LEG_SOURCES:
+        with open(os.path.join(ROOT, "paper_2511_16821_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def leg_traffic():
+    if LEG_TRAFFIC_BYTES is None or leg_sources_sha256() != LEG_TRAFFIC_SOURCES_SHA256:
+        return None
+    return LEG_TRAFFIC_BYTES
+
+
 def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0, warm: int | None = None) -> W.ProblemSpec:
     """The benchmark workload; source iteration starts from the previous step's collided flux
     (the same fixed point, fewer sweeps)."""
@@ -478,7 +501,7 @@ def main():
         "phase_ms": r32["phase_ms"],
         "roofline": {"bound": "atomic", "kernel": "mc_leg_kernel<float>", "achieved": adds_rate / 1e9,
                      "peak": atomic_peak / 1e9, "unit": "Gatomic/s", "frac": adds_rate / atomic_peak,
-                     "traffic": None,
+                     "traffic": leg_traffic(),
                      "peak_src": "measured live: hyb_atomic_rate, 64-bit adds to 6 x ncells random addresses",
                      "leg_ms": prof["ms"], "leg_histories": prof["histories"], "leg_segments": prof["segments"],
                      "tally_adds": prof["tally_adds"],
