@@ -128,6 +128,29 @@ __device__ __forceinline__ uint32_t div_direct(uint32_t c_lo, uint32_t c_hi, uin
     return (uint32_t)(((unsigned long long)c_hi * n + __umulhi(c_lo, n)) >> 32);
 }
 
+// Cell index k -> (ix, iy) for a mesh nx wide, without an integer division: iy = k / nx by the
+// same direct computation (c = ceil(2^64 / nx), exact for every 32-bit k); nx = 1 (c would not
+// fit in 64 bits) is the identity.
+struct CellSplit {
+    uint32_t c_lo, c_hi;
+    int nx;
+    __device__ __forceinline__ void operator()(int k, int* ix, int* iy) const {
+        const uint32_t q = nx == 1 ? (uint32_t)k : div_direct(c_lo, c_hi, (uint32_t)k);
+        *iy = (int)q;
+        *ix = k - (int)q * nx;
+    }
+};
+
+inline CellSplit make_cell_split(int nx) {
+    CellSplit s;
+    s.nx = nx;
+    const unsigned __int128 two64 = (unsigned __int128)1 << 64;
+    const unsigned long long c = nx > 1 ? (unsigned long long)((two64 + (unsigned)nx - 1) / (unsigned)nx) : 0ull;
+    s.c_lo = (uint32_t)c;
+    s.c_hi = (uint32_t)(c >> 32);
+    return s;
+}
+
 __device__ __forceinline__ uint32_t halton_u(const uint32_t* t, uint32_t i) {
     if (t[0] == 2u) return __brev(i);   // base 2: the bit reversal is floor(2^32 phi_2(i))
     const uint32_t B = t[1], QB = t[3], RB = t[4], c_lo = t[5], c_hi = t[6], fb = t[7];

@@ -33,6 +33,7 @@ struct LegArgs {
     BankView<T> cens;           // N_s = infinity: end state of history j at slot j (cell -1 unless census)
     int stage_census;
     const int32_t* ns_cell;     // per-cell scatter limits (space-dependent N_s), or null: n_s everywhere
+    CellSplit split;            // cell index -> (ix, iy)
     Cdf2DView cdf;
     long long n_src;
     T w0;
@@ -110,7 +111,7 @@ __device__ __forceinline__ void birth_state(const LegArgs<T>& a, const Points& p
     using P = Prec<T>;
     T frx, fry;
     const int k = sample_cell<T>(a.cdf, a.nx, a.ny, pts(i, 0), pts(i, 1), &frx, &fry);
-    *ix = k % a.nx; *iy = k / a.nx;
+    a.split(k, ix, iy);
     *fx = frx * a.dx; *fy = fry * a.dy;
     iso_dir<T>(pts(i, 3), pts(i, 4), ox, oy);
     *srem = a.cdt * P::unit_c(pts(i, 2));
@@ -227,7 +228,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                     const int k = a.bank.cell[j];
                     if (k < 0 || k >= nx * ny) { t.status |= kStBounds; ok = false; }
                     else {
-                        h.ix = k % nx; h.iy = k / nx;
+                        a.split(k, &h.ix, &h.iy);
                         h.fx = a.bank.fx[j]; h.fy = a.bank.fy[j];
                         h.ox = a.bank.ox[j]; h.oy = a.bank.oy[j];
                         h.w = a.bank.w[j];
@@ -238,7 +239,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                     h.census_stream = false;
                     if (a.births.cell) {
                         const int k = a.births.cell[h.idx];
-                        h.ix = k % nx; h.iy = k / nx;
+                        a.split(k, &h.ix, &h.iy);
                         h.fx = a.births.fx[h.idx]; h.fy = a.births.fy[h.idx];
                         h.ox = a.births.ox[h.idx]; h.oy = a.births.oy[h.idx];
                         h.srem = a.births.srem[h.idx];
@@ -713,6 +714,7 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.sig_inv = (const float4*)p->sig_inv;
     a.n_s = p->d.n_s; a.sampler = p->d.sampler; a.handoff_full = p->d.handoff_full;
     a.ns_cell = p->ns_cell;
+    a.split = make_cell_split(p->nx);
     a.ntab = p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS;
     a.w_min = (T)p->d.w_min;
     a.V = p->point_tab;

@@ -253,6 +253,7 @@ struct RemapArgs {
     long long nslots;          // staging slots (bank capacity + n_hist); the sort covers all of them
     int perm_slots;            // 1: the census is sorted by cell after the count pass
     int lead_staged;           // 1 (steps 3'/4'): slots ahead of the births hold the MC leg's staged census
+    CellSplit split;           // cell index -> (ix, iy)
 };
 
 template <typename T>
@@ -301,14 +302,14 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
     T fx, fy, ox, oy, w, srem;
     if (j < nb) {
         const int k = a.in.cell[j];
-        ix = k % a.nx; iy = k / a.nx;
+        a.split(k, &ix, &iy);
         fx = a.in.fx[j]; fy = a.in.fy[j]; ox = a.in.ox[j]; oy = a.in.oy[j]; w = a.in.w[j];
         srem = a.cdt;
     } else {
         const uint32_t i = (uint32_t)(j - nb);
         T frx, fry;
         const int k = sample_cell<T>(a.cdf, a.nx, a.ny, pts(i, 0), pts(i, 1), &frx, &fry);
-        ix = k % a.nx; iy = k / a.nx;
+        a.split(k, &ix, &iy);
         T f0, f1, f2, f3;
         if constexpr (sizeof(T) == 4) {
             const float4 fk = __ldg(reinterpret_cast<const float4*>(a.f32) + k);
@@ -887,6 +888,7 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.dx = (T)p->dx; a.dy = (T)p->dy;
     a.cdt = (T)(p->d.c * p->d.dt);
     a.w_min = (T)p->d.w_min;
+    a.split = make_cell_split(p->nx);
     a.sig = (const T*)p->sig;
     a.in = bank_view<T>(p, p->cur);
     a.out = bank_view<T>(p, 1 - p->cur);
