@@ -109,8 +109,8 @@ WARM = 1
 # DRAM bytes (read + write) of one launch of the FP32 leg kernel on this workload, from one ncu
 # capture (profiles/mc_leg_kernel_fp32_checkerboard112_ns2.md), with the SHA-256 of the sources the
 # kernel is built from at that capture: the value is reported only while they are unchanged.
-LEG_TRAFFIC_BYTES = None
-LEG_TRAFFIC_SOURCES_SHA256 = None
+LEG_TRAFFIC_BYTES = 52_201_472 + 83_968
+LEG_TRAFFIC_SOURCES_SHA256 = "452712a520f39a5839c9f1959cc01b0a539ed9fc5d22867d89dea195efed70cf"
 LEG_SOURCES = ("mc_leg.cu", "hyb_device.cuh", "hyb_internal.h")
 
 
@@ -482,14 +482,15 @@ def main():
     prof = leg_profile(W.FP32)
     # The MC leg's roofline (the hot path's target): its algorithmic work is one fixed-point tally
     # addition per pre-limit segment and five per post-limit segment (all counted by the kernel:
-    # hyb_leg_stats.tally_adds) plus the census pick-up stream of 24 B per bank particle. Its
+    # hyb_leg_stats.tally_adds) plus its read stream: 24 B per bank particle and the 28 B start
+    # state of each staged birth. Its
     # bound is the rate of 64-bit global atomic additions to the tally footprint (measured live
     # with hyb_atomic_rate on 6 x ncells addresses); the HBM view is reported beside it.
     from paper_2511_16821_gb300 import hyb
     atomic_peak = hyb.atomic_rate(6 * prof["ncells"])
     leg_s = prof["ms"] / 1000.0
     adds_rate = prof["tally_adds"] / leg_s
-    leg_bytes = prof["bank"] * 24
+    leg_bytes = prof["bank"] * 24 + (prof["histories"] - prof["bank"]) * 28
     hbm_achieved = leg_bytes / leg_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
