@@ -690,7 +690,19 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
         hi += h + (nl < lo ? 1ull : 0ull);
         lo = nl;
     }
-    slo[t] = lo; shi[t] = hi;
+    // the 128-bit sum of |w| over the block: a shuffle tree per warp, then the warp sums (exact
+    // modular integer additions, so the order does not matter)
+    {
+        unsigned long long wl = lo, wh = hi;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long l2 = __shfl_down_sync(0xffffffffu, wl, o), h2 = __shfl_down_sync(0xffffffffu, wh, o);
+            const unsigned long long nl = wl + l2;
+            wh += h2 + (nl < wl ? 1ull : 0ull);
+            wl = nl;
+        }
+        if ((t & 31) == 0) { slo[t >> 5] = wl; shi[t >> 5] = wh; }
+    }
     long long ac, aq;
     const long long exc = block_exclusive_scan(c, &ac);
     const long long exq = block_exclusive_scan(q, &aq);
@@ -698,7 +710,7 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
     __syncthreads();
     if (t == 0) {
         unsigned long long al = 0, ah = 0;
-        for (int u = 0; u < nt; ++u) {
+        for (int u = 0; u < (nt + 31) / 32; ++u) {
             const unsigned long long nl = al + slo[u];
             ah += shi[u] + (nl < al ? 1ull : 0ull);
             al = nl;
