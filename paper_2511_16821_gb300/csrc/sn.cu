@@ -666,16 +666,19 @@ __global__ void sn_seed_kernel(const double* prev, const double* prev2, T* phi, 
     phi[i] = w == 0 ? T(0) : (extrap && w >= 2 ? (T)(2.0 * prev[i] - prev2[i]) : (T)prev[i]);
 }
 
-// solves finished with warm starts enabled, counted up to 2
-__global__ void sn_done_kernel(DevState* st, int warm) { st->sn_warm = warm ? min(st->sn_warm + 1, 2) : 0; }
-
-// the solution's FP64 copy; with keep, the copy it replaces moves to out_prev
+// The end of a solve: the solution's FP64 copy (with an extrapolating warm start, the copy it
+// replaces moves to out_prev), the step flux phi_pre + phi_post + phi_c0 per cell, and the count
+// of finished solves with warm starts enabled (up to 2), in one launch.
 template <typename T>
-__global__ void sn_to_double_kernel(const T* phi, double* out, double* out_prev, int n) {
+__global__ void sn_finish_kernel(const T* phi, double* out, double* out_prev, int n, const double* pre,
+                                 const double* post, double* flux, DevState* st, int warm) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) st->sn_warm = warm ? min(st->sn_warm + 1, 2) : 0;
     if (i >= n) return;
     if (out_prev) out_prev[i] = out[i];
-    out[i] = (double)phi[i];
+    const double v = (double)phi[i];
+    out[i] = v;
+    if ((i & 3) == 0) flux[i >> 2] = pre[i >> 2] + post[i >> 2] + v;
 }
 
 // the sn_norm buffer: kAAPart partials per reduction block, then per group, then the group counters
@@ -794,16 +797,14 @@ cudaError_t sn_iteration(hyb_problem* p, int first) {
 cudaError_t sn_finish(hyb_problem* p) {
     const int n = 4 * p->ncells;
     double* keep = p->d.sn_warm_start == 2 ? p->sn_phi_d2 : nullptr;
+    const int warm = p->d.sn_warm_start ? 1 : 0;
     if (p->prec == HYB_FP64)
-        sn_to_double_kernel<double><<<(n + 255) / 256, 256, 0, p->stream>>>((const double*)p->sn_phi_old, p->sn_phi_d,
-                                                                            keep, n);
+        sn_finish_kernel<double><<<(n + 255) / 256, 256, 0, p->stream>>>(
+            (const double*)p->sn_phi_old, p->sn_phi_d, keep, n, p->pre_d, p->post_d, p->flux_d, p->st, warm);
     else
-        sn_to_double_kernel<float><<<(n + 255) / 256, 256, 0, p->stream>>>((const float*)p->sn_phi_old, p->sn_phi_d,
-                                                                           keep, n);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    sn_done_kernel<<<1, 1, 0, p->stream>>>(p->st, p->d.sn_warm_start ? 1 : 0);
-    return launch_flux(p);
+        sn_finish_kernel<float><<<(n + 255) / 256, 256, 0, p->stream>>>(
+            (const float*)p->sn_phi_old, p->sn_phi_d, keep, n, p->pre_d, p->post_d, p->flux_d, p->st, warm);
+    return cudaGetLastError();
 }
 
 }  // namespace hyb
