@@ -267,7 +267,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
-        sn4, sn16, sntx, snty, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell,
+        sn4, sn16, sntx, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell,
         sortkey;
     int64_t cap, nblk, slots;
     int gr, gc;
@@ -318,10 +318,9 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.d1 = nc * 8;
     z.d4 = 4 * nc * 8;
     z.sn4 = 4 * nc * T;
-    z.sn16 = 5 * nc * T;                          // source (4) and sigma* A (1) per cell
-    z.sntx = (size_t)nord * nc * 4 * T;           // w_m psi_m per ordinate and cell
-    z.snty = (size_t)nord * d->nx * 2 * T;        // strip-top traces per ordinate
-    z.snqb = 3 * kMaxOrd * T;
+    z.sn16 = hyb::sn_src_bytes(d->nx, d->ny, d->precision == HYB_FP64);          // sweep sources (padded mesh)
+    z.sntx = (size_t)nord * nc * 4 * T;           // psi per ordinate and cell
+    z.snqb = 7 * kMaxOrd * T;                     // ox, oy, w, then 4 signed weights per ordinate
     z.snnorm = hyb::sn_norm_bytes((int)nc);       // reduction partials per block and group, group counters
     z.nblk = (z.slots + 2047) / 2048;
     z.blk = 4 * (size_t)z.nblk * 8;
@@ -347,7 +346,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
     Layout L;
     const size_t parts[] = {z.st, z.sobol, z.sig, z.sa, z.ss, z.Q, z.cdf_q, z.cdf_row, z.cdf_col, z.cdf_q, z.cdf_row,
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
-                            z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snty, z.snqb, z.d4, z.d4,
+                            z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snqb, z.d4, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
                             z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey};
     for (size_t b : parts) L.add(b);
@@ -391,7 +390,6 @@ void assign(hyb_problem* p) {
     p->sn_phi_old = take(z.sn4);
     p->sn_quad = take(z.sn16);
     p->sn_psi = take(z.sntx);
-    p->sn_ty = take(z.snty);
     p->sn_quadbuf = take(z.snqb);
     p->sn_phi_d = (double*)take(z.d4);
     p->sn_phi_d2 = (double*)take(z.d4);
@@ -488,10 +486,18 @@ void put_sig(const hyb_problem_desc* d, std::vector<unsigned char>* out) {
 
 template <typename T>
 void put_quad(const hyb_problem* p, std::vector<unsigned char>* out) {
-    out->assign(3 * kMaxOrd * sizeof(T), 0);
+    out->assign(7 * kMaxOrd * sizeof(T), 0);
     T* q = (T*)out->data();
+    const int nq = p->n_ord / 4;
     for (int m = 0; m < p->n_ord; ++m) {
         q[m] = (T)p->quad_ox[m]; q[kMaxOrd + m] = (T)p->quad_oy[m]; q[2 * kMaxOrd + m] = (T)p->quad_w[m];
+        // the sweep works in coordinates mirrored to +x, +y (quadrants 0..3: (+,+), (-,+), (-,-), (+,-));
+        // its xi and eta coefficients change sign with the mirror
+        const int quad = m / nq;
+        const double sx = (quad == 0 || quad == 3) ? 1.0 : -1.0, sy = quad <= 1 ? 1.0 : -1.0;
+        const double w = p->quad_w[m];
+        T* wv = q + 3 * kMaxOrd + 4 * m;
+        wv[0] = (T)w; wv[1] = (T)(w * sx); wv[2] = (T)(w * sy); wv[3] = (T)(w * sx * sy);
     }
 }
 
@@ -752,6 +758,9 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     if (chk(cudaMemsetAsync(p->sn_phi_d, 0, 4 * nc * 8, st), "memset phi") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemsetAsync(p->sn_phi_d2, 0, 4 * nc * 8, st), "memset phi") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(sn_clear_counters(p), "memset reduction counters") != HYB_OK) return bail(HYB_ECUDA);
+    // the halo of the sweep sources stays zero (only interior cells are ever written)
+    if (chk(cudaMemsetAsync(p->sn_quad, 0, sn_src_bytes(d->nx, d->ny, p->prec == HYB_FP64), st), "memset sweep sources") != HYB_OK)
+        return bail(HYB_ECUDA);
     // quadrature
     p->n_ord = 0;
     quadrature_host(d->sn_order, p->quad_ox, p->quad_oy, p->quad_w, &p->n_ord);

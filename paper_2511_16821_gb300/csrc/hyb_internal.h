@@ -140,10 +140,9 @@ struct hyb_problem {
     double *pre_raw, *post_raw;                     // raw track-length sums (FP64)
     double sig_s_max;         // max sigma_s (bound of the hand-off moments)
     void* sn_phi; void* sn_phi_old;   // collided flux, 4 Legendre coefficients per cell (T)
-    void* sn_quad;            // per-iteration source (4 per cell) and sigma* A (1 per cell) (T)
-    void* sn_psi;             // w_m psi_m per ordinate and cell (T)
-    void* sn_ty;              // strip-top y traces per ordinate (T)
-    void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, precision T
+    void* sn_quad;            // sweep sources on the padded mesh: S_0..S_3 per cell, then sigma* A per cell (T)
+    void* sn_psi;             // psi_m per ordinate and cell, mirrored coordinates (T)
+    void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, then 4 signed weights per ordinate (T)
     double* sn_phi_d;         // collided flux, FP64 copy (4 x ncells)
     double* sn_phi_d2;        // the solution of the step before (extrapolated warm start only)
     double* sn_norm;          // per-block norm partials (Anderson: kAAMax + 2 per block)
@@ -163,10 +162,11 @@ namespace hyb {
 cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev);
 cudaError_t launch_leg_normalise(hyb_problem* p);
 cudaError_t launch_remap(hyb_problem* p);
-cudaError_t launch_census(hyb_problem* p);
-size_t sn_accel_state_bytes();
+cudaError_t launch_census(hyb_problem* p);   // N_s = infinity: MC-leg census -> new bank
+size_t sn_accel_state_bytes();                // device bytes of the Anderson state
 size_t sn_norm_bytes(int ncells);            // reduction scratch of the source iteration
-cudaError_t sn_clear_counters(hyb_problem* p);               // device bytes of the Anderson state   // N_s = infinity: MC-leg census -> new bank
+cudaError_t sn_clear_counters(hyb_problem* p);
+size_t sn_src_bytes(int nx, int ny, bool fp64);             // sweep sources on the padded mesh
 cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView cdf, double* W_out_dev,
                              double* qmax_out_dev);
 cudaError_t launch_flux(hyb_problem* p);

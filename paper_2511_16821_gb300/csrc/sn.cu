@@ -10,7 +10,8 @@
 // Sweep: one CTA per ordinate; its warps walk 32-row strips as wavefronts (lane = row, one
 // anti-diagonal per step); the trace entering a row from below comes from the neighbouring lane by
 // shuffle (from the strip below through a shared-memory ring), the trace from the left stays in
-// registers, so a step needs no block barrier. Strips are pipelined across the warps, so the
+// registers, so a step needs no block barrier. Sources and solutions live on a mesh padded with
+// halo columns and an extra row, so a step also needs no bound test. Strips are pipelined across the warps, so the
 // critical path is about (nx + 31) + 32 (ceil(ny/32) - 1) cell solves per sweep. Coordinates are mirrored per quadrant so that every
 // sweep runs towards +x,+y; in mirrored coordinates the 4x4 cell system is the same for every
 // quadrant and is diagonally dominant, so it is solved by elimination without pivoting. The
@@ -23,14 +24,32 @@
 
 namespace hyb {
 
+// Padded mesh of the sweep's sources: every row carries kHalo columns on both sides, and one extra
+// row follows the last; halo and extra row are zero. A lane before its row's first column, past its
+// last, or on a row beyond the mesh then loads zero data without a bound test, and a cell solve with
+// zero data and zero inflow returns zero traces, so the inflow of column 0 is zero without a reset.
+// kHalo covers the columns a lane reads: loads run PF steps ahead of the step, the last block of
+// steps overruns the wavefront by up to PF - 1, and lane l trails lane 0 by l. The solutions psi
+// stay on the plain mesh: their store is predicated on the lane holding a mesh cell.
+// cell data prefetch depth of the sweep, in wavefront steps (a ring of register sets, unrolled so
+// that no value moves between registers while its load is in flight)
+template <typename T> struct SweepDepth { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
+
+template <typename T> struct SweepPad {
+    static constexpr int kHalo = 32 + 2 * SweepDepth<T>::value;
+    static __host__ __device__ int nxp(int nx) { return nx + 2 * kHalo; }
+    static __host__ __device__ size_t plane(int nx, int ny) { return (size_t)(ny + 1) * nxp(nx); }
+    static __host__ __device__ size_t at(int nx, int ix, int iy) { return (size_t)iy * nxp(nx) + kHalo + ix; }
+};
+
 template <typename T>
 struct SweepArgs {
-    int nx, ny, nq, nord, W;
+    int nx, ny, nq, nord, W, re;   // re: ring entries per slot
     T dx, dy;
-    const T* sgA;            // (sigma_t + 1/(c dt)) A per cell
-    const T* src;            // per cell the four source integrals S_i (un-mirrored)
-    const T* qox; const T* qoy; const T* qw;   // ordinates by quadrant: m = quad * nq + q
-    T* psi;                  // per ordinate and cell: w_m psi (4 Legendre coefficients)
+    const T* src;            // per padded cell the four source integrals S_i (un-mirrored)
+    const T* sgA;            // per padded cell (sigma_t + 1/(c dt)) A
+    const T* qox; const T* qoy;    // ordinates by quadrant: m = quad * nq + q
+    T* psi;                  // per ordinate and cell, psi (4 Legendre coefficients, mirrored coordinates)
     int* status;             // device status word (bounded waits)
     const int* conv;         // converged flag: set -> the sweep returns at once
 };
@@ -46,52 +65,67 @@ __device__ __forceinline__ void source4(T ss, T area, const T* po, const double*
 }
 
 template <typename T>
-__global__ void sn_source_kernel(int ncells, const T* sig, const T* phi_old, const double* mom, T area,
+__global__ void sn_source_kernel(int ncells, CellSplit split, const T* sig, const T* phi_old, const double* mom, T area,
                                  T inv_4pi_dt, T inv_cdt, T* src, T* sgA) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ncells) return;
+    int ix, iy;
+    split(k, &ix, &iy);
+    const size_t pk = SweepPad<T>::at(split.nx, ix, iy);
     const T sa = sig[2 * k], ss = sig[2 * k + 1];
-    source4<T>(ss, area, phi_old + 4 * (size_t)k, mom + 4 * (size_t)k, inv_4pi_dt, src + 4 * (size_t)k);
-    sgA[k] = (sa + ss + inv_cdt) * area;
+    source4<T>(ss, area, phi_old + 4 * (size_t)k, mom + 4 * (size_t)k, inv_4pi_dt, src + 4 * pk);
+    sgA[pk] = (sa + ss + inv_cdt) * area;
 }
 
 // Cell data of one wavefront step: the four source integrals (un-mirrored) and (sigma_t + 1/(c dt)) A.
 template <typename T> struct CellIn { T s0, s1, s2, s3, sA; };
 
-template <typename T>
-__device__ __forceinline__ void load_cell(const T* src, const T* sgA, size_t k, CellIn<T>& d);
-template <>
-__device__ __forceinline__ void load_cell<float>(const float* src, const float* sgA, size_t k, CellIn<float>& d) {
-    const float4 v = __ldg(reinterpret_cast<const float4*>(src) + k);
+// s4: the cell's four source integrals, sa: its sigma* A (two arrays, so that the cells a lane takes
+// in consecutive steps share sectors)
+__device__ __forceinline__ void load_cell(const float* s4, const float* sa, CellIn<float>& d) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(s4));
     d.s0 = v.x; d.s1 = v.y; d.s2 = v.z; d.s3 = v.w;
-    d.sA = __ldg(sgA + k);
+    d.sA = __ldg(sa);
 }
-template <>
-__device__ __forceinline__ void load_cell<double>(const double* src, const double* sgA, size_t k, CellIn<double>& d) {
-    const double2 v0 = __ldg(reinterpret_cast<const double2*>(src) + 2 * k);
-    const double2 v1 = __ldg(reinterpret_cast<const double2*>(src) + 2 * k + 1);
+__device__ __forceinline__ void load_cell(const double* s4, const double* sa, CellIn<double>& d) {
+    const double2 v0 = __ldg(reinterpret_cast<const double2*>(s4));
+    const double2 v1 = __ldg(reinterpret_cast<const double2*>(s4) + 1);
     d.s0 = v0.x; d.s1 = v0.y; d.s2 = v1.x; d.s3 = v1.y;
-    d.sA = __ldg(sgA + k);
+    d.sA = __ldg(sa);
 }
 
-__device__ __forceinline__ void store_cell(float* d, float a0, float a1, float a2, float a3) {
-    *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
+// a predicated store of one cell's four coefficients (no branch in the step; an address formed for a
+// lane that holds no cell is never accessed)
+__device__ __forceinline__ void store_cell_if(bool p, float* d, float a0, float a1, float a2, float a3) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t@q st.global.v4.f32 [%1], {%2, %3, %4, %5};\n\t}"
+        ::"r"((uint32_t)p), "l"(d), "f"(a0), "f"(a1), "f"(a2), "f"(a3)
+        : "memory");
 }
-__device__ __forceinline__ void store_cell(double* d, double a0, double a1, double a2, double a3) {
-    reinterpret_cast<double2*>(d)[0] = make_double2(a0, a1);
-    reinterpret_cast<double2*>(d)[1] = make_double2(a2, a3);
+__device__ __forceinline__ void store_cell_if(bool p, double* d, double a0, double a1, double a2, double a3) {
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+        "@q st.global.v2.f64 [%1], {%2, %3};\n\t@q st.global.v2.f64 [%1+16], {%4, %5};\n\t}"
+        ::"r"((uint32_t)p), "l"(d), "d"(a0), "d"(a1), "d"(a2), "d"(a3)
+        : "memory");
 }
 
 // Strip-to-strip trace ring: each 32-bit piece of the two traces of a column travels with a 32-bit
-// sequence tag in one 64-bit shared-memory word (a single-copy-atomic access), so a reader that
-// sees the expected tag in every word of the entry has the values, with no fence and no counter.
+// sequence tag in one 64-bit shared-memory word (a single-copy-atomic access; a vector store of
+// such words is one access per word), so a reader that sees the expected tag in every word of the
+// entry has the values, with no fence and no counter.
 template <typename T> struct Ring;
 template <> struct Ring<float> {
     static constexpr int kWords = 2;
-    static __device__ __forceinline__ void put(volatile unsigned long long* e, float v0, float v1, uint32_t tag) {
-        const unsigned long long hi = (unsigned long long)tag << 32;
-        e[0] = hi | __float_as_uint(v0);
-        e[1] = hi | __float_as_uint(v1);
+    // stores the entry at shared address e when p (a predicated store: no branch in the step)
+    static __device__ __forceinline__ void put_if(bool p, uint32_t e, float v0, float v1, uint32_t tag) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t.reg .b64 w0, w1;\n\t"
+            "setp.ne.u32 q, %0, 0;\n\t"
+            "mov.b64 w0, {%2, %4};\n\tmov.b64 w1, {%3, %4};\n\t"
+            "@q st.volatile.shared.v2.u64 [%1], {w0, w1};\n\t}"
+            ::"r"((uint32_t)p), "r"(e), "r"(__float_as_uint(v0)), "r"(__float_as_uint(v1)), "r"(tag)
+            : "memory");
     }
     // true when both words carry the tag; the values in v0, v1
     static __device__ __forceinline__ bool get(const volatile unsigned long long* e, uint32_t tag, float* v0, float* v1) {
@@ -103,12 +137,17 @@ template <> struct Ring<float> {
 };
 template <> struct Ring<double> {
     static constexpr int kWords = 4;
-    static __device__ __forceinline__ void put(volatile unsigned long long* e, double v0, double v1, uint32_t tag) {
-        const unsigned long long hi = (unsigned long long)tag << 32;
-        e[0] = hi | (uint32_t)__double2loint(v0);
-        e[1] = hi | (uint32_t)__double2hiint(v0);
-        e[2] = hi | (uint32_t)__double2loint(v1);
-        e[3] = hi | (uint32_t)__double2hiint(v1);
+    static __device__ __forceinline__ void put_if(bool p, uint32_t e, double v0, double v1, uint32_t tag) {
+        asm volatile(
+            "{\n\t.reg .pred q;\n\t.reg .b64 w0, w1, w2, w3;\n\t"
+            "setp.ne.u32 q, %0, 0;\n\t"
+            "mov.b64 w0, {%2, %6};\n\tmov.b64 w1, {%3, %6};\n\t"
+            "mov.b64 w2, {%4, %6};\n\tmov.b64 w3, {%5, %6};\n\t"
+            "@q st.volatile.shared.v2.u64 [%1], {w0, w1};\n\t"
+            "@q st.volatile.shared.v2.u64 [%1+16], {w2, w3};\n\t}"
+            ::"r"((uint32_t)p), "r"(e), "r"((uint32_t)__double2loint(v0)), "r"((uint32_t)__double2hiint(v0)),
+              "r"((uint32_t)__double2loint(v1)), "r"((uint32_t)__double2hiint(v1)), "r"(tag)
+            : "memory");
     }
     static __device__ __forceinline__ bool get(const volatile unsigned long long* e, uint32_t tag, double* v0, double* v1) {
         const unsigned long long a = e[0], b = e[1], c = e[2], d = e[3];
@@ -160,66 +199,55 @@ __device__ __forceinline__ CellSolve<T> cell_solve(T sA, T X, T Y) {
     return c;
 }
 
-// cell data prefetch depth of the sweep, in wavefront steps (a ring of register sets, unrolled so
-// that no value moves between registers while its load is in flight)
-template <typename T> struct SweepDepth { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
 
-// Pipelined strip sweep, one CTA per ordinate, W warps. Warp w sweeps strips w, w+W, ... (lane =
-// row, one anti-diagonal per step). The trace leaving the top row of strip s goes through entry
-// (slot s mod W, column c) of a tagged shared-memory ring to the first row of strip s+1; the
-// reader waits until the entry carries its sequence number. When strips outnumber the warps a
-// slot is reused, and its writer first waits for the previous reader's consumed-column counter
-// (published once per prefetch block). Every wait is bounded and records kStSegments on
-// exhaustion. Dependencies only point to lower strips, and all warps of the CTA are resident, so
-// the pipeline always advances. The step body is branch-free apart from the (uniform) waits.
-template <typename T>
-__global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
+// Pipelined strip sweep of one ordinate, W warps, in coordinates mirrored to +x, +y (SX: the x
+// direction of the ordinate before mirroring; the y mirror only changes a strip's first row). Warp w
+// sweeps strips w, w+W, ... (lane = row, one anti-diagonal per step). The trace leaving the top row
+// of strip s goes through entry (slot s mod W, step) of a tagged shared-memory ring to the first row
+// of strip s+1; the reader waits until the entries of its next PF columns carry their sequence
+// numbers. When strips outnumber the warps a slot is reused, and its writer first waits for the
+// previous reader's consumed-column counter (published once per prefetch block). Every wait is
+// bounded and records kStSegments on exhaustion. Dependencies only point to lower strips, and all
+// warps of the CTA are resident, so the pipeline always advances. Between the waits a block of PF
+// steps is straight-line code: addresses are the lane's base plus compile-time offsets on the padded
+// mesh, the store into the ring is predicated, and nothing is tested per step.
+template <typename T, int SX>
+__device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int sy, volatile int* cons,
+                                               volatile unsigned long long* ring, uint32_t ring_sa,
+                                               bool& timed_out) {
     constexpr int PF = SweepDepth<T>::value;
     constexpr int RW = Ring<T>::kWords;
-    if (*(volatile const int*)a.conv) return;
-    extern __shared__ unsigned char smraw[];
     const int W = a.W;
-    const int nx = a.nx, ny = a.ny;
-    volatile int* cons = (volatile int*)smraw;
-    volatile unsigned long long* ring =
-        (volatile unsigned long long*)(smraw + ((W * sizeof(int) + 15) / 16) * 16);   // W x nx x RW
-    for (int i = threadIdx.x; i < W; i += blockDim.x) cons[i] = 0;
-    for (int i = threadIdx.x; i < W * nx * RW; i += blockDim.x) ring[i] = 0ull;   // no tag is 0
-    __syncthreads();
-    const int m = blockIdx.x;
+    const int nx = a.nx, ny = a.ny, re = a.re;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int quad = m / a.nq;
-    const int sx = (quad == 0 || quad == 3) ? 1 : -1;
-    const int sy = (quad <= 1) ? 1 : -1;
-    const T sxf = (T)sx, syf = (T)sy, sxy = (T)(sx * sy);
-    const T wq = a.qw[m];
+    const T syf = (T)sy, sxy = (T)(SX * sy), sxf = (T)SX;
     const T X = fabs(a.qox[m]) * a.dy * T(0.5), Y = fabs(a.qoy[m]) * a.dx * T(0.5);
     const T twoX = T(2) * X, twoY = T(2) * Y, tX = T(2.0 / 3.0) * X, tY = T(2.0 / 3.0) * Y;
-    const T w1 = wq * sxf, w2 = wq * syf, w3 = wq * sxy;
     T* out = a.psi + (size_t)m * nx * ny * 4;
     const int nstrip = (ny + 31) / 32;
     const bool reuse = nstrip > W;
     const int nsteps = nx + 31;
-    bool timed_out = false;
     for (int s = warp; s < nstrip && !timed_out; s += W) {
         const int ly = 32 * s + lane;
-        const bool row_ok = ly < ny;
-        const int iy = sy > 0 ? ly : ny - 1 - ly;
-        const size_t rowk = (size_t)iy * nx;
+        const int iy = ly < ny ? (sy > 0 ? ly : ny - 1 - ly) : ny;   // rows past the mesh: the extra row
+        // padded index of this lane's cell at step t is base + SX t (column t - lane in mirrored x)
+        const long long base = (long long)SweepPad<T>::at(nx, SX > 0 ? 0 : nx - 1, iy) - (long long)SX * lane;
+        const T* src = a.src + base * 4;
+        const T* sga = a.sgA + base;
+        // psi of this lane's cell at step t: po + 4 SX t (formed only where the lane holds a cell)
+        T* po = out + ((long long)iy * nx + (SX > 0 ? 0 : nx - 1) - (long long)SX * lane) * 4;
+        const unsigned nxl = ly < ny ? (unsigned)nx : 0u;   // columns this lane stores
         const int bin = (s - 1 + W) % W, bout = s % W;
         const int qin = ((s - 1) / W) * nx, qout = (s / W) * nx;   // sequence bases of the ring slots
         const bool has_in = s > 0, has_out = s + 1 < nstrip;
         const bool put = has_out && lane == 31;
-        volatile unsigned long long* rin = ring + (size_t)bin * nx * RW;
-        volatile unsigned long long* rout = ring + (size_t)bout * nx * RW;
+        // the reader takes column t from entry t + 31; lane 31 writes column t - 31 into entry t
+        volatile unsigned long long* rin = ring + (size_t)bin * re * RW;
+        const uint32_t rout = ring_sa + (uint32_t)((size_t)bout * re * RW * 8);
         T bx0 = 0, bx1 = 0, oy0 = 0, oy1 = 0;
         CellIn<T> q[PF];
 #pragma unroll
-        for (int i = 0; i < PF; ++i) {
-            q[i] = CellIn<T>{0, 0, 0, 0, 1};
-            const int col = i - lane;
-            if (row_ok && col >= 0 && col < nx) load_cell<T>(a.src, a.sgA, rowk + (sx > 0 ? col : nx - 1 - col), q[i]);
-        }
+        for (int i = 0; i < PF; ++i) load_cell(src + SX * i * 4, sga + SX * i, q[i]);
         for (int t0 = 0; t0 < nsteps; t0 += PF) {
             // a reused slot: the previous reader must have taken the columns this block writes
             if (reuse && has_out && s >= W) {
@@ -231,11 +259,9 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
                 }
             }
             // the incoming traces of this block's columns (lane 0's row), taken from the ring once all
-            // carry their tags. Waiting once per block keeps the block's steps one branch-free
+            // carry their tags. Waiting once per block keeps the block's steps one straight-line
             // sequence, so the trace-independent cell solves of later steps fill the latency of the
-            // current step's chain (measured: 0.44 -> 0.39 ms per solve of the 112^2 S8 benchmark,
-            // against waits every step; every 2 or 4 steps lie between). Every lane reads the same
-            // entries (broadcast), so the wait is uniform.
+            // current step's chain. Every lane reads the same entries (broadcast): the wait is uniform.
             T rv0[PF], rv1[PF];
 #pragma unroll
             for (int i = 0; i < PF; ++i) { rv0[i] = T(0); rv1[i] = T(0); }
@@ -246,24 +272,24 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
 #pragma unroll
                     for (int i = 0; i < PF; ++i) {
                         const int t = t0 + i;
-                        if (t < nx) ok &= Ring<T>::get(rin + (size_t)t * RW, (uint32_t)(qin + t + 1), &rv0[i], &rv1[i]);
+                        if (t < nx) ok &= Ring<T>::get(rin + (size_t)(t + 31) * RW, (uint32_t)(qin + t + 1), &rv0[i], &rv1[i]);
                     }
                     if (ok) break;
                     if (++spins > (1 << 22)) { timed_out = true; break; }
                     __nanosleep(20);
                 }
             }
+            const T* sb = src + (long long)SX * (t0 + PF) * 4;
+            const T* ab = sga + (long long)SX * (t0 + PF);
+            T* pb = po + (long long)SX * t0 * 4;
+            const uint32_t wb = rout + (uint32_t)(t0 * RW * 8);
+            const uint32_t tagb = (uint32_t)(qout + t0 - 30);
 #pragma unroll
             for (int i = 0; i < PF; ++i) {
-                const int t = t0 + i;
-                const int c = t - lane;
-                const bool act = row_ok && c >= 0 && c < nx;
                 const T u0 = __shfl_up_sync(0xffffffffu, oy0, 1);
                 const T u1 = __shfl_up_sync(0xffffffffu, oy1, 1);
                 const T by0 = lane == 0 ? rv0[i] : u0;
                 const T by1 = lane == 0 ? rv1[i] : u1;
-                bx0 = c == 0 ? T(0) : bx0;
-                bx1 = c == 0 ? T(0) : bx1;
                 const CellSolve<T> cs = cell_solve<T>(q[i].sA, X, Y);
                 const T b0 = q[i].s0 + twoX * bx0 + twoY * by0;
                 const T b1 = sxf * q[i].s1 - twoX * bx0 + tY * by1;
@@ -273,17 +299,13 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
                 const T r2 = b2 + cs.k3 * b0 - cs.k4 * b3;
                 const T a1 = cs.Di * r1 - cs.Bi * r2;
                 const T a2 = cs.Ai * r2 - cs.Bi * r1;
-                const T a0 = (b0 - twoX * a1 - twoY * a2) * cs.i0;
-                const T a3 = (b3 + tY * a1 + tX * a2) * cs.i3;
+                const T a0 = cs.i0 * b0 - cs.k1 * a1 - cs.k3 * a2;   // (b0 - 2X a1 - 2Y a2) / d0
+                const T a3 = cs.i3 * b3 + cs.k2 * a1 + cs.k4 * a2;   // (b3 + tY a1 + tX a2) / d3
                 bx0 = a0 + a1; bx1 = a2 + a3;
                 oy0 = a0 + a2; oy1 = a1 + a3;
-                if (act) {
-                    const int ix = sx > 0 ? c : nx - 1 - c;
-                    store_cell(out + (rowk + ix) * 4, wq * a0, w1 * a1, w2 * a2, w3 * a3);
-                    if (put) Ring<T>::put(rout + (size_t)c * RW, oy0, oy1, (uint32_t)(qout + c + 1));
-                }
-                const int col = c + PF;
-                if (row_ok && col >= 0 && col < nx) load_cell<T>(a.src, a.sgA, rowk + (sx > 0 ? col : nx - 1 - col), q[i]);
+                store_cell_if((unsigned)(t0 + i - lane) < nxl, pb + SX * i * 4, a0, a1, a2, a3);
+                Ring<T>::put_if(put, wb + (uint32_t)(i * RW * 8), oy0, oy1, tagb + (uint32_t)i);
+                load_cell(sb + SX * i * 4, ab + SX * i, q[i]);
             }
             // publish the columns this warp has taken from its input slot (only needed on reuse)
             if (reuse && has_in && lane == 0) {
@@ -293,7 +315,28 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
             if (__any_sync(0xffffffffu, timed_out)) { timed_out = true; break; }
         }
     }
-    if (timed_out && lane == 0) atomicOr(a.status, kStSegments);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
+    constexpr int RW = Ring<T>::kWords;
+    if (*(volatile const int*)a.conv) return;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int W = a.W;
+    volatile int* cons = (volatile int*)smraw;
+    const size_t ring_off = ((W * sizeof(int) + 15) / 16) * 16;
+    volatile unsigned long long* ring = (volatile unsigned long long*)(smraw + ring_off);   // W x re x RW
+    for (int i = threadIdx.x; i < W; i += blockDim.x) cons[i] = 0;
+    for (int i = threadIdx.x; i < W * a.re * RW; i += blockDim.x) ring[i] = 0ull;   // no tag is 0
+    __syncthreads();
+    const int m = blockIdx.x;
+    const int quad = m / a.nq;
+    const int sy = (quad <= 1) ? 1 : -1;
+    const uint32_t ring_sa = (uint32_t)__cvta_generic_to_shared(smraw + ring_off);
+    bool timed_out = false;
+    if (quad == 0 || quad == 3) sweep_ordinate<T, 1>(a, m, sy, cons, ring, ring_sa, timed_out);
+    else sweep_ordinate<T, -1>(a, m, sy, cons, ring, ring_sa, timed_out);
+    if (timed_out && (threadIdx.x & 31) == 0) atomicOr(a.status, kStSegments);
 }
 
 // One source iteration's reduction. A block covers 32 cells: thread (g, c) sums the weighted
@@ -402,10 +445,40 @@ template <> struct Vec4<double> {
     }
 };
 
+// The ordinate sum of one cell over ordinates g, g + kRedGroups, ...: psi_m (mirrored coefficients)
+// times the signed weights (w_m, w_m s_x, w_m s_y, w_m s_x s_y) that undo the mirror, in ordinate
+// order.
+template <typename T>
+__device__ __forceinline__ void weighted_psi_sum(const T* psi, int nord, const T* qwv, int k, int ncells, int g,
+                                                 T* out) {
+    constexpr int kPer = (kMaxOrd + kRedGroups - 1) / kRedGroups;   // ordinates per thread, at most
+    T acc[4] = {0, 0, 0, 0};
+    if (k < ncells) {
+        // all loads first (in flight together), then the sum in ordinate order
+        T v[kPer][4];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int m = g + j * kRedGroups;
+            if (m < nord) Vec4<T>::load(psi + ((size_t)m * ncells + k) * 4, v[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int m = g + j * kRedGroups;
+            if (m < nord) {
+                T w[4];
+                Vec4<T>::load(qwv + 4 * m, w);
+                acc[0] += w[0] * v[j][0]; acc[1] += w[1] * v[j][1]; acc[2] += w[2] * v[j][2]; acc[3] += w[3] * v[j][3];
+            }
+        }
+    }
+    out[0] = acc[0]; out[1] = acc[1]; out[2] = acc[2]; out[3] = acc[3];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kRedCells * kRedGroups)
-sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, RedScratch rs, const T* sig,
-                 const double* mom, T area, T inv_4pi_dt, T* src, DevState* st, double tol) {
+sn_reduce_kernel(const T* psi, int nord, const T* qwv, CellSplit split, const T* phi_old, T* phi_new,
+                 int ncells, RedScratch rs, const T* sig, const double* mom, T area, T inv_4pi_dt, T* src, DevState* st,
+                 double tol) {
     __shared__ T sp[kRedGroups][kRedCells][4];
     __shared__ double sred[2][kRedCells * 4 / 32];
     __shared__ double s_tot[2];
@@ -419,17 +492,7 @@ sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncell
         }
         return;
     }
-    {
-        const int k = k0 + c;
-        T acc[4] = {0, 0, 0, 0};
-        if (k < ncells)
-            for (int m = g; m < nord; m += kRedGroups) {
-                T v[4];
-                Vec4<T>::load(psi + ((size_t)m * ncells + k) * 4, v);
-                acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2]; acc[3] += v[3];
-            }
-        sp[g][c][0] = acc[0]; sp[g][c][1] = acc[1]; sp[g][c][2] = acc[2]; sp[g][c][3] = acc[3];
-    }
+    weighted_psi_sum<T>(psi, nord, qwv, k0 + c, ncells, g, sp[g][c]);
     __syncthreads();
     if (threadIdx.x < kRedCells * 4) {
         const int cc = threadIdx.x >> 2, i = threadIdx.x & 3;
@@ -448,7 +511,9 @@ sn_reduce_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncell
             den = nrm * v * v;
             // source integral i: sigma_s A n_i phi_i / (4 pi) + m_i / (4 pi dt)
             const T cs = sig[2 * (size_t)k + 1] * area * T(0.07957747154594767);
-            src[e] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
+            int ix, iy;
+            split(k, &ix, &iy);
+            src[SweepPad<T>::at(split.nx, ix, iy) * 4 + i] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
         }
         // warp sums (fixed tree), then block sum in warp order
         for (int o = 16; o > 0; o >>= 1) {
@@ -535,8 +600,8 @@ __device__ void aa_solve(AAState* aa, const int* slots, int n) {
 // completes the Gram matrix, applies the stop test and, if the solve goes on, forms the weights.
 template <typename T>
 __global__ void __launch_bounds__(kRedCells * kRedGroups)
-sn_reduce_aa_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int ncells, RedScratch rs, T* g_hist,
-                    T* f_hist, int depth, AAState* aa, DevState* st, double tol) {
+sn_reduce_aa_kernel(const T* psi, int nord, const T* qwv, const T* phi_old, T* phi_new,
+                    int ncells, RedScratch rs, T* g_hist, T* f_hist, int depth, AAState* aa, DevState* st, double tol) {
     __shared__ T sp[kRedGroups][kRedCells][4];
     __shared__ double sred[kAAPart][kRedCells * 4 / 32];
     __shared__ double s_tot[kAAPart];
@@ -552,17 +617,7 @@ sn_reduce_aa_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int nc
     const int nslot = depth + 1;
     const int head = aa->head, n_new = aa->n + 1 < nslot ? aa->n + 1 : nslot;
     const size_t nv = (size_t)ncells * 4;
-    {
-        const int k = k0 + c;
-        T acc[4] = {0, 0, 0, 0};
-        if (k < ncells)
-            for (int m = g; m < nord; m += kRedGroups) {
-                T v[4];
-                Vec4<T>::load(psi + ((size_t)m * ncells + k) * 4, v);
-                acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2]; acc[3] += v[3];
-            }
-        sp[g][c][0] = acc[0]; sp[g][c][1] = acc[1]; sp[g][c][2] = acc[2]; sp[g][c][3] = acc[3];
-    }
+    weighted_psi_sum<T>(psi, nord, qwv, k0 + c, ncells, g, sp[g][c]);
     __syncthreads();
     if (threadIdx.x < kRedCells * 4) {
         const int cc = threadIdx.x >> 2, i = threadIdx.x & 3;
@@ -632,7 +687,8 @@ sn_reduce_aa_kernel(const T* psi, int nord, const T* phi_old, T* phi_new, int nc
 // source integrals of the next sweep from it.
 template <typename T>
 __global__ void sn_mix_kernel(T* phi_new, const T* g_hist, int ncells, int depth, const AAState* aa,
-                              const DevState* st, const T* sig, const double* mom, T area, T inv_4pi_dt, T* src) {
+                              const DevState* st, const T* sig, const double* mom, T area, T inv_4pi_dt,
+                              CellSplit split, T* src) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nv = (size_t)ncells * 4;
     if (e >= nv || *(volatile const int*)&st->sn_conv) return;
@@ -650,7 +706,9 @@ __global__ void sn_mix_kernel(T* phi_new, const T* g_hist, int ncells, int depth
     const size_t k = e >> 2;
     const T n_i = i == 0 ? T(1) : (i == 3 ? T(1.0 / 9.0) : T(1.0 / 3.0));
     const T cs = sig[2 * k + 1] * area * T(0.07957747154594767);
-    src[e] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
+    int ix, iy;
+    split((int)k, &ix, &iy);
+    src[SweepPad<T>::at(split.nx, ix, iy) * 4 + i] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
 }
 
 // start of a solve: clear the stop state; the iterate starts from zero, from the previous step's
@@ -705,10 +763,18 @@ cudaError_t sn_clear_counters(hyb_problem* p) {
     return cudaMemsetAsync(r.gcnt, 0, ngrp * sizeof(unsigned), p->stream);
 }
 
+size_t sn_src_bytes(int nx, int ny, bool fp64) {
+    return fp64 ? SweepPad<double>::plane(nx, ny) * 5 * sizeof(double) : SweepPad<float>::plane(nx, ny) * 5 * sizeof(float);
+}
+
+// ring entries per slot: every step of a strip's last block, lane 31 trailing lane 0 by 31 columns
+template <typename T>
+static int ring_entries(int nx) { return nx + 31 + SweepDepth<T>::value; }
+
 template <typename T>
 static int sweep_warps(const hyb_problem* p, size_t* smem) {
     const int nstrip = (p->ny + 31) / 32;
-    const size_t per = (size_t)p->nx * Ring<T>::kWords * sizeof(unsigned long long);
+    const size_t per = (size_t)ring_entries<T>(p->nx) * Ring<T>::kWords * sizeof(unsigned long long);
     int W = nstrip < 16 ? nstrip : 16;
     while (W > 1 && (size_t)W * per + 256 > 160 * 1024) --W;
     *smem = ((W * sizeof(int) + 15) / 16) * 16 + (size_t)W * per;
@@ -719,21 +785,25 @@ template <typename T>
 static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     cudaStream_t s = p->stream;
     const int g = (p->ncells + 255) / 256;
-    T* src = (T*)p->sn_quad;                      // 4 per cell
-    T* sgA = src + 4 * (size_t)p->ncells;         // 1 per cell
+    const size_t plane = SweepPad<T>::plane(p->nx, p->ny);
+    T* src = (T*)p->sn_quad;          // 4 per padded cell
+    T* sgA = src + 4 * plane;         // 1 per padded cell
+    const CellSplit split = make_cell_split(p->nx);
     const T inv4pidt = (T)(1.0 / (4.0 * 3.14159265358979323846 * p->d.dt));
     if (first)
-        sn_source_kernel<T><<<g, 256, 0, s>>>(p->ncells, (const T*)p->sig, (const T*)p->sn_phi_old, p->mom_d,
+        sn_source_kernel<T><<<g, 256, 0, s>>>(p->ncells, split, (const T*)p->sig, (const T*)p->sn_phi_old, p->mom_d,
                                               (T)p->area, inv4pidt, (T)(1.0 / (p->d.c * p->d.dt)), src, sgA);
+    const T* qbuf = (const T*)p->sn_quadbuf;
+    const T* qwv = qbuf + 3 * kMaxOrd;
     SweepArgs<T> a;
     a.nx = p->nx; a.ny = p->ny;
     a.nq = p->n_ord / 4;
     a.nord = p->n_ord;
+    a.re = ring_entries<T>(p->nx);
     a.dx = (T)p->dx; a.dy = (T)p->dy;
-    a.sgA = sgA;
     a.src = src;
-    T* qbuf = (T*)p->sn_quadbuf;
-    a.qox = qbuf; a.qoy = qbuf + kMaxOrd; a.qw = qbuf + 2 * kMaxOrd;
+    a.sgA = sgA;
+    a.qox = qbuf; a.qoy = qbuf + kMaxOrd;
     a.psi = (T*)p->sn_psi;
     a.status = &p->st->status;
     a.conv = &p->st->sn_conv;
@@ -752,18 +822,18 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
         T* gh = (T*)p->aa_hist;
         T* fh = gh + (size_t)(depth + 1) * nv;
         sn_reduce_aa_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>(
-            (const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, gh, fh, depth,
-            (AAState*)p->aa_state, p->st, sn_tol_eff(p));
+            (const T*)p->sn_psi, p->n_ord, qwv, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, gh,
+            fh, depth, (AAState*)p->aa_state, p->st, sn_tol_eff(p));
         sn_mix_kernel<T><<<(unsigned)((nv + 255) / 256), 256, 0, s>>>((T*)p->sn_phi, gh, p->ncells, depth,
                                                                       (const AAState*)p->aa_state, p->st,
                                                                       (const T*)p->sig, p->mom_d, (T)p->area,
-                                                                      inv4pidt, src);
+                                                                      inv4pidt, split, src);
         return cudaGetLastError();
     }
-    sn_reduce_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, (const T*)p->sn_phi_old,
-                                                              (T*)p->sn_phi, p->ncells, rs, (const T*)p->sig,
-                                                              p->mom_d, (T)p->area, inv4pidt, src, p->st,
-                                                              sn_tol_eff(p));
+    sn_reduce_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, qwv, split,
+                                                              (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs,
+                                                              (const T*)p->sig, p->mom_d, (T)p->area, inv4pidt, src,
+                                                              p->st, sn_tol_eff(p));
     return cudaGetLastError();
 }
 
