@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -267,7 +268,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
-        sn4, sn16, sntx, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell,
+        sn4, sn16, sntx, sntab, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell,
         sortkey;
     int64_t cap, nblk, slots;
     int gr, gc;
@@ -320,6 +321,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.sn4 = 4 * nc * T;
     z.sn16 = hyb::sn_src_bytes(d->nx, d->ny, d->precision == HYB_FP64);          // sweep sources (padded mesh)
     z.sntx = (size_t)nord * nc * 4 * T;           // psi per ordinate and cell
+    z.sntab = hyb::sn_table_bytes(d->nx, d->ny, nord, d->precision == HYB_FP64);   // cell-solve table or 0
     z.snqb = 7 * kMaxOrd * T;                     // ox, oy, w, then 4 signed weights per ordinate
     z.snnorm = hyb::sn_norm_bytes((int)nc);       // reduction partials per block and group, group counters
     z.nblk = (z.slots + 2047) / 2048;
@@ -346,7 +348,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
     Layout L;
     const size_t parts[] = {z.st, z.sobol, z.sig, z.sa, z.ss, z.Q, z.cdf_q, z.cdf_row, z.cdf_col, z.cdf_q, z.cdf_row,
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
-                            z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.snqb, z.d4, z.d4,
+                            z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.sntab, z.snqb, z.d4, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
                             z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey};
     for (size_t b : parts) L.add(b);
@@ -390,6 +392,7 @@ void assign(hyb_problem* p) {
     p->sn_phi_old = take(z.sn4);
     p->sn_quad = take(z.sn16);
     p->sn_psi = take(z.sntx);
+    p->sn_table = z.sntab ? take(z.sntab) : nullptr;
     p->sn_quadbuf = take(z.snqb);
     p->sn_phi_d = (double*)take(z.d4);
     p->sn_phi_d2 = (double*)take(z.d4);
@@ -767,6 +770,7 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     std::vector<unsigned char> qb;
     if (p->prec == HYB_FP64) put_quad<double>(p, &qb); else put_quad<float>(p, &qb);
     if (chk(cudaMemcpyAsync(p->sn_quadbuf, qb.data(), qb.size(), cudaMemcpyHostToDevice, st), "copy quad") != HYB_OK) return bail(HYB_ECUDA);
+    if (chk(sn_build_table(p), "cell-solve table") != HYB_OK) return bail(HYB_ECUDA);
     // static source CDF: cell weights Q A dt
     double* cw = p->cell_scratch + 256 + p->ny;
     double* scal = (double*)p->rem_f;   // two scalars of scratch before the first remap
@@ -862,18 +866,18 @@ static hyb_status sn_run(hyb_problem* p, int* iters, bool keep_status) {
     if (!keep_status) HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
     HYB_CU(p, sn_start(p));
     const int unchecked = (p->sn_warm && p->last_sn_iters > 0) ? std::min(p->last_sn_iters, p->d.sn_max_iter) : 0;
+    // one read-back brings the status word and the stop state together (the span from status to
+    // sn_iters); the loop only ends right after such a read, so no further read is needed
+    const size_t off = offsetof(DevState, status);
+    const size_t len = offsetof(DevState, sn_iters) + sizeof(int) - off;
     for (int it = 1; it <= p->d.sn_max_iter; ++it) {
         HYB_CU(p, sn_iteration(p, it == 1));
         if (it < unchecked) continue;
-        HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_conv, &p->st->sn_conv, 2 * sizeof(int), cudaMemcpyDeviceToHost,
+        HYB_CU(p, cudaMemcpyAsync((char*)p->st_host + off, (const char*)p->st + off, len, cudaMemcpyDeviceToHost,
                                   p->stream));
         HYB_CU(p, cudaStreamSynchronize(p->stream));
         if (p->st_host->sn_conv) break;
     }
-    HYB_CU(p, cudaMemcpyAsync(&p->st_host->status, &p->st->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
-    HYB_CU(p, cudaMemcpyAsync(&p->st_host->sn_conv, &p->st->sn_conv, 2 * sizeof(int), cudaMemcpyDeviceToHost,
-                              p->stream));
-    HYB_CU(p, cudaStreamSynchronize(p->stream));
     if (p->st_host->status & kStBounds) return fail(p, HYB_EBOUNDS, "device index check failed (bank cell out of range)");
     if (p->st_host->status & kStSegments)
         return fail(p, HYB_ETIMEOUT, keep_status ? "a device loop bound was exhausted (history segments or sweep wait)"

@@ -142,6 +142,7 @@ struct hyb_problem {
     void* sn_phi; void* sn_phi_old;   // collided flux, 4 Legendre coefficients per cell (T)
     void* sn_quad;            // sweep sources on the padded mesh: S_0..S_3 per cell, then sigma* A per cell (T)
     void* sn_psi;             // psi_m per ordinate and cell, mirrored coordinates (T)
+    void* sn_table;           // cell-solve table per ordinate class and padded cell (T), or null
     void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, then 4 signed weights per ordinate (T)
     double* sn_phi_d;         // collided flux, FP64 copy (4 x ncells)
     double* sn_phi_d2;        // the solution of the step before (extrapolated warm start only)
@@ -167,6 +168,8 @@ size_t sn_accel_state_bytes();                // device bytes of the Anderson st
 size_t sn_norm_bytes(int ncells);            // reduction scratch of the source iteration
 cudaError_t sn_clear_counters(hyb_problem* p);
 size_t sn_src_bytes(int nx, int ny, bool fp64);             // sweep sources on the padded mesh
+size_t sn_table_bytes(int nx, int ny, int nord, bool fp64);  // cell-solve table, 0 where none is kept
+cudaError_t sn_build_table(hyb_problem* p);
 cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView cdf, double* W_out_dev,
                              double* qmax_out_dev);
 cudaError_t launch_flux(hyb_problem* p);

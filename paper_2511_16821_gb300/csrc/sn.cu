@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "hyb_device.cuh"
 
@@ -48,7 +49,10 @@ struct SweepArgs {
     T dx, dy;
     const T* src;            // per padded cell the four source integrals S_i (un-mirrored)
     const T* sgA;            // per padded cell (sigma_t + 1/(c dt)) A
+    const T* k8;             // cell-solve table (or null): per class q and padded cell k1..k4, Ai, Bi, Di, i0
+    const T* i3;             //   and i3
     const T* qox; const T* qoy;    // ordinates by quadrant: m = quad * nq + q
+    size_t plane;            // cells per padded plane (rows of the table)
     T* psi;                  // per ordinate and cell, psi (4 Legendre coefficients, mirrored coordinates)
     int* status;             // device status word (bounded waits)
     const int* conv;         // converged flag: set -> the sweep returns at once
@@ -200,6 +204,62 @@ __device__ __forceinline__ CellSolve<T> cell_solve(T sA, T X, T Y) {
 }
 
 
+// The cell-solve table: the mirrored cell system depends only on the cell's (sigma_t + 1/(c dt)) A
+// and on |Omega_x|, |Omega_y|, which the four quadrants share, so per class q (the ordinates m with
+// m mod nq = q) and padded cell it holds the nine coefficients of the solve (k1..k4, Ai, Bi, Di, i0
+// in k8; i3). The cross sections are fixed for a problem's life, so it is built once; halo entries
+// are zero, and a solve with zero coefficients returns zero. The expressions are the step's own,
+// so the tabulated and the in-step solve agree bit for bit. Kept for FP64 only: there the step's
+// three correctly rounded divisions on the FP64 pipe cost more than the table's loads (measured:
+// the 6-iteration S8 solve on 112^2 cells 6.18 -> 2.94 ms), while FP32's approximate reciprocals
+// cost less than the extra loads and registers (0.318 -> 0.380 ms with the table).
+constexpr size_t kTableMaxBytes = size_t(32) << 20;   // kept only where it stays resident in L2
+constexpr int kTableMaxStrips = 8;                    // the table sweep runs at most 8 warps per CTA
+
+template <typename T>
+__global__ void sn_table_kernel(int ncells, int nq, CellSplit split, const T* sig, T area, T inv_cdt, const T* qox,
+                                const T* qoy, T dx, T dy, size_t plane, T* k8, T* i3) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)ncells * nq) return;
+    const int q = (int)(e / ncells), k = (int)(e - (long long)q * ncells);
+    int ix, iy;
+    split(k, &ix, &iy);
+    const size_t r = (size_t)q * plane + SweepPad<T>::at(split.nx, ix, iy);
+    const T sa = sig[2 * k], ss = sig[2 * k + 1];
+    const T sA = (sa + ss + inv_cdt) * area;
+    const T X = fabs(qox[q]) * dy * T(0.5), Y = fabs(qoy[q]) * dx * T(0.5);
+    const CellSolve<T> c = cell_solve<T>(sA, X, Y);
+    T* o = k8 + r * 8;
+    o[0] = c.k1; o[1] = c.k2; o[2] = c.k3; o[3] = c.k4;
+    o[4] = c.Ai; o[5] = c.Bi; o[6] = c.Di; o[7] = c.i0;
+    i3[r] = c.i3;
+}
+
+// Cell data of one wavefront step with the cell solve taken from the table.
+template <typename T> struct CellInT { T s0, s1, s2, s3; CellSolve<T> cs; };
+
+__device__ __forceinline__ void load_cell_tab(const float* s4, const float* k8, const float* i3, CellInT<float>& d) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(s4));
+    const float4 a = __ldg(reinterpret_cast<const float4*>(k8));
+    const float4 b = __ldg(reinterpret_cast<const float4*>(k8) + 1);
+    d.s0 = v.x; d.s1 = v.y; d.s2 = v.z; d.s3 = v.w;
+    d.cs.k1 = a.x; d.cs.k2 = a.y; d.cs.k3 = a.z; d.cs.k4 = a.w;
+    d.cs.Ai = b.x; d.cs.Bi = b.y; d.cs.Di = b.z; d.cs.i0 = b.w;
+    d.cs.i3 = __ldg(i3);
+}
+__device__ __forceinline__ void load_cell_tab(const double* s4, const double* k8, const double* i3, CellInT<double>& d) {
+    const double2 v0 = __ldg(reinterpret_cast<const double2*>(s4));
+    const double2 v1 = __ldg(reinterpret_cast<const double2*>(s4) + 1);
+    const double2 a0 = __ldg(reinterpret_cast<const double2*>(k8));
+    const double2 a1 = __ldg(reinterpret_cast<const double2*>(k8) + 1);
+    const double2 b0 = __ldg(reinterpret_cast<const double2*>(k8) + 2);
+    const double2 b1 = __ldg(reinterpret_cast<const double2*>(k8) + 3);
+    d.s0 = v0.x; d.s1 = v0.y; d.s2 = v1.x; d.s3 = v1.y;
+    d.cs.k1 = a0.x; d.cs.k2 = a0.y; d.cs.k3 = a1.x; d.cs.k4 = a1.y;
+    d.cs.Ai = b0.x; d.cs.Bi = b0.y; d.cs.Di = b1.x; d.cs.i0 = b1.y;
+    d.cs.i3 = __ldg(i3);
+}
+
 // Pipelined strip sweep of one ordinate, W warps, in coordinates mirrored to +x, +y (SX: the x
 // direction of the ordinate before mirroring; the y mirror only changes a strip's first row). Warp w
 // sweeps strips w, w+W, ... (lane = row, one anti-diagonal per step). The trace leaving the top row
@@ -210,8 +270,9 @@ __device__ __forceinline__ CellSolve<T> cell_solve(T sA, T X, T Y) {
 // bounded and records kStSegments on exhaustion. Dependencies only point to lower strips, and all
 // warps of the CTA are resident, so the pipeline always advances. Between the waits a block of PF
 // steps is straight-line code: addresses are the lane's base plus compile-time offsets on the padded
-// mesh, the store into the ring is predicated, and nothing is tested per step.
-template <typename T, int SX>
+// mesh, the stores are predicated, and nothing is tested per step. TAB: the cell solve comes from the
+// precomputed table instead of being formed in the step.
+template <typename T, int SX, bool TAB>
 __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int sy, volatile int* cons,
                                                volatile unsigned long long* ring, uint32_t ring_sa,
                                                bool& timed_out) {
@@ -234,6 +295,9 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
         const long long base = (long long)SweepPad<T>::at(nx, SX > 0 ? 0 : nx - 1, iy) - (long long)SX * lane;
         const T* src = a.src + base * 4;
         const T* sga = a.sgA + base;
+        const size_t toff = TAB ? (size_t)(m % a.nq) * a.plane : 0;   // table rows of this ordinate's class
+        const T* tk8 = TAB ? a.k8 + (toff + base) * 8 : nullptr;
+        const T* ti3 = TAB ? a.i3 + toff + base : nullptr;
         // psi of this lane's cell at step t: po + 4 SX t (formed only where the lane holds a cell)
         T* po = out + ((long long)iy * nx + (SX > 0 ? 0 : nx - 1) - (long long)SX * lane) * 4;
         const unsigned nxl = ly < ny ? (unsigned)nx : 0u;   // columns this lane stores
@@ -245,9 +309,12 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
         volatile unsigned long long* rin = ring + (size_t)bin * re * RW;
         const uint32_t rout = ring_sa + (uint32_t)((size_t)bout * re * RW * 8);
         T bx0 = 0, bx1 = 0, oy0 = 0, oy1 = 0;
-        CellIn<T> q[PF];
+        typename std::conditional<TAB, CellInT<T>, CellIn<T>>::type q[PF];
 #pragma unroll
-        for (int i = 0; i < PF; ++i) load_cell(src + SX * i * 4, sga + SX * i, q[i]);
+        for (int i = 0; i < PF; ++i) {
+            if constexpr (TAB) load_cell_tab(src + SX * i * 4, tk8 + SX * i * 8, ti3 + SX * i, q[i]);
+            else load_cell(src + SX * i * 4, sga + SX * i, q[i]);
+        }
         for (int t0 = 0; t0 < nsteps; t0 += PF) {
             // a reused slot: the previous reader must have taken the columns this block writes
             if (reuse && has_out && s >= W) {
@@ -281,6 +348,8 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
             }
             const T* sb = src + (long long)SX * (t0 + PF) * 4;
             const T* ab = sga + (long long)SX * (t0 + PF);
+            const T* kb = TAB ? tk8 + (long long)SX * (t0 + PF) * 8 : nullptr;
+            const T* jb = TAB ? ti3 + (long long)SX * (t0 + PF) : nullptr;
             T* pb = po + (long long)SX * t0 * 4;
             const uint32_t wb = rout + (uint32_t)(t0 * RW * 8);
             const uint32_t tagb = (uint32_t)(qout + t0 - 30);
@@ -290,7 +359,9 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
                 const T u1 = __shfl_up_sync(0xffffffffu, oy1, 1);
                 const T by0 = lane == 0 ? rv0[i] : u0;
                 const T by1 = lane == 0 ? rv1[i] : u1;
-                const CellSolve<T> cs = cell_solve<T>(q[i].sA, X, Y);
+                CellSolve<T> cs;
+                if constexpr (TAB) cs = q[i].cs;
+                else cs = cell_solve<T>(q[i].sA, X, Y);
                 const T b0 = q[i].s0 + twoX * bx0 + twoY * by0;
                 const T b1 = sxf * q[i].s1 - twoX * bx0 + tY * by1;
                 const T b2 = syf * q[i].s2 + tX * bx1 - twoY * by0;
@@ -305,7 +376,8 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
                 oy0 = a0 + a2; oy1 = a1 + a3;
                 store_cell_if((unsigned)(t0 + i - lane) < nxl, pb + SX * i * 4, a0, a1, a2, a3);
                 Ring<T>::put_if(put, wb + (uint32_t)(i * RW * 8), oy0, oy1, tagb + (uint32_t)i);
-                load_cell(sb + SX * i * 4, ab + SX * i, q[i]);
+                if constexpr (TAB) load_cell_tab(sb + SX * i * 4, kb + SX * i * 8, jb + SX * i, q[i]);
+                else load_cell(sb + SX * i * 4, ab + SX * i, q[i]);
             }
             // publish the columns this warp has taken from its input slot (only needed on reuse)
             if (reuse && has_in && lane == 0) {
@@ -317,8 +389,8 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
+template <typename T, bool TAB>
+__global__ void __launch_bounds__(TAB ? 256 : 512) sweep_pipe_kernel(SweepArgs<T> a) {
     constexpr int RW = Ring<T>::kWords;
     if (*(volatile const int*)a.conv) return;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -334,8 +406,8 @@ __global__ void __launch_bounds__(512) sweep_pipe_kernel(SweepArgs<T> a) {
     const int sy = (quad <= 1) ? 1 : -1;
     const uint32_t ring_sa = (uint32_t)__cvta_generic_to_shared(smraw + ring_off);
     bool timed_out = false;
-    if (quad == 0 || quad == 3) sweep_ordinate<T, 1>(a, m, sy, cons, ring, ring_sa, timed_out);
-    else sweep_ordinate<T, -1>(a, m, sy, cons, ring, ring_sa, timed_out);
+    if (quad == 0 || quad == 3) sweep_ordinate<T, 1, TAB>(a, m, sy, cons, ring, ring_sa, timed_out);
+    else sweep_ordinate<T, -1, TAB>(a, m, sy, cons, ring, ring_sa, timed_out);
     if (timed_out && (threadIdx.x & 31) == 0) atomicOr(a.status, kStSegments);
 }
 
@@ -807,13 +879,18 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     a.psi = (T*)p->sn_psi;
     a.status = &p->st->status;
     a.conv = &p->st->sn_conv;
+    a.plane = plane;
     size_t smem = 0;
     a.W = sweep_warps<T>(p, &smem);
+    const bool tab = p->sn_table != nullptr && a.W <= kTableMaxStrips;
+    a.k8 = tab ? (const T*)p->sn_table : nullptr;
+    a.i3 = tab ? a.k8 + (size_t)a.nq * plane * 8 : nullptr;
+    auto kern = tab ? sweep_pipe_kernel<T, true> : sweep_pipe_kernel<T, false>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_pipe_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sweep_pipe_kernel<T><<<p->n_ord, 32 * a.W, smem, s>>>(a);
+    kern<<<p->n_ord, 32 * a.W, smem, s>>>(a);
     const int gr = (p->ncells + kRedCells - 1) / kRedCells;
     const RedScratch rs = red_scratch(p);
     if (p->d.sn_accel > 0) {
@@ -835,6 +912,34 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
                                                               (const T*)p->sig, p->mom_d, (T)p->area, inv4pidt, src,
                                                               p->st, sn_tol_eff(p));
     return cudaGetLastError();
+}
+
+size_t sn_table_bytes(int nx, int ny, int nord, bool fp64) {
+    if (!fp64 || (ny + 31) / 32 > kTableMaxStrips) return 0;
+    const size_t b = fp64 ? (size_t)(nord / 4) * SweepPad<double>::plane(nx, ny) * 9 * sizeof(double)
+                          : (size_t)(nord / 4) * SweepPad<float>::plane(nx, ny) * 9 * sizeof(float);
+    return b <= kTableMaxBytes ? b : 0;
+}
+
+template <typename T>
+static cudaError_t sn_build_table_t(hyb_problem* p) {
+    const size_t plane = SweepPad<T>::plane(p->nx, p->ny);
+    const int nq = p->n_ord / 4;
+    T* k8 = (T*)p->sn_table;
+    T* i3 = k8 + (size_t)nq * plane * 8;
+    cudaError_t e = cudaMemsetAsync(p->sn_table, 0, (size_t)nq * plane * 9 * sizeof(T), p->stream);
+    if (e != cudaSuccess) return e;
+    const T* qbuf = (const T*)p->sn_quadbuf;
+    const long long n = (long long)p->ncells * nq;
+    sn_table_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(
+        p->ncells, nq, make_cell_split(p->nx), (const T*)p->sig, (T)p->area, (T)(1.0 / (p->d.c * p->d.dt)), qbuf,
+        qbuf + kMaxOrd, (T)p->dx, (T)p->dy, plane, k8, i3);
+    return cudaGetLastError();
+}
+
+cudaError_t sn_build_table(hyb_problem* p) {
+    if (!p->sn_table) return cudaSuccess;
+    return p->prec == HYB_FP64 ? sn_build_table_t<double>(p) : sn_build_table_t<float>(p);
 }
 
 size_t sn_accel_state_bytes() { return sizeof(AAState); }
