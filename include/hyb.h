@@ -123,6 +123,11 @@ typedef struct {
                                  is below n_s_cell[k], post-limit otherwise; n_s (finite) is the
                                  largest limit and fixes the point dimensions. Host pointer,
                                  copied at creation */
+    int32_t sn_layout;        /* memory layout of the collided solve's sweep (no counterpart in the
+                                 paper; results are the same): 0 automatic (the padded mesh while
+                                 the per-ordinate solutions fit in 48 MB, else the wavefront
+                                 order), 1 padded mesh, 2 wavefront order */
+    int32_t pad2;
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */

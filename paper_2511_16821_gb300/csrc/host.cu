@@ -319,9 +319,9 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.d1 = nc * 8;
     z.d4 = 4 * nc * 8;
     z.sn4 = 4 * nc * T;
-    z.sn16 = hyb::sn_src_bytes(d->nx, d->ny, d->precision == HYB_FP64);          // sweep sources (padded mesh)
-    z.sntx = (size_t)nord * nc * 4 * T;           // psi per ordinate and cell
-    z.sntab = hyb::sn_table_bytes(d->nx, d->ny, nord, d->precision == HYB_FP64);   // cell-solve table or 0
+    z.sn16 = hyb::sn_src_bytes(d->nx, d->ny, nord, d->precision == HYB_FP64, d->sn_layout);    // sweep sources
+    z.sntx = hyb::sn_psi_bytes(d->nx, d->ny, nord, d->precision == HYB_FP64, d->sn_layout);    // psi per ordinate
+    z.sntab = hyb::sn_table_bytes(d->nx, d->ny, nord, d->precision == HYB_FP64, d->sn_layout);   // cell-solve table or 0
     z.snqb = 7 * kMaxOrd * T;                     // ox, oy, w, then 4 signed weights per ordinate
     z.snnorm = hyb::sn_norm_bytes((int)nc);       // reduction partials per block and group, group counters
     z.nblk = (z.slots + 2047) / 2048;
@@ -454,6 +454,7 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->sn_accel < 0 || d->sn_accel > 8) { *why = "sn_accel must be in [0, 8]"; return HYB_EINVAL; }
     if (d->sn_warm_start < 0 || d->sn_warm_start > 2) { *why = "sn_warm_start must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->remap_variant != 0 && d->remap_variant != 1) { *why = "remap_variant must be 0 or 1"; return HYB_EINVAL; }
+    if (d->sn_layout < 0 || d->sn_layout > 2) { *why = "sn_layout must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->remap_variant == 1 && d->n_s == HYB_NS_INF) {
         *why = "remap_variant 1 needs a finite N_s (N_s = infinity has no remap)";
         return HYB_EINVAL;
@@ -761,8 +762,8 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     if (chk(cudaMemsetAsync(p->sn_phi_d, 0, 4 * nc * 8, st), "memset phi") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemsetAsync(p->sn_phi_d2, 0, 4 * nc * 8, st), "memset phi") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(sn_clear_counters(p), "memset reduction counters") != HYB_OK) return bail(HYB_ECUDA);
-    // the halo of the sweep sources stays zero (only interior cells are ever written)
-    if (chk(cudaMemsetAsync(p->sn_quad, 0, sn_src_bytes(d->nx, d->ny, p->prec == HYB_FP64), st), "memset sweep sources") != HYB_OK)
+    // sweep-source entries that hold no cell stay zero (only cells are ever written)
+    if (chk(cudaMemsetAsync(p->sn_quad, 0, sn_src_bytes(d->nx, d->ny, d->sn_order == 8 ? 40 : 12, p->prec == HYB_FP64, d->sn_layout), st), "memset sweep sources") != HYB_OK)
         return bail(HYB_ECUDA);
     // quadrature
     p->n_ord = 0;

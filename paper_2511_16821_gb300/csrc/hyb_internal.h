@@ -140,8 +140,9 @@ struct hyb_problem {
     double *pre_raw, *post_raw;                     // raw track-length sums (FP64)
     double sig_s_max;         // max sigma_s (bound of the hand-off moments)
     void* sn_phi; void* sn_phi_old;   // collided flux, 4 Legendre coefficients per cell (T)
-    void* sn_quad;            // sweep sources on the padded mesh: S_0..S_3 per cell, then sigma* A per cell (T)
-    void* sn_psi;             // psi_m per ordinate and cell, mirrored coordinates (T)
+    void* sn_quad;            // sweep sources: S_0..S_3 per entry, then sigma* A per entry (T); entries: the padded
+                              //   mesh, or per direction the wavefront order (solves too large for L2)
+    void* sn_psi;             // psi_m per ordinate, mirrored coordinates (T): plain mesh or wavefront order
     void* sn_table;           // cell-solve table per ordinate class and padded cell (T), or null
     void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, then 4 signed weights per ordinate (T)
     double* sn_phi_d;         // collided flux, FP64 copy (4 x ncells)
@@ -167,8 +168,11 @@ cudaError_t launch_census(hyb_problem* p);   // N_s = infinity: MC-leg census ->
 size_t sn_accel_state_bytes();                // device bytes of the Anderson state
 size_t sn_norm_bytes(int ncells);            // reduction scratch of the source iteration
 cudaError_t sn_clear_counters(hyb_problem* p);
-size_t sn_src_bytes(int nx, int ny, bool fp64);             // sweep sources on the padded mesh
-size_t sn_table_bytes(int nx, int ny, int nord, bool fp64);  // cell-solve table, 0 where none is kept
+// the collided solve's memory (layout: the desc's sn_layout)
+size_t sn_src_bytes(int nx, int ny, int nord, bool fp64, int layout);   // sweep sources
+size_t sn_psi_bytes(int nx, int ny, int nord, bool fp64, int layout);   // per-ordinate solutions
+bool sn_wave_layout(int nx, int ny, int nord, bool fp64, int layout);   // the wavefront order is kept
+size_t sn_table_bytes(int nx, int ny, int nord, bool fp64, int layout);  // cell-solve table, 0 if none
 cudaError_t sn_build_table(hyb_problem* p);
 cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView cdf, double* W_out_dev,
                              double* qmax_out_dev);

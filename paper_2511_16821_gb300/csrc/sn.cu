@@ -11,7 +11,8 @@
 // anti-diagonal per step); the trace entering a row from below comes from the neighbouring lane by
 // shuffle (from the strip below through a shared-memory ring), the trace from the left stays in
 // registers, so a step needs no block barrier. Sources and solutions live on a mesh padded with
-// halo columns and an extra row, so a step also needs no bound test. Strips are pipelined across the warps, so the
+// halo columns and an extra row (or, for solves too large for L2, in the sweep's own wavefront
+// order), so a step also needs no bound test. Strips are pipelined across the warps, so the
 // critical path is about (nx + 31) + 32 (ceil(ny/32) - 1) cell solves per sweep. Coordinates are mirrored per quadrant so that every
 // sweep runs towards +x,+y; in mirrored coordinates the 4x4 cell system is the same for every
 // quadrant and is diagonally dominant, so it is solved by elimination without pivoting. The
@@ -43,17 +44,62 @@ template <typename T> struct SweepPad {
     static __host__ __device__ size_t at(int nx, int ix, int iy) { return (size_t)iy * nxp(nx) + kHalo + ix; }
 };
 
+// Mirror signs of quadrant Q (ordinates m = Q nq + q): the sweep of every quadrant runs towards
+// +x, +y in coordinates mirrored by (sx, sy).
+__host__ __device__ __forceinline__ int quad_sx(int Q) { return (Q == 0 || Q == 3) ? 1 : -1; }
+__host__ __device__ __forceinline__ int quad_sy(int Q) { return Q <= 1 ? 1 : -1; }
+
+// The other memory layout of the sweep, for problems whose solve does not stay in L2: the wavefront
+// order of each direction. Entry (s, t, l) -- strip s, step t, lane l -- holds the cell of mirrored
+// row 32 s + l and mirrored column t - l, so the 32 lanes of a step read or write 32 consecutive
+// entries (one coalesced access to DRAM) and a lane's next step is 32 entries on; the scatter
+// between mesh order and this order is done by the fully parallel kernels that write the sources
+// and read the solutions. Entries that hold no cell are zero in the source arrays and take the junk
+// stores of psi, so a step tests no bound (zero data and zero inflow give zero traces, as on the
+// padded mesh). nt covers the last block of steps and the loads PF steps ahead of it. On the padded
+// mesh a lane walks its own row, so the lines of consecutive steps are reused from L1; in wavefront
+// order every step takes new lines, which costs more than the coalescing saves while the data sit in
+// L2 (measured on 112^2 cells, S8: sweep 37 -> 43 us) and saves a fifth of the solve once they do
+// not (1024^2 cells: 1.44 -> 1.14 ms per source iteration).
+template <typename T> struct Wave {
+    int nx, ny, nstrip, nt;
+    __host__ __device__ static Wave make(int nx, int ny) {
+        constexpr int PF = SweepDepth<T>::value;
+        Wave w;
+        w.nx = nx; w.ny = ny;
+        w.nstrip = (ny + 31) / 32;
+        w.nt = (nx + 31 + PF - 1) / PF * PF + PF;
+        return w;
+    }
+    __host__ __device__ size_t size() const { return (size_t)nstrip * nt * 32; }
+    // entry of mesh cell (ix, iy) in the direction mirrored by (sx, sy)
+    __host__ __device__ size_t at(int ix, int iy, int sx, int sy) const {
+        const int ly = sy > 0 ? iy : ny - 1 - iy, c = sx > 0 ? ix : nx - 1 - ix;
+        const int l = ly & 31;
+        return ((size_t)(ly >> 5) * nt + c + l) * 32 + l;
+    }
+};
+
+// the wavefront layout is taken when the per-ordinate solutions of the plain mesh exceed this
+constexpr size_t kWaveMinPsiBytes = size_t(48) << 20;
+
+bool sn_wave_layout(int nx, int ny, int nord, bool fp64, int layout) {
+    if (layout != 0) return layout == 2;
+    return (size_t)nord * nx * ny * 4 * (fp64 ? 8 : 4) > kWaveMinPsiBytes;
+}
+
 template <typename T>
 struct SweepArgs {
     int nx, ny, nq, nord, W, re;   // re: ring entries per slot
     T dx, dy;
-    const T* src;            // per padded cell the four source integrals S_i (un-mirrored)
-    const T* sgA;            // per padded cell (sigma_t + 1/(c dt)) A
+    const T* src;            // the four source integrals S_i (un-mirrored): padded mesh, or per direction in
+    const T* sgA;            //   wavefront order; (sigma_t + 1/(c dt)) A, the same way
+    Wave<T> wv;              // the wavefront layout (used by the wavefront sweep)
     const T* k8;             // cell-solve table (or null): per class q and padded cell k1..k4, Ai, Bi, Di, i0
     const T* i3;             //   and i3
     const T* qox; const T* qoy;    // ordinates by quadrant: m = quad * nq + q
     size_t plane;            // cells per padded plane (rows of the table)
-    T* psi;                  // per ordinate and cell, psi (4 Legendre coefficients, mirrored coordinates)
+    T* psi;                  // per ordinate, psi (4 Legendre coefficients, mirrored): plain mesh or wavefront
     int* status;             // device status word (bounded waits)
     const int* conv;         // converged flag: set -> the sweep returns at once
 };
@@ -68,17 +114,42 @@ __device__ __forceinline__ void source4(T ss, T area, const T* po, const double*
     S[3] = cs * po[3] * T(1.0 / 9.0) + (T)mm[3] * inv_4pi_dt;
 }
 
+// the sweep entries of cell (ix, iy): one on the padded mesh, one per direction in wavefront order
 template <typename T>
-__global__ void sn_source_kernel(int ncells, CellSplit split, const T* sig, const T* phi_old, const double* mom, T area,
-                                 T inv_4pi_dt, T inv_cdt, T* src, T* sgA) {
+__device__ __forceinline__ int sweep_entries(bool wave, const Wave<T>& wv, int nx, int ix, int iy, size_t* e) {
+    if (!wave) { e[0] = SweepPad<T>::at(nx, ix, iy); return 1; }
+    const size_t wsz = wv.size();
+#pragma unroll
+    for (int Q = 0; Q < 4; ++Q) e[Q] = (size_t)Q * wsz + wv.at(ix, iy, quad_sx(Q), quad_sy(Q));
+    return 4;
+}
+
+template <typename T>
+__global__ void sn_source_kernel(int ncells, CellSplit split, int wave, Wave<T> wv, const T* sig, const T* phi_old,
+                                 const double* mom, T area, T inv_4pi_dt, T inv_cdt, T* src, T* sgA) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ncells) return;
     int ix, iy;
     split(k, &ix, &iy);
-    const size_t pk = SweepPad<T>::at(split.nx, ix, iy);
     const T sa = sig[2 * k], ss = sig[2 * k + 1];
-    source4<T>(ss, area, phi_old + 4 * (size_t)k, mom + 4 * (size_t)k, inv_4pi_dt, src + 4 * pk);
-    sgA[pk] = (sa + ss + inv_cdt) * area;
+    T S[4];
+    source4<T>(ss, area, phi_old + 4 * (size_t)k, mom + 4 * (size_t)k, inv_4pi_dt, S);
+    const T g = (sa + ss + inv_cdt) * area;
+    size_t e[4];
+    const int n = sweep_entries<T>(wave != 0, wv, split.nx, ix, iy, e);
+    for (int j = 0; j < n; ++j) {
+        T* d = src + 4 * e[j];
+        d[0] = S[0]; d[1] = S[1]; d[2] = S[2]; d[3] = S[3];
+        sgA[e[j]] = g;
+    }
+}
+
+// source integral i of cell (ix, iy) into the sweep's entries
+template <typename T>
+__device__ __forceinline__ void put_source(T* src, bool wave, const Wave<T>& wv, int nx, int ix, int iy, int i, T v) {
+    size_t e[4];
+    const int n = sweep_entries<T>(wave, wv, nx, ix, iy, e);
+    for (int j = 0; j < n; ++j) src[4 * e[j] + i] = v;
 }
 
 // Cell data of one wavefront step: the four source integrals (un-mirrored) and (sigma_t + 1/(c dt)) A.
@@ -96,6 +167,14 @@ __device__ __forceinline__ void load_cell(const double* s4, const double* sa, Ce
     const double2 v1 = __ldg(reinterpret_cast<const double2*>(s4) + 1);
     d.s0 = v0.x; d.s1 = v0.y; d.s2 = v1.x; d.s3 = v1.y;
     d.sA = __ldg(sa);
+}
+
+__device__ __forceinline__ void store_cell(float* d, float a0, float a1, float a2, float a3) {
+    *reinterpret_cast<float4*>(d) = make_float4(a0, a1, a2, a3);
+}
+__device__ __forceinline__ void store_cell(double* d, double a0, double a1, double a2, double a3) {
+    reinterpret_cast<double2*>(d)[0] = make_double2(a0, a1);
+    reinterpret_cast<double2*>(d)[1] = make_double2(a2, a3);
 }
 
 // a predicated store of one cell's four coefficients (no branch in the step; an address formed for a
@@ -271,8 +350,10 @@ __device__ __forceinline__ void load_cell_tab(const double* s4, const double* k8
 // warps of the CTA are resident, so the pipeline always advances. Between the waits a block of PF
 // steps is straight-line code: addresses are the lane's base plus compile-time offsets on the padded
 // mesh, the stores are predicated, and nothing is tested per step. TAB: the cell solve comes from the
-// precomputed table instead of being formed in the step.
-template <typename T, int SX, bool TAB>
+// precomputed table instead of being formed in the step. WAVE: sources and psi in the wavefront order
+// of the ordinate's direction (a step's accesses are coalesced runs, psi is stored unpredicated into
+// entries that hold no cell).
+template <typename T, int SX, bool TAB, bool WAVE>
 __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int sy, volatile int* cons,
                                                volatile unsigned long long* ring, uint32_t ring_sa,
                                                bool& timed_out) {
@@ -284,23 +365,31 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
     const T syf = (T)sy, sxy = (T)(SX * sy), sxf = (T)SX;
     const T X = fabs(a.qox[m]) * a.dy * T(0.5), Y = fabs(a.qoy[m]) * a.dx * T(0.5);
     const T twoX = T(2) * X, twoY = T(2) * Y, tX = T(2.0 / 3.0) * X, tY = T(2.0 / 3.0) * Y;
-    T* out = a.psi + (size_t)m * nx * ny * 4;
+    // per-step strides (in T) of a lane's source, sigma* A and psi pointers
+    constexpr long long SS = WAVE ? 128 : SX * 4, AS = WAVE ? 32 : SX, PS = WAVE ? 128 : SX * 4;
+    const size_t wsz = a.wv.size();
+    const int Q = m / a.nq;
+    T* out = a.psi + (size_t)m * (WAVE ? wsz : (size_t)nx * ny) * 4;
     const int nstrip = (ny + 31) / 32;
     const bool reuse = nstrip > W;
     const int nsteps = nx + 31;
     for (int s = warp; s < nstrip && !timed_out; s += W) {
         const int ly = 32 * s + lane;
         const int iy = ly < ny ? (sy > 0 ? ly : ny - 1 - ly) : ny;   // rows past the mesh: the extra row
-        // padded index of this lane's cell at step t is base + SX t (column t - lane in mirrored x)
+        // padded mesh: this lane's cell at step t is base + SX t (column t - lane in mirrored x);
+        // wavefront order: entry e0 + 32 t of the direction's arrays
         const long long base = (long long)SweepPad<T>::at(nx, SX > 0 ? 0 : nx - 1, iy) - (long long)SX * lane;
-        const T* src = a.src + base * 4;
-        const T* sga = a.sgA + base;
+        const size_t e0 = (size_t)Q * wsz + (size_t)s * a.wv.nt * 32 + lane;
+        const T* src = WAVE ? a.src + e0 * 4 : a.src + base * 4;
+        const T* sga = WAVE ? a.sgA + e0 : a.sgA + base;
         const size_t toff = TAB ? (size_t)(m % a.nq) * a.plane : 0;   // table rows of this ordinate's class
         const T* tk8 = TAB ? a.k8 + (toff + base) * 8 : nullptr;
         const T* ti3 = TAB ? a.i3 + toff + base : nullptr;
-        // psi of this lane's cell at step t: po + 4 SX t (formed only where the lane holds a cell)
-        T* po = out + ((long long)iy * nx + (SX > 0 ? 0 : nx - 1) - (long long)SX * lane) * 4;
-        const unsigned nxl = ly < ny ? (unsigned)nx : 0u;   // columns this lane stores
+        // psi of this lane's cell at step t: po + PS t (on the plain mesh formed only where the lane
+        // holds a cell)
+        T* po = WAVE ? out + (e0 - (size_t)Q * wsz) * 4
+                     : out + ((long long)iy * nx + (SX > 0 ? 0 : nx - 1) - (long long)SX * lane) * 4;
+        const unsigned nxl = ly < ny ? (unsigned)nx : 0u;   // columns this lane stores (plain mesh)
         const int bin = (s - 1 + W) % W, bout = s % W;
         const int qin = ((s - 1) / W) * nx, qout = (s / W) * nx;   // sequence bases of the ring slots
         const bool has_in = s > 0, has_out = s + 1 < nstrip;
@@ -313,7 +402,7 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
 #pragma unroll
         for (int i = 0; i < PF; ++i) {
             if constexpr (TAB) load_cell_tab(src + SX * i * 4, tk8 + SX * i * 8, ti3 + SX * i, q[i]);
-            else load_cell(src + SX * i * 4, sga + SX * i, q[i]);
+            else load_cell(src + SS * i, sga + AS * i, q[i]);
         }
         for (int t0 = 0; t0 < nsteps; t0 += PF) {
             // a reused slot: the previous reader must have taken the columns this block writes
@@ -346,11 +435,11 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
                     __nanosleep(20);
                 }
             }
-            const T* sb = src + (long long)SX * (t0 + PF) * 4;
-            const T* ab = sga + (long long)SX * (t0 + PF);
+            const T* sb = src + SS * (t0 + PF);
+            const T* ab = sga + AS * (t0 + PF);
             const T* kb = TAB ? tk8 + (long long)SX * (t0 + PF) * 8 : nullptr;
             const T* jb = TAB ? ti3 + (long long)SX * (t0 + PF) : nullptr;
-            T* pb = po + (long long)SX * t0 * 4;
+            T* pb = po + PS * t0;
             const uint32_t wb = rout + (uint32_t)(t0 * RW * 8);
             const uint32_t tagb = (uint32_t)(qout + t0 - 30);
 #pragma unroll
@@ -374,10 +463,11 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
                 const T a3 = cs.i3 * b3 + cs.k2 * a1 + cs.k4 * a2;   // (b3 + tY a1 + tX a2) / d3
                 bx0 = a0 + a1; bx1 = a2 + a3;
                 oy0 = a0 + a2; oy1 = a1 + a3;
-                store_cell_if((unsigned)(t0 + i - lane) < nxl, pb + SX * i * 4, a0, a1, a2, a3);
+                if constexpr (WAVE) store_cell(pb + PS * i, a0, a1, a2, a3);
+                else store_cell_if((unsigned)(t0 + i - lane) < nxl, pb + PS * i, a0, a1, a2, a3);
                 Ring<T>::put_if(put, wb + (uint32_t)(i * RW * 8), oy0, oy1, tagb + (uint32_t)i);
                 if constexpr (TAB) load_cell_tab(sb + SX * i * 4, kb + SX * i * 8, jb + SX * i, q[i]);
-                else load_cell(sb + SX * i * 4, ab + SX * i, q[i]);
+                else load_cell(sb + SS * i, ab + AS * i, q[i]);
             }
             // publish the columns this warp has taken from its input slot (only needed on reuse)
             if (reuse && has_in && lane == 0) {
@@ -389,8 +479,9 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
     }
 }
 
-template <typename T, bool TAB>
+template <typename T, bool TAB, bool WAVE>
 __global__ void __launch_bounds__(TAB ? 256 : 512) sweep_pipe_kernel(SweepArgs<T> a) {
+    static_assert(!(TAB && WAVE), "the cell-solve table is kept on the padded mesh only");
     constexpr int RW = Ring<T>::kWords;
     if (*(volatile const int*)a.conv) return;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -406,8 +497,8 @@ __global__ void __launch_bounds__(TAB ? 256 : 512) sweep_pipe_kernel(SweepArgs<T
     const int sy = (quad <= 1) ? 1 : -1;
     const uint32_t ring_sa = (uint32_t)__cvta_generic_to_shared(smraw + ring_off);
     bool timed_out = false;
-    if (quad == 0 || quad == 3) sweep_ordinate<T, 1, TAB>(a, m, sy, cons, ring, ring_sa, timed_out);
-    else sweep_ordinate<T, -1, TAB>(a, m, sy, cons, ring, ring_sa, timed_out);
+    if (quad == 0 || quad == 3) sweep_ordinate<T, 1, TAB, WAVE>(a, m, sy, cons, ring, ring_sa, timed_out);
+    else sweep_ordinate<T, -1, TAB, WAVE>(a, m, sy, cons, ring, ring_sa, timed_out);
     if (timed_out && (threadIdx.x & 31) == 0) atomicOr(a.status, kStSegments);
 }
 
@@ -517,21 +608,33 @@ template <> struct Vec4<double> {
     }
 };
 
-// The ordinate sum of one cell over ordinates g, g + kRedGroups, ...: psi_m (mirrored coefficients)
-// times the signed weights (w_m, w_m s_x, w_m s_y, w_m s_x s_y) that undo the mirror, in ordinate
-// order.
+// The ordinate sum of one cell over ordinates g, g + kRedGroups, ...: psi_m (mirrored coefficients;
+// plain mesh, or the cell's entry in the wavefront order of m's quadrant) times the signed weights
+// (w_m, w_m s_x, w_m s_y, w_m s_x s_y) that undo the mirror, in ordinate order.
 template <typename T>
-__device__ __forceinline__ void weighted_psi_sum(const T* psi, int nord, const T* qwv, int k, int ncells, int g,
-                                                 T* out) {
+__device__ __forceinline__ void weighted_psi_sum(const T* psi, int nord, int nq, bool wave, const Wave<T>& wv,
+                                                 CellSplit split, const T* qwv, int k, int ncells, int g, T* out) {
     constexpr int kPer = (kMaxOrd + kRedGroups - 1) / kRedGroups;   // ordinates per thread, at most
     T acc[4] = {0, 0, 0, 0};
     if (k < ncells) {
+        size_t e[4] = {(size_t)k, (size_t)k, (size_t)k, (size_t)k};   // per quadrant: entry of the cell
+        size_t plane = (size_t)ncells;
+        if (wave) {
+            int ix, iy;
+            split(k, &ix, &iy);
+#pragma unroll
+            for (int Q = 0; Q < 4; ++Q) e[Q] = wv.at(ix, iy, quad_sx(Q), quad_sy(Q));
+            plane = wv.size();
+        }
         // all loads first (in flight together), then the sum in ordinate order
         T v[kPer][4];
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
             const int m = g + j * kRedGroups;
-            if (m < nord) Vec4<T>::load(psi + ((size_t)m * ncells + k) * 4, v[j]);
+            if (m < nord) {
+                const int Q = (m >= nq) + (m >= 2 * nq) + (m >= 3 * nq);
+                Vec4<T>::load(psi + ((size_t)m * plane + e[Q]) * 4, v[j]);
+            }
         }
 #pragma unroll
         for (int j = 0; j < kPer; ++j) {
@@ -548,7 +651,8 @@ __device__ __forceinline__ void weighted_psi_sum(const T* psi, int nord, const T
 
 template <typename T>
 __global__ void __launch_bounds__(kRedCells * kRedGroups)
-sn_reduce_kernel(const T* psi, int nord, const T* qwv, CellSplit split, const T* phi_old, T* phi_new,
+sn_reduce_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, const T* qwv, CellSplit split, const T* phi_old,
+                 T* phi_new,
                  int ncells, RedScratch rs, const T* sig, const double* mom, T area, T inv_4pi_dt, T* src, DevState* st,
                  double tol) {
     __shared__ T sp[kRedGroups][kRedCells][4];
@@ -564,7 +668,7 @@ sn_reduce_kernel(const T* psi, int nord, const T* qwv, CellSplit split, const T*
         }
         return;
     }
-    weighted_psi_sum<T>(psi, nord, qwv, k0 + c, ncells, g, sp[g][c]);
+    weighted_psi_sum<T>(psi, nord, nq, wave != 0, wv, split, qwv, k0 + c, ncells, g, sp[g][c]);
     __syncthreads();
     if (threadIdx.x < kRedCells * 4) {
         const int cc = threadIdx.x >> 2, i = threadIdx.x & 3;
@@ -585,7 +689,7 @@ sn_reduce_kernel(const T* psi, int nord, const T* qwv, CellSplit split, const T*
             const T cs = sig[2 * (size_t)k + 1] * area * T(0.07957747154594767);
             int ix, iy;
             split(k, &ix, &iy);
-            src[SweepPad<T>::at(split.nx, ix, iy) * 4 + i] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
+            put_source<T>(src, wave != 0, wv, split.nx, ix, iy, i, cs * v * n_i + (T)mom[e] * inv_4pi_dt);
         }
         // warp sums (fixed tree), then block sum in warp order
         for (int o = 16; o > 0; o >>= 1) {
@@ -672,7 +776,7 @@ __device__ void aa_solve(AAState* aa, const int* slots, int n) {
 // completes the Gram matrix, applies the stop test and, if the solve goes on, forms the weights.
 template <typename T>
 __global__ void __launch_bounds__(kRedCells * kRedGroups)
-sn_reduce_aa_kernel(const T* psi, int nord, const T* qwv, const T* phi_old, T* phi_new,
+sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSplit split, const T* qwv, const T* phi_old, T* phi_new,
                     int ncells, RedScratch rs, T* g_hist, T* f_hist, int depth, AAState* aa, DevState* st, double tol) {
     __shared__ T sp[kRedGroups][kRedCells][4];
     __shared__ double sred[kAAPart][kRedCells * 4 / 32];
@@ -689,7 +793,7 @@ sn_reduce_aa_kernel(const T* psi, int nord, const T* qwv, const T* phi_old, T* p
     const int nslot = depth + 1;
     const int head = aa->head, n_new = aa->n + 1 < nslot ? aa->n + 1 : nslot;
     const size_t nv = (size_t)ncells * 4;
-    weighted_psi_sum<T>(psi, nord, qwv, k0 + c, ncells, g, sp[g][c]);
+    weighted_psi_sum<T>(psi, nord, nq, wave != 0, wv, split, qwv, k0 + c, ncells, g, sp[g][c]);
     __syncthreads();
     if (threadIdx.x < kRedCells * 4) {
         const int cc = threadIdx.x >> 2, i = threadIdx.x & 3;
@@ -760,7 +864,7 @@ sn_reduce_aa_kernel(const T* psi, int nord, const T* qwv, const T* phi_old, T* p
 template <typename T>
 __global__ void sn_mix_kernel(T* phi_new, const T* g_hist, int ncells, int depth, const AAState* aa,
                               const DevState* st, const T* sig, const double* mom, T area, T inv_4pi_dt,
-                              CellSplit split, T* src) {
+                              CellSplit split, int wave, Wave<T> wv, T* src) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nv = (size_t)ncells * 4;
     if (e >= nv || *(volatile const int*)&st->sn_conv) return;
@@ -780,7 +884,7 @@ __global__ void sn_mix_kernel(T* phi_new, const T* g_hist, int ncells, int depth
     const T cs = sig[2 * k + 1] * area * T(0.07957747154594767);
     int ix, iy;
     split((int)k, &ix, &iy);
-    src[SweepPad<T>::at(split.nx, ix, iy) * 4 + i] = cs * v * n_i + (T)mom[e] * inv_4pi_dt;
+    put_source<T>(src, wave != 0, wv, split.nx, ix, iy, i, cs * v * n_i + (T)mom[e] * inv_4pi_dt);
 }
 
 // start of a solve: clear the stop state; the iterate starts from zero, from the previous step's
@@ -835,8 +939,22 @@ cudaError_t sn_clear_counters(hyb_problem* p) {
     return cudaMemsetAsync(r.gcnt, 0, ngrp * sizeof(unsigned), p->stream);
 }
 
-size_t sn_src_bytes(int nx, int ny, bool fp64) {
-    return fp64 ? SweepPad<double>::plane(nx, ny) * 5 * sizeof(double) : SweepPad<float>::plane(nx, ny) * 5 * sizeof(float);
+template <typename T>
+static size_t src_entries(int nx, int ny, int nord, int layout) {
+    return sn_wave_layout(nx, ny, nord, sizeof(T) == 8, layout) ? 4 * Wave<T>::make(nx, ny).size()
+                                                                 : SweepPad<T>::plane(nx, ny);
+}
+
+size_t sn_src_bytes(int nx, int ny, int nord, bool fp64, int layout) {
+    return fp64 ? src_entries<double>(nx, ny, nord, layout) * 5 * sizeof(double)
+                : src_entries<float>(nx, ny, nord, layout) * 5 * sizeof(float);
+}
+
+size_t sn_psi_bytes(int nx, int ny, int nord, bool fp64, int layout) {
+    const size_t per = sn_wave_layout(nx, ny, nord, fp64, layout)
+                           ? (fp64 ? Wave<double>::make(nx, ny).size() : Wave<float>::make(nx, ny).size())
+                           : (size_t)nx * ny;
+    return (size_t)nord * per * 4 * (fp64 ? 8 : 4);
 }
 
 // ring entries per slot: every step of a strip's last block, lane 31 trailing lane 0 by 31 columns
@@ -858,13 +976,17 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     cudaStream_t s = p->stream;
     const int g = (p->ncells + 255) / 256;
     const size_t plane = SweepPad<T>::plane(p->nx, p->ny);
-    T* src = (T*)p->sn_quad;          // 4 per padded cell
-    T* sgA = src + 4 * plane;         // 1 per padded cell
+    const int wave = sn_wave_layout(p->nx, p->ny, p->n_ord, sizeof(T) == 8, p->d.sn_layout) ? 1 : 0;
+    const Wave<T> wv = Wave<T>::make(p->nx, p->ny);
+    T* src = (T*)p->sn_quad;                                // 4 per entry
+    T* sgA = src + 4 * src_entries<T>(p->nx, p->ny, p->n_ord, p->d.sn_layout);   // 1 per entry
     const CellSplit split = make_cell_split(p->nx);
+    const int nq = p->n_ord / 4;
     const T inv4pidt = (T)(1.0 / (4.0 * 3.14159265358979323846 * p->d.dt));
     if (first)
-        sn_source_kernel<T><<<g, 256, 0, s>>>(p->ncells, split, (const T*)p->sig, (const T*)p->sn_phi_old, p->mom_d,
-                                              (T)p->area, inv4pidt, (T)(1.0 / (p->d.c * p->d.dt)), src, sgA);
+        sn_source_kernel<T><<<g, 256, 0, s>>>(p->ncells, split, wave, wv, (const T*)p->sig, (const T*)p->sn_phi_old,
+                                              p->mom_d, (T)p->area, inv4pidt, (T)(1.0 / (p->d.c * p->d.dt)), src,
+                                              sgA);
     const T* qbuf = (const T*)p->sn_quadbuf;
     const T* qwv = qbuf + 3 * kMaxOrd;
     SweepArgs<T> a;
@@ -880,12 +1002,14 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     a.status = &p->st->status;
     a.conv = &p->st->sn_conv;
     a.plane = plane;
+    a.wv = wv;
     size_t smem = 0;
     a.W = sweep_warps<T>(p, &smem);
-    const bool tab = p->sn_table != nullptr && a.W <= kTableMaxStrips;
+    const bool tab = p->sn_table != nullptr && a.W <= kTableMaxStrips && !wave;
     a.k8 = tab ? (const T*)p->sn_table : nullptr;
     a.i3 = tab ? a.k8 + (size_t)a.nq * plane * 8 : nullptr;
-    auto kern = tab ? sweep_pipe_kernel<T, true> : sweep_pipe_kernel<T, false>;
+    auto kern = wave ? sweep_pipe_kernel<T, false, true>
+                     : (tab ? sweep_pipe_kernel<T, true, false> : sweep_pipe_kernel<T, false, false>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -899,23 +1023,23 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
         T* gh = (T*)p->aa_hist;
         T* fh = gh + (size_t)(depth + 1) * nv;
         sn_reduce_aa_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>(
-            (const T*)p->sn_psi, p->n_ord, qwv, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, gh,
-            fh, depth, (AAState*)p->aa_state, p->st, sn_tol_eff(p));
+            (const T*)p->sn_psi, p->n_ord, nq, wave, wv, split, qwv, (const T*)p->sn_phi_old, (T*)p->sn_phi,
+            p->ncells, rs, gh, fh, depth, (AAState*)p->aa_state, p->st, sn_tol_eff(p));
         sn_mix_kernel<T><<<(unsigned)((nv + 255) / 256), 256, 0, s>>>((T*)p->sn_phi, gh, p->ncells, depth,
                                                                       (const AAState*)p->aa_state, p->st,
                                                                       (const T*)p->sig, p->mom_d, (T)p->area,
-                                                                      inv4pidt, split, src);
+                                                                      inv4pidt, split, wave, wv, src);
         return cudaGetLastError();
     }
-    sn_reduce_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, qwv, split,
+    sn_reduce_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, nq, wave, wv, qwv, split,
                                                               (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs,
                                                               (const T*)p->sig, p->mom_d, (T)p->area, inv4pidt, src,
                                                               p->st, sn_tol_eff(p));
     return cudaGetLastError();
 }
 
-size_t sn_table_bytes(int nx, int ny, int nord, bool fp64) {
-    if (!fp64 || (ny + 31) / 32 > kTableMaxStrips) return 0;
+size_t sn_table_bytes(int nx, int ny, int nord, bool fp64, int layout) {
+    if (!fp64 || (ny + 31) / 32 > kTableMaxStrips || sn_wave_layout(nx, ny, nord, fp64, layout)) return 0;
     const size_t b = fp64 ? (size_t)(nord / 4) * SweepPad<double>::plane(nx, ny) * 9 * sizeof(double)
                           : (size_t)(nord / 4) * SweepPad<float>::plane(nx, ny) * 9 * sizeof(float);
     return b <= kTableMaxBytes ? b : 0;

@@ -38,7 +38,8 @@ class Desc(C.Structure):
                 ("sn_order", C.c_int32), ("handoff_full", C.c_int32), ("sn_max_iter", C.c_int32),
                 ("sn_tol", C.c_double), ("w_min", C.c_double), ("census_cap", C.c_int64),
                 ("sn_warm_start", C.c_int32), ("census_order", C.c_int32), ("sn_accel", C.c_int32),
-                ("remap_variant", C.c_int32), ("n_s_cell", C.POINTER(C.c_int32))]
+                ("remap_variant", C.c_int32), ("n_s_cell", C.POINTER(C.c_int32)), ("sn_layout", C.c_int32),
+                ("pad2", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -143,7 +144,7 @@ def make_desc(spec: ProblemSpec) -> tuple[Desc, list]:
              precision=spec.precision, sn_order=spec.sn_order, handoff_full=spec.handoff_full,
              sn_max_iter=spec.sn_max_iter, sn_tol=spec.sn_tol, w_min=spec.w_min,
              census_cap=spec.census_cap, sn_warm_start=spec.sn_warm_start, census_order=spec.census_order,
-             sn_accel=spec.sn_accel, remap_variant=spec.remap_variant)
+             sn_accel=spec.sn_accel, remap_variant=spec.remap_variant, sn_layout=spec.sn_layout)
     if spec.n_s_cell is not None:
         lim = np.ascontiguousarray(np.asarray(spec.n_s_cell, dtype=np.int32).ravel())
         keep.append(lim)

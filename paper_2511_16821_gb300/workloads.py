@@ -55,6 +55,7 @@ class ProblemSpec:
     sn_accel: int = 0
     remap_variant: int = 0          # 0: Eq. (R) relabelling remap; 1: steps 3'/4' of the previous hybrids
     n_s_cell: np.ndarray | None = None   # per-cell scatter limits in [0, n_s] (space-dependent N_s)
+    sn_layout: int = 0              # sweep memory layout: 0 automatic, 1 padded mesh, 2 wavefront order
     name: str = field(default="problem")
 
     @property

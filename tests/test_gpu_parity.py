@@ -226,9 +226,13 @@ def test_mc_leg_fp32_tolerance(H, orc, case):
 # ------------------------------------------------------------------------------------------------
 # collided S_N-DG and remap
 # ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("layout", [1, 2])
 @pytest.mark.parametrize("order,n", [(4, 35), (8, 40), (8, 7)])
-def test_collided_solve_parity(H, orc, order, n):
-    spec = W.checkerboard(n_s=1, n_hist=20_000, cells_per_block=max(1, n // 7)).with_(sn_order=order, sn_tol=1e-13)
+def test_collided_solve_parity(H, orc, order, n, layout):
+    """FP64 collided stage against the oracle, on the padded-mesh layout (1, with the cell-solve
+    table) and the wavefront layout (2) of the sweep."""
+    spec = W.checkerboard(n_s=1, n_hist=20_000, cells_per_block=max(1, n // 7)).with_(sn_order=order, sn_tol=1e-13,
+                                                                                      sn_layout=layout)
     bank = W.random_bank(spec, 4000, seed=3)
     o = orc.mc_leg(spec, 0, bank)
     phi_o, it_o = orc.sn_solve(spec, o["mom"])
@@ -240,12 +244,14 @@ def test_collided_solve_parity(H, orc, order, n):
     assert np.allclose(phi_g, phi_o, rtol=1e-9, atol=1e-10 * scale)
 
 
+@pytest.mark.parametrize("layout", [1, 2])
 @pytest.mark.parametrize("order", [4, 8])
-def test_collided_solve_fp32(H, orc, order):
+def test_collided_solve_fp32(H, orc, order, layout):
     """FP32 collided stage: the GPU's own hand-off moments solved by the FP64 oracle; cells above
     1e-3 of the peak agree within 1e-4 relative (stop test at 2e-6 relative change)."""
     spec = W.checkerboard(n_s=1, n_hist=20_000, cells_per_block=5, precision=W.FP32).with_(sn_order=order,
-                                                                                          sn_tol=1e-7)
+                                                                                          sn_tol=1e-7,
+                                                                                          sn_layout=layout)
     bank = W.random_bank(spec, 4000, seed=5)
     g = gpu_leg(H, spec, bank, 0)
     g["P"].collided_solve()
@@ -259,14 +265,16 @@ def test_collided_solve_fp32(H, orc, order):
     assert np.allclose(phi_g[:, 1:], phi_o[:, 1:], rtol=0, atol=1e-4 * peak)
 
 
+@pytest.mark.parametrize("layout", [1, 2])
 @pytest.mark.parametrize("prec", [W.FP64, W.FP32])
-def test_collided_solve_tall_mesh(H, orc, prec):
+def test_collided_solve_tall_mesh(H, orc, prec, layout):
     """8 x 700 cells: 22 row strips for at most 16 warps, so strip-to-strip ring slots are reused."""
     n = 8
     sa = np.full(n * 700, 0.2)
     ss = np.full(n * 700, 0.8)
     spec = W.ProblemSpec(nx=n, ny=700, lx=1.0, ly=87.5, sigma_a=sa, sigma_s=ss, Q=np.ones(n * 700), c=1.0, dt=0.5,
-                         n_s=0, n_hist=20_000, seed=2, precision=prec, sn_order=8, sn_tol=1e-13 if prec == W.FP64 else 1e-7)
+                         n_s=0, n_hist=20_000, seed=2, precision=prec, sn_order=8, sn_tol=1e-13 if prec == W.FP64 else 1e-7,
+                         sn_layout=layout)
     g = gpu_leg(H, spec, None, 0)
     g["P"].collided_solve()
     phi_g = g["P"].tally("sn_phi")
@@ -276,6 +284,38 @@ def test_collided_solve_tall_mesh(H, orc, prec):
         assert np.allclose(phi_g, phi_o, rtol=1e-9, atol=1e-10 * scale)
     else:
         assert np.allclose(phi_g, phi_o, rtol=1e-4, atol=1e-5 * scale)
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32])
+def test_sweep_layouts_agree(H, prec):
+    """The two memory layouts of the sweep (padded mesh, wavefront order) run the same arithmetic in
+    the same order: the collided flux agrees to rounding (FP32: bit for bit expected; FP64: the
+    padded mesh takes the tabulated cell solve), on a mesh with a ragged last strip and ragged
+    columns."""
+    base = W.checkerboard(n_s=1, n_hist=20_000, cells_per_block=3, precision=prec)
+    base = base.with_(nx=37, ny=45, sigma_a=np.resize(base.sigma_a, 37 * 45), sigma_s=np.resize(base.sigma_s, 37 * 45),
+                      Q=np.resize(base.Q, 37 * 45), ic=None, sn_tol=1e-13 if prec == W.FP64 else 1e-7)
+    bank = W.random_bank(base, 3000, seed=4)
+    out = {}
+    for layout in (1, 2):
+        P = H.Problem(base.with_(sn_layout=layout))
+        P.set_bank(bank)
+        P.set_step(0)
+        P.mc_leg()
+        st = P.collided_solve()
+        out[layout] = (P.tally("sn_phi"), st["sn_iterations"])
+        P.close()
+    a, b = out[1][0], out[2][0]
+    scale = np.max(np.abs(a[:, 0]))
+    print(f"\nlayouts: iterations {out[1][1]} / {out[2][1]}, bitwise equal: {np.array_equal(a, b)}")
+    assert out[1][1] == out[2][1]
+    assert np.allclose(a, b, rtol=0, atol=(1e-12 if prec == W.FP64 else 1e-6) * scale)
+
+
+def test_sweep_layout_validation(H):
+    spec = W.checkerboard(n_s=1, n_hist=1000, cells_per_block=1)
+    with pytest.raises(H.HybError):
+        H.Problem(spec.with_(sn_layout=3))
 
 
 @pytest.mark.parametrize("cap,order", [(0, 0), (10 ** 7, 0), (0, 1), (10 ** 7, 1), (9000, 1), (0, 2), (10 ** 7, 2),
