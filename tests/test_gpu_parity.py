@@ -344,6 +344,8 @@ def test_remap_parity(H, orc, cap, order):
     assert np.allclose(gb["w"], ob["w"], rtol=1e-10, atol=0)
     assert rs["histories"] == ost["histories"] and rs["leaked"] == ost["leaked"]
     assert math.isclose(rs["w_source"], ost["w_source"], rel_tol=1e-10)
+    for k in ("w_absorbed", "w_leaked", "w_killed"):
+        assert math.isclose(rs[k], ost[k], rel_tol=1e-10, abs_tol=1e-12 * ost["w_source"]), (k, rs[k], ost[k])
 
 
 @pytest.mark.parametrize("prec,order,sampler,limits", [(W.FP64, 0, W.SOBOL, 0), (W.FP32, 0, W.SOBOL, 0),
