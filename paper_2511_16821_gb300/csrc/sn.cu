@@ -774,13 +774,14 @@ __device__ void aa_solve(AAState* aa, const int* slots, int n) {
 // The reduction of an accelerated iteration: g = sum of w_m psi_m (into phi_new and the history),
 // f = g - phi_old, the weighted dots of f with every stored residual and <g, g>; the last block
 // completes the Gram matrix, applies the stop test and, if the solve goes on, forms the weights.
-template <typename T>
+template <typename T, int NS>
 __global__ void __launch_bounds__(kRedCells * kRedGroups)
 sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSplit split, const T* qwv, const T* phi_old, T* phi_new,
                     int ncells, RedScratch rs, T* g_hist, T* f_hist, int depth, AAState* aa, DevState* st, double tol) {
+    constexpr int NP = NS + 1;   // per block: the dots with the NS slots, then <g, g>
     __shared__ T sp[kRedGroups][kRedCells][4];
-    __shared__ double sred[kAAPart][kRedCells * 4 / 32];
-    __shared__ double s_tot[kAAPart];
+    __shared__ double sred[NP][kRedCells * 4 / 32];
+    __shared__ double s_tot[NP];
     const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
     const int k0 = blockIdx.x * kRedCells;
     if (*(volatile const int*)&st->sn_conv) {
@@ -790,7 +791,7 @@ sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSp
         }
         return;
     }
-    const int nslot = depth + 1;
+    const int nslot = NS;   // depth + 1
     const int head = aa->head, n_new = aa->n + 1 < nslot ? aa->n + 1 : nslot;
     const size_t nv = (size_t)ncells * 4;
     weighted_psi_sum<T>(psi, nord, nq, wave != 0, wv, split, qwv, k0 + c, ncells, g, sp[g][c]);
@@ -798,10 +799,10 @@ sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSp
     if (threadIdx.x < kRedCells * 4) {
         const int cc = threadIdx.x >> 2, i = threadIdx.x & 3;
         const int k = k0 + cc;
-        T dots[kAAMax + 1];
+        T dots[NS];
         T den = 0;
 #pragma unroll
-        for (int q = 0; q <= kAAMax; ++q) dots[q] = 0;
+        for (int q = 0; q < NS; ++q) dots[q] = 0;
         if (k < ncells) {
             T v = 0;
 #pragma unroll
@@ -815,31 +816,31 @@ sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSp
             den = nrm * v * v;
             // the stored slots: head and the n_new - 1 before it in ring order
 #pragma unroll
-            for (int q = 0; q <= kAAMax; ++q) {
+            for (int q = 0; q < NS; ++q) {
                 const int j = (head - q + nslot) % nslot;
-                if (q < nslot && j < n_new) dots[q] = nrm * f * (q == head ? f : f_hist[q * nv + e]);
+                if (j < n_new) dots[q] = nrm * f * (q == head ? f : f_hist[q * nv + e]);
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
             den += __shfl_down_sync(0xffffffffu, den, o);
 #pragma unroll
-            for (int q = 0; q <= kAAMax; ++q) dots[q] += __shfl_down_sync(0xffffffffu, dots[q], o);
+            for (int q = 0; q < NS; ++q) dots[q] += __shfl_down_sync(0xffffffffu, dots[q], o);
         }
         if ((threadIdx.x & 31) == 0) {
             const int w = threadIdx.x >> 5;
 #pragma unroll
-            for (int q = 0; q <= kAAMax; ++q) sred[q][w] = (double)dots[q];
-            sred[kAAMax + 1][w] = (double)den;
+            for (int q = 0; q < NS; ++q) sred[q][w] = (double)dots[q];
+            sred[NS][w] = (double)den;
         }
     }
     __syncthreads();
-    if (threadIdx.x < kAAPart) {
+    if (threadIdx.x < NP) {
         double a = 0;
         for (int w = 0; w < kRedCells * 4 / 32; ++w) a += sred[threadIdx.x][w];
-        rs.part[(size_t)blockIdx.x * kAAPart + threadIdx.x] = a;
+        rs.part[(size_t)blockIdx.x * NP + threadIdx.x] = a;
         __threadfence();
     }
-    if (reduce_partials<kAAPart>(rs.part, (int)gridDim.x, rs.gpart, rs.gcnt, &st->sn_blocks_done, s_tot) &&
+    if (reduce_partials<NP>(rs.part, (int)gridDim.x, rs.gpart, rs.gcnt, &st->sn_blocks_done, s_tot) &&
         threadIdx.x == 0) {
         int slots[kAAMax + 1];
         for (int j = 0; j < n_new; ++j) {
@@ -848,7 +849,7 @@ sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSp
             aa->gram[head][sl] = s_tot[sl];
             aa->gram[sl][head] = s_tot[sl];
         }
-        const double num = s_tot[head], d = s_tot[kAAMax + 1];
+        const double num = s_tot[head], d = s_tot[NS];
         st->sn_norm_num = num;
         st->sn_norm_den = d;
         st->sn_iters += 1;
@@ -1022,9 +1023,14 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
         const size_t nv = 4 * (size_t)p->ncells;
         T* gh = (T*)p->aa_hist;
         T* fh = gh + (size_t)(depth + 1) * nv;
-        sn_reduce_aa_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>(
-            (const T*)p->sn_psi, p->n_ord, nq, wave, wv, split, qwv, (const T*)p->sn_phi_old, (T*)p->sn_phi,
-            p->ncells, rs, gh, fh, depth, (AAState*)p->aa_state, p->st, sn_tol_eff(p));
+        // the reduction carries depth + 2 partial sums per block: one instance per depth
+        auto red = depth == 1 ? sn_reduce_aa_kernel<T, 2> : depth == 2 ? sn_reduce_aa_kernel<T, 3>
+                 : depth == 3 ? sn_reduce_aa_kernel<T, 4> : depth == 4 ? sn_reduce_aa_kernel<T, 5>
+                 : depth == 5 ? sn_reduce_aa_kernel<T, 6> : depth == 6 ? sn_reduce_aa_kernel<T, 7>
+                 : depth == 7 ? sn_reduce_aa_kernel<T, 8> : sn_reduce_aa_kernel<T, 9>;
+        red<<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, nq, wave, wv, split, qwv,
+                                                  (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, gh, fh,
+                                                  depth, (AAState*)p->aa_state, p->st, sn_tol_eff(p));
         sn_mix_kernel<T><<<(unsigned)((nv + 255) / 256), 256, 0, s>>>((T*)p->sn_phi, gh, p->ncells, depth,
                                                                       (const AAState*)p->aa_state, p->st,
                                                                       (const T*)p->sig, p->mom_d, (T)p->area,
