@@ -51,6 +51,7 @@ def _bad(spec, **kw):
 @pytest.mark.parametrize("mut", [
     dict(nx=0), dict(ny=5000), dict(dt=0.0), dict(c=-1.0), dict(n_s=-1), dict(sn_order=6),
     dict(n_hist=0), dict(sampler=7), dict(precision=3), dict(w_min=1.5), dict(sn_max_iter=0),
+    dict(sn_layout=3), dict(sn_layout=-1),
 ])
 def test_workspace_size_rejects_bad_descriptors(hyb, mut):
     spec = W.pulse(n_hist=100)
@@ -77,6 +78,42 @@ def test_workspace_size_scales_with_histories(hyb):
     b = hyb.workspace_size(W.checkerboard(n_hist=1_000_000))
     c = hyb.workspace_size(W.checkerboard(n_hist=1_000_000, precision=W.FP32))
     assert a < b and c < b
+
+
+def _sweep_bytes(nx, ny, nord, fp64, wave):
+    """The collided solve's sweep buffers as the layouts define them: sources (4 + 1 values per
+    entry) and per-ordinate psi (4 per entry), plus the FP64 cell-solve table (9 per ordinate
+    class and entry, padded mesh only, at most 8 strips and 64 MB)."""
+    T = 8 if fp64 else 4
+    PF = 4 if fp64 else 8
+    nstrip = (ny + 31) // 32
+    if wave:
+        nt = (nx + 31 + PF - 1) // PF * PF + PF
+        ent = nstrip * nt * 32
+        return 4 * ent * 5 * T + nord * ent * 4 * T
+    plane = (ny + 1) * (nx + 2 * (32 + 2 * PF))
+    tab = (nord // 4) * plane * 9 * T if fp64 and nstrip <= 8 else 0
+    tab = tab if tab <= 64 << 20 else 0
+    return plane * 5 * T + nord * nx * ny * 4 * T + tab
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32])
+def test_workspace_size_by_sweep_layout(hyb, prec):
+    """Host-side layout choice: the workspaces of the padded-mesh (1) and wavefront (2) layouts
+    differ by exactly the difference of their sweep buffers (to the 256-byte alignment of the
+    workspace's parts), and the automatic choice (0) keeps the padded mesh on the 112^2 benchmark
+    mesh and takes the wavefront order on the 1024^2 mesh (per-ordinate solutions above 48 MB)."""
+    spec = W.checkerboard(n_hist=10_000, precision=prec)
+    fp64 = prec == W.FP64
+    ws = {L: hyb.workspace_size(spec.with_(sn_layout=L)) for L in (0, 1, 2)}
+    want = _sweep_bytes(112, 112, 40, fp64, True) - _sweep_bytes(112, 112, 40, fp64, False)
+    assert abs((ws[2] - ws[1]) - want) <= 3 * 256
+    assert ws[0] == ws[1]
+    big = W.large(n=1024, n_hist=10_000, precision=prec)
+    wb = {L: hyb.workspace_size(big.with_(sn_layout=L)) for L in (0, 1, 2)}
+    assert wb[0] == wb[2]
+    want_b = _sweep_bytes(1024, 1024, 40, fp64, True) - _sweep_bytes(1024, 1024, 40, fp64, False)
+    assert abs((wb[2] - wb[1]) - want_b) <= 3 * 256
 
 
 def test_no_cpu_fallback_without_gpu(hyb):
