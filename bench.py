@@ -142,7 +142,8 @@ def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
     """Kernels of this library launched by one single-problem step (memsets not counted)."""
     leg = 3                                   # births, leg kernel, normalisation
     sn = 1 + 1 + 2 * sn_iters + 1             # seed, source; sweep + reduce per iteration; finish (copy, flux)
-    remap = 1 + 5 + 1 + 3 + 1                 # density, CDF (5 with the guide tables), prep, count/scan/write, finish
+    remap = 1 + 3 + 1 + 3 + 1                 # density, CDF (reduce, total, rows with marginal and guides), prep,
+                                              # count/scan/write, finish
     return leg + sn + remap
 
 

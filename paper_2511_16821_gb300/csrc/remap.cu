@@ -2,8 +2,9 @@
 //
 // CDF build (shared by the static source and the remap source): per cell |q| -> max and sum
 // (deterministic block order) -> q_int = rint(|q| / max |q| 2^40) -> per-row exclusive scans
-// (column conditional) -> row-total scan (row marginal). Exact integer arithmetic, so cells are
-// picked identically on the FP32 and FP64 paths.
+// (column conditional) and column guides -> row-total scan (row marginal) and row guide in the
+// last row block. Exact integer arithmetic, so cells are picked identically on the FP32 and FP64
+// paths.
 //
 // Remap: slot j in [bank slots | births] is re-streamed straight with sigma_t attenuation from its
 // step-start state (bank particles are copied, births come from the remap source density
@@ -51,17 +52,40 @@ __global__ void cdf_reduce_kernel(const double* __restrict__ w, int ncells, doub
     }
 }
 
-// one warp: strided partial sums, then a fixed-order shuffle tree (deterministic)
-__global__ void cdf_total_kernel(const double* part_sum, int nparts, double* W) {
+// one warp: strided partial sums, then a fixed-order shuffle tree (deterministic); afterwards the
+// first partial's word is the row kernel's arrival counter, so it is zeroed here
+__global__ void cdf_total_kernel(double* part_sum, int nparts, double* W) {
     double t = 0;
     for (int i = threadIdx.x; i < nparts; i += 32) t += part_sum[i];
     t = warp_sum(t);
-    if (threadIdx.x == 0) *W = t;
+    if (threadIdx.x == 0) {
+        *W = t;
+        *reinterpret_cast<unsigned*>(part_sum) = 0u;
+    }
 }
 
-// one block per row: q_int and the exclusive column scan of the row
-__global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax, int nx, Cdf2DView C,
-                                long long* row_tot) {
+// the bin of point x in pre[0..n] searched in [lo, hi]: the decisions of pick_bin, for the guide
+// tables (pre may have been written earlier in the same launch, so it is read without __restrict__)
+__device__ __forceinline__ int guide_bin(const long long* pre, int n, uint32_t x, int lo, int hi) {
+    const unsigned long long total = (unsigned long long)pre[n];
+    const unsigned long long m = 2ull * (unsigned long long)x + 1ull;
+    const unsigned long long Plo = m * total, Phi = __umul64hi(m, total);
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const unsigned long long v = (unsigned long long)pre[mid];
+        const unsigned long long vhi = v >> 31, vlo = v << 33;
+        if (vhi < Phi || (vhi == Phi && vlo <= Plo)) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long* total);
+
+// one block per row: q_int, the exclusive column scan of the row and the row's column guide; the
+// last block to finish (arrival counter *done, zeroed beforehand) forms the row marginal from the
+// row totals and the row guide, so the whole table is one launch
+__global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax, int nx, int ny, Cdf2DView C,
+                                long long* row_tot, unsigned* done) {
     const int iy = blockIdx.x;
     const double qm = *qmax;
     const int per = (nx + blockDim.x - 1) / blockDim.x;
@@ -104,6 +128,38 @@ __global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax
         pre[nx] = tot;
         row_tot[iy] = tot;
     }
+    __syncthreads();
+    // column guide of this row: entry g is the bin of the bucket's smallest point g 2^(32-gc)
+    const bool guides = C.row_g != nullptr && C.col_g != nullptr;
+    if (guides) {
+        const int Gc = 1 << C.gc;
+        int* cg = C.col_g + (size_t)iy * (Gc + 1);
+        for (int g = threadIdx.x; g <= Gc; g += blockDim.x)
+            cg[g] = g == Gc ? nx - 1 : guide_bin(pre, nx, (uint32_t)((unsigned long long)g << (32 - C.gc)), 0, nx - 1);
+    }
+    // the last row block: row marginal and row guide
+    __shared__ bool s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == (unsigned)ny - 1u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int rper = (ny + blockDim.x - 1) / blockDim.x;
+    const int r0 = threadIdx.x * rper;
+    long long rl = 0;
+    for (int r = r0; r < r0 + rper && r < ny; ++r) rl += __ldcg(row_tot + r);
+    long long total;
+    long long rrun = block_exclusive_scan(rl, &total);
+    for (int r = r0; r < r0 + rper && r < ny; ++r) { C.row_pre[r] = rrun; rrun += __ldcg(row_tot + r); }
+    if (threadIdx.x == 0) C.row_pre[ny] = total;
+    __syncthreads();
+    if (guides) {
+        const int Gr = 1 << C.gr;
+        for (int g = threadIdx.x; g <= Gr; g += blockDim.x)
+            C.row_g[g] = g == Gr ? ny - 1 : guide_bin(C.row_pre, ny, (uint32_t)((unsigned long long)g << (32 - C.gr)), 0, ny - 1);
+    }
+    if (threadIdx.x == 0) *done = 0u;   // ready for the next build
 }
 
 // block inclusive scan of a per-thread total (int64, exact); returns the exclusive prefix
@@ -132,37 +188,8 @@ __device__ __forceinline__ long long block_exclusive_scan(long long v, long long
     return ex;
 }
 
-// row marginal: exclusive prefix of the row totals (one block, contiguous chunks per thread)
-__global__ void cdf_rowpre_kernel(const long long* row_tot, int ny, long long* row_pre) {
-    const int per = (ny + blockDim.x - 1) / blockDim.x;
-    const int r0 = threadIdx.x * per;
-    long long local = 0;
-    for (int r = r0; r < r0 + per && r < ny; ++r) local += row_tot[r];
-    long long total;
-    long long run = block_exclusive_scan(local, &total);
-    for (int r = r0; r < r0 + per && r < ny; ++r) { row_pre[r] = run; run += row_tot[r]; }
-    if (threadIdx.x == 0) row_pre[ny] = total;
-}
-
-// guide tables: thread t < 2^gr + 1 fills row-guide entry t, the others the column guides row by
-// row; entry b is the pick of the bucket's smallest point b 2^(32-g), the last entry the last bin
-__global__ void cdf_guide_kernel(Cdf2DView C, int nx, int ny) {
-    const long long Gr = 1ll << C.gr, Gc = 1ll << C.gc;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long nrow = Gr + 1;
-    if (t >= nrow + (long long)ny * (Gc + 1)) return;
-    unsigned long long a, b, W;
-    if (t < nrow) {
-        C.row_g[t] = t == Gr ? ny - 1 : pick_bin(C.row_pre, ny, (uint32_t)(t << (32 - C.gr)), 0, ny - 1, &a, &b, &W);
-    } else {
-        const long long u = t - nrow;
-        const long long r = u / (Gc + 1), g = u % (Gc + 1);
-        C.col_g[u] = g == Gc ? nx - 1
-                             : pick_bin(C.col_pre + r * (nx + 1), nx, (uint32_t)(g << (32 - C.gc)), 0, nx - 1, &a, &b, &W);
-    }
-}
-
-// scratch: kCdfParts doubles of block partial sums, then ny int64 row totals
+// scratch: kCdfParts doubles of block partial sums (the first word then the rows' arrival
+// counter), then ny int64 row totals
 cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
                                  double* qmax_out, double* scratch, cudaStream_t stream) {
     cudaError_t e = cudaMemsetAsync(qmax_out, 0, sizeof(double), stream);
@@ -171,12 +198,7 @@ cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView
     long long* row_tot = (long long*)(scratch + kCdfParts);
     cdf_reduce_kernel<<<kCdfParts, 256, 0, stream>>>(cell_w, nx * ny, part, qmax_out);
     cdf_total_kernel<<<1, 32, 0, stream>>>(part, kCdfParts, W_out);
-    cdf_rows_kernel<<<ny, 256, 0, stream>>>(cell_w, qmax_out, nx, cdf, row_tot);
-    cdf_rowpre_kernel<<<1, 1024, 0, stream>>>(row_tot, ny, cdf.row_pre);
-    if (cdf.row_g && cdf.col_g) {
-        const long long n = (1ll << cdf.gr) + 1 + (long long)ny * ((1ll << cdf.gc) + 1);
-        cdf_guide_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(cdf, nx, ny);
-    }
+    cdf_rows_kernel<<<ny, 256, 0, stream>>>(cell_w, qmax_out, nx, ny, cdf, row_tot, reinterpret_cast<unsigned*>(part));
     return cudaGetLastError();
 }
 
