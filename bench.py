@@ -279,7 +279,10 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0, sn_acc
     probs = [hyb.Problem(sp, stream=stream) for sp in specs]
     B = hyb.Batch(probs, stream=stream)
     tune = tune_batch(B, steps=1, space={"block": (256,), "chunk": (2048, 8192, 32768), "streams": (16, 48)})
-    B.step(1)
+    # steady state: a problem whose source iteration outgrows its cap in the step graphs is finished
+    # eagerly and the graphs are re-captured with a larger cap, a one-off cost of ~20 ms for 256
+    # problems; three steps let the caps settle before the timed ones
+    B.step(3)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
