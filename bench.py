@@ -141,7 +141,8 @@ def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0
 def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
     """Kernels of this library launched by one single-problem step (memsets not counted)."""
     leg = 3                                   # births, leg kernel, normalisation
-    sn = 1 + 1 + 2 * sn_iters + 1             # seed, source; sweep + reduce per iteration; finish (copy, flux)
+    sn = 1 + 2 * sn_iters + 1                 # source (with the starting iterate); sweep + reduce per iteration;
+                                              # finish (copy, flux)
     remap = 1 + 3 + 1 + 3 + 1                 # density, CDF (reduce, total, rows with marginal and guides), prep,
                                               # count/scan/write, finish
     return leg + sn + remap

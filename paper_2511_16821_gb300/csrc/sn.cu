@@ -124,16 +124,30 @@ __device__ __forceinline__ int sweep_entries(bool wave, const Wave<T>& wv, int n
     return 4;
 }
 
+// The first iteration's sources. The solve's starting iterate is formed here too: zero, the
+// previous step's solution (warm start, re-read from its FP64 copy), or the linear extrapolation
+// 2 phi_{n-1} - phi_{n-2} of the last two (extrap, once two solves exist); the fixed point is the
+// same whatever the start. It is written to phi_old (the first reduction's reference) and the
+// sources are formed from it.
 template <typename T>
-__global__ void sn_source_kernel(int ncells, CellSplit split, int wave, Wave<T> wv, const T* sig, const T* phi_old,
+__global__ void sn_source_kernel(int ncells, CellSplit split, int wave, Wave<T> wv, const T* sig, T* phi_old,
+                                 const double* prev, const double* prev2, const DevState* st, int extrap,
                                  const double* mom, T area, T inv_4pi_dt, T inv_cdt, T* src, T* sgA) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ncells) return;
     int ix, iy;
     split(k, &ix, &iy);
+    const int wst = st->sn_warm;
+    T po[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const size_t e = 4 * (size_t)k + i;
+        po[i] = wst == 0 ? T(0) : (extrap && wst >= 2 ? (T)(2.0 * prev[e] - prev2[e]) : (T)prev[e]);
+        phi_old[e] = po[i];
+    }
     const T sa = sig[2 * k], ss = sig[2 * k + 1];
     T S[4];
-    source4<T>(ss, area, phi_old + 4 * (size_t)k, mom + 4 * (size_t)k, inv_4pi_dt, S);
+    source4<T>(ss, area, po, mom + 4 * (size_t)k, inv_4pi_dt, S);
     const T g = (sa + ss + inv_cdt) * area;
     size_t e[4];
     const int n = sweep_entries<T>(wave != 0, wv, split.nx, ix, iy, e);
@@ -888,19 +902,6 @@ __global__ void sn_mix_kernel(T* phi_new, const T* g_hist, int ncells, int depth
     put_source<T>(src, wave != 0, wv, split.nx, ix, iy, i, cs * v * n_i + (T)mom[e] * inv_4pi_dt);
 }
 
-// start of a solve: clear the stop state; the iterate starts from zero, from the previous step's
-// solution (warm start, re-read from its FP64 copy), or from the linear extrapolation
-// 2 phi_{n-1} - phi_{n-2} of the last two (extrap, once two solves exist). The fixed point is
-// the same whatever the start.
-template <typename T>
-__global__ void sn_seed_kernel(const double* prev, const double* prev2, T* phi, int n, const DevState* st,
-                               int extrap) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int w = st->sn_warm;
-    phi[i] = w == 0 ? T(0) : (extrap && w >= 2 ? (T)(2.0 * prev[i] - prev2[i]) : (T)prev[i]);
-}
-
 // The end of a solve: the solution's FP64 copy (with an extrapolating warm start, the copy it
 // replaces moves to out_prev), the step flux phi_pre + phi_post + phi_c0 per cell, and the count
 // of finished solves with warm starts enabled (up to 2), in one launch.
@@ -985,7 +986,8 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     const int nq = p->n_ord / 4;
     const T inv4pidt = (T)(1.0 / (4.0 * 3.14159265358979323846 * p->d.dt));
     if (first)
-        sn_source_kernel<T><<<g, 256, 0, s>>>(p->ncells, split, wave, wv, (const T*)p->sig, (const T*)p->sn_phi_old,
+        sn_source_kernel<T><<<g, 256, 0, s>>>(p->ncells, split, wave, wv, (const T*)p->sig, (T*)p->sn_phi_old,
+                                              p->sn_phi_d, p->sn_phi_d2, p->st, p->d.sn_warm_start == 2 ? 1 : 0,
                                               p->mom_d, (T)p->area, inv4pidt, (T)(1.0 / (p->d.c * p->d.dt)), src,
                                               sgA);
     const T* qbuf = (const T*)p->sn_quadbuf;
@@ -1081,15 +1083,7 @@ cudaError_t sn_start(hyb_problem* p) {
         e = cudaMemsetAsync(p->aa_state, 0, sizeof(AAState), p->stream);
         if (e != cudaSuccess) return e;
     }
-    const int n = 4 * p->ncells, g = (n + 255) / 256;
-    const int extrap = p->d.sn_warm_start == 2 ? 1 : 0;
-    if (p->prec == HYB_FP64)
-        sn_seed_kernel<double><<<g, 256, 0, p->stream>>>(p->sn_phi_d, p->sn_phi_d2, (double*)p->sn_phi_old, n, p->st,
-                                                         extrap);
-    else
-        sn_seed_kernel<float><<<g, 256, 0, p->stream>>>(p->sn_phi_d, p->sn_phi_d2, (float*)p->sn_phi_old, n, p->st,
-                                                        extrap);
-    return cudaGetLastError();
+    return cudaSuccess;   // the starting iterate is formed by the first iteration's source kernel
 }
 
 cudaError_t sn_iteration(hyb_problem* p, int first) {
