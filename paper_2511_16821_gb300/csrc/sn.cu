@@ -10,13 +10,14 @@
 // Sweep: one CTA per ordinate; its warps walk 32-row strips as wavefronts (lane = row, one
 // anti-diagonal per step); the trace entering a row from below comes from the neighbouring lane by
 // shuffle (from the strip below through a shared-memory ring), the trace from the left stays in
-// registers, so a step needs no block barrier. Sources and solutions live on a mesh padded with
-// halo columns and an extra row (or, for solves too large for L2, in the sweep's own wavefront
-// order), so a step also needs no bound test. Strips are pipelined across the warps, so the
-// critical path is about (nx + 31) + 32 (ceil(ny/32) - 1) cell solves per sweep. Coordinates are mirrored per quadrant so that every
-// sweep runs towards +x,+y; in mirrored coordinates the 4x4 cell system is the same for every
-// quadrant and is diagonally dominant, so it is solved by elimination without pivoting. The
-// per-ordinate results are summed over ordinates in a fixed order (deterministic).
+// registers, so a step needs no block barrier. The sources live on a mesh padded with zero halo
+// columns and an extra row, the solutions on the plain mesh behind predicated stores (or, for
+// solves too large for L2, both in the sweep's own wavefront order), so a step needs no bound
+// test. Strips are pipelined across the warps, so the critical path is about
+// (nx + 31) + (32 + PF - 1)(ceil(ny/32) - 1) cell solves per sweep. Coordinates are mirrored per
+// quadrant so that every sweep runs towards +x,+y; in mirrored coordinates the 4x4 cell system is
+// the same for every quadrant and is diagonally dominant, so it is solved by elimination without
+// pivoting. The per-ordinate results are summed over ordinates in a fixed order (deterministic).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -33,8 +34,10 @@ namespace hyb {
 // kHalo covers the columns a lane reads: loads run PF steps ahead of the step, the last block of
 // steps overruns the wavefront by up to PF - 1, and lane l trails lane 0 by l. The solutions psi
 // stay on the plain mesh: their store is predicated on the lane holding a mesh cell.
-// cell data prefetch depth of the sweep, in wavefront steps (a ring of register sets, unrolled so
-// that no value moves between registers while its load is in flight)
+//
+// PF: the cell data prefetch depth of the sweep, in wavefront steps (a ring of register sets,
+// unrolled so that no value moves between registers while its load is in flight), which is also the
+// length of the block of steps between two ring waits
 template <typename T> struct SweepDepth { static constexpr int value = sizeof(T) == 4 ? 8 : 4; };
 
 template <typename T> struct SweepPad {
