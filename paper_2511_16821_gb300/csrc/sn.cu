@@ -22,10 +22,36 @@
 
 #include <cmath>
 #include <type_traits>
+#include <utility>
 
 #include "hyb_device.cuh"
 
 namespace hyb {
+
+// Programmatic dependent launch between the source iteration's kernels: each sweep and reduction
+// is launched with programmatic stream serialisation, lets its successor be scheduled as soon as it
+// starts (launch_dependents), and waits for its predecessor's completion and memory (wait) before
+// it reads anything the predecessor wrote. The successor's blocks are then resident when the
+// predecessor ends, instead of being launched after it. Without a programmatic predecessor the
+// wait returns at once.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // Padded mesh of the sweep's sources: every row carries kHalo columns on both sides, and one extra
 // row follows the last; halo and extra row are zero. A lane before its row's first column, past its
@@ -500,6 +526,8 @@ template <typename T, bool TAB, bool WAVE>
 __global__ void __launch_bounds__(TAB ? 256 : 512) sweep_pipe_kernel(SweepArgs<T> a) {
     static_assert(!(TAB && WAVE), "the cell-solve table is kept on the padded mesh only");
     constexpr int RW = Ring<T>::kWords;
+    pdl_wait();
+    pdl_trigger();
     if (*(volatile const int*)a.conv) return;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int W = a.W;
@@ -677,6 +705,8 @@ sn_reduce_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, const T* 
     __shared__ double s_tot[2];
     const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
     const int k0 = blockIdx.x * kRedCells;
+    pdl_wait();
+    pdl_trigger();
     if (*(volatile const int*)&st->sn_conv) {
         // converged earlier: carry the solution forward so the buffer alternation stays aligned
         if (threadIdx.x < kRedCells * 4) {
@@ -801,6 +831,8 @@ sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSp
     __shared__ double s_tot[NP];
     const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
     const int k0 = blockIdx.x * kRedCells;
+    pdl_wait();
+    pdl_trigger();
     if (*(volatile const int*)&st->sn_conv) {
         if (threadIdx.x < kRedCells * 4) {
             const size_t e = (size_t)k0 * 4 + threadIdx.x;
@@ -1020,7 +1052,8 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<p->n_ord, 32 * a.W, smem, s>>>(a);
+    cudaError_t le = launch_pdl(kern, dim3(p->n_ord), dim3(32 * a.W), smem, s, a);
+    if (le != cudaSuccess) return le;
     const int gr = (p->ncells + kRedCells - 1) / kRedCells;
     const RedScratch rs = red_scratch(p);
     if (p->d.sn_accel > 0) {
@@ -1033,19 +1066,20 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
                  : depth == 3 ? sn_reduce_aa_kernel<T, 4> : depth == 4 ? sn_reduce_aa_kernel<T, 5>
                  : depth == 5 ? sn_reduce_aa_kernel<T, 6> : depth == 6 ? sn_reduce_aa_kernel<T, 7>
                  : depth == 7 ? sn_reduce_aa_kernel<T, 8> : sn_reduce_aa_kernel<T, 9>;
-        red<<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, nq, wave, wv, split, qwv,
-                                                  (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, gh, fh,
-                                                  depth, (AAState*)p->aa_state, p->st, sn_tol_eff(p));
+        le = launch_pdl(red, dim3(gr), dim3(kRedCells * kRedGroups), 0, s, (const T*)p->sn_psi, p->n_ord, nq, wave, wv,
+                        split, qwv, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, gh, fh, depth,
+                        (AAState*)p->aa_state, p->st, sn_tol_eff(p));
+        if (le != cudaSuccess) return le;
         sn_mix_kernel<T><<<(unsigned)((nv + 255) / 256), 256, 0, s>>>((T*)p->sn_phi, gh, p->ncells, depth,
                                                                       (const AAState*)p->aa_state, p->st,
                                                                       (const T*)p->sig, p->mom_d, (T)p->area,
                                                                       inv4pidt, split, wave, wv, src);
         return cudaGetLastError();
     }
-    sn_reduce_kernel<T><<<gr, kRedCells * kRedGroups, 0, s>>>((const T*)p->sn_psi, p->n_ord, nq, wave, wv, qwv, split,
-                                                              (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs,
-                                                              (const T*)p->sig, p->mom_d, (T)p->area, inv4pidt, src,
-                                                              p->st, sn_tol_eff(p));
+    le = launch_pdl(sn_reduce_kernel<T>, dim3(gr), dim3(kRedCells * kRedGroups), 0, s, (const T*)p->sn_psi, p->n_ord,
+                    nq, wave, wv, qwv, split, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, (const T*)p->sig,
+                    p->mom_d, (T)p->area, inv4pidt, src, p->st, sn_tol_eff(p));
+    if (le != cudaSuccess) return le;
     return cudaGetLastError();
 }
 
