@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "hyb_device.cuh"
+#include "pdl.cuh"
 
 namespace hyb {
 
@@ -31,6 +32,8 @@ constexpr int kSlotsPerBlock = kTile * kRounds;
 // CDF build
 // ---------------------------------------------------------------------------------------------
 __global__ void cdf_reduce_kernel(const double* __restrict__ w, int ncells, double* part_sum, double* qmax) {
+    pdl_wait();
+    pdl_trigger();
     double s = 0, m = 0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < ncells; k += gridDim.x * blockDim.x) {
         const double a = fabs(w[k]);
@@ -55,6 +58,8 @@ __global__ void cdf_reduce_kernel(const double* __restrict__ w, int ncells, doub
 // one warp: strided partial sums, then a fixed-order shuffle tree (deterministic); afterwards the
 // first partial's word is the row kernel's arrival counter, so it is zeroed here
 __global__ void cdf_total_kernel(double* part_sum, int nparts, double* W) {
+    pdl_wait();
+    pdl_trigger();
     double t = 0;
     for (int i = threadIdx.x; i < nparts; i += 32) t += part_sum[i];
     t = warp_sum(t);
@@ -86,6 +91,8 @@ __device__ __forceinline__ long long block_exclusive_scan(long long v, long long
 // row totals and the row guide, so the whole table is one launch
 __global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax, int nx, int ny, Cdf2DView C,
                                 long long* row_tot, unsigned* done) {
+    pdl_wait();
+    pdl_trigger();
     const int iy = blockIdx.x;
     const double qm = *qmax;
     const int per = (nx + blockDim.x - 1) / blockDim.x;
@@ -197,8 +204,11 @@ cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView
     double* part = scratch;
     long long* row_tot = (long long*)(scratch + kCdfParts);
     cdf_reduce_kernel<<<kCdfParts, 256, 0, stream>>>(cell_w, nx * ny, part, qmax_out);
-    cdf_total_kernel<<<1, 32, 0, stream>>>(part, kCdfParts, W_out);
-    cdf_rows_kernel<<<ny, 256, 0, stream>>>(cell_w, qmax_out, nx, ny, cdf, row_tot, reinterpret_cast<unsigned*>(part));
+    e = launch_pdl(cdf_total_kernel, dim3(1), dim3(32), 0, stream, part, (int)kCdfParts, W_out);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(cdf_rows_kernel, dim3(ny), dim3(256), 0, stream, cell_w, (const double*)qmax_out, nx, ny, cdf,
+                   row_tot, reinterpret_cast<unsigned*>(part));
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -214,6 +224,8 @@ __global__ void remap_density_kernel(int ncells, double adt, const double* __res
                                      const double* __restrict__ pre, const double* __restrict__ post,
                                      const double* __restrict__ phi, double* f, float* f32, int* fpos, double* q,
                                      DevState* st, int relabel) {
+    pdl_wait();
+    pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double r = 0;
     if (k < ncells) {
@@ -245,6 +257,8 @@ __host__ __device__ inline double pow2_ceil(double w) {
 // the births (steps 3'/4'), whose weights are bounded by the step-start bank's and by the leg's
 // birth weight w_lead
 __global__ void remap_prep_kernel(DevState* st, long long n_hist, long long lead, double w_lead) {
+    pdl_wait();
+    pdl_trigger();
     const double W = st->remap_W;
     const double wbar = W > 0 ? W / (double)n_hist : 0.0;
     st->r_lead = lead;
@@ -460,6 +474,8 @@ __device__ __forceinline__ RemapScal remap_scalars(const DevState* st, long long
 
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
     uint32_t* sSh = sm + a.ntab * kNibbleWords;
@@ -705,6 +721,8 @@ static cudaError_t sort_census(hyb_problem* p, const BankView<T>& stg, long long
 // one block: exclusive scan of block counts and quantised sums; totals, comb decision
 __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long long cap, uint64_t seed, int sampler,
                                   long long n_hist) {
+    pdl_wait();
+    pdl_trigger();
     const uint32_t x_off = first_point(dstream_key(seed, (uint64_t)st->step, HYB_STREAM_REMAP_COMB), sampler);
     __shared__ long long sc[1024], sq[1024];
     __shared__ unsigned long long slo[1024], shi[1024];
@@ -822,6 +840,8 @@ __device__ __forceinline__ long long first_tooth(long long S, long long M, long 
 
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ long long s_c[kTile / 32], s_q[kTile / 32];
     __shared__ RemapScal s_rs;
     if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
@@ -903,6 +923,8 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
 }
 
 __global__ void remap_finish_kernel(DevState* st) {
+    pdl_wait();
+    pdl_trigger();
     st->n_bank = st->out_count;
     st->step += 1;              // census of t_{n+1}: the next leg belongs to step n + 1
 }
@@ -914,6 +936,9 @@ static cudaError_t remap_t(hyb_problem* p) {
     const int g = (p->ncells + 255) / 256;
     cudaError_t e = cudaMemsetAsync(&p->st->remap_rmax, 0, sizeof(double), s);
     if (e != cudaSuccess) return e;
+    // zero the remap counters (here, so that no memset separates the kernels below)
+    e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
+    if (e != cudaSuccess) return e;
     const bool additive = p->d.remap_variant == 1;
     remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_d, p->post_d,
                                            p->sn_phi_d, p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st,
@@ -923,7 +948,8 @@ static cudaError_t remap_t(hyb_problem* p) {
     // steps 3'/4': the leg's census (bank slots, then its n_hist source births) leads the slots
     const long long lead = additive && p->has_src ? p->d.n_hist : 0;
     const double w_lead = additive && p->has_src ? p->w_src / (double)p->d.n_hist : 0.0;
-    remap_prep_kernel<<<1, 1, 0, s>>>(p->st, p->d.n_hist, lead, w_lead);
+    e = launch_pdl(remap_prep_kernel, dim3(1), dim3(1), 0, s, p->st, (long long)p->d.n_hist, lead, w_lead);
+    if (e != cudaSuccess) return e;
 
     RemapArgs<T> a;
     a.nx = p->nx; a.ny = p->ny;
@@ -952,23 +978,24 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.lead_staged = additive ? 1 : 0;
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
     const size_t smem = (size_t)(a.ntab * kNibbleWords + a.ntab + 1) * sizeof(uint32_t);
-    // zero the remap counters
-    e = cudaMemsetAsync(&p->st->r_histories, 0,
-                        (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
-    if (e != cudaSuccess) return e;
     a.perm = nullptr;
     a.nslots = maxN;
     a.perm_slots = p->d.census_order >= 1 ? 1 : 0;
-    remap_count_kernel<T><<<nblk, kTile, smem, s>>>(a);
+    e = launch_pdl(remap_count_kernel<T>, dim3(nblk), dim3(kTile), smem, s, a);
+    if (e != cudaSuccess) return e;
     if (p->d.census_order >= 1) {
         // survivors in cell (or phase-space) order, stable: the comb and the census write follow it
         e = sort_census<T>(p, a.stg, maxN, s, &a.perm);
         if (e != cudaSuccess) return e;
         remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);
     }
-    remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nblk, p->st, a.cap, a.seed, a.sampler, p->d.n_hist);
-    remap_write_kernel<T><<<nblk, kTile, 0, s>>>(a);
-    remap_finish_kernel<<<1, 1, 0, s>>>(p->st);
+    e = launch_pdl(remap_scan_kernel, dim3(1), dim3(1024), 0, s, p->blk, nblk, p->st, a.cap, a.seed, a.sampler,
+                   (long long)p->d.n_hist);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(remap_write_kernel<T>, dim3(nblk), dim3(kTile), 0, s, a);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(remap_finish_kernel, dim3(1), dim3(1), 0, s, p->st);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

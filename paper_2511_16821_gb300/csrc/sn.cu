@@ -25,33 +25,13 @@
 #include <utility>
 
 #include "hyb_device.cuh"
+#include "pdl.cuh"
 
 namespace hyb {
 
-// Programmatic dependent launch between the source iteration's kernels: each sweep and reduction
-// is launched with programmatic stream serialisation, lets its successor be scheduled as soon as it
-// starts (launch_dependents), and waits for its predecessor's completion and memory (wait) before
-// it reads anything the predecessor wrote. The successor's blocks are then resident when the
-// predecessor ends, instead of being launched after it. Without a programmatic predecessor the
-// wait returns at once.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
-                              Args&&... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
-}
+// Each sweep and reduction of the source iteration is launched as a programmatic dependent of its
+// predecessor (pdl.cuh): it waits for the predecessor before reading, and lets its successor be
+// scheduled as soon as it starts.
 
 // Padded mesh of the sweep's sources: every row carries kHalo columns on both sides, and one extra
 // row follows the last; halo and extra row are zero. A lane before its row's first column, past its
