@@ -705,6 +705,7 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     p->cur = 0;
     p->ndims = d->n_s == HYB_NS_INF ? HYB_SOBOL_DIMS : 5 + 3 * d->n_s;   // dims past the table: counter hash
     p->leg_done = p->sn_done = false;
+    p->pdl = true;
     p->sn_warm = false;
     p->ev0 = p->ev1 = nullptr;
     for (auto& e : p->evs) e = nullptr;
@@ -929,6 +930,7 @@ static hyb_status remap_launch(hyb_problem* p) {
     p->cur = 1 - p->cur;
     p->step += 1;           // the remap's last kernel advances the device step
     p->leg_done = p->sn_done = false;
+    p->pdl = true;
     return HYB_OK;
 }
 
@@ -1069,6 +1071,7 @@ hyb_status hyb_set_step(hyb_problem* p, int64_t step) {
     HYB_CU(p, cudaMemcpyAsync(&p->st->step, &p->st_host->step, sizeof(long long), cudaMemcpyHostToDevice, p->stream));
     HYB_CU(p, cudaStreamSynchronize(p->stream));
     p->leg_done = p->sn_done = false;
+    p->pdl = true;
     return HYB_OK;
 }
 

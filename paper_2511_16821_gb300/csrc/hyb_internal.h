@@ -144,6 +144,8 @@ struct hyb_problem {
                               //   mesh, or per direction the wavefront order (solves too large for L2)
     void* sn_psi;             // psi_m per ordinate, mirrored coordinates (T): plain mesh or wavefront order
     void* sn_table;           // cell-solve table per ordinate class and padded cell (T), or null
+    bool pdl;                 // launch the source iteration's and the remap's kernels as programmatic
+                              //   dependents (true when stepped alone; a batch turns it off)
     void* sn_quadbuf;         // ordinates (ox, oy, w) x kMaxOrd, then 4 signed weights per ordinate (T)
     double* sn_phi_d;         // collided flux, FP64 copy (4 x ncells)
     double* sn_phi_d2;        // the solution of the step before (extrapolated warm start only)
@@ -178,7 +180,7 @@ cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w_dev, Cdf2DView
                              double* qmax_out_dev);
 cudaError_t launch_flux(hyb_problem* p);
 cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
-                                 double* qmax_out, double* scratch, cudaStream_t stream);
+                                 double* qmax_out, double* scratch, cudaStream_t stream, bool pdl = false);
 cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0);
 cudaError_t launch_census_sort(const int32_t* cells, long long n, uint32_t ncells, unsigned long long* const pairs[2],
                                uint32_t* counts, cudaStream_t s, const unsigned long long** sorted);

@@ -198,22 +198,22 @@ __device__ __forceinline__ long long block_exclusive_scan(long long v, long long
 // scratch: kCdfParts doubles of block partial sums (the first word then the rows' arrival
 // counter), then ny int64 row totals
 cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
-                                 double* qmax_out, double* scratch, cudaStream_t stream) {
+                                 double* qmax_out, double* scratch, cudaStream_t stream, bool pdl) {
     cudaError_t e = cudaMemsetAsync(qmax_out, 0, sizeof(double), stream);
     if (e != cudaSuccess) return e;
     double* part = scratch;
     long long* row_tot = (long long*)(scratch + kCdfParts);
     cdf_reduce_kernel<<<kCdfParts, 256, 0, stream>>>(cell_w, nx * ny, part, qmax_out);
-    e = launch_pdl(cdf_total_kernel, dim3(1), dim3(32), 0, stream, part, (int)kCdfParts, W_out);
+    e = launch_pdl(pdl, cdf_total_kernel, dim3(1), dim3(32), 0, stream, part, (int)kCdfParts, W_out);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(cdf_rows_kernel, dim3(ny), dim3(256), 0, stream, cell_w, (const double*)qmax_out, nx, ny, cdf,
+    e = launch_pdl(pdl, cdf_rows_kernel, dim3(ny), dim3(256), 0, stream, cell_w, (const double*)qmax_out, nx, ny, cdf,
                    row_tot, reinterpret_cast<unsigned*>(part));
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w, Cdf2DView cdf, double* W_out, double* qmax_out) {
-    return launch_cdf_build_raw(cell_w, p->nx, p->ny, cdf, W_out, qmax_out, p->cell_scratch, p->stream);
+    return launch_cdf_build_raw(cell_w, p->nx, p->ny, cdf, W_out, qmax_out, p->cell_scratch, p->stream, p->pdl);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -948,7 +948,7 @@ static cudaError_t remap_t(hyb_problem* p) {
     // steps 3'/4': the leg's census (bank slots, then its n_hist source births) leads the slots
     const long long lead = additive && p->has_src ? p->d.n_hist : 0;
     const double w_lead = additive && p->has_src ? p->w_src / (double)p->d.n_hist : 0.0;
-    e = launch_pdl(remap_prep_kernel, dim3(1), dim3(1), 0, s, p->st, (long long)p->d.n_hist, lead, w_lead);
+    e = launch_pdl(p->pdl, remap_prep_kernel, dim3(1), dim3(1), 0, s, p->st, (long long)p->d.n_hist, lead, w_lead);
     if (e != cudaSuccess) return e;
 
     RemapArgs<T> a;
@@ -981,7 +981,7 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.perm = nullptr;
     a.nslots = maxN;
     a.perm_slots = p->d.census_order >= 1 ? 1 : 0;
-    e = launch_pdl(remap_count_kernel<T>, dim3(nblk), dim3(kTile), smem, s, a);
+    e = launch_pdl(p->pdl, remap_count_kernel<T>, dim3(nblk), dim3(kTile), smem, s, a);
     if (e != cudaSuccess) return e;
     if (p->d.census_order >= 1) {
         // survivors in cell (or phase-space) order, stable: the comb and the census write follow it
@@ -989,12 +989,12 @@ static cudaError_t remap_t(hyb_problem* p) {
         if (e != cudaSuccess) return e;
         remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);
     }
-    e = launch_pdl(remap_scan_kernel, dim3(1), dim3(1024), 0, s, p->blk, nblk, p->st, a.cap, a.seed, a.sampler,
+    e = launch_pdl(p->pdl, remap_scan_kernel, dim3(1), dim3(1024), 0, s, p->blk, nblk, p->st, a.cap, a.seed, a.sampler,
                    (long long)p->d.n_hist);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(remap_write_kernel<T>, dim3(nblk), dim3(kTile), 0, s, a);
+    e = launch_pdl(p->pdl, remap_write_kernel<T>, dim3(nblk), dim3(kTile), 0, s, a);
     if (e != cudaSuccess) return e;
-    e = launch_pdl(remap_finish_kernel, dim3(1), dim3(1), 0, s, p->st);
+    e = launch_pdl(p->pdl, remap_finish_kernel, dim3(1), dim3(1), 0, s, p->st);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -142,6 +142,8 @@ template <typename T>
 __global__ void sn_source_kernel(int ncells, CellSplit split, int wave, Wave<T> wv, const T* sig, T* phi_old,
                                  const double* prev, const double* prev2, const DevState* st, int extrap,
                                  const double* mom, T area, T inv_4pi_dt, T inv_cdt, T* src, T* sgA) {
+    pdl_wait();
+    pdl_trigger();   // the first sweep may be scheduled now; it waits for this kernel before reading
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ncells) return;
     int ix, iy;
@@ -1032,7 +1034,7 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    cudaError_t le = launch_pdl(kern, dim3(p->n_ord), dim3(32 * a.W), smem, s, a);
+    cudaError_t le = launch_pdl(p->pdl, kern, dim3(p->n_ord), dim3(32 * a.W), smem, s, a);
     if (le != cudaSuccess) return le;
     const int gr = (p->ncells + kRedCells - 1) / kRedCells;
     const RedScratch rs = red_scratch(p);
@@ -1046,7 +1048,7 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
                  : depth == 3 ? sn_reduce_aa_kernel<T, 4> : depth == 4 ? sn_reduce_aa_kernel<T, 5>
                  : depth == 5 ? sn_reduce_aa_kernel<T, 6> : depth == 6 ? sn_reduce_aa_kernel<T, 7>
                  : depth == 7 ? sn_reduce_aa_kernel<T, 8> : sn_reduce_aa_kernel<T, 9>;
-        le = launch_pdl(red, dim3(gr), dim3(kRedCells * kRedGroups), 0, s, (const T*)p->sn_psi, p->n_ord, nq, wave, wv,
+        le = launch_pdl(p->pdl, red, dim3(gr), dim3(kRedCells * kRedGroups), 0, s, (const T*)p->sn_psi, p->n_ord, nq, wave, wv,
                         split, qwv, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, gh, fh, depth,
                         (AAState*)p->aa_state, p->st, sn_tol_eff(p));
         if (le != cudaSuccess) return le;
@@ -1056,7 +1058,7 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
                                                                       inv4pidt, split, wave, wv, src);
         return cudaGetLastError();
     }
-    le = launch_pdl(sn_reduce_kernel<T>, dim3(gr), dim3(kRedCells * kRedGroups), 0, s, (const T*)p->sn_psi, p->n_ord,
+    le = launch_pdl(p->pdl, sn_reduce_kernel<T>, dim3(gr), dim3(kRedCells * kRedGroups), 0, s, (const T*)p->sn_psi, p->n_ord,
                     nq, wave, wv, qwv, split, (const T*)p->sn_phi_old, (T*)p->sn_phi, p->ncells, rs, (const T*)p->sig,
                     p->mom_d, (T)p->area, inv4pidt, src, p->st, sn_tol_eff(p));
     if (le != cudaSuccess) return le;
