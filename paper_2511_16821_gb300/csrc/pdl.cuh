@@ -8,7 +8,8 @@
 // memory is visible); it calls pdl_trigger() to let its own successor be scheduled. Without a
 // programmatic predecessor the wait returns at once. A successor is scheduled only after every
 // block of its predecessor has started, so waiting blocks never hold resources the predecessor
-// still needs.
+// still needs. Problems stepped in a batch launch normally (their step graphs run many streams
+// at once, where programmatic launch measured slower).
 #pragma once
 
 #include <cuda_runtime.h>

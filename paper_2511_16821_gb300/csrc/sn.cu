@@ -29,9 +29,9 @@
 
 namespace hyb {
 
-// Each sweep and reduction of the source iteration is launched as a programmatic dependent of its
-// predecessor (pdl.cuh): it waits for the predecessor before reading, and lets its successor be
-// scheduled as soon as it starts.
+// Each sweep and reduction of the source iteration of a problem stepped alone (hyb_problem::pdl) is
+// launched as a programmatic dependent of its predecessor (pdl.cuh): it waits for the predecessor
+// before reading, and lets its successor be scheduled as soon as it starts.
 
 // Padded mesh of the sweep's sources: every row carries kHalo columns on both sides, and one extra
 // row follows the last; halo and extra row are zero. A lane before its row's first column, past its
