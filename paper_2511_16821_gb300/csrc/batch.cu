@@ -258,12 +258,10 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         if (p->d.remap_variant != 0) return bfail(b, HYB_EINVAL, "the additive remap variant is stepped alone");
         probs.push_back(p);
     }
+    if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");
     // programmatic dependent launch is kept for problems stepped alone: in the batch's multi-stream
     // step graphs it measured slower (256 problems: 73 -> 101 ms per step)
-    for (hyb_problem* p : probs) {
-        p->pdl = false;
-    }
-    if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");
+    for (hyb_problem* p : probs) p->pdl = false;
     b->prec = prec;
     b->probs = probs;
     b->cur0.clear(); b->kmax.clear();
