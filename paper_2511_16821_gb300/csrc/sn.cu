@@ -688,8 +688,8 @@ sn_reduce_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, const T* 
     const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
     const int k0 = blockIdx.x * kRedCells;
     pdl_wait();
-    pdl_trigger();
     if (*(volatile const int*)&st->sn_conv) {
+        pdl_trigger();
         // converged earlier: carry the solution forward so the buffer alternation stays aligned
         if (threadIdx.x < kRedCells * 4) {
             const size_t e = (size_t)k0 * 4 + threadIdx.x;
@@ -735,6 +735,7 @@ sn_reduce_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, const T* 
         rs.part[2 * blockIdx.x + 1] = b;
         __threadfence();
     }
+    pdl_trigger();   // late: the next sweep is scheduled as this reduction completes
     if (reduce_partials<2>(rs.part, (int)gridDim.x, rs.gpart, rs.gcnt, &st->sn_blocks_done, s_tot) &&
         threadIdx.x == 0) {
         const double a = s_tot[0], b = s_tot[1];
@@ -814,8 +815,8 @@ sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSp
     const int c = threadIdx.x % kRedCells, g = threadIdx.x / kRedCells;
     const int k0 = blockIdx.x * kRedCells;
     pdl_wait();
-    pdl_trigger();
     if (*(volatile const int*)&st->sn_conv) {
+        pdl_trigger();
         if (threadIdx.x < kRedCells * 4) {
             const size_t e = (size_t)k0 * 4 + threadIdx.x;
             if (e < (size_t)ncells * 4) phi_new[e] = phi_old[e];
@@ -871,6 +872,7 @@ sn_reduce_aa_kernel(const T* psi, int nord, int nq, int wave, Wave<T> wv, CellSp
         rs.part[(size_t)blockIdx.x * NP + threadIdx.x] = a;
         __threadfence();
     }
+    pdl_trigger();   // late: the next sweep is scheduled as this reduction completes
     if (reduce_partials<NP>(rs.part, (int)gridDim.x, rs.gpart, rs.gcnt, &st->sn_blocks_done, s_tot) &&
         threadIdx.x == 0) {
         int slots[kAAMax + 1];
