@@ -272,7 +272,8 @@ HYB_API hyb_status hyb_batch_destroy(hyb_batch* b);
 HYB_API const char* hyb_batch_last_error(const hyb_batch* b);
 
 /* Integer 2-D CDF over cells (the sampling map of Sec. 2.3 births and of the Eq. (R) remap):
- * q_k = rint(|w_k| / max|w| 2^40); col_pre: per row the exclusive prefix of q over the row's cells
+ * q_k = rint(|w_k| / max|w| 2^B), B = min(40, 62 - ceil(log2(nx*ny))) so that the total stays below
+ * 2^62 on every accepted mesh (B = 40 up to 2^22 cells); col_pre: per row the exclusive prefix of q over the row's cells
  * (ny x (nx+1), last entry = row total); row_pre: exclusive prefix of the row totals (ny+1).
  * w_dev: nx*ny FP64 cell weights (device, sign ignored). W_qmax_dev: two device doubles written
  * with sum|w| and max|w|. scratch_dev: caller-owned device scratch of >= hyb_cdf_scratch_bytes

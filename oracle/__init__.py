@@ -10,6 +10,7 @@ Sec. 2.4 (QMC points), App. B (Erlang transfer law, used as a pin).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import os
 import subprocess
@@ -22,6 +23,24 @@ _SRC = os.path.join(_HERE, "oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 NS_INF = 2147483647
+# Evaluation of the direction and optical-depth maps sin/cos(2 pi u), -log u (Sec. 2.3-2.4):
+# LIBM = the host libm (the default, the plain reading of the paper's maps); SERIES = explicit
+# series in a fixed operation order, pinned to a 40-digit reference (the recipe the GPU FP64 path
+# also follows, so comparing with it checks the rest of that path bit for bit).
+LIBM, SERIES = 0, 1
+_elem_default = LIBM
+
+
+@contextlib.contextmanager
+def elementary(mode: int):
+    """Evaluate the maps with `mode` (LIBM or SERIES) inside the block."""
+    global _elem_default
+    old = _elem_default
+    _elem_default = mode
+    try:
+        yield
+    finally:
+        _elem_default = old
 STREAM_INIT, STREAM_LEG_CENSUS, STREAM_LEG_SOURCE, STREAM_REMAP_SOURCE, STREAM_REMAP_COMB = range(5)
 FATE_LEAKED, FATE_CENSUS, FATE_KILLED, FATE_ERROR = range(4)
 
@@ -44,7 +63,7 @@ class _Problem(C.Structure):
                 ("seed", C.c_uint64), ("sn_order", C.c_int32), ("handoff_full", C.c_int32),
                 ("w_min", C.c_double), ("census_cap", C.c_int64), ("sn_tol", C.c_double),
                 ("sn_max_iter", C.c_int32), ("census_order", C.c_int32), ("remap_variant", C.c_int32),
-                ("n_s_cell", C.POINTER(C.c_int32))]
+                ("n_s_cell", C.POINTER(C.c_int32)), ("elem", C.c_int32), ("pad", C.c_int32)]
 
 
 class _Bank(C.Structure):
@@ -95,7 +114,7 @@ class _Keep:
     nsc: np.ndarray | None = None
 
 
-def _problem(spec) -> tuple[_Problem, _Keep]:
+def _problem(spec, elem: int | None = None) -> tuple[_Problem, _Keep]:
     sa = np.ascontiguousarray(spec.sigma_a, dtype=np.float64).ravel()
     ss = np.ascontiguousarray(spec.sigma_s, dtype=np.float64).ravel()
     q = None if spec.Q is None else np.ascontiguousarray(spec.Q, dtype=np.float64).ravel()
@@ -108,7 +127,8 @@ def _problem(spec) -> tuple[_Problem, _Keep]:
                  sn_tol=spec.sn_tol, sn_max_iter=spec.sn_max_iter,
                  census_order=getattr(spec, "census_order", 0),
                  remap_variant=getattr(spec, "remap_variant", 0),
-                 n_s_cell=None if nsc is None else nsc.ctypes.data_as(C.POINTER(C.c_int32)))
+                 n_s_cell=None if nsc is None else nsc.ctypes.data_as(C.POINTER(C.c_int32)),
+                 elem=_elem_default if elem is None else elem)
     return p, _Keep(sa, ss, q, nsc)
 
 
@@ -161,8 +181,8 @@ def quadrature(order: int):
     return ox[:m], oy[:m], oz[:m], w[:m]
 
 
-def init_bank(spec, ic_cell_w: np.ndarray) -> dict:
-    p, keep = _problem(spec)
+def init_bank(spec, ic_cell_w: np.ndarray, elem: int | None = None) -> dict:
+    p, keep = _problem(spec, elem)
     b = empty_bank(spec.n_hist)
     cb = _bank(b)
     icw = np.ascontiguousarray(ic_cell_w, dtype=np.float64).ravel()
@@ -171,8 +191,8 @@ def init_bank(spec, ic_cell_w: np.ndarray) -> dict:
     return _trim(b, cb.n)
 
 
-def sample_births(spec, step: int, n: int):
-    p, keep = _problem(spec)
+def sample_births(spec, step: int, n: int, elem: int | None = None):
+    p, keep = _problem(spec, elem)
     cell = np.zeros(n, np.int32)
     fx, fy, ox, oy, tf = (np.zeros(n) for _ in range(5))
     w0 = C.c_double(0)
@@ -182,38 +202,55 @@ def sample_births(spec, step: int, n: int):
     return dict(cell=cell, fx=fx, fy=fy, ox=ox, oy=oy, t_frac=tf, w0=w0.value)
 
 
-def mc_leg(spec, step: int, bank: dict | None, want_hist: bool = False, want_census: bool = False):
-    """Returns dict(pre, post, mom, stats, hist?, census?); tallies are raw track-length sums."""
-    p, keep = _problem(spec)
+def n_histories(spec, bank: dict | None) -> int:
+    """Histories of a leg: the bank's particles, then n_hist births when Q is not zero."""
+    nb = 0 if bank is None else int(bank.get("n", len(bank["w"])))
+    has_src = spec.Q is not None and float(np.sum(spec.Q)) > 0
+    return nb + (spec.n_hist if has_src else 0)
+
+
+def mc_leg(spec, step: int, bank: dict | None, want_hist: bool = False, want_census: bool = False,
+           want_margin: bool = False, h0: int = 0, h1: int | None = None, skip: np.ndarray | None = None,
+           elem: int | None = None):
+    """Returns dict(pre, post, mom, stats, pre_n, post_n, hist?, margin?, census?); tallies are raw
+    track-length sums. Only histories with global index in [h0, h1) and skip[h] == 0 are tracked
+    (skip: uint8 per history, or None); hist / margin rows cover those, in index order."""
+    p, keep = _problem(spec, elem)
     nc = spec.nx * spec.ny
     pre, post, mom = np.zeros(nc), np.zeros(nc), np.zeros(4 * nc)
     st = _Stats()
     cb = _bank(bank)
-    nb = 0 if bank is None else int(bank.get("n", len(bank["w"])))
-    has_src = spec.Q is not None and float(np.sum(spec.Q)) > 0
-    nh = nb + (spec.n_hist if has_src else 0)
-    hist = np.zeros((max(nh, 1), 4), np.int32) if want_hist else None
+    nh = n_histories(spec, bank)
+    h1 = nh if h1 is None else min(h1, nh)
+    nr = max(h1 - h0, 0)
+    hist = np.zeros((max(nr, 1), 4), np.int32) if want_hist else None
+    marg = np.zeros(max(nr, 1)) if want_margin else None
     cens = empty_bank(max(nh, 1)) if want_census else None
     cc = _bank(cens)
     pre_n, post_n = np.zeros(nc, np.int64), np.zeros(nc, np.int64)
+    if skip is not None:
+        skip = np.ascontiguousarray(skip, dtype=np.uint8)
+        assert skip.size >= nh
     P64 = C.POINTER(C.c_int64)
-    rc = lib().or_mc_leg_counts(C.byref(p), C.c_int64(step), C.byref(cb) if cb else None, _dp(pre), _dp(post),
-                                _dp(mom), C.byref(st), _ip(hist) if hist is not None else None,
-                                C.byref(cc) if cc else None, pre_n.ctypes.data_as(P64),
-                                post_n.ctypes.data_as(P64))
-    out = dict(pre=pre, post=post, mom=mom.reshape(nc, 4), stats=_stats_dict(st), rc=rc,
-               pre_n=pre_n, post_n=post_n)
+    rc = lib().or_mc_leg_ex(C.byref(p), C.c_int64(step), C.byref(cb) if cb else None, C.c_int64(h0), C.c_int64(h1),
+                            skip.ctypes.data_as(C.c_void_p) if skip is not None else None, _dp(pre), _dp(post),
+                            _dp(mom), C.byref(st), _ip(hist) if hist is not None else None, _dp(marg),
+                            C.byref(cc) if cc else None, pre_n.ctypes.data_as(P64), post_n.ctypes.data_as(P64))
+    s = _stats_dict(st)
+    out = dict(pre=pre, post=post, mom=mom.reshape(nc, 4), stats=s, rc=rc, pre_n=pre_n, post_n=post_n)
     if want_hist:
-        out["hist"] = hist[:nh]
+        out["hist"] = hist[: s["histories"]]
+    if want_margin:
+        out["margin"] = marg[: s["histories"]]
     if want_census:
         out["census"] = _trim(cens, cc.n)
     return out
 
 
-def mc_leg_range(spec, step: int, bank: dict | None, h0: int, h1: int):
+def mc_leg_range(spec, step: int, bank: dict | None, h0: int, h1: int, elem: int | None = None):
     """The leg over global history indices [h0, h1) (bank slots first, then births), as one rank
     of a history-sharded leg: dict(pre, post, mom, stats, hist) for that range only."""
-    p, keep = _problem(spec)
+    p, keep = _problem(spec, elem)
     nc = spec.nx * spec.ny
     pre, post, mom = np.zeros(nc), np.zeros(nc), np.zeros(4 * nc)
     st = _Stats()
@@ -225,8 +262,8 @@ def mc_leg_range(spec, step: int, bank: dict | None, h0: int, h1: int):
     return dict(pre=pre, post=post, mom=mom.reshape(nc, 4), stats=s, rc=rc, hist=hist[: s["histories"]])
 
 
-def sn_solve(spec, mom: np.ndarray):
-    p, keep = _problem(spec)
+def sn_solve(spec, mom: np.ndarray, elem: int | None = None):
+    p, keep = _problem(spec, elem)
     nc = spec.nx * spec.ny
     m = np.ascontiguousarray(mom, dtype=np.float64).ravel()
     phi = np.zeros(4 * nc)
@@ -247,8 +284,8 @@ def dg_sweep(nx, ny, lx, ly, sig, ox, oy, S, in_x=None, in_y=None):
     return psi.reshape(nx * ny, 4)
 
 
-def remap_density(spec, pre, post, phi):
-    p, keep = _problem(spec)
+def remap_density(spec, pre, post, phi, elem: int | None = None):
+    p, keep = _problem(spec, elem)
     nc = spec.nx * spec.ny
     f = np.zeros(4 * nc)
     args = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (pre, post, phi)]
@@ -256,8 +293,8 @@ def remap_density(spec, pre, post, phi):
     return f.reshape(nc, 4)
 
 
-def remap(spec, step: int, bank: dict | None, pre, post, phi):
-    p, keep = _problem(spec)
+def remap(spec, step: int, bank: dict | None, pre, post, phi, elem: int | None = None):
+    p, keep = _problem(spec, elem)
     nb = 0 if bank is None else int(bank.get("n", len(bank["w"])))
     cap = nb + spec.n_hist
     out = empty_bank(max(cap, 1))
@@ -272,9 +309,9 @@ def remap(spec, step: int, bank: dict | None, pre, post, phi):
     return res, _stats_dict(st), bool(combed.value)
 
 
-def phase_keys(spec, bank: dict):
+def phase_keys(spec, bank: dict, elem: int | None = None):
     """The census_order-2 keys of the particles of a bank and the bits per coordinate."""
-    p, keep = _problem(spec)
+    p, keep = _problem(spec, elem)
     cb = _bank(bank)
     n = int(bank.get("n", len(bank["w"])))
     out = np.zeros(max(n, 1), np.uint32)
@@ -282,10 +319,10 @@ def phase_keys(spec, bank: dict):
     return out[:n], bits
 
 
-def remap_additive(spec, step: int, bank: dict | None, leg_census: dict | None, post, phi):
+def remap_additive(spec, step: int, bank: dict | None, leg_census: dict | None, post, phi, elem: int | None = None):
     """Steps 3' and 4' (the previous hybrids' remap): the leg census followed by the survivors of
     births from sigma_s (phi_post + phi_c), combed. bank: the step-start bank."""
-    p, keep = _problem(spec)
+    p, keep = _problem(spec, elem)
     nb = 0 if bank is None else int(bank.get("n", len(bank["w"])))
     nl = 0 if leg_census is None else int(leg_census.get("n", len(leg_census["w"])))
     out = empty_bank(max(nl + spec.n_hist, 1))
@@ -300,8 +337,8 @@ def remap_additive(spec, step: int, bank: dict | None, leg_census: dict | None, 
     return _trim(out, co.n), _stats_dict(st), bool(combed.value)
 
 
-def step(spec, step_index: int, bank: dict | None):
-    p, keep = _problem(spec)
+def step(spec, step_index: int, bank: dict | None, elem: int | None = None):
+    p, keep = _problem(spec, elem)
     nc = spec.nx * spec.ny
     nb = 0 if bank is None else int(bank.get("n", len(bank["w"])))
     cap = nb + 2 * spec.n_hist
@@ -328,15 +365,15 @@ def build_cdf(nx: int, ny: int, w: np.ndarray):
     return q, rp, cp
 
 
-def sincos_2pi(u: np.ndarray):
+def sincos_2pi(u: np.ndarray, elem: int | None = None):
     u = np.ascontiguousarray(u, dtype=np.float64)
     s, c = np.zeros_like(u), np.zeros_like(u)
-    lib().or_sincos_2pi(_dp(u), C.c_int64(u.size), _dp(s), _dp(c))
+    lib().or_sincos_2pi(_dp(u), C.c_int64(u.size), _dp(s), _dp(c), C.c_int32(_elem_default if elem is None else elem))
     return s, c
 
 
-def neg_log(u: np.ndarray):
+def neg_log(u: np.ndarray, elem: int | None = None):
     u = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros_like(u)
-    lib().or_neg_log(_dp(u), C.c_int64(u.size), _dp(out))
+    lib().or_neg_log(_dp(u), C.c_int64(u.size), _dp(out), C.c_int32(_elem_default if elem is None else elem))
     return out

@@ -261,6 +261,8 @@ typedef struct {
                             // phase space (Morton order of in-cell x, y and direction angle)
     int32_t remap_variant;  // 0: Eq. (R) relabelling remap; 1: steps 3'/4' (additive, previous hybrids)
     const int32_t* n_s_cell;  // nx*ny scatter limits per cell in [0, n_s] (space-dependent N_s), or NULL
+    int32_t elem;             // evaluation of sin/cos(2 pi u) and -log u: 0 host libm, 1 explicit series
+    int32_t pad;
 } or_problem;
 
 typedef struct {
@@ -297,7 +299,8 @@ bool bank_push(or_bank* b, int32_t cell, double fx, double fy, double ox, double
 
 // ------------------------------------------------------------------------------------------
 // Integer 2-D CDF over cells (row marginal, then the column conditional within the row).
-// Weights are quantised q_k = rint(|w_k| / max|w| * 2^40); a point x (32-bit) selects by the
+// Weights are quantised q_k = rint(|w_k| / max|w| * 2^B) with B = min(40, 62 - ceil(log2 ncells)),
+// so the total stays below 2^62 on every mesh (B = 40 up to 2^22 cells); a point x (32-bit) selects by the
 // exact product (2x+1) * total / 2^33, so selection is exact integer arithmetic and the
 // remainder gives the uniform in-cell fraction.
 // ------------------------------------------------------------------------------------------
@@ -312,9 +315,12 @@ Cdf2D build_cdf(const Mesh& M, const std::vector<double>& w) {
     double wmax = 0.0;
     for (double v : w) wmax = std::max(wmax, std::fabs(v));
     C.q.assign(w.size(), 0);
+    int lg = 0;
+    while (((size_t)1 << lg) < w.size()) ++lg;
+    const double scale = std::ldexp(1.0, std::min(40, 62 - lg));
     if (wmax > 0.0)
         for (size_t k = 0; k < w.size(); ++k)
-            C.q[k] = (int64_t)std::nearbyint((std::fabs(w[k]) / wmax) * 0x1p40);
+            C.q[k] = (int64_t)std::nearbyint((std::fabs(w[k]) / wmax) * scale);
     C.row_pre.assign(M.ny + 1, 0);
     C.col_pre.assign((size_t)M.ny * (M.nx + 1), 0);
     for (int iy = 0; iy < M.ny; ++iy) {
@@ -357,9 +363,11 @@ int sample_cell(const Cdf2D& C, uint32_t x0, uint32_t x1, double* frac_x, double
     return iy * C.nx + ix;
 }
 
-// sin and cos of 2 pi u for a point uniform u, and -log u, evaluated by explicit series with
-// IEEE operations in a fixed order (so that any implementation written to the same recipe gives
-// the same bits):
+// Second evaluation mode (elem = 1) of sin and cos of 2 pi u for a point uniform u, and of -log u:
+// explicit series with IEEE operations in a fixed order, so that any implementation written to the
+// same recipe gives the same bits (the GPU FP64 path evaluates the maps this way; comparing it with
+// this mode checks the rest of its arithmetic bit for bit, comparing it with the libm mode shows
+// how often a last-bit difference in a direction or optical depth changes a decision):
 //   2 pi u = 2 pi r + q pi/2 with q = rint(4u), r = u - q/4 in [-1/8, 1/8] (both exact), Taylor
 //   series of sin and cos of a = 2 pi r to a^17 / a^18, then the quadrant rotation;
 //   u = m 2^e with m in [1/sqrt2, sqrt2), log m = 2 atanh(s), s = (m-1)/(m+1), series to s^23.
@@ -378,7 +386,13 @@ struct SeriesCoef {
 };
 const SeriesCoef kSer;
 
-void sincos_2pi(double u, double* s_out, double* c_out) {
+// Which evaluation of the direction and optical-depth maps the current call uses (set from the
+// problem's `elem` field at every entry point; the oracle is single-threaded): 0 = the host libm
+// (std::sin, std::cos of the rounded product 2 pi u, std::log), the plain reading of Sec. 2.3-2.4;
+// 1 = the explicit series below.
+int g_elem = 0;
+
+void sincos_2pi_series(double u, double* s_out, double* c_out) {
     const double q = std::nearbyint(4.0 * u);
     const double r = u - 0.25 * q;
     const double a = 6.283185307179586 * r;
@@ -396,7 +410,7 @@ void sincos_2pi(double u, double* s_out, double* c_out) {
     }
 }
 
-double neg_log(double u) {
+double neg_log_series(double u) {
     int e = 0;
     double m = std::frexp(u, &e);
     if (m < 0.7071067811865476) { m = 2.0 * m; e -= 1; }
@@ -407,6 +421,15 @@ double neg_log(double u) {
     const double lm = 2.0 * s * P;
     return -((double)e * 0.6931471805599453 + lm);
 }
+
+void sincos_2pi(double u, double* s_out, double* c_out) {
+    if (g_elem == 1) { sincos_2pi_series(u, s_out, c_out); return; }
+    const double a = 2.0 * kPi * u;
+    *s_out = std::sin(a);
+    *c_out = std::cos(a);
+}
+
+double neg_log(double u) { return g_elem == 1 ? neg_log_series(u) : -std::log(u); }
 
 // Isotropic direction: mu = 2u - 1, phi = 2 pi u'; the 2-D motion uses (Omega_x, Omega_y) and
 // the path length is the 3-D one (the domain is extruded in z).
@@ -461,8 +484,22 @@ struct Leg {
     // N_s(k) = n_s everywhere.
     int limit(int k) const { return P->n_s_cell ? P->n_s_cell[k] : P->n_s; }
 
+    // Decision margin of one segment: the event is the smallest of the candidate distances
+    // (collision, x face, y face, census); the relative gap (d2 - d1) / d2 between the two smallest
+    // says how far the decision is from a tie (0: an exact tie such as a corner; 1: one finite
+    // candidate). A last-bit change of a distance can only change a decision whose gap is of the
+    // order of the rounding error.
+    static double decision_gap(double dcol, double dxf, double dyf, double dcen) {
+        double d[4] = {dcol, dxf, dyf, dcen};
+        std::sort(d, d + 4);
+        if (!(d[1] < kInf)) return 1.0;
+        if (d[1] <= 0.0) return 0.0;
+        return (d[1] - d[0]) / d[1];
+    }
+
     void run(uint64_t idx, int ix, int iy, double fx, double fy, double ox, double oy,
-             double w, double s_rem, int32_t* rec) {
+             double w, double s_rem, int32_t* rec, double* margin = nullptr) {
+        double gap = 1.0;
         const int Ns = P->n_s;   // the largest limit: sets the point dimensions
         const double DX = M.dx, DY = M.dy;
         const double w_start = w;
@@ -482,6 +519,7 @@ struct Leg {
             const double dyf = oy > 0 ? (DY - fy) / oy : (oy < 0 ? fy / (-oy) : kInf);
             const double dcol = (n < Nk && ss > 0) ? tau / ss : kInf;
             const double dcen = s_rem;
+            if (margin) gap = std::min(gap, decision_gap(dcol, dxf, dyf, dcen));
             // event: collision wins ties over faces, faces over census
             double l; int ev; bool xc = false, yc = false;
             if (dcol <= dxf && dcol <= dyf && dcol <= dcen) { l = dcol; ev = 0; }
@@ -548,6 +586,7 @@ struct Leg {
                 tau = n < Ns ? neg_log(unit(pts(idx, 5 + 3 * n))) : 0.0;
                 if (n >= Nk) ++reached;
             }
+            if (margin && P->w_min > 0) gap = std::min(gap, std::fabs(w - P->w_min * w_start) / (P->w_min * w_start));
             if (P->w_min > 0 && w < P->w_min * w_start) {
                 fate = kFateKilled; ++killed; w_killed += w;
                 break;
@@ -556,6 +595,7 @@ struct Leg {
         segments += seg;
         if (fate == kFateError) ++errors;
         if (rec) { rec[0] = iy * M.nx + ix; rec[1] = fate; rec[2] = n; rec[3] = (int32_t)seg; }
+        if (margin) *margin = gap;
     }
 };
 
@@ -895,10 +935,12 @@ extern "C" {
 uint64_t or_mix64(uint64_t z) { return mix64(z); }
 
 // the direction and optical-depth maps, exposed for their accuracy pins
-void or_sincos_2pi(const double* u, int64_t n, double* s, double* c) {
+void or_sincos_2pi(const double* u, int64_t n, double* s, double* c, int32_t elem) {
+    g_elem = elem;
     for (int64_t i = 0; i < n; ++i) sincos_2pi(u[i], &s[i], &c[i]);
 }
-void or_neg_log(const double* u, int64_t n, double* out) {
+void or_neg_log(const double* u, int64_t n, double* out, int32_t elem) {
+    g_elem = elem;
     for (int64_t i = 0; i < n; ++i) out[i] = neg_log(u[i]);
 }
 
@@ -944,6 +986,7 @@ int or_quadrature(int order, double* ox, double* oy, double* oz, double* w) {
 // Initial bank (Sec. 2.2, Eq. (IC)): n_hist particles from the per-cell initial weight,
 // uniform in each cell and isotropic, at t = 0 (stream INIT, dims 0-1 position, 3-4 direction).
 int or_init_bank(const or_problem* P, const double* ic_cell_w, or_bank* out) {
+    g_elem = P->elem;
     build_sobol_table();
     build_primes();
     Mesh M(P);
@@ -970,6 +1013,7 @@ int or_init_bank(const or_problem* P, const double* ic_cell_w, or_bank* out) {
 // sum of w0 = int Q). Exposed for the uniform-source pin. t_frac = (t - t_n)/dt.
 int or_sample_births(const or_problem* P, int64_t step, int64_t n, int32_t* cell, double* fx,
                      double* fy, double* ox, double* oy, double* t_frac, double* w0_out) {
+    g_elem = P->elem;
     build_sobol_table();
     build_primes();
     Mesh M(P);
@@ -996,35 +1040,39 @@ int or_sample_births(const or_problem* P, int64_t step, int64_t n, int32_t* cell
 // pre/post: track-length integrals sum w l g0 per cell; mom: hand-off moments (4 per cell).
 // hist (optional): 4 int32 per history (final cell, fate, final n, segments).
 // census_out (optional): the MC-leg census survivors.
-int or_mc_leg_counts(const or_problem* P, int64_t step, const or_bank* census, double* pre, double* post,
-                     double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n, int64_t* post_n);
+// The general form: only the histories with global index h in [h0, h1) (index order: census bank
+// slots, then source births) and skip[h] == 0 (skip may be NULL) are tracked, as one rank of a
+// history-sharded leg would run them. hist and margin rows (when given) and the statistics cover
+// the histories tracked, in index order. margin[r]: the smallest relative gap of the history's
+// decisions (see Leg::run), to tell a decision that rounding can flip from a robust one.
+int or_mc_leg_ex(const or_problem* P, int64_t step, const or_bank* census, int64_t h0, int64_t h1,
+                 const uint8_t* skip, double* pre, double* post, double* mom, or_stats* st, int32_t* hist,
+                 double* margin, or_bank* census_out, int64_t* pre_n, int64_t* post_n);
 
 int or_mc_leg(const or_problem* P, int64_t step, const or_bank* census, double* pre, double* post,
               double* mom, or_stats* st, int32_t* hist, or_bank* census_out) {
-    return or_mc_leg_counts(P, step, census, pre, post, mom, st, hist, census_out, nullptr, nullptr);
+    return or_mc_leg_ex(P, step, census, 0, INT64_MAX, nullptr, pre, post, mom, st, hist, nullptr, census_out,
+                        nullptr, nullptr);
 }
 
 // The MC leg with, per cell, the number of segments scored into the pre and post tallies.
-// The MC leg over the histories with global index h in [h0, h1) only (index order: census bank
-// slots, then source births), as one rank of a history-sharded leg would run it; hist rows and
-// statistics cover that range.
-static int leg_range(const or_problem* P, int64_t step, const or_bank* census, int64_t h0, int64_t h1, double* pre,
-                     double* post, double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n,
-                     int64_t* post_n);
-
 int or_mc_leg_counts(const or_problem* P, int64_t step, const or_bank* census, double* pre, double* post,
                      double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n, int64_t* post_n) {
-    return leg_range(P, step, census, 0, INT64_MAX, pre, post, mom, st, hist, census_out, pre_n, post_n);
+    return or_mc_leg_ex(P, step, census, 0, INT64_MAX, nullptr, pre, post, mom, st, hist, nullptr, census_out,
+                        pre_n, post_n);
 }
 
 int or_mc_leg_range(const or_problem* P, int64_t step, const or_bank* census, int64_t h0, int64_t h1, double* pre,
                     double* post, double* mom, or_stats* st, int32_t* hist) {
-    return leg_range(P, step, census, h0, h1, pre, post, mom, st, hist, nullptr, nullptr, nullptr);
+    return or_mc_leg_ex(P, step, census, h0, h1, nullptr, pre, post, mom, st, hist, nullptr, nullptr, nullptr,
+                        nullptr);
 }
 
-static int leg_range(const or_problem* P, int64_t step, const or_bank* census, int64_t h0, int64_t h1, double* pre,
-                     double* post, double* mom, or_stats* st, int32_t* hist, or_bank* census_out, int64_t* pre_n,
-                     int64_t* post_n) {
+int or_mc_leg_ex(const or_problem* P, int64_t step, const or_bank* census, int64_t h0, int64_t h1,
+                 const uint8_t* skip, double* pre, double* post, double* mom, or_stats* st, int32_t* hist,
+                 double* margin, or_bank* census_out, int64_t* pre_n, int64_t* post_n) {
+
+    g_elem = P->elem;
     build_sobol_table();
     build_primes();
     Leg L(P);
@@ -1037,10 +1085,10 @@ static int leg_range(const or_problem* P, int64_t step, const or_bank* census, i
     if (census && census->n > 0) {
         L.pts.key = stream_key(P->seed, (uint64_t)step, kStreamLegCensus);
         for (int64_t j = 0; j < census->n; ++j, ++h) {
-            if (h < h0 || h >= h1) continue;
+            if (h < h0 || h >= h1 || (skip && skip[h])) continue;
             int k = census->cell[j];
             L.run((uint64_t)j, k % M.nx, k / M.nx, census->fx[j], census->fy[j], census->ox[j],
-                  census->oy[j], census->w[j], cdt, hist ? hist + 4 * ran : nullptr);
+                  census->oy[j], census->w[j], cdt, hist ? hist + 4 * ran : nullptr, margin ? margin + ran : nullptr);
             ++ran;
         }
     }
@@ -1052,13 +1100,13 @@ static int leg_range(const or_problem* P, int64_t step, const or_bank* census, i
         const double w0 = W / (double)P->n_hist;
         L.pts.key = stream_key(P->seed, (uint64_t)step, kStreamLegSource);
         for (int64_t i = 0; i < P->n_hist; ++i, ++h) {
-            if (h < h0 || h >= h1) continue;
+            if (h < h0 || h >= h1 || (skip && skip[h])) continue;
             double frx, fry, ox, oy;
             int k = sample_cell(C, L.pts(i, 0), L.pts(i, 1), &frx, &fry);
             const double tf = unit(L.pts(i, 2));
             iso_direction(unit(L.pts(i, 3)), unit(L.pts(i, 4)), &ox, &oy);
             L.run((uint64_t)i, k % M.nx, k / M.nx, frx * M.dx, fry * M.dy, ox, oy, w0,
-                  cdt * (1.0 - tf), hist ? hist + 4 * ran : nullptr);
+                  cdt * (1.0 - tf), hist ? hist + 4 * ran : nullptr, margin ? margin + ran : nullptr);
             ++ran;
         }
     }
@@ -1228,6 +1276,7 @@ static int census_from(const or_problem* P, int64_t step, std::vector<Streamed>&
 // or bank + births). combed: 1 if the comb ran.
 int or_remap(const or_problem* P, int64_t step, const or_bank* census, const double* pre,
              const double* post, const double* phi, or_bank* out, or_stats* st, int32_t* combed) {
+    g_elem = P->elem;
     build_sobol_table();
     build_primes();
     Mesh M(P);
@@ -1276,6 +1325,7 @@ int or_remap(const or_problem* P, int64_t step, const or_bank* census, const dou
 // census particles in history order.
 int or_remap_additive(const or_problem* P, int64_t step, const or_bank* bank, const or_bank* leg_census,
                       const double* post, const double* phi, or_bank* out, or_stats* st, int32_t* combed) {
+    g_elem = P->elem;
     build_sobol_table();
     build_primes();
     Mesh M(P);
@@ -1316,6 +1366,7 @@ int or_remap_additive(const or_problem* P, int64_t step, const or_bank* bank, co
 
 // the phase-space census key (census_order 2), exposed for its pins
 int or_phase_keys(const or_problem* P, const or_bank* b, uint32_t* keys) {
+    g_elem = P->elem;
     Mesh M(P);
     int cb = 0;
     const int bits = (int)phase_key_bits((int64_t)M.nx * M.ny, &cb);
@@ -1329,6 +1380,7 @@ int or_phase_keys(const or_problem* P, const or_bank* b, uint32_t* keys) {
 int or_step(const or_problem* P, int64_t step, const or_bank* bank, or_bank* out, double* flux,
             double* pre, double* post, double* mom, double* phi, or_stats* leg_st,
             or_stats* remap_st) {
+    g_elem = P->elem;
     Mesh M(P);
     const size_t nc = (size_t)M.nx * M.ny;
     int rc;

@@ -1,7 +1,8 @@
 // remap.cu -- scatter-free census remap (Sec. 2.2 steps 3-4, Eq. (R)) and the integer 2-D CDF.
 //
 // CDF build (shared by the static source and the remap source): per cell |q| -> max and sum
-// (deterministic block order) -> q_int = rint(|q| / max |q| 2^40) -> per-row exclusive scans
+// (deterministic block order) -> q_int = rint(|q| / max |q| 2^B), B = min(40, 62 - ceil(log2 ncells))
+// -> per-row exclusive scans
 // (column conditional) and column guides -> row-total scan (row marginal) and row guide in the
 // last row block. Exact integer arithmetic, so cells are picked identically on the FP32 and FP64
 // paths.
@@ -95,12 +96,16 @@ __global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax
     pdl_trigger();
     const int iy = blockIdx.x;
     const double qm = *qmax;
+    // 2^B with B = min(40, 62 - ceil(log2 ncells)): the table's total stays below 2^62
+    int lg = 0;
+    while ((1ll << lg) < (long long)nx * ny) ++lg;
+    const double qsc = ldexp(1.0, min(40, 62 - lg));
     const int per = (nx + blockDim.x - 1) / blockDim.x;
     const int c0 = threadIdx.x * per;
     long long local = 0;
     for (int c = c0; c < c0 + per && c < nx; ++c) {
         const size_t k = (size_t)iy * nx + c;
-        const long long q = qm > 0 ? __double2ll_rn((fabs(w[k]) / qm) * 0x1p40) : 0;
+        const long long q = qm > 0 ? __double2ll_rn((fabs(w[k]) / qm) * qsc) : 0;
         C.q[k] = q;
         local += q;
     }

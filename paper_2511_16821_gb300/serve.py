@@ -40,13 +40,15 @@ class Request:
     step_latency: list = field(default_factory=list)
     histories: int = 0
     flux: np.ndarray | None = None
+    bank: dict | None = None
 
 
 class Server:
     def __init__(self, budget_bytes: float = 120e9, max_active: int = 512, tuning: dict | None = None,
-                 clock=None):
+                 clock=None, keep_banks: bool = False):
         import torch
         self.torch = torch
+        self.keep_banks = keep_banks      # copy each finished request's census bank to the host
         self.budget = float(budget_bytes)
         self.max_active = max_active
         self.tuning = dict(block=256, chunk=4096, streams=16, use_graph=0)
@@ -91,6 +93,8 @@ class Server:
         for r in self.active:
             if r.done_steps >= r.steps:
                 r.flux = r.problem.tally("flux")
+                if self.keep_banks:
+                    r.bank = r.problem.bank()
                 r.problem.close()
                 r.problem = None
                 self.used -= r.ws_bytes

@@ -18,3 +18,13 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def opool():
+    """Oracle workers over history-index slices or whole problems (spawn-started, one per core)."""
+    import oracle
+    from oracle.parallel import Pool
+    oracle.build()
+    with Pool() as P:
+        yield P

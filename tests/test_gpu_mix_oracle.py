@@ -1,0 +1,106 @@
+"""Batched and served problems against the oracle (Sec. 2.2 steps 1-4 on every problem of a mix).
+
+Problems of the batched distribution (mesh side 32-128, per-cell sigma_t log-uniform up to 100 and
+scattering ratio up to 0.99, N_s from 0 to 4) are stepped three times together -- through one batch
+of persistent work-queue launches, and through the continuous-batching server that admits them at
+different ticks -- and each problem is compared with the oracle's own three steps of it alone:
+FP64 census banks cell for cell and counters exactly (the oracle on the FP64 path's map recipe),
+fluxes to 1e-9 (the collided solves converge to 1e-12); FP32 leg tallies at the FP32 bar against
+the libm oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_2511_16821_gb300 import workloads as W
+from parity_checks import FP32_RTOL, fp32_report, fp32_weighted
+
+pytestmark = pytest.mark.gpu
+
+PROBLEMS = (1, 2, 4, 6, 8, 10)     # sides 32, 64, 64, 128, 128, 64; N_s 0, 0, 4, 2, 3, 2
+NSTEPS = 3
+
+
+def _specs(prec):
+    return [W.random_batch_problem(3, p, max_side=128, precision=prec).with_(
+        n_hist=8000, sn_tol=1e-12 if prec == W.FP64 else 1e-7, sn_max_iter=5000, sn_warm_start=1)
+        for p in PROBLEMS]
+
+
+def _check_bank(gb, ob, spec, what):
+    assert gb["n"] == ob["n"], what
+    assert np.array_equal(gb["cell"], ob["cell"]), what
+    for q in ("fx", "fy", "ox", "oy"):
+        assert np.allclose(gb[q], ob[q], rtol=0, atol=1e-12 * max(spec.lx, 1.0)), (what, q)
+    assert np.allclose(gb["w"], ob["w"], rtol=1e-9, atol=0), what
+
+
+def _check_flux(f, of, what):
+    assert np.allclose(f, of, rtol=1e-9, atol=1e-12 * np.max(np.abs(of))), \
+        (what, float(np.max(np.abs(f - of)) / np.max(np.abs(of))))
+
+
+@pytest.fixture(scope="module")
+def oracle_fp64(orc, opool):
+    return opool.steps(_specs(W.FP64), NSTEPS, elem=orc.SERIES)
+
+
+def test_batch_matches_oracle_fp64(orc, oracle_fp64):
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    specs = _specs(W.FP64)
+    probs = [hyb.Problem(sp) for sp in specs]
+    B = hyb.Batch(probs, tuning=dict(block=256, chunk=1024, streams=4))
+    for k in range(NSTEPS):
+        bst = B.step(1)
+        torch.cuda.synchronize()
+        for i, P in enumerate(probs):
+            r = oracle_fp64[i][k]
+            what = (specs[i].name, k)
+            for key in ("histories", "segments", "collisions", "leaked", "census", "killed", "reached_limit"):
+                assert bst[i][key] == r["leg"][key], (what, key, bst[i][key], r["leg"][key])
+            _check_flux(P.tally("flux"), r["flux"], what)
+            _check_bank(P.bank(), r["bank"], specs[i], what)
+    B.close()
+    for P in probs:
+        P.close()
+
+
+def test_served_mix_matches_oracle_fp64(orc, oracle_fp64):
+    from paper_2511_16821_gb300.serve import Server
+    specs = _specs(W.FP64)
+    ticks = [0, 1, 1, 2, 4, 4]
+    srv = Server(budget_bytes=64e9, keep_banks=True)
+    done = srv.run_schedule([(t, sp, NSTEPS) for t, sp in zip(ticks, specs)])
+    srv.close()
+    assert len(done) == len(specs) and srv.rebuilds >= 3
+    for r in done:
+        o = oracle_fp64[r.rid][NSTEPS - 1]
+        _check_flux(r.flux, o["flux"], r.spec.name)
+        _check_bank(r.bank, o["bank"], r.spec, r.spec.name)
+        assert len(r.step_latency) == NSTEPS
+
+
+def test_batch_fp32_leg_against_oracle(orc, opool):
+    """First step of the FP32 batch: its leg tallies against the libm oracle's leg at the FP32 bar
+    (resolved cells 1e-4, every cell above 1e-3 of the peak 1e-2, tally-weighted 1e-5)."""
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    specs = _specs(W.FP32)
+    probs = [hyb.Problem(sp) for sp in specs]
+    B = hyb.Batch(probs, tuning=dict(block=256, chunk=1024, streams=4))
+    B.step(1)
+    torch.cuda.synchronize()
+    for sp, P in zip(specs, probs):
+        o = opool.mc_leg(sp.with_(precision=W.FP64), 0, None, elem=orc.LIBM)
+        g = dict(pre=P.tally("pre_raw"), post=P.tally("post_raw"), mom=P.tally("handoff"))
+        rep, raw, wtd = fp32_report(g, o), fp32_report(g, o, min_seg=0), fp32_weighted(g, o)
+        print(f"\nbatched FP32 {sp.name} (N_s={sp.n_s}, {sp.nx}^2): resolved {rep}; unrestricted {raw}; weighted {wtd}")
+        for k, v in rep.items():
+            assert v < FP32_RTOL, (sp.name, k, v)
+        for k, v in raw.items():
+            assert v < 1e-2, (sp.name, k, v)
+        for k, v in wtd.items():
+            assert v < 1e-5, (sp.name, k, v)
+    B.close()
+    for P in probs:
+        P.close()

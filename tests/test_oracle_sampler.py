@@ -151,22 +151,39 @@ def test_prng_uniformity(orc):
     assert len(np.unique(P[:1000].ravel())) > 3990
 
 
-def test_direction_and_depth_maps_accuracy(orc):
-    # the series evaluations of sin/cos(2 pi u) and -log u against 40-digit arithmetic over the
-    # point lattice, including the quadrant boundaries and u -> 0, 1
+@pytest.mark.parametrize("mode,tol_sc", [(1, 3e-16), (0, 1.2e-15)], ids=["series", "libm"])
+def test_direction_and_depth_maps_accuracy(orc, mode, tol_sc):
+    # both evaluations of sin/cos(2 pi u) and -log u against 40-digit arithmetic over the point
+    # lattice, including the quadrant boundaries and u -> 0, 1. The libm mode rounds the argument
+    # 2 pi u first (an absolute error up to half an ulp of 2 pi, 4.4e-16), then libm's own error;
+    # the series mode reduces u exactly first.
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 40
     x = np.concatenate([np.arange(0, 2 ** 32, 2 ** 32 // 2003, dtype=np.uint64),
                         np.array([0, 1, 2 ** 30 - 1, 2 ** 30, 2 ** 31, 3 * 2 ** 30, 2 ** 32 - 1], np.uint64)])
     u = (x.astype(np.float64) + 0.5) * 2.0 ** -32
-    s, c = orc.sincos_2pi(u)
-    t = orc.neg_log(u)
+    s, c = orc.sincos_2pi(u, elem=mode)
+    t = orc.neg_log(u, elem=mode)
     for i in range(u.size):
         a = 2 * mpmath.pi * mpmath.mpf(float(u[i]))
-        assert abs(s[i] - float(mpmath.sin(a))) < 3e-16
-        assert abs(c[i] - float(mpmath.cos(a))) < 3e-16
+        assert abs(s[i] - float(mpmath.sin(a))) < tol_sc
+        assert abs(c[i] - float(mpmath.cos(a))) < tol_sc
         ref = -mpmath.log(mpmath.mpf(float(u[i])))
         assert abs(t[i] - float(ref)) <= 3e-16 * abs(float(ref))
+
+
+def test_elementary_modes_are_distinct_evaluations(orc):
+    # the two modes evaluate the same maps (agreement to rounding) by different operations (they
+    # differ in the last bits somewhere), and the module default is libm
+    u = (np.arange(0, 2 ** 32, 2 ** 32 // 4001, dtype=np.uint64).astype(np.float64) + 0.5) * 2.0 ** -32
+    s0, c0 = orc.sincos_2pi(u, elem=orc.LIBM)
+    s1, c1 = orc.sincos_2pi(u, elem=orc.SERIES)
+    t0, t1 = orc.neg_log(u, elem=orc.LIBM), orc.neg_log(u, elem=orc.SERIES)
+    assert np.max(np.abs(s0 - s1)) < 2e-15 and np.max(np.abs(c0 - c1)) < 2e-15
+    assert np.max(np.abs(t0 - t1) / t0) < 6e-16
+    assert np.any(s0 != s1) and np.any(c0 != c1)
+    sd, cd = orc.sincos_2pi(u)
+    assert np.array_equal(sd, s0) and np.array_equal(cd, c0)
 
 
 # ---------------------------------------------------------------------------------------------

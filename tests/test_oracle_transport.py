@@ -228,6 +228,60 @@ def test_uniform_source_is_stratified(orc):
     assert np.allclose(b["fy"], u2 * 0.5, rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("nx,ny", [(4096, 2048), (4096, 4096)])
+def test_cdf_total_fits_on_the_largest_meshes(orc, nx, ny):
+    # uniform weights on the largest accepted meshes: the quantisation 2^B with B = min(40, 62 -
+    # ceil(log2 ncells)) keeps the total at 2^62 (2^40 per cell would overflow int64 from 2^23 cells
+    # on); every prefix is non-negative and strictly increasing, and a point's cell is the
+    # uniform map floor(u n)
+    q, rp, cp = orc.build_cdf(nx, ny, np.ones(nx * ny))
+    B = min(40, 62 - int(math.ceil(math.log2(nx * ny))))
+    assert np.all(q == 2 ** B)
+    assert int(rp[-1]) == nx * ny * 2 ** B <= 2 ** 62
+    assert np.all(np.diff(rp) == nx * 2 ** B)
+    row = cp.reshape(ny, nx + 1)
+    assert np.all(np.diff(row, axis=1) == 2 ** B)
+
+
+def test_cdf_quantisation_unchanged_below_2_22_cells(orc):
+    # meshes up to 2^22 cells keep the 2^40 scale
+    w = np.random.default_rng(1).uniform(0.1, 1, 2048 * 2048)
+    q, rp, _ = orc.build_cdf(2048, 2048, w)
+    assert np.array_equal(q, np.rint(w / w.max() * 2.0 ** 40).astype(np.int64))
+
+
+def test_decision_margins_and_history_subsets(orc):
+    # margins lie in [0, 1] and are small only where two event distances nearly tie; a leg over a
+    # subset (index range, skip mask) tracks exactly those histories: the records of the subsets
+    # are the whole leg's rows, and the counters and tallies of complementary subsets add up
+    spec = W.checkerboard(n_s=2, n_hist=3000, cells_per_block=3)
+    bank = W.random_bank(spec, 1000, seed=2)
+    full = orc.mc_leg(spec, 1, bank, want_hist=True, want_margin=True)
+    m = full["margin"]
+    n = full["stats"]["histories"]
+    assert n == 4000 and m.shape == (n,) and np.all((m >= 0) & (m <= 1))
+    skip = np.zeros(n, np.uint8)
+    skip[::7] = 1
+    a = orc.mc_leg(spec, 1, bank, want_hist=True, want_margin=True, skip=skip)
+    b = orc.mc_leg(spec, 1, bank, want_hist=True, want_margin=True, skip=1 - skip)
+    assert np.array_equal(a["hist"], full["hist"][skip == 0]) and np.array_equal(b["hist"], full["hist"][skip == 1])
+    assert np.array_equal(a["margin"], m[skip == 0])
+    for k in ("histories", "segments", "collisions", "leaked", "census", "killed", "reached_limit"):
+        assert a["stats"][k] + b["stats"][k] == full["stats"][k], k
+    for k in ("pre", "post", "mom"):
+        assert np.allclose(a[k] + b[k], full[k], rtol=1e-13, atol=1e-300), k
+    r = orc.mc_leg(spec, 1, bank, want_hist=True, h0=1500, h1=2500)
+    assert np.array_equal(r["hist"], full["hist"][1500:2500])
+    # a history whose two smallest event distances are equal (an exact corner: start at the cell's
+    # centre moving along the diagonal) has margin 0
+    one = W.homogeneous(n=2, L=2.0, sigma_a=0.1, sigma_s=0.0, Q=None, n_hist=1, dt=10.0, n_s=0)
+    c = math.sqrt(0.5)
+    bk = {"cell": np.array([0], np.int32), "fx": np.array([0.5]), "fy": np.array([0.5]),
+          "ox": np.array([c]), "oy": np.array([c]), "w": np.array([1.0]), "n": 1}
+    r1 = orc.mc_leg(one, 0, bk, want_margin=True)
+    assert r1["margin"][0] == 0.0
+
+
 def test_nonuniform_source_cell_frequencies(orc):
     # Births land in cells in proportion to Q * area (integer CDF), to within the 1-D Sobol
     # stratification error of the row/column picks.
