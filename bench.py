@@ -140,7 +140,7 @@ def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0
 
 def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
     """Kernels of this library launched by one single-problem step (memsets not counted)."""
-    leg = 3                                   # births, leg kernel, normalisation
+    leg = 2                                   # leg kernel (births generated inside it), normalisation
     sn = 1 + 2 * sn_iters + 1                 # source (with the starting iterate); sweep + reduce per iteration;
                                               # finish (copy, flux)
     remap = 1 + 3 + 1 + 3 + 1                 # density, CDF (reduce, total, rows with marginal and guides), prep,
@@ -195,7 +195,8 @@ def run_gpu(args, rank: int, world: int) -> dict:
 
 def leg_profile(prec: int, reps: int = 5) -> dict:
     """Device time of the MC leg alone (events recorded by the library around the leg kernel and
-    its normalisation, on the problem's stream) at the benchmark workload."""
+    its normalisation, on the problem's stream) at the benchmark workload, with the leg's inputs
+    (the steady-state census bank, step 2) and raw tallies for the error against the oracle."""
     import torch
     from paper_2511_16821_gb300 import hyb
     spec = spec_for(prec)
@@ -212,8 +213,32 @@ def leg_profile(prec: int, reps: int = 5) -> dict:
         hist, segs, adds = st["histories"], st["segments"], st["tally_adds"]
     bank = P.bank()
     nb = bank["n"]
+    tallies = {"pre": P.tally("pre_raw"), "post": P.tally("post_raw"), "mom": P.tally("handoff")}
+    P.close()
     return dict(ms=statistics.median(ms), histories=hist, segments=segs, tally_adds=adds, bank=nb,
-                ncells=spec.ncells)
+                ncells=spec.ncells, bank_host=bank, tallies=tallies, step=2, spec=spec)
+
+
+def tally_error(g: dict, o: dict, frac: float = 1e-3, min_seg: int = 32) -> dict:
+    """FP32 tallies against the FP64 oracle's: per tally the largest relative error on the cells it
+    resolves (above `frac` of its peak with >= min_seg scored segments), on every cell above `frac`
+    of the peak, and the tally-weighted mean relative error."""
+    out = {}
+    cnt = {"pre": o["pre_n"], "post": o["post_n"]}
+    for key in ("pre", "post", "mom0", "mom1", "mom2", "mom3"):
+        if key.startswith("mom"):
+            j = int(key[3])
+            a, b, ref, n = g["mom"][:, j], o["mom"][:, j], np.abs(o["mom"][:, 0]), o["post_n"]
+        else:
+            a, b, ref, n = g[key], o[key], np.abs(o[key]), cnt[key]
+        peak = float(np.max(ref)) if ref.size else 0.0
+        err = np.abs(a - b) / np.maximum(ref, 1e-300)
+        sel = ref >= frac * peak if peak > 0 else np.zeros_like(ref, bool)
+        res = sel & (n >= min_seg)
+        out[key] = {"resolved_max": float(np.max(err[res])) if res.any() else 0.0,
+                    "max": float(np.max(err[sel])) if sel.any() else 0.0,
+                    "weighted": float(np.sum(np.abs(a - b)) / max(float(np.sum(np.abs(b))), 1e-300))}
+    return out
 
 
 def e2e_measure(spec: W.ProblemSpec, steps: int) -> dict:
@@ -247,9 +272,12 @@ def e2e_measure(spec: W.ProblemSpec, steps: int) -> dict:
             "d2h_bytes_per_step": int(spec.nx * spec.ny * 8)}
 
 
-def cpu_baseline(n_hist: int, steps: int) -> dict:
-    """The FP64 oracle, single-threaded, on a bounded sample of the workload (same mesh, N_s,
-    dt and quadrature; n_hist histories per step)."""
+def cpu_baseline(n_hist: int, steps: int, leg: dict | None = None) -> dict:
+    """The FP64 oracle on the host cores: (1) one thread, whole hybrid steps on a bounded sample of
+    the workload (same mesh, N_s, dt and quadrature; n_hist histories per step); (2) every core
+    (one spawn-started process per core over contiguous history-index slices, integer counters
+    summed) on the benchmark's own MC leg (its census bank and step), whose result also gives the
+    FP32 path's tally error against the oracle."""
     import oracle
     oracle.build()
     spec = spec_for(W.FP64, n_hist=n_hist, warm=0)
@@ -261,9 +289,27 @@ def cpu_baseline(n_hist: int, steps: int) -> dict:
         bank = r["bank"]
         hist += r["leg"]["histories"]
     dt = time.perf_counter() - t0
-    return {"value": hist / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full hybrid steps of the checkerboard-112 workload at {n_hist} "
-                      f"histories/step (FP64 oracle, one thread)", "seconds": round(dt, 2)}
+    one = {"value": hist / dt, "unit": METRIC, "cores": 1,
+           "sample": f"{steps} full hybrid steps of the checkerboard-112 workload at {n_hist} "
+                     f"histories/step (FP64 oracle, one thread)", "seconds": round(dt, 2)}
+    out = dict(one, kind="oracle")
+    if leg is None:
+        return out
+    from oracle.parallel import Pool
+    ncores = os.cpu_count() or 1
+    ospec = leg["spec"].with_(precision=W.FP64)
+    with Pool(ncores) as pool:
+        pool.mc_leg(ospec, leg["step"], None, nslices=ncores)     # start-up of the workers, untimed
+        t0 = time.perf_counter()
+        o = pool.mc_leg(ospec, leg["step"], leg["bank_host"])
+        dt = time.perf_counter() - t0
+    n = o["stats"]["histories"]
+    out.update({"value": n / dt, "cores": ncores, "seconds": round(dt, 2),
+                "sample": f"the benchmark's MC leg ({leg['bank']} census particles + births, step "
+                          f"{leg['step']}) on {ncores} processes over index slices (FP64 oracle)",
+                "one_core": one})
+    out["fp32_tally_error"] = tally_error(leg["tallies"], o)
+    return out
 
 
 def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0, sn_accel: int = 0,
@@ -292,11 +338,22 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0, sn_acc
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     hist = sum(x["histories"] for x in st)
+    # the batched leg launch against the atomic roofline (its tally additions over its device time,
+    # events around the launch inside the step), with the HBM view of the banks' pick-ups
+    adds = sum(x["tally_adds"] for x in st)
+    ms_leg = st[-1]["ms_leg"]
+    nbank = sum(x["histories"] for x in st) - sum(sp.n_hist for sp in specs)
+    peak = hyb.atomic_rate(6 * sum(sp.nx * sp.ny for sp in specs))
     B.close()
     for P in probs:
         P.close()
     out = {"problems": n_problems, "sn_accel": sn_accel, "histories_per_step": hist, "ms_per_step": ms,
-           "histories_per_s": hist / (ms / 1e3), "tuning": tune["best"]}
+           "histories_per_s": hist / (ms / 1e3), "tuning": tune["best"],
+           "roofline": {"bound": "atomic", "kernel": "mc_leg_batch_kernel<float>",
+                        "achieved": adds / (ms_leg / 1e3) / 1e9, "peak": peak / 1e9, "unit": "Gatomic/s",
+                        "frac": adds / (ms_leg / 1e3) / peak, "leg_ms": ms_leg, "tally_adds": adds,
+                        "hbm": {"bytes": 24 * nbank, "achieved": 24 * nbank / (ms_leg / 1e3) / 1e9,
+                                "unit": "GB/s"}}}
     if not single:
         return out
     # plain path: each problem alone, the same number of steps, one after the other
@@ -383,9 +440,13 @@ def serving_measure(lam: float, duration: float, seed: int = 0, hist_cap: int | 
 
 
 def reference_arm(args, rank: int, world: int) -> None:
+    """The oracle (one thread, FP64) on the benchmark workload: whole hybrid steps at the
+    benchmark's 10^6 histories/step when warm-up plus timed steps fit in about two minutes (about
+    4 s per step on one core), else at a proportionally smaller history count, stated in the line."""
     if rank != 0:
         return
-    n_hist = 200_000
+    n_hist = N_HIST if (args.steps + args.warmup) * 5.0 <= 150.0 else \
+        max(10_000, int(N_HIST * 150.0 / (5.0 * (args.steps + args.warmup))))
     import oracle
     oracle.build()
     spec = spec_for(W.FP64, n_hist=n_hist, warm=0)
@@ -405,7 +466,8 @@ def reference_arm(args, rank: int, world: int) -> None:
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_block(),
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} hybrid steps at {n_hist} histories/step"},
+                             "sample": f"{args.steps} whole hybrid steps at {n_hist} histories/step "
+                                       f"(after {args.warmup} untimed ones), one thread"},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -413,7 +475,9 @@ def reference_arm(args, rank: int, world: int) -> None:
 def config_block() -> dict:
     return {"workload": "checkerboard 7x7 blocks, 112x112 mesh, N_s=2, 1e6 histories/step, dt=0.1, S8",
             "mesh": "112x112", "n_s": N_S, "n_hist": N_HIST, "sampler": "sobol+digital shift",
-            "sn_order": 8, "dt": 0.1, "l2": "flushed (512 MiB write) before every timed step"}
+            "sn_order": 8, "dt": 0.1, "l2": "flushed (512 MiB write) before every timed step",
+            "histories_counted": "MC-leg histories per step: the census bank's pick-ups (1e6 after the "
+                                 "comb) plus the 1e6 source births"}
 
 
 def main():
@@ -487,15 +551,15 @@ def main():
     prof = leg_profile(W.FP32)
     # The MC leg's roofline (the hot path's target): its algorithmic work is one fixed-point tally
     # addition per pre-limit segment and five per post-limit segment (all counted by the kernel:
-    # hyb_leg_stats.tally_adds) plus its read stream: 24 B per bank particle and the 28 B start
-    # state of each staged birth. Its
-    # bound is the rate of 64-bit global atomic additions to the tally footprint (measured live
-    # with hyb_atomic_rate on 6 x ncells addresses); the HBM view is reported beside it.
+    # hyb_leg_stats.tally_adds) plus its read stream: 24 B per bank particle (births are generated
+    # in the kernel: 0 B). Its bound is the rate of 64-bit global atomic additions to the tally
+    # footprint (measured live with hyb_atomic_rate on 6 x ncells addresses); the HBM view is
+    # reported beside it.
     from paper_2511_16821_gb300 import hyb
     atomic_peak = hyb.atomic_rate(6 * prof["ncells"])
     leg_s = prof["ms"] / 1000.0
     adds_rate = prof["tally_adds"] / leg_s
-    leg_bytes = prof["bank"] * 24 + (prof["histories"] - prof["bank"]) * 28
+    leg_bytes = prof["bank"] * 24
     hbm_achieved = leg_bytes / leg_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -507,6 +571,7 @@ def main():
         "phase_ms": r32["phase_ms"],
         "roofline": {"bound": "atomic", "kernel": "mc_leg_kernel<float>", "achieved": adds_rate / 1e9,
                      "peak": atomic_peak / 1e9, "unit": "Gatomic/s", "frac": adds_rate / atomic_peak,
+                     "target_frac": 0.5,
                      "traffic": leg_traffic(),
                      "peak_src": "measured live: hyb_atomic_rate, 64-bit adds to 6 x ncells random addresses",
                      "leg_ms": prof["ms"], "leg_histories": prof["histories"], "leg_segments": prof["segments"],
@@ -516,12 +581,29 @@ def main():
         "gpu_launches": launches_per_step(r32["spec"], int(np.mean(r32["sn_iters"]) + 0.5)) * args.steps,
         "clocks": r32["clocks"],
     }
+    # the remap phase against HBM: 24 B read per copied census particle and 24 B written per
+    # census survivor (the bank of the next step); births are generated (0 B)
+    rb = r32["bank"] * 24 * 2
+    rms = r32["phase_ms"]["remap"]
+    line["roofline_remap"] = {"bound": "hbm", "kernel": "remap phase (density, CDF, count, scan, write)",
+                              "achieved": rb / (rms / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                              "frac": rb / (rms / 1e3) / 1e9 / pk["hbm_gbs"], "bytes": rb, "ms": rms,
+                              "peak_src": pk["src"]}
     if W.FP64 in res:
         r64 = res[W.FP64]
         ms64 = sum(r64["step_ms"])
+        p64 = leg_profile(W.FP64)
+        s64 = p64["ms"] / 1000.0
         line["fp64"] = {"value": r64["hist"] / (ms64 / 1000.0), "unit": METRIC,
                         "segments_per_s": r64["segs"] / (ms64 / 1000.0), "ms_per_step": ms64 / args.steps,
-                        "phase_ms": r64["phase_ms"]}
+                        "phase_ms": r64["phase_ms"],
+                        "roofline": {"bound": "atomic", "kernel": "mc_leg_kernel<double>",
+                                     "achieved": p64["tally_adds"] / s64 / 1e9, "peak": atomic_peak / 1e9,
+                                     "unit": "Gatomic/s", "frac": p64["tally_adds"] / s64 / atomic_peak,
+                                     "leg_ms": p64["ms"], "tally_adds": p64["tally_adds"],
+                                     "hbm": {"achieved": p64["bank"] * 44 / s64 / 1e9, "peak": pk["hbm_gbs"],
+                                             "unit": "GB/s", "frac": p64["bank"] * 44 / s64 / 1e9 / pk["hbm_gbs"],
+                                             "bytes": p64["bank"] * 44}}}
     if not args.no_e2e:
         line["e2e"] = e2e_measure(spec_for(W.FP32), max(2, min(args.steps, 5)))
     if CENSUS_ORDER == 0:
@@ -535,7 +617,9 @@ def main():
         line["batched_anderson"] = batched_measure(sn_accel=4, single=False)
         line["serving"] = serving_measure(100.0, 3.0)
     if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(n_hist=200_000, steps=2)
+        cb = cpu_baseline(n_hist=200_000, steps=2, leg=prof)
+        line["fp32_tally_error"] = cb.pop("fp32_tally_error")
+        line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
 
 

@@ -127,7 +127,13 @@ typedef struct {
                                  paper; results are the same): 0 automatic (the padded mesh while
                                  the per-ordinate solutions fit in 48 MB, else the wavefront
                                  order), 1 padded mesh, 2 wavefront order */
-    int32_t pad2;
+    int32_t seg_limit;        /* bound on segments per history (a guard on every device loop): a
+                                 history that reaches it ends as an error and the leg returns
+                                 HYB_ETIMEOUT; 0 = 2^20; at most 2^30 */
+    int32_t wait_limit;       /* polls (20 ns sleeps apart) of one wait of the collided solve's
+                                 strip pipeline before it gives up and the solve returns
+                                 HYB_ETIMEOUT; 0 = 2^22 (about 0.1 s per wait) */
+    int32_t pad3;
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */
@@ -182,6 +188,29 @@ HYB_API hyb_status hyb_destroy_problem(hyb_problem* p);
  * segments), histories ordered bank slots first, then births; capacity bank_size + n_hist. */
 HYB_API hyb_status hyb_mc_leg(hyb_problem* p, hyb_leg_stats* stats);
 HYB_API hyb_status hyb_mc_leg_trace(hyb_problem* p, int32_t* hist_dev, hyb_leg_stats* stats);
+
+/* History-sharded MC leg (Sec. 2.3: histories are independent, each drawing its own point, so a
+ * leg split by history index over several GPUs, with its integer results summed, is the one-GPU
+ * leg bit for bit). Every rank holds the same problem (bank, step, sigma, Q) and tracks a disjoint
+ * part of the index space [bank slots | births]:
+ *   hyb_leg_exchange_bytes: bytes of the exchange block (int64 words, 8-byte aligned).
+ *   hyb_mc_leg_range: the leg over the histories with global index h in [h0, h1) (clamped to the
+ *     leg's count; an empty range is allowed), with the whole leg's fixed-point scales, written to
+ *     the caller's device block x_dev (x_bytes >= hyb_leg_exchange_bytes) as raw integer tallies
+ *     and counters; hist_dev as for hyb_mc_leg_trace (rows at global indices, may be NULL).
+ *     Asynchronous on the problem's stream; the problem's tallies are not normalised after it.
+ *   The caller sums the blocks of all ranks element-wise as int64 (an all-reduce with a plain
+ *     integer sum; two's-complement wrap-around is part of the format: 128-bit values travel as
+ *     four 32-bit limbs, value = sum_i limb_i 2^(32 i) mod 2^128).
+ *   hyb_mc_leg_reduce_finish: the summed block becomes the problem's leg (tallies, hand-off
+ *     moments, counters, normalisation), as after hyb_mc_leg; stats as for hyb_mc_leg.
+ * Errors: EINVAL (range, null or misaligned block), ENOMEM (block too small), ECUDA; the device
+ * status bits of any rank survive the sum and are reported by the finish. */
+HYB_API hyb_status hyb_leg_exchange_bytes(const hyb_problem* p, size_t* bytes);
+HYB_API hyb_status hyb_mc_leg_range(hyb_problem* p, int64_t h0, int64_t h1, void* x_dev, size_t x_bytes,
+                                    int32_t* hist_dev);
+HYB_API hyb_status hyb_mc_leg_reduce_finish(hyb_problem* p, const void* x_dev, size_t x_bytes,
+                                            hyb_leg_stats* stats);
 
 /* Step 2 (Sec. 2.2; Eq. (floor N_s+1)): the collided S_N-DG solve fed by the hand-off
  * moments of the last MC leg. Synchronises per SI iteration (convergence test). */
@@ -266,7 +295,8 @@ HYB_API hyb_status hyb_batch_set_tuning(hyb_batch* b, const hyb_batch_tuning* tu
  * Synchronises the batch stream. */
 HYB_API hyb_status hyb_batch_set_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n);
 /* nsteps steps of every problem; per_problem (host, n entries, may be NULL): the last step's leg
- * statistics with sn_iterations / combed / bank_size, ms = device time of the last graph. */
+ * statistics with sn_iterations / combed / bank_size, ms = device time of the last step, ms_leg =
+ * device time of its batched births and MC-leg launches (the same for every problem). */
 HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* per_problem);
 HYB_API hyb_status hyb_batch_destroy(hyb_batch* b);
 HYB_API const char* hyb_batch_last_error(const hyb_batch* b);
@@ -291,10 +321,12 @@ HYB_API hyb_status hyb_build_cdf(const double* w_dev, int32_t nx, int32_t ny, in
  * (This entry point has no counterpart in the paper.)
  * Its scratch is one fixed __device__ array of 34,816 bytes, resident on every GPU that loads the
  * library until the process exits; ny is limited to 4096 rows (EINVAL beyond, like nx). The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress), so make that first
- * call before any stream capture. All calls share the array: calls that overlap on the GPU (other
- * streams, other threads) race and must be serialised by the caller. Outputs as hyb_build_cdf;
- * asynchronous on cuda_stream; allocates nothing. */
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) and keeps it for the
+ * life of the process, so make that first call before any stream capture, and do not call it on a
+ * device after cudaDeviceReset (the reset ends the context that address belongs to). All calls
+ * share the array: calls that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. Outputs as hyb_build_cdf; asynchronous on cuda_stream; allocates
+ * nothing. */
 HYB_API hyb_status hyb_build_cdf_noalloc(const double* w_dev, int32_t nx, int32_t ny, int64_t* q_dev,
                                          int64_t* row_pre_dev, int64_t* col_pre_dev, double* W_qmax_dev,
                                          void* cuda_stream);

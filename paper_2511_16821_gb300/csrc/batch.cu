@@ -35,6 +35,7 @@ struct hyb_batch {
     std::vector<cudaStream_t> pool;
     std::vector<cudaEvent_t> join_ev;
     cudaEvent_t fork_ev = nullptr, ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t evl0 = nullptr, evl1 = nullptr;   // around the batched births and leg (external nodes in graphs)
     void* d_args[2] = {nullptr, nullptr};   // per parity: LegArgs of every problem
     size_t cap_probs = 0;                   // problems the per-problem buffers hold (grow-only)
     size_t cap_chunks = 0, cap_bchunks = 0; // chunk queue capacities (grow-only)
@@ -138,8 +139,15 @@ cudaError_t issue_phase(hyb_batch* b, int q, int phase) {
         const int per_sm = b->tune.ctas_per_sm > 0 ? b->tune.ctas_per_sm
                                                    : hyb::leg_batch_ctas_per_sm(b->prec) * 256 / b->tune.block;
         const int grid = std::max(1, std::min(b->nchunks, sms * per_sm));
+        // events around the births and the leg: external event nodes inside a captured graph (so
+        // their times can be read after a replay), plain records when issued directly
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        ck(cudaStreamIsCapturing(b->s0, &cs));
+        const bool capt = cs == cudaStreamCaptureStatusActive;
+        ck(capt ? cudaEventRecordWithFlags(b->evl0, b->s0, cudaEventRecordExternal) : cudaEventRecord(b->evl0, b->s0));
         ck(hyb::launch_mc_leg_batch(b->prec, b->d_args[q], b->d_chunks, b->nchunks, b->d_head, b->d_V, b->ntab_max,
                                     grid, b->tune.block, b->s0, b->d_bchunks, b->nbchunks, b->d_head + 1));
+        ck(capt ? cudaEventRecordWithFlags(b->evl1, b->s0, cudaEventRecordExternal) : cudaEventRecord(b->evl1, b->s0));
     }
     ck(cudaEventRecord(b->fork_ev, b->s0));
     for (auto s : b->pool) ck(cudaStreamWaitEvent(s, b->fork_ev, 0));
@@ -259,9 +267,7 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         probs.push_back(p);
     }
     if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");
-    // programmatic dependent launch is kept for problems stepped alone: in the batch's multi-stream
-    // step graphs it measured slower (256 problems: 73 -> 101 ms per step)
-    for (hyb_problem* p : probs) p->pdl = false;
+    const std::vector<hyb_problem*> before = b->probs;
     b->prec = prec;
     b->probs = probs;
     b->cur0.clear(); b->kmax.clear();
@@ -293,6 +299,11 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         if (cudaMemcpy(b->d_args[q], host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
             return bfail(b, HYB_ECUDA, "args upload");
     }
+    // programmatic dependent launch is kept for problems stepped alone: in the batch's multi-stream
+    // step graphs it measured slower (256 problems: 73 -> 101 ms per step). Members launch normally
+    // once the batch holds them; problems that left the set get it back.
+    for (hyb_problem* p : before) p->pdl = true;
+    for (hyb_problem* p : probs) p->pdl = false;
     return HYB_OK;
 }
 
@@ -324,7 +335,8 @@ HYB_API hyb_status hyb_batch_create(hyb_problem* const* problems, int32_t n, voi
     if (cudaMemcpy(b->d_V, hyb::sobol_table_host(), HYB_SOBOL_DIMS * 32 * 4, cudaMemcpyHostToDevice) != cudaSuccess)
         return fail_all(HYB_ECUDA, "table upload");
     if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess)
+        cudaEventCreate(&b->ev0) != cudaSuccess || cudaEventCreate(&b->ev1) != cudaSuccess ||
+        cudaEventCreate(&b->evl0) != cudaSuccess || cudaEventCreate(&b->evl1) != cudaSuccess)
         return fail_all(HYB_ECUDA, "events");
     hyb_status s = load_problems(b, problems, n);
     if (s == HYB_OK) s = hyb_batch_set_tuning(b, &b->tune);
@@ -420,8 +432,9 @@ HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* p
         if (bad != HYB_OK) return bfail(b, bad, "a problem of the batch reported a device check failure");
     }
     if (per_problem) {
-        float ms = 0;
+        float ms = 0, ms_leg = 0;
         cudaEventElapsedTime(&ms, b->ev0, b->ev1);
+        cudaEventElapsedTime(&ms_leg, b->evl0, b->evl1);
         for (size_t i = 0; i < n; ++i) {
             hyb_problem* p = b->probs[i];
             const hyb::DevState& h = b->h_report[i];
@@ -441,6 +454,7 @@ HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* p
             s.combed = h.comb_on;
             s.bank_size = h.n_bank;
             s.ms = ms;
+            s.ms_leg = ms_leg;
             (void)p;
         }
     }
@@ -450,10 +464,13 @@ HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* p
 HYB_API hyb_status hyb_batch_destroy(hyb_batch* b) {
     if (!b) return HYB_OK;
     if (b->s0) cudaStreamSynchronize(b->s0); else cudaDeviceSynchronize();
+    for (hyb_problem* p : b->probs) p->pdl = true;    // stepped alone from now on
     drop_graphs(b);
     for (auto s : b->pool) cudaStreamDestroy(s);
     for (auto e : b->join_ev) cudaEventDestroy(e);
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->evl0) cudaEventDestroy(b->evl0);
+    if (b->evl1) cudaEventDestroy(b->evl1);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     for (int q = 0; q < 2; ++q) if (b->d_args[q]) cudaFree(b->d_args[q]);

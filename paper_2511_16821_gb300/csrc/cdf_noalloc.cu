@@ -3,7 +3,10 @@
 // Its scratch (block partial sums and per-row totals) lives in one file-scope __device__ array of
 // fixed size, held by every GPU that loads this library until the process exits. Host code may not
 // hand the array's name to a kernel (on the host it is only a stand-in symbol), so the device
-// address is looked up once per device with cudaGetSymbolAddress and cached.
+// address is looked up once per device with cudaGetSymbolAddress and cached for the life of the
+// process. A cudaDeviceReset ends the context that address belongs to (with every other device
+// object of this library: problems, batches), so the library is not called on that device again
+// after a reset.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstddef>
@@ -331,7 +332,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.grow = ((size_t(1) << z.gr) + 1) * 4;
     z.gcol = (size_t)d->ny * ((size_t(1) << z.gc) + 1) * 4;
     z.remf32 = 4 * nc * 4;
-    z.siginv = 4 * nc * 4;
+    z.siginv = 8 * nc * 4;
     z.nscell = d->n_s_cell ? nc * 4 : 0;
     z.aah = d->sn_accel > 0 ? 2 * (size_t)(d->sn_accel + 1) * 4 * nc * T : 0;   // Anderson history
     z.aas = d->sn_accel > 0 ? sn_accel_state_bytes() : 0;
@@ -455,6 +456,8 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->sn_warm_start < 0 || d->sn_warm_start > 2) { *why = "sn_warm_start must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->remap_variant != 0 && d->remap_variant != 1) { *why = "remap_variant must be 0 or 1"; return HYB_EINVAL; }
     if (d->sn_layout < 0 || d->sn_layout > 2) { *why = "sn_layout must be 0, 1 or 2"; return HYB_EINVAL; }
+    if (d->seg_limit < 0 || d->seg_limit > (1 << 30)) { *why = "seg_limit must be in [0, 2^30]"; return HYB_EINVAL; }
+    if (d->wait_limit < 0) { *why = "wait_limit must be >= 0"; return HYB_EINVAL; }
     if (d->remap_variant == 1 && d->n_s == HYB_NS_INF) {
         *why = "remap_variant 1 needs a finite N_s (N_s = infinity has no remap)";
         return HYB_EINVAL;
@@ -505,9 +508,10 @@ void put_quad(const hyb_problem* p, std::vector<unsigned char>* out) {
     }
 }
 
-__global__ void cell_weight_kernel(const double* v, int n, double area_dt, double* out) {
+// per-cell weight of one step's emission, (Q A) dt in that order of rounding
+__global__ void cell_weight_kernel(const double* v, int n, double area, double dt, double* out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) out[k] = v[k] * area_dt;
+    if (k < n) out[k] = __dmul_rn(__dmul_rn(v[k], area), dt);
 }
 
 __global__ void set_nbank_kernel(DevState* st, long long n) { st->n_bank = n; }
@@ -741,16 +745,19 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     const uint32_t* ptab = point_table_host(d->sampler, &ptab_bytes);
     if (chk(cudaMemcpyAsync(p->point_tab, ptab, ptab_bytes, cudaMemcpyHostToDevice, st), "copy point table") != HYB_OK) return bail(HYB_ECUDA);
     if (chk(cudaMemcpyAsync(p->sig, sig.data(), sig.size(), cudaMemcpyHostToDevice, st), "copy sigma") != HYB_OK) return bail(HYB_ECUDA);
-    // FP32 path: per-cell reciprocals (1/sigma_a, 1/sigma_s, 1/sigma_t), 0 where the cross section is
-    // 0, and the cell's scatter limit as the bits of the fourth word (space-dependent N_s)
-    std::vector<float> sinv(4 * nc, 0.0f);
+    // FP32 path: one 32-byte record per cell (a single memory sector): the reciprocals (1/sigma_a,
+    // 1/sigma_s, 1/sigma_t), 0 where the cross section is 0, the cell's scatter limit as the bits of
+    // the fourth word (space-dependent N_s), then sigma_a and sigma_s
+    std::vector<float> sinv(8 * nc, 0.0f);
     for (size_t k = 0; k < nc; ++k) {
         const double sa = d->sigma_a[k], ss = d->sigma_s[k], stt = sa + ss;
-        sinv[4 * k] = sa > 0 ? (float)(1.0 / sa) : 0.0f;
-        sinv[4 * k + 1] = ss > 0 ? (float)(1.0 / ss) : 0.0f;
-        sinv[4 * k + 2] = stt > 0 ? (float)(1.0 / stt) : 0.0f;
+        sinv[8 * k] = sa > 0 ? (float)(1.0 / sa) : 0.0f;
+        sinv[8 * k + 1] = ss > 0 ? (float)(1.0 / ss) : 0.0f;
+        sinv[8 * k + 2] = stt > 0 ? (float)(1.0 / stt) : 0.0f;
         const int32_t lim = d->n_s_cell ? d->n_s_cell[k] : 0;
-        std::memcpy(&sinv[4 * k + 3], &lim, 4);
+        std::memcpy(&sinv[8 * k + 3], &lim, 4);
+        sinv[8 * k + 4] = (float)sa;
+        sinv[8 * k + 5] = (float)ss;
     }
     if (d->n_s_cell &&
         chk(cudaMemcpyAsync(p->ns_cell, d->n_s_cell, nc * 4, cudaMemcpyHostToDevice, st), "copy limits") != HYB_OK)
@@ -781,7 +788,7 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     p->w_src = 0;
     if (d->Q) {
         if (chk(cudaMemcpyAsync(cw, d->Q, nc * 8, cudaMemcpyHostToDevice, st), "copy Q weights") != HYB_OK) return bail(HYB_ECUDA);
-        cell_weight_kernel<<<(p->ncells + 255) / 256, 256, 0, st>>>(cw, p->ncells, p->area * d->dt, cw);
+        cell_weight_kernel<<<(p->ncells + 255) / 256, 256, 0, st>>>(cw, p->ncells, p->area, d->dt, cw);
         if (chk(launch_cdf_build(p, cw, p->src_cdf, scal, scal + 1), "source cdf") != HYB_OK) return bail(HYB_ECUDA);
         if (chk(cudaMemcpyAsync(host_sc, scal, 16, cudaMemcpyDeviceToHost, st), "read W") != HYB_OK) return bail(HYB_ECUDA);
         if (chk(cudaStreamSynchronize(st), "sync") != HYB_OK) return bail(HYB_ECUDA);
@@ -822,8 +829,10 @@ hyb_status hyb_destroy_problem(hyb_problem* p) {
     return HYB_OK;
 }
 
-// step 1 launches (no host synchronisation)
-static hyb_status leg_launch(hyb_problem* p, int32_t* hist) {
+// step 1 launches over the history range [h0, h1) (no host synchronisation); normalise = false
+// leaves the raw integer tallies (a shard of a history-sharded leg)
+static hyb_status leg_launch(hyb_problem* p, int32_t* hist, long long h0 = 0, long long h1 = LLONG_MAX,
+                             bool normalise = true) {
     const size_t nc = (size_t)p->ncells;
     const size_t acc = p->prec == HYB_FP64 ? 16 : 8;
     const size_t ncp = (size_t)p->tally_copies;
@@ -832,9 +841,9 @@ static hyb_status leg_launch(hyb_problem* p, int32_t* hist) {
     HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, ncp * 4 * nc * acc, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->st, 0, offsetof(DevState, r_histories), p->stream));
     HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
-    HYB_CU(p, launch_mc_leg(p, hist));
-    HYB_CU(p, launch_leg_normalise(p));
-    p->leg_done = true;
+    HYB_CU(p, launch_mc_leg(p, hist, h0, h1));
+    if (normalise) HYB_CU(p, launch_leg_normalise(p));
+    p->leg_done = normalise;
     p->sn_done = false;
     return HYB_OK;
 }
@@ -858,6 +867,41 @@ static hyb_status leg_impl(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) {
 
 hyb_status hyb_mc_leg(hyb_problem* p, hyb_leg_stats* out) { return leg_impl(p, nullptr, out); }
 hyb_status hyb_mc_leg_trace(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) { return leg_impl(p, hist, out); }
+
+// history-sharded leg: a range of the history index space into an exchange block, and a summed
+// block back into the problem's tallies
+hyb_status hyb_leg_exchange_bytes(const hyb_problem* p, size_t* bytes) {
+    if (!p || !bytes) return fail(nullptr, HYB_EINVAL, "null argument");
+    *bytes = leg_exchange_words(p) * sizeof(long long);
+    return HYB_OK;
+}
+
+hyb_status hyb_mc_leg_range(hyb_problem* p, int64_t h0, int64_t h1, void* x_dev, size_t x_bytes, int32_t* hist_dev) {
+    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    if (h0 < 0 || h1 < h0) return fail(p, HYB_EINVAL, "history range must satisfy 0 <= h0 <= h1");
+    if (!x_dev || ((uintptr_t)x_dev & 7)) return fail(p, HYB_EINVAL, "exchange block must be an 8-byte aligned device pointer");
+    if (x_bytes < leg_exchange_words(p) * sizeof(long long)) return fail(p, HYB_ENOMEM, "exchange block too small");
+    hyb_status s = leg_launch(p, hist_dev, h0, h1, false);
+    if (s != HYB_OK) return s;
+    HYB_CU(p, launch_leg_pack(p, (long long*)x_dev));
+    return HYB_OK;
+}
+
+hyb_status hyb_mc_leg_reduce_finish(hyb_problem* p, const void* x_dev, size_t x_bytes, hyb_leg_stats* out) {
+    if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    if (!x_dev || ((uintptr_t)x_dev & 7)) return fail(p, HYB_EINVAL, "exchange block must be an 8-byte aligned device pointer");
+    if (x_bytes < leg_exchange_words(p) * sizeof(long long)) return fail(p, HYB_ENOMEM, "exchange block too small");
+    HYB_CU(p, launch_leg_unpack(p, (const long long*)x_dev));
+    HYB_CU(p, launch_leg_normalise(p));
+    p->leg_done = true;
+    p->sn_done = false;
+    if (out) {
+        hyb_status s = pull_state(p);
+        fill_leg_stats(p, out);
+        if (s != HYB_OK) return s;
+    }
+    return HYB_OK;
+}
 
 // step 2: source iteration with a device-side stop test. With a warm start the previous step's
 // count predicts this one: that many iterations are queued without a read-back (iterations after

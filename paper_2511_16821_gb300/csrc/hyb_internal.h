@@ -118,8 +118,9 @@ struct hyb_problem {
     uint32_t* point_tab;      // Sobol direction numbers (HYB_SOBOL_DIMS x 32) or Halton tables
                               // (HYB_SOBOL_DIMS x kHaltonWords), by the sampler
     void* sig;                // ncells x 2 (T): sigma_a, sigma_s
-    float* sig_inv;           // ncells x 4: 1/sigma_a, 1/sigma_s, 1/sigma_t (FP32 leg; 0 where sigma = 0),
-                              // then the cell's scatter limit as int bits (space-dependent N_s)
+    float* sig_inv;           // ncells x 8 (FP32 leg): 1/sigma_a, 1/sigma_s, 1/sigma_t (0 where sigma = 0),
+                              // the cell's scatter limit as int bits (space-dependent N_s), sigma_a,
+                              // sigma_s, 0, 0
     int32_t* ns_cell;         // per-cell scatter limits (space-dependent N_s), or null
     int32_t* sort_keys;       // census in phase-space order: the sort key of every staging slot
     double *sa_d, *ss_d, *Q_d;  // FP64 copies for the remap density
@@ -163,8 +164,14 @@ struct hyb_problem {
 namespace hyb {
 
 // launchers (defined in the .cu files)
-cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev);
+// the leg over the history index range [h0, h1) of [bank slots | births] (0, LLONG_MAX: all)
+cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev, long long h0, long long h1);
 cudaError_t launch_leg_normalise(hyb_problem* p);
+// the exchange block of a history-sharded leg (int64 words): size, pack after a range leg, and
+// unpack of a summed block into the tallies and counters
+size_t leg_exchange_words(const hyb_problem* p);
+cudaError_t launch_leg_pack(hyb_problem* p, long long* x);
+cudaError_t launch_leg_unpack(hyb_problem* p, const long long* x);
 cudaError_t launch_remap(hyb_problem* p);
 cudaError_t launch_census(hyb_problem* p);   // N_s = infinity: MC-leg census -> new bank
 size_t sn_accel_state_bytes();                // device bytes of the Anderson state

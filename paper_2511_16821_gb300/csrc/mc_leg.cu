@@ -10,6 +10,7 @@
 // moments per cell. Tallies are fixed-point integer atomics (order-free, deterministic).
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <cmath>
 #include <type_traits>
 
@@ -22,7 +23,8 @@ struct LegArgs {
     int nx, ny;
     T dx, dy, cdt;
     const T* sig;               // (sigma_a, sigma_s) per cell
-    const float4* sig_inv;      // FP32 path: (1/sigma_a, 1/sigma_s, 1/sigma_t, 0) per cell (0 where sigma = 0)
+    const float4* sig_inv;      // FP32 path: per cell two float4: (1/sigma_a, 1/sigma_s, 1/sigma_t, limit bits)
+                                // (0 where sigma = 0), then (sigma_a, sigma_s, 0, 0)
     int n_s, sampler, handoff_full, ntab;
     T w_min;
     const uint32_t* V;
@@ -42,6 +44,8 @@ struct LegArgs {
     DevState* st;
     int32_t* hist;
     double sig_s_max, w_src_total, cdt_d;
+    long long h0, h1;           // history index range tracked: [h0, h1) of [bank slots | births]
+    int seg_limit;              // segments per history before the history ends as an error
 };
 
 // State of one live history in a lane.
@@ -50,8 +54,7 @@ struct Hist {
     int ix, iy, n, seg;
     T fx, fy, ox, oy, w, w_start, srem, tau;
     T rox, roy;                 // 1/ox, 1/oy (FP32 face distances)
-    uint32_t idx;
-    long long j;
+    uint32_t idx;               // point index: bank slot or birth index (global index: idx, or nb + idx)
     bool census_stream;
 };
 
@@ -59,7 +62,9 @@ struct Hist {
 struct LegTally {
     unsigned int c[9];         // histories, segments, collisions, leaked, census, killed, reached, errors,
                                // fixed-point tally additions issued
-    long long f[6];            // fixed-point weights: source, absorbed, leaked, census, handoff, killed
+    Acc128 f[4];               // fixed-point weights (128-bit sums): source, leaked, census, killed (the
+                               // absorbed and handed-off weights are derived from the tallies by the
+                               // normalisation)
     int status;
 };
 
@@ -67,13 +72,26 @@ __device__ __forceinline__ void leg_tally_zero(LegTally& t) {
 #pragma unroll
     for (int q = 0; q < 9; ++q) t.c[q] = 0;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) t.f[q] = 0;
+    for (int q = 0; q < 4; ++q) t.f[q] = Acc128{0ull, 0ull};
     t.status = 0;
 }
 
-// Scales of one leg (fixed point of the tallies and of the weight totals). On the FP32 path the
-// exponents are capped at 126 so that every scale is a finite float: a float product by a power of
-// two is exact, and the per-segment bookkeeping then needs no FP64 arithmetic.
+// a += v (v a signed 64-bit value, a a 128-bit two's-complement sum)
+__device__ __forceinline__ void add128(unsigned long long* lo, unsigned long long* hi, long long v) {
+    const unsigned long long nl = *lo + (unsigned long long)v;
+    *hi += (v < 0 ? ~0ull : 0ull) + (nl < *lo ? 1ull : 0ull);
+    *lo = nl;
+}
+
+// Scales of one leg (fixed point of the tallies and of the weight totals). Tallies: sums over the
+// whole leg are bounded by the step's starting weight W (x c dt, x sigma_s,max for the moments),
+// so the scale is 2^(kbits - ceil(log2 bound)). Weight statistics: every value one history adds is
+// at most its starting weight, bounded by the largest bank weight or the birth weight, so each is an
+// int64 at scale 2^(62 - ceil(log2 w_max)) and the sums are 128-bit: the resolution is set by a
+// single history's weight, not by the step total (many identical small birth weights would
+// otherwise round alike). On the FP32 path the exponents are capped at 126 so that every scale is a
+// finite float: a float product by a power of two is exact, and the per-segment bookkeeping then
+// needs no FP64 arithmetic.
 struct LegScales {
     int kt, km, kw;
     double scw, sct, scm;     // 2^kw, 2^kt, 2^km
@@ -85,7 +103,8 @@ __device__ __forceinline__ LegScales leg_scales(const LegArgs<T>& a) {
     LegScales s;
     s.kt = scale_exponent(Wstep * a.cdt_d, Prec<T>::kbits);
     s.km = scale_exponent(Wstep * a.cdt_d * a.sig_s_max, Prec<T>::kbits);
-    s.kw = scale_exponent(Wstep, 61);
+    const double w0 = a.n_src > 0 ? a.w_src_total / (double)a.n_src : 0.0;
+    s.kw = scale_exponent(fmax(a.st->bank_wmax, w0), 62);
     if (sizeof(T) == 4) {
         s.kt = min(s.kt, 126);
         s.km = min(s.km, 126);
@@ -118,33 +137,22 @@ __device__ __forceinline__ void birth_state(const LegArgs<T>& a, const Points& p
     *tau = a.n_s > 0 ? P::neglog(P::unit(pts(i, 5))) : T(0);
 }
 
-// Work sources of a warp: a fixed range (one chunk of a batch), or chunks of kWarpChunk histories
-// taken from the problem's device counter until [0, N) is exhausted (the single-problem leg, so
-// warps that drew short histories take more and none waits at the end). Integer tallies make the
-// results independent of which warp runs which history.
-struct FixedRange {
-    long long j0, j1;
-    bool given = false;
-    __device__ bool operator()(long long* next, long long* last) {
-        if (given) return false;
-        given = true;
-        *next = j0; *last = j1;
-        return j0 < j1;
-    }
-};
-
+// Work sources of a warp: chunks of kWarpChunk histories taken from a counter (the single-problem
+// leg: warps that drew short histories take more and none waits at the end; the batched leg: the
+// CTA's share of one work-queue chunk). Global history index = base + counter value, below `end`.
+// Integer tallies make the results independent of which warp runs which history.
 constexpr long long kWarpChunk = 64;
 
 struct CounterChunks {
     unsigned long long* counter;
-    long long N;
+    long long base, end;
     __device__ bool operator()(long long* next, long long* last) {
         long long s = 0;
         if ((threadIdx.x & 31) == 0) s = (long long)atomicAdd(counter, (unsigned long long)kWarpChunk);
-        s = __shfl_sync(0xffffffffu, s, 0);
-        if (s >= N) return false;
+        s = base + __shfl_sync(0xffffffffu, s, 0);
+        if (s >= end) return false;
         *next = s;
-        *last = s + kWarpChunk < N ? s + kWarpChunk : N;
+        *last = s + kWarpChunk < end ? s + kWarpChunk : end;
         return true;
     }
 };
@@ -176,6 +184,11 @@ template <typename T, typename Src>
 __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const uint32_t* sV, const uint32_t* sShC,
                                const uint32_t* sShS, uint64_t key_c, uint64_t key_s, const LegScales& sc,
                                LegTally& t) {
+    // this thread's 128-bit weight sums (source, leaked, census, killed) live in shared memory,
+    // not in registers: the segment loop then fits its register budget without spills
+    __shared__ unsigned long long s_wl[4][kTile], s_wh[4][kTile];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { s_wl[q][threadIdx.x] = 0ull; s_wh[q][threadIdx.x] = 0ull; }
     using P = Prec<T>;
     const T sc_t = (T)sc.sct, sc_m = (T)sc.scm;
     const double scw = sc.scw;
@@ -200,9 +213,6 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
     pts.ntab = a.ntab;
     Hist<T> h;
     bool alive = false;
-    // weight removed from the live history so far (FP32 path: float, one conversion per history)
-    using wacc_t = typename std::conditional<sizeof(T) == 4, float, double>::type;
-    wacc_t d_abs = 0, d_hand = 0;
     long long next = 0, last = 0;
     bool exhausted = false;
 
@@ -220,7 +230,6 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             need &= ~__ballot_sync(0xffffffffu, mine);
             if (mine) {
                 // ---- start a history: bank pick-up or birth from Q -----------------------------
-                h.j = j;
                 bool ok = true;
                 if (j < nb) {
                     h.idx = (uint32_t)j;
@@ -256,8 +265,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                     if constexpr (kF32) { h.rox = P::rcp(h.ox); h.roy = P::rcp(h.oy); }
                     ++t.c[0];
                     h.w_start = h.w;
-                    t.f[0] += fix_w(h.w, scw, scw_f);
-                    d_abs = 0; d_hand = 0;
+                    add128(&s_wl[0][threadIdx.x], &s_wh[0][threadIdx.x], fix_w(h.w, scw, scw_f));
                     h.n = 0;
                     h.seg = 0;
                     if ((a.ns_cell ? __ldg(a.ns_cell + h.iy * nx + h.ix) : Ns) == 0) ++t.c[6];
@@ -285,7 +293,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
         if constexpr (kF32) {
             // FP32: products with per-cell and per-flight reciprocals instead of divisions; the
             // fourth word of the reciprocal record carries the cell's scatter limit
-            const float4 iv = __ldg(a.sig_inv + k);
+            const float4 iv = __ldg(a.sig_inv + 2 * (size_t)k);
             isa = iv.x; iss = iv.y; ist = iv.z;
             if (a.ns_cell) Nk = __float_as_int(iv.w);
             dxf = h.ox > T(0) ? (DX - h.fx) * h.rox : (h.ox < T(0) ? h.fx * (-h.rox) : INF);
@@ -307,12 +315,15 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
         } else { l = h.srem; ev = 2; }
 
         if (h.n < Nk) {
-            T att, e;
-            P::att_e(sa * l, &att, &e);
-            const T pre_c = sa > T(0) ? (kF32 ? h.w * att * isa : h.w * att / sa) : h.w * l;
+            // implicit capture with sigma_a (a pure scatterer keeps its weight and scores w l)
+            T pre_c = h.w * l;
+            if (sa > T(0)) {
+                T att, e;
+                P::att_e(sa * l, &att, &e);
+                pre_c = kF32 ? h.w * att * isa : h.w * att / sa;
+                h.w = h.w * e;
+            }
             t.c[8] += P::add(&pre_b[k], pre_c, sc_t);
-            d_abs += (wacc_t)(h.w * att);
-            h.w = h.w * e;
             h.tau = P::msub(h.tau, ss, l);
         } else {
             T att, e;
@@ -335,10 +346,6 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                            sw * P::fma_(xi0 * eta0, I0, P::fma_(P::fma_(xi0, aeta, eta0 * axi), I1, axi * aeta * I2)),
                            sc_m);
                 }
-            }
-            if (st > T(0)) {
-                d_hand += (wacc_t)(h.w * att * (kF32 ? ss * ist : ss / st));
-                d_abs += (wacc_t)(h.w * att * (kF32 ? sa * ist : sa / st));
             }
             h.w = h.w * e;
         }
@@ -370,13 +377,13 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             if (h.n >= Nk) ++t.c[6];
         }
         if (fate < 0 && a.w_min > T(0) && h.w < a.w_min * h.w_start) fate = kFateKilled;
-        if (fate < 0 && h.seg >= (int)kMaxSegments) fate = kFateError;
+        if (fate < 0 && h.seg >= a.seg_limit) fate = kFateError;
         if (fate >= 0) {
             // ---- end of the history ------------------------------------------------------------
             const long long fw = fix_w(h.w, scw, scw_f);
             if (a.stage_census) {
                 // N_s = infinity or steps 3'/4': the census survivors are kept (history order)
-                const long long j = h.j;
+                const long long j = h.census_stream ? (long long)h.idx : nb + (long long)h.idx;
                 if (fate == kFateCensus) {
                     a.cens.cell[j] = h.iy * nx + h.ix;
                     a.cens.fx[j] = clamp_(h.fx, T(0), DX); a.cens.fy[j] = clamp_(h.fy, T(0), DY);
@@ -385,51 +392,74 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                     a.cens.cell[j] = -1;
                 }
             }
-            if (fate == kFateCensus) { ++t.c[4]; t.f[3] += fw; }
-            else if (fate == kFateLeaked) { ++t.c[3]; t.f[2] += fw; }
-            else if (fate == kFateKilled) { ++t.c[5]; t.f[5] += fw; }
+            if (fate == kFateCensus) { ++t.c[4]; add128(&s_wl[2][threadIdx.x], &s_wh[2][threadIdx.x], fw); }
+            else if (fate == kFateLeaked) { ++t.c[3]; add128(&s_wl[1][threadIdx.x], &s_wh[1][threadIdx.x], fw); }
+            else if (fate == kFateKilled) { ++t.c[5]; add128(&s_wl[3][threadIdx.x], &s_wh[3][threadIdx.x], fw); }
             else { ++t.c[7]; t.status |= kStSegments; }
-            t.f[1] += fix_w(d_abs, scw, scw_f);
-            t.f[4] += fix_w(d_hand, scw, scw_f);
             t.c[1] += (unsigned int)h.seg;
             if (a.hist) {
                 const int4 r = make_int4(h.iy * nx + h.ix, fate, h.n, h.seg);
-                reinterpret_cast<int4*>(a.hist)[h.j] = r;
+                reinterpret_cast<int4*>(a.hist)[h.census_stream ? (long long)h.idx : nb + (long long)h.idx] = r;
             }
             alive = false;
         }
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const unsigned long long nl = t.f[q].lo + s_wl[q][threadIdx.x];
+        t.f[q].hi += s_wh[q][threadIdx.x] + (nl < t.f[q].lo ? 1ull : 0ull);
+        t.f[q].lo = nl;
+    }
+}
+
+// 128-bit warp sum (lane 0 gets the total)
+__device__ __forceinline__ Acc128 warp_sum_128(Acc128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+        const unsigned long long hi = __shfl_down_sync(0xffffffffu, v.hi, o);
+        const unsigned long long nl = v.lo + lo;
+        v.hi += hi + (nl < v.lo ? 1ull : 0ull);
+        v.lo = nl;
+    }
+    return v;
 }
 
 // Block reduction of the per-thread statistics into the problem's counters (all threads call).
 __device__ void leg_flush(DevState* st, LegTally& t, const LegScales& sc, bool write_scales) {
-    __shared__ unsigned long long s_c[kTile / 32][15];
+    __shared__ unsigned long long s_c[kTile / 32][9];
+    __shared__ Acc128 s_w[kTile / 32][4];
     const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
-    unsigned long long cs[15];
+    unsigned long long cs[9];
+    Acc128 ws[4];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) cs[q] = (unsigned long long)t.c[q];
+    for (int q = 0; q < 9; ++q) cs[q] = warp_sum_u64((unsigned long long)t.c[q]);
 #pragma unroll
-    for (int q = 0; q < 6; ++q) cs[9 + q] = (unsigned long long)t.f[q];
-#pragma unroll
-    for (int q = 0; q < 15; ++q) cs[q] = warp_sum_u64(cs[q]);
-    if (lane == 0)
-        for (int q = 0; q < 15; ++q) s_c[wl][q] = cs[q];
+    for (int q = 0; q < 4; ++q) ws[q] = warp_sum_128(t.f[q]);
+    if (lane == 0) {
+        for (int q = 0; q < 9; ++q) s_c[wl][q] = cs[q];
+        for (int q = 0; q < 4; ++q) s_w[wl][q] = ws[q];
+    }
     if (t.status) atomicOr(&st->status, t.status);
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long* cdst[9] = {&st->histories, &st->segments, &st->collisions, &st->leaked,
                                        &st->census, &st->killed, &st->reached, &st->errors, &st->tally_adds};
-        Acc128* wdst[6] = {&st->w_source, &st->w_absorbed, &st->w_leaked, &st->w_census,
-                           &st->w_handoff, &st->w_killed};
+        Acc128* wdst[4] = {&st->w_source, &st->w_leaked, &st->w_census, &st->w_killed};
         const int nw = (int)(blockDim.x >> 5);
-        for (int q = 0; q < 15; ++q) {
+        for (int q = 0; q < 9; ++q) {
             unsigned long long v = 0;
             for (int ww = 0; ww < nw; ++ww) v += s_c[ww][q];
-            if (q < 9) { if (v) atomicAdd(cdst[q], v); }
-            else if (v) {
-                const long long sv = (long long)v;
-                atomic_add128(wdst[q - 9], (unsigned long long)sv, sv < 0 ? ~0ull : 0ull);
+            if (v) atomicAdd(cdst[q], v);
+        }
+        for (int q = 0; q < 4; ++q) {
+            unsigned long long lo = 0, hi = 0;
+            for (int ww = 0; ww < nw; ++ww) {
+                const unsigned long long nl = lo + s_w[ww][q].lo;
+                hi += s_w[ww][q].hi + (nl < lo ? 1ull : 0ull);
+                lo = nl;
             }
+            if (lo || hi) atomic_add128(wdst[q], lo, hi);
         }
         if (write_scales) {
             st->k_track = sc.kt;
@@ -440,9 +470,12 @@ __device__ void leg_flush(DevState* st, LegTally& t, const LegScales& sc, bool w
     __syncthreads();
 }
 
-// Single problem: the grid's warps split [bank slots | births] into contiguous slices.
+// Single problem: a persistent grid whose warps take chunks of the history index range [h0, h1)
+// (clamped to [0, bank + births)) from the problem's counter.
+// FP32: four CTAs of 256 threads per SM (64 registers; a few bytes spill outside the segment loop,
+// measured 5 % faster than three CTAs without spills); FP64: two
 template <typename T>
-__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(LegArgs<T> a) {
+__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) mc_leg_kernel(LegArgs<T> a) {
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
     uint32_t* sShC = sm + a.ntab * kNibbleWords;
@@ -460,10 +493,11 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) mc_leg_kernel(L
     __syncthreads();
     const long long nb = a.st->n_bank;
     const long long N = nb + a.n_src;
+    const long long h1 = a.h1 < N ? a.h1 : N;
     const LegScales sc = s_sc;
     LegTally t;
     leg_tally_zero(t);
-    leg_warp_range<T>(a, CounterChunks{&a.st->leg_next, N}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+    leg_warp_range<T>(a, CounterChunks{&a.st->leg_next, a.h0, h1}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
     leg_flush(a.st, t, sc, blockIdx.x == 0);
 }
 
@@ -494,7 +528,7 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
         const LegChunk ch = chunks[c];
         const unsigned int* src = reinterpret_cast<const unsigned int*>(args + ch.p);
         for (int i = threadIdx.x; i < (int)(sizeof(LegArgs<T>) / 4); i += blockDim.x) s_args[i] = src[i];
-        if (threadIdx.x == 0) s_next = (unsigned long long)ch.j0;
+        if (threadIdx.x == 0) s_next = 0ull;
         __syncthreads();
         const LegArgs<T>& a = *reinterpret_cast<const LegArgs<T>*>(s_args);
         const uint64_t step = (uint64_t)a.st->step;
@@ -512,7 +546,7 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
         const LegScales sc = s_sc;
         LegTally t;
         leg_tally_zero(t);
-        if (ch.j0 < e) leg_warp_range<T>(a, CounterChunks{&s_next, e}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+        if (ch.j0 < e) leg_warp_range<T>(a, CounterChunks{&s_next, ch.j0, e}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
         leg_flush(a.st, t, sc, ch.j0 == 0);
     }
 }
@@ -544,8 +578,11 @@ __global__ void __launch_bounds__(kTile) mc_birth_kernel(LegArgs<T> a) {
     if (threadIdx.x < nt) sSh[threadIdx.x] = dshift(key, (uint64_t)threadIdx.x);
     __syncthreads();
     const Points pts{sV, sSh, key, a.sampler, nt};
-    births_range<T>(a, pts, (long long)blockIdx.x * blockDim.x + threadIdx.x, a.n_src,
-                    (long long)gridDim.x * blockDim.x);
+    // the births inside the leg's history range [h0, h1) of [bank slots | births]
+    const long long nb = a.st->n_bank;
+    const long long i0 = a.h0 > nb ? a.h0 - nb : 0;
+    const long long i1 = a.h1 - nb < a.n_src ? a.h1 - nb : a.n_src;
+    births_range<T>(a, pts, i0 + (long long)blockIdx.x * blockDim.x + threadIdx.x, i1, (long long)gridDim.x * blockDim.x);
 }
 
 // The births of many problems: CTAs pull (problem, [i0, i1)) chunks from a queue.
@@ -581,21 +618,38 @@ mc_birth_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __res
 
 // fixed point -> FP64: raw track-length sums, step-average fluxes and hand-off moments, each the
 // exact integer sum of the ncopy tally copies
+// The leg's absorbed and handed-off weights follow from its tallies: a pre-limit segment scores
+// w (1 - e^{-sigma_a l}) / sigma_a (w l where sigma_a = 0) and loses sigma_a times that to
+// absorption; a post-limit one scores w (1 - e^{-sigma_t l}) / sigma_t and loses sigma_a and
+// sigma_s times that to absorption and to the hand-off. So w_absorbed = sum_k sigma_a,k (pre_k +
+// post_k) and w_handoff = sum_k sigma_s,k post_k, each cell's product added in 128-bit fixed point
+// (order-free) at the weight statistics' scale.
 template <typename T>
 __global__ void leg_normalise_kernel(const typename Prec<T>::acc_t* pre, const typename Prec<T>::acc_t* post,
-                                     const typename Prec<T>::acc_t* mom, int ncopy, const DevState* st, int ncells,
-                                     double inv_adt, double* pre_raw, double* post_raw, double* pre_d,
-                                     double* post_d, double* mom_d) {
+                                     const typename Prec<T>::acc_t* mom, int ncopy, DevState* st, int ncells,
+                                     double inv_adt, const double* sa, const double* ss, double* pre_raw,
+                                     double* post_raw, double* pre_d, double* post_d, double* mom_d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= ncells) return;
-    const double it = ldexp(1.0, -st->k_track), im = ldexp(1.0, -st->k_mom);
-    const size_t n1 = (size_t)ncells, n4 = 4 * (size_t)ncells;
-    const double a = Prec<T>::sum_to_double(&pre[k], n1, ncopy, it), b = Prec<T>::sum_to_double(&post[k], n1, ncopy, it);
-    pre_raw[k] = a;
-    post_raw[k] = b;
-    pre_d[k] = a * inv_adt;
-    post_d[k] = b * inv_adt;
-    for (int j = 0; j < 4; ++j) mom_d[4 * k + j] = Prec<T>::sum_to_double(&mom[4 * k + j], n4, ncopy, im);
+    Acc128 wa{0ull, 0ull}, wh{0ull, 0ull};
+    if (k < ncells) {
+        const double it = ldexp(1.0, -st->k_track), im = ldexp(1.0, -st->k_mom);
+        const size_t n1 = (size_t)ncells, n4 = 4 * (size_t)ncells;
+        const double a = Prec<T>::sum_to_double(&pre[k], n1, ncopy, it), b = Prec<T>::sum_to_double(&post[k], n1, ncopy, it);
+        pre_raw[k] = a;
+        post_raw[k] = b;
+        pre_d[k] = a * inv_adt;
+        post_d[k] = b * inv_adt;
+        for (int j = 0; j < 4; ++j) mom_d[4 * k + j] = Prec<T>::sum_to_double(&mom[4 * k + j], n4, ncopy, im);
+        const double scw = ldexp(1.0, st->k_w);
+        to_i128(sa[k] * (a + b) * scw, &wa.lo, &wa.hi);
+        to_i128(ss[k] * b * scw, &wh.lo, &wh.hi);
+    }
+    wa = warp_sum_128(wa);
+    wh = warp_sum_128(wh);
+    if ((threadIdx.x & 31) == 0) {
+        if (wa.lo || wa.hi) atomic_add128(&st->w_absorbed, wa.lo, wa.hi);
+        if (wh.lo || wh.hi) atomic_add128(&st->w_handoff, wh.lo, wh.hi);
+    }
 }
 
 // initial bank: n particles from the initial-weight CDF (stream INIT, step 0), isotropic, t = 0
@@ -688,8 +742,8 @@ static int stride_grid(long long work) {
 }
 
 // resident CTAs of kTile threads per SM: the single-problem leg keeps its descriptor in constant
-// memory and fits 3 (FP32); the batched leg holds a chunk's descriptor in registers and runs 2
-static int leg_ctas_per_sm(int prec) { return prec == HYB_FP64 ? 2 : 3; }
+// memory and fits 4 (FP32); the batched leg holds a chunk's descriptor in registers and runs 2
+static int leg_ctas_per_sm(int prec) { return prec == HYB_FP64 ? 2 : 4; }
 
 // persistent grid: every CTA resident at once (warps then take history chunks from the counter)
 static int leg_grid(long long work, int prec) {
@@ -737,18 +791,36 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.hist = hist;
     a.sig_s_max = p->sig_s_max;
     a.w_src_total = p->has_src ? p->w_src : 0.0;
+    a.h0 = 0;
+    a.h1 = LLONG_MAX;
+    a.seg_limit = p->d.seg_limit > 0 ? p->d.seg_limit : (int)kMaxSegments;
     return a;
 }
 
+// the leg kernels' dynamic shared memory (point tables: up to 65 dimensions) beside their static
+// per-thread weight sums exceeds the default 48 KB per block: raise the kernel's limit once
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t dynamic_bytes) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    if (fa.sharedSizeBytes + dynamic_bytes <= (48u << 10)) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dynamic_bytes);
+}
+
 template <typename T>
-static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist) {
-    const LegArgs<T> a = leg_args<T>(p, hist, p->cur);
+static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist, long long h0, long long h1) {
+    LegArgs<T> a = leg_args<T>(p, hist, p->cur);
+    a.h0 = h0;
+    a.h1 = h1;
     const size_t smem = (size_t)(a.ntab * kNibbleWords + 2 * a.ntab) * sizeof(uint32_t);
-    const long long work = p->bank_cap + a.n_src;
+    const long long work = (h1 < p->bank_cap + a.n_src ? h1 : p->bank_cap + a.n_src) - h0;
     if (a.n_src > 0 && a.births.cell) {
         const long long g = (a.n_src + kTile - 1) / kTile;
         mc_birth_kernel<T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kTile, 0, p->stream>>>(a);
     }
+    cudaError_t e = allow_smem(mc_leg_kernel<T>, smem);
+    if (e != cudaSuccess) return e;
     mc_leg_kernel<T><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
     return cudaGetLastError();
 }
@@ -777,6 +849,9 @@ cudaError_t launch_mc_leg_batch(int prec, const void* d_args, const void* d_chun
             mc_birth_batch_kernel<float><<<bg, kTile, 0, s>>>((const LegArgs<float>*)d_args,
                                                               (const LegChunk*)d_bchunks, nbchunks, d_bhead);
     }
+    cudaError_t e = prec == HYB_FP64 ? allow_smem(mc_leg_batch_kernel<double>, smem)
+                                     : allow_smem(mc_leg_batch_kernel<float>, smem);
+    if (e != cudaSuccess) return e;
     if (prec == HYB_FP64)
         mc_leg_batch_kernel<double><<<grid, block, smem, s>>>((const LegArgs<double>*)d_args,
                                                              (const LegChunk*)d_chunks, nchunks, d_head, V, ntab_max);
@@ -786,8 +861,152 @@ cudaError_t launch_mc_leg_batch(int prec, const void* d_args, const void* d_chun
     return cudaGetLastError();
 }
 
-cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev) {
-    return p->prec == HYB_FP64 ? mc_leg_t<double>(p, hist_dev) : mc_leg_t<float>(p, hist_dev);
+cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev, long long h0, long long h1) {
+    return p->prec == HYB_FP64 ? mc_leg_t<double>(p, hist_dev, h0, h1) : mc_leg_t<float>(p, hist_dev, h0, h1);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Exchange block of a history-sharded leg: the raw integer results of a leg over one index range,
+// laid out so that the element-wise int64 sum of the blocks of ranges that partition [0, N) is
+// the block of the whole leg (an all-reduce with a plain integer sum). Words: [0, 12) counters
+// (histories, segments, collisions, leaked, census, killed, reached, errors, tally adds, then how
+// many ranges raised the bounds / segments / capacity status bits); [12, 36) the six weight sums,
+// four 32-bit limbs each (value = sum_i limb_i 2^(32 i) mod 2^128, top limb signed); then the
+// tallies pre, post (ncells each) and the moments (4 ncells): FP32 path one int64 word per value
+// (two's-complement sums wrap consistently), FP64 path four limbs per 128-bit accumulator.
+// ---------------------------------------------------------------------------------------------
+constexpr int kXHead = 12 + 6 * 4;
+
+__host__ __device__ inline size_t xblk_words(int prec, long long ncells) {
+    return (size_t)kXHead + (size_t)6 * ncells * (prec == HYB_FP64 ? 4 : 1);
+}
+
+__device__ __forceinline__ void to_limbs(unsigned long long lo, unsigned long long hi, long long* w) {
+    w[0] = (long long)(lo & 0xffffffffull);
+    w[1] = (long long)(lo >> 32);
+    w[2] = (long long)(hi & 0xffffffffull);
+    w[3] = (long long)(int)(unsigned int)(hi >> 32);
+}
+
+// sum_i w_i 2^(32 i) mod 2^128 for signed 64-bit limb sums w_i
+__device__ __forceinline__ void from_limbs(const long long* w, unsigned long long* lo, unsigned long long* hi) {
+    unsigned long long L = 0, H = 0;
+    auto add = [&](unsigned long long al, unsigned long long ah) {
+        const unsigned long long nl = L + al;
+        H += ah + (nl < L ? 1ull : 0ull);
+        L = nl;
+    };
+    add((unsigned long long)w[0], w[0] < 0 ? ~0ull : 0ull);
+    add((unsigned long long)w[1] << 32, (unsigned long long)(w[1] >> 32));
+    add(0ull, (unsigned long long)w[2]);
+    add(0ull, (unsigned long long)w[3] << 32);
+    *lo = L;
+    *hi = H;
+}
+
+__device__ __forceinline__ void acc_fold(const unsigned long long* p, size_t stride, int n, long long* w) {
+    unsigned long long v = 0;
+    for (int c = 0; c < n; ++c) v += p[c * stride];
+    w[0] = (long long)v;
+}
+__device__ __forceinline__ void acc_fold(const Acc128* p, size_t stride, int n, long long* w) {
+    unsigned long long lo = 0, hi = 0;
+    for (int c = 0; c < n; ++c) {
+        const Acc128 v = p[c * stride];
+        const unsigned long long nl = lo + v.lo;
+        hi += v.hi + (nl < lo ? 1ull : 0ull);
+        lo = nl;
+    }
+    to_limbs(lo, hi, w);
+}
+__device__ __forceinline__ void acc_put(unsigned long long* p, const long long* w) { *p = (unsigned long long)w[0]; }
+__device__ __forceinline__ void acc_put(Acc128* p, const long long* w) { from_limbs(w, &p->lo, &p->hi); }
+
+template <typename T>
+__global__ void leg_pack_kernel(const typename Prec<T>::acc_t* pre, const typename Prec<T>::acc_t* post,
+                                const typename Prec<T>::acc_t* mom, int ncopy, int ncells, const DevState* st,
+                                long long* x) {
+    constexpr int L = sizeof(T) == 8 ? 4 : 1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n1 = (size_t)ncells, n4 = 4 * (size_t)ncells;
+    long long* t = x + kXHead;
+    if (k < ncells) {
+        acc_fold(pre + k, n1, ncopy, t + (size_t)L * k);
+        acc_fold(post + k, n1, ncopy, t + (size_t)L * (n1 + k));
+        for (int j = 0; j < 4; ++j) acc_fold(mom + 4 * (size_t)k + j, n4, ncopy, t + (size_t)L * (2 * n1 + 4 * (size_t)k + j));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long c[9] = {st->histories, st->segments, st->collisions, st->leaked, st->census,
+                                         st->killed, st->reached, st->errors, st->tally_adds};
+        for (int i = 0; i < 9; ++i) x[i] = (long long)c[i];
+        x[9] = (st->status & kStBounds) ? 1 : 0;
+        x[10] = (st->status & kStSegments) ? 1 : 0;
+        x[11] = (st->status & kStCapacity) ? 1 : 0;
+        const Acc128* ws[6] = {&st->w_source, &st->w_absorbed, &st->w_leaked, &st->w_census, &st->w_handoff,
+                               &st->w_killed};
+        for (int i = 0; i < 6; ++i) to_limbs(ws[i]->lo, ws[i]->hi, x + 12 + 4 * i);
+    }
+}
+
+// the (summed) block into tally copy 0 (other copies zero) and the leg counters
+template <typename T>
+__global__ void leg_unpack_kernel(typename Prec<T>::acc_t* pre, typename Prec<T>::acc_t* post,
+                                  typename Prec<T>::acc_t* mom, int ncopy, int ncells, DevState* st,
+                                  const long long* x) {
+    using acc_t = typename Prec<T>::acc_t;
+    constexpr int L = sizeof(T) == 8 ? 4 : 1;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n1 = (size_t)ncells, n4 = 4 * (size_t)ncells;
+    const long long* t = x + kXHead;
+    if (k < ncells) {
+        acc_t z;
+        memset(&z, 0, sizeof(z));
+        acc_put(pre + k, t + (size_t)L * k);
+        acc_put(post + k, t + (size_t)L * (n1 + k));
+        for (int j = 0; j < 4; ++j) acc_put(mom + 4 * (size_t)k + j, t + (size_t)L * (2 * n1 + 4 * (size_t)k + j));
+        for (int c = 1; c < ncopy; ++c) {
+            pre[c * n1 + k] = z;
+            post[c * n1 + k] = z;
+            for (int j = 0; j < 4; ++j) mom[c * n4 + 4 * (size_t)k + j] = z;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        unsigned long long* c[9] = {&st->histories, &st->segments, &st->collisions, &st->leaked, &st->census,
+                                    &st->killed, &st->reached, &st->errors, &st->tally_adds};
+        for (int i = 0; i < 9; ++i) *c[i] = (unsigned long long)x[i];
+        st->status = (x[9] ? kStBounds : 0) | (x[10] ? kStSegments : 0) | (x[11] ? kStCapacity : 0);
+        Acc128* ws[6] = {&st->w_source, &st->w_absorbed, &st->w_leaked, &st->w_census, &st->w_handoff,
+                         &st->w_killed};
+        for (int i = 0; i < 6; ++i) from_limbs(x + 12 + 4 * i, &ws[i]->lo, &ws[i]->hi);
+    }
+}
+
+size_t leg_exchange_words(const hyb_problem* p) { return xblk_words(p->prec, p->ncells); }
+
+cudaError_t launch_leg_pack(hyb_problem* p, long long* x) {
+    const int g = (p->ncells + 255) / 256;
+    if (p->prec == HYB_FP64)
+        leg_pack_kernel<double><<<g, 256, 0, p->stream>>>((const Acc128*)p->acc_pre, (const Acc128*)p->acc_post,
+                                                          (const Acc128*)p->acc_mom, p->tally_copies, p->ncells, p->st, x);
+    else
+        leg_pack_kernel<float><<<g, 256, 0, p->stream>>>((const unsigned long long*)p->acc_pre,
+                                                         (const unsigned long long*)p->acc_post,
+                                                         (const unsigned long long*)p->acc_mom, p->tally_copies,
+                                                         p->ncells, p->st, x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_leg_unpack(hyb_problem* p, const long long* x) {
+    const int g = (p->ncells + 255) / 256;
+    if (p->prec == HYB_FP64)
+        leg_unpack_kernel<double><<<g, 256, 0, p->stream>>>((Acc128*)p->acc_pre, (Acc128*)p->acc_post,
+                                                            (Acc128*)p->acc_mom, p->tally_copies, p->ncells, p->st, x);
+    else
+        leg_unpack_kernel<float><<<g, 256, 0, p->stream>>>((unsigned long long*)p->acc_pre,
+                                                           (unsigned long long*)p->acc_post,
+                                                           (unsigned long long*)p->acc_mom, p->tally_copies,
+                                                           p->ncells, p->st, x);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_leg_normalise(hyb_problem* p) {
@@ -796,14 +1015,13 @@ cudaError_t launch_leg_normalise(hyb_problem* p) {
     if (p->prec == HYB_FP64)
         leg_normalise_kernel<double><<<g, 256, 0, p->stream>>>((const Acc128*)p->acc_pre, (const Acc128*)p->acc_post,
                                                                (const Acc128*)p->acc_mom, p->tally_copies, p->st,
-                                                               p->ncells, inv_adt,
+                                                               p->ncells, inv_adt, p->sa_d, p->ss_d,
                                                                p->pre_raw, p->post_raw, p->pre_d, p->post_d, p->mom_d);
     else
         leg_normalise_kernel<float><<<g, 256, 0, p->stream>>>(
             (const unsigned long long*)p->acc_pre, (const unsigned long long*)p->acc_post,
-            (const unsigned long long*)p->acc_mom, p->tally_copies, p->st, p->ncells, inv_adt, p->pre_raw,
-            p->post_raw, p->pre_d,
-            p->post_d, p->mom_d);
+            (const unsigned long long*)p->acc_mom, p->tally_copies, p->st, p->ncells, inv_adt, p->sa_d, p->ss_d,
+            p->pre_raw, p->post_raw, p->pre_d, p->post_d, p->mom_d);
     return cudaGetLastError();
 }
 

@@ -225,21 +225,28 @@ cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w, Cdf2DView cdf
 // remap density: f = (Q + sigma_s (phi_pre + phi_post) + sigma_s phi_c0, sigma_s phi_c1..3) for
 // Eq. (R); (sigma_s phi_post + sigma_s phi_c0, sigma_s phi_c1..3) for Eq. (R') (relabel = 0)
 // ---------------------------------------------------------------------------------------------
+// pre_raw, post_raw: the leg's raw track-length sums (the step-average flux times A dt); the
+// density is formed in separately rounded operations in the order of its definition, so the FP64
+// remap follows the reference arithmetic bit for bit
 __global__ void remap_density_kernel(int ncells, double adt, const double* __restrict__ Q, const double* __restrict__ ss,
-                                     const double* __restrict__ pre, const double* __restrict__ post,
+                                     const double* __restrict__ pre_raw, const double* __restrict__ post_raw,
                                      const double* __restrict__ phi, double* f, float* f32, int* fpos, double* q,
-                                     DevState* st, int relabel) {
+                                     DevState* st, int relabel, double area, double dt) {
     pdl_wait();
     pdl_trigger();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     double r = 0;
     if (k < ncells) {
         const double s = ss[k];
-        const double f0 = relabel ? Q[k] + s * (pre[k] + post[k]) + s * phi[4 * k] : s * post[k] + s * phi[4 * k];
+        // Eq. (R): Q + sigma_s (T_pre + T_post) / (A dt) + sigma_s phi_c; Eq. (R'): sigma_s T_post / (A dt)
+        // + sigma_s phi_c
+        const double sphi = __dmul_rn(s, phi[4 * k]);
+        const double f0 = relabel ? __dadd_rn(__dadd_rn(Q[k], __ddiv_rn(__dmul_rn(s, __dadd_rn(pre_raw[k], post_raw[k])), adt)), sphi)
+                                  : __dadd_rn(__ddiv_rn(__dmul_rn(s, post_raw[k]), adt), sphi);
         const double f1 = s * phi[4 * k + 1], f2 = s * phi[4 * k + 2], f3 = s * phi[4 * k + 3];
         f[4 * k] = f0; f[4 * k + 1] = f1; f[4 * k + 2] = f2; f[4 * k + 3] = f3;
         reinterpret_cast<float4*>(f32)[k] = make_float4((float)f0, (float)f1, (float)f2, (float)f3);
-        const double qc = f0 * adt;
+        const double qc = __dmul_rn(__dmul_rn(f0, area), dt);   // (f0 A) dt
         q[k] = qc;
         // all four nodal values >= 0: births sampled from the bilinear density itself
         const bool pos = f0 - f1 - f2 + f3 >= 0 && f0 + f1 - f2 - f3 >= 0 && f0 - f1 + f2 - f3 >= 0 &&
@@ -303,10 +310,12 @@ struct Particle { int cell; T fx, fy, ox, oy, w; bool alive; };
 // inverse CDF on [-1,1] of the density proportional to a + b s (a > 0, |b| <= a)
 template <typename T>
 __device__ __forceinline__ T inv_linear(T a, T b, T u) {
+    using P = Prec<T>;
     if (!(a > T(0))) return T(2) * u - T(1);
     const T amb = a - b;
-    const T disc = amb * amb + T(4) * a * b * u;
-    const T t = T(4) * a * u / (amb + Prec<T>::sqrt_(disc > T(0) ? disc : T(0)));
+    // (a - b)^2 + 4 a b u with the products rounded apart on the FP64 path (a fused form on FP32)
+    const T disc = P::madd(amb, amb, T(4) * a * b * u);
+    const T t = T(4) * a * u / (amb + P::sqrt_(disc > T(0) ? disc : T(0)));
     return clamp_(t - T(1), T(-1), T(1));
 }
 
@@ -365,12 +374,13 @@ __device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long
         T xi, eta;
         if (a.fpos[k]) {
             xi = inv_linear<T>(f0, f1, frx);
-            eta = inv_linear<T>(f0 + f1 * xi, f2 + f3 * xi, fry);
+            eta = inv_linear<T>(P::madd(f1, xi, f0), P::madd(f3, xi, f2), fry);
             w = wbar;
         } else {
             xi = T(2) * frx - T(1);
             eta = T(2) * fry - T(1);
-            w = wbar * (f0 + f1 * xi + f2 * eta + f3 * xi * eta) / (f0 < T(0) ? -f0 : f0);
+            // f(xi, eta) = ((f0 + f1 xi) + f2 eta) + (f3 xi) eta, products rounded apart on FP64
+            w = wbar * P::madd(f3 * xi, eta, P::madd(f2, eta, P::madd(f1, xi, f0))) / (f0 < T(0) ? -f0 : f0);
         }
         fx = T(0.5) * (xi + T(1)) * a.dx;
         fy = T(0.5) * (eta + T(1)) * a.dy;
@@ -945,9 +955,9 @@ static cudaError_t remap_t(hyb_problem* p) {
     e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
     if (e != cudaSuccess) return e;
     const bool additive = p->d.remap_variant == 1;
-    remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_d, p->post_d,
+    remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_raw, p->post_raw,
                                            p->sn_phi_d, p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st,
-                                           additive ? 0 : 1);
+                                           additive ? 0 : 1, p->area, p->d.dt);
     e = launch_cdf_build(p, p->rem_q, p->rem_cdf, &p->st->remap_W, &p->st->remap_qmax);
     if (e != cudaSuccess) return e;
     // steps 3'/4': the leg's census (bank slots, then its n_hist source births) leads the slots

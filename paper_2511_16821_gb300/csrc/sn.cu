@@ -111,6 +111,7 @@ struct SweepArgs {
     T* psi;                  // per ordinate, psi (4 Legendre coefficients, mirrored): plain mesh or wavefront
     int* status;             // device status word (bounded waits)
     const int* conv;         // converged flag: set -> the sweep returns at once
+    int poll_limit;          // polls of a strip-pipeline wait before it gives up (status kStSegments)
 };
 
 // source integrals against P_i: sigma_s A n_i phi_i / (4 pi) + m_i / (4 pi dt)
@@ -435,7 +436,7 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
                 const int need = qout - nx + (t0 + PF - 31 < nx ? t0 + PF - 31 : nx);
                 int spins = 0;
                 while (cons[bout] < need) {
-                    if (++spins > (1 << 22)) { timed_out = true; break; }
+                    if (++spins > a.poll_limit) { timed_out = true; break; }
                     __nanosleep(20);
                 }
             }
@@ -456,7 +457,7 @@ __device__ __forceinline__ void sweep_ordinate(const SweepArgs<T>& a, int m, int
                         if (t < nx) ok &= Ring<T>::get(rin + (size_t)(t + 31) * RW, (uint32_t)(qin + t + 1), &rv0[i], &rv1[i]);
                     }
                     if (ok) break;
-                    if (++spins > (1 << 22)) { timed_out = true; break; }
+                    if (++spins > a.poll_limit) { timed_out = true; break; }
                     __nanosleep(20);
                 }
             }
@@ -1022,6 +1023,7 @@ static cudaError_t sn_iteration_t(hyb_problem* p, int first) {
     a.qox = qbuf; a.qoy = qbuf + kMaxOrd;
     a.psi = (T*)p->sn_psi;
     a.status = &p->st->status;
+    a.poll_limit = p->d.wait_limit > 0 ? p->d.wait_limit : (1 << 22);
     a.conv = &p->st->sn_conv;
     a.plane = plane;
     a.wv = wv;

@@ -39,7 +39,7 @@ class Desc(C.Structure):
                 ("sn_tol", C.c_double), ("w_min", C.c_double), ("census_cap", C.c_int64),
                 ("sn_warm_start", C.c_int32), ("census_order", C.c_int32), ("sn_accel", C.c_int32),
                 ("remap_variant", C.c_int32), ("n_s_cell", C.POINTER(C.c_int32)), ("sn_layout", C.c_int32),
-                ("pad2", C.c_int32)]
+                ("seg_limit", C.c_int32), ("wait_limit", C.c_int32), ("pad3", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -82,6 +82,9 @@ def lib():
         L.hyb_destroy_problem.argtypes = [P]
         L.hyb_mc_leg.argtypes = [P, C.POINTER(Stats)]
         L.hyb_mc_leg_trace.argtypes = [P, P, C.POINTER(Stats)]
+        L.hyb_leg_exchange_bytes.argtypes = [P, C.POINTER(C.c_size_t)]
+        L.hyb_mc_leg_range.argtypes = [P, C.c_int64, C.c_int64, P, C.c_size_t, P]
+        L.hyb_mc_leg_reduce_finish.argtypes = [P, P, C.c_size_t, C.POINTER(Stats)]
         L.hyb_collided_solve.argtypes = [P, C.POINTER(Stats)]
         L.hyb_remap.argtypes = [P, C.POINTER(Stats)]
         L.hyb_step.argtypes = [P, C.c_int32, C.POINTER(Stats)]
@@ -144,7 +147,8 @@ def make_desc(spec: ProblemSpec) -> tuple[Desc, list]:
              precision=spec.precision, sn_order=spec.sn_order, handoff_full=spec.handoff_full,
              sn_max_iter=spec.sn_max_iter, sn_tol=spec.sn_tol, w_min=spec.w_min,
              census_cap=spec.census_cap, sn_warm_start=spec.sn_warm_start, census_order=spec.census_order,
-             sn_accel=spec.sn_accel, remap_variant=spec.remap_variant, sn_layout=spec.sn_layout)
+             sn_accel=spec.sn_accel, remap_variant=spec.remap_variant, sn_layout=spec.sn_layout,
+             seg_limit=spec.seg_limit, wait_limit=spec.wait_limit)
     if spec.n_s_cell is not None:
         lim = np.ascontiguousarray(np.asarray(spec.n_s_cell, dtype=np.int32).ravel())
         keep.append(lim)
@@ -206,6 +210,26 @@ class Problem:
             _check(lib().hyb_mc_leg_trace(self.h, C.c_void_p(trace.data_ptr()), ps), self.h)
         else:
             _check(lib().hyb_mc_leg(self.h, ps), self.h)
+        return s.as_dict() if stats else None
+
+    # --- history-sharded leg --------------------------------------------------------------
+    def exchange_block(self):
+        """A zeroed device int64 tensor of the leg's exchange-block size."""
+        torch = _torch_cuda()
+        n = C.c_size_t(0)
+        _check(lib().hyb_leg_exchange_bytes(self.h, C.byref(n)), self.h)
+        return torch.zeros(int(n.value) // 8, dtype=torch.int64, device="cuda")
+
+    def mc_leg_range(self, h0: int, h1: int, block, trace=None) -> None:
+        """The leg over global history indices [h0, h1) into `block` (see exchange_block)."""
+        _check(lib().hyb_mc_leg_range(self.h, h0, h1, C.c_void_p(block.data_ptr()), block.numel() * 8,
+                                      C.c_void_p(trace.data_ptr()) if trace is not None else None), self.h)
+
+    def mc_leg_reduce_finish(self, block, stats: bool = True) -> dict | None:
+        """Make the (summed) exchange block the problem's leg."""
+        s = Stats()
+        _check(lib().hyb_mc_leg_reduce_finish(self.h, C.c_void_p(block.data_ptr()), block.numel() * 8,
+                                              C.byref(s) if stats else None), self.h)
         return s.as_dict() if stats else None
 
     def collided_solve(self, stats: bool = True) -> dict | None:

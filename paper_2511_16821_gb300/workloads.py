@@ -56,6 +56,8 @@ class ProblemSpec:
     remap_variant: int = 0          # 0: Eq. (R) relabelling remap; 1: steps 3'/4' of the previous hybrids
     n_s_cell: np.ndarray | None = None   # per-cell scatter limits in [0, n_s] (space-dependent N_s)
     sn_layout: int = 0              # sweep memory layout: 0 automatic, 1 padded mesh, 2 wavefront order
+    seg_limit: int = 0              # segments per history before HYB_ETIMEOUT (0: the default 2^20)
+    wait_limit: int = 0             # polls of a collided-solve pipeline wait before HYB_ETIMEOUT (0: 2^22)
     name: str = field(default="problem")
 
     @property

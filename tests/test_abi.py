@@ -51,7 +51,7 @@ def _bad(spec, **kw):
 @pytest.mark.parametrize("mut", [
     dict(nx=0), dict(ny=5000), dict(dt=0.0), dict(c=-1.0), dict(n_s=-1), dict(sn_order=6),
     dict(n_hist=0), dict(sampler=7), dict(precision=3), dict(w_min=1.5), dict(sn_max_iter=0),
-    dict(sn_layout=3), dict(sn_layout=-1),
+    dict(sn_layout=3), dict(sn_layout=-1), dict(seg_limit=-1), dict(seg_limit=(1 << 30) + 1), dict(wait_limit=-5),
 ])
 def test_workspace_size_rejects_bad_descriptors(hyb, mut):
     spec = W.pulse(n_hist=100)
@@ -132,3 +132,14 @@ def test_input_generators_are_deterministic():
     assert c.nx == 28 and c.Q.sum() == 16 and c.sigma_s.reshape(28, 28)[13, 13] == 1.0
     big = W.large(n=64, block=8, n_hist=10)
     assert set(np.round(big.sigma_a + big.sigma_s, 6)) <= {1.0, 10.0, 1000.0}
+
+
+def test_descriptor_layout_matches_header(hyb):
+    # the binding's descriptor struct has the header's size (fields appended at the end keep the
+    # 8-byte alignment of the C struct)
+    assert C.sizeof(hyb.Desc) % 8 == 0
+    names = [f for f, _ in hyb.Desc._fields_]
+    txt = open(os.path.join(ROOT, "include", "hyb.h")).read()
+    body = txt[txt.index("typedef struct {\n    int32_t nx, ny;"):txt.index("} hyb_problem_desc;")]
+    for n in ("seg_limit", "wait_limit", "sn_layout", "n_s_cell"):
+        assert n in names and n in body

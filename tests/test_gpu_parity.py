@@ -18,7 +18,7 @@ from paper_2511_16821_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-from parity_checks import (FLIP_MARGIN_FP64, FP32_RTOL, FP64_RTOL, check_counts, check_fp64_libm,  # noqa: E402
+from parity_checks import (FP32_RTOL, FP32_RTOL_THICK, FP64_RTOL, check_counts, check_fp64_libm,  # noqa: E402
                            check_fp64_tallies, fp32_check, rel_err)
 
 
@@ -104,6 +104,36 @@ def leg_cases():
     ]
 
 
+def gpu_leg_without(H, spec, bank, step, skip_idx):
+    """The leg with the histories at global indices skip_idx left out: range legs over the gaps,
+    their exchange blocks summed and finished (raw tallies as gpu_leg)."""
+    P = H.Problem(spec.with_(ic=None))
+    P.set_bank(bank if bank is not None else {"cell": np.zeros(0, np.int32), **{k: np.zeros(0) for k in ("fx", "fy", "ox", "oy", "w")}, "n": 0})
+    P.set_step(step)
+    total = P.exchange_block()
+    lo = 0
+    for h in sorted(int(x) for x in skip_idx) + [1 << 62]:
+        if h > lo:
+            blk = P.exchange_block()
+            P.mc_leg_range(lo, h, blk)
+            total += blk
+        lo = h + 1
+    st = P.mc_leg_reduce_finish(total)
+    out = dict(pre=P.tally("pre_raw"), post=P.tally("post_raw"), mom=P.tally("handoff"), stats=st)
+    P.close()
+    return out
+
+
+def fp32_without(H, orc, spec32, bank, step, run_oracle):
+    """Regrade of an FP32 leg with some histories taken out of both sides."""
+    def f(idx):
+        n = int(orc.n_histories(spec32, bank))
+        skip = np.zeros(n, np.uint8)
+        skip[idx] = 1
+        return gpu_leg_without(H, spec32, bank, step, idx), run_oracle(skip)
+    return f
+
+
 def bank_for(orc, spec, nb):
     if nb == "ic":
         return orc.init_bank(spec, spec.ic)
@@ -165,8 +195,9 @@ def test_mc_leg_fp32_tolerance(H, orc, case):
     name, spec, nb, step = case
     bank = bank_for(orc, spec, nb)
     o = orc.mc_leg(spec, step, bank, want_hist=True, want_margin=True)
-    g = gpu_leg(H, spec.with_(precision=W.FP32), bank, step)
-    fp32_check(g, o, name)
+    s32 = spec.with_(precision=W.FP32)
+    g = gpu_leg(H, s32, bank, step)
+    fp32_check(g, o, name, fp32_without(H, orc, s32, bank, step, lambda skip: orc.mc_leg(spec, step, bank, skip=skip)))
     s = g["stats"]
     tot = s["w_absorbed"] + s["w_leaked"] + s["w_census"] + s["w_handoff"] + s["w_killed"]
     assert math.isclose(s["w_source"], tot, rel_tol=1e-5)
@@ -350,8 +381,10 @@ def test_checkerboard_full_size_leg(H, orc, opool, n_s):
     check_fp64_tallies(g, o)
     ol = opool.mc_leg(spec, 1, bank, want_hist=True, want_margin=True, elem=orc.LIBM)
     check_fp64_libm(g, ol, spec, bank, f"checkerboard N_s={n_s}")
-    g32 = gpu_leg(H, spec.with_(precision=W.FP32), bank, 1)
-    fp32_check(g32, ol, f"checkerboard N_s={n_s}")
+    s32 = spec.with_(precision=W.FP32)
+    g32 = gpu_leg(H, s32, bank, 1)
+    fp32_check(g32, ol, f"checkerboard N_s={n_s}",
+               fp32_without(H, orc, s32, bank, 1, lambda skip: opool.mc_leg(spec, 1, bank, skip=skip)))
 
 
 def test_large_diffusive_subsample(H, orc, opool):
@@ -373,8 +406,11 @@ def test_large_diffusive_subsample(H, orc, opool):
     ol = opool.mc_leg(spec, 3, bank, want_hist=True, want_margin=True, elem=orc.LIBM)
     check_fp64_libm(g, ol, spec, bank, "large 1024^2 subsample")
     del g
-    g32 = gpu_leg(H, spec.with_(precision=W.FP32), bank, 3)
-    fp32_check(g32, ol, "large 1024^2 subsample")
+    s32 = spec.with_(precision=W.FP32)
+    g32 = gpu_leg(H, s32, bank, 3)
+    fp32_check(g32, ol, "large 1024^2 subsample",
+               fp32_without(H, orc, s32, bank, 3, lambda skip: opool.mc_leg(spec, 3, bank, skip=skip)),
+               rtol=FP32_RTOL_THICK)
     s = g32["stats"]
     tot = s["w_absorbed"] + s["w_leaked"] + s["w_census"] + s["w_handoff"] + s["w_killed"]
     assert math.isclose(s["w_source"], tot, rel_tol=1e-5)
