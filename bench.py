@@ -431,11 +431,17 @@ def large_measure(steps: int = 2, n_hist: int = 100_000_000, sn_accel: int = 0) 
             "phase_ms": phase, "sn_iterations": it}
 
 
-def serving_measure(lam: float, duration: float, seed: int = 0, hist_cap: int | None = None) -> dict:
-    from paper_2511_16821_gb300.serve import Server
+def serving_measure(lam: float, duration: float, seed: int = 0, hist_cap: int | None = None,
+                    plain: bool = False, drain: float = 30.0) -> dict:
+    """Poisson arrivals of rate lam for `duration` seconds through the continuous-batching server
+    (120 GB admission budget), then at most `drain` seconds more; with plain=True also the plain
+    single-problem path on the same request stream."""
+    from paper_2511_16821_gb300.serve import Server, run_poisson_plain
     srv = Server(budget_bytes=120e9)
-    res = srv.run_poisson(lam, duration, seed=seed, hist_cap=hist_cap)
+    res = srv.run_poisson(lam, duration, seed=seed, hist_cap=hist_cap, drain=drain)
     srv.close()
+    if plain:
+        res["plain_single_problem"] = run_poisson_plain(lam, duration, seed=seed, hist_cap=hist_cap, drain=drain)
     return res
 
 
@@ -493,6 +499,9 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the large-mesh measurement")
     ap.add_argument("--serve-sweep", default="", help="comma-separated arrival rates: run only the serving sweep")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-drain", type=float, default=30.0, help="seconds served after the arrival window")
+    ap.add_argument("--serve-plain", action="store_true",
+                    help="also serve the same request stream through the plain single-problem path")
     ap.add_argument("--lean", action="store_true",
                     help="timed steps only (FP32, no profile/e2e/CPU legs): the case used for ncu captures")
     ap.add_argument("--sn-accel", type=int, default=0, help="Anderson depth of the collided solve (0: plain SI)")
@@ -521,7 +530,8 @@ def main():
     if args.serve_sweep:
         if rank == 0:
             for lam in [float(x) for x in args.serve_sweep.split(",")]:
-                print(json.dumps({"serving": serving_measure(lam, args.serve_seconds)}), flush=True)
+                print(json.dumps({"serving": serving_measure(lam, args.serve_seconds, plain=args.serve_plain,
+                                                             drain=args.serve_drain)}), flush=True)
         return
     if args.lean:
         args.fp32_only = args.no_cpu = args.no_e2e = args.no_batch = args.no_large = True
@@ -615,7 +625,7 @@ def main():
     if not args.no_batch:
         line["batched"] = batched_measure()
         line["batched_anderson"] = batched_measure(sn_accel=4, single=False)
-        line["serving"] = serving_measure(100.0, 3.0)
+        line["serving"] = serving_measure(100.0, 3.0, plain=True, drain=10.0)
     if not args.no_cpu:
         cb = cpu_baseline(n_hist=200_000, steps=2, leg=prof)
         line["fp32_tally_error"] = cb.pop("fp32_tally_error")

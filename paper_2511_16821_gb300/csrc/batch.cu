@@ -267,7 +267,6 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         probs.push_back(p);
     }
     if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");
-    const std::vector<hyb_problem*> before = b->probs;
     b->prec = prec;
     b->probs = probs;
     b->cur0.clear(); b->kmax.clear();
@@ -301,8 +300,8 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
     }
     // programmatic dependent launch is kept for problems stepped alone: in the batch's multi-stream
     // step graphs it measured slower (256 problems: 73 -> 101 ms per step). Members launch normally
-    // once the batch holds them; problems that left the set get it back.
-    for (hyb_problem* p : before) p->pdl = true;
+    // once the batch holds them (problems that left the set may already be destroyed: they get it
+    // back when they are next stepped alone)
     for (hyb_problem* p : probs) p->pdl = false;
     return HYB_OK;
 }
@@ -464,7 +463,6 @@ HYB_API hyb_status hyb_batch_step(hyb_batch* b, int32_t nsteps, hyb_leg_stats* p
 HYB_API hyb_status hyb_batch_destroy(hyb_batch* b) {
     if (!b) return HYB_OK;
     if (b->s0) cudaStreamSynchronize(b->s0); else cudaDeviceSynchronize();
-    for (hyb_problem* p : b->probs) p->pdl = true;    // stepped alone from now on
     drop_graphs(b);
     for (auto s : b->pool) cudaStreamDestroy(s);
     for (auto e : b->join_ev) cudaEventDestroy(e);

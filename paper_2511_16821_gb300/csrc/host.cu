@@ -939,6 +939,7 @@ static hyb_status sn_run(hyb_problem* p, int* iters, bool keep_status) {
 
 hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
     if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    p->pdl = true;   // stepped alone (a batch sets its members' launches itself)
     if (!p->leg_done) return fail(p, HYB_ESTATE, "collided solve needs an MC leg of this step");
     if (p->d.n_s == HYB_NS_INF) {   // nothing is handed off: the collided flux stays zero
         p->sn_done = true;
@@ -980,6 +981,7 @@ static hyb_status remap_launch(hyb_problem* p) {
 
 hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* out) {
     if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
+    p->pdl = true;
     if (!p->leg_done || (!p->sn_done && p->d.n_s != HYB_NS_INF))
         return fail(p, HYB_ESTATE, "remap needs an MC leg and a collided solve of this step");
     HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
@@ -1002,6 +1004,7 @@ hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* out) {
 // device state) are read together. The leg's status bits are checked with the remap's.
 hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
     if (!p || nsteps < 0) return fail(p, HYB_EINVAL, "bad arguments");
+    p->pdl = true;   // stepped alone (a batch sets its members' launches itself)
     for (int32_t i = 0; i < nsteps; ++i) {
         HYB_CU(p, cudaEventRecord(p->evs[0], p->stream));
         hyb_status s = leg_launch(p, nullptr);
