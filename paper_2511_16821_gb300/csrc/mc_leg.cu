@@ -180,7 +180,10 @@ __device__ __forceinline__ void load_sig(const double* sig, int k, double* sa, d
 // The histories of one problem that `src` hands out, tracked by the calling warp with lane refill:
 // a lane whose history ends takes the next index at once (ranks by ballot, deterministic order),
 // so the warp keeps its lanes on segments instead of waiting for its longest history.
-template <typename T, typename Src>
+// kStaged: the births were staged by the birth kernel (every leg but the ones that keep their
+// census as particles, N_s = infinity and steps 3'/4', whose staging buffer holds that census);
+// the kernel without the in-loop birth code keeps the loop body small
+template <typename T, bool kStaged, typename Src>
 __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const uint32_t* sV, const uint32_t* sShC,
                                const uint32_t* sShS, uint64_t key_c, uint64_t key_s, const LegScales& sc,
                                LegTally& t) {
@@ -213,6 +216,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
     pts.ntab = a.ntab;
     Hist<T> h;
     bool alive = false;
+    bool pending = false;   // scattered, waiting for its new direction and optical depth
     long long next = 0, last = 0;
     bool exhausted = false;
 
@@ -246,7 +250,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                 } else {
                     h.idx = (uint32_t)(j - nb);
                     h.census_stream = false;
-                    if (a.births.cell) {
+                    if constexpr (kStaged) {
                         const int k = a.births.cell[h.idx];
                         a.split(k, &h.ix, &h.iy);
                         h.fx = a.births.fx[h.idx]; h.fy = a.births.fy[h.idx];
@@ -278,9 +282,28 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             if (exhausted) break;
             continue;
         }
-        if (!alive) continue;
         pts.key = h.census_stream ? key_c : key_s;
         pts.shift = h.census_stream ? sShC : sShS;
+        // a scatter's new direction and optical depth (three point dimensions, the direction map
+        // and a logarithm) are drawn for the warp's scattered histories together, once 6 have
+        // collected or no other lane could run a segment, instead of for one or two lanes in every
+        // iteration (a scatter ends ~5 % of the segments on the benchmark)
+        {
+            const unsigned pend = __ballot_sync(0xffffffffu, pending);
+            if (pend) {
+                const unsigned runnable = __ballot_sync(0xffffffffu, alive && !pending);
+                if (__popc(pend) >= 6 || __popc(runnable) < 6) {
+                    if (pending) {
+                        const int base = 5 + 3 * (h.n - 1);
+                        iso_dir<T>(pts(h.idx, base + 1), pts(h.idx, base + 2), &h.ox, &h.oy);
+                        if constexpr (kF32) { h.rox = P::rcp(h.ox); h.roy = P::rcp(h.oy); }
+                        h.tau = h.n < Ns ? P::neglog(P::unit(pts(h.idx, 5 + 3 * h.n))) : T(0);
+                        pending = false;
+                    }
+                }
+            }
+        }
+        if (!alive || pending) continue;
 
         // ---- one segment ----------------------------------------------------------------------
         ++h.seg;
@@ -370,10 +393,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             h.fx = clamp_(h.fx, T(0), DX);
             h.fy = clamp_(h.fy, T(0), DY);
             ++h.n; ++t.c[2];
-            const int base = 5 + 3 * (h.n - 1);
-            iso_dir<T>(pts(h.idx, base + 1), pts(h.idx, base + 2), &h.ox, &h.oy);
-            if constexpr (kF32) { h.rox = P::rcp(h.ox); h.roy = P::rcp(h.oy); }
-            h.tau = h.n < Ns ? P::neglog(P::unit(pts(h.idx, 5 + 3 * h.n))) : T(0);
+            pending = true;
             if (h.n >= Nk) ++t.c[6];
         }
         if (fate < 0 && a.w_min > T(0) && h.w < a.w_min * h.w_start) fate = kFateKilled;
@@ -474,7 +494,7 @@ __device__ void leg_flush(DevState* st, LegTally& t, const LegScales& sc, bool w
 // (clamped to [0, bank + births)) from the problem's counter.
 // FP32: four CTAs of 256 threads per SM (64 registers; a few bytes spill outside the segment loop,
 // measured 5 % faster than three CTAs without spills); FP64: two
-template <typename T>
+template <typename T, bool kStaged>
 __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) mc_leg_kernel(LegArgs<T> a) {
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
@@ -497,7 +517,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) mc_leg_kernel(L
     const LegScales sc = s_sc;
     LegTally t;
     leg_tally_zero(t);
-    leg_warp_range<T>(a, CounterChunks{&a.st->leg_next, a.h0, h1}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+    leg_warp_range<T, kStaged>(a, CounterChunks{&a.st->leg_next, a.h0, h1}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
     leg_flush(a.st, t, sc, blockIdx.x == 0);
 }
 
@@ -546,7 +566,8 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
         const LegScales sc = s_sc;
         LegTally t;
         leg_tally_zero(t);
-        if (ch.j0 < e) leg_warp_range<T>(a, CounterChunks{&s_next, ch.j0, e}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+        if (ch.j0 < e)   // batches always stage their births (no N_s = infinity or steps 3'/4' in a batch)
+            leg_warp_range<T, true>(a, CounterChunks{&s_next, ch.j0, e}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
         leg_flush(a.st, t, sc, ch.j0 == 0);
     }
 }
@@ -819,9 +840,11 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist, long long h0, long lo
         const long long g = (a.n_src + kTile - 1) / kTile;
         mc_birth_kernel<T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kTile, 0, p->stream>>>(a);
     }
-    cudaError_t e = allow_smem(mc_leg_kernel<T>, smem);
+    const bool staged = a.births.cell != nullptr;
+    cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true>, smem) : allow_smem(mc_leg_kernel<T, false>, smem);
     if (e != cudaSuccess) return e;
-    mc_leg_kernel<T><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
+    if (staged) mc_leg_kernel<T, true><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
+    else mc_leg_kernel<T, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
     return cudaGetLastError();
 }
 
