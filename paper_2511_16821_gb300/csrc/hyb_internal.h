@@ -25,6 +25,15 @@ constexpr int kStBounds = 1, kStSegments = 2, kStCapacity = 4;
 struct Acc128 { unsigned long long lo, hi; };
 
 // Device-resident per-leg counters and scalars (one block of memory per problem).
+// Per-step scalars of the remap passes, formed once per remap by one thread (FP64 work that
+// every block repeating it would put on the critical path of its slots)
+struct RemapScal {
+    long long N;               // slots: bank + births
+    double wbar, w_ref;        // birth weight, comb quantisation base
+    float qsc, sca;            // FP32 comb scale 2^(32 - log2 w_ref), FP32 |w|-sum scale 2^kfa
+    int krw, kw, kfa, kf;      // 128-bit scales of sum |w| and of the statistics; FP32 per-thread ones
+};
+
 struct DevState {
     // counters of the last MC leg
     unsigned long long histories, segments, collisions, leaked, census, killed, reached, errors;
@@ -62,6 +71,7 @@ struct DevState {
     int sn_warm;               // solves finished with warm starts enabled (counted up to 2)
     unsigned int sn_blocks_done;   // source-iteration reduction: blocks finished (last one resets it)
     unsigned int bank_bad;     // particles of a native-layout bank upload outside the problem's domain
+    RemapScal rs;              // scalars of the current remap (remap_prep_kernel)
 };
 
 template <typename T>

@@ -268,16 +268,6 @@ __host__ __device__ inline double pow2_ceil(double w) {
 // comb base w_ref and birth weight; runs after the CDF build. lead: the leg-census slots ahead of
 // the births (steps 3'/4'), whose weights are bounded by the step-start bank's and by the leg's
 // birth weight w_lead
-__global__ void remap_prep_kernel(DevState* st, long long n_hist, long long lead, double w_lead) {
-    pdl_wait();
-    pdl_trigger();
-    const double W = st->remap_W;
-    const double wbar = W > 0 ? W / (double)n_hist : 0.0;
-    st->r_lead = lead;
-    double wmax = fmax(fmax(st->bank_wmax, w_lead), wbar * st->remap_rmax);
-    st->w_ref = wmax > 0 ? pow2_ceil(wmax) : 1.0;
-}
-
 // ---------------------------------------------------------------------------------------------
 // remap streaming
 // ---------------------------------------------------------------------------------------------
@@ -462,15 +452,7 @@ __device__ __forceinline__ long long quant(T w, double w_ref, float qsc) {
     return quant_w(w, w_ref, qsc);
 }
 
-// Per-step scalars of the remap kernels, formed once per block by one thread (FP64 work that
-// every thread repeating it would cost more than its slots' arithmetic on this GPU).
-struct RemapScal {
-    long long N;               // slots: bank + births
-    double wbar, w_ref;        // birth weight, comb quantisation base
-    float qsc, sca;            // FP32 comb scale 2^(32 - log2 w_ref), FP32 |w|-sum scale 2^kfa
-    int krw, kw, kfa, kf;      // 128-bit scales of sum |w| and of the statistics; FP32 per-thread ones
-};
-
+// The per-step scalars of the remap passes (RemapScal), formed once by remap_prep_kernel.
 __device__ __forceinline__ RemapScal remap_scalars(const DevState* st, long long n_hist) {
     RemapScal r;
     const long long nb = st->n_bank + st->r_lead;
@@ -487,6 +469,18 @@ __device__ __forceinline__ RemapScal remap_scalars(const DevState* st, long long
     return r;
 }
 
+// one thread: the comb's quantisation base and the remap passes' scalars of this step
+__global__ void remap_prep_kernel(DevState* st, long long n_hist, long long lead, double w_lead) {
+    pdl_wait();
+    pdl_trigger();
+    const double W = st->remap_W;
+    const double wbar = W > 0 ? W / (double)n_hist : 0.0;
+    st->r_lead = lead;
+    double wmax = fmax(fmax(st->bank_wmax, w_lead), wbar * st->remap_rmax);
+    st->w_ref = wmax > 0 ? pow2_ceil(wmax) : 1.0;
+    st->rs = remap_scalars(st, n_hist);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     pdl_wait();
@@ -498,7 +492,7 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     build_point_tables(a.V, a.ntab, sV, a.sampler);
     for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
     __shared__ RemapScal s_rs;
-    if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
+    if (threadIdx.x == 0) s_rs = a.st->rs;
     __syncthreads();
     Points pts{sV, sSh, key, a.sampler, a.ntab};
     const long long nb = a.st->n_bank + a.st->r_lead;   // slots ahead of the births
@@ -621,7 +615,7 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_partials_kernel(RemapArgs<T> a) {
     __shared__ RemapScal s_rs;
-    if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
+    if (threadIdx.x == 0) s_rs = a.st->rs;
     __syncthreads();
     const long long N = s_rs.N;
     const double w_ref = s_rs.w_ref;
@@ -853,13 +847,52 @@ __device__ __forceinline__ long long first_tooth(long long S, long long M, long 
     return ceil_div(hi, nlo, (unsigned long long)T);
 }
 
+// block exclusive scan of a (count, sum) pair per thread; totals in *tc, *tq
+__device__ __forceinline__ void block_exclusive_scan2(long long c, long long q, long long* ec, long long* eq,
+                                                      long long* tc, long long* tq) {
+    __shared__ long long s2c[kTile / 32], s2q[kTile / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long ic = c, iq = q;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long vc = __shfl_up_sync(0xffffffffu, ic, off), vq = __shfl_up_sync(0xffffffffu, iq, off);
+        if (lane >= off) { ic += vc; iq += vq; }
+    }
+    if (lane == 31) { s2c[wid] = ic; s2q[wid] = iq; }
+    __syncthreads();
+    long long wc = 0, wq = 0, ac = 0, aq = 0;
+#pragma unroll
+    for (int ww = 0; ww < kTile / 32; ++ww) {
+        if (ww < wid) { wc += s2c[ww]; wq += s2q[ww]; }
+        ac += s2c[ww]; aq += s2q[ww];
+    }
+    *ec = wc + ic - c; *eq = wq + iq - q;
+    *tc = ac; *tq = aq;
+}
+
+// teeth of a position whose q M - ph exceeds T or 64 bits (a weight far above the mean tooth
+// spacing): the exact 128-bit form, kept out of line
+__device__ __noinline__ long long comb_teeth_wide(long long S, long long q, long long M, long long o, long long T,
+                                                 long long t, unsigned long long ph) {
+    const unsigned long long uq = (unsigned long long)q, uM = (unsigned long long)M;
+    if (__umul64hi(uq, uM) != 0ull) return first_tooth(S + q, M, o, T) - t;
+    return ceil_div(0ull, uq * uM - ph, (unsigned long long)T);
+}
+
+// Pass B. Thread i of block b takes the kRounds consecutive census positions starting at
+// b kSlotsPerBlock + i kRounds (census order: slot order, or the sorted order of perm).
+// Comb: position j with cumulative quantised weight S_j before it and q_j of its own takes the
+// teeth t in [first_tooth(S_j), first_tooth(S_j + q_j)), tooth t standing at t T + o on the axis
+// S M. With the phase ph = t T + o - S M of the next tooth t (in [0, T)), position j takes
+// n = ceil((q_j M - ph) / T) teeth when q_j M > ph and none otherwise, so a thread divides 128-bit
+// numbers once (its first tooth) and advances t by 64-bit comparisons: the same teeth as a
+// first_tooth per position.
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
     pdl_wait();
     pdl_trigger();
-    __shared__ long long s_c[kTile / 32], s_q[kTile / 32];
     __shared__ RemapScal s_rs;
-    if (threadIdx.x == 0) s_rs = remap_scalars(a.st, a.n_hist);
+    if (threadIdx.x == 0) s_rs = a.st->rs;
     __syncthreads();
     const long long N = s_rs.N;
     const double w_ref = s_rs.w_ref;
@@ -867,71 +900,102 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
     const int comb = a.st->comb_on;
     const long long M = a.cap, o = a.st->comb_o, Ttot = a.st->comb_T;
     const T wcopy = (T)a.st->wcopy;
-    long long run_c = a.blk[4 * (size_t)blockIdx.x], run_q = a.blk[4 * (size_t)blockIdx.x + 1];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // Comb teeth: slot j takes teeth [first_tooth(S_j), first_tooth(S_j + q_j)) and S_j + q_j is
-    // the next slot's S, so each thread divides once (its end tooth) and takes its start from the
-    // slot before: the lane below, the last lane of the warp below, or the previous round's last
-    // slot (the block's first start is divided once by thread 0)
     const bool combing = comb && Ttot > 0;
-    __shared__ long long s_t1[kTile / 32];
-    __shared__ long long s_carry;
-    if (combing && threadIdx.x == 0) s_carry = first_tooth(run_q, M, o, Ttot);
-    T wmax = 0;
-    const long long base = (long long)blockIdx.x * kSlotsPerBlock;
-    for (int r = 0; r < kRounds; ++r) {
-        const long long j = base + r * kTile + threadIdx.x;
-        Particle<T> pr;
-        pr.alive = false;
-        if (j < N) {
-            const long long js = a.perm ? (long long)(uint32_t)a.perm[j] : j;
-            pr.cell = a.stg.cell[js];
-            pr.alive = pr.cell >= 0;
-            pr.fx = a.stg.fx[js]; pr.fy = a.stg.fy[js]; pr.ox = a.stg.ox[js]; pr.oy = a.stg.oy[js]; pr.w = a.stg.w[js];
+    const long long j0 = (long long)blockIdx.x * kSlotsPerBlock + (long long)threadIdx.x * kRounds;
+    int cell[kRounds];
+    T w[kRounds];
+    if (!a.perm && j0 + kRounds <= N) {
+        // slot order, all kRounds positions in range: 16-byte loads (the stage arrays start on
+        // 16-byte boundaries and j0 is a multiple of kRounds)
+        const int4* pc = reinterpret_cast<const int4*>(a.stg.cell + j0);
+#pragma unroll
+        for (int v = 0; v < kRounds / 4; ++v) {
+            const int4 c4 = pc[v];
+            cell[4 * v] = c4.x; cell[4 * v + 1] = c4.y; cell[4 * v + 2] = c4.z; cell[4 * v + 3] = c4.w;
         }
-        long long c = pr.alive ? 1 : 0;
-        long long q = pr.alive ? quant<T>(pr.w, w_ref, qsc) : 0;
-        // block exclusive scan of (c, q) in census order
-        long long ic = c, iq = q;
-        for (int off = 1; off < 32; off <<= 1) {
-            const long long vc = __shfl_up_sync(0xffffffffu, ic, off), vq = __shfl_up_sync(0xffffffffu, iq, off);
-            if (lane >= off) { ic += vc; iq += vq; }
-        }
-        if (lane == 31) { s_c[wid] = ic; s_q[wid] = iq; }
-        __syncthreads();
-        long long wc = 0, wq = 0, tc = 0, tq = 0;
-        for (int ww = 0; ww < kTile / 32; ++ww) {
-            if (ww < wid) { wc += s_c[ww]; wq += s_q[ww]; }
-            tc += s_c[ww]; tq += s_q[ww];
-        }
-        const long long pos_c = run_c + wc + ic - c;
-        const long long S = run_q + wq + iq - q;
-        long long t0 = 0, t1 = 0;
-        if (combing) {
-            t1 = first_tooth(S + q, M, o, Ttot);
-            const long long below = __shfl_up_sync(0xffffffffu, t1, 1);
-            if (lane == 31) s_t1[wid] = t1;
-            __syncthreads();
-            t0 = lane > 0 ? below : (wid > 0 ? s_t1[wid - 1] : s_carry);
-        }
-        if (pr.alive) {
-            if (combing) {
-                const T wc_ = pr.w < T(0) ? -wcopy : wcopy;
-                for (long long t = t0; t < t1 && t < M; ++t) {
-                    a.out.cell[t] = pr.cell; a.out.fx[t] = pr.fx; a.out.fy[t] = pr.fy;
-                    a.out.ox[t] = pr.ox; a.out.oy[t] = pr.oy; a.out.w[t] = wc_;
-                }
-            } else if (pos_c < M) {
-                a.out.cell[pos_c] = pr.cell; a.out.fx[pos_c] = pr.fx; a.out.fy[pos_c] = pr.fy;
-                a.out.ox[pos_c] = pr.ox; a.out.oy[pos_c] = pr.oy; a.out.w[pos_c] = pr.w;
-                wmax = fmax(wmax, fabs(pr.w));
+        if constexpr (sizeof(T) == 4) {
+            const float4* pw = reinterpret_cast<const float4*>(a.stg.w + j0);
+#pragma unroll
+            for (int v = 0; v < kRounds / 4; ++v) {
+                const float4 w4 = pw[v];
+                w[4 * v] = w4.x; w[4 * v + 1] = w4.y; w[4 * v + 2] = w4.z; w[4 * v + 3] = w4.w;
+            }
+        } else {
+            const double2* pw = reinterpret_cast<const double2*>(a.stg.w + j0);
+#pragma unroll
+            for (int v = 0; v < kRounds / 2; ++v) {
+                const double2 w2 = pw[v];
+                w[2 * v] = w2.x; w[2 * v + 1] = w2.y;
             }
         }
-        run_c += tc;
-        run_q += tq;
-        __syncthreads();
-        if (combing && threadIdx.x == kTile - 1) s_carry = t1;   // read after the next round's barrier
+    } else {
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            const long long j = j0 + r;
+            cell[r] = -1;
+            w[r] = T(0);
+            if (j < N) {
+                const long long js = a.perm ? (long long)(uint32_t)a.perm[j] : j;
+                cell[r] = a.stg.cell[js];
+                w[r] = a.stg.w[js];
+            }
+        }
     }
+    long long q[kRounds];
+    long long c = 0, qt = 0;
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const bool alive = cell[r] >= 0;
+        q[r] = alive ? quant<T>(w[r], w_ref, qsc) : 0;
+        c += alive ? 1 : 0;
+        qt += q[r];
+    }
+    long long ec, eq, tc, tq;
+    block_exclusive_scan2(c, qt, &ec, &eq, &tc, &tq);
+    long long pos = a.blk[4 * (size_t)blockIdx.x] + ec;
+    long long S = a.blk[4 * (size_t)blockIdx.x + 1] + eq;
+    T wmax = 0;
+    if (combing) {
+        const unsigned long long uT = (unsigned long long)Ttot, uM = (unsigned long long)M, uo = (unsigned long long)o;
+        long long t = first_tooth(S, M, o, Ttot);
+        // phase of tooth t, exact modulo 2^64 (its value lies in [0, T))
+        unsigned long long ph = (unsigned long long)t * uT + uo - (unsigned long long)S * uM;
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            if (q[r] <= 0) continue;
+            const unsigned long long uq = (unsigned long long)q[r], qm = uq * uM;
+            long long n;
+            if (__umul64hi(uq, uM) == 0ull && qm <= ph) n = 0;
+            else if (__umul64hi(uq, uM) == 0ull && qm - ph <= uT) n = 1;
+            else n = comb_teeth_wide(S, q[r], M, o, Ttot, t, ph);
+            S += q[r];
+            if (n > 0) {
+                const long long js = a.perm ? (long long)(uint32_t)a.perm[j0 + r] : j0 + r;
+                const T fx = a.stg.fx[js], fy = a.stg.fy[js], ox = a.stg.ox[js], oy = a.stg.oy[js];
+                const T wc_ = w[r] < T(0) ? -wcopy : wcopy;
+                const long long te = t + n < M ? t + n : M;
+                for (long long u = t; u < te; ++u) {
+                    a.out.cell[u] = cell[r]; a.out.fx[u] = fx; a.out.fy[u] = fy;
+                    a.out.ox[u] = ox; a.out.oy[u] = oy; a.out.w[u] = wc_;
+                }
+                t += n;
+            }
+            ph = (unsigned long long)t * uT + uo - (unsigned long long)S * uM;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < kRounds; ++r) {
+            if (cell[r] < 0) continue;
+            if (pos < M) {
+                const long long js = a.perm ? (long long)(uint32_t)a.perm[j0 + r] : j0 + r;
+                a.out.cell[pos] = cell[r]; a.out.fx[pos] = a.stg.fx[js]; a.out.fy[pos] = a.stg.fy[js];
+                a.out.ox[pos] = a.stg.ox[js]; a.out.oy[pos] = a.stg.oy[js]; a.out.w[pos] = w[r];
+                wmax = fmax(wmax, fabs(w[r]));
+            }
+            ++pos;
+        }
+    }
+    const int lane = threadIdx.x & 31;
     for (int off = 16; off > 0; off >>= 1) wmax = fmax(wmax, __shfl_down_sync(0xffffffffu, wmax, off));
     if (lane == 0 && wmax > T(0))
         atomicMax((unsigned long long*)&a.st->bank_wmax, (unsigned long long)__double_as_longlong((double)wmax));
@@ -1023,6 +1087,7 @@ __global__ void census_prep_kernel(DevState* st, double w_src, long long n_hist)
     st->r_lead = 0;
     const double wmax = fmax(st->bank_wmax, w_src > 0 ? w_src / (double)n_hist : 0.0);
     st->w_ref = wmax > 0 ? pow2_ceil(wmax) : 1.0;
+    st->rs = remap_scalars(st, n_hist);
 }
 
 // staging slots past the leg's histories hold nothing: mark them dead (they sort last)
