@@ -228,6 +228,16 @@ HYB_API hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* stats);
  * EBOUNDS. */
 HYB_API hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step);
 
+/* Statistics of the last remap (of hyb_step or hyb_remap): histories (slots streamed: bank +
+ * births), segments, leaked, killed, errors, census (particles written), w_source / w_absorbed /
+ * w_leaked / w_killed (weight of the slots' start states, removed by sigma_t attenuation, leaving
+ * the domain, below the weight cut-off), w_census (sum |w| of the survivors before the comb),
+ * combed, bank_size. Synchronises the problem's stream. Inside hyb_step, an Eq. (R) remap's bank
+ * slots are re-streamed on an internal stream beside the collided solve; their weight sums are
+ * formed at the bank's own fixed-point scale and added here (equal to the single-pass sums up to
+ * the rounding of that scale). */
+HYB_API hyb_status hyb_remap_stats(hyb_problem* p, hyb_leg_stats* stats);
+
 /* Copy a tally (see HYB_TALLY_*) into dst (host if dst_on_device == 0, else device), n values.
  * Synchronises the stream. EINVAL if n is not the tally's size. */
 HYB_API hyb_status hyb_get_tally(hyb_problem* p, int32_t which, double* dst, size_t n, int32_t dst_on_device);

@@ -302,7 +302,12 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
     // step graphs it measured slower (256 problems: 73 -> 101 ms per step). Members launch normally
     // once the batch holds them (problems that left the set may already be destroyed: they get it
     // back when they are next stepped alone)
-    for (hyb_problem* p : probs) p->pdl = false;
+    for (hyb_problem* p : probs) {
+        p->pdl = false;
+        // a bank pre-pass left pending by a failed single-problem step is ordered and forgotten:
+        // the batch re-streams every slot itself
+        if (hyb::drop_bank_prepass(p) != cudaSuccess) return bfail(b, HYB_ECUDA, "bank pre-pass");
+    }
     return HYB_OK;
 }
 

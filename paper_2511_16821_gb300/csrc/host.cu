@@ -535,8 +535,11 @@ void fill_remap_stats(const hyb_problem* p, hyb_leg_stats* s) {
     std::memset(s, 0, sizeof(*s));
     s->histories = (int64_t)h.r_histories; s->segments = (int64_t)h.r_segments; s->leaked = (int64_t)h.r_leaked;
     s->killed = (int64_t)h.r_killed; s->errors = (int64_t)h.r_errors; s->census = h.out_count;
-    s->w_source = stat_w(h.r_w_source, h.k_rw); s->w_absorbed = stat_w(h.r_w_absorbed, h.k_rw);
-    s->w_leaked = stat_w(h.r_w_leaked, h.k_rw); s->w_killed = stat_w(h.r_w_killed, h.k_rw);
+    // a bank pre-pass (if any) summed its slots at its own scale: zero accumulators otherwise
+    s->w_source = stat_w(h.r_w_source, h.k_rw) + stat_w(h.r_wb[0], h.k_rwb);
+    s->w_absorbed = stat_w(h.r_w_absorbed, h.k_rw) + stat_w(h.r_wb[1], h.k_rwb);
+    s->w_leaked = stat_w(h.r_w_leaked, h.k_rw) + stat_w(h.r_wb[2], h.k_rwb);
+    s->w_killed = stat_w(h.r_w_killed, h.k_rw) + stat_w(h.r_wb[3], h.k_rwb);
     s->w_census = h.bank_wsum;
     s->combed = h.comb_on;
     s->bank_size = h.n_bank;
@@ -731,6 +734,10 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
         return bail(fail(p, HYB_ECUDA, "event create"));
     for (auto& e : p->evs)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(p, HYB_ECUDA, "event create"));
+    if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(p, HYB_ECUDA, "side stream create"));
     const size_t nc = (size_t)p->ncells;
     p->sig_s_max = 0;
     for (size_t k = 0; k < nc; ++k) p->sig_s_max = std::max(p->sig_s_max, d->sigma_s[k]);
@@ -819,6 +826,9 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
 hyb_status hyb_destroy_problem(hyb_problem* p) {
     if (!p) return HYB_OK;
     if (p->stream) cudaStreamSynchronize(p->stream); else cudaDeviceSynchronize();
+    if (p->side) { cudaStreamSynchronize(p->side); cudaStreamDestroy(p->side); }
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     if (p->owns_ws && p->ws) cudaFree(p->ws);
     if (p->st_host) cudaFreeHost(p->st_host);
     if (p->ev0) cudaEventDestroy(p->ev0);
@@ -836,6 +846,7 @@ static hyb_status leg_launch(hyb_problem* p, int32_t* hist, long long h0 = 0, lo
     const size_t nc = (size_t)p->ncells;
     const size_t acc = p->prec == HYB_FP64 ? 16 : 8;
     const size_t ncp = (size_t)p->tally_copies;
+    HYB_CU(p, drop_bank_prepass(p));   // the leg's births reuse the staging buffer
     HYB_CU(p, cudaMemsetAsync(p->acc_pre, 0, ncp * nc * acc, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->acc_post, 0, ncp * nc * acc, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, ncp * 4 * nc * acc, p->stream));
@@ -1012,6 +1023,9 @@ hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
         HYB_CU(p, cudaEventRecord(p->evs[1], p->stream));
         int it = 0;
         if (p->d.n_s != HYB_NS_INF) {
+            // Eq. (R): the step-start bank's re-stream needs neither the collided flux nor the remap
+            // density, so it runs on the side stream beside the solve
+            if (p->d.remap_variant == 0) HYB_CU(p, launch_remap_bank_prepass(p));
             s = sn_run(p, &it, true);
             if (s != HYB_OK) return s;
         } else {
@@ -1041,6 +1055,13 @@ hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
     }
     if (!per_step) return pull_state(p);
     return HYB_OK;
+}
+
+hyb_status hyb_remap_stats(hyb_problem* p, hyb_leg_stats* out) {
+    if (!p || !out) return fail(p, HYB_EINVAL, "null argument");
+    hyb_status s = pull_state(p);
+    fill_remap_stats(p, out);
+    return s;
 }
 
 hyb_status hyb_get_tally(hyb_problem* p, int32_t which, double* dst, size_t n, int32_t on_dev) {
@@ -1084,6 +1105,7 @@ hyb_status hyb_set_bank(hyb_problem* p, const int32_t* cell, const double* fx, c
                         const double* oy, const double* w, int64_t n) {
     if (!p || n < 0 || (n > 0 && (!cell || !fx || !fy || !ox || !oy || !w))) return fail(p, HYB_EINVAL, "bad arguments");
     if (n > p->bank_cap) return fail(p, HYB_ECAPACITY, "bank larger than its capacity");
+    HYB_CU(p, drop_bank_prepass(p));
     for (int64_t i = 0; i < n; ++i) {
         if (cell[i] < 0 || cell[i] >= p->ncells) return fail(p, HYB_EINVAL, "bank cell index out of range");
         // FP32 banks read back in FP64 carry float rounding: allow a few float ulps
@@ -1101,6 +1123,7 @@ hyb_status hyb_set_bank_native(hyb_problem* p, const int32_t* cell, const void* 
                                const void* oy, const void* w, int64_t n) {
     if (!p || n < 0 || (n > 0 && (!cell || !fx || !fy || !ox || !oy || !w))) return fail(p, HYB_EINVAL, "bad arguments");
     if (n > p->bank_cap) return fail(p, HYB_ECAPACITY, "bank larger than its capacity");
+    HYB_CU(p, drop_bank_prepass(p));
     const void* f[5] = {fx, fy, ox, oy, w};
     return p->prec == HYB_FP64 ? set_bank_native_t<double>(p, cell, f, n) : set_bank_native_t<float>(p, cell, f, n);
 }
@@ -1113,6 +1136,7 @@ hyb_status hyb_bank_capacity(const hyb_problem* p, int64_t* cap) {
 
 hyb_status hyb_set_step(hyb_problem* p, int64_t step) {
     if (!p || step < 0) return fail(p, HYB_EINVAL, "bad arguments");
+    HYB_CU(p, drop_bank_prepass(p));
     p->step = step;
     p->st_host->step = step;
     HYB_CU(p, cudaMemcpyAsync(&p->st->step, &p->st_host->step, sizeof(long long), cudaMemcpyHostToDevice, p->stream));

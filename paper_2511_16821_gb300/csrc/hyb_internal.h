@@ -43,6 +43,8 @@ struct DevState {
     // counters of the last remap
     unsigned long long r_histories, r_segments, r_leaked, r_killed, r_errors, r_alive;
     Acc128 r_w_source, r_w_absorbed, r_w_leaked, r_w_killed, r_w_census;
+    Acc128 r_wb[4];            // the bank pre-pass's source, absorbed, leaked, killed weights (scale k_rwb)
+    int k_rwb, pad_rwb;
     // bank descriptors
     long long n_bank;          // particles in the current bank
     double bank_wmax;          // max |w| of the current bank
@@ -72,6 +74,7 @@ struct DevState {
     unsigned int sn_blocks_done;   // source-iteration reduction: blocks finished (last one resets it)
     unsigned int bank_bad;     // particles of a native-layout bank upload outside the problem's domain
     RemapScal rs;              // scalars of the current remap (remap_prep_kernel)
+    RemapScal rsb;             // scalars of the bank pre-pass (remap_bank_prep_kernel)
 };
 
 template <typename T>
@@ -169,6 +172,12 @@ struct hyb_problem {
     hyb::DevState* st_host;   // pinned host mirror
     cudaEvent_t ev0, ev1;
     cudaEvent_t evs[4];       // hyb_step phase boundaries: leg start, solve start, remap start, end
+    // bank pre-pass of the remap (Eq. (R) remaps stepped by hyb_step): the step-start bank slots are
+    // re-streamed on `side` while the collided solve runs on `stream` (its sweeps leave most SMs
+    // idle); ev_fork orders it after the leg, ev_join orders the remap's pass A after it
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
+    bool bank_prepass;        // a pre-pass of this step's bank is in flight or done (not yet consumed)
 };
 
 namespace hyb {
@@ -183,6 +192,12 @@ size_t leg_exchange_words(const hyb_problem* p);
 cudaError_t launch_leg_pack(hyb_problem* p, long long* x);
 cudaError_t launch_leg_unpack(hyb_problem* p, const long long* x);
 cudaError_t launch_remap(hyb_problem* p);
+// Eq. (R) remap: re-stream the step-start bank's slots on p->side (after the work queued on
+// p->stream so far) and mark the pre-pass pending; launch_remap consumes it. No-op for an empty bank.
+cudaError_t launch_remap_bank_prepass(hyb_problem* p);
+// order p->stream after a pending bank pre-pass and forget it (the bank, the step or the staging
+// buffer is about to change)
+cudaError_t drop_bank_prepass(hyb_problem* p);
 cudaError_t launch_census(hyb_problem* p);   // N_s = infinity: MC-leg census -> new bank
 size_t sn_accel_state_bytes();                // device bytes of the Anderson state
 size_t sn_norm_bytes(int ncells);            // reduction scratch of the source iteration

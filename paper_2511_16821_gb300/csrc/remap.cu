@@ -19,6 +19,7 @@
 // the point draws, sincos) and its stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "hyb_device.cuh"
@@ -291,6 +292,8 @@ struct RemapArgs {
     long long nslots;          // staging slots (bank capacity + n_hist); the sort covers all of them
     int perm_slots;            // 1: the census is sorted by cell after the count pass
     int lead_staged;           // 1 (steps 3'/4'): slots ahead of the births hold the MC leg's staged census
+    int mode;                  // pass A: 0 every slot; 1 bank pre-pass (bank slots only, statistics at the
+                               // bank's scale, no census partials); 2 after a bank pre-pass (bank slots staged)
     CellSplit split;           // cell index -> (ix, iy)
 };
 
@@ -481,6 +484,23 @@ __global__ void remap_prep_kernel(DevState* st, long long n_hist, long long lead
     st->rs = remap_scalars(st, n_hist);
 }
 
+// one thread: the scalars of the bank pre-pass, from the step-start bank alone (n_bank slots, the
+// power of two at or above its max |w| as the statistics' base)
+__global__ void remap_bank_prep_kernel(DevState* st) {
+    RemapScal r;
+    const long long nb = st->n_bank;
+    r.N = nb;
+    r.wbar = 0.0;
+    r.w_ref = st->bank_wmax > 0 ? pow2_ceil(st->bank_wmax) : 1.0;
+    r.qsc = quant_scale(r.w_ref);
+    r.krw = scale_exponent((double)(nb > 0 ? nb : 1) * r.w_ref, 125);
+    r.kw = scale_exponent((double)(nb > 0 ? nb : 1) * r.w_ref * 4.0, 125);
+    r.kfa = min(r.krw - 64, 126);
+    r.kf = min(r.kw - 64, 126);
+    r.sca = pow2f(r.kfa);
+    st->rsb = r;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     pdl_wait();
@@ -488,16 +508,24 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
     uint32_t* sSh = sm + a.ntab * kNibbleWords;
+    const bool prepass = a.mode == 1;
+    // the bank pre-pass runs before the remap density exists: bank slots only (no step-start
+    // r_lead slots there), scales from the bank alone; its blocks loop over the slot blocks (a
+    // grid of fewer blocks than SMs leaves room for the collided solve's kernels beside it)
+    const long long nb = prepass ? a.st->n_bank : a.st->n_bank + a.st->r_lead;   // slots ahead of the births
+    if (prepass && (long long)blockIdx.x * kSlotsPerBlock >= nb) return;
     const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_REMAP_SOURCE);
-    build_point_tables(a.V, a.ntab, sV, a.sampler);
-    for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
+    // point tables only where the block holds births
+    if (!prepass && (long long)(blockIdx.x + 1) * kSlotsPerBlock > nb) {
+        build_point_tables(a.V, a.ntab, sV, a.sampler);
+        for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
+    }
     __shared__ RemapScal s_rs;
-    if (threadIdx.x == 0) s_rs = a.st->rs;
+    if (threadIdx.x == 0) s_rs = prepass ? a.st->rsb : a.st->rs;
     __syncthreads();
     Points pts{sV, sSh, key, a.sampler, a.ntab};
-    const long long nb = a.st->n_bank + a.st->r_lead;   // slots ahead of the births
-    const bool lead_staged = a.lead_staged != 0;
-    const long long N = s_rs.N;
+    const bool staged = a.lead_staged != 0 || a.mode == 2;   // slots below nb hold end states already
+    const long long N = prepass ? nb : s_rs.N;
     const T wbar_t = (T)s_rs.wbar;
     const double w_ref = s_rs.w_ref;
     const float qsc = s_rs.qsc;
@@ -511,16 +539,18 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     long long cnt = 0, qs = 0, wsf = 0;
     double ws = 0;
     int leaked = 0, killed = 0, segs = 0, err = 0;
-    const long long base = (long long)blockIdx.x * kSlotsPerBlock;
+    const long long nbb = prepass ? (nb + kSlotsPerBlock - 1) / kSlotsPerBlock : (long long)blockIdx.x + 1;
+    for (long long bb = blockIdx.x; bb < nbb; bb += prepass ? gridDim.x : 1)
     for (int r = 0; r < kRounds; ++r) {
-        const long long j = base + r * kTile + threadIdx.x;
+        const long long j = bb * kSlotsPerBlock + r * kTile + threadIdx.x;
         if (j >= N) {
-            if (a.perm_slots && j < a.nslots) a.stg.cell[j] = -1;   // unused slots sort last, as dead
+            if (!prepass && a.perm_slots && j < a.nslots) a.stg.cell[j] = -1;   // unused slots sort last, as dead
             continue;
         }
         Particle<T> pr;
-        if (lead_staged && j < nb) {
-            // steps 3'/4': the MC leg staged its census here; it enters the census as it is
+        if (staged && j < nb) {
+            // steps 3'/4': the MC leg staged its census here; it enters the census as it is. After a
+            // bank pre-pass: the bank particle's end state, staged (and counted) by the pre-pass
             pr.cell = a.stg.cell[j];
             pr.alive = pr.cell >= 0;
             pr.w = pr.alive ? a.stg.w[j] : T(0);
@@ -579,17 +609,20 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
             for (int t = 0; t < 4; ++t) iv[t] += s_i[ww][t];
         }
         unsigned long long lo, hi;
-        long long* b = a.blk + 4 * (size_t)blockIdx.x;
-        if constexpr (kF32) {
-            // af 2^-kfa = af 2^(krw - kfa) 2^-krw: the 128-bit value is af shifted left by krw - kfa >= 64
-            const int sh = krw - kfa - 64;
-            lo = 0ull;
-            hi = sh < 63 ? (unsigned long long)af << sh : 0ull;
-        } else {
-            to_i128(d[0] * ldexp(1.0, krw), &lo, &hi);
+        if (!prepass) {
+            long long* b = a.blk + 4 * (size_t)blockIdx.x;
+            if constexpr (kF32) {
+                // af 2^-kfa = af 2^(krw - kfa) 2^-krw: the 128-bit value is af shifted left by krw - kfa >= 64
+                const int sh = krw - kfa - 64;
+                lo = 0ull;
+                hi = sh < 63 ? (unsigned long long)af << sh : 0ull;
+            } else {
+                to_i128(d[0] * ldexp(1.0, krw), &lo, &hi);
+            }
+            b[0] = c; b[1] = q; b[2] = (long long)lo; b[3] = (long long)hi;
         }
-        b[0] = c; b[1] = q; b[2] = (long long)lo; b[3] = (long long)hi;
         Acc128* wd[4] = {&a.st->r_w_source, &a.st->r_w_absorbed, &a.st->r_w_leaked, &a.st->r_w_killed};
+        if (prepass) { wd[0] = &a.st->r_wb[0]; wd[1] = &a.st->r_wb[1]; wd[2] = &a.st->r_wb[2]; wd[3] = &a.st->r_wb[3]; }
         for (int t = 0; t < 4; ++t) {
             if constexpr (kF32) {
                 const int sh = kw - kf - 64;
@@ -604,7 +637,12 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
         if (iv[1]) atomicAdd(&a.st->r_killed, (unsigned long long)iv[1]);
         if (iv[2]) atomicAdd(&a.st->r_segments, (unsigned long long)iv[2]);
         if (iv[3]) { atomicAdd(&a.st->r_errors, (unsigned long long)iv[3]); atomicOr(&a.st->status, kStSegments); }
-        if (blockIdx.x == 0) { a.st->k_rw = kw; a.st->r_histories = (unsigned long long)(N - a.st->r_lead); }
+        if (blockIdx.x == 0) {
+            if (prepass) a.st->k_rwb = kw;
+            else { a.st->k_rw = kw; a.st->r_histories = (unsigned long long)(N - a.st->r_lead); }
+            // a pre-pass error flag may have been cleared with the status word since
+            if (a.mode == 2 && a.st->r_errors) atomicOr(&a.st->status, kStSegments);
+        }
     }
 }
 
@@ -1008,28 +1046,9 @@ __global__ void remap_finish_kernel(DevState* st) {
     st->step += 1;              // census of t_{n+1}: the next leg belongs to step n + 1
 }
 
+// the arguments of the remap passes (census in slot order, every slot streamed)
 template <typename T>
-static cudaError_t remap_t(hyb_problem* p) {
-    cudaStream_t s = p->stream;
-    // remap density and its CDF
-    const int g = (p->ncells + 255) / 256;
-    cudaError_t e = cudaMemsetAsync(&p->st->remap_rmax, 0, sizeof(double), s);
-    if (e != cudaSuccess) return e;
-    // zero the remap counters (here, so that no memset separates the kernels below)
-    e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
-    if (e != cudaSuccess) return e;
-    const bool additive = p->d.remap_variant == 1;
-    remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_raw, p->post_raw,
-                                           p->sn_phi_d, p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st,
-                                           additive ? 0 : 1, p->area, p->d.dt);
-    e = launch_cdf_build(p, p->rem_q, p->rem_cdf, &p->st->remap_W, &p->st->remap_qmax);
-    if (e != cudaSuccess) return e;
-    // steps 3'/4': the leg's census (bank slots, then its n_hist source births) leads the slots
-    const long long lead = additive && p->has_src ? p->d.n_hist : 0;
-    const double w_lead = additive && p->has_src ? p->w_src / (double)p->d.n_hist : 0.0;
-    e = launch_pdl(p->pdl, remap_prep_kernel, dim3(1), dim3(1), 0, s, p->st, (long long)p->d.n_hist, lead, w_lead);
-    if (e != cudaSuccess) return e;
-
+static RemapArgs<T> remap_args(hyb_problem* p) {
     RemapArgs<T> a;
     a.nx = p->nx; a.ny = p->ny;
     a.dx = (T)p->dx; a.dy = (T)p->dy;
@@ -1052,14 +1071,111 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.seed = p->d.seed;
     a.st = p->st;
     a.blk = p->blk;
-    const long long maxN = p->stage_slots;
     a.stg = stage_view<T>(p);
+    a.perm = nullptr;
+    a.nslots = p->stage_slots;
+    a.perm_slots = p->d.census_order >= 1 ? 1 : 0;
+    a.lead_staged = 0;
+    a.mode = 0;
+    return a;
+}
+
+// Bank pre-pass: zero the remap counters, form the bank's scalars and re-stream slots [0, n_bank)
+// into the staging buffer, all on p->side after the work queued on p->stream so far (the leg that
+// last used the staging buffer for its births)
+// the SM count the pre-pass sizes its grid from (queried once per device)
+struct PrepassLimits { int dev = -1, sms = 0; };
+static PrepassLimits g_prepass;
+
+static cudaError_t prepass_limits() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || (g_prepass.sms > 0 && g_prepass.dev == dev)) return e;
+    g_prepass.dev = dev;
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) g_prepass.sms = sms;
+    return e;
+}
+
+template <typename T>
+static cudaError_t bank_prepass_t(hyb_problem* p) {
+    cudaStream_t s = p->side;
+    cudaError_t e = prepass_limits();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(p->ev_fork, p->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamWaitEvent(s, p->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
+    if (e != cudaSuccess) return e;
+    remap_bank_prep_kernel<<<1, 1, 0, s>>>(p->st);
+    RemapArgs<T> a = remap_args<T>(p);
+    a.mode = 1;
+    // One block per SM, each looping over slot blocks: the solve's kernels always find room beside
+    // it (a full-occupancy grid delays the first sweep until its blocks drain; measured: +18 us of
+    // solve per step against +7 us this way)
+    const int nblk = (int)std::min<long long>((p->bank_cap + kSlotsPerBlock - 1) / kSlotsPerBlock,
+                                              (long long)g_prepass.sms);
+    if (nblk > 0) remap_count_kernel<T><<<nblk, kTile, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(p->ev_join, s);
+    if (e != cudaSuccess) return e;
+    p->bank_prepass = true;
+    return cudaSuccess;
+}
+
+cudaError_t launch_remap_bank_prepass(hyb_problem* p) {
+    cudaError_t e = drop_bank_prepass(p);
+    if (e != cudaSuccess) return e;
+    return p->prec == HYB_FP64 ? bank_prepass_t<double>(p) : bank_prepass_t<float>(p);
+}
+
+cudaError_t drop_bank_prepass(hyb_problem* p) {
+    if (!p->bank_prepass) return cudaSuccess;
+    p->bank_prepass = false;
+    return cudaStreamWaitEvent(p->stream, p->ev_join, 0);
+}
+
+template <typename T>
+static cudaError_t remap_t(hyb_problem* p) {
+    cudaStream_t s = p->stream;
+    // remap density and its CDF
+    const int g = (p->ncells + 255) / 256;
+    cudaError_t e = cudaMemsetAsync(&p->st->remap_rmax, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    // a bank pre-pass of this step (launch_remap_bank_prepass) zeroed the remap counters and
+    // staged the bank slots' end states; otherwise zero them here (so that no memset separates
+    // the kernels below)
+    const bool pre = p->bank_prepass;
+    p->bank_prepass = false;
+    if (!pre) {
+        e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
+        if (e != cudaSuccess) return e;
+    }
+    const bool additive = p->d.remap_variant == 1;
+    remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_raw, p->post_raw,
+                                           p->sn_phi_d, p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st,
+                                           additive ? 0 : 1, p->area, p->d.dt);
+    e = launch_cdf_build(p, p->rem_q, p->rem_cdf, &p->st->remap_W, &p->st->remap_qmax);
+    if (e != cudaSuccess) return e;
+    // steps 3'/4': the leg's census (bank slots, then its n_hist source births) leads the slots
+    const long long lead = additive && p->has_src ? p->d.n_hist : 0;
+    const double w_lead = additive && p->has_src ? p->w_src / (double)p->d.n_hist : 0.0;
+    e = launch_pdl(p->pdl, remap_prep_kernel, dim3(1), dim3(1), 0, s, p->st, (long long)p->d.n_hist, lead, w_lead);
+    if (e != cudaSuccess) return e;
+
+    RemapArgs<T> a = remap_args<T>(p);
+    const long long maxN = p->stage_slots;
     a.lead_staged = additive ? 1 : 0;
+    a.mode = pre ? 2 : 0;
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
     const size_t smem = (size_t)(a.ntab * kNibbleWords + a.ntab + 1) * sizeof(uint32_t);
-    a.perm = nullptr;
-    a.nslots = maxN;
-    a.perm_slots = p->d.census_order >= 1 ? 1 : 0;
+    if (pre) {
+        e = cudaStreamWaitEvent(s, p->ev_join, 0);
+        if (e != cudaSuccess) return e;
+    }
     e = launch_pdl(p->pdl, remap_count_kernel<T>, dim3(nblk), dim3(kTile), smem, s, a);
     if (e != cudaSuccess) return e;
     if (p->d.census_order >= 1) {
@@ -1121,6 +1237,7 @@ static cudaError_t census_t(hyb_problem* p) {
     a.nslots = maxN;
     a.perm_slots = 0;
     a.lead_staged = 0;
+    a.mode = 0;
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
     cudaError_t e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
     if (e != cudaSuccess) return e;

@@ -88,6 +88,7 @@ def lib():
         L.hyb_collided_solve.argtypes = [P, C.POINTER(Stats)]
         L.hyb_remap.argtypes = [P, C.POINTER(Stats)]
         L.hyb_step.argtypes = [P, C.c_int32, C.POINTER(Stats)]
+        L.hyb_remap_stats.argtypes = [P, C.POINTER(Stats)]
         L.hyb_get_tally.argtypes = [P, C.c_int32, P, C.c_size_t, C.c_int32]
         L.hyb_set_sn_phi.argtypes = [P, P, C.c_size_t]
         L.hyb_get_bank.argtypes = [P] + [P] * 6 + [C.POINTER(C.c_int64)]
@@ -241,6 +242,12 @@ class Problem:
         s = Stats()
         _check(lib().hyb_remap(self.h, C.byref(s) if stats else None), self.h)
         return s.as_dict() if stats else None
+
+    def remap_stats(self) -> dict:
+        """Statistics of the last remap (of step or remap)."""
+        s = Stats()
+        _check(lib().hyb_remap_stats(self.h, C.byref(s)), self.h)
+        return s.as_dict()
 
     def step(self, n: int = 1, stats: bool = True) -> list[dict] | None:
         arr = (Stats * max(n, 1))()
