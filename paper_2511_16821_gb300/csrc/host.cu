@@ -325,7 +325,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.sntab = hyb::sn_table_bytes(d->nx, d->ny, nord, d->precision == HYB_FP64, d->sn_layout);   // cell-solve table or 0
     z.snqb = 7 * kMaxOrd * T;                     // ox, oy, w, then 4 signed weights per ordinate
     z.snnorm = hyb::sn_norm_bytes((int)nc);       // reduction partials per block and group, group counters
-    z.nblk = (z.slots + 2047) / 2048;
+    z.nblk = (z.slots + 2047) / 2048;   // remap census pieces of 2048 slots (partials)
     z.blk = 4 * (size_t)z.nblk * 8;
     z.gr = hyb::guide_bits(d->ny);
     z.gc = hyb::guide_bits(d->nx);

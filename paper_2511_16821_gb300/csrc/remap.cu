@@ -27,8 +27,10 @@
 
 namespace hyb {
 
-constexpr int kRounds = 8;                       // slot rounds per block (2048 slots per block)
+constexpr int kRounds = 8;                       // slot rounds per pass-B block (2048 census positions)
 constexpr int kSlotsPerBlock = kTile * kRounds;
+constexpr int kPartSlots = kSlotsPerBlock;      // census piece: the unit of the partials (one pass B block)
+constexpr int kPartsPerBlock = kSlotsPerBlock / kPartSlots;
 
 // ---------------------------------------------------------------------------------------------
 // CDF build
@@ -501,8 +503,46 @@ __global__ void remap_bank_prep_kernel(DevState* st) {
     st->rsb = r;
 }
 
+// Block sum of v (one value per thread) in a fixed order (warp trees, then the warps in order);
+// the result is valid in thread 0. Ends with the block synchronised (s may be reused after it).
+template <typename V>
+__device__ __forceinline__ V block_sum_fixed(V v, V* s) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    V t = V(0);
+    if (threadIdx.x == 0)
+        for (int w = 0; w < kTile / 32; ++w) t += s[w];
+    __syncthreads();
+    return t;
+}
+
+// 128-bit fixed point of a block's FP64 |w| sum (scale 2^k) or of an FP32 int64 sum at per-thread
+// scale 2^kt (k - kt >= 64: the value shifted left by k - kt - 64 in the high word)
+__device__ __forceinline__ void fixed128(double d, long long f, bool f32, int k, int kt, unsigned long long* lo,
+                                         unsigned long long* hi) {
+    if (f32) {
+        const int sh = k - kt - 64;
+        *lo = 0ull;
+        *hi = sh < 63 ? (unsigned long long)f << sh : 0ull;   // two's complement: signed sums too
+    } else {
+        to_i128(d * ldexp(1.0, k), lo, hi);
+    }
+}
+
+// Pass A. Slots are taken in rounds of 32 (one slot per lane of a warp), dealt to the warps of
+// a persistent grid in a fixed interleave: warp g takes rounds g, g + W, g + 2W, ... of the order
+// births first, then the slots ahead of them (a birth costs several times a staged or re-streamed
+// bank slot). Every warp so ends within one round of the others, where a block per 2048 slots
+// left a second, nearly empty wave of latency-bound birth blocks behind the first. Each round adds
+// its census partials (alive count, quantised |w|, fixed-point |w|) to the piece of kPartSlots
+// slots it belongs to (blk zeroed beforehand; integer additions, so the order does not matter).
+// The bank pre-pass (mode 1) takes the bank slots' rounds and adds no partials. The rounds of a
+// thread are fixed, so its weight sums (FP32 int64, FP64 doubles, summed per block in a fixed
+// order at the end) are reproducible run to run.
 template <typename T>
-__global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
+__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) remap_count_kernel(RemapArgs<T> a) {
     pdl_wait();
     pdl_trigger();
     extern __shared__ uint32_t sm[];
@@ -510,17 +550,19 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     uint32_t* sSh = sm + a.ntab * kNibbleWords;
     const bool prepass = a.mode == 1;
     // the bank pre-pass runs before the remap density exists: bank slots only (no step-start
-    // r_lead slots there), scales from the bank alone; its blocks loop over the slot blocks (a
-    // grid of fewer blocks than SMs leaves room for the collided solve's kernels beside it)
+    // r_lead slots there), scales from the bank alone
     const long long nb = prepass ? a.st->n_bank : a.st->n_bank + a.st->r_lead;   // slots ahead of the births
-    if (prepass && (long long)blockIdx.x * kSlotsPerBlock >= nb) return;
+    const long long nrounds = prepass ? (nb + 31) / 32 : (a.nslots + 31) / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const long long gwarp = (long long)blockIdx.x * (kTile / 32) + wid, nwarps = (long long)gridDim.x * (kTile / 32);
     const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_REMAP_SOURCE);
-    // point tables only where the block holds births
-    if (!prepass && (long long)(blockIdx.x + 1) * kSlotsPerBlock > nb) {
+    if (!prepass) {
         build_point_tables(a.V, a.ntab, sV, a.sampler);
         for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
     }
     __shared__ RemapScal s_rs;
+    __shared__ long long s_red[kTile / 32];
+    __shared__ double s_redd[kTile / 32];
     if (threadIdx.x == 0) s_rs = prepass ? a.st->rsb : a.st->rs;
     __syncthreads();
     Points pts{sV, sSh, key, a.sampler, a.ntab};
@@ -529,114 +571,93 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     const T wbar_t = (T)s_rs.wbar;
     const double w_ref = s_rs.w_ref;
     const float qsc = s_rs.qsc;
-    // block scales (128-bit): krw for the survivors' sum |w|, kw for the statistics
+    // scales (128-bit): krw for the survivors' sum |w|, kw for the statistics
     const int krw = s_rs.krw, kw = s_rs.kw;
     constexpr bool kF32 = sizeof(T) == 4;
     const int kfa = s_rs.kfa, kf = s_rs.kf;   // FP32 per-thread scales
     const float sca = s_rs.sca;
+    Acc128* wd[4] = {&a.st->r_w_source, &a.st->r_w_absorbed, &a.st->r_w_leaked, &a.st->r_w_killed};
+    if (prepass) { wd[0] = &a.st->r_wb[0]; wd[1] = &a.st->r_wb[1]; wd[2] = &a.st->r_wb[2]; wd[3] = &a.st->r_wb[3]; }
     RemapSums<T> sums;
     sums.init(kf);
-    long long cnt = 0, qs = 0, wsf = 0;
-    double ws = 0;
     int leaked = 0, killed = 0, segs = 0, err = 0;
-    const long long nbb = prepass ? (nb + kSlotsPerBlock - 1) / kSlotsPerBlock : (long long)blockIdx.x + 1;
-    for (long long bb = blockIdx.x; bb < nbb; bb += prepass ? gridDim.x : 1)
-    for (int r = 0; r < kRounds; ++r) {
-        const long long j = bb * kSlotsPerBlock + r * kTile + threadIdx.x;
-        if (j >= N) {
-            if (!prepass && a.perm_slots && j < a.nslots) a.stg.cell[j] = -1;   // unused slots sort last, as dead
-            continue;
+    const long long first_birth = prepass ? 0 : nb / 32;   // births-first order of the rounds
+    for (long long rr = gwarp; rr < nrounds; rr += nwarps) {
+        const long long round = prepass ? rr : (rr + first_birth < nrounds ? rr + first_birth : rr + first_birth - nrounds);
+        const long long j = round * 32 + lane;
+        long long cnt = 0, qs = 0, wsf = 0;
+        double ws = 0;
+        if (j < N) {
+            Particle<T> pr;
+            if (staged && j < nb) {
+                // steps 3'/4': the MC leg staged its census here; it enters the census as it is. After
+                // a bank pre-pass: the bank particle's end state, staged (and counted) by the pre-pass
+                pr.cell = a.stg.cell[j];
+                pr.alive = pr.cell >= 0;
+                pr.w = pr.alive ? a.stg.w[j] : T(0);
+            } else {
+                pr = remap_slot<T>(a, pts, j, nb, wbar_t, sums, &leaked, &killed, &segs, &err);
+                a.stg.cell[j] = pr.alive ? pr.cell : -1;
+                a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
+            }
+            if (pr.alive) {
+                cnt = 1;
+                qs = quant<T>(pr.w, w_ref, qsc);
+                if constexpr (kF32) wsf = f2ll_rn(fabsf(pr.w) * sca);
+                else ws = fabs((double)pr.w);
+            }
+        } else if (!prepass && a.perm_slots && j < a.nslots) {
+            a.stg.cell[j] = -1;   // unused slots sort last, as dead
         }
-        Particle<T> pr;
-        if (staged && j < nb) {
-            // steps 3'/4': the MC leg staged its census here; it enters the census as it is. After a
-            // bank pre-pass: the bank particle's end state, staged (and counted) by the pre-pass
-            pr.cell = a.stg.cell[j];
-            pr.alive = pr.cell >= 0;
-            pr.w = pr.alive ? a.stg.w[j] : T(0);
-        } else {
-            pr = remap_slot<T>(a, pts, j, nb, wbar_t, sums, &leaked, &killed, &segs, &err);
-            a.stg.cell[j] = pr.alive ? pr.cell : -1;
-            a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
-        }
-        if (pr.alive) {
-            ++cnt;
-            qs += quant<T>(pr.w, w_ref, qsc);
-            if constexpr (kF32) wsf += f2ll_rn(fabsf(pr.w) * sca);
-            else ws += fabs((double)pr.w);
-        }
-    }
-    // block sums in fixed order
-    __shared__ long long s_l[kTile / 32][3];
-    __shared__ double s_d[kTile / 32][5];
-    __shared__ long long s_f[kTile / 32][4];
-    __shared__ int s_i[kTile / 32][4];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-        qs += __shfl_down_sync(0xffffffffu, qs, o);
-        wsf += __shfl_down_sync(0xffffffffu, wsf, o);
-        leaked += __shfl_down_sync(0xffffffffu, leaked, o);
-        killed += __shfl_down_sync(0xffffffffu, killed, o);
-        segs += __shfl_down_sync(0xffffffffu, segs, o);
-        err += __shfl_down_sync(0xffffffffu, err, o);
-    }
-    if constexpr (kF32) {
-        for (int t = 0; t < 4; ++t) sums.v[t] = (long long)warp_sum_u64((unsigned long long)sums.v[t]);
-    } else {
-        ws = warp_sum(ws);
-        for (int t = 0; t < 4; ++t) sums.v[t] = warp_sum(sums.v[t]);
-    }
-    if (lane == 0) {
-        s_l[wid][0] = cnt; s_l[wid][1] = qs; s_l[wid][2] = wsf;
-        s_d[wid][0] = ws;
-        for (int t = 0; t < 4; ++t) {
-            if constexpr (kF32) s_f[wid][t] = sums.v[t];
-            else s_d[wid][t + 1] = sums.v[t];
-        }
-        s_i[wid][0] = leaked; s_i[wid][1] = killed; s_i[wid][2] = segs; s_i[wid][3] = err;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long c = 0, q = 0, af = 0;
-        double d[5] = {0, 0, 0, 0, 0};
-        long long fv[4] = {0, 0, 0, 0};
-        long long iv[4] = {0, 0, 0, 0};
-        for (int ww = 0; ww < kTile / 32; ++ww) {
-            c += s_l[ww][0]; q += s_l[ww][1]; af += s_l[ww][2];
-            for (int t = 0; t < 5; ++t) d[t] += s_d[ww][t];
-            for (int t = 0; t < 4; ++t) fv[t] += s_f[ww][t];
-            for (int t = 0; t < 4; ++t) iv[t] += s_i[ww][t];
-        }
-        unsigned long long lo, hi;
         if (!prepass) {
-            long long* b = a.blk + 4 * (size_t)blockIdx.x;
-            if constexpr (kF32) {
-                // af 2^-kfa = af 2^(krw - kfa) 2^-krw: the 128-bit value is af shifted left by krw - kfa >= 64
-                const int sh = krw - kfa - 64;
-                lo = 0ull;
-                hi = sh < 63 ? (unsigned long long)af << sh : 0ull;
-            } else {
-                to_i128(d[0] * ldexp(1.0, krw), &lo, &hi);
+            // the round's census partials into its piece (warp trees: a fixed order per round)
+            cnt = (long long)__popc(__ballot_sync(0xffffffffu, cnt != 0));
+            if (cnt) {
+                qs = (long long)warp_sum_u64((unsigned long long)qs);
+                if constexpr (kF32) wsf = (long long)warp_sum_u64((unsigned long long)wsf);
+                else ws = warp_sum(ws);
+                if (lane == 0) {
+                    unsigned long long lo, hi;
+                    fixed128(ws, wsf, kF32, krw, kfa, &lo, &hi);
+                    long long* b = a.blk + 4 * (size_t)(round / (kPartSlots / 32));
+                    atomicAdd((unsigned long long*)b, (unsigned long long)cnt);
+                    if (qs) atomicAdd((unsigned long long*)(b + 1), (unsigned long long)qs);
+                    atomic_add128(reinterpret_cast<Acc128*>(b + 2), lo, hi);
+                }
             }
-            b[0] = c; b[1] = q; b[2] = (long long)lo; b[3] = (long long)hi;
         }
-        Acc128* wd[4] = {&a.st->r_w_source, &a.st->r_w_absorbed, &a.st->r_w_leaked, &a.st->r_w_killed};
-        if (prepass) { wd[0] = &a.st->r_wb[0]; wd[1] = &a.st->r_wb[1]; wd[2] = &a.st->r_wb[2]; wd[3] = &a.st->r_wb[3]; }
+    }
+    if constexpr (!kF32) {
+        // FP64 weight statistics: a fixed-order block sum, then 128-bit fixed point
         for (int t = 0; t < 4; ++t) {
-            if constexpr (kF32) {
-                const int sh = kw - kf - 64;
-                lo = 0ull;
-                hi = sh < 63 ? (unsigned long long)fv[t] << sh : 0ull;   // two's complement: signed sums too
-            } else {
-                to_i128(d[t + 1] * ldexp(1.0, kw), &lo, &hi);
+            const double v = block_sum_fixed(sums.v[t], s_redd);
+            if (threadIdx.x == 0) {
+                unsigned long long lo, hi;
+                to_i128(v * ldexp(1.0, kw), &lo, &hi);
+                if (lo | hi) atomic_add128(wd[t], lo, hi);
             }
-            atomic_add128(wd[t], lo, hi);
         }
-        if (iv[0]) atomicAdd(&a.st->r_leaked, (unsigned long long)iv[0]);
-        if (iv[1]) atomicAdd(&a.st->r_killed, (unsigned long long)iv[1]);
-        if (iv[2]) atomicAdd(&a.st->r_segments, (unsigned long long)iv[2]);
-        if (iv[3]) { atomicAdd(&a.st->r_errors, (unsigned long long)iv[3]); atomicOr(&a.st->status, kStSegments); }
+    }
+    // counters and the FP32 weight statistics, once per block
+    const long long il = block_sum_fixed((long long)leaked, s_red);
+    const long long ik = block_sum_fixed((long long)killed, s_red);
+    const long long is = block_sum_fixed((long long)segs, s_red);
+    const long long ie = block_sum_fixed((long long)err, s_red);
+    long long fv[4] = {0, 0, 0, 0};
+    if constexpr (kF32)
+        for (int t = 0; t < 4; ++t) fv[t] = block_sum_fixed((long long)sums.v[t], s_red);
+    if (threadIdx.x == 0) {
+        if constexpr (kF32) {
+            for (int t = 0; t < 4; ++t) {
+                unsigned long long lo, hi;
+                fixed128(0.0, fv[t], true, kw, kf, &lo, &hi);
+                if (lo | hi) atomic_add128(wd[t], lo, hi);
+            }
+        }
+        if (il) atomicAdd(&a.st->r_leaked, (unsigned long long)il);
+        if (ik) atomicAdd(&a.st->r_killed, (unsigned long long)ik);
+        if (is) atomicAdd(&a.st->r_segments, (unsigned long long)is);
+        if (ie) { atomicAdd(&a.st->r_errors, (unsigned long long)ie); atomicOr(&a.st->status, kStSegments); }
         if (blockIdx.x == 0) {
             if (prepass) a.st->k_rwb = kw;
             else { a.st->k_rw = kw; a.st->r_histories = (unsigned long long)(N - a.st->r_lead); }
@@ -646,8 +667,8 @@ __global__ void __launch_bounds__(kTile) remap_count_kernel(RemapArgs<T> a) {
     }
 }
 
-// The per-block partials (alive count, quantised |w| sum, fixed-point |w| sum) of the staged end
-// states in census order (sorted positions, or slots when perm is null). For a cell-ordered
+// The per-piece partials (alive count, quantised |w| sum, fixed-point |w| sum) of the staged end
+// states in census order (sorted positions, or slots when perm is null), one block per piece. For a cell-ordered
 // remap census they replace the slot-order partials of the count pass (the totals are the same
 // integers in any order); for N_s = infinity they are the only partials.
 template <typename T>
@@ -664,8 +685,8 @@ __global__ void __launch_bounds__(kTile) remap_partials_kernel(RemapArgs<T> a) {
     constexpr bool kF32 = sizeof(T) == 4;
     long long cnt = 0, qs = 0, wsf = 0;
     double ws = 0;
-    const long long base = (long long)blockIdx.x * kSlotsPerBlock;
-    for (int r = 0; r < kRounds; ++r) {
+    const long long base = (long long)blockIdx.x * kPartSlots;
+    for (int r = 0; r < kPartSlots / kTile; ++r) {
         const long long j = base + r * kTile + threadIdx.x;
         if (j >= N) break;
         const long long js = a.perm ? (long long)(uint32_t)a.perm[j] : j;
@@ -765,28 +786,38 @@ static cudaError_t sort_census(hyb_problem* p, const BankView<T>& stg, long long
     return launch_census_sort(stg.cell, n, (uint32_t)p->ncells, pairs, p->sort_counts, s, perm);
 }
 
-// one block: exclusive scan of block counts and quantised sums; totals, comb decision
+// One block: exclusive scan of the pieces' alive counts and quantised sums in place (tiles of
+// blockDim.x consecutive pieces, one per thread, so that every load and store is coalesced; the
+// running totals carry from tile to tile), the 128-bit |w| total, and the comb decision.
 __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long long cap, uint64_t seed, int sampler,
                                   long long n_hist) {
     pdl_wait();
     pdl_trigger();
     const uint32_t x_off = first_point(dstream_key(seed, (uint64_t)st->step, HYB_STREAM_REMAP_COMB), sampler);
-    __shared__ long long sc[1024], sq[1024];
-    __shared__ unsigned long long slo[1024], shi[1024];
+    __shared__ unsigned long long slo[32], shi[32];
     const int t = threadIdx.x, nt = blockDim.x;
-    const int per = (nblk + nt - 1) / nt;
-    const int b0 = t * per;
-    long long c = 0, q = 0;
-    unsigned long long lo = 0, hi = 0;
-    for (int b = b0; b < b0 + per && b < nblk; ++b) {
-        c += blk[4 * b]; q += blk[4 * b + 1];
-        const unsigned long long l = (unsigned long long)blk[4 * b + 2], h = (unsigned long long)blk[4 * b + 3];
-        const unsigned long long nl = lo + l;
-        hi += h + (nl < lo ? 1ull : 0ull);
-        lo = nl;
+    long long run_c = 0, run_q = 0;          // totals of the tiles before (the same in every thread)
+    unsigned long long lo = 0, hi = 0;       // this thread's share of the 128-bit |w| total
+    for (int t0 = 0; t0 < nblk; t0 += nt) {
+        const int b = t0 + t;
+        long long c = 0, q = 0;
+        if (b < nblk) {
+            const longlong4_32a v = *reinterpret_cast<const longlong4_32a*>(blk + 4 * (size_t)b);
+            c = v.x; q = v.y;
+            const unsigned long long l = (unsigned long long)v.z, h = (unsigned long long)v.w;
+            const unsigned long long nl = lo + l;
+            hi += h + (nl < lo ? 1ull : 0ull);
+            lo = nl;
+        }
+        long long tc, tq;
+        const long long exc = block_exclusive_scan(c, &tc);
+        const long long exq = block_exclusive_scan(q, &tq);
+        if (b < nblk) { blk[4 * (size_t)b] = run_c + exc; blk[4 * (size_t)b + 1] = run_q + exq; }
+        run_c += tc;
+        run_q += tq;
     }
-    // the 128-bit sum of |w| over the block: a shuffle tree per warp, then the warp sums (exact
-    // modular integer additions, so the order does not matter)
+    // the 128-bit sum of |w|: a shuffle tree per warp, then the warp sums (exact modular integer
+    // additions, so the order does not matter)
     {
         unsigned long long wl = lo, wh = hi;
 #pragma unroll
@@ -798,10 +829,6 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
         }
         if ((t & 31) == 0) { slo[t >> 5] = wl; shi[t >> 5] = wh; }
     }
-    long long ac, aq;
-    const long long exc = block_exclusive_scan(c, &ac);
-    const long long exq = block_exclusive_scan(q, &aq);
-    sc[t] = exc; sq[t] = exq;
     __syncthreads();
     if (t == 0) {
         unsigned long long al = 0, ah = 0;
@@ -810,6 +837,7 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
             ah += shi[u] + (nl < al ? 1ull : 0ull);
             al = nl;
         }
+        const long long ac = run_c, aq = run_q;
         const long long nb = st->n_bank + st->r_lead;
         const long long nbirth = st->remap_W > 0 ? n_hist : 0;
         const long long N = nb + nbirth;
@@ -828,13 +856,6 @@ __global__ void remap_scan_kernel(long long* blk, int nblk, DevState* st, long l
         st->r_alive = (unsigned long long)ac;
         st->bank_wsum = wsum;
         st->bank_wmax = comb ? st->wcopy : 0.0;   // non-comb: max gathered in pass B
-    }
-    __syncthreads();
-    long long rc = sc[t], rq = sq[t];
-    for (int b = b0; b < b0 + per && b < nblk; ++b) {
-        const long long cc = blk[4 * b], qq = blk[4 * b + 1];
-        blk[4 * b] = rc; blk[4 * b + 1] = rq;
-        rc += cc; rq += qq;
     }
 }
 
@@ -990,8 +1011,9 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
     }
     long long ec, eq, tc, tq;
     block_exclusive_scan2(c, qt, &ec, &eq, &tc, &tq);
-    long long pos = a.blk[4 * (size_t)blockIdx.x] + ec;
-    long long S = a.blk[4 * (size_t)blockIdx.x + 1] + eq;
+    const size_t b0 = 4 * (size_t)blockIdx.x * kPartsPerBlock;   // the block's first census piece
+    long long pos = a.blk[b0] + ec;
+    long long S = a.blk[b0 + 1] + eq;
     T wmax = 0;
     if (combing) {
         const unsigned long long uT = (unsigned long long)Ttot, uM = (unsigned long long)M, uo = (unsigned long long)o;
@@ -1098,6 +1120,25 @@ static cudaError_t prepass_limits() {
     return e;
 }
 
+// resident blocks of pass A on this device (blocks per SM at its shared memory, times the SMs)
+template <typename T>
+static cudaError_t count_grid(size_t smem, int* blocks) {
+    static int per_sm[2] = {0, 0};
+    static size_t per_smem[2] = {0, 0};
+    cudaError_t e = prepass_limits();
+    if (e != cudaSuccess) return e;
+    const int t = sizeof(T) == 4 ? 0 : 1;
+    if (per_sm[t] == 0 || per_smem[t] != smem) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, remap_count_kernel<T>, kTile, smem);
+        if (e != cudaSuccess) return e;
+        per_sm[t] = n > 0 ? n : 1;
+        per_smem[t] = smem;
+    }
+    *blocks = per_sm[t] * g_prepass.sms;
+    return cudaSuccess;
+}
+
 template <typename T>
 static cudaError_t bank_prepass_t(hyb_problem* p) {
     cudaStream_t s = p->side;
@@ -1115,8 +1156,7 @@ static cudaError_t bank_prepass_t(hyb_problem* p) {
     // One block per SM, each looping over slot blocks: the solve's kernels always find room beside
     // it (a full-occupancy grid delays the first sweep until its blocks drain; measured: +18 us of
     // solve per step against +7 us this way)
-    const int nblk = (int)std::min<long long>((p->bank_cap + kSlotsPerBlock - 1) / kSlotsPerBlock,
-                                              (long long)g_prepass.sms);
+    const int nblk = (int)std::min<long long>((p->bank_cap + kSlotsPerBlock - 1) / kSlotsPerBlock, (long long)g_prepass.sms);
     if (nblk > 0) remap_count_kernel<T><<<nblk, kTile, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1150,6 +1190,9 @@ static cudaError_t remap_t(hyb_problem* p) {
     // the kernels below)
     const bool pre = p->bank_prepass;
     p->bank_prepass = false;
+    // pass A adds each round's census partials to its piece
+    e = cudaMemsetAsync(p->blk, 0, 4 * sizeof(long long) * (size_t)((p->stage_slots + kPartSlots - 1) / kPartSlots), s);
+    if (e != cudaSuccess) return e;
     if (!pre) {
         e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
         if (e != cudaSuccess) return e;
@@ -1170,22 +1213,26 @@ static cudaError_t remap_t(hyb_problem* p) {
     const long long maxN = p->stage_slots;
     a.lead_staged = additive ? 1 : 0;
     a.mode = pre ? 2 : 0;
-    const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
+    const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);    // pass B blocks
+    const int nparts = (int)((maxN + kPartSlots - 1) / kPartSlots);          // census pieces
     const size_t smem = (size_t)(a.ntab * kNibbleWords + a.ntab + 1) * sizeof(uint32_t);
+    int resident = 0;
+    e = count_grid<T>(smem, &resident);
+    if (e != cudaSuccess) return e;
     if (pre) {
         e = cudaStreamWaitEvent(s, p->ev_join, 0);
         if (e != cudaSuccess) return e;
     }
-    e = launch_pdl(p->pdl, remap_count_kernel<T>, dim3(nblk), dim3(kTile), smem, s, a);
+    e = launch_pdl(p->pdl, remap_count_kernel<T>, dim3(std::min(nparts, resident)), dim3(kTile), smem, s, a);
     if (e != cudaSuccess) return e;
     if (p->d.census_order >= 1) {
         // survivors in cell (or phase-space) order, stable: the comb and the census write follow it
         e = sort_census<T>(p, a.stg, maxN, s, &a.perm);
         if (e != cudaSuccess) return e;
-        remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);
+        remap_partials_kernel<T><<<nparts, kTile, 0, s>>>(a);
     }
-    e = launch_pdl(p->pdl, remap_scan_kernel, dim3(1), dim3(1024), 0, s, p->blk, nblk, p->st, a.cap, a.seed, a.sampler,
-                   (long long)p->d.n_hist);
+    e = launch_pdl(p->pdl, remap_scan_kernel, dim3(1), dim3(1024), 0, s, p->blk, nparts, p->st, a.cap, a.seed,
+                   a.sampler, (long long)p->d.n_hist);
     if (e != cudaSuccess) return e;
     e = launch_pdl(p->pdl, remap_write_kernel<T>, dim3(nblk), dim3(kTile), 0, s, a);
     if (e != cudaSuccess) return e;
@@ -1239,6 +1286,7 @@ static cudaError_t census_t(hyb_problem* p) {
     a.lead_staged = 0;
     a.mode = 0;
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);
+    const int nparts = (int)((maxN + kPartSlots - 1) / kPartSlots);
     cudaError_t e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
     if (e != cudaSuccess) return e;
     if (p->d.census_order >= 1) {
@@ -1246,8 +1294,8 @@ static cudaError_t census_t(hyb_problem* p) {
         e = sort_census<T>(p, a.stg, maxN, s, &a.perm);
         if (e != cudaSuccess) return e;
     }
-    remap_partials_kernel<T><<<nblk, kTile, 0, s>>>(a);
-    remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nblk, p->st, a.cap, a.seed, a.sampler, p->d.n_hist);
+    remap_partials_kernel<T><<<nparts, kTile, 0, s>>>(a);
+    remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nparts, p->st, a.cap, a.seed, a.sampler, p->d.n_hist);
     remap_write_kernel<T><<<nblk, kTile, 0, s>>>(a);
     remap_finish_kernel<<<1, 1, 0, s>>>(p->st);
     return cudaGetLastError();
