@@ -270,7 +270,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
         sn4, sn16, sntx, sntab, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell,
-        sortkey;
+        sortkey, btab;
     int64_t cap, nblk, slots;
     int gr, gc;
 };
@@ -341,6 +341,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.sortkv = d->census_order >= 1 ? nslots * 8 : 0;                    // x2: (key, slot) pairs, ping-pong
     z.sortc = d->census_order >= 1 ? 256 * ((nslots + 2047) / 2048 + 1) * 4 : 0;
     z.sortkey = d->census_order == 2 ? nslots * 4 : 0;                   // phase-space keys per slot
+    z.btab = d->sampler == HYB_SOBOL_DS ? (size_t)kByteDims * kByteWords * 4 : 0;   // births' Sobol byte tables
     return z;
 }
 
@@ -351,7 +352,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.sntab, z.snqb, z.d4, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
-                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey};
+                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey, z.btab};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -414,6 +415,7 @@ void assign(hyb_problem* p) {
     p->aa_state = z.aas ? take(z.aas) : nullptr;
     p->ns_cell = z.nscell ? (int32_t*)take(z.nscell) : nullptr;
     p->sort_keys = z.sortkey ? (int32_t*)take(z.sortkey) : nullptr;
+    p->byte_tab = z.btab ? (uint32_t*)take(z.btab) : nullptr;
     p->bank_cap = z.cap;
     p->stage_slots = z.slots;
     p->nblk_max = z.nblk;
@@ -751,6 +753,22 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     size_t ptab_bytes = 0;
     const uint32_t* ptab = point_table_host(d->sampler, &ptab_bytes);
     if (chk(cudaMemcpyAsync(p->point_tab, ptab, ptab_bytes, cudaMemcpyHostToDevice, st), "copy point table") != HYB_OK) return bail(HYB_ECUDA);
+    std::vector<uint32_t> btab;
+    if (p->byte_tab) {
+        // Sobol byte tables of the births' dimensions: entry (d, k, v) = XOR of the direction numbers
+        // of dimension d over the set bits of v, bits 8k..8k+7 of the index
+        btab.assign((size_t)kByteDims * kByteWords, 0u);
+        for (int dd = 0; dd < kByteDims; ++dd)
+            for (int k = 0; k < 4; ++k)
+                for (int v = 0; v < 256; ++v) {
+                    uint32_t x = 0;
+                    for (int j = 0; j < 8; ++j)
+                        if ((v >> j) & 1) x ^= ptab[dd * 32 + 8 * k + j];
+                    btab[(size_t)dd * kByteWords + 256 * k + v] = x;
+                }
+        if (chk(cudaMemcpyAsync(p->byte_tab, btab.data(), btab.size() * 4, cudaMemcpyHostToDevice, st), "copy byte tables") != HYB_OK)
+            return bail(HYB_ECUDA);
+    }
     if (chk(cudaMemcpyAsync(p->sig, sig.data(), sig.size(), cudaMemcpyHostToDevice, st), "copy sigma") != HYB_OK) return bail(HYB_ECUDA);
     // FP32 path: one 32-byte record per cell (a single memory sector): the reciprocals (1/sigma_a,
     // 1/sigma_s, 1/sigma_t), 0 where the cross section is 0, the cell's scatter limit as the bits of

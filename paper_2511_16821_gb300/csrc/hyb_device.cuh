@@ -202,6 +202,37 @@ struct Points {
     }
 };
 
+// Sobol byte tables: for dimension d < kByteDims and byte k of the index, entry v is the XOR of the
+// direction numbers of the set bits of v (bits 8k..8k+7 of the index): a point is four table
+// reads (three below 2^24). Consecutive indices differ in their low byte, so a warp's reads of the
+// first table hit distinct banks; the other three are broadcasts. The births' dimensions use them.
+constexpr int kByteDims = 6;
+constexpr int kByteWords = 1024;   // 4 bytes x 256 entries per dimension
+
+// A point set whose first nbt dimensions come from byte tables BT (Sobol with digital shift), the
+// rest as in Points (nbt = 0 for the other samplers)
+struct PointsB {
+    const uint32_t* BT;
+    int nbt;
+    Points base;
+    __device__ __forceinline__ uint32_t operator()(uint32_t i, int d) const {
+        if (d < nbt) {
+            const uint32_t* t = BT + d * kByteWords;
+            return base.shift[d] ^ t[i & 255u] ^ t[256 + ((i >> 8) & 255u)] ^ t[512 + ((i >> 16) & 255u)] ^
+                   t[768 + (i >> 24)];
+        }
+        return base(i, d);
+    }
+};
+
+// copies the byte tables of nbt dimensions (global, nbt x kByteWords words) into sBT; all threads
+// of the block call it, the caller synchronises
+__device__ __forceinline__ void copy_byte_tables(const uint32_t* __restrict__ bt, int nbt, uint32_t* sBT) {
+    const uint4* src = reinterpret_cast<const uint4*>(bt);
+    uint4* dst = reinterpret_cast<uint4*>(sBT);
+    for (int e = threadIdx.x; e < nbt * kByteWords / 4; e += blockDim.x) dst[e] = __ldg(src + e);
+}
+
 // ---------------------------------------------------------------------------------------------
 // Integer <-> float conversions on the integer pipe. The conversion instructions count against
 // the FP64 pipe on this GPU (a small fraction of the FP32 rate; measured as FP64-pipe activity in
@@ -498,26 +529,24 @@ __device__ __forceinline__ void iso_dir(uint32_t x_mu, uint32_t x_phi, T* ox, T*
 
 // ---------------------------------------------------------------------------------------------
 // integer CDF pick: bin j of pre[0..n] with pre[j] 2^33 <= (2x+1) total < pre[j+1] 2^33, searched
-// in [lo, hi] (which must hold it); a, b: the remainder split as rem = a 2^33 + b; W: the bin weight
+// in [lo, hi] (which must hold it); a, b: the remainder split as rem = a 2^33 + b; W: the bin weight.
+// With P = (2x+1) total < 2^95 and Tx = floor(P / 2^33) < 2^62, pre[j] 2^33 <= P is pre[j] <= Tx
+// (pre[j] an integer), so the search compares 64-bit integers, and rem = (Tx - pre[j]) 2^33 +
+// (P mod 2^33): a = Tx - pre[j], b = P mod 2^33.
 __device__ __forceinline__ int pick_bin(const long long* __restrict__ pre, int n, uint32_t x, int lo, int hi,
-                                        unsigned long long* a, unsigned long long* b,
-                                        unsigned long long* W) {
+                                        unsigned long long* a, unsigned long long* b, unsigned long long* W) {
     const unsigned long long total = (unsigned long long)pre[n];
     const unsigned long long m = 2ull * (unsigned long long)x + 1ull;
     const unsigned long long Plo = m * total, Phi = __umul64hi(m, total);
+    const unsigned long long Tx = (Phi << 31) | (Plo >> 33);
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const unsigned long long v = (unsigned long long)pre[mid];
-        const unsigned long long vhi = v >> 31, vlo = v << 33;
-        if (vhi < Phi || (vhi == Phi && vlo <= Plo)) lo = mid; else hi = mid - 1;
+        if ((unsigned long long)pre[mid] <= Tx) lo = mid; else hi = mid - 1;
     }
     const unsigned long long v = (unsigned long long)pre[lo];
-    const unsigned long long vhi = v >> 31, vlo = v << 33;
-    const unsigned long long rlo = Plo - vlo;
-    const unsigned long long rhi = Phi - vhi - (Plo < vlo ? 1ull : 0ull);
-    *a = (rhi << 31) | (rlo >> 33);
-    *b = rlo & ((1ull << 33) - 1ull);
-    *W = (unsigned long long)(pre[lo + 1] - pre[lo]);
+    *a = Tx - v;
+    *b = Plo & ((1ull << 33) - 1ull);
+    *W = (unsigned long long)pre[lo + 1] - v;
     return lo;
 }
 

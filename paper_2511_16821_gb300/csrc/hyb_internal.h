@@ -136,6 +136,7 @@ struct hyb_problem {
                               // sigma_s, 0, 0
     int32_t* ns_cell;         // per-cell scatter limits (space-dependent N_s), or null
     int32_t* sort_keys;       // census in phase-space order: the sort key of every staging slot
+    uint32_t* byte_tab;       // Sobol byte tables of the births' dimensions (Sobol sampler only)
     double *sa_d, *ss_d, *Q_d;  // FP64 copies for the remap density
     hyb::Cdf2DView src_cdf, rem_cdf;
     double* rem_f;            // 4 x ncells remap density coefficients

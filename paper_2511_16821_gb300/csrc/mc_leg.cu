@@ -28,6 +28,7 @@ struct LegArgs {
     int n_s, sampler, handoff_full, ntab;
     T w_min;
     const uint32_t* V;
+    const uint32_t* bt;         // Sobol byte tables of the births' dimensions (kByteDims x kByteWords), or null
     uint64_t seed;              // keys of the census and source point sets come from (seed, step)
     BankView<T> bank;
     BirthView<T> births;        // staged source births (cell == nullptr: drawn inside the leg)
@@ -124,8 +125,8 @@ __device__ __forceinline__ long long fix_w(double x, double scw, float) { return
 // (dims 0, 1), remaining flight c dt (1 - u) from the birth time (dim 2), isotropic direction
 // (dims 3, 4), first optical depth -log u (dim 5) when N_s > 0. Used by the birth kernel and by
 // the leg when births are not staged, so both give the same state bit for bit.
-template <typename T>
-__device__ __forceinline__ void birth_state(const LegArgs<T>& a, const Points& pts, uint32_t i, int* ix, int* iy, T* fx,
+template <typename T, typename Pts>
+__device__ __forceinline__ void birth_state(const LegArgs<T>& a, const Pts& pts, uint32_t i, int* ix, int* iy, T* fx,
                                             T* fy, T* ox, T* oy, T* srem, T* tau) {
     using P = Prec<T>;
     T frx, fry;
@@ -259,7 +260,7 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                         h.tau = a.births.tau[h.idx];
                     } else {
                         pts.key = key_s; pts.shift = sShS;
-                        birth_state<T>(a, pts, h.idx, &h.ix, &h.iy, &h.fx, &h.fy, &h.ox, &h.oy, &h.srem, &h.tau);
+                        birth_state<T, Points>(a, pts, h.idx, &h.ix, &h.iy, &h.fx, &h.fy, &h.ox, &h.oy, &h.srem, &h.tau);
                     }
                     h.w = a.w0;
                 }
@@ -573,13 +574,13 @@ mc_leg_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __restr
 }
 
 // Source births of one problem, [i0, i1) of its birth indices, into its birth staging arrays.
-template <typename T>
-__device__ __forceinline__ void births_range(const LegArgs<T>& a, const Points& pts, long long i0, long long i1,
+template <typename T, typename Pts>
+__device__ __forceinline__ void births_range(const LegArgs<T>& a, const Pts& pts, long long i0, long long i1,
                                              long long stride) {
     for (long long i = i0; i < i1; i += stride) {
         int ix, iy;
         T fx, fy, ox, oy, srem, tau;
-        birth_state<T>(a, pts, (uint32_t)i, &ix, &iy, &fx, &fy, &ox, &oy, &srem, &tau);
+        birth_state<T, Pts>(a, pts, (uint32_t)i, &ix, &iy, &fx, &fy, &ox, &oy, &srem, &tau);
         a.births.cell[i] = iy * a.nx + ix;
         a.births.fx[i] = fx; a.births.fy[i] = fy;
         a.births.ox[i] = ox; a.births.oy[i] = oy;
@@ -591,14 +592,16 @@ __device__ __forceinline__ void births_range(const LegArgs<T>& a, const Points& 
 // births and bank pick-ups, no refill), and the leg then reads them like bank particles.
 template <typename T>
 __global__ void __launch_bounds__(kTile) mc_birth_kernel(LegArgs<T> a) {
-    __shared__ uint32_t sV[6 * kNibbleWords];
+    __shared__ __align__(16) uint32_t sV[kByteDims * kByteWords];   // byte tables, or Halton tables
     __shared__ uint32_t sSh[6];
     const int nt = a.ntab < 6 ? a.ntab : 6;
     const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_LEG_SOURCE);
-    build_point_tables(a.V, nt, sV, a.sampler);
+    const int nbt = a.sampler == HYB_SOBOL_DS && a.bt ? nt : 0;
+    if (nbt) copy_byte_tables(a.bt, nbt, sV);
+    else build_point_tables(a.V, nt, sV, a.sampler);
     if (threadIdx.x < nt) sSh[threadIdx.x] = dshift(key, (uint64_t)threadIdx.x);
     __syncthreads();
-    const Points pts{sV, sSh, key, a.sampler, nt};
+    const PointsB pts{sV, nbt, Points{sV, sSh, key, a.sampler, nt}};
     // the births inside the leg's history range [h0, h1) of [bank slots | births]
     const long long nb = a.st->n_bank;
     const long long i0 = a.h0 > nb ? a.h0 - nb : 0;
@@ -793,6 +796,7 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.ntab = p->ndims < HYB_SOBOL_DIMS ? p->ndims : HYB_SOBOL_DIMS;
     a.w_min = (T)p->d.w_min;
     a.V = p->point_tab;
+    a.bt = p->byte_tab;
     a.seed = p->d.seed;
     a.bank = bank_view<T>(p, cur);
     a.births = birth_view<T>(p);

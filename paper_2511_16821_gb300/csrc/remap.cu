@@ -274,6 +274,12 @@ __host__ __device__ inline double pow2_ceil(double w) {
 // ---------------------------------------------------------------------------------------------
 // remap streaming
 // ---------------------------------------------------------------------------------------------
+// shared-memory words of pass A's point tables (Sobol byte tables for its nbt birth dimensions, or
+// nibble / Halton tables of ntab dimensions), ahead of the ntab digital shifts
+__host__ __device__ __forceinline__ int remap_table_words(int ntab, int nbt) {
+    return nbt ? nbt * kByteWords : ntab * kNibbleWords;
+}
+
 template <typename T>
 struct RemapArgs {
     int nx, ny;
@@ -286,7 +292,8 @@ struct RemapArgs {
     const int* fpos;           // per cell: 1 if all four nodal values of f are >= 0
     long long n_hist, cap;
     const uint32_t* V;
-    int ntab, sampler;
+    const uint32_t* bt;        // Sobol byte tables of the births' dimensions, or null
+    int ntab, nbt, sampler;    // point-table dimensions; of them, dimensions with byte tables
     uint64_t seed;             // keys of the birth and comb point sets come from (seed, step)
     DevState* st;
     long long* blk;            // per block: alive count, sum q, sum|w| lo, sum|w| hi
@@ -342,8 +349,8 @@ enum { kRsSrc = 0, kRsAbs = 1, kRsLeak = 2, kRsKill = 3 };
 // scattering the weight removed along the stream telescopes, sum_s w_s (1 - e_s) = w_0 - w_end, so
 // the absorbed-weight statistic is added once per slot (its fixed-point conversion is ~15 integer
 // instructions on the FP32 path) rather than once per segment.
-template <typename T>
-__device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Points& pts, long long j, long long nb, T wbar,
+template <typename T, typename Pts>
+__device__ Particle<T> remap_slot(const RemapArgs<T>& a, const Pts& pts, long long j, long long nb, T wbar,
                                   RemapSums<T>& sums, int* leaked, int* killed, int* segs, int* err) {
     using P = Prec<T>;
     int ix, iy;
@@ -545,9 +552,9 @@ template <typename T>
 __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) remap_count_kernel(RemapArgs<T> a) {
     pdl_wait();
     pdl_trigger();
-    extern __shared__ uint32_t sm[];
+    extern __shared__ __align__(16) uint32_t sm[];
     uint32_t* sV = sm;
-    uint32_t* sSh = sm + a.ntab * kNibbleWords;
+    uint32_t* sSh = sm + remap_table_words(a.ntab, a.nbt);
     const bool prepass = a.mode == 1;
     // the bank pre-pass runs before the remap density exists: bank slots only (no step-start
     // r_lead slots there), scales from the bank alone
@@ -557,7 +564,8 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) remap_count_ker
     const long long gwarp = (long long)blockIdx.x * (kTile / 32) + wid, nwarps = (long long)gridDim.x * (kTile / 32);
     const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_REMAP_SOURCE);
     if (!prepass) {
-        build_point_tables(a.V, a.ntab, sV, a.sampler);
+        if (a.nbt) copy_byte_tables(a.bt, a.nbt, sV);
+        else build_point_tables(a.V, a.ntab, sV, a.sampler);
         for (int d = threadIdx.x; d < a.ntab; d += blockDim.x) sSh[d] = dshift(key, (uint64_t)d);
     }
     __shared__ RemapScal s_rs;
@@ -565,7 +573,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) remap_count_ker
     __shared__ double s_redd[kTile / 32];
     if (threadIdx.x == 0) s_rs = prepass ? a.st->rsb : a.st->rs;
     __syncthreads();
-    Points pts{sV, sSh, key, a.sampler, a.ntab};
+    const PointsB pts{sV, a.nbt, Points{sV, sSh, key, a.sampler, a.ntab}};
     const bool staged = a.lead_staged != 0 || a.mode == 2;   // slots below nb hold end states already
     const long long N = prepass ? nb : s_rs.N;
     const T wbar_t = (T)s_rs.wbar;
@@ -596,7 +604,7 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 3 : 2) remap_count_ker
                 pr.alive = pr.cell >= 0;
                 pr.w = pr.alive ? a.stg.w[j] : T(0);
             } else {
-                pr = remap_slot<T>(a, pts, j, nb, wbar_t, sums, &leaked, &killed, &segs, &err);
+                pr = remap_slot<T, PointsB>(a, pts, j, nb, wbar_t, sums, &leaked, &killed, &segs, &err);
                 a.stg.cell[j] = pr.alive ? pr.cell : -1;
                 a.stg.fx[j] = pr.fx; a.stg.fy[j] = pr.fy; a.stg.ox[j] = pr.ox; a.stg.oy[j] = pr.oy; a.stg.w[j] = pr.w;
             }
@@ -1089,6 +1097,8 @@ static RemapArgs<T> remap_args(hyb_problem* p) {
     if (a.cap > p->bank_cap) a.cap = p->bank_cap;
     a.V = p->point_tab;
     a.ntab = p->d.sampler != HYB_PRNG ? 5 : 0;
+    a.bt = p->byte_tab;
+    a.nbt = p->d.sampler == HYB_SOBOL_DS && p->byte_tab ? a.ntab : 0;
     a.sampler = p->d.sampler;
     a.seed = p->d.seed;
     a.st = p->st;
@@ -1215,7 +1225,7 @@ static cudaError_t remap_t(hyb_problem* p) {
     a.mode = pre ? 2 : 0;
     const int nblk = (int)((maxN + kSlotsPerBlock - 1) / kSlotsPerBlock);    // pass B blocks
     const int nparts = (int)((maxN + kPartSlots - 1) / kPartSlots);          // census pieces
-    const size_t smem = (size_t)(a.ntab * kNibbleWords + a.ntab + 1) * sizeof(uint32_t);
+    const size_t smem = (size_t)(remap_table_words(a.ntab, a.nbt) + a.ntab + 1) * sizeof(uint32_t);
     int resident = 0;
     e = count_grid<T>(smem, &resident);
     if (e != cudaSuccess) return e;
