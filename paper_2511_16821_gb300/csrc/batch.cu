@@ -307,6 +307,7 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         // a bank pre-pass left pending by a failed single-problem step is ordered and forgotten:
         // the batch re-streams every slot itself
         if (hyb::drop_bank_prepass(p) != cudaSuccess) return bfail(b, HYB_ECUDA, "bank pre-pass");
+        p->births_step = -1;   // the batch draws its members' births into their buffers itself
     }
     return HYB_OK;
 }

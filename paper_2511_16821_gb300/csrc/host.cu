@@ -270,7 +270,7 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
         sn4, sn16, sntx, sntab, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell,
-        sortkey, btab;
+        sortkey, btab, births;
     int64_t cap, nblk, slots;
     int gr, gc;
 };
@@ -342,6 +342,9 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.sortc = d->census_order >= 1 ? 256 * ((nslots + 2047) / 2048 + 1) * 4 : 0;
     z.sortkey = d->census_order == 2 ? nslots * 4 : 0;                   // phase-space keys per slot
     z.btab = d->sampler == HYB_SOBOL_DS ? (size_t)kByteDims * kByteWords * 4 : 0;   // births' Sobol byte tables
+    // staged source births (the legs that keep no census of their own: N_s finite, Eq. (R))
+    z.births = d->n_s != HYB_NS_INF && d->remap_variant == 0
+                   ? bank_cell_bytes(d->n_hist) + 6 * (size_t)d->n_hist * T : 0;
     return z;
 }
 
@@ -352,7 +355,7 @@ size_t layout_bytes(const hyb_problem_desc* d) {
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.sntab, z.snqb, z.d4, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
-                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey, z.btab};
+                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey, z.btab, z.births};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -416,6 +419,8 @@ void assign(hyb_problem* p) {
     p->ns_cell = z.nscell ? (int32_t*)take(z.nscell) : nullptr;
     p->sort_keys = z.sortkey ? (int32_t*)take(z.sortkey) : nullptr;
     p->byte_tab = z.btab ? (uint32_t*)take(z.btab) : nullptr;
+    p->births_buf = z.births ? take(z.births) : nullptr;
+    p->births_step = -1;
     p->bank_cap = z.cap;
     p->stage_slots = z.slots;
     p->nblk_max = z.nblk;
@@ -1043,7 +1048,11 @@ hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
         if (p->d.n_s != HYB_NS_INF) {
             // Eq. (R): the step-start bank's re-stream needs neither the collided flux nor the remap
             // density, so it runs on the side stream beside the solve
-            if (p->d.remap_variant == 0) HYB_CU(p, launch_remap_bank_prepass(p));
+            if (p->d.remap_variant == 0) {
+                HYB_CU(p, launch_remap_bank_prepass(p));
+                // and the next step's source births (they depend on the step index alone)
+                HYB_CU(p, launch_births_ahead(p));
+            }
             s = sn_run(p, &it, true);
             if (s != HYB_OK) return s;
         } else {

@@ -37,14 +37,19 @@ inline BankView<T> stage_view(hyb_problem* p) {
     return b;
 }
 
-// Birth staging inside the remap staging buffer (idle during the leg): cell (int32, n_hist, padded
-// to 256 B), then fx, fy, ox, oy, srem, tau (n_hist each). The staging buffer holds at least
-// 2 n_hist slots of 4 + 5 sizeof(T) bytes, more than this needs.
+// Birth staging (its own buffer, so that the next step's births can be drawn while this step's
+// remap uses the staging buffer): cell (int32, n_hist, padded to 256 B), then fx, fy, ox, oy,
+// srem, tau (n_hist each). cell is null when the problem stages no births.
 template <typename T>
 inline BirthView<T> birth_view(hyb_problem* p) {
     BirthView<T> b;
     const int64_t n = p->d.n_hist;
-    char* base = (char*)p->stage;
+    char* base = (char*)p->births_buf;
+    if (!base) {
+        b.cell = nullptr;
+        b.fx = b.fy = b.ox = b.oy = b.srem = b.tau = nullptr;
+        return b;
+    }
     b.cell = (int32_t*)base;
     T* f = (T*)(base + bank_cell_bytes(n));
     b.fx = f; b.fy = f + n; b.ox = f + 2 * n; b.oy = f + 3 * n; b.srem = f + 4 * n; b.tau = f + 5 * n;

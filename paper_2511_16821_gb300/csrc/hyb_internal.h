@@ -169,6 +169,8 @@ struct hyb_problem {
     void* aa_state;           // Anderson: slots, Gram matrix, mixing weights
     long long* blk;           // remap block partials (4 x nblk)
     int64_t nblk_max;
+    void* births_buf;         // staged source births of one step (BirthView layout), or null
+    long long births_step;    // the step index whose births births_buf holds in full, or -1
     hyb::DevState* st;        // device counters
     hyb::DevState* st_host;   // pinned host mirror
     cudaEvent_t ev0, ev1;
@@ -199,6 +201,9 @@ cudaError_t launch_remap_bank_prepass(hyb_problem* p);
 // order p->stream after a pending bank pre-pass and forget it (the bank, the step or the staging
 // buffer is about to change)
 cudaError_t drop_bank_prepass(hyb_problem* p);
+// the source births of step p->step + 1 into births_buf on p->side, after the work queued there
+// so far (launch_remap_bank_prepass, which records p->ev_join after them)
+cudaError_t launch_births_ahead(hyb_problem* p);
 cudaError_t launch_census(hyb_problem* p);   // N_s = infinity: MC-leg census -> new bank
 size_t sn_accel_state_bytes();                // device bytes of the Anderson state
 size_t sn_norm_bytes(int ncells);            // reduction scratch of the source iteration

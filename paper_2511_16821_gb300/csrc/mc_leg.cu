@@ -46,6 +46,7 @@ struct LegArgs {
     int32_t* hist;
     double sig_s_max, w_src_total, cdt_d;
     long long h0, h1;           // history index range tracked: [h0, h1) of [bank slots | births]
+    long long birth_step;       // step index of the births drawn by mc_birth_kernel (-1: the device's step)
     int seg_limit;              // segments per history before the history ends as an error
 };
 
@@ -595,7 +596,8 @@ __global__ void __launch_bounds__(kTile) mc_birth_kernel(LegArgs<T> a) {
     __shared__ __align__(16) uint32_t sV[kByteDims * kByteWords];   // byte tables, or Halton tables
     __shared__ uint32_t sSh[6];
     const int nt = a.ntab < 6 ? a.ntab : 6;
-    const uint64_t key = dstream_key(a.seed, (uint64_t)a.st->step, HYB_STREAM_LEG_SOURCE);
+    const uint64_t key = dstream_key(a.seed, (uint64_t)(a.birth_step >= 0 ? a.birth_step : a.st->step),
+                                     HYB_STREAM_LEG_SOURCE);
     const int nbt = a.sampler == HYB_SOBOL_DS && a.bt ? nt : 0;
     if (nbt) copy_byte_tables(a.bt, nbt, sV);
     else build_point_tables(a.V, nt, sV, a.sampler);
@@ -800,6 +802,7 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.seed = p->d.seed;
     a.bank = bank_view<T>(p, cur);
     a.births = birth_view<T>(p);
+    a.birth_step = -1;
     a.spread_bank = p->d.census_order >= 1 ? 1 : 0;
     // N_s = infinity and steps 3'/4' keep the leg's census as particles
     a.stage_census = p->d.n_s == HYB_NS_INF || p->d.remap_variant == 1 ? 1 : 0;
@@ -840,9 +843,11 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist, long long h0, long lo
     a.h1 = h1;
     const size_t smem = (size_t)(a.ntab * kNibbleWords + 2 * a.ntab) * sizeof(uint32_t);
     const long long work = (h1 < p->bank_cap + a.n_src ? h1 : p->bank_cap + a.n_src) - h0;
-    if (a.n_src > 0 && a.births.cell) {
+    if (a.n_src > 0 && a.births.cell && p->births_step != p->step) {
+        // births not drawn ahead (beside the previous step's collided solve): draw them now
         const long long g = (a.n_src + kTile - 1) / kTile;
         mc_birth_kernel<T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kTile, 0, p->stream>>>(a);
+        p->births_step = h0 == 0 && h1 == LLONG_MAX ? p->step : -1;   // a range leg draws only its share
     }
     const bool staged = a.births.cell != nullptr;
     cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true>, smem) : allow_smem(mc_leg_kernel<T, false>, smem);
@@ -886,6 +891,35 @@ cudaError_t launch_mc_leg_batch(int prec, const void* d_args, const void* d_chun
         mc_leg_batch_kernel<float><<<grid, block, smem, s>>>((const LegArgs<float>*)d_args,
                                                             (const LegChunk*)d_chunks, nchunks, d_head, V, ntab_max);
     return cudaGetLastError();
+}
+
+// The next step's births on the side stream, one block per SM (the collided solve's kernels keep
+// room beside them), then ev_join again so that the remap (and every later use of the staging
+// side) is ordered after them.
+template <typename T>
+static cudaError_t births_ahead_t(hyb_problem* p) {
+    LegArgs<T> a = leg_args<T>(p, nullptr, p->cur);
+    a.h0 = 0;
+    a.h1 = LLONG_MAX;
+    a.birth_step = p->step + 1;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long g = (a.n_src + kTile - 1) / kTile;
+    mc_birth_kernel<T><<<(unsigned)(g < sms ? g : sms), kTile, 0, p->side>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(p->ev_join, p->side);
+    if (e != cudaSuccess) return e;
+    p->births_step = p->step + 1;
+    return cudaSuccess;
+}
+
+cudaError_t launch_births_ahead(hyb_problem* p) {
+    // only beside a bank pre-pass (the side stream is then ordered after this step's leg, which
+    // read the births buffer, and the remap waits for ev_join)
+    if (!p->bank_prepass || !p->births_buf || !p->has_src || p->d.n_hist <= 0) return cudaSuccess;
+    return p->prec == HYB_FP64 ? births_ahead_t<double>(p) : births_ahead_t<float>(p);
 }
 
 cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev, long long h0, long long h1) {

@@ -1,15 +1,16 @@
-"""The bank pre-pass of the Eq. (R) remap.
+"""The bank pre-pass of the Eq. (R) remap and the births drawn ahead.
 
 hyb_step re-streams the step-start bank's slots on a side stream while the collided solve runs
 (the straight sigma_t-attenuated flight to t_{n+1} needs neither the collided flux nor the remap
-density), and the remap's pass A then streams only the births. The same steps taken through the
-separate calls (mc_leg, collided_solve, remap: every slot streamed by pass A) give the same census
-bit for bit -- cells, positions, directions, weights -- the same fluxes and the same remap
-counters; the remap's weight statistics, summed at the bank's own fixed-point scale for the bank
-slots, agree to rounding. Covered: FP32 and FP64, a comb and a census that fits, a census sorted
-by cell, and a bank pre-pass dropped by set_bank before the remap consumed it.
-"""
-import numpy as np
+density), and the remap's pass A then streams only the births; on the same stream it draws the
+next step's source births (they depend on the step index alone), which the next leg takes. The
+same steps taken through the separate calls (mc_leg, collided_solve, remap: births drawn by the
+leg, every slot streamed by pass A) give the same leg statistics, the same census bit for bit --
+cells, positions, directions, weights -- the same fluxes and the same remap counters; the remap's
+weight statistics, summed at the bank's own fixed-point scale for the bank slots, agree to
+rounding. Covered: FP32 and FP64, a comb and a census that fits, a census sorted by cell, and a
+pre-pass left pending by a failed step, ordered before the next leg.
+"""import numpy as np
 import pytest
 
 from paper_2511_16821_gb300 import workloads as W
@@ -35,7 +36,11 @@ def test_step_with_prepass_equals_separate_calls(prec, cap, order):
     B = hyb.Problem(spec)
     for k in range(4):
         sa = A.step(1)[0]
-        B.mc_leg()
+        lb = B.mc_leg()
+        # from the second step on, A's leg takes births drawn beside the previous solve
+        for key in ("histories", "segments", "collisions", "leaked", "census", "killed", "tally_adds",
+                    "w_source", "w_absorbed", "w_census", "w_handoff"):
+            assert sa[key] == lb[key], (k, key, sa[key], lb[key])
         B.collided_solve()
         rb = B.remap()
         _same_bank(A.bank(), B.bank(), (prec, cap, order, k))
