@@ -10,7 +10,8 @@ cells, positions, directions, weights -- the same fluxes and the same remap coun
 weight statistics, summed at the bank's own fixed-point scale for the bank slots, agree to
 rounding. Covered: FP32 and FP64, a comb and a census that fits, a census sorted by cell, and a
 pre-pass left pending by a failed step, ordered before the next leg.
-"""import numpy as np
+"""
+import numpy as np
 import pytest
 
 from paper_2511_16821_gb300 import workloads as W
