@@ -141,13 +141,14 @@ def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0
 
 def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
     """Kernels of this library launched by one single-problem step (memsets not counted)."""
-    leg = 3                                   # births, leg kernel, normalisation
+    leg = 2                                   # leg kernel, normalisation (births: drawn in the step before)
+    side = 3                                  # beside the collided solve: bank pre-pass scalars, bank re-stream,
+                                              # the next step's births
     sn = 1 + 2 * sn_iters + 1                 # source (with the starting iterate); sweep + reduce per iteration;
                                               # finish (copy, flux)
-    remap = 1 + 3 + 1 + 3 + 1                 # density, CDF (reduce, total, rows with marginal and guides), prep,
-                                              # count/scan/write, finish
-    return leg + sn + remap
-
+    remap = 2 + 3                             # density with the CDF reduction, CDF rows (marginal, guides,
+                                              # scalars); births' pass, scan, write (with the finish)
+    return leg + side + sn + remap
 
 def run_gpu(args, rank: int, world: int) -> dict:
     import torch

@@ -311,7 +311,7 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.cdf_col = (size_t)d->ny * (d->nx + 1) * 8;
     z.rem_f = 4 * nc * 8;
     z.rem_q = nc * 8;
-    z.scratch = (256 + d->ny + nc) * 8;
+    z.scratch = (256 + d->ny + nc + 2 * 256) * 8;   // CDF partials, row totals, cell weights, remap partials
     z.bank = bank_cell_bytes(z.cap) + 5 * (size_t)z.cap * T;
     z.slots = stage_slots(d, z.cap);
     z.stage = bank_cell_bytes(z.slots) + 5 * (size_t)z.slots * T;

@@ -72,8 +72,10 @@ struct DevState {
     int sn_iters;              // collided solve: iterations run in the current solve
     int sn_warm;               // solves finished with warm starts enabled (counted up to 2)
     unsigned int sn_blocks_done;   // source-iteration reduction: blocks finished (last one resets it)
+    unsigned int dens_done;    // remap density + CDF reduction: blocks finished (the last one resets it)
+    unsigned int write_done;   // remap pass B: blocks finished (the last one resets it)
     unsigned int bank_bad;     // particles of a native-layout bank upload outside the problem's domain
-    RemapScal rs;              // scalars of the current remap (remap_prep_kernel)
+    RemapScal rs;              // scalars of the current remap (remap_prep_body)
     RemapScal rsb;             // scalars of the bank pre-pass (remap_bank_prep_kernel)
 };
 

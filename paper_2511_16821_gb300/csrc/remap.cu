@@ -93,8 +93,14 @@ __device__ __forceinline__ long long block_exclusive_scan(long long v, long long
 // one block per row: q_int, the exclusive column scan of the row and the row's column guide; the
 // last block to finish (arrival counter *done, zeroed beforehand) forms the row marginal from the
 // row totals and the row guide, so the whole table is one launch
+// the remap's per-step scalars (the comb's quantisation base, RemapScal); defined below
+__device__ void remap_prep_body(DevState* st, long long n_hist, long long lead, double w_lead);
+
+// prep: the remap's CDF (non-null) -- its last row block also forms the remap's per-step scalars
+// (n_hist, lead, w_lead as for remap_prep_body), so that no launch of its own is needed
 __global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax, int nx, int ny, Cdf2DView C,
-                                long long* row_tot, unsigned* done) {
+                                long long* row_tot, unsigned* done, DevState* prep, long long n_hist,
+                                long long lead, double w_lead) {
     pdl_wait();
     pdl_trigger();
     const int iy = blockIdx.x;
@@ -174,7 +180,10 @@ __global__ void cdf_rows_kernel(const double* __restrict__ w, const double* qmax
         for (int g = threadIdx.x; g <= Gr; g += blockDim.x)
             C.row_g[g] = g == Gr ? ny - 1 : guide_bin(C.row_pre, ny, (uint32_t)((unsigned long long)g << (32 - C.gr)), 0, ny - 1);
     }
-    if (threadIdx.x == 0) *done = 0u;   // ready for the next build
+    if (threadIdx.x == 0) {
+        *done = 0u;   // ready for the next build
+        if (prep) remap_prep_body(prep, n_hist, lead, w_lead);
+    }
 }
 
 // block inclusive scan of a per-thread total (int64, exact); returns the exclusive prefix
@@ -215,7 +224,7 @@ cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView
     e = launch_pdl(pdl, cdf_total_kernel, dim3(1), dim3(32), 0, stream, part, (int)kCdfParts, W_out);
     if (e != cudaSuccess) return e;
     e = launch_pdl(pdl, cdf_rows_kernel, dim3(ny), dim3(256), 0, stream, cell_w, (const double*)qmax_out, nx, ny, cdf,
-                   row_tot, reinterpret_cast<unsigned*>(part));
+                   row_tot, reinterpret_cast<unsigned*>(part), (DevState*)nullptr, 0ll, 0ll, 0.0);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -231,15 +240,31 @@ cudaError_t launch_cdf_build(hyb_problem* p, const double* cell_w, Cdf2DView cdf
 // pre_raw, post_raw: the leg's raw track-length sums (the step-average flux times A dt); the
 // density is formed in separately rounded operations in the order of its definition, so the FP64
 // remap follows the reference arithmetic bit for bit
-__global__ void remap_density_kernel(int ncells, double adt, const double* __restrict__ Q, const double* __restrict__ ss,
-                                     const double* __restrict__ pre_raw, const double* __restrict__ post_raw,
-                                     const double* __restrict__ phi, double* f, float* f32, int* fpos, double* q,
-                                     DevState* st, int relabel, double area, double dt) {
+// The remap density, its cells' weights q and the reduction the CDF build needs, in one launch of
+// kCdfParts blocks: thread (b, t) takes cells b 256 + t + i kCdfParts 256 (cdf_reduce_kernel's
+// partition, so sum |q| comes out in the same order, bit for bit), the blocks leave their
+// partials (sum |q|, max |q|, max weight-factor bound) in scratch, and the last block to arrive
+// forms remap_W, remap_qmax and remap_rmax (cdf_total_kernel's order for the sum) and zeroes the
+// row kernel's arrival counter. The same launch zeroes the census pieces of pass A and, without a
+// bank pre-pass, the remap counters.
+__global__ void remap_density_cdf_kernel(int ncells, double adt, const double* __restrict__ Q,
+                                         const double* __restrict__ ss, const double* __restrict__ pre_raw,
+                                         const double* __restrict__ post_raw, const double* __restrict__ phi,
+                                         double* f, float* f32, int* fpos, double* q, DevState* st, int relabel,
+                                         double area, double dt, double* part, double* part_max, double* part_r,
+                                         long long* blk, long long blk_words, int zero_counters) {
     pdl_wait();
     pdl_trigger();
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    double r = 0;
-    if (k < ncells) {
+    const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+    for (long long i = gt; i < blk_words; i += gs) blk[i] = 0;
+    if (zero_counters) {
+        unsigned long long* rc = reinterpret_cast<unsigned long long*>(&st->r_histories);
+        const long long nw = (long long)(offsetof(DevState, n_bank) - offsetof(DevState, r_histories)) / 8;
+        for (long long i = gt; i < nw; i += gs) rc[i] = 0ull;
+    }
+    double sq = 0, mq = 0, r = 0;
+    for (long long kk = gt; kk < ncells; kk += gs) {
+        const int k = (int)kk;
         const double s = ss[k];
         // Eq. (R): Q + sigma_s (T_pre + T_post) / (A dt) + sigma_s phi_c; Eq. (R'): sigma_s T_post / (A dt)
         // + sigma_s phi_c
@@ -255,11 +280,50 @@ __global__ void remap_density_kernel(int ncells, double adt, const double* __res
         const bool pos = f0 - f1 - f2 + f3 >= 0 && f0 + f1 - f2 - f3 >= 0 && f0 - f1 + f2 - f3 >= 0 &&
                          f0 + f1 + f2 + f3 >= 0;
         fpos[k] = pos ? 1 : 0;
-        if (qc != 0.0) r = pos ? 1.0 : (fabs(f0) + fabs(f1) + fabs(f2) + fabs(f3)) / fabs(f0);
+        if (qc != 0.0) r = fmax(r, pos ? 1.0 : (fabs(f0) + fabs(f1) + fabs(f2) + fabs(f3)) / fabs(f0));
+        const double a = fabs(qc);
+        sq += a;
+        mq = fmax(mq, a);
     }
-    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
-    if ((threadIdx.x & 31) == 0 && r > 0)
-        atomicMax((unsigned long long*)&st->remap_rmax, (unsigned long long)__double_as_longlong(r));
+    sq = warp_sum(sq);
+    for (int o = 16; o > 0; o >>= 1) {
+        mq = fmax(mq, __shfl_down_sync(0xffffffffu, mq, o));
+        r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+    }
+    __shared__ double s_s[32], s_m[32], s_r[32];
+    __shared__ bool s_last;
+    if ((threadIdx.x & 31) == 0) { s_s[threadIdx.x >> 5] = sq; s_m[threadIdx.x >> 5] = mq; s_r[threadIdx.x >> 5] = r; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0, m = 0, rr = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { t += s_s[w]; m = fmax(m, s_m[w]); rr = fmax(rr, s_r[w]); }
+        part[blockIdx.x] = t;
+        part_max[blockIdx.x] = m;
+        part_r[blockIdx.x] = rr;
+        __threadfence();
+        s_last = atomicAdd(&st->dens_done, 1u) == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x >= 32) return;
+    __threadfence();
+    double t = 0, m = 0, rr = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) {
+        t += __ldcg(part + i);
+        m = fmax(m, __ldcg(part_max + i));
+        rr = fmax(rr, __ldcg(part_r + i));
+    }
+    t = warp_sum(t);
+    for (int o = 16; o > 0; o >>= 1) {
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+        rr = fmax(rr, __shfl_down_sync(0xffffffffu, rr, o));
+    }
+    if (threadIdx.x == 0) {
+        st->remap_W = t;
+        st->remap_qmax = m;
+        st->remap_rmax = rr;
+        *reinterpret_cast<unsigned*>(part) = 0u;   // the row kernel's arrival counter
+        st->dens_done = 0u;
+    }
 }
 
 __host__ __device__ inline double pow2_ceil(double w) {
@@ -464,7 +528,8 @@ __device__ __forceinline__ long long quant(T w, double w_ref, float qsc) {
     return quant_w(w, w_ref, qsc);
 }
 
-// The per-step scalars of the remap passes (RemapScal), formed once by remap_prep_kernel.
+// The per-step scalars of the remap passes (RemapScal), formed once per step (remap_prep_body, in
+// the last block of the remap CDF's row kernel).
 __device__ __forceinline__ RemapScal remap_scalars(const DevState* st, long long n_hist) {
     RemapScal r;
     const long long nb = st->n_bank + st->r_lead;
@@ -482,9 +547,7 @@ __device__ __forceinline__ RemapScal remap_scalars(const DevState* st, long long
 }
 
 // one thread: the comb's quantisation base and the remap passes' scalars of this step
-__global__ void remap_prep_kernel(DevState* st, long long n_hist, long long lead, double w_lead) {
-    pdl_wait();
-    pdl_trigger();
+__device__ void remap_prep_body(DevState* st, long long n_hist, long long lead, double w_lead) {
     const double W = st->remap_W;
     const double wbar = W > 0 ? W / (double)n_hist : 0.0;
     st->r_lead = lead;
@@ -1067,14 +1130,20 @@ __global__ void __launch_bounds__(kTile) remap_write_kernel(RemapArgs<T> a) {
     for (int off = 16; off > 0; off >>= 1) wmax = fmax(wmax, __shfl_down_sync(0xffffffffu, wmax, off));
     if (lane == 0 && wmax > T(0))
         atomicMax((unsigned long long*)&a.st->bank_wmax, (unsigned long long)__double_as_longlong((double)wmax));
+    // the last block to finish: the new bank's size, and the census of t_{n+1} makes the next
+    // leg and remap those of step n + 1
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&a.st->write_done, 1u) == gridDim.x - 1u) {
+            __threadfence();
+            a.st->n_bank = a.st->out_count;
+            a.st->step += 1;
+            a.st->write_done = 0u;
+        }
+    }
 }
 
-__global__ void remap_finish_kernel(DevState* st) {
-    pdl_wait();
-    pdl_trigger();
-    st->n_bank = st->out_count;
-    st->step += 1;              // census of t_{n+1}: the next leg belongs to step n + 1
-}
 
 // the arguments of the remap passes (census in slot order, every slot streamed)
 template <typename T>
@@ -1191,32 +1260,30 @@ cudaError_t drop_bank_prepass(hyb_problem* p) {
 template <typename T>
 static cudaError_t remap_t(hyb_problem* p) {
     cudaStream_t s = p->stream;
-    // remap density and its CDF
-    const int g = (p->ncells + 255) / 256;
-    cudaError_t e = cudaMemsetAsync(&p->st->remap_rmax, 0, sizeof(double), s);
-    if (e != cudaSuccess) return e;
     // a bank pre-pass of this step (launch_remap_bank_prepass) zeroed the remap counters and
-    // staged the bank slots' end states; otherwise zero them here (so that no memset separates
-    // the kernels below)
+    // staged the bank slots' end states; otherwise the density launch zeroes them (no memset
+    // separates the programmatically launched kernels below)
     const bool pre = p->bank_prepass;
     p->bank_prepass = false;
-    // pass A adds each round's census partials to its piece
-    e = cudaMemsetAsync(p->blk, 0, 4 * sizeof(long long) * (size_t)((p->stage_slots + kPartSlots - 1) / kPartSlots), s);
-    if (e != cudaSuccess) return e;
-    if (!pre) {
-        e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
-        if (e != cudaSuccess) return e;
-    }
     const bool additive = p->d.remap_variant == 1;
-    remap_density_kernel<<<g, 256, 0, s>>>(p->ncells, p->area * p->d.dt, p->Q_d, p->ss_d, p->pre_raw, p->post_raw,
-                                           p->sn_phi_d, p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st,
-                                           additive ? 0 : 1, p->area, p->d.dt);
-    e = launch_cdf_build(p, p->rem_q, p->rem_cdf, &p->st->remap_W, &p->st->remap_qmax);
+    // the remap density with the CDF's reduction (and the zeroing of pass A's census pieces),
+    // then the CDF rows, whose last block also forms the per-step scalars
+    double* part = p->cell_scratch;
+    long long* row_tot = (long long*)(p->cell_scratch + kCdfParts);
+    double* part_max = p->cell_scratch + kCdfParts + p->ny + p->ncells;
+    const long long blk_words = 4 * ((p->stage_slots + kPartSlots - 1) / kPartSlots);
+    cudaError_t e = launch_pdl(p->pdl, remap_density_cdf_kernel, dim3(kCdfParts), dim3(256), 0, s, p->ncells,
+                               p->area * p->d.dt, (const double*)p->Q_d, (const double*)p->ss_d,
+                               (const double*)p->pre_raw, (const double*)p->post_raw, (const double*)p->sn_phi_d,
+                               p->rem_f, p->rem_f32, p->rem_pos, p->rem_q, p->st, additive ? 0 : 1, p->area,
+                               p->d.dt, part, part_max, part_max + kCdfParts, p->blk, blk_words, pre ? 0 : 1);
     if (e != cudaSuccess) return e;
     // steps 3'/4': the leg's census (bank slots, then its n_hist source births) leads the slots
     const long long lead = additive && p->has_src ? p->d.n_hist : 0;
     const double w_lead = additive && p->has_src ? p->w_src / (double)p->d.n_hist : 0.0;
-    e = launch_pdl(p->pdl, remap_prep_kernel, dim3(1), dim3(1), 0, s, p->st, (long long)p->d.n_hist, lead, w_lead);
+    e = launch_pdl(p->pdl, cdf_rows_kernel, dim3(p->ny), dim3(256), 0, s, (const double*)p->rem_q,
+                   (const double*)&p->st->remap_qmax, p->nx, p->ny, p->rem_cdf, row_tot,
+                   reinterpret_cast<unsigned*>(part), p->st, (long long)p->d.n_hist, lead, w_lead);
     if (e != cudaSuccess) return e;
 
     RemapArgs<T> a = remap_args<T>(p);
@@ -1245,8 +1312,6 @@ static cudaError_t remap_t(hyb_problem* p) {
                    a.sampler, (long long)p->d.n_hist);
     if (e != cudaSuccess) return e;
     e = launch_pdl(p->pdl, remap_write_kernel<T>, dim3(nblk), dim3(kTile), 0, s, a);
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(p->pdl, remap_finish_kernel, dim3(1), dim3(1), 0, s, p->st);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -1307,7 +1372,6 @@ static cudaError_t census_t(hyb_problem* p) {
     remap_partials_kernel<T><<<nparts, kTile, 0, s>>>(a);
     remap_scan_kernel<<<1, 1024, 0, s>>>(p->blk, nparts, p->st, a.cap, a.seed, a.sampler, p->d.n_hist);
     remap_write_kernel<T><<<nblk, kTile, 0, s>>>(a);
-    remap_finish_kernel<<<1, 1, 0, s>>>(p->st);
     return cudaGetLastError();
 }
 
