@@ -112,3 +112,29 @@ def test_pending_prepass_ordered_before_the_next_leg():
         assert np.array_equal(P.tally(t), Q.tally(t)), t
     P.close()
     Q.close()
+
+
+@pytest.mark.parametrize("next_step", [1, 5])
+def test_births_drawn_ahead_only_for_their_step(next_step):
+    """After a step, the births of step 1 lie ready; a leg of step 1 takes them, a leg of any other
+    step (set_step) draws its own: either leg equals a fresh problem's leg of that step."""
+    from paper_2511_16821_gb300 import hyb
+    spec = W.checkerboard(n_s=2, n_hist=40_000, cells_per_block=5).with_(precision=W.FP64, sn_warm_start=1)
+    bank = W.random_bank(spec, 30_000, seed=7)
+    A = hyb.Problem(spec)
+    A.set_bank(bank)
+    A.step(1)
+    A.set_bank(bank)
+    A.set_step(next_step)
+    sa = A.mc_leg()
+    B = hyb.Problem(spec)
+    B.set_bank(bank)
+    B.set_step(next_step)
+    sb = B.mc_leg()
+    for k in ("histories", "segments", "collisions", "leaked", "census", "killed", "tally_adds",
+              "w_source", "w_census", "w_handoff"):
+        assert sa[k] == sb[k], (k, sa[k], sb[k])
+    for t in ("pre_raw", "post_raw", "handoff"):
+        assert np.array_equal(A.tally(t), B.tally(t)), t
+    A.close()
+    B.close()
