@@ -228,6 +228,15 @@ HYB_API hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* stats);
  * EBOUNDS. */
 HYB_API hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step);
 
+/* nsteps full steps as hyb_step, without per-step statistics and without the final
+ * synchronisation: the host waits only inside each source iteration (the stop test), so the call
+ * returns while the last step's remap may still run on the problem's stream, and work the caller
+ * queues after it on that stream (the next bank upload with hyb_set_bank_native, a device copy
+ * with hyb_get_tally) overlaps it. Errors of that remap (device loop bounds, index checks) stay in
+ * the device status word and are returned by the next call that reads it: the next step's stop
+ * test, hyb_step, hyb_mc_leg, hyb_remap_stats. */
+HYB_API hyb_status hyb_step_async(hyb_problem* p, int32_t nsteps);
+
 /* Statistics of the last remap (of hyb_step or hyb_remap): histories (slots streamed: bank +
  * births), segments, leaked, killed, errors, census (particles written), w_source / w_absorbed /
  * w_leaked / w_killed (weight of the slots' start states, removed by sigma_t attenuation, leaving
@@ -239,7 +248,8 @@ HYB_API hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_s
 HYB_API hyb_status hyb_remap_stats(hyb_problem* p, hyb_leg_stats* stats);
 
 /* Copy a tally (see HYB_TALLY_*) into dst (host if dst_on_device == 0, else device), n values.
- * Synchronises the stream. EINVAL if n is not the tally's size. */
+ * A host copy synchronises the stream; a device copy is asynchronous, ordered on the problem's
+ * stream. EINVAL if n is not the tally's size. */
 HYB_API hyb_status hyb_get_tally(hyb_problem* p, int32_t which, double* dst, size_t n, int32_t dst_on_device);
 
 /* Overwrite the collided flux (4 Legendre coefficients per cell, host FP64) -- parity

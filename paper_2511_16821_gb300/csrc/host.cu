@@ -555,6 +555,7 @@ void fill_remap_stats(const hyb_problem* p, hyb_leg_stats* s) {
 hyb_status pull_state(hyb_problem* p) {
     HYB_CU(p, cudaMemcpyAsync(p->st_host, p->st, sizeof(DevState), cudaMemcpyDeviceToHost, p->stream));
     HYB_CU(p, cudaStreamSynchronize(p->stream));
+    p->status_pending = false;   // every error bit set so far is in this read
     if (p->st_host->bank_bad) {   // reported once, by the first check after the upload
         HYB_CU(p, cudaMemsetAsync(&p->st->bank_bad, 0, sizeof(unsigned int), p->stream));
         return fail(p, HYB_EINVAL, "the bank set with hyb_set_bank_native holds particles outside the problem "
@@ -864,6 +865,13 @@ hyb_status hyb_destroy_problem(hyb_problem* p) {
 
 // step 1 launches over the history range [h0, h1) (no host synchronisation); normalise = false
 // leaves the raw integer tallies (a shard of a history-sharded leg)
+// zero the device status word for the call about to run, unless an unchecked asynchronous step
+// may have set error bits there (they stay until a synchronising call reads them)
+static cudaError_t clear_status(hyb_problem* p) {
+    if (p->status_pending) return cudaSuccess;
+    return cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream);
+}
+
 static hyb_status leg_launch(hyb_problem* p, int32_t* hist, long long h0 = 0, long long h1 = LLONG_MAX,
                              bool normalise = true) {
     const size_t nc = (size_t)p->ncells;
@@ -874,7 +882,7 @@ static hyb_status leg_launch(hyb_problem* p, int32_t* hist, long long h0 = 0, lo
     HYB_CU(p, cudaMemsetAsync(p->acc_post, 0, ncp * nc * acc, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, ncp * 4 * nc * acc, p->stream));
     HYB_CU(p, cudaMemsetAsync(p->st, 0, offsetof(DevState, r_histories), p->stream));
-    HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+    HYB_CU(p, clear_status(p));
     HYB_CU(p, launch_mc_leg(p, hist, h0, h1));
     if (normalise) HYB_CU(p, launch_leg_normalise(p));
     p->leg_done = normalise;
@@ -943,7 +951,7 @@ hyb_status hyb_mc_leg_reduce_finish(hyb_problem* p, const void* x_dev, size_t x_
 // iterations reads it after each further one. *iters: iterations taken. keep_status: the status
 // word still holds the leg's bits of this step (checked here together with the sweep's).
 static hyb_status sn_run(hyb_problem* p, int* iters, bool keep_status) {
-    if (!keep_status) HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+    if (!keep_status) HYB_CU(p, clear_status(p));
     HYB_CU(p, sn_start(p));
     const int unchecked = (p->sn_warm && p->last_sn_iters > 0) ? std::min(p->last_sn_iters, p->d.sn_max_iter) : 0;
     // one read-back brings the status word and the stop state together (the span from status to
@@ -956,6 +964,7 @@ static hyb_status sn_run(hyb_problem* p, int* iters, bool keep_status) {
         HYB_CU(p, cudaMemcpyAsync((char*)p->st_host + off, (const char*)p->st + off, len, cudaMemcpyDeviceToHost,
                                   p->stream));
         HYB_CU(p, cudaStreamSynchronize(p->stream));
+        p->status_pending = false;   // the read holds every error bit set so far
         if (p->st_host->sn_conv) break;
     }
     if (p->st_host->status & kStBounds) return fail(p, HYB_EBOUNDS, "device index check failed (bank cell out of range)");
@@ -999,7 +1008,7 @@ hyb_status hyb_collided_solve(hyb_problem* p, hyb_leg_stats* out) {
 // steps 3-4 launches (no host synchronisation); for N_s = infinity the MC-leg census is the new
 // bank (no remap) and the step flux is the MC tally alone
 static hyb_status remap_launch(hyb_problem* p) {
-    HYB_CU(p, cudaMemsetAsync(&p->st->status, 0, sizeof(int), p->stream));
+    HYB_CU(p, clear_status(p));
     if (p->d.n_s == HYB_NS_INF) {
         HYB_CU(p, launch_census(p));
         HYB_CU(p, launch_flux(p));
@@ -1036,32 +1045,41 @@ hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* out) {
 // A whole step synchronises with the host twice: once inside the source iteration (stop test)
 // and, with statistics, once at the end, when the leg and remap counters (kept apart in the
 // device state) are read together. The leg's status bits are checked with the remap's.
+// One step's launches (steps 1-4). The host waits inside the collided solve (stop test) only;
+// with events, the phase boundaries are recorded on the stream.
+static hyb_status step_launch(hyb_problem* p, int* iters, bool events) {
+    if (events) HYB_CU(p, cudaEventRecord(p->evs[0], p->stream));
+    hyb_status s = leg_launch(p, nullptr);
+    if (s != HYB_OK) return s;
+    if (events) HYB_CU(p, cudaEventRecord(p->evs[1], p->stream));
+    *iters = 0;
+    if (p->d.n_s != HYB_NS_INF) {
+        // Eq. (R): the step-start bank's re-stream needs neither the collided flux nor the remap
+        // density, so it runs on the side stream beside the solve
+        if (p->d.remap_variant == 0) {
+            HYB_CU(p, launch_remap_bank_prepass(p));
+            // and the next step's source births (they depend on the step index alone)
+            HYB_CU(p, launch_births_ahead(p));
+        }
+        s = sn_run(p, iters, true);
+        if (s != HYB_OK) return s;
+    } else {
+        p->sn_done = true;
+    }
+    if (events) HYB_CU(p, cudaEventRecord(p->evs[2], p->stream));
+    s = remap_launch(p);
+    if (s != HYB_OK) return s;
+    if (events) HYB_CU(p, cudaEventRecord(p->evs[3], p->stream));
+    return HYB_OK;
+}
+
 hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
     if (!p || nsteps < 0) return fail(p, HYB_EINVAL, "bad arguments");
     p->pdl = true;   // stepped alone (a batch sets its members' launches itself)
     for (int32_t i = 0; i < nsteps; ++i) {
-        HYB_CU(p, cudaEventRecord(p->evs[0], p->stream));
-        hyb_status s = leg_launch(p, nullptr);
-        if (s != HYB_OK) return s;
-        HYB_CU(p, cudaEventRecord(p->evs[1], p->stream));
         int it = 0;
-        if (p->d.n_s != HYB_NS_INF) {
-            // Eq. (R): the step-start bank's re-stream needs neither the collided flux nor the remap
-            // density, so it runs on the side stream beside the solve
-            if (p->d.remap_variant == 0) {
-                HYB_CU(p, launch_remap_bank_prepass(p));
-                // and the next step's source births (they depend on the step index alone)
-                HYB_CU(p, launch_births_ahead(p));
-            }
-            s = sn_run(p, &it, true);
-            if (s != HYB_OK) return s;
-        } else {
-            p->sn_done = true;
-        }
-        HYB_CU(p, cudaEventRecord(p->evs[2], p->stream));
-        s = remap_launch(p);
+        hyb_status s = step_launch(p, &it, true);
         if (s != HYB_OK) return s;
-        HYB_CU(p, cudaEventRecord(p->evs[3], p->stream));
         if (per_step) {
             s = pull_state(p);
             hyb_leg_stats rs;
@@ -1081,6 +1099,18 @@ hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
         }
     }
     if (!per_step) return pull_state(p);
+    return HYB_OK;
+}
+
+hyb_status hyb_step_async(hyb_problem* p, int32_t nsteps) {
+    if (!p || nsteps < 0) return fail(p, HYB_EINVAL, "bad arguments");
+    p->pdl = true;
+    for (int32_t i = 0; i < nsteps; ++i) {
+        int it = 0;
+        hyb_status s = step_launch(p, &it, false);
+        if (s != HYB_OK) return s;
+        p->status_pending = true;   // this step's remap is unchecked
+    }
     return HYB_OK;
 }
 
@@ -1108,7 +1138,7 @@ hyb_status hyb_get_tally(hyb_problem* p, int32_t which, double* dst, size_t n, i
     }
     if (n != need) return fail(p, HYB_EINVAL, "n does not match the tally size");
     HYB_CU(p, cudaMemcpyAsync(dst, src, need * 8, on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream));
-    HYB_CU(p, cudaStreamSynchronize(p->stream));
+    if (!on_dev) HYB_CU(p, cudaStreamSynchronize(p->stream));   // device copies stay ordered on the stream
     return HYB_OK;
 }
 

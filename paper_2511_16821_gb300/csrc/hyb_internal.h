@@ -183,6 +183,8 @@ struct hyb_problem {
     cudaStream_t side;
     cudaEvent_t ev_fork, ev_join;
     bool bank_prepass;        // a pre-pass of this step's bank is in flight or done (not yet consumed)
+    bool status_pending;      // a step launched by hyb_step_async has not been checked: the status word
+                              // keeps its error bits until a synchronising call reads them
 };
 
 namespace hyb {

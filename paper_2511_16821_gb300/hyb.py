@@ -88,6 +88,7 @@ def lib():
         L.hyb_collided_solve.argtypes = [P, C.POINTER(Stats)]
         L.hyb_remap.argtypes = [P, C.POINTER(Stats)]
         L.hyb_step.argtypes = [P, C.c_int32, C.POINTER(Stats)]
+        L.hyb_step_async.argtypes = [P, C.c_int32]
         L.hyb_remap_stats.argtypes = [P, C.POINTER(Stats)]
         L.hyb_get_tally.argtypes = [P, C.c_int32, P, C.c_size_t, C.c_int32]
         L.hyb_set_sn_phi.argtypes = [P, P, C.c_size_t]
@@ -243,6 +244,11 @@ class Problem:
         _check(lib().hyb_remap(self.h, C.byref(s) if stats else None), self.h)
         return s.as_dict() if stats else None
 
+    def step_async(self, n: int = 1) -> None:
+        """n steps without statistics and without the final synchronisation (hyb_step_async): the
+        last remap may still run on the problem's stream when this returns."""
+        _check(lib().hyb_step_async(self.h, n), self.h)
+
     def remap_stats(self) -> dict:
         """Statistics of the last remap (of step or remap)."""
         s = Stats()
@@ -262,7 +268,8 @@ class Problem:
         return out.reshape(self.ncells, 4) if n != self.ncells else out
 
     def tally_to(self, which: str, dst) -> None:
-        """Copy a tally into a device tensor (float64, right size)."""
+        """Copy a tally into a device tensor (float64, right size), asynchronously on the problem's
+        stream."""
         _check(lib().hyb_get_tally(self.h, TALLY[which], C.c_void_p(dst.data_ptr()), dst.numel(), 1), self.h)
 
     def set_sn_phi(self, phi: np.ndarray) -> None:
