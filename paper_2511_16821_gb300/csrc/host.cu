@@ -604,11 +604,98 @@ __global__ void bank_check_kernel(BankView<T> b, long long n, int ncells, T dx, 
     if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&st->bank_bad, bad);
 }
 
+// Bank upload from device memory in three launches: the new size with the statistics zeroed;
+// copy, checks and max |w| in one pass; sum |w| (at the scale its max fixes) with the final
+// conversion in the last block.
+__global__ void bank_begin_kernel(DevState* st, long long n) {
+    st->n_bank = n;
+    st->bank_bad = 0u;
+    st->bank_wmax = 0.0;
+    st->bank_wsum_acc.lo = 0ull;
+    st->bank_wsum_acc.hi = 0ull;
+}
+
+template <typename T>
+__global__ void bank_load_kernel(BankView<T> b, const int32_t* __restrict__ sc, const T* __restrict__ sfx,
+                                 const T* __restrict__ sfy, const T* __restrict__ sox, const T* __restrict__ soy,
+                                 const T* __restrict__ sw, long long n, int ncells, T dx, T dy, DevState* st) {
+    unsigned int bad = 0;
+    double m = 0;
+    const T tx = dx * T(1.000001), ty = dy * T(1.000001), one = T(1.000001);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = sc[i];
+        const T fx = sfx[i], fy = sfy[i], ox = sox[i], oy = soy[i], w = sw[i];
+        b.cell[i] = c; b.fx[i] = fx; b.fy[i] = fy; b.ox[i] = ox; b.oy[i] = oy; b.w[i] = w;
+        const bool ok = c >= 0 && c < ncells && fx >= T(0) && fx <= tx && fy >= T(0) && fy <= ty && isfinite(ox) &&
+                        isfinite(oy) && ox * ox + oy * oy <= one && isfinite(w);
+        bad += ok ? 0u : 1u;
+        m = fmax(m, fabs((double)w));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad) atomicAdd(&st->bank_bad, bad);
+        if (m > 0) atomicMax((unsigned long long*)&st->bank_wmax, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+// sum |w| of the bank (block order, 128-bit fixed point at the scale n max|w| fixes), the last
+// block converting it to bank_wsum
+template <typename T>
+__global__ void bank_wsum_last_kernel(const T* w, DevState* st) {
+    const long long n = st->n_bank;
+    const int kw = scale_exponent((double)n * st->bank_wmax, 125);
+    double s = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        s += fabs((double)w[i]);
+    s = warp_sum(s);
+    __shared__ double sw[32];
+    if ((threadIdx.x & 31) == 0) sw[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += sw[q];
+        unsigned long long lo, hi;
+        to_i128(t * ldexp(1.0, kw), &lo, &hi);
+        atomic_add128(&st->bank_wsum_acc, lo, hi);
+        __threadfence();
+        if (atomicAdd(&st->bank_done, 1u) == gridDim.x - 1u) {
+            __threadfence();
+            const unsigned long long alo = atomicAdd(&st->bank_wsum_acc.lo, 0ull);
+            const unsigned long long ahi = atomicAdd(&st->bank_wsum_acc.hi, 0ull);
+            st->bank_wsum = acc128_to_double(alo, ahi, ldexp(1.0, -kw));
+            st->bank_done = 0u;
+        }
+    }
+}
+
+static bool on_device(const void* ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 // A bank already in the problem's layout and precision (host memory, pinned for an asynchronous
 // copy, or device memory): copied on the problem's stream and checked on the device.
 template <typename T>
 static hyb_status set_bank_native_t(hyb_problem* p, const int32_t* cell, const void* const* f, int64_t n) {
     BankView<T> b = bank_view<T>(p, p->cur);
+    if (n && on_device(cell) && on_device(f[0]) && on_device(f[1]) && on_device(f[2]) && on_device(f[3]) &&
+        on_device(f[4])) {
+        const int g = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+        bank_begin_kernel<<<1, 1, 0, p->stream>>>(p->st, n);
+        bank_load_kernel<T><<<g, 256, 0, p->stream>>>(b, cell, (const T*)f[0], (const T*)f[1], (const T*)f[2],
+                                                      (const T*)f[3], (const T*)f[4], n, p->ncells, (T)p->dx,
+                                                      (T)p->dy, p->st);
+        // the same grid as the statistics kernels of the other uploads (same block sums, same total)
+        const int gs = (int)std::min<long long>((p->bank_cap + kTile - 1) / kTile, 152 * 8);
+        bank_wsum_last_kernel<T><<<gs > 0 ? gs : 1, kTile, 0, p->stream>>>(b.w, p->st);
+        HYB_CU(p, cudaGetLastError());
+        return HYB_OK;
+    }
     HYB_CU(p, cudaMemsetAsync(&p->st->bank_bad, 0, sizeof(unsigned int), p->stream));
     if (n) {
         HYB_CU(p, cudaMemcpyAsync(b.cell, cell, (size_t)n * 4, cudaMemcpyDefault, p->stream));

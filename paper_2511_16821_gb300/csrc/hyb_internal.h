@@ -74,6 +74,7 @@ struct DevState {
     unsigned int sn_blocks_done;   // source-iteration reduction: blocks finished (last one resets it)
     unsigned int dens_done;    // remap density + CDF reduction: blocks finished (the last one resets it)
     unsigned int write_done;   // remap pass B: blocks finished (the last one resets it)
+    unsigned int bank_done;    // bank |w| sum of an upload: blocks finished (the last one resets it)
     unsigned int bank_bad;     // particles of a native-layout bank upload outside the problem's domain
     RemapScal rs;              // scalars of the current remap (remap_prep_body)
     RemapScal rsb;             // scalars of the bank pre-pass (remap_bank_prep_kernel)

@@ -520,11 +520,12 @@ def test_remap_variant_validation(H):
         H.Problem(W.pulse(n_hist=100).with_(remap_variant=2))
 
 
+@pytest.mark.parametrize("where", ["host", "device"])
 @pytest.mark.parametrize("prec", [W.FP32, W.FP64])
-def test_set_bank_native_equals_set_bank(H, prec):
-    """A bank given in the problem's own layout (page-locked host arrays, asynchronous copy) steps
-    exactly like the same bank given through the checked FP64 host path; an invalid particle in a
-    native upload is reported by the next step."""
+def test_set_bank_native_equals_set_bank(H, prec, where):
+    """A bank given in the problem's own layout (page-locked host arrays: asynchronous copies;
+    device arrays: one copy-and-check kernel) steps exactly like the same bank given through the
+    checked FP64 host path; an invalid particle in a native upload is reported by the next step."""
     import torch
     spec = W.checkerboard(n_s=2, n_hist=20_000, cells_per_block=2).with_(precision=prec)
     bank = W.random_bank(spec, 5000, seed=3)
@@ -539,6 +540,8 @@ def test_set_bank_native_equals_set_bank(H, prec):
     B = H.Problem(spec)
     arrs = [torch.from_numpy(bank["cell"].astype(np.int32)).pin_memory()]
     arrs += [torch.from_numpy(bank[k].astype(npdt)).pin_memory() for k in ("fx", "fy", "ox", "oy", "w")]
+    if where == "device":
+        arrs = [a.cuda() for a in arrs]
     assert arrs[1].dtype == fdt
     B.set_bank_native(*arrs)
     B.step(2)
