@@ -965,9 +965,12 @@ static hyb_status leg_launch(hyb_problem* p, int32_t* hist, long long h0 = 0, lo
     const size_t acc = p->prec == HYB_FP64 ? 16 : 8;
     const size_t ncp = (size_t)p->tally_copies;
     HYB_CU(p, drop_bank_prepass(p));   // the leg's births reuse the staging buffer
-    HYB_CU(p, cudaMemsetAsync(p->acc_pre, 0, ncp * nc * acc, p->stream));
-    HYB_CU(p, cudaMemsetAsync(p->acc_post, 0, ncp * nc * acc, p->stream));
-    HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, ncp * 4 * nc * acc, p->stream));
+    if (!p->acc_clean) {   // else the last normalisation zeroed them
+        HYB_CU(p, cudaMemsetAsync(p->acc_pre, 0, ncp * nc * acc, p->stream));
+        HYB_CU(p, cudaMemsetAsync(p->acc_post, 0, ncp * nc * acc, p->stream));
+        HYB_CU(p, cudaMemsetAsync(p->acc_mom, 0, ncp * 4 * nc * acc, p->stream));
+    }
+    p->acc_clean = false;
     HYB_CU(p, cudaMemsetAsync(p->st, 0, offsetof(DevState, r_histories), p->stream));
     HYB_CU(p, clear_status(p));
     HYB_CU(p, launch_mc_leg(p, hist, h0, h1));

@@ -184,6 +184,7 @@ struct hyb_problem {
     cudaStream_t side;
     cudaEvent_t ev_fork, ev_join;
     bool bank_prepass;        // a pre-pass of this step's bank is in flight or done (not yet consumed)
+    bool acc_clean;           // the fixed-point tally copies are zero (the last normalisation cleared them)
     bool status_pending;      // a step launched by hyb_step_async has not been checked: the status word
                               // keeps its error bits until a synchronising call reads them
 };

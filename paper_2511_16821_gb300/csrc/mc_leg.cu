@@ -651,8 +651,8 @@ mc_birth_batch_kernel(const LegArgs<T>* __restrict__ args, const LegChunk* __res
 // post_k) and w_handoff = sum_k sigma_s,k post_k, each cell's product added in 128-bit fixed point
 // (order-free) at the weight statistics' scale.
 template <typename T>
-__global__ void leg_normalise_kernel(const typename Prec<T>::acc_t* pre, const typename Prec<T>::acc_t* post,
-                                     const typename Prec<T>::acc_t* mom, int ncopy, DevState* st, int ncells,
+__global__ void leg_normalise_kernel(typename Prec<T>::acc_t* pre, typename Prec<T>::acc_t* post,
+                                     typename Prec<T>::acc_t* mom, int ncopy, DevState* st, int ncells,
                                      double inv_adt, const double* sa, const double* ss, double* pre_raw,
                                      double* post_raw, double* pre_d, double* post_d, double* mom_d) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -666,6 +666,13 @@ __global__ void leg_normalise_kernel(const typename Prec<T>::acc_t* pre, const t
         pre_d[k] = a * inv_adt;
         post_d[k] = b * inv_adt;
         for (int j = 0; j < 4; ++j) mom_d[4 * k + j] = Prec<T>::sum_to_double(&mom[4 * k + j], n4, ncopy, im);
+        // the fixed-point copies are read: zero them for the next leg (which then needs no memset)
+        const typename Prec<T>::acc_t z{};
+        for (int c = 0; c < ncopy; ++c) {
+            pre[k + c * n1] = z;
+            post[k + c * n1] = z;
+            for (int j = 0; j < 4; ++j) mom[4 * k + j + c * n4] = z;
+        }
         const double scw = ldexp(1.0, st->k_w);
         to_i128(sa[k] * (a + b) * scw, &wa.lo, &wa.hi);
         to_i128(ss[k] * b * scw, &wh.lo, &wh.hi);
@@ -1074,16 +1081,18 @@ cudaError_t launch_leg_normalise(hyb_problem* p) {
     const double inv_adt = 1.0 / (p->area * p->d.dt);
     const int g = (p->ncells + 255) / 256;
     if (p->prec == HYB_FP64)
-        leg_normalise_kernel<double><<<g, 256, 0, p->stream>>>((const Acc128*)p->acc_pre, (const Acc128*)p->acc_post,
-                                                               (const Acc128*)p->acc_mom, p->tally_copies, p->st,
+        leg_normalise_kernel<double><<<g, 256, 0, p->stream>>>((Acc128*)p->acc_pre, (Acc128*)p->acc_post,
+                                                               (Acc128*)p->acc_mom, p->tally_copies, p->st,
                                                                p->ncells, inv_adt, p->sa_d, p->ss_d,
                                                                p->pre_raw, p->post_raw, p->pre_d, p->post_d, p->mom_d);
     else
         leg_normalise_kernel<float><<<g, 256, 0, p->stream>>>(
-            (const unsigned long long*)p->acc_pre, (const unsigned long long*)p->acc_post,
-            (const unsigned long long*)p->acc_mom, p->tally_copies, p->st, p->ncells, inv_adt, p->sa_d, p->ss_d,
+            (unsigned long long*)p->acc_pre, (unsigned long long*)p->acc_post,
+            (unsigned long long*)p->acc_mom, p->tally_copies, p->st, p->ncells, inv_adt, p->sa_d, p->ss_d,
             p->pre_raw, p->post_raw, p->pre_d, p->post_d, p->mom_d);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) p->acc_clean = true;
+    return e;
 }
 
 cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0) {
