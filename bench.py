@@ -197,7 +197,8 @@ def run_gpu(args, rank: int, world: int) -> dict:
 
 def leg_profile(prec: int, reps: int = 5) -> dict:
     """Device time of the MC leg alone (events recorded by the library around the leg kernel and
-    its normalisation, on the problem's stream) at the benchmark workload, with the leg's inputs
+    its normalisation, on the problem's stream; the leg's source births were drawn beside the
+    previous step's collided solve, as in a step) at the benchmark workload, with the leg's inputs
     (the steady-state census bank, step 2) and raw tallies for the error against the oracle."""
     import torch
     from paper_2511_16821_gb300 import hyb
