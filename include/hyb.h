@@ -264,11 +264,13 @@ HYB_API hyb_status hyb_set_bank(hyb_problem* p, const int32_t* cell, const doubl
                         const double* ox, const double* oy, const double* w, int64_t n);
 /* Census bank input in the problem's own layout, for callers that stream banks in every step: cell
  * (n int32) and fx, fy, ox, oy, w (n values each of the problem precision: float for HYB_FP32,
- * double for HYB_FP64), in host memory (page-locked for an asynchronous copy) or device memory.
+ * double for HYB_FP64), in host memory (page-locked for an asynchronous copy) or device memory
+ * (all six device-resident: one kernel copies and checks them, two more form the bank's statistics).
  * Copied asynchronously on the problem's stream; the particles are checked on the device (cell
  * index, in-cell offsets in [0, dx] x [0, dy], |Omega_xy| <= 1, finite weight) and a bank with
- * invalid particles makes the next synchronising call (hyb_step, hyb_mc_leg) return EINVAL.
- * The host arrays must stay valid until the stream has passed the copy. ECAPACITY if n exceeds
+ * invalid particles makes the next fully synchronising call (hyb_step, hyb_mc_leg,
+ * hyb_remap_stats) return EINVAL. The source arrays must stay valid until the stream has passed
+ * the copy. ECAPACITY if n exceeds
  * the bank capacity. */
 HYB_API hyb_status hyb_set_bank_native(hyb_problem* p, const int32_t* cell, const void* fx, const void* fy,
                                        const void* ox, const void* oy, const void* w, int64_t n);
