@@ -63,7 +63,7 @@ class _Problem(C.Structure):
                 ("seed", C.c_uint64), ("sn_order", C.c_int32), ("handoff_full", C.c_int32),
                 ("w_min", C.c_double), ("census_cap", C.c_int64), ("sn_tol", C.c_double),
                 ("sn_max_iter", C.c_int32), ("census_order", C.c_int32), ("remap_variant", C.c_int32),
-                ("n_s_cell", C.POINTER(C.c_int32)), ("elem", C.c_int32), ("pad", C.c_int32)]
+                ("n_s_cell", C.POINTER(C.c_int32)), ("elem", C.c_int32), ("sort_every", C.c_int32)]
 
 
 class _Bank(C.Structure):
@@ -128,7 +128,8 @@ def _problem(spec, elem: int | None = None) -> tuple[_Problem, _Keep]:
                  census_order=getattr(spec, "census_order", 0),
                  remap_variant=getattr(spec, "remap_variant", 0),
                  n_s_cell=None if nsc is None else nsc.ctypes.data_as(C.POINTER(C.c_int32)),
-                 elem=_elem_default if elem is None else elem)
+                 elem=_elem_default if elem is None else elem,
+                 sort_every=getattr(spec, "sort_every", 0))
     return p, _Keep(sa, ss, q, nsc)
 
 

@@ -262,7 +262,7 @@ typedef struct {
     int32_t remap_variant;  // 0: Eq. (R) relabelling remap; 1: steps 3'/4' (additive, previous hybrids)
     const int32_t* n_s_cell;  // nx*ny scatter limits per cell in [0, n_s] (space-dependent N_s), or NULL
     int32_t elem;             // evaluation of sin/cos(2 pi u) and -log u: 0 host libm, 1 explicit series
-    int32_t pad;
+    int32_t sort_every;       // census_order >= 1 applies on the steps n with n mod sort_every == 0 (0, 1: all)
 } or_problem;
 
 typedef struct {
@@ -1232,11 +1232,13 @@ uint32_t phase_key(const Mesh& M, int cell, double fx, double fy, double ox, dou
 
 // The census order of step 4: slot order (0), cell order (1), or cell then in-cell phase-space order
 // (2), each a stable sort, so that the systematic comb along it samples each cell (and, for 2, the
-// position and direction within it) in strata.
-void order_census(const or_problem* P, std::vector<Streamed>& v) {
-    if (P->census_order == 1) {
+// position and direction within it) in strata. With sort_every > 1 the sorted orders apply on every
+// sort_every-th step only (step n with n mod sort_every == 0), slot order on the others.
+void order_census(const or_problem* P, int64_t step, std::vector<Streamed>& v) {
+    const int order = (P->sort_every <= 1 || step % P->sort_every == 0) ? P->census_order : 0;
+    if (order == 1) {
         std::stable_sort(v.begin(), v.end(), [](const Streamed& a, const Streamed& b) { return a.cell < b.cell; });
-    } else if (P->census_order == 2) {
+    } else if (order == 2) {
         Mesh M(P);
         int cb = 0;
         const int b = (int)phase_key_bits((int64_t)M.nx * M.ny, &cb);
@@ -1256,7 +1258,7 @@ void order_census(const or_problem* P, std::vector<Streamed>& v) {
 static int census_from(const or_problem* P, int64_t step, std::vector<Streamed>& surv, double wmax,
                        or_bank* out, int32_t* combed, long double* wc) {
     const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
-    order_census(P, surv);
+    order_census(P, step, surv);
     std::vector<Streamed> fin;
     int did_comb = 0;
     if ((int64_t)surv.size() > cap) {
@@ -1395,7 +1397,7 @@ int or_step(const or_problem* P, int64_t step, const or_bank* bank, or_bank* out
         std::fill(phi, phi + 4 * nc, 0.0);
         std::vector<Streamed> s, fin;
         for (int64_t j = 0; j < tmp.n; ++j) s.push_back(Streamed{true, c[j], a[j], b[j], d[j], e[j], g[j]});
-        order_census(P, s);
+        order_census(P, step, s);
         const int64_t cap = P->census_cap > 0 ? P->census_cap : P->n_hist;
         if ((int64_t)s.size() > cap) {
             double wmax = 0.0;

@@ -288,6 +288,7 @@ static int64_t stage_slots(const hyb_problem_desc* d, int64_t cap) {
 // copies must stay in L2 with the rest of the leg's working set (on the 1024^2 mesh four copies,
 // 192 MB, made the leg 6 % slower than one).
 int tally_copies(const hyb_problem_desc* d) {
+    if (d->tally_copies > 0) return d->tally_copies;
     const size_t acc = d->precision == HYB_FP64 ? 16 : 8;
     const size_t per = 6 * (size_t)d->nx * d->ny * acc;   // pre, post, 4 moments
     int c = 4;
@@ -421,6 +422,7 @@ void assign(hyb_problem* p) {
     p->byte_tab = z.btab ? (uint32_t*)take(z.btab) : nullptr;
     p->births_buf = z.births ? take(z.births) : nullptr;
     p->births_step = -1;
+    p->bank_sorted = p->d.census_order >= 1;   // the transposed pick-up order from the first leg on
     p->bank_cap = z.cap;
     p->stage_slots = z.slots;
     p->nblk_max = z.nblk;
@@ -459,6 +461,8 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->sn_order != 4 && d->sn_order != 8) { *why = "sn_order must be 4 or 8"; return HYB_EINVAL; }
     if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
     if (d->census_order < 0 || d->census_order > 2) { *why = "census_order must be 0, 1 or 2"; return HYB_EINVAL; }
+    if (d->tally_copies < 0 || d->tally_copies > 64) { *why = "tally_copies must be in [0, 64]"; return HYB_EINVAL; }
+    if (d->sort_every < 0) { *why = "sort_every must be >= 0"; return HYB_EINVAL; }
     if (d->sn_accel < 0 || d->sn_accel > 8) { *why = "sn_accel must be in [0, 8]"; return HYB_EINVAL; }
     if (d->sn_warm_start < 0 || d->sn_warm_start > 2) { *why = "sn_warm_start must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->remap_variant != 0 && d->remap_variant != 1) { *why = "remap_variant must be 0 or 1"; return HYB_EINVAL; }

@@ -185,6 +185,8 @@ struct hyb_problem {
     cudaEvent_t ev_fork, ev_join;
     bool bank_prepass;        // a pre-pass of this step's bank is in flight or done (not yet consumed)
     bool acc_clean;           // the fixed-point tally copies are zero (the last normalisation cleared them)
+    bool bank_sorted;         // the current bank is in cell (or phase-space) order: the leg takes it
+                              // in transposed order (lanes in different cells)
     bool status_pending;      // a step launched by hyb_step_async has not been checked: the status word
                               // keeps its error bits until a synchronising call reads them
 };
@@ -193,6 +195,11 @@ namespace hyb {
 
 // launchers (defined in the .cu files)
 // the leg over the history index range [h0, h1) of [bank slots | births] (0, LLONG_MAX: all)
+// census_order >= 1: is the census of the step being remapped sorted (every sort_every-th step)?
+inline bool census_sorted_now(const hyb_problem* p) {
+    return p->d.census_order >= 1 && (p->d.sort_every <= 1 || p->step % p->d.sort_every == 0);
+}
+
 cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev, long long h0, long long h1);
 cudaError_t launch_leg_normalise(hyb_problem* p);
 // the exchange block of a history-sharded leg (int64 words): size, pack after a range leg, and

@@ -810,7 +810,7 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.bank = bank_view<T>(p, cur);
     a.births = birth_view<T>(p);
     a.birth_step = -1;
-    a.spread_bank = p->d.census_order >= 1 ? 1 : 0;
+    a.spread_bank = p->bank_sorted ? 1 : 0;
     // N_s = infinity and steps 3'/4' keep the leg's census as particles
     a.stage_census = p->d.n_s == HYB_NS_INF || p->d.remap_variant == 1 ? 1 : 0;
     a.cens = stage_view<T>(p);

@@ -1175,7 +1175,7 @@ static RemapArgs<T> remap_args(hyb_problem* p) {
     a.stg = stage_view<T>(p);
     a.perm = nullptr;
     a.nslots = p->stage_slots;
-    a.perm_slots = p->d.census_order >= 1 ? 1 : 0;
+    a.perm_slots = census_sorted_now(p) ? 1 : 0;
     a.lead_staged = 0;
     a.mode = 0;
     return a;
@@ -1302,7 +1302,8 @@ static cudaError_t remap_t(hyb_problem* p) {
     }
     e = launch_pdl(p->pdl, remap_count_kernel<T>, dim3(std::min(nparts, resident)), dim3(kTile), smem, s, a);
     if (e != cudaSuccess) return e;
-    if (p->d.census_order >= 1) {
+    p->bank_sorted = census_sorted_now(p);
+    if (p->bank_sorted) {
         // survivors in cell (or phase-space) order, stable: the comb and the census write follow it
         e = sort_census<T>(p, a.stg, maxN, s, &a.perm);
         if (e != cudaSuccess) return e;
@@ -1364,7 +1365,8 @@ static cudaError_t census_t(hyb_problem* p) {
     const int nparts = (int)((maxN + kPartSlots - 1) / kPartSlots);
     cudaError_t e = cudaMemsetAsync(&p->st->r_histories, 0, (char*)&p->st->n_bank - (char*)&p->st->r_histories, s);
     if (e != cudaSuccess) return e;
-    if (p->d.census_order >= 1) {
+    p->bank_sorted = census_sorted_now(p);
+    if (p->bank_sorted) {
         stage_tail_kernel<<<152, 256, 0, s>>>(a.stg.cell, p->st, p->has_src ? p->d.n_hist : 0, maxN);
         e = sort_census<T>(p, a.stg, maxN, s, &a.perm);
         if (e != cudaSuccess) return e;

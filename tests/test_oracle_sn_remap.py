@@ -251,6 +251,25 @@ def test_census_cell_order_is_a_stable_sort(orc):
         assert np.array_equal(b[k], a[k][order]), k
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_census_sort_interval(orc, order):
+    """With sort_every = 3 the sorted order applies on the steps n with n mod 3 == 0 only: the
+    census of step 3 (and 0) equals the sorted one, that of steps 1 and 2 the slot-ordered one."""
+    spec, bank, r, phi = _remap_inputs(orc)
+    spec = spec.with_(census_cap=r["stats"]["census"] // 2 + 1)   # a comb along the census order
+    for step in (0, 1, 2, 3):
+        a, _, _ = orc.remap(spec.with_(census_order=order, sort_every=3), step, bank, r["pre"], r["post"], phi)
+        want = order if step % 3 == 0 else 0
+        b, _, _ = orc.remap(spec.with_(census_order=want), step, bank, r["pre"], r["post"], phi)
+        assert a["n"] == b["n"], step
+        for k in ("cell", "fx", "fy", "ox", "oy", "w"):
+            assert np.array_equal(a[k], b[k]), (step, k)
+    # and sorting on every step differs from never sorting, so the check above can fail
+    c, _, _ = orc.remap(spec.with_(census_order=order), 1, bank, r["pre"], r["post"], phi)
+    d, _, _ = orc.remap(spec.with_(census_order=0), 1, bank, r["pre"], r["post"], phi)
+    assert not np.array_equal(c["cell"], d["cell"])
+
+
 def test_cell_ordered_comb_keeps_each_cell_within_one_copy(orc):
     """A systematic comb along the cell-ordered census gives every cell the number of copies its
     quantised weight asks for, rounded up or down: its census weight is within one copy weight
