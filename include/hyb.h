@@ -130,16 +130,18 @@ typedef struct {
     int32_t seg_limit;        /* bound on segments per history (a guard on every device loop): a
                                  history that reaches it ends as an error and the leg returns
                                  HYB_ETIMEOUT; 0 = 2^20; at most 2^30 */
-    int32_t wait_limit;       /* polls (20 ns sleeps apart) of one wait of the collided solve's
-                                 strip pipeline before it gives up and the solve returns
-                                 HYB_ETIMEOUT; 0 = 2^22 (about 0.1 s per wait) */
+    int32_t wait_limit;       /* polls (20 ns sleeps apart) of one device wait -- the collided
+                                 solve's strip pipeline, the census sort's look-back -- before it
+                                 gives up and the call returns HYB_ETIMEOUT; 0 = 2^22 (about
+                                 0.1 s per wait) */
     int32_t tally_copies;     /* copies of the fixed-point tally arrays the leg's warps add into
                                  (warp index mod copies; the normalisation sums them exactly, so
                                  the tallies do not depend on it): 0 automatic (4 while they take
                                  at most 32 MB, fewer above), else 1..64 */
     int32_t sort_every;       /* with census_order >= 1: sort the census on the steps n with
                                  n mod sort_every == 0 only (0 or 1: every step); the other steps
-                                 comb the census in slot order */
+                                 comb the census in slot order. A batch rejects sort_every > 1
+                                 (its step graphs replay one sort decision) */
     int32_t pad3;
 } hyb_problem_desc;
 

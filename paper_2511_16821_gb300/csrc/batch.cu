@@ -264,6 +264,9 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         if (p->d.n_s == HYB_NS_INF) return bfail(b, HYB_EINVAL, "N_s = infinity problems are stepped alone");
         if (p->d.sampler == HYB_HALTON) return bfail(b, HYB_EINVAL, "Halton problems are stepped alone");
         if (p->d.remap_variant != 0) return bfail(b, HYB_EINVAL, "the additive remap variant is stepped alone");
+        // a step graph replays one sort decision: a census sorted on some steps only is stepped alone
+        if (p->d.census_order >= 1 && p->d.sort_every > 1)
+            return bfail(b, HYB_EINVAL, "a census sort interval (sort_every > 1) is stepped alone");
         probs.push_back(p);
     }
     if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");

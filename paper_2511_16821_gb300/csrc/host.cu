@@ -340,7 +340,9 @@ Sizes sizes(const hyb_problem_desc* d) {
     z.rempos = nc * 4;
     const size_t nslots = (size_t)z.slots;
     z.sortkv = d->census_order >= 1 ? nslots * 8 : 0;                    // x2: (key, slot) pairs, ping-pong
-    z.sortc = d->census_order >= 1 ? 256 * ((nslots + 2047) / 2048 + 1) * 4 : 0;
+    z.sortc = d->census_order >= 1
+                  ? census_sort_scratch_bytes((long long)nslots, census_sort_sentinel(d->census_order, d->nx * d->ny))
+                  : 0;
     z.sortkey = d->census_order == 2 ? nslots * 4 : 0;                   // phase-space keys per slot
     z.btab = d->sampler == HYB_SOBOL_DS ? (size_t)kByteDims * kByteWords * 4 : 0;   // births' Sobol byte tables
     // staged source births (the legs that keep no census of their own: N_s finite, Eq. (R))
@@ -413,7 +415,7 @@ void assign(hyb_problem* p) {
     p->rem_f32 = (float*)take(z.remf32);
     p->rem_pos = (int*)take(z.rempos);
     for (int i = 0; i < 2; ++i) p->sort_pairs[i] = z.sortkv ? (unsigned long long*)take(z.sortkv) : nullptr;
-    p->sort_counts = z.sortc ? (uint32_t*)take(z.sortc) : nullptr;
+    p->sort_scratch = z.sortc ? take(z.sortc) : nullptr;
     p->sig_inv = (float*)take(z.siginv);
     p->aa_hist = z.aah ? take(z.aah) : nullptr;
     p->aa_state = z.aas ? take(z.aas) : nullptr;
@@ -566,7 +568,8 @@ hyb_status pull_state(hyb_problem* p) {
                                    "(cell index, in-cell offset, direction or weight)");
     }
     if (p->st_host->status & kStBounds) return fail(p, HYB_EBOUNDS, "device index check failed (bank cell out of range)");
-    if (p->st_host->status & kStSegments) return fail(p, HYB_ETIMEOUT, "a history exceeded the segment bound");
+    if (p->st_host->status & kStSegments)
+        return fail(p, HYB_ETIMEOUT, "a device loop bound was exhausted (history segments, sweep or census-sort wait)");
     return HYB_OK;
 }
 

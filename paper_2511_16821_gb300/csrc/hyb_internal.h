@@ -145,7 +145,7 @@ struct hyb_problem {
     double* rem_f;            // 4 x ncells remap density coefficients
     float* rem_f32;           // the same in FP32 (FP32 path)
     unsigned long long* sort_pairs[2];   // census sort (census_order 1): ping-pong (cell, slot) pairs
-    uint32_t* sort_counts;               //   and the per-tile digit counts; null for slot order
+    void* sort_scratch;                  //   digit counts, tile counters and look-back records; null for slot order
     int* rem_pos;             // ncells: 1 where the bilinear remap density is non-negative
     double* rem_q;            // ncells signed remap cell weights q = f0 A dt
     double* cell_scratch;     // per-row partials for the CDF build
@@ -233,8 +233,16 @@ cudaError_t launch_flux(hyb_problem* p);
 cudaError_t launch_cdf_build_raw(const double* cell_w, int nx, int ny, Cdf2DView cdf, double* W_out,
                                  double* qmax_out, double* scratch, cudaStream_t stream, bool pdl = false);
 cudaError_t launch_init_bank(hyb_problem* p, const Cdf2DView& cdf, double w0);
-cudaError_t launch_census_sort(const int32_t* cells, long long n, uint32_t ncells, unsigned long long* const pairs[2],
-                               uint32_t* counts, cudaStream_t s, const unsigned long long** sorted);
+// census sort: the scratch holds the digit counts and tile counters (kSortScratchHead bytes), then
+// one record per (tile, digit)
+constexpr size_t kSortScratchHead = 8192;
+size_t census_sort_scratch_bytes(long long n, uint32_t sentinel);
+cudaError_t launch_census_sort(const int32_t* keys, long long n, uint32_t sentinel, unsigned long long* const pairs[2],
+                               void* scratch, int wait_limit, int* status, cudaStream_t s,
+                               const unsigned long long** sorted);
+// the sort key's sentinel (above every key): the cell count (census_order 1), or 2^(cell bits + 3 b)
+// for the phase-space key of b bits per coordinate (census_order 2)
+uint32_t census_sort_sentinel(int census_order, int ncells);
 cudaError_t launch_bank_stats(hyb_problem* p);
 cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,
                           uint32_t* out, cudaStream_t s);

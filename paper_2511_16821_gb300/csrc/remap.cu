@@ -810,6 +810,15 @@ int phase_key_bits(int ncells, int* cell_bits) {
     return b < 0 ? 0 : (b > 5 ? 5 : b);
 }
 
+// keys below 2^(cell bits + 3b) <= 2^31 (phase space) or below the cell count: that bound is the
+// sentinel of dead slots
+uint32_t census_sort_sentinel(int census_order, int ncells) {
+    if (census_order != 2) return (uint32_t)ncells;
+    int cb = 0;
+    const int b = phase_key_bits(ncells, &cb);
+    return (uint32_t)1u << (cb + 3 * b);
+}
+
 template <typename T>
 __device__ __forceinline__ uint32_t phase_quant(T v, T s) {
     T t = floor(v * s);
@@ -839,6 +848,9 @@ __global__ void phase_key_kernel(BankView<T> stg, long long nslots, T dx, T dy, 
 
 // The sort of the census (cell order, or phase-space order with its keys formed first) over the n
 // staging slots; *perm: the sorted (key << 32 | slot) pairs.
+// polls of one look-back wait of the census sort (the problem's device wait bound)
+static int sort_wait_limit(const hyb_problem* p) { return p->d.wait_limit > 0 ? p->d.wait_limit : (1 << 22); }
+
 template <typename T>
 static cudaError_t sort_census(hyb_problem* p, const BankView<T>& stg, long long n, cudaStream_t s,
                                const unsigned long long** perm) {
@@ -851,10 +863,10 @@ static cudaError_t sort_census(hyb_problem* p, const BankView<T>& stg, long long
                                                                                  p->sort_keys);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        // keys below 2^(cell bits + 3b) <= 2^31; that value is the sentinel of dead slots
-        return launch_census_sort(p->sort_keys, n, (uint32_t)1u << (cb + 3 * b), pairs, p->sort_counts, s, perm);
     }
-    return launch_census_sort(stg.cell, n, (uint32_t)p->ncells, pairs, p->sort_counts, s, perm);
+    return launch_census_sort(p->d.census_order == 2 ? p->sort_keys : stg.cell, n,
+                              census_sort_sentinel(p->d.census_order, p->ncells), pairs, p->sort_scratch,
+                              sort_wait_limit(p), &p->st->status, s, perm);
 }
 
 // One block: exclusive scan of the pieces' alive counts and quantised sums in place (tiles of

@@ -57,7 +57,7 @@ class ProblemSpec:
     n_s_cell: np.ndarray | None = None   # per-cell scatter limits in [0, n_s] (space-dependent N_s)
     sn_layout: int = 0              # sweep memory layout: 0 automatic, 1 padded mesh, 2 wavefront order
     seg_limit: int = 0              # segments per history before HYB_ETIMEOUT (0: the default 2^20)
-    wait_limit: int = 0             # polls of a collided-solve pipeline wait before HYB_ETIMEOUT (0: 2^22)
+    wait_limit: int = 0             # polls of a device wait (solve pipeline, sort look-back) before HYB_ETIMEOUT (0: 2^22)
     tally_copies: int = 0           # copies of the fixed-point tally arrays (0: automatic)
     sort_every: int = 0             # census_order >= 1: sort on the steps n with n mod sort_every == 0 (0, 1: all)
     name: str = field(default="problem")
