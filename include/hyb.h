@@ -157,7 +157,8 @@ typedef struct {
     int64_t tally_adds;       /* MC leg: fixed-point tally additions issued (global 64-bit atomics;
                                  the FP64 path adds up to two words per contribution) */
     float ms_leg, ms_sn, ms_remap;   /* hyb_step: device time of steps 1, 2 and 3-4 */
-    int32_t pad1;
+    float ms_leg_kernel;      /* hyb_step, hyb_mc_leg: device time of the MC leg kernel alone
+                                 (events around its launch), 0 if not measured */
 } hyb_leg_stats;
 
 typedef struct hyb_problem hyb_problem;

@@ -836,6 +836,8 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
         return bail(fail(p, HYB_ECUDA, "event create"));
     for (auto& e : p->evs)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(p, HYB_ECUDA, "event create"));
+    for (auto& e : p->evk)
+        if (cudaEventCreate(&e) != cudaSuccess) return bail(fail(p, HYB_ECUDA, "event create"));
     if (cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
@@ -953,6 +955,8 @@ hyb_status hyb_destroy_problem(hyb_problem* p) {
     if (p->ev1) cudaEventDestroy(p->ev1);
     for (auto e : p->evs)
         if (e) cudaEventDestroy(e);
+    for (auto e : p->evk)
+        if (e) cudaEventDestroy(e);
     delete p;
     return HYB_OK;
 }
@@ -987,6 +991,16 @@ static hyb_status leg_launch(hyb_problem* p, int32_t* hist, long long h0 = 0, lo
     return HYB_OK;
 }
 
+// device time of the last MC leg kernel (events around its launch; the stream has been synchronised)
+static float leg_kernel_ms(hyb_problem* p) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p->evk[0], p->evk[1]) != cudaSuccess) {
+        cudaGetLastError();   // events not recorded yet: report 0
+        return 0.f;
+    }
+    return ms;
+}
+
 static hyb_status leg_impl(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) {
     if (!p) return fail(nullptr, HYB_EINVAL, "null problem");
     HYB_CU(p, cudaEventRecord(p->ev0, p->stream));
@@ -999,6 +1013,7 @@ static hyb_status leg_impl(hyb_problem* p, int32_t* hist, hyb_leg_stats* out) {
         float ms = 0;
         cudaEventElapsedTime(&ms, p->ev0, p->ev1);
         out->ms = ms;
+        out->ms_leg_kernel = leg_kernel_ms(p);
         if (s != HYB_OK) return s;
     }
     return HYB_OK;
@@ -1192,6 +1207,7 @@ hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step) {
             per_step[i].ms = m0 + m1 + m2;
             per_step[i].pad = 0;
             per_step[i].ms_leg = m0; per_step[i].ms_sn = m1; per_step[i].ms_remap = m2;
+            per_step[i].ms_leg_kernel = leg_kernel_ms(p);
             if (s != HYB_OK) return s;
         }
     }

@@ -178,6 +178,7 @@ struct hyb_problem {
     hyb::DevState* st_host;   // pinned host mirror
     cudaEvent_t ev0, ev1;
     cudaEvent_t evs[4];       // hyb_step phase boundaries: leg start, solve start, remap start, end
+    cudaEvent_t evk[2];       // around the MC leg kernel alone (recorded at its launch)
     // bank pre-pass of the remap (Eq. (R) remaps stepped by hyb_step): the step-start bank slots are
     // re-streamed on `side` while the collided solve runs on `stream` (its sweeps leave most SMs
     // idle); ev_fork orders it after the leg, ev_join orders the remap's pass A after it

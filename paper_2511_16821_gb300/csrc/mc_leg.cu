@@ -859,9 +859,13 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist, long long h0, long lo
     const bool staged = a.births.cell != nullptr;
     cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true>, smem) : allow_smem(mc_leg_kernel<T, false>, smem);
     if (e != cudaSuccess) return e;
+    e = cudaEventRecord(p->evk[0], p->stream);
+    if (e != cudaSuccess) return e;
     if (staged) mc_leg_kernel<T, true><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
     else mc_leg_kernel<T, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaEventRecord(p->evk[1], p->stream);
 }
 
 size_t leg_args_bytes(int prec) { return prec == HYB_FP64 ? sizeof(LegArgs<double>) : sizeof(LegArgs<float>); }

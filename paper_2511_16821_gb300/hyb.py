@@ -50,7 +50,7 @@ class Stats(C.Structure):
                                           "w_handoff", "w_killed")] + \
                [("sn_iterations", C.c_int32), ("combed", C.c_int32), ("bank_size", C.c_int64),
                 ("ms", C.c_float), ("pad", C.c_int32), ("tally_adds", C.c_int64),
-                ("ms_leg", C.c_float), ("ms_sn", C.c_float), ("ms_remap", C.c_float), ("pad1", C.c_int32)]
+                ("ms_leg", C.c_float), ("ms_sn", C.c_float), ("ms_remap", C.c_float), ("ms_leg_kernel", C.c_float)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("pad", "pad1")}
