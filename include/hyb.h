@@ -142,7 +142,14 @@ typedef struct {
                                  n mod sort_every == 0 only (0 or 1: every step); the other steps
                                  comb the census in slot order. A batch rejects sort_every > 1
                                  (its step graphs replay one sort decision) */
-    int32_t pad3;
+    int32_t leg_sort_every;   /* 0: the fused MC leg (each warp lane takes a history to its end,
+                                 then the next one). K >= 1: the phased leg -- every history
+                                 advances at most K segments per phase, and between phases the
+                                 live histories are compacted and sorted by cell (stable), so
+                                 the lanes of a warp track histories in nearby cells. Results are
+                                 the fused leg's bit for bit; the host waits once per phase. A
+                                 leg over a history range (hyb_mc_leg_range) stays fused; a
+                                 batch rejects K >= 1 */
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */

@@ -9,17 +9,19 @@ per problem).
 
 tune_problem times one problem's creation-time knobs: the copies of the fixed-point tally arrays
 (the privatisation of the leg's atomic adds: more copies spread the adds to hot cells, fewer keep
-the copies in L2) and the census sort interval (with census_order >= 1, the census is sorted and
-combed in cell order on every sort_every-th step only). The copies never change a result; the sort
-interval does (an unsorted comb samples each cell's weight less evenly), so it is searched only
-when the space names it, and the caller accepts the variance that comes with a longer interval.
+the copies in L2), the leg's sort interval (leg_sort_every = K: 0 runs the fused leg, K >= 1 the
+phased leg, whose live histories are sorted by cell every K segments) and the census sort interval
+(with census_order >= 1, the census is sorted and combed in cell order on every sort_every-th step
+only). The copies and the leg's sort interval never change a result; the census sort interval
+does (an unsorted comb samples each cell's weight less evenly), so it is searched only when the
+space names it, and the caller accepts the variance that comes with a longer interval.
 """
 from __future__ import annotations
 
 import itertools
 
 DEFAULT_SPACE = {"block": (128, 256), "chunk": (1024, 4096, 16384), "ctas_per_sm": (0,), "streams": (8, 32)}
-PROBLEM_SPACE = {"tally_copies": (1, 2, 4, 8)}
+PROBLEM_SPACE = {"tally_copies": (1, 2, 4, 8), "leg_sort_every": (0, 4, 16)}
 L2_FLUSH_BYTES = 256 << 20
 
 

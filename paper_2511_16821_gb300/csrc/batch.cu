@@ -267,6 +267,7 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
         // a step graph replays one sort decision: a census sorted on some steps only is stepped alone
         if (p->d.census_order >= 1 && p->d.sort_every > 1)
             return bfail(b, HYB_EINVAL, "a census sort interval (sort_every > 1) is stepped alone");
+        if (p->d.leg_sort_every > 0) return bfail(b, HYB_EINVAL, "the phased leg (leg_sort_every > 0) is stepped alone");
         probs.push_back(p);
     }
     if (!b->probs.empty() && prec != b->prec) return bfail(b, HYB_EINVAL, "a batch keeps one precision");

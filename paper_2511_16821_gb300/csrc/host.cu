@@ -270,8 +270,8 @@ int64_t eff_cap(const hyb_problem_desc* d) {
 struct Sizes {
     size_t st, sobol, sig, sa, ss, Q, cdf_q, cdf_row, cdf_col, rem_f, rem_q, scratch, bank, stage, acc1, acc4, d1, d4,
         sn4, sn16, sntx, sntab, snqb, snnorm, blk, grow, gcol, remf32, rempos, sortkv, sortc, siginv, aah, aas, nscell,
-        sortkey, btab, births;
-    int64_t cap, nblk, slots;
+        sortkey, btab, births, live, livekv, livesc;
+    int64_t cap, nblk, slots, live_cap;
     int gr, gc;
 };
 
@@ -348,6 +348,11 @@ Sizes sizes(const hyb_problem_desc* d) {
     // staged source births (the legs that keep no census of their own: N_s finite, Eq. (R))
     z.births = d->n_s != HYB_NS_INF && d->remap_variant == 0
                    ? bank_cell_bytes(d->n_hist) + 6 * (size_t)d->n_hist * T : 0;
+    // phased leg: two buffers of saved histories (bank capacity + births), their sort by cell
+    z.live_cap = z.cap + d->n_hist;
+    z.live = d->leg_sort_every > 0 ? live_buf_bytes(z.live_cap, d->precision) : 0;
+    z.livekv = d->leg_sort_every > 0 ? (size_t)z.live_cap * 8 : 0;
+    z.livesc = d->leg_sort_every > 0 ? census_sort_scratch_bytes(z.live_cap, (uint32_t)(d->nx * d->ny)) : 0;
     return z;
 }
 
@@ -358,7 +363,8 @@ size_t layout_bytes(const hyb_problem_desc* d) {
                             z.cdf_col, z.rem_f, z.rem_q, z.scratch, z.bank, z.bank, z.stage, z.acc1, z.acc1, z.acc4, z.d1,
                             z.d1, z.d4, z.d1, z.d1, z.d1, z.sn4, z.sn4, z.sn16, z.sntx, z.sntab, z.snqb, z.d4, z.d4,
                             z.snnorm, z.blk, z.grow, z.gcol, z.grow, z.gcol, z.remf32, z.rempos, z.sortkv,
-                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey, z.btab, z.births};
+                            z.sortkv, z.sortc, z.siginv, z.aah, z.aas, z.nscell, z.sortkey, z.btab, z.births, z.live,
+                            z.live, z.livekv, z.livekv, z.livesc};
     for (size_t b : parts) L.add(b);
     return L.total;
 }
@@ -423,6 +429,10 @@ void assign(hyb_problem* p) {
     p->sort_keys = z.sortkey ? (int32_t*)take(z.sortkey) : nullptr;
     p->byte_tab = z.btab ? (uint32_t*)take(z.btab) : nullptr;
     p->births_buf = z.births ? take(z.births) : nullptr;
+    for (int i = 0; i < 2; ++i) p->live_buf[i] = z.live ? take(z.live) : nullptr;
+    for (int i = 0; i < 2; ++i) p->live_pairs[i] = z.livekv ? (unsigned long long*)take(z.livekv) : nullptr;
+    p->live_scratch = z.livesc ? take(z.livesc) : nullptr;
+    p->live_cap = z.live_cap;
     p->births_step = -1;
     p->bank_sorted = p->d.census_order >= 1;   // the transposed pick-up order from the first leg on
     p->bank_cap = z.cap;
@@ -465,6 +475,11 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->census_order < 0 || d->census_order > 2) { *why = "census_order must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->tally_copies < 0 || d->tally_copies > 64) { *why = "tally_copies must be in [0, 64]"; return HYB_EINVAL; }
     if (d->sort_every < 0) { *why = "sort_every must be >= 0"; return HYB_EINVAL; }
+    if (d->leg_sort_every < 0) { *why = "leg_sort_every must be >= 0"; return HYB_EINVAL; }
+    if (d->leg_sort_every > 0 && eff_cap(d) + d->n_hist >= ((int64_t)1 << 31)) {
+        *why = "the phased leg holds fewer than 2^31 histories (bank capacity + births)";   // 31-bit saved indices
+        return HYB_EINVAL;
+    }
     if (d->sn_accel < 0 || d->sn_accel > 8) { *why = "sn_accel must be in [0, 8]"; return HYB_EINVAL; }
     if (d->sn_warm_start < 0 || d->sn_warm_start > 2) { *why = "sn_warm_start must be 0, 1 or 2"; return HYB_EINVAL; }
     if (d->remap_variant != 0 && d->remap_variant != 1) { *why = "remap_variant must be 0 or 1"; return HYB_EINVAL; }

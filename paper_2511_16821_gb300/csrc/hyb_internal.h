@@ -39,6 +39,8 @@ struct DevState {
     unsigned long long histories, segments, collisions, leaked, census, killed, reached, errors;
     unsigned long long tally_adds;   // fixed-point tally additions (global atomics) issued
     unsigned long long leg_next;     // next history index handed to a warp (single-problem leg)
+    unsigned long long live_count;   // phased leg: histories saved by the phase (alive after it)
+    unsigned long long live_in;      // phased leg: histories the phase takes up
     Acc128 w_source, w_absorbed, w_leaked, w_census, w_handoff, w_killed;
     // counters of the last remap
     unsigned long long r_histories, r_segments, r_leaked, r_killed, r_errors, r_alive;
@@ -146,6 +148,10 @@ struct hyb_problem {
     float* rem_f32;           // the same in FP32 (FP32 path)
     unsigned long long* sort_pairs[2];   // census sort (census_order 1): ping-pong (cell, slot) pairs
     void* sort_scratch;                  //   digit counts, tile counters and look-back records; null for slot order
+    void* live_buf[2];                   // phased leg (leg_sort_every >= 1): saved histories, ping-pong
+    unsigned long long* live_pairs[2];   //   their (cell, index) pairs for the sort by cell
+    void* live_scratch;                  //   and the sort's scratch; all null for the fused leg
+    long long live_cap;                  //   histories a leg can hold (bank capacity + births)
     int* rem_pos;             // ncells: 1 where the bilinear remap density is non-negative
     double* rem_q;            // ncells signed remap cell weights q = f0 A dt
     double* cell_scratch;     // per-row partials for the CDF build
@@ -244,6 +250,7 @@ cudaError_t launch_census_sort(const int32_t* keys, long long n, uint32_t sentin
 // the sort key's sentinel (above every key): the cell count (census_order 1), or 2^(cell bits + 3 b)
 // for the phase-space key of b bits per coordinate (census_order 2)
 uint32_t census_sort_sentinel(int census_order, int ncells);
+size_t live_buf_bytes(long long cap, int prec);   // one live-state buffer of the phased leg
 cudaError_t launch_bank_stats(hyb_problem* p);
 cudaError_t launch_points(uint64_t key, int sampler, const uint32_t* V, int64_t i0, int64_t n, int ndims,
                           uint32_t* out, cudaStream_t s);

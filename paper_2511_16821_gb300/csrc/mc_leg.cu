@@ -60,6 +60,27 @@ struct Hist {
     bool census_stream;
 };
 
+// The phased leg (leg_sort_every = K >= 1): every history advances at most K segments per phase;
+// the histories still alive at the end of a phase are saved here (compacted), sorted by cell, and
+// taken up again by the next phase. A saved history is exactly its lane state (a scatter's new
+// direction and optical depth already drawn), so the phases do the fused leg's arithmetic.
+template <typename T>
+struct LiveView {
+    uint32_t* id;               // point index, census stream in bit 31
+    int32_t* cell;
+    T *fx, *fy, *ox, *oy, *w, *w0, *srem, *tau;
+    int32_t *n, *seg;
+};
+
+template <typename T>
+struct PhaseArgs {
+    LiveView<T> in, out;                  // in: the phase's histories (later phases); out: those alive after it
+    unsigned long long* out_count;        // histories saved to `out`
+    const unsigned long long* in_count;   // histories in `in`
+    int first;                            // 1: the histories start from the bank and the births
+    int budget;                           // segments per history per phase (K)
+};
+
 // Per-thread statistics of the histories a thread finished (integers: order-free sums).
 struct LegTally {
     unsigned int c[9];         // histories, segments, collisions, leaked, census, killed, reached, errors,
@@ -185,10 +206,13 @@ __device__ __forceinline__ void load_sig(const double* sig, int k, double* sa, d
 // kStaged: the births were staged by the birth kernel (every leg but the ones that keep their
 // census as particles, N_s = infinity and steps 3'/4', whose staging buffer holds that census);
 // the kernel without the in-loop birth code keeps the loop body small
-template <typename T, bool kStaged, typename Src>
+// kPhased: histories of one phase of the phased leg (ph): they start from the bank and births
+// (first phase) or from the saved states, and a history that completes its phase's budget of
+// segments alive is saved for the next phase.
+template <typename T, bool kStaged, typename Src, bool kPhased = false>
 __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const uint32_t* sV, const uint32_t* sShC,
                                const uint32_t* sShS, uint64_t key_c, uint64_t key_s, const LegScales& sc,
-                               LegTally& t) {
+                               LegTally& t, const PhaseArgs<T>* ph = nullptr) {
     // this thread's 128-bit weight sums (source, leaked, census, killed) live in shared memory,
     // not in registers: the segment loop then fits its register budget without spills
     __shared__ unsigned long long s_wl[4][kTile], s_wh[4][kTile];
@@ -221,8 +245,29 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
     bool pending = false;   // scattered, waiting for its new direction and optical depth
     long long next = 0, last = 0;
     bool exhausted = false;
+    bool to_save = false;   // phased leg: the lane's history completed its phase alive
+    int seg0 = 0;           // phased leg: the history's segments before this phase
 
     for (;;) {
+        if constexpr (kPhased) {
+            // histories that completed the phase's segments alive: saved (compacted) for the next
+            const unsigned sv = __ballot_sync(0xffffffffu, to_save);
+            if (sv) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(ph->out_count, (unsigned long long)__popc(sv));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (to_save) {
+                    const size_t o = (size_t)(base + (unsigned long long)__popc(sv & lt_mask));
+                    ph->out.id[o] = h.idx | (h.census_stream ? 0x80000000u : 0u);
+                    ph->out.cell[o] = h.iy * nx + h.ix;
+                    ph->out.fx[o] = h.fx; ph->out.fy[o] = h.fy; ph->out.ox[o] = h.ox; ph->out.oy[o] = h.oy;
+                    ph->out.w[o] = h.w; ph->out.w0[o] = h.w_start; ph->out.srem[o] = h.srem; ph->out.tau[o] = h.tau;
+                    ph->out.n[o] = h.n; ph->out.seg[o] = h.seg;
+                    to_save = false;
+                    alive = false;
+                }
+            }
+        }
         unsigned need = __ballot_sync(0xffffffffu, !alive);
         while (need && !exhausted) {
             if (next >= last && !src(&next, &last)) { exhausted = true; break; }
@@ -231,13 +276,23 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
             const int rank = __popc(need & lt_mask);
             const bool mine = ((need >> lane) & 1u) && rank < take;
             long long j = next + rank;
-            if (a.spread_bank && j < nb) j = spread_slot(j, nb);
+            if (a.spread_bank && j < nb && !(kPhased && !ph->first)) j = spread_slot(j, nb);
             next += take;
             need &= ~__ballot_sync(0xffffffffu, mine);
             if (mine) {
                 // ---- start a history: bank pick-up or birth from Q -----------------------------
-                bool ok = true;
-                if (j < nb) {
+                bool ok = true, resumed = false;
+                if (kPhased && !ph->first) {
+                    // a history of the previous phase, taken up where it stopped
+                    const uint32_t id = ph->in.id[j];
+                    h.idx = id & 0x7fffffffu;
+                    h.census_stream = (id >> 31) != 0u;
+                    a.split(ph->in.cell[j], &h.ix, &h.iy);
+                    h.fx = ph->in.fx[j]; h.fy = ph->in.fy[j]; h.ox = ph->in.ox[j]; h.oy = ph->in.oy[j];
+                    h.w = ph->in.w[j]; h.w_start = ph->in.w0[j]; h.srem = ph->in.srem[j]; h.tau = ph->in.tau[j];
+                    h.n = ph->in.n[j]; h.seg = ph->in.seg[j];
+                    resumed = true;
+                } else if (j < nb) {
                     h.idx = (uint32_t)j;
                     h.census_stream = true;
                     const int k = a.bank.cell[j];
@@ -265,7 +320,12 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                     }
                     h.w = a.w0;
                 }
-                if (ok) {
+                if (resumed) {
+                    if constexpr (kF32) { h.rox = P::rcp(h.ox); h.roy = P::rcp(h.oy); }
+                    seg0 = h.seg;
+                    alive = true;
+                } else if (ok) {
+                    seg0 = 0;
                     pts.key = h.census_stream ? key_c : key_s;
                     pts.shift = h.census_stream ? sShC : sShS;
                     if constexpr (kF32) { h.rox = P::rcp(h.ox); h.roy = P::rcp(h.oy); }
@@ -424,6 +484,18 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                 reinterpret_cast<int4*>(a.hist)[h.census_stream ? (long long)h.idx : nb + (long long)h.idx] = r;
             }
             alive = false;
+        } else if constexpr (kPhased) {
+            if (h.seg - seg0 >= ph->budget) {
+                // the phase's segments done: saved at the top of the next iteration, with a
+                // scatter's new direction and optical depth drawn now (as the fused leg draws them)
+                if (pending) {
+                    const int base = 5 + 3 * (h.n - 1);
+                    iso_dir<T>(pts(h.idx, base + 1), pts(h.idx, base + 2), &h.ox, &h.oy);
+                    h.tau = h.n < Ns ? P::neglog(P::unit(pts(h.idx, 5 + 3 * h.n))) : T(0);
+                    pending = false;
+                }
+                to_save = true;
+            }
         }
     }
 #pragma unroll
@@ -496,8 +568,10 @@ __device__ void leg_flush(DevState* st, LegTally& t, const LegScales& sc, bool w
 // (clamped to [0, bank + births)) from the problem's counter.
 // FP32: four CTAs of 256 threads per SM (64 registers; a few bytes spill outside the segment loop,
 // measured 5 % faster than three CTAs without spills); FP64: two
-template <typename T, bool kStaged>
-__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) mc_leg_kernel(LegArgs<T> a) {
+// kPhased: one phase of the phased leg (ph), over the bank and births (first phase) or the saved
+// histories of the previous phase.
+template <typename T, bool kStaged, bool kPhased>
+__global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) mc_leg_kernel(LegArgs<T> a, PhaseArgs<T> ph) {
     extern __shared__ uint32_t sm[];
     uint32_t* sV = sm;
     uint32_t* sShC = sm + a.ntab * kNibbleWords;
@@ -513,13 +587,22 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) mc_leg_kernel(L
     __shared__ LegScales s_sc;   // formed once per block (FP64 work)
     if (threadIdx.x == 0) s_sc = leg_scales<T>(a);
     __syncthreads();
-    const long long nb = a.st->n_bank;
-    const long long N = nb + a.n_src;
-    const long long h1 = a.h1 < N ? a.h1 : N;
     const LegScales sc = s_sc;
     LegTally t;
     leg_tally_zero(t);
-    leg_warp_range<T, kStaged>(a, CounterChunks{&a.st->leg_next, a.h0, h1}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+    if constexpr (kPhased) {
+        // nb: the bank size in every phase (a finished history's record and census slot follow
+        // [bank slots | births]); later phases take up saved histories [0, in_count)
+        const long long nb = a.st->n_bank;
+        const long long N = ph.first ? nb + a.n_src : (long long)*ph.in_count;
+        leg_warp_range<T, kStaged, CounterChunks, true>(a, CounterChunks{&a.st->leg_next, 0, N}, nb, sV, sShC, sShS,
+                                                        key_c, key_s, sc, t, &ph);
+    } else {
+        const long long nb = a.st->n_bank;
+        const long long N = nb + a.n_src;
+        const long long h1 = a.h1 < N ? a.h1 : N;
+        leg_warp_range<T, kStaged>(a, CounterChunks{&a.st->leg_next, a.h0, h1}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+    }
     leg_flush(a.st, t, sc, blockIdx.x == 0);
 }
 
@@ -857,14 +940,109 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist, long long h0, long lo
         p->births_step = h0 == 0 && h1 == LLONG_MAX ? p->step : -1;   // a range leg draws only its share
     }
     const bool staged = a.births.cell != nullptr;
-    cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true>, smem) : allow_smem(mc_leg_kernel<T, false>, smem);
+    cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true, false>, smem) : allow_smem(mc_leg_kernel<T, false, false>, smem);
     if (e != cudaSuccess) return e;
     e = cudaEventRecord(p->evk[0], p->stream);
     if (e != cudaSuccess) return e;
-    if (staged) mc_leg_kernel<T, true><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
-    else mc_leg_kernel<T, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a);
+    const PhaseArgs<T> none{};
+    if (staged) mc_leg_kernel<T, true, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, none);
+    else mc_leg_kernel<T, false, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, none);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    return cudaEventRecord(p->evk[1], p->stream);
+}
+
+// Live-state buffer b (0, 1) of the phased leg: the eight T arrays first (8-byte alignment on the
+// FP64 path), then id, cell, n and seg
+template <typename T>
+static LiveView<T> live_view(hyb_problem* p, int b) {
+    const size_t n = (size_t)p->live_cap;
+    T* f = static_cast<T*>(p->live_buf[b]);
+    LiveView<T> v;
+    v.fx = f; v.fy = f + n; v.ox = f + 2 * n; v.oy = f + 3 * n;
+    v.w = f + 4 * n; v.w0 = f + 5 * n; v.srem = f + 6 * n; v.tau = f + 7 * n;
+    uint32_t* u = reinterpret_cast<uint32_t*>(f + 8 * n);
+    v.id = u;
+    v.cell = reinterpret_cast<int32_t*>(u + n);
+    v.n = reinterpret_cast<int32_t*>(u + 2 * n);
+    v.seg = reinterpret_cast<int32_t*>(u + 3 * n);
+    return v;
+}
+
+size_t live_buf_bytes(long long cap, int prec) {
+    return (size_t)cap * (8 * (prec == HYB_FP64 ? sizeof(double) : sizeof(float)) + 4 * sizeof(uint32_t));
+}
+
+// the saved histories in cell order: dst[q] = src[perm[q]] (low half of the sorted pair)
+template <typename T>
+__global__ void __launch_bounds__(kTile) live_gather_kernel(LiveView<T> src, LiveView<T> dst,
+                                                            const unsigned long long* perm, long long n) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const uint32_t j = (uint32_t)perm[q];
+        dst.id[q] = src.id[j]; dst.cell[q] = src.cell[j];
+        dst.fx[q] = src.fx[j]; dst.fy[q] = src.fy[j]; dst.ox[q] = src.ox[j]; dst.oy[q] = src.oy[j];
+        dst.w[q] = src.w[j]; dst.w0[q] = src.w0[j]; dst.srem[q] = src.srem[j]; dst.tau[q] = src.tau[j];
+        dst.n[q] = src.n[j]; dst.seg[q] = src.seg[j];
+    }
+}
+
+// The phased leg (leg_sort_every = K >= 1): phase 0 starts every history (bank slots, then
+// births) and runs each for at most K segments; the histories alive after a phase are saved
+// (compacted), sorted by cell (stable radix sort of their cells), and the next phase takes them up
+// in that order, until none is left. The host reads the live count after each phase. Every
+// history does the fused leg's arithmetic on the same points, and every sum is an order-free
+// integer sum, so the tallies, counters and weight statistics equal the fused leg's bit for bit.
+template <typename T>
+static cudaError_t mc_leg_phased_t(hyb_problem* p, int32_t* hist) {
+    LegArgs<T> a = leg_args<T>(p, hist, p->cur);
+    const size_t smem = (size_t)(a.ntab * kNibbleWords + 2 * a.ntab) * sizeof(uint32_t);
+    if (a.n_src > 0 && a.births.cell && p->births_step != p->step) {
+        const long long g = (a.n_src + kTile - 1) / kTile;
+        mc_birth_kernel<T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kTile, 0, p->stream>>>(a);
+        p->births_step = p->step;
+    }
+    const bool staged = a.births.cell != nullptr;
+    cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true, true>, smem) : allow_smem(mc_leg_kernel<T, false, true>, smem);
+    if (e != cudaSuccess) return e;
+    PhaseArgs<T> ph{};
+    ph.budget = p->d.leg_sort_every;
+    ph.out_count = &p->st->live_count;
+    ph.in_count = &p->st->live_in;
+    ph.in = live_view<T>(p, 1);
+    ph.out = live_view<T>(p, 0);
+    // every phase adds at least K segments to each history it saves, and a history ends (as an
+    // error) at the segment bound: the phases are bounded
+    const long long max_phases = (long long)a.seg_limit / ph.budget + 2;
+    const int wait = p->d.wait_limit > 0 ? p->d.wait_limit : (1 << 22);
+    long long work = p->bank_cap + a.n_src;
+    e = cudaEventRecord(p->evk[0], p->stream);
+    if (e != cudaSuccess) return e;
+    for (long long phase = 0;; ++phase) {
+        if (phase > max_phases) return cudaErrorIllegalState;
+        ph.first = phase == 0 ? 1 : 0;
+        e = cudaMemsetAsync(&p->st->leg_next, 0, 2 * sizeof(unsigned long long), p->stream);   // leg_next, live_count
+        if (e != cudaSuccess) return e;
+        if (staged) mc_leg_kernel<T, true, true><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, ph);
+        else mc_leg_kernel<T, false, true><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, ph);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(&p->st_host->live_count, &p->st->live_count, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) return e;
+        const long long n = (long long)p->st_host->live_count;
+        if (n == 0) break;
+        const unsigned long long* perm = nullptr;
+        e = launch_census_sort(ph.out.cell, n, (uint32_t)p->ncells, p->live_pairs, p->live_scratch, wait,
+                               &p->st->status, p->stream, &perm);
+        if (e != cudaSuccess) return e;
+        const long long g = (n + kTile - 1) / kTile;
+        live_gather_kernel<T><<<(unsigned)(g < 152 * 8 ? g : 152 * 8), kTile, 0, p->stream>>>(ph.out, ph.in, perm, n);
+        e = cudaMemcpyAsync(&p->st->live_in, &p->st->live_count, sizeof(unsigned long long), cudaMemcpyDeviceToDevice,
+                            p->stream);
+        if (e != cudaSuccess) return e;
+        work = n;
+    }
     return cudaEventRecord(p->evk[1], p->stream);
 }
 
@@ -934,6 +1112,8 @@ cudaError_t launch_births_ahead(hyb_problem* p) {
 }
 
 cudaError_t launch_mc_leg(hyb_problem* p, int32_t* hist_dev, long long h0, long long h1) {
+    if (p->d.leg_sort_every > 0 && h0 == 0 && h1 == LLONG_MAX)   // a whole leg: phases sorted by cell
+        return p->prec == HYB_FP64 ? mc_leg_phased_t<double>(p, hist_dev) : mc_leg_phased_t<float>(p, hist_dev);
     return p->prec == HYB_FP64 ? mc_leg_t<double>(p, hist_dev, h0, h1) : mc_leg_t<float>(p, hist_dev, h0, h1);
 }
 

@@ -60,6 +60,7 @@ class ProblemSpec:
     wait_limit: int = 0             # polls of a device wait (solve pipeline, sort look-back) before HYB_ETIMEOUT (0: 2^22)
     tally_copies: int = 0           # copies of the fixed-point tally arrays (0: automatic)
     sort_every: int = 0             # census_order >= 1: sort on the steps n with n mod sort_every == 0 (0, 1: all)
+    leg_sort_every: int = 0         # 0: fused leg; K >= 1: phases of K segments, live histories sorted by cell between
     name: str = field(default="problem")
 
     @property

@@ -55,11 +55,12 @@ def test_batch_equals_alone(prec, order):
 
 
 def test_batch_rejects_halton_and_infinite_ns():
-    """... and a census sorted on some steps only (a step graph replays one sort decision)."""
+    """... a census sorted on some steps only (a step graph replays one sort decision), and the
+    phased leg (its phases wait on the host)."""
     from paper_2511_16821_gb300 import hyb
     base = _problems(2, 5, precision=W.FP32)
     for bad in (base[1].with_(sampler=W.HALTON), base[1].with_(n_s=W.NS_INF),
-                base[1].with_(census_order=1, sort_every=2)):
+                base[1].with_(census_order=1, sort_every=2), base[1].with_(leg_sort_every=2)):
         probs = [hyb.Problem(base[0]), hyb.Problem(bad)]
         with pytest.raises(hyb.HybError) as e:
             hyb.Batch(probs)
