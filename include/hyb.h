@@ -150,6 +150,13 @@ typedef struct {
                                  the fused leg's bit for bit; the host waits once per phase. A
                                  leg over a history range (hyb_mc_leg_range) stays fused; a
                                  batch rejects K >= 1 */
+    int32_t priv_tile;        /* 0: every tally addition of the fused MC leg goes to the global
+                                 tally copies. 1..32: each CTA keeps the tallies of a square window
+                                 of priv_tile x priv_tile cells -- placed where the source weight
+                                 Q (else the initial weight) is largest -- in shared memory and
+                                 adds them to its global copy once, at its end (integer sums: the
+                                 results do not change). Not used by the phased leg or batches */
+    int32_t pad4;
 } hyb_problem_desc;
 
 /* Per-leg (or per-step) statistics. Weights are exact fixed-point sums converted to double. */

@@ -8,11 +8,12 @@ tuning, as in the first steps of a run; results do not depend on the tuning (the
 per problem).
 
 tune_problem times one problem's creation-time knobs: the copies of the fixed-point tally arrays
-(the privatisation of the leg's atomic adds: more copies spread the adds to hot cells, fewer keep
-the copies in L2), the leg's sort interval (leg_sort_every = K: 0 runs the fused leg, K >= 1 the
+(more copies spread the leg's atomic adds to hot cells, fewer keep the copies in L2), the
+privatisation tile (priv_tile: the side of the window of cells whose tallies each CTA keeps in
+shared memory, placed on the densest source region; 0: none), the leg's sort interval (leg_sort_every = K: 0 runs the fused leg, K >= 1 the
 phased leg, whose live histories are sorted by cell every K segments) and the census sort interval
 (with census_order >= 1, the census is sorted and combed in cell order on every sort_every-th step
-only). The copies and the leg's sort interval never change a result; the census sort interval
+only). The copies, the tile and the leg's sort interval never change a result; the census sort interval
 does (an unsorted comb samples each cell's weight less evenly), so it is searched only when the
 space names it, and the caller accepts the variance that comes with a longer interval.
 """
@@ -21,7 +22,7 @@ from __future__ import annotations
 import itertools
 
 DEFAULT_SPACE = {"block": (128, 256), "chunk": (1024, 4096, 16384), "ctas_per_sm": (0,), "streams": (8, 32)}
-PROBLEM_SPACE = {"tally_copies": (1, 2, 4, 8), "leg_sort_every": (0, 4, 16)}
+PROBLEM_SPACE = {"tally_copies": (1, 4), "priv_tile": (0, 8, 16), "leg_sort_every": (0, 8)}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -64,7 +65,8 @@ def tune_problem(spec, steps: int = 4, warmup: int = 3, space: dict | None = Non
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     best, best_ms, table = None, float("inf"), []
     with torch.cuda.stream(stream):
-        for cand in candidates(space, PROBLEM_SPACE):
+        # the knobs the space names (by default PROBLEM_SPACE); the others keep the spec's values
+        for cand in candidates(space, {}) if space else candidates(None, PROBLEM_SPACE):
             P = hyb.Problem(spec.with_(**cand), stream=stream)
             try:
                 P.step(warmup, stats=False)

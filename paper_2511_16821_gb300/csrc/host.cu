@@ -262,6 +262,34 @@ struct Layout {
     }
 };
 
+// The leg's privatised window (priv_tile > 0): the square of priv_tile cells on a side (at most the
+// mesh) holding the largest source weight sum Q (2-D prefix sums; the first such square in row
+// order), or the initial weight where there is no source, else the mesh centre. Births and the
+// census concentrate there, so their tally additions stay in each block's shared memory.
+void choose_priv_window(const hyb_problem_desc* d, int* x0, int* y0, int* side) {
+    *x0 = *y0 = *side = 0;
+    if (d->priv_tile <= 0) return;
+    const int nx = d->nx, ny = d->ny;
+    const int s = std::min(d->priv_tile, std::min(nx, ny));
+    const double* q = d->Q ? d->Q : d->ic_cell_w;
+    *side = s;
+    *x0 = (nx - s) / 2;
+    *y0 = (ny - s) / 2;
+    if (!q) return;
+    std::vector<double> ps((size_t)(nx + 1) * (ny + 1), 0.0);   // ps[(y) (nx + 1) + x]: sum over [0, x) x [0, y)
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x)
+            ps[(size_t)(y + 1) * (nx + 1) + x + 1] = q[(size_t)y * nx + x] + ps[(size_t)y * (nx + 1) + x + 1] +
+                                                    ps[(size_t)(y + 1) * (nx + 1) + x] - ps[(size_t)y * (nx + 1) + x];
+    double best = -1.0;
+    for (int y = 0; y + s <= ny; ++y)
+        for (int x = 0; x + s <= nx; ++x) {
+            const double v = ps[(size_t)(y + s) * (nx + 1) + x + s] - ps[(size_t)y * (nx + 1) + x + s] -
+                             ps[(size_t)(y + s) * (nx + 1) + x] + ps[(size_t)y * (nx + 1) + x];
+            if (v > best) { best = v; *x0 = x; *y0 = y; }
+        }
+}
+
 int64_t eff_cap(const hyb_problem_desc* d) {
     const int64_t cc = d->census_cap > 0 ? d->census_cap : d->n_hist;
     return std::max<int64_t>(cc, d->n_hist);
@@ -476,6 +504,7 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->tally_copies < 0 || d->tally_copies > 64) { *why = "tally_copies must be in [0, 64]"; return HYB_EINVAL; }
     if (d->sort_every < 0) { *why = "sort_every must be >= 0"; return HYB_EINVAL; }
     if (d->leg_sort_every < 0) { *why = "leg_sort_every must be >= 0"; return HYB_EINVAL; }
+    if (d->priv_tile < 0 || d->priv_tile > 32) { *why = "priv_tile must be in [0, 32]"; return HYB_EINVAL; }
     if (d->leg_sort_every > 0 && eff_cap(d) + d->n_hist >= ((int64_t)1 << 31)) {
         *why = "the phased leg holds fewer than 2^31 histories (bank capacity + births)";   // 31-bit saved indices
         return HYB_EINVAL;
@@ -820,6 +849,7 @@ hyb_status hyb_create_problem(const hyb_problem_desc* d, void* workspace, size_t
     hyb_problem* p = new (std::nothrow) hyb_problem();
     if (!p) return fail(nullptr, HYB_ENOMEM, "host allocation failed");
     p->d = *d;
+    choose_priv_window(d, &p->priv_x0, &p->priv_y0, &p->priv_side);
     p->d.sigma_a = p->d.sigma_s = p->d.Q = p->d.ic_cell_w = nullptr;
     p->nx = d->nx; p->ny = d->ny; p->ncells = d->nx * d->ny;
     p->dx = d->lx / d->nx; p->dy = d->ly / d->ny; p->area = p->dx * p->dy;

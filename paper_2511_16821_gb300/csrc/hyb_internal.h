@@ -152,6 +152,7 @@ struct hyb_problem {
     unsigned long long* live_pairs[2];   //   their (cell, index) pairs for the sort by cell
     void* live_scratch;                  //   and the sort's scratch; all null for the fused leg
     long long live_cap;                  //   histories a leg can hold (bank capacity + births)
+    int priv_x0, priv_y0, priv_side;     // the leg's privatised window of cells (side 0: none)
     int* rem_pos;             // ncells: 1 where the bilinear remap density is non-negative
     double* rem_q;            // ncells signed remap cell weights q = f0 A dt
     double* cell_scratch;     // per-row partials for the CDF build

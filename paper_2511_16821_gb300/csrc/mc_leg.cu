@@ -48,6 +48,7 @@ struct LegArgs {
     long long h0, h1;           // history index range tracked: [h0, h1) of [bank slots | births]
     long long birth_step;       // step index of the births drawn by mc_birth_kernel (-1: the device's step)
     int seg_limit;              // segments per history before the history ends as an error
+    int wx0, wy0, wside;        // privatised window of cells (single-problem fused leg; wside 0: none)
 };
 
 // State of one live history in a lane.
@@ -209,10 +210,13 @@ __device__ __forceinline__ void load_sig(const double* sig, int k, double* sa, d
 // kPhased: histories of one phase of the phased leg (ph): they start from the bank and births
 // (first phase) or from the saved states, and a history that completes its phase's budget of
 // segments alive is saved for the next phase.
-template <typename T, bool kStaged, typename Src, bool kPhased = false>
+// kPriv: the tallies of the cells in the window (a.wx0, a.wy0, a.wside) go to the block's copy in
+// shared memory (tile: pre, post, then the 4 moments per cell of the window), flushed by the caller.
+template <typename T, bool kStaged, typename Src, bool kPhased = false, bool kPriv = false>
 __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const uint32_t* sV, const uint32_t* sShC,
                                const uint32_t* sShS, uint64_t key_c, uint64_t key_s, const LegScales& sc,
-                               LegTally& t, const PhaseArgs<T>* ph = nullptr) {
+                               LegTally& t, const PhaseArgs<T>* ph = nullptr,
+                               typename Prec<T>::acc_t* tile = nullptr) {
     // this thread's 128-bit weight sums (source, leaked, census, killed) live in shared memory,
     // not in registers: the segment loop then fits its register budget without spills
     __shared__ unsigned long long s_wl[4][kTile], s_wh[4][kTile];
@@ -370,6 +374,18 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
         // ---- one segment ----------------------------------------------------------------------
         ++h.seg;
         const int k = h.iy * nx + h.ix;
+        typename P::acc_t* pre_p = &pre_b[k];
+        typename P::acc_t* post_p = &post_b[k];
+        typename P::acc_t* mom_p = &mom_b[4 * k];
+        if constexpr (kPriv) {
+            const unsigned lx = (unsigned)(h.ix - a.wx0), ly = (unsigned)(h.iy - a.wy0);
+            if (lx < (unsigned)a.wside && ly < (unsigned)a.wside) {
+                const int kl = (int)(ly * (unsigned)a.wside + lx), w2 = a.wside * a.wside;
+                pre_p = tile + kl;
+                post_p = tile + w2 + kl;
+                mom_p = tile + 2 * w2 + 4 * kl;
+            }
+        }
         T sa, ss;
         load_sig(a.sig, k, &sa, &ss);
         const T st = sa + ss;
@@ -408,26 +424,26 @@ __device__ void leg_warp_range(const LegArgs<T>& a, Src src, long long nb, const
                 pre_c = kF32 ? h.w * att * isa : h.w * att / sa;
                 h.w = h.w * e;
             }
-            t.c[8] += P::add(&pre_b[k], pre_c, sc_t);
+            t.c[8] += P::add(pre_p, pre_c, sc_t);
             h.tau = P::msub(h.tau, ss, l);
         } else {
             T att, e;
             P::att_e(st * l, &att, &e);
             const T post_c = st > T(0) ? (kF32 ? h.w * att * ist : h.w * att / st) : h.w * l;
-            t.c[8] += P::add(&post_b[k], post_c, sc_t);
+            t.c[8] += P::add(post_p, post_c, sc_t);
             if (ss > T(0)) {
                 T g0, g1, g2;
                 gfun<T>(st * l, e, att, &g0, &g1, &g2);
                 const T I0 = l * g0, I1 = l * l * g1, I2 = l * l * l * g2;
                 const T sw = ss * h.w;
-                t.c[8] += P::add(&mom_b[4 * k + 0], sw * I0, sc_m);
+                t.c[8] += P::add(mom_p + 0, sw * I0, sc_m);
                 if (a.handoff_full) {
                     const T xi0 = T(2) * h.fx / DX - T(1), eta0 = T(2) * h.fy / DY - T(1);
                     const T axi = T(2) * h.ox / DX, aeta = T(2) * h.oy / DY;
                     // explicit fused forms: the same rounding in every kernel this is inlined into
-                    t.c[8] += P::add(&mom_b[4 * k + 1], sw * P::fma_(xi0, I0, axi * I1), sc_m);
-                    t.c[8] += P::add(&mom_b[4 * k + 2], sw * P::fma_(eta0, I0, aeta * I1), sc_m);
-                    t.c[8] += P::add(&mom_b[4 * k + 3],
+                    t.c[8] += P::add(mom_p + 1, sw * P::fma_(xi0, I0, axi * I1), sc_m);
+                    t.c[8] += P::add(mom_p + 2, sw * P::fma_(eta0, I0, aeta * I1), sc_m);
+                    t.c[8] += P::add(mom_p + 3,
                            sw * P::fma_(xi0 * eta0, I0, P::fma_(P::fma_(xi0, aeta, eta0 * axi), I1, axi * aeta * I2)),
                            sc_m);
                 }
@@ -568,12 +584,27 @@ __device__ void leg_flush(DevState* st, LegTally& t, const LegScales& sc, bool w
 // (clamped to [0, bank + births)) from the problem's counter.
 // FP32: four CTAs of 256 threads per SM (64 registers; a few bytes spill outside the segment loop,
 // measured 5 % faster than three CTAs without spills); FP64: two
+// byte offset of the privatised tile in the leg kernel's dynamic shared memory (after the point
+// tables and the two digital-shift vectors, 16-byte aligned)
+__host__ __device__ __forceinline__ size_t leg_tile_offset(int ntab) {
+    return ((size_t)(ntab * kNibbleWords + 2 * ntab) * sizeof(uint32_t) + 15) & ~(size_t)15;
+}
+
 // kPhased: one phase of the phased leg (ph), over the bank and births (first phase) or the saved
-// histories of the previous phase.
-template <typename T, bool kStaged, bool kPhased>
+// histories of the previous phase. kPriv: the block keeps the tallies of the window's cells in
+// shared memory (after the point tables) and adds them to its global copy at the end, one
+// coalesced atomic per nonzero entry.
+template <typename T, bool kStaged, bool kPhased, bool kPriv>
 __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) mc_leg_kernel(LegArgs<T> a, PhaseArgs<T> ph) {
-    extern __shared__ uint32_t sm[];
+    using acc_t = typename Prec<T>::acc_t;
+    extern __shared__ __align__(16) uint32_t sm[];
     uint32_t* sV = sm;
+    acc_t* tile = nullptr;
+    if constexpr (kPriv) {
+        tile = reinterpret_cast<acc_t*>(reinterpret_cast<char*>(sm) + leg_tile_offset(a.ntab));
+        const int ne = 6 * a.wside * a.wside;
+        for (int i = threadIdx.x; i < ne; i += blockDim.x) tile[i] = acc_t{};
+    }
     uint32_t* sShC = sm + a.ntab * kNibbleWords;
     uint32_t* sShS = sShC + a.ntab;
     const uint64_t step = (uint64_t)a.st->step;
@@ -601,7 +632,27 @@ __global__ void __launch_bounds__(kTile, sizeof(T) == 4 ? 4 : 2) mc_leg_kernel(L
         const long long nb = a.st->n_bank;
         const long long N = nb + a.n_src;
         const long long h1 = a.h1 < N ? a.h1 : N;
-        leg_warp_range<T, kStaged>(a, CounterChunks{&a.st->leg_next, a.h0, h1}, nb, sV, sShC, sShS, key_c, key_s, sc, t);
+        leg_warp_range<T, kStaged, CounterChunks, false, kPriv>(a, CounterChunks{&a.st->leg_next, a.h0, h1}, nb, sV,
+                                                                sShC, sShS, key_c, key_s, sc, t, nullptr, tile);
+    }
+    if constexpr (kPriv) {
+        // the window's tallies into the block's global copy (integer sums: any copy, any order)
+        __syncthreads();
+        const int ws = a.wside, w2 = ws * ws;
+        const size_t nc = (size_t)a.nx * a.ny, cb = (size_t)(blockIdx.x % a.ncopy);
+        for (int i = threadIdx.x; i < 6 * w2; i += blockDim.x) {
+            const acc_t v = tile[i];
+            const int kl = i < 2 * w2 ? i % w2 : (i - 2 * w2) >> 2;
+            const size_t cell = (size_t)(a.wy0 + kl / ws) * a.nx + (size_t)(a.wx0 + kl % ws);
+            acc_t* dst = i < w2 ? a.pre + cb * nc + cell
+                       : i < 2 * w2 ? a.post + cb * nc + cell
+                                    : a.mom + cb * 4 * nc + 4 * cell + ((i - 2 * w2) & 3);
+            if constexpr (sizeof(T) == 4) {
+                if (v) atomicAdd(dst, v);
+            } else {
+                if (v.lo || v.hi) atomic_add128(dst, v.lo, v.hi);
+            }
+        }
     }
     leg_flush(a.st, t, sc, blockIdx.x == 0);
 }
@@ -873,6 +924,20 @@ static int leg_grid(long long work, int prec) {
     return (int)g;
 }
 
+// persistent grid of the privatised leg: as many CTAs per SM as its shared memory leaves resident
+static int leg_grid_priv(long long work, int prec, size_t smem, const void* kernel) {
+    int dev = 0, sms = 152, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kTile, smem) != cudaSuccess || per < 1) per = 1;
+    if (per > leg_ctas_per_sm(prec)) per = leg_ctas_per_sm(prec);
+    long long g = (work + kTile - 1) / kTile;
+    const long long cap = (long long)sms * per;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
 template <typename T>
 LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     LegArgs<T> a;
@@ -912,6 +977,9 @@ LegArgs<T> leg_args(hyb_problem* p, int32_t* hist, int cur) {
     a.h0 = 0;
     a.h1 = LLONG_MAX;
     a.seg_limit = p->d.seg_limit > 0 ? p->d.seg_limit : (int)kMaxSegments;
+    a.wx0 = p->priv_x0;
+    a.wy0 = p->priv_y0;
+    a.wside = p->priv_side;
     return a;
 }
 
@@ -940,13 +1008,29 @@ static cudaError_t mc_leg_t(hyb_problem* p, int32_t* hist, long long h0, long lo
         p->births_step = h0 == 0 && h1 == LLONG_MAX ? p->step : -1;   // a range leg draws only its share
     }
     const bool staged = a.births.cell != nullptr;
-    cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true, false>, smem) : allow_smem(mc_leg_kernel<T, false, false>, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaEventRecord(p->evk[0], p->stream);
-    if (e != cudaSuccess) return e;
     const PhaseArgs<T> none{};
-    if (staged) mc_leg_kernel<T, true, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, none);
-    else mc_leg_kernel<T, false, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, none);
+    cudaError_t e;
+    if (a.wside > 0) {
+        // the privatised window: its tile after the tables (allow_smem raises the limit as needed)
+        const size_t smem_t = leg_tile_offset(a.ntab) + (size_t)6 * a.wside * a.wside * sizeof(typename Prec<T>::acc_t);
+        e = staged ? allow_smem(mc_leg_kernel<T, true, false, true>, smem_t)
+                   : allow_smem(mc_leg_kernel<T, false, false, true>, smem_t);
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecord(p->evk[0], p->stream);
+        if (e != cudaSuccess) return e;
+        const int g = leg_grid_priv(work, p->prec, smem_t, staged ? (const void*)mc_leg_kernel<T, true, false, true>
+                                                                  : (const void*)mc_leg_kernel<T, false, false, true>);
+        if (staged) mc_leg_kernel<T, true, false, true><<<g, kTile, smem_t, p->stream>>>(a, none);
+        else mc_leg_kernel<T, false, false, true><<<g, kTile, smem_t, p->stream>>>(a, none);
+    } else {
+        e = staged ? allow_smem(mc_leg_kernel<T, true, false, false>, smem)
+                   : allow_smem(mc_leg_kernel<T, false, false, false>, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaEventRecord(p->evk[0], p->stream);
+        if (e != cudaSuccess) return e;
+        if (staged) mc_leg_kernel<T, true, false, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, none);
+        else mc_leg_kernel<T, false, false, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, none);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return cudaEventRecord(p->evk[1], p->stream);
@@ -1002,7 +1086,8 @@ static cudaError_t mc_leg_phased_t(hyb_problem* p, int32_t* hist) {
         p->births_step = p->step;
     }
     const bool staged = a.births.cell != nullptr;
-    cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true, true>, smem) : allow_smem(mc_leg_kernel<T, false, true>, smem);
+    cudaError_t e = staged ? allow_smem(mc_leg_kernel<T, true, true, false>, smem)
+                           : allow_smem(mc_leg_kernel<T, false, true, false>, smem);
     if (e != cudaSuccess) return e;
     PhaseArgs<T> ph{};
     ph.budget = p->d.leg_sort_every;
@@ -1022,8 +1107,8 @@ static cudaError_t mc_leg_phased_t(hyb_problem* p, int32_t* hist) {
         ph.first = phase == 0 ? 1 : 0;
         e = cudaMemsetAsync(&p->st->leg_next, 0, 2 * sizeof(unsigned long long), p->stream);   // leg_next, live_count
         if (e != cudaSuccess) return e;
-        if (staged) mc_leg_kernel<T, true, true><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, ph);
-        else mc_leg_kernel<T, false, true><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, ph);
+        if (staged) mc_leg_kernel<T, true, true, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, ph);
+        else mc_leg_kernel<T, false, true, false><<<leg_grid(work, p->prec), kTile, smem, p->stream>>>(a, ph);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = cudaMemcpyAsync(&p->st_host->live_count, &p->st->live_count, sizeof(unsigned long long),

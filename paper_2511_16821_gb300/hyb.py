@@ -40,7 +40,8 @@ class Desc(C.Structure):
                 ("sn_warm_start", C.c_int32), ("census_order", C.c_int32), ("sn_accel", C.c_int32),
                 ("remap_variant", C.c_int32), ("n_s_cell", C.POINTER(C.c_int32)), ("sn_layout", C.c_int32),
                 ("seg_limit", C.c_int32), ("wait_limit", C.c_int32), ("tally_copies", C.c_int32),
-                ("sort_every", C.c_int32), ("leg_sort_every", C.c_int32)]
+                ("sort_every", C.c_int32), ("leg_sort_every", C.c_int32), ("priv_tile", C.c_int32),
+                ("pad4", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -152,7 +153,7 @@ def make_desc(spec: ProblemSpec) -> tuple[Desc, list]:
              census_cap=spec.census_cap, sn_warm_start=spec.sn_warm_start, census_order=spec.census_order,
              sn_accel=spec.sn_accel, remap_variant=spec.remap_variant, sn_layout=spec.sn_layout,
              seg_limit=spec.seg_limit, wait_limit=spec.wait_limit, tally_copies=spec.tally_copies,
-             sort_every=spec.sort_every, leg_sort_every=spec.leg_sort_every)
+             sort_every=spec.sort_every, leg_sort_every=spec.leg_sort_every, priv_tile=spec.priv_tile)
     if spec.n_s_cell is not None:
         lim = np.ascontiguousarray(np.asarray(spec.n_s_cell, dtype=np.int32).ravel())
         keep.append(lim)

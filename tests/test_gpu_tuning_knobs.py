@@ -25,12 +25,15 @@ def H():
 
 @pytest.mark.parametrize("prec", [W.FP32, W.FP64])
 def test_tally_copies_do_not_change_the_leg(H, prec):
+    """Copies of the tally arrays and the shared-memory window (priv_tile: the source block's cells
+    and beyond; 32 is wider than the 25-cell source block, 7 straddles its edge) change where the
+    integer additions land, never their sums."""
     hyb = H
     spec = W.checkerboard(n_s=2, n_hist=60_000, cells_per_block=5).with_(precision=prec)
     bank = W.random_bank(spec, 40_000, seed=5)
     ref = None
-    for copies in (0, 1, 3, 8):
-        P = hyb.Problem(spec.with_(tally_copies=copies))
+    for copies, priv in ((0, 0), (1, 0), (3, 0), (8, 0), (0, 7), (1, 16), (4, 32)):
+        P = hyb.Problem(spec.with_(tally_copies=copies, priv_tile=priv))
         P.set_bank(bank)
         P.set_step(2)
         st = P.mc_leg()
@@ -40,9 +43,9 @@ def test_tally_copies_do_not_change_the_leg(H, prec):
             ref = got
             continue
         for k in ("histories", "segments", "collisions", "tally_adds", "w_source", "w_absorbed", "w_handoff"):
-            assert got[0][k] == ref[0][k], (copies, k)
+            assert got[0][k] == ref[0][k], (copies, priv, k)
         for t in ("pre_raw", "post_raw", "handoff"):
-            assert np.array_equal(got[1][t], ref[1][t]), (copies, t)
+            assert np.array_equal(got[1][t], ref[1][t]), (copies, priv, t)
 
 
 @pytest.mark.parametrize("order", [1, 2])
