@@ -409,6 +409,47 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0, sn_acc
     return out
 
 
+LEG_PLACEMENTS = ((0, 0), (1, 0), (4, 0), (1, 16), (4, 16), (4, 8))   # (tally_copies, priv_tile)
+
+
+def leg_ns_sweep(atomic_peak: float, reps: int = 5) -> list:
+    """The benchmark leg at the checkerboard family's scatter limits N_s = 0, 1, 2, 4: the leg
+    kernel's device time (CUDA events at its launch, median of `reps` launches on the step-2 bank,
+    the L2 flushed before each) with the default tally placement and with the best of
+    LEG_PLACEMENTS (global copies of the tally arrays x the shared-memory window over the source
+    block); its tally additions over that time against the measured atomic rate."""
+    import torch
+    from paper_2511_16821_gb300 import hyb
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    out = []
+    for ns in (0, 1, 2, 4):
+        spec = spec_for(W.FP32, n_s=ns)
+        P0 = hyb.Problem(spec)
+        P0.step(2)
+        bank = P0.bank()
+        P0.close()
+        rows = []
+        for copies, priv in LEG_PLACEMENTS:
+            P = hyb.Problem(spec.with_(tally_copies=copies, priv_tile=priv))
+            P.set_bank(bank)
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                torch.cuda.synchronize()
+                P.set_step(2)
+                st = P.mc_leg()
+                ms.append(st["ms_leg_kernel"])
+            P.close()
+            m = statistics.median(ms)
+            rate = st["tally_adds"] / (m / 1e3)
+            rows.append({"tally_copies": copies, "priv_tile": priv, "leg_kernel_ms": m,
+                         "achieved": rate / 1e9, "frac": rate / atomic_peak})
+        best = min(rows, key=lambda r: r["leg_kernel_ms"])
+        out.append({"n_s": ns, "histories": st["histories"], "segments": st["segments"],
+                    "tally_adds": st["tally_adds"], "unit": "Gatomic/s", "default": rows[0], "best": best})
+    return out
+
+
 def census_order_measure(steps: int = 5, order: int = 1) -> dict:
     """The benchmark workload with the census sorted before the comb (FP32), by cell (order 1) or by
     cell and phase space (order 2): device time per step. At equal histories their multi-step
@@ -662,6 +703,7 @@ def main():
                                              "bytes": bank64 * 44}}}
     if not args.no_e2e:
         line["e2e"] = e2e_measure(spec_for(W.FP32), max(2, min(args.steps, 20)))
+    line["leg_ns_sweep"] = leg_ns_sweep(atomic_peak)
     if CENSUS_ORDER == 0:
         line["census_cell_order"] = census_order_measure(order=1)
         line["census_phase_order"] = census_order_measure(order=2)
