@@ -76,3 +76,29 @@ def test_phased_steps_equal_fused(prec, n_s):
     for x, y in zip(sa, sb):
         for key in ("histories", "segments", "census", "bank_size", "w_census", "sn_iterations"):
             assert x[key] == y[key], key
+
+
+@pytest.mark.parametrize("prec", [W.FP32, W.FP64])
+def test_phased_leg_segment_bound(prec):
+    """Histories that reach the segment bound end as errors in the phase that reaches it (the
+    phases stay bounded) and the leg returns HYB_ETIMEOUT, as the fused leg does; without the
+    bound the phased leg equals the fused one on these long histories."""
+    from paper_2511_16821_gb300 import hyb
+    spec = W.homogeneous(n=64, L=1.0, sigma_a=0.0, sigma_s=0.5, Q=1.0, n_hist=2000, dt=10.0, n_s=1,
+                         precision=prec)
+    for k in (0, 3):
+        P = hyb.Problem(spec.with_(seg_limit=8, leg_sort_every=k))
+        with pytest.raises(hyb.HybError) as e:
+            P.mc_leg()
+        assert e.value.status == hyb.HYB_ETIMEOUT, k
+        P.close()
+    res = []
+    for k in (0, 5):
+        P = hyb.Problem(spec.with_(leg_sort_every=k))
+        st = P.mc_leg()
+        res.append((st, P.tally("pre_raw"), P.tally("post_raw")))
+        P.close()
+    assert res[0][0]["segments"] > 8 * res[0][0]["histories"] // 2
+    for key in KEYS:
+        assert res[0][0][key] == res[1][0][key], key
+    assert np.array_equal(res[0][1], res[1][1]) and np.array_equal(res[0][2], res[1][2])
