@@ -102,6 +102,7 @@ class Clocks:
 
 
 CENSUS_ORDER = 0
+PRIV_TILE = 0
 SN_ACCEL = 0
 WARM = 1
 
@@ -130,13 +131,16 @@ def leg_traffic():
     return LEG_TRAFFIC_BYTES
 
 
-def spec_for(precision: int, n_hist: int = N_HIST, n_s: int = N_S, seed: int = 0, warm: int | None = None) -> W.ProblemSpec:
+def spec_for(precision: int, n_hist: int = N_HIST, n_s: int | None = None, seed: int = 0,
+             warm: int | None = None) -> W.ProblemSpec:
     """The benchmark workload; source iteration starts from the previous step's collided flux
     (the same fixed point, fewer sweeps)."""
     warm = WARM if warm is None else warm
+    n_s = N_S if n_s is None else n_s
     return W.checkerboard(n_s=n_s, n_hist=n_hist, seed=seed, precision=precision).with_(sn_warm_start=warm,
                                                                                        census_order=CENSUS_ORDER,
-                                                                                       sn_accel=SN_ACCEL)
+                                                                                       sn_accel=SN_ACCEL,
+                                                                                       priv_tile=PRIV_TILE)
 
 
 def launches_per_step(spec: W.ProblemSpec, sn_iters: int) -> int:
@@ -563,6 +567,7 @@ def config_block() -> dict:
 
 
 def main():
+    global CENSUS_ORDER, SN_ACCEL, WARM, N_S, PRIV_TILE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -586,9 +591,16 @@ def main():
     ap.add_argument("--census-order", type=int, default=0, choices=[0, 1, 2],
                     help="census in slot order (0), sorted by cell (1) or by cell and phase space (2) "
                          "before the comb")
+    ap.add_argument("--lean-n-s", type=int, default=N_S,
+                    help="with --lean: the scatter limit of the checkerboard (profiling other members of the family)")
+    ap.add_argument("--lean-priv-tile", type=int, default=0,
+                    help="with --lean: the leg's shared-memory window of cells (priv_tile)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    global CENSUS_ORDER, SN_ACCEL, WARM
+    if (args.lean_n_s != N_S or args.lean_priv_tile != 0) and not args.lean:
+        ap.error("--lean-n-s and --lean-priv-tile change the workload: --lean runs only")
+    N_S = args.lean_n_s
+    PRIV_TILE = args.lean_priv_tile
     CENSUS_ORDER = args.census_order
     SN_ACCEL = args.sn_accel
     WARM = args.sn_warm
