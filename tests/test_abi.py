@@ -52,6 +52,8 @@ def _bad(spec, **kw):
     dict(nx=0), dict(ny=5000), dict(dt=0.0), dict(c=-1.0), dict(n_s=-1), dict(sn_order=6),
     dict(n_hist=0), dict(sampler=7), dict(precision=3), dict(w_min=1.5), dict(sn_max_iter=0),
     dict(sn_layout=3), dict(sn_layout=-1), dict(seg_limit=-1), dict(seg_limit=(1 << 30) + 1), dict(wait_limit=-5),
+    dict(tally_copies=-1), dict(tally_copies=65), dict(sort_every=-1), dict(leg_sort_every=-1), dict(priv_tile=-1),
+    dict(priv_tile=33),
 ])
 def test_workspace_size_rejects_bad_descriptors(hyb, mut):
     spec = W.pulse(n_hist=100)
@@ -141,5 +143,39 @@ def test_descriptor_layout_matches_header(hyb):
     names = [f for f, _ in hyb.Desc._fields_]
     txt = open(os.path.join(ROOT, "include", "hyb.h")).read()
     body = txt[txt.index("typedef struct {\n    int32_t nx, ny;"):txt.index("} hyb_problem_desc;")]
-    for n in ("seg_limit", "wait_limit", "sn_layout", "n_s_cell"):
+    for n in ("seg_limit", "wait_limit", "sn_layout", "n_s_cell", "tally_copies", "sort_every", "leg_sort_every",
+              "priv_tile"):
         assert n in names and n in body
+    # the binding's fields follow the header's order
+    order = [n for n in names if not n.startswith("pad")]
+    pos = [body.index(" " + n + ";") if (" " + n + ";") in body else body.index(n) for n in order]
+    assert pos == sorted(pos)
+
+
+def test_workspace_size_by_leg_options(hyb):
+    """The phased leg adds two buffers of saved histories (48 B each in FP32) and their sort; the
+    copies of the tally arrays scale the tally storage; the shared-memory window adds nothing."""
+    spec = W.checkerboard(n_s=2, n_hist=10_000, cells_per_block=4).with_(precision=W.FP32)
+    base = hyb.workspace_size(spec)
+    cap = 10_000 + 10_000                       # bank capacity + births
+    assert hyb.workspace_size(spec.with_(leg_sort_every=4)) - base >= 2 * cap * 48 + 2 * cap * 8
+    assert hyb.workspace_size(spec.with_(priv_tile=16)) == base
+    nc = spec.nx * spec.ny
+    grow = hyb.workspace_size(spec.with_(tally_copies=8)) - hyb.workspace_size(spec.with_(tally_copies=1))
+    assert abs(grow - 7 * 6 * nc * 8) <= 3 * 256   # each array 256-byte aligned
+
+
+def test_tuning_spaces():
+    from paper_2511_16821_gb300 import autotune
+    # the batch's space: the named values replace the defaults, the rest keep them
+    c = autotune.candidates({"block": (256,), "chunk": (2048,)})
+    assert len(c) == len(autotune.DEFAULT_SPACE["streams"]) * len(autotune.DEFAULT_SPACE["ctas_per_sm"])
+    assert all(x["block"] == 256 and x["chunk"] == 2048 for x in c)
+    # one problem's space: every combination of the named knobs, nothing else
+    c = autotune.candidates({"tally_copies": (1, 4), "priv_tile": (0, 16)}, {})
+    assert sorted((x["tally_copies"], x["priv_tile"]) for x in c) == [(1, 0), (1, 16), (4, 0), (4, 16)]
+    assert all(set(x) == {"tally_copies", "priv_tile"} for x in c)
+    n = 1
+    for v in autotune.PROBLEM_SPACE.values():
+        n *= len(v)
+    assert len(autotune.candidates(None, autotune.PROBLEM_SPACE)) == n
