@@ -307,10 +307,13 @@ hyb_status load_problems(hyb_batch* b, hyb_problem* const* problems, int32_t n) 
     // once the batch holds them (problems that left the set may already be destroyed: they get it
     // back when they are next stepped alone)
     for (hyb_problem* p : probs) {
-        p->pdl = false;
         // a bank pre-pass left pending by a failed single-problem step is ordered and forgotten:
         // the batch re-streams every slot itself
         if (hyb::drop_bank_prepass(p) != cudaSuccess) return bfail(b, HYB_ECUDA, "bank pre-pass");
+    }
+    // nothing below can fail: the members' state changes only for a batch that holds them
+    for (hyb_problem* p : probs) {
+        p->pdl = false;
         p->births_step = -1;   // the batch draws its members' births into their buffers itself
     }
     return HYB_OK;
