@@ -247,13 +247,15 @@ HYB_API hyb_status hyb_remap(hyb_problem* p, hyb_leg_stats* stats);
 /* nsteps full steps (1-4, Sec. 2.2). per_step (host, may be NULL): nsteps entries, leg
  * statistics with sn_iterations / combed / bank_size of the step, ms = whole step and
  * ms_leg / ms_sn / ms_remap per phase. A step waits for the device once inside the source
- * iteration (stop test) and, with per_step, once at its end; without per_step the call
+ * iteration (stop test), after each phase of the phased leg (leg_sort_every >= 1) and, with
+ * per_step, once at its end; without per_step the call
  * synchronises the stream at the end. Device loop bounds map to ETIMEOUT, index checks to
  * EBOUNDS. */
 HYB_API hyb_status hyb_step(hyb_problem* p, int32_t nsteps, hyb_leg_stats* per_step);
 
 /* nsteps full steps as hyb_step, without per-step statistics and without the final
- * synchronisation: the host waits only inside each source iteration (the stop test), so the call
+ * synchronisation: the host waits only inside each source iteration (the stop test) and, with
+ * the phased leg (leg_sort_every >= 1), after each of its phases, so the call
  * returns while the last step's remap may still run on the problem's stream, and work the caller
  * queues after it on that stream (the next bank upload with hyb_set_bank_native, a device copy
  * with hyb_get_tally) overlaps it. Errors of that remap (device loop bounds, index checks) stay in
