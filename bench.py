@@ -102,7 +102,7 @@ class Clocks:
 
 
 CENSUS_ORDER = 0
-PRIV_TILE = 0
+PRIV_TILE = -1          # the library's automatic window (none at the benchmark's N_s = 2)
 SN_ACCEL = 0
 WARM = 1
 
@@ -413,7 +413,8 @@ def batched_measure(n_problems: int = 256, steps: int = 3, seed: int = 0, sn_acc
     return out
 
 
-LEG_PLACEMENTS = ((0, 0), (1, 0), (4, 0), (1, 16), (4, 16), (4, 8))   # (tally_copies, priv_tile)
+# (tally_copies, priv_tile); the first is the library's default (automatic copies and window)
+LEG_PLACEMENTS = ((0, -1), (0, 0), (1, 0), (4, 0), (1, 16), (4, 16), (4, 8))
 
 
 def leg_ns_sweep(atomic_peak: float, reps: int = 5) -> list:
@@ -593,11 +594,11 @@ def main():
                          "before the comb")
     ap.add_argument("--lean-n-s", type=int, default=N_S,
                     help="with --lean: the scatter limit of the checkerboard (profiling other members of the family)")
-    ap.add_argument("--lean-priv-tile", type=int, default=0,
-                    help="with --lean: the leg's shared-memory window of cells (priv_tile)")
+    ap.add_argument("--lean-priv-tile", type=int, default=-1,
+                    help="with --lean: the leg's shared-memory window of cells (priv_tile; -1 automatic)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    if (args.lean_n_s != N_S or args.lean_priv_tile != 0) and not args.lean:
+    if (args.lean_n_s != N_S or args.lean_priv_tile != -1) and not args.lean:
         ap.error("--lean-n-s and --lean-priv-tile change the workload: --lean runs only")
     N_S = args.lean_n_s
     PRIV_TILE = args.lean_priv_tile

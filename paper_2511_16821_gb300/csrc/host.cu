@@ -266,11 +266,16 @@ struct Layout {
 // mesh) holding the largest source weight sum Q (2-D prefix sums; the first such square in row
 // order), or the initial weight where there is no source, else the mesh centre. Births and the
 // census concentrate there, so their tally additions stay in each block's shared memory.
+// priv_tile = -1 (automatic): a 16 x 16 window where every segment adds to five tallies (N_s = 0)
+// and that window holds at least a quarter of the source weight (measured on the checkerboard:
+// the leg 2.2x faster there; with N_s >= 1 the leg is issue-bound and a window does not pay).
 void choose_priv_window(const hyb_problem_desc* d, int* x0, int* y0, int* side) {
     *x0 = *y0 = *side = 0;
-    if (d->priv_tile <= 0) return;
+    const bool automatic = d->priv_tile < 0;
+    if (d->priv_tile == 0) return;
     const int nx = d->nx, ny = d->ny;
-    const int s = std::min(d->priv_tile, std::min(nx, ny));
+    if (automatic && (d->n_s != 0 || !d->Q || nx < 16 || ny < 16)) return;
+    const int s = std::min(automatic ? 16 : d->priv_tile, std::min(nx, ny));
     const double* q = d->Q ? d->Q : d->ic_cell_w;
     *side = s;
     *x0 = (nx - s) / 2;
@@ -288,6 +293,7 @@ void choose_priv_window(const hyb_problem_desc* d, int* x0, int* y0, int* side) 
                              ps[(size_t)(y + s) * (nx + 1) + x] + ps[(size_t)y * (nx + 1) + x];
             if (v > best) { best = v; *x0 = x; *y0 = y; }
         }
+    if (automatic && !(best >= 0.25 * ps[(size_t)ny * (nx + 1) + nx] && best > 0)) *side = 0;
 }
 
 int64_t eff_cap(const hyb_problem_desc* d) {
@@ -504,7 +510,7 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->tally_copies < 0 || d->tally_copies > 64) { *why = "tally_copies must be in [0, 64]"; return HYB_EINVAL; }
     if (d->sort_every < 0) { *why = "sort_every must be >= 0"; return HYB_EINVAL; }
     if (d->leg_sort_every < 0) { *why = "leg_sort_every must be >= 0"; return HYB_EINVAL; }
-    if (d->priv_tile < 0 || d->priv_tile > 32) { *why = "priv_tile must be in [0, 32]"; return HYB_EINVAL; }
+    if (d->priv_tile < -1 || d->priv_tile > 32) { *why = "priv_tile must be in [-1, 32]"; return HYB_EINVAL; }
     if (d->leg_sort_every > 0 && eff_cap(d) + d->n_hist >= ((int64_t)1 << 31)) {
         *why = "the phased leg holds fewer than 2^31 histories (bank capacity + births)";   // 31-bit saved indices
         return HYB_EINVAL;

@@ -52,7 +52,7 @@ def _bad(spec, **kw):
     dict(nx=0), dict(ny=5000), dict(dt=0.0), dict(c=-1.0), dict(n_s=-1), dict(sn_order=6),
     dict(n_hist=0), dict(sampler=7), dict(precision=3), dict(w_min=1.5), dict(sn_max_iter=0),
     dict(sn_layout=3), dict(sn_layout=-1), dict(seg_limit=-1), dict(seg_limit=(1 << 30) + 1), dict(wait_limit=-5),
-    dict(tally_copies=-1), dict(tally_copies=65), dict(sort_every=-1), dict(leg_sort_every=-1), dict(priv_tile=-1),
+    dict(tally_copies=-1), dict(tally_copies=65), dict(sort_every=-1), dict(leg_sort_every=-1), dict(priv_tile=-2),
     dict(priv_tile=33),
 ])
 def test_workspace_size_rejects_bad_descriptors(hyb, mut):
@@ -159,7 +159,7 @@ def test_workspace_size_by_leg_options(hyb):
     base = hyb.workspace_size(spec)
     cap = 10_000 + 10_000                       # bank capacity + births
     assert hyb.workspace_size(spec.with_(leg_sort_every=4)) - base >= 2 * cap * 48 + 2 * cap * 8
-    assert hyb.workspace_size(spec.with_(priv_tile=16)) == base
+    assert hyb.workspace_size(spec.with_(priv_tile=16)) == base == hyb.workspace_size(spec.with_(priv_tile=0))
     nc = spec.nx * spec.ny
     grow = hyb.workspace_size(spec.with_(tally_copies=8)) - hyb.workspace_size(spec.with_(tally_copies=1))
     assert abs(grow - 7 * 6 * nc * 8) <= 3 * 256   # each array 256-byte aligned
