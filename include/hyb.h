@@ -156,8 +156,9 @@ typedef struct {
                                  Q (else the initial weight) is largest -- in shared memory and
                                  adds them to its global copy once, at its end (integer sums: the
                                  results do not change). -1: automatic -- a 16 x 16 window when
-                                 n_s = 0 and it holds at least a quarter of the weight of Q, else
-                                 none. Not used by the phased leg or batches */
+                                 n_s = 0 and it holds at least a quarter of the weight of Q and
+                                 four times its share of the area, else none. Not used by the
+                                 phased leg or batches */
     int32_t pad4;
 } hyb_problem_desc;
 

@@ -267,8 +267,10 @@ struct Layout {
 // order), or the initial weight where there is no source, else the mesh centre. Births and the
 // census concentrate there, so their tally additions stay in each block's shared memory.
 // priv_tile = -1 (automatic): a 16 x 16 window where every segment adds to five tallies (N_s = 0)
-// and that window holds at least a quarter of the source weight (measured on the checkerboard:
-// the leg 2.2x faster there; with N_s >= 1 the leg is issue-bound and a window does not pay).
+// and the source is concentrated there -- the window holds at least a quarter of the source
+// weight and at least four times its share of the area (measured on the checkerboard: the leg
+// 2.2x faster there; with N_s >= 1 the leg is issue-bound, and with a spread source the additions
+// do not crowd any window, so a window does not pay).
 void choose_priv_window(const hyb_problem_desc* d, int* x0, int* y0, int* side) {
     *x0 = *y0 = *side = 0;
     const bool automatic = d->priv_tile < 0;
@@ -293,7 +295,9 @@ void choose_priv_window(const hyb_problem_desc* d, int* x0, int* y0, int* side) 
                              ps[(size_t)(y + s) * (nx + 1) + x] + ps[(size_t)y * (nx + 1) + x];
             if (v > best) { best = v; *x0 = x; *y0 = y; }
         }
-    if (automatic && !(best >= 0.25 * ps[(size_t)ny * (nx + 1) + nx] && best > 0)) *side = 0;
+    const double total = ps[(size_t)ny * (nx + 1) + nx];
+    const double area_share = (double)s * s / ((double)nx * ny);
+    if (automatic && !(best > 0 && best >= 0.25 * total && best >= 4.0 * area_share * total)) *side = 0;
 }
 
 int64_t eff_cap(const hyb_problem_desc* d) {

@@ -62,7 +62,7 @@ class ProblemSpec:
     sort_every: int = 0             # census_order >= 1: sort on the steps n with n mod sort_every == 0 (0, 1: all)
     leg_sort_every: int = 0         # 0: fused leg; K >= 1: phases of K segments, live histories sorted by cell between
     priv_tile: int = -1             # fused leg: a window of priv_tile^2 cells' tallies in each CTA's shared memory
-                                    # (-1: 16 x 16 where N_s = 0 and the source is concentrated, else none)
+                                    # (-1: 16 x 16 where N_s = 0 and the source is concentrated there, else none)
     name: str = field(default="problem")
 
     @property
