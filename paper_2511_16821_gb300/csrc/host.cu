@@ -511,6 +511,10 @@ hyb_status validate(const hyb_problem_desc* d, std::string* why) {
     if (d->sn_order != 4 && d->sn_order != 8) { *why = "sn_order must be 4 or 8"; return HYB_EINVAL; }
     if (d->sn_max_iter < 1) { *why = "sn_max_iter must be >= 1"; return HYB_EINVAL; }
     if (d->census_order < 0 || d->census_order > 2) { *why = "census_order must be 0, 1 or 2"; return HYB_EINVAL; }
+    if (d->census_order >= 1 && stage_slots(d, eff_cap(d)) >= ((int64_t)1 << 32)) {
+        *why = "a sorted census holds fewer than 2^32 remap slots";   // 32-bit slot indices in the sort
+        return HYB_EINVAL;
+    }
     if (d->tally_copies < 0 || d->tally_copies > 64) { *why = "tally_copies must be in [0, 64]"; return HYB_EINVAL; }
     if (d->sort_every < 0) { *why = "sort_every must be >= 0"; return HYB_EINVAL; }
     if (d->leg_sort_every < 0) { *why = "leg_sort_every must be >= 0"; return HYB_EINVAL; }

@@ -53,7 +53,7 @@ def _bad(spec, **kw):
     dict(n_hist=0), dict(sampler=7), dict(precision=3), dict(w_min=1.5), dict(sn_max_iter=0),
     dict(sn_layout=3), dict(sn_layout=-1), dict(seg_limit=-1), dict(seg_limit=(1 << 30) + 1), dict(wait_limit=-5),
     dict(tally_copies=-1), dict(tally_copies=65), dict(sort_every=-1), dict(leg_sort_every=-1), dict(priv_tile=-2),
-    dict(priv_tile=33),
+    dict(priv_tile=33), dict(census_order=1, remap_variant=1, census_cap=(1 << 31) - 1, n_hist=(1 << 31) - 1),
 ])
 def test_workspace_size_rejects_bad_descriptors(hyb, mut):
     spec = W.pulse(n_hist=100)
