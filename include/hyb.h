@@ -198,6 +198,12 @@ typedef struct hyb_problem hyb_problem;
 /* Device workspace bytes a problem needs (banks, mesh, tallies, CDFs, S_N state). */
 HYB_API hyb_status hyb_workspace_size(const hyb_problem_desc* desc, size_t* bytes);
 
+/* The window of cells whose tallies the fused MC leg keeps in each CTA's shared memory for this
+ * descriptor (priv_tile; -1 resolved by its rule): first cell (*x0, *y0) and side *side (0: no
+ * window). Host computation only (no device needed); EINVAL for an invalid descriptor or a NULL
+ * output. */
+HYB_API hyb_status hyb_priv_window(const hyb_problem_desc* desc, int32_t* x0, int32_t* y0, int32_t* side);
+
 /* Create a problem. workspace: device memory of >= hyb_workspace_size bytes, 256-byte
  * aligned, owned by the caller and kept alive until hyb_destroy_problem; NULL lets the library
  * allocate (and later free) it. cuda_stream: a cudaStream_t (borrowed; NULL = legacy stream).

@@ -834,6 +834,17 @@ hyb_status hyb_workspace_size(const hyb_problem_desc* d, size_t* bytes) {
     return HYB_OK;
 }
 
+hyb_status hyb_priv_window(const hyb_problem_desc* d, int32_t* x0, int32_t* y0, int32_t* side) {
+    std::string why;
+    hyb_status s = validate(d, &why);
+    if (s != HYB_OK) return fail(nullptr, s, why);
+    if (!x0 || !y0 || !side) return fail(nullptr, HYB_EINVAL, "output is NULL");
+    int a = 0, b = 0, c = 0;
+    choose_priv_window(d, &a, &b, &c);
+    *x0 = a; *y0 = b; *side = c;
+    return HYB_OK;
+}
+
 hyb_status hyb_sobol_table(int32_t ndims, uint32_t* out) {
     if (ndims < 1 || ndims > HYB_SOBOL_DIMS || !out) return fail(nullptr, HYB_EINVAL, "ndims out of range");
     std::memcpy(out, sobol_table_host(), (size_t)ndims * 32 * sizeof(uint32_t));

@@ -80,6 +80,7 @@ def lib():
         L.hyb_last_error.restype = C.c_char_p
         L.hyb_last_error.argtypes = [P]
         L.hyb_workspace_size.argtypes = [C.POINTER(Desc), C.POINTER(C.c_size_t)]
+        L.hyb_priv_window.argtypes = [C.POINTER(Desc)] + [C.POINTER(C.c_int32)] * 3
         L.hyb_create_problem.argtypes = [C.POINTER(Desc), P, C.c_size_t, P, C.POINTER(P)]
         L.hyb_destroy_problem.argtypes = [P]
         L.hyb_mc_leg.argtypes = [P, C.POINTER(Stats)]
@@ -166,6 +167,14 @@ def workspace_size(spec: ProblemSpec) -> int:
     n = C.c_size_t(0)
     _check(lib().hyb_workspace_size(C.byref(d), C.byref(n)))
     return int(n.value)
+
+
+def priv_window(spec: ProblemSpec) -> tuple[int, int, int]:
+    """(x0, y0, side) of the leg's shared-memory window for this problem (side 0: none)."""
+    d, keep = make_desc(spec)
+    x0, y0, s = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+    _check(lib().hyb_priv_window(C.byref(d), C.byref(x0), C.byref(y0), C.byref(s)))
+    return x0.value, y0.value, s.value
 
 
 class Problem:

@@ -179,3 +179,18 @@ def test_tuning_spaces():
     for v in autotune.PROBLEM_SPACE.values():
         n *= len(v)
     assert len(autotune.candidates(None, autotune.PROBLEM_SPACE)) == n
+
+
+def test_priv_window_choice(hyb):
+    """The leg's shared-memory window: the densest square of the source (the checkerboard's
+    source block, cells 48..63 of 112), automatic only at N_s = 0 with a concentrated source."""
+    cb0 = W.checkerboard(n_s=0, n_hist=1000)
+    assert hyb.priv_window(cb0) == (48, 48, 16)                      # automatic (the default, -1)
+    assert hyb.priv_window(cb0.with_(priv_tile=0)) == (0, 0, 0)
+    x0, y0, s = hyb.priv_window(cb0.with_(priv_tile=8))              # inside the block
+    assert s == 8 and 48 <= x0 <= 56 and 48 <= y0 <= 56
+    assert hyb.priv_window(W.checkerboard(n_s=2, n_hist=1000))[2] == 0   # N_s >= 1: none by default
+    assert hyb.priv_window(W.checkerboard(n_s=2, n_hist=1000).with_(priv_tile=16)) == (48, 48, 16)
+    uni = W.homogeneous(n=32, Q=1.0, n_s=0)
+    assert hyb.priv_window(uni)[2] == 0                              # spread source: none
+    assert hyb.priv_window(W.homogeneous(n=12, Q=1.0, n_s=0).with_(priv_tile=16)) == (0, 0, 12)   # at most the mesh
