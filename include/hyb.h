@@ -134,7 +134,8 @@ typedef struct {
                                  solve's strip pipeline, the census sort's look-back -- before it
                                  gives up and the call returns HYB_ETIMEOUT; 0 = 2^22 (about
                                  0.1 s per wait) */
-    int32_t tally_copies;     /* copies of the fixed-point tally arrays the leg's warps add into
+    int32_t tally_copies;     /* (no counterpart in the paper; results are the same) copies of the
+                                 fixed-point tally arrays the leg's warps add into
                                  (warp index mod copies; the normalisation sums them exactly, so
                                  the tallies do not depend on it): 0 automatic (4 while they take
                                  at most 32 MB, fewer above), else 1..64 */
@@ -142,7 +143,8 @@ typedef struct {
                                  n mod sort_every == 0 only (0 or 1: every step); the other steps
                                  comb the census in slot order. A batch rejects sort_every > 1
                                  (its step graphs replay one sort decision) */
-    int32_t leg_sort_every;   /* 0: the fused MC leg (each warp lane takes a history to its end,
+    int32_t leg_sort_every;   /* (no counterpart in the paper; results are the same)
+                                 0: the fused MC leg (each warp lane takes a history to its end,
                                  then the next one). K >= 1: the phased leg -- every history
                                  advances at most K segments per phase, and between phases the
                                  live histories are compacted and sorted by cell (stable), so
@@ -150,7 +152,8 @@ typedef struct {
                                  the fused leg's bit for bit; the host waits once per phase. A
                                  leg over a history range (hyb_mc_leg_range) stays fused; a
                                  batch rejects K >= 1 */
-    int32_t priv_tile;        /* 0: every tally addition of the fused MC leg goes to the global
+    int32_t priv_tile;        /* (no counterpart in the paper; results are the same)
+                                 0: every tally addition of the fused MC leg goes to the global
                                  tally copies. 1..32: each CTA keeps the tallies of a square window
                                  of priv_tile x priv_tile cells -- placed where the source weight
                                  Q (else the initial weight) is largest -- in shared memory and
