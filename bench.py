@@ -202,10 +202,11 @@ def run_gpu(args, rank: int, world: int) -> dict:
 
 
 def leg_profile(prec: int, reps: int = 5) -> dict:
-    """Device time of the MC leg alone (events recorded by the library around the leg kernel and
-    its normalisation, on the problem's stream; the leg's source births were drawn beside the
-    previous step's collided solve, as in a step) at the benchmark workload, with the leg's inputs
-    (the steady-state census bank, step 2) and raw tallies for the error against the oracle."""
+    """The benchmark leg on its steady-state census bank (step 2; the leg's source births drawn
+    beside the previous step's collided solve, as in a step): the inputs of the oracle's all-cores
+    leg (bank, step, workload) and the raw tallies for the FP32 error against it, with the leg's
+    device time (events around the leg kernel and its normalisation; the roofline itself takes
+    the leg kernel's time inside the timed steps)."""
     import torch
     from paper_2511_16821_gb300 import hyb
     spec = spec_for(prec)
